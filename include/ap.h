@@ -1,0 +1,219 @@
+/*
+ * ap.h -- C ABI of the GB300 (sm_103a) adaptive-precision EAM+ACE force library.
+ *
+ * The library evaluates, on one GPU, the adaptive-precision (AP) energy of arXiv
+ * 2505.12958 (Sec. 2.2.3, Eq. energy_hyb)
+ *     E = sum_i [ w_i E_i^ACE + (1 - w_i) E_i^EAM ] + sum_i V_ind(r_i)
+ * and its exact negative gradient, and integrates Newton's equations with velocity
+ * Verlet.  w_i is the ACE weight; the paper's switching parameter is lambda_i = 1 - w_i
+ * (lambda = 1 is the fast EAM description).  One MD step is: cell binning and
+ * neighbour list (rebuilt when an atom has moved more than skin/2), ACE weights and
+ * stream compaction of the atoms with w_i > 0, the EAM density / embedding / pair pass
+ * (Sec. 2.2.1, Eq. energy_eam; Appendix B forms), the ACE pass on the compacted atoms
+ * (Sec. 2.2.2, Eq. energy_ace), the blend with the spherical indenter (Sec. 2.1,
+ * Eq. V_indenter) and the indentation load (Sec. 3.1, Eq. P_ind), and the FP64
+ * velocity-Verlet update.
+ *
+ * Conventions.  Units eV, Angstrom, fs, amu.  Positions and velocities are FP64,
+ * forces FP32, energies, virial and load FP64.  Arrays of vectors are row-major n x 3
+ * (AoS), like numpy / torch (n, 3) tensors.  "device" pointers are CUDA device memory
+ * on the current device, "host" pointers are host memory (pinned memory makes the
+ * copies asynchronous).  A cuda stream argument of NULL means the stream given to
+ * ap_init.  Every call returns an ap_status; nothing aborts, prints, or traps on the
+ * device.  Device-side errors (domain, capacity) are sticky and reported by the next
+ * synchronising call (ap_energy, ap_check).  Only ap_init, ap_energy, ap_check,
+ * ap_get_state, ap_get_forces, ap_compute_forces_host and ap_destroy synchronise.
+ * A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef AP_H
+#define AP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AP_API_VERSION 1
+
+typedef struct ap_ctx ap_ctx;
+
+typedef enum {
+    AP_OK = 0,
+    AP_ERR_ARG = -1,       /* invalid argument or unsupported parameter              */
+    AP_ERR_OOM = -2,       /* device or host allocation failed                       */
+    AP_ERR_CUDA = -3,      /* a CUDA runtime call failed (text in ap_last_error)     */
+    AP_ERR_DOMAIN = -4,    /* phi2 <= 1e-3, rho < 0 or a non-finite value; atom index in ap_last_error */
+    AP_ERR_CAPACITY = -5,  /* neighbour capacity exceeded; the next call rebuilds with a larger one */
+    AP_ERR_TIMEOUT = -6,   /* reserved for bounded waits                             */
+    AP_ERR_STATE = -7      /* call not valid in the current state                   */
+} ap_status;
+
+/* Precision of the atomic-base contraction A_nlm = sum_j g_n(r_ij) Y_lm(rhat_ij). */
+enum {
+    AP_ACE_FP32 = 0,       /* FP32 FMA (default)                                     */
+    AP_ACE_TC_TF32X3 = 1,  /* tensor cores, mma.sync TF32 with hi/lo split, 3 products */
+    AP_ACE_TC_BF16 = 2,    /* tensor cores, BF16 inputs, FP32 accumulate             */
+    AP_ACE_TC_FP16 = 3,    /* tensor cores, FP16 inputs, FP32 accumulate             */
+    AP_ACE_FP64 = 4        /* FP64 FMA                                               */
+};
+
+/* Potential parameters (copied by ap_init).
+ * EAM, Appendix B: xi(x) = a1 sqrt(x) + a2 x^2 + Delta xi (Eqs. eam_F_Marinica,
+ * tungsten_F_up); Phi(r) = sum_i a_i (d_i - r)^3 Theta(d_i - r) (Eq. eam_Phi_Marinica),
+ * replaced by the ZBL form below r_lo and by sum_m b_m r^m on [r_lo, r_hi] when
+ * eam_zbl = 1 (Eq. tungsten_Phi_up); zeta_0(r) = same cubic-knot form (Eq.
+ * eam_rho_Marinica), held at zeta_0(r_clamp) for r <= r_clamp when r_clamp > 0
+ * (Eq. tungsten_rho_up).
+ * ACE, Sec. 2.2.2: E_i = phi1 + sqrt(phi2), phi_p = c_p0 + sum_v c_p[v] B_v (Eq.
+ * energy_ace), B_v products of A_nlm = (1/nref) sum_j g_n(r_ij) Y_lm(rhat_ij) with
+ * g_n = T_n(2r/rc - 1) (1 + cos(pi r/rc))/2 and real orthonormal Y_lm.  The basis is a
+ * host table ace_idx (ace_nfunc x 7 ints): (nu, n1, l1, n2, l2, n3, l3), unused -1;
+ * nu = 1: A_n00; nu = 2: sum_m A_n1lm A_n2lm; nu = 3: sum_m1m2m3 G A A A with the real
+ * Gaunt coefficients G.  Supported: ace_nmax = 8, ace_lmax = 4, nu <= 3. */
+typedef struct {
+    int eam_n_phi;
+    double eam_phi_a[32], eam_phi_d[32];
+    int eam_n_rho;
+    double eam_rho_a[16], eam_rho_d[16];
+    double eam_rho_rclamp;
+    double eam_F_a1, eam_F_a2, eam_F_dxi;
+    int eam_zbl;
+    double eam_zbl_Z, eam_zbl_eps0, eam_zbl_a, eam_r_lo, eam_r_hi, eam_b[6];
+
+    double ace_rc, ace_nref;
+    int ace_nmax, ace_lmax, ace_nfunc;
+    const int* ace_idx;          /* host, ace_nfunc x 7, copied                     */
+    const double* ace_c1;        /* host, ace_nfunc, copied                         */
+    const double* ace_c2;        /* host, ace_nfunc, copied                         */
+    double ace_c1_0, ace_c2_0;
+    int ace_precision;           /* AP_ACE_*                                        */
+
+    double mass_amu;             /* one species per context                         */
+    double skin;                 /* neighbour-list skin (Angstrom), e.g. 1.0         */
+} ap_potential;
+
+/* Box: edge vectors as rows of h (triclinic allowed), lower corner at origin.  In a
+ * non-periodic direction the box only sizes the cell grid; atoms may leave it. */
+typedef struct {
+    double h[9];
+    double origin[3];
+    int periodic[3];
+} ap_box;
+
+/* ACE weight w_i.  AP_REGION_NONE: w = 0 (pure EAM).  AP_REGION_CONST: w = w_const.
+ * AP_REGION_EXPLICIT: w from a host array (frozen between ap_set_weights calls).
+ * AP_REGION_SPHERE: w = S(d), d = |r_i - c| (minimum image in periodic directions),
+ * S = 1 for d < r_in, (1 + cos(pi (d - r_in)/r_switch))/2 up to r_in + r_switch, 0
+ * beyond; the force then carries -grad w_i (E_i^ACE - E_i^EAM).  A sphere centred on
+ * the surface point under the tip is the hemisphere of the paper's fixed zones
+ * (Sec. 2.2.3).  follow_indenter moves c with the indenter.  ACE runs on w_i > 0. */
+enum { AP_REGION_NONE = 0, AP_REGION_SPHERE = 1, AP_REGION_EXPLICIT = 2, AP_REGION_CONST = 3 };
+typedef struct {
+    int kind;
+    double center[3];
+    double r_in, r_switch;
+    int follow_indenter;
+    const double* w_explicit;    /* host, n, for AP_REGION_EXPLICIT, copied          */
+    double w_const;
+} ap_region;
+
+/* Spherical indenter, Eq. V_indenter: V = (K/3) Theta(R - d) (R - d)^3, d = |r - c(t)|,
+ * c(t) = center0 - vel t.  load = sum_i F_ind,i . dir (Eq. P_ind; dir is the unit
+ * indentation direction, e.g. (0,0,-1)). */
+typedef struct {
+    int enabled;
+    double center0[3];
+    double vel[3];               /* Angstrom/fs */
+    double R, K;
+    double dir[3];
+} ap_indenter;
+
+/* Results of the last force evaluation (ap_energy). */
+typedef struct {
+    double e_total;              /* e_pot + e_ind                                    */
+    double e_pot;                /* sum_i w_i E_i^ACE + (1 - w_i) E_i^EAM             */
+    double e_ind;                /* sum_i V_ind(r_i)                                 */
+    double e_kin;                /* sum_i m v_i^2 / 2 of the current velocities       */
+    double virial[6];            /* xx yy zz xy xz yz of -sum_i sum_j r_ij (x) dE_i/dr_ij */
+    double load;                 /* Eq. P_ind                                        */
+    double time_fs;
+    long long step;
+    int n_ace;                   /* atoms with w > 0                                 */
+    int n_atoms;
+} ap_report;
+
+/* Create a context on the current CUDA device: copies parameters and the host arrays
+ * pos (n x 3), vel (n x 3 or NULL = 0) and fixed (n bytes, nonzero = frozen, or NULL),
+ * builds the tables, allocates device memory, and evaluates nothing yet.  n >= 1.
+ * Errors: AP_ERR_ARG (bad parameter, box thinner than half the list cutoff),
+ * AP_ERR_OOM, AP_ERR_CUDA.  Synchronises. */
+ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* region,
+                  const ap_indenter* indenter, int n_atoms, const double* pos,
+                  const double* vel, const unsigned char* fixed, void* stream, ap_ctx** out);
+
+/* One AP force evaluation of the internal positions, or of d_pos (device, n x 3 FP64;
+ * copied into the context state first) when not NULL.  Forces (n x 3 FP32) go to
+ * d_force (device) when not NULL and to the context.  Asynchronous. */
+ap_status ap_compute_forces(ap_ctx* ctx, const double* d_pos, float* d_force, void* stream);
+
+/* The same with host buffers: h_pos (n x 3 FP64) is copied in, h_force (n x 3 FP32)
+ * and *h_energy (total energy) are copied out.  Synchronises. */
+ap_status ap_compute_forces_host(ap_ctx* ctx, const double* h_pos, float* h_force,
+                                 double* h_energy, void* stream);
+
+/* n_steps velocity-Verlet steps of dt_fs on the library-owned positions and velocities.
+ * Fixed atoms keep x and v.  The indenter (and a following region) advance with time.
+ * Asynchronous. */
+ap_status ap_step(ap_ctx* ctx, int n_steps, double dt_fs, void* stream);
+
+/* Totals of the last force evaluation; d_e_atom (device, n FP64, nullable) receives
+ * the per-atom energies E_i + V_ind(r_i).  Synchronises; returns sticky device errors. */
+ap_status ap_energy(ap_ctx* ctx, ap_report* out, double* d_e_atom);
+
+/* Synchronise and return the sticky device error status (AP_OK if none). */
+ap_status ap_check(ap_ctx* ctx);
+
+/* Host copies of positions, velocities (n x 3, either may be NULL) and time. */
+ap_status ap_get_state(ap_ctx* ctx, double* x, double* v, double* t_fs);
+/* Replace positions / velocities (host, n x 3, either may be NULL) and time; forces a
+ * neighbour rebuild and a fresh force evaluation before the next step. */
+ap_status ap_set_state(ap_ctx* ctx, const double* x, const double* v, double t_fs);
+/* Host copy of the last forces (n x 3 FP32). */
+ap_status ap_get_forces(ap_ctx* ctx, float* f);
+/* Host copy of the current weights w_i (n FP64). */
+ap_status ap_get_weights(ap_ctx* ctx, double* w);
+/* Replace explicit weights (AP_REGION_EXPLICIT contexts only; host, n). */
+ap_status ap_set_weights(ap_ctx* ctx, const double* w);
+
+/* Per-stage CUDA-event timing of later calls (enable = 1) and its readout: ms[k] is
+ * the accumulated time of stage k over launches[k] launches, stages AP_STAGE_*. */
+enum { AP_STAGE_NEIGHBOR = 0, AP_STAGE_PREPARE = 1, AP_STAGE_EAM_DENSITY = 2,
+       AP_STAGE_EAM_FORCE = 3, AP_STAGE_ACE = 4, AP_STAGE_BLEND = 5, AP_STAGE_INTEGRATE = 6,
+       AP_NSTAGE = 7 };
+ap_status ap_profile(ap_ctx* ctx, int enable);
+ap_status ap_profile_read(ap_ctx* ctx, double* ms, long long* launches);
+
+/* Number of kernels this context has launched since creation. */
+long long ap_launch_count(const ap_ctx* ctx);
+/* Neighbour-list capacity per atom and the number of list rebuilds so far. */
+ap_status ap_neighbor_info(ap_ctx* ctx, int* capacity, long long* rebuilds);
+/* Device bytes a context of n atoms needs (an upper estimate). */
+size_t ap_footprint_bytes(const ap_potential* pot, int n_atoms, double ace_fraction);
+/* Text of the last error of ctx (or of the last failed ap_init when ctx is NULL). */
+const char* ap_last_error(const ap_ctx* ctx);
+void ap_destroy(ap_ctx* ctx);
+int ap_version(void);
+
+/* Host-side table generators, exposed so that they can be checked without a GPU.
+ * ap_gaunt_real: real Gaunt coefficient integral(Y_l1m1 Y_l2m2 Y_l3m3) from the Racah
+ * formula for Wigner 3j symbols and the complex-to-real transform (l <= 4).
+ * ap_eam_table_eval: the piecewise polynomials the kernels evaluate (which = 0: Phi,
+ * 1: zeta), re-expanded in FP64 about each interval's midpoint, evaluated in FP64. */
+ap_status ap_gaunt_real(int l1, int m1, int l2, int m2, int l3, int m3, double* out);
+ap_status ap_eam_table_eval(const ap_potential* pot, int which, double r, double* f, double* df);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -528,12 +528,23 @@ static void nl_push(void* ctx, int i, int j, const double* r) {
 /* ------------------------------------------------------------------------- */
 /* weights and indenter                                                        */
 /* ------------------------------------------------------------------------- */
-static void region_weight(const or_region* reg, int i, const double* x, double* w, double* gw) {
+/* Cosine switch of the distance to the region centre.  In periodic directions the
+ * distance is taken to the nearest image of the centre (fractional coordinates rounded). */
+static void region_weight(const or_region* reg, int i, const or_system* sys, const double* Minv,
+                          double* w, double* gw) {
     gw[0] = gw[1] = gw[2] = 0.0;
     if (reg == NULL) { *w = 0.0; return; }
     if (reg->kind == 0) { *w = reg->w_explicit ? reg->w_explicit[i] : 0.0; return; }
     if (reg->kind == 2) { *w = reg->w_const; return; }
+    const double* x = sys->x + 3 * i;
     double d[3] = {x[0] - reg->center[0], x[1] - reg->center[1], x[2] - reg->center[2]};
+    double s[3];
+    for (int k = 0; k < 3; ++k) s[k] = d[0] * Minv[0 + k] + d[1] * Minv[3 + k] + d[2] * Minv[6 + k];
+    for (int k = 0; k < 3; ++k)
+        if (sys->periodic[k]) {
+            double m = floor(s[k] + 0.5);
+            for (int c = 0; c < 3; ++c) d[c] -= m * sys->h[3 * k + c];
+        }
     double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     if (r < reg->r_in) { *w = 1.0; return; }
     if (r >= reg->r_in + reg->r_sw) { *w = 0.0; return; }
@@ -597,7 +608,7 @@ int or_evaluate(const or_system* sys, const or_eam* eam, const or_ace* ace,
         long s0 = start[q], s1 = start[q + 1];
         int nn = (int)(s1 - s0);
         double w;
-        region_weight(reg, i, sys->x + 3 * i, &w, gw + 3 * q);
+        region_weight(reg, i, sys, G.Minv, &w, gw + 3 * q);
         wv[q] = w;
         double u = 1.0 - w;
         if (u > 0.0 && eam) {
