@@ -1,0 +1,345 @@
+"""Benchmark: adaptive-precision (AP) EAM+ACE MD steps on one GB300 (or N replicas).
+
+Workload: the W BCC (001) nanoindentation slab, 40 x 40 x 40 cells = 128,000 atoms,
+periodic x/y, free top surface, bottom 3 layers fixed, spherical indenter R = 40 A,
+K = 10 eV/A^3 moving at 10 m/s, 300 K Maxwell velocities, ACE hemisphere of radius
+50 A plus a 4 A cosine shell (21,241 atoms with w > 0), velocity Verlet with dt = 1 fs.
+One step = one full pass of the hot path (neighbour check / rebuild, weights and
+compaction, EAM, ACE, blend with indenter, FP64 integration).
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle (the reference arm of
+this build) on bounded samples of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "AP atom-steps/s vs pure-ACE/EAM at ≤1e-4 eV/Å force err; p50/p99 latency"
+UNIT = "atom-steps/s"
+WORKLOAD = "W BCC (001) nanoindentation slab 40x40x40 cells, 128000 atoms, ACE hemisphere r=50+4 A (21241 atoms), indenter R=40 A K=10 eV/A^3 v=10 m/s, 300 K, dt=1 fs"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(torch, seconds, device):
+    """The slowest rank's time (replicas run the same workload; the job ends with the last)."""
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return seconds
+    t = torch.tensor([seconds], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world_size, atoms, steps, seconds):
+    """Whole-job atom-steps/s: every replica advances its own copy of the workload."""
+    return world_size * atoms * steps / seconds
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.p = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                       "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_ctx(ap, c, region="cfg", skin=1.0):
+    reg = c["region"] if region == "cfg" else region
+    return ap.APContext(c["eam"], c["ace"], c["box"], c["x"], c["v"], c["fixed"], reg, c["indenter"], c["ind_vel"],
+                        c["mass"], skin)
+
+
+def timed_steps(torch, ctx, steps, flush, profile=False):
+    """Per-step device time (CUDA events on the launch stream), L2 flushed before each step."""
+    s = torch.cuda.current_stream()
+    evs = []
+    if profile:
+        ctx.profile(True)
+        ctx.profile_read()
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        ctx.step(1, 1.0)
+        b.record(s)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    prof = ctx.profile_read() if profile else None
+    if profile:
+        ctx.profile(False)
+    return ms, prof
+
+
+def cpu_baseline(c, nthreads=0):
+    """One full FP64 oracle AP force evaluation of the workload on the host cores."""
+    import oracle
+    oracle.build()
+    cores = oracle.num_threads() if nthreads <= 0 else nthreads
+    t = time.perf_counter()
+    r = oracle.evaluate(c["x"], c["box"], c["eam"], c["ace"], c["region"], c["indenter"], nthreads=nthreads)
+    dt = time.perf_counter() - t
+    assert r["status"] == 0
+    return {"value": len(c["x"]) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "one full FP64 AP force evaluation of all %d atoms (%.2f s), OpenMP over atoms" % (len(c["x"]), dt)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    c = synth.configs.w_slab()
+    n = len(c["x"])
+    frac = 32
+    rng = np.random.default_rng(4242)
+
+    def one():
+        centers = rng.choice(n, size=n // frac, replace=False)
+        t = time.perf_counter()
+        r = oracle.evaluate(c["x"], c["box"], c["eam"], c["ace"], c["region"], c["indenter"], centers=centers)
+        assert r["status"] == 0
+        return len(centers), time.perf_counter() - t
+
+    for _ in range(args.warmup):
+        one()
+    tot_a, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        a, t = one()
+        tot_a += a
+        tot_t += t
+    value = tot_a / tot_t
+    cores = oracle.num_threads()
+    sample = "per step: the AP energy terms of a random 1/%d of the %d atoms (%d centres, seeded), FP64 oracle" % (frac, n, n // frac)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "atoms": n, "l2": "not applicable (host)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def ace_kernel_roofline(prof, n_steps, c, pk, peak_src, ctx_atoms_in_rc):
+    from paper_2505_12958_gb300.workload import ace_flops_per_atom
+    ms, nl = prof["ace"]
+    avg_s = ms / max(1, nl) / 1000.0
+    flops = sum(ace_flops_per_atom(k) for k in ctx_atoms_in_rc)
+    achieved = flops / avg_s / 1e12
+    peak = 152 * 128 * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "k_ace_traffic.json")
+    if os.path.exists(tf):
+        from paper_2505_12958_gb300.buildlib import source_hash
+        rec = json.load(open(tf))
+        if rec.get("source_hash") == source_hash():
+            traffic = rec["dram_bytes_per_launch"]
+    return {"kernel": "k_ace", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock, %s peaks file)"
+                           % (float(pk.get("sm_max_mhz", 2070.0)), peak_src),
+            "algorithmic_flops_per_launch": int(flops), "avg_launch_ms": avg_s * 1000.0}
+
+
+def neighbors_in_ace_cutoff(c):
+    """Neighbour counts within the ACE cutoff of the atoms with w > 0 (host, for the flop count)."""
+    from scipy.spatial import cKDTree
+    x = c["x"]
+    reg = c["region"]
+    d = np.linalg.norm(x - np.asarray(reg["center"]), axis=1)
+    ace = np.where(d < reg["r_in"] + reg["r_sw"])[0]
+    L = np.asarray(c["box"]["h"]).reshape(3, 3)
+    boxsize = [L[0, 0], L[1, 1], 1e9]
+    xx = x.copy()
+    xx[:, 2] -= xx[:, 2].min()
+    t = cKDTree(xx, boxsize=boxsize)
+    cnt = t.query_ball_point(xx[ace], r=c["ace"]["rc"], return_length=True) - 1
+    return cnt
+
+
+def main():
+    ap_ = argparse.ArgumentParser()
+    ap_.add_argument("--gpus", type=int, default=1)
+    ap_.add_argument("--steps", type=int, default=200)
+    ap_.add_argument("--warmup", type=int, default=10)
+    ap_.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap_.add_argument("--no-cpu-baseline", action="store_true")
+    ap_.add_argument("--variants", default="ace,eam", help="extra single-potential runs (comma list or 'none')")
+    args = ap_.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2505_12958_gb300 as ap
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    ap.build()
+    c = synth.configs.w_slab()
+    n = len(c["x"])
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    pk, peak_src = peaks()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- AP (the metric) ----
+    ctx = make_ctx(ap, c)
+    ctx.step(args.warmup, 1.0)
+    ctx.check()
+    barrier()
+    l0 = ctx.launch_count
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        ms, prof = timed_steps(torch, ctx, args.steps, flush, profile=True)
+        barrier()
+        wall = time.perf_counter() - t0
+    launches = ctx.launch_count - l0
+    ctx.check()
+    rep = ctx.energy()
+    dev_s = max_over_ranks(torch, sum(ms) / 1000.0, "cuda")
+    value = aggregate_rate(ws, n, args.steps, dev_s)
+    clocks = clk.summary()
+
+    # ---- end to end through the host API (pinned buffers, copies inside the timed region) ----
+    pos_h = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
+    f_h = torch.empty((n, 3), dtype=torch.float32, pin_memory=True)
+    x_now, _, _ = ctx.get_state()
+    pos_h.numpy()[:] = x_now
+    pn, fn = pos_h.numpy(), f_h.numpy()
+    for _ in range(3):
+        ctx.compute_forces_host(pn, fn)
+    barrier()
+    k_e2e = max(10, args.steps // 4)
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        ctx.compute_forces_host(pn, fn)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": ws * n * k_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 24 * n, "d2h_bytes_per_step": 12 * n + 16,
+           "step": "H2D positions (pinned) + AP force evaluation + D2H forces and energy, ap_compute_forces_host"}
+
+    # ---- roofline of the dominant kernel ----
+    stage_ms = {k: v[0] / max(1, v[1]) for k, v in prof.items()}
+    roof = ace_kernel_roofline(prof, args.steps, c, pk, peak_src, neighbors_in_ace_cutoff(c))
+    ctx.close()
+
+    extra = {}
+    variants = [] if args.variants == "none" else args.variants.split(",")
+    for name in variants:
+        reg = {"kind": "const", "w": 1.0} if name == "ace" else None
+        cv = make_ctx(ap, c, region=reg)
+        kk = max(5, args.steps // (8 if name == "ace" else 1))
+        cv.step(3, 1.0)
+        cv.check()
+        barrier()
+        msv, _ = timed_steps(torch, cv, kk, flush)
+        cv.check()
+        extra[name + "_only"] = {"value": n * kk / (sum(msv) / 1000.0), "unit": UNIT, "steps": kk,
+                                 "ms_per_step": sum(msv) / kk}
+        cv.close()
+
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * dev_s / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 forces / f64 integration", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "atoms": n, "n_ace": rep["n_ace"], "parallelism": "replicas" if ws > 1 else "1 GPU",
+                       "l2": "flushed before every timed step (256 MB write)", "timing": "CUDA events per step on the launch stream"},
+            "p50_ms_per_step": float(np.percentile(ms, 50)), "p99_ms_per_step": float(np.percentile(ms, 99)),
+            "stage_ms_per_step": stage_ms, "gpu_launches": launches, "clocks": clocks, "e2e": e2e, "roofline": roof,
+            "wall_s_timed_region": wall}
+    line.update(extra)
+    if "ace_only" in extra:
+        line["ap_vs_ace_speedup"] = value / extra["ace_only"]["value"]
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(c)
+    print(json.dumps(line, default=_jsonable), flush=True)
+
+
+def _jsonable(o):
+    if isinstance(o, (np.integer,)):
+        return int(o)
+    if isinstance(o, (np.floating,)):
+        return float(o)
+    if isinstance(o, np.ndarray):
+        return o.tolist()
+    raise TypeError(type(o))
+
+
+if __name__ == "__main__":
+    main()

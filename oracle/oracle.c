@@ -679,7 +679,15 @@ int or_evaluate(const or_system* sys, const or_eam* eam, const or_ace* ace,
         if (reg && reg->kind == 1 && w > 0.0 && u > 0.0)
             for (int k = 0; k < 3; ++k) forces[3 * i + k] -= gw[3 * q + k] * (eA[q] - eE[q]);
         if (ind && ind->enabled) {
+            /* the tip interacts with the nearest periodic image of each atom */
             double d[3] = {sys->x[3 * i] - ind->center[0], sys->x[3 * i + 1] - ind->center[1], sys->x[3 * i + 2] - ind->center[2]};
+            double s[3];
+            for (int k = 0; k < 3; ++k) s[k] = d[0] * G.Minv[0 + k] + d[1] * G.Minv[3 + k] + d[2] * G.Minv[6 + k];
+            for (int k = 0; k < 3; ++k)
+                if (sys->periodic[k]) {
+                    double m = floor(s[k] + 0.5);
+                    for (int c = 0; c < 3; ++c) d[c] -= m * sys->h[3 * k + c];
+                }
             double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
             if (r < ind->R && r > 0.0) {
                 double h = ind->R - r;

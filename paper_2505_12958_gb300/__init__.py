@@ -1,0 +1,272 @@
+"""GB300 (sm_103a) adaptive-precision EAM+ACE force evaluation and MD step.
+
+Python binding of the C ABI in include/ap.h.  Every step of the force evaluation runs
+in the CUDA kernels of libapforce.so; this module only marshals arguments.  PyTorch is
+used, when given, for device memory and streams (tensors are passed by pointer).
+
+    ctx = APContext(eam, ace, box, x, v=None, fixed=None, region=None, indenter=None,
+                    ind_vel=None, mass=183.84)
+    f = ctx.compute_forces()          # (n, 3) float32 on the host
+    ctx.step(100, 1.0)                # velocity Verlet, dt in fs
+    rep = ctx.energy()                # totals of the last evaluation
+
+Weights: w_i is the ACE weight; the paper's switching parameter is lambda_i = 1 - w_i.
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import _capi
+from ._capi import PRECISION, REGION, STAGES, STATUS
+
+__all__ = ["APContext", "APError", "build", "PRECISION", "STAGES", "potential_struct", "gaunt_real",
+           "eam_table_eval"]
+
+
+class APError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+def build(force=False, verbose=False):
+    from .buildlib import build as _b
+    return _b(force=force, verbose=verbose)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def potential_struct(eam, ace, mass, skin=1.0, precision="fp32"):
+    """Fill the ap_potential struct; returns (struct, keep-alive arrays)."""
+    p = _capi.Potential()
+    p.eam_n_phi = len(eam["phi_a"])
+    p.eam_n_rho = len(eam["rho_a"])
+    for k in range(p.eam_n_phi):
+        p.eam_phi_a[k] = float(eam["phi_a"][k])
+        p.eam_phi_d[k] = float(eam["phi_d"][k])
+    for k in range(p.eam_n_rho):
+        p.eam_rho_a[k] = float(eam["rho_a"][k])
+        p.eam_rho_d[k] = float(eam["rho_d"][k])
+    p.eam_rho_rclamp = float(eam.get("rho_rclamp", 0.0))
+    p.eam_F_a1, p.eam_F_a2, p.eam_F_dxi = float(eam["F_a1"]), float(eam["F_a2"]), float(eam.get("F_dxi", 0.0))
+    p.eam_zbl = int(eam.get("zbl", 0))
+    if p.eam_zbl:
+        p.eam_zbl_Z, p.eam_zbl_eps0, p.eam_zbl_a = float(eam["zbl_Z"]), float(eam["zbl_eps0"]), float(eam["zbl_a"])
+        p.eam_r_lo, p.eam_r_hi = float(eam["r_lo"]), float(eam["r_hi"])
+        for k in range(6):
+            p.eam_b[k] = float(eam["b"][k])
+    idx = np.ascontiguousarray(ace["idx"], dtype=np.int32).ravel()
+    c1, c2 = _f64(ace["c1"]), _f64(ace["c2"])
+    p.ace_rc, p.ace_nref = float(ace["rc"]), float(ace["nref"])
+    p.ace_nmax, p.ace_lmax, p.ace_nfunc = int(ace["nmax"]), int(ace["lmax"]), len(c1)
+    p.ace_idx = idx.ctypes.data_as(_capi.PI)
+    p.ace_c1, p.ace_c2 = c1.ctypes.data_as(_capi.PD), c2.ctypes.data_as(_capi.PD)
+    p.ace_c1_0, p.ace_c2_0 = float(ace["c1_0"]), float(ace["c2_0"])
+    p.ace_precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    p.mass_amu = float(mass)
+    p.skin = float(skin)
+    return p, (idx, c1, c2)
+
+
+def _box_struct(box):
+    b = _capi.Box()
+    h = np.asarray(box["h"], dtype=np.float64).ravel()
+    for k in range(9):
+        b.h[k] = h[k]
+    o = box.get("origin", (0.0, 0.0, 0.0))
+    for k in range(3):
+        b.origin[k] = float(o[k])
+        b.periodic[k] = int(box["periodic"][k])
+    return b
+
+
+def _region_struct(region, n):
+    r = _capi.Region()
+    keep = None
+    if region is None:
+        return r, None
+    r.kind = REGION[region["kind"]]
+    if region["kind"] == "sphere":
+        for k in range(3):
+            r.center[k] = float(region["center"][k])
+        r.r_in, r.r_switch = float(region["r_in"]), float(region["r_sw"])
+        r.follow_indenter = int(region.get("follow", 0))
+    elif region["kind"] == "explicit":
+        keep = _f64(region["w"])
+        assert keep.shape == (n,)
+        r.w_explicit = keep.ctypes.data_as(_capi.PD)
+    elif region["kind"] == "const":
+        r.w_const = float(region["w"])
+    return r, keep
+
+
+def _indenter_struct(ind, vel):
+    s = _capi.Indenter()
+    if ind is None:
+        return s
+    s.enabled = 1
+    v = (0.0, 0.0, 0.0) if vel is None else vel
+    for k in range(3):
+        s.center0[k] = float(ind["center"][k])
+        s.vel[k] = float(v[k])
+        s.dir[k] = float(ind.get("dir", (0.0, 0.0, -1.0))[k])
+    s.R, s.K = float(ind["R"]), float(ind["K"])
+    return s
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor, or None."""
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+class APContext:
+    """One structure on the current CUDA device (wraps ap_init / ap_destroy)."""
+
+    def __init__(self, eam, ace, box, x, v=None, fixed=None, region=None, indenter=None, ind_vel=None,
+                 mass=1.0, skin=1.0, precision="fp32", stream=None):
+        L = _capi.lib()
+        x = _f64(x, (-1, 3))
+        self.n = x.shape[0]
+        pot, keep = potential_struct(eam, ace, mass, skin, precision)
+        bs = _box_struct(box)
+        rs, rkeep = _region_struct(region, self.n)
+        ins = _indenter_struct(indenter, ind_vel)
+        vv = None if v is None else _f64(v, (-1, 3))
+        fx = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.uint8)
+        h = C.c_void_p()
+        st = L.ap_init(C.byref(pot), C.byref(bs), C.byref(rs), C.byref(ins), self.n,
+                       x.ctypes.data_as(_capi.PD), None if vv is None else vv.ctypes.data_as(_capi.PD),
+                       None if fx is None else fx.ctypes.data_as(C.POINTER(C.c_ubyte)), _stream(stream),
+                       C.byref(h))
+        del keep, rkeep
+        if st != 0:
+            raise APError(st, L.ap_last_error(None).decode())
+        self._h = h
+        self._L = L
+
+    def _chk(self, st):
+        if st != 0:
+            raise APError(st, self._L.ap_last_error(self._h).decode())
+
+    def compute_forces(self, pos=None, out=None, stream=None):
+        """Device path: pos / out are CUDA torch tensors ((n,3) float64 / float32) or None."""
+        self._chk(self._L.ap_compute_forces(self._h, _ptr(pos), _ptr(out), _stream(stream)))
+        return out
+
+    def compute_forces_host(self, pos=None, out=None, stream=None):
+        """Host path: numpy (n,3) float64 in, (n,3) float32 out; returns (forces, energy)."""
+        if out is None:
+            out = np.empty((self.n, 3), dtype=np.float32)
+        e = C.c_double()
+        p = None if pos is None else _f64(pos, (-1, 3))
+        self._chk(self._L.ap_compute_forces_host(self._h, None if p is None else p.ctypes.data_as(_capi.PD),
+                                                 out.ctypes.data_as(_capi.PF), C.byref(e), _stream(stream)))
+        return out, e.value
+
+    def step(self, n_steps, dt, stream=None):
+        self._chk(self._L.ap_step(self._h, int(n_steps), float(dt), _stream(stream)))
+
+    def energy(self, e_atom=None):
+        r = _capi.Report()
+        self._chk(self._L.ap_energy(self._h, C.byref(r), _ptr(e_atom)))
+        return {"e_total": r.e_total, "e_pot": r.e_pot, "e_ind": r.e_ind, "e_kin": r.e_kin,
+                "virial": np.array(r.virial[:]), "load": r.load, "time_fs": r.time_fs, "step": r.step,
+                "n_ace": r.n_ace, "n_atoms": r.n_atoms}
+
+    def check(self):
+        self._chk(self._L.ap_check(self._h))
+
+    def forces(self):
+        f = np.empty((self.n, 3), dtype=np.float32)
+        self._chk(self._L.ap_get_forces(self._h, f.ctypes.data_as(_capi.PF)))
+        return f
+
+    def weights(self):
+        w = np.empty(self.n)
+        self._chk(self._L.ap_get_weights(self._h, w.ctypes.data_as(_capi.PD)))
+        return w
+
+    def set_weights(self, w):
+        w = _f64(w)
+        self._chk(self._L.ap_set_weights(self._h, w.ctypes.data_as(_capi.PD)))
+
+    def get_state(self):
+        x = np.empty((self.n, 3))
+        v = np.empty((self.n, 3))
+        t = C.c_double()
+        self._chk(self._L.ap_get_state(self._h, x.ctypes.data_as(_capi.PD), v.ctypes.data_as(_capi.PD), C.byref(t)))
+        return x, v, t.value
+
+    def set_state(self, x=None, v=None, t=0.0):
+        xx = None if x is None else _f64(x, (-1, 3))
+        vv = None if v is None else _f64(v, (-1, 3))
+        self._chk(self._L.ap_set_state(self._h, None if xx is None else xx.ctypes.data_as(_capi.PD),
+                                       None if vv is None else vv.ctypes.data_as(_capi.PD), float(t)))
+
+    def profile(self, enable=True):
+        self._chk(self._L.ap_profile(self._h, int(enable)))
+
+    def profile_read(self):
+        ms = (C.c_double * len(STAGES))()
+        nl = (C.c_longlong * len(STAGES))()
+        self._chk(self._L.ap_profile_read(self._h, ms, nl))
+        return {s: (ms[k], nl[k]) for k, s in enumerate(STAGES)}
+
+    @property
+    def launch_count(self):
+        return int(self._L.ap_launch_count(self._h))
+
+    def neighbor_info(self):
+        cap = C.c_int()
+        nreb = C.c_longlong()
+        self._chk(self._L.ap_neighbor_info(self._h, C.byref(cap), C.byref(nreb)))
+        return cap.value, nreb.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.ap_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def gaunt_real(l1, m1, l2, m2, l3, m3):
+    """The library's host-side real Gaunt coefficient (Racah formula route)."""
+    out = C.c_double()
+    st = _capi.lib().ap_gaunt_real(l1, m1, l2, m2, l3, m3, C.byref(out))
+    if st != 0:
+        raise APError(st, "ap_gaunt_real")
+    return out.value
+
+
+def eam_table_eval(eam, which, r, mass=1.0):
+    """The library's host-side piecewise-polynomial EAM table, evaluated in FP64."""
+    dummy_ace = {"idx": np.zeros((0, 7), np.int32), "c1": np.zeros(0), "c2": np.zeros(0), "rc": 5.0,
+                 "nref": 1.0, "nmax": 8, "lmax": 4, "c1_0": 0.0, "c2_0": 1.0}
+    p, keep = potential_struct(eam, dummy_ace, mass)
+    f, df = C.c_double(), C.c_double()
+    st = _capi.lib().ap_eam_table_eval(C.byref(p), int(which), float(r), C.byref(f), C.byref(df))
+    if st != 0:
+        raise APError(st, "ap_eam_table_eval")
+    return f.value, df.value

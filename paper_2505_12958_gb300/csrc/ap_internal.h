@@ -1,0 +1,187 @@
+// ap_internal.h -- device data layout, context and kernel launchers of the AP library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "ap.h"
+#include "ace_pattern.h"
+
+namespace ap {
+
+// ---------------------------------------------------------------------------------
+// EAM functions as piecewise polynomials (degree <= 5) in t = r - mid on each interval.
+// Built on the host in FP64 from the Appendix B forms, evaluated on the device in FP32.
+// ---------------------------------------------------------------------------------
+constexpr int kMaxInt = 40;
+constexpr int kNBin = 256;
+
+struct PolyTab {
+    int nint;                 // intervals [start[k], start[k+1]), k < nint
+    int zbl;                  // 1: interval 0 is the screened-Coulomb (ZBL) form
+    float rcut;               // zero at and beyond rcut
+    float bin_inv;            // kNBin / rcut
+    float start[kMaxInt + 1];
+    float mid[kMaxInt];
+    float c[kMaxInt][6];
+    unsigned char bin[kNBin]; // first interval that overlaps bin b
+};
+
+struct alignas(16) EamDev {
+    PolyTab phi, rho;
+    float zbl_k;              // Z^2 / (4 pi eps0), eV Angstrom
+    float zbl_ainv;           // 1 / a_ZBL
+    float rc;                 // max(phi.rcut, rho.rcut)
+    float pad;
+    double F_a1, F_a2, F_dxi;
+};
+
+// The same piecewise polynomials in FP64, for the on-demand FP64 energy pass.
+struct PolyTab64 {
+    int nint, zbl;
+    double rcut;
+    double start[kMaxInt + 1];
+    double mid[kMaxInt];
+    double c[kMaxInt][6];
+};
+
+struct EamDev64 {
+    PolyTab64 phi, rho;
+    double zbl_k, zbl_a, F_a1, F_a2, F_dxi;
+};
+
+// ACE coefficient tensors, zero-padded to full n-ranges (a basis function sits at its
+// sorted (n, l) position; the other orderings carry zero).
+struct AceDev {
+    float c3[2][kNT][64][8];  // [density][l-triple][n1 * 8 + n2][n3]
+    float c2[2][5][64];       // [density][l][n1 * 8 + n2]
+    float c1[2][8];           // [density][n]
+    float c1_0, c2_0, nref_inv, rc;
+};
+
+// Cell grid: cells are the parallelepipeds of the box divided n_d times along each edge;
+// an atom's FP32 position is stored relative to its cell's origin, and a neighbour in
+// the cell offset o (per edge, -S..S) is at x_rel_j + D[code(o)] - x_rel_i.
+struct GridDev {
+    double origin[3];
+    double h[9];              // edge vectors as rows
+    double hinv[9];           // s = (r - origin) . hinv gives fractional coordinates
+    double cellvec[9];        // h rows / n_d
+    int periodic[3];
+    int nc[3];
+    int S[3];
+    int ncode;                // (2 S0 + 1)(2 S1 + 1)(2 S2 + 1) <= 125
+    int ncell;
+    float rlist2;
+};
+
+struct DynDev {               // time-dependent geometry; time is read from device memory
+    double reg_c0[3];
+    double r_in, r_sw, w_const;
+    int reg_kind;
+    int follow;
+    int ind_on;
+    int pad;
+    double ind_c0[3], ind_vel[3], ind_dir[3];
+    double R, K;
+};
+
+enum : int { kFlagRebuild = 0, kFlagNAce = 1, kFlagErr = 2, kFlagBad = 3, kFlagMaxNbr = 4, kFlagRebuilds = 5, kFlagCount = 8 };
+enum : int { kErrDomain = 1, kErrCapacity = 2, kErrAceCapacity = 4 };
+
+constexpr int kNbrShift = 25;               // neighbour entry = j | code << 25
+constexpr int kNbrMask = (1 << kNbrShift) - 1;
+constexpr int kMaxAtoms = (1 << kNbrShift) - 1;
+constexpr double kFixScale = 1099511627776.0;   // 2^40: fixed-point scale of ACE force sums
+constexpr int kAceNbrCap = 128;                 // neighbours within the ACE cutoff per atom
+constexpr int kRedBlock = 256;
+
+struct Ctx {
+    int n = 0, dev = 0;
+    cudaStream_t stream = nullptr;
+    double mass = 1.0, skin = 1.0, rc_eam = 0.0, rc_ace = 0.0, rc_list = 0.0;
+    int ace_prec = AP_ACE_FP32;
+    int region_kind = AP_REGION_NONE;
+
+    EamDev eam_h{};
+    EamDev* eam_d = nullptr;
+    EamDev64 eam64_h{};
+    EamDev64* eam64_d = nullptr;
+    bool energy_fresh = false;                           // FP64 energy pass done for the last forces
+    AceDev* ace_h = nullptr;
+    AceDev* ace_d = nullptr;
+    GridDev grid{};
+    float4* D = nullptr;
+    DynDev dyn{};
+
+    double *x = nullptr, *v = nullptr, *xb = nullptr;   // SoA [3][n]
+    float* f = nullptr;                                  // SoA [3][n]
+    float4* pos4 = nullptr;                              // x_rel (3) and u = 1 - w
+    float* uxi = nullptr;                                // u_i xi'(rho_i)
+    float* w = nullptr;
+    double* e_emb = nullptr;                             // xi(rho_i) + Delta xi
+    double* e_eam = nullptr;                             // E_i^EAM (FP64)
+    float* e_ace = nullptr;                              // E_i^ACE - c1_0
+    double ace_c1_0 = 0.0;
+    float* vir_eam = nullptr;                            // [6][n]
+    float* vir_ace = nullptr;                            // [6][n]
+    unsigned long long* acc = nullptr;                   // [3][n] fixed-point ACE forces
+    unsigned char* fixed = nullptr;
+    double* w_fixed = nullptr;
+    int *cell = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cell_atoms = nullptr;
+    int* nbr = nullptr;                                  // [cap][n]
+    int* nnbr = nullptr;
+    int cap = 0;
+    int* ace_list = nullptr;
+    int* flags = nullptr;                                // kFlag*
+    double* d_time = nullptr;
+    double* partials = nullptr;
+    double* totals = nullptr;                            // 16 doubles
+    double* e_atom = nullptr;
+    double* pos_stage = nullptr;                         // n x 3 host-transfer staging
+    float* f_stage = nullptr;                            // n x 3 host-transfer staging
+    int nred = 0;
+
+    int* h_flags = nullptr;                              // pinned
+    double* h_totals = nullptr;                          // pinned
+    long long launches = 0, rebuilds = 0, step = 0;
+    double t = 0.0;
+    bool forces_valid = false;
+    std::string err;
+
+    bool prof = false;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    double stage_ms[AP_NSTAGE] = {0};
+    long long stage_n[AP_NSTAGE] = {0};
+};
+
+static_assert(sizeof(EamDev) % 16 == 0, "EamDev is staged in 16-byte words");
+static_assert(sizeof(AceDev) % 16 == 0, "AceDev is staged in 16-byte words");
+
+// kernel launchers (one per stage); each returns the number of kernels launched
+int launch_rebuild(Ctx& c, cudaStream_t s);          // wrap, bin, scan, scatter, sort (skip when no rebuild)
+int launch_prepare(Ctx& c, cudaStream_t s);          // x_rel, weights, compaction
+int launch_build(Ctx& c, cudaStream_t s, int count_only);
+int launch_eam_density(Ctx& c, cudaStream_t s);
+int launch_eam_force(Ctx& c, cudaStream_t s);
+int launch_ace(Ctx& c, cudaStream_t s);
+int launch_blend(Ctx& c, cudaStream_t s, float* out_aos);
+int launch_energy64(Ctx& c, cudaStream_t s);         // FP64 EAM energies + energy blend
+int launch_reduce(Ctx& c, cudaStream_t s, int with_kinetic);
+int launch_kick_drift(Ctx& c, cudaStream_t s, double dt, int first_half);
+int launch_kick(Ctx& c, cudaStream_t s, double dt);
+int launch_pos_in(Ctx& c, cudaStream_t s, const double* pos_aos);
+int launch_check(Ctx& c, cudaStream_t s);
+
+// host-side tables (tables.cpp)
+int build_eam_tables(const ap_potential& p, EamDev& out, EamDev64& out64, std::string& err);
+int build_ace_tables(const ap_potential& p, AceDev& out, std::string& err);
+double gaunt_real_racah(int l1, int m1, int l2, int m2, int l3, int m3);
+int gaunt_values(float* out, std::string& err);      // kNG entries in pattern order
+double poly_eval_host(const PolyTab& t, const double* coef64, double r, double* df);
+int eam_table_eval_fp64(const ap_potential& p, int which, double r, double* f, double* df);
+void upload_gaunt(const float* g);                   // kernels_ace.cu
+
+}  // namespace ap

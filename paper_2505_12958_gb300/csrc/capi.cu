@@ -1,0 +1,563 @@
+// capi.cu -- the C ABI declared in include/ap.h: context set-up, the per-step pipeline,
+// state transfer and timing.  The step pipeline is launched on one stream with no host
+// synchronisation: the neighbour rebuild decision, the ACE atom count and all error
+// conditions live in device memory.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ap_internal.h"
+
+struct ap_ctx {
+    ap::Ctx c;
+    struct Pending { int stage; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> free_ev;
+};
+
+namespace {
+
+thread_local std::string g_init_err;
+
+ap_status set_err(ap::Ctx& c, ap_status s, const std::string& m) {
+    c.err = m;
+    return s;
+}
+
+ap_status cuda_check(ap::Ctx& c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return AP_OK;
+    c.err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? AP_ERR_OOM : AP_ERR_CUDA;
+}
+
+cudaStream_t pick(ap_ctx* x, void* s) { return s ? (cudaStream_t)s : x->c.stream; }
+
+cudaEvent_t get_event(ap_ctx* x) {
+    if (!x->free_ev.empty()) { cudaEvent_t e = x->free_ev.back(); x->free_ev.pop_back(); return e; }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// run one stage; with profiling on, bracket it with events on the same stream
+template <class F>
+void stage(ap_ctx* x, int st, cudaStream_t s, F&& launch) {
+    ap::Ctx& c = x->c;
+    if (!c.prof) { c.launches += launch(); return; }
+    cudaEvent_t a = get_event(x), b = get_event(x);
+    cudaEventRecord(a, s);
+    c.launches += launch();
+    cudaEventRecord(b, s);
+    x->pending.push_back({st, a, b});
+}
+
+void drain_events(ap_ctx* x) {
+    ap::Ctx& c = x->c;
+    for (auto& p : x->pending) {
+        float ms = 0.f;
+        cudaEventSynchronize(p.b);
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        c.stage_ms[p.stage] += ms;
+        c.stage_n[p.stage] += 1;
+        x->free_ev.push_back(p.a);
+        x->free_ev.push_back(p.b);
+    }
+    x->pending.clear();
+}
+
+void inv3(const double* M, double* R) {
+    double a = M[0], b = M[1], cc = M[2], d = M[3], e = M[4], f = M[5], g = M[6], h = M[7], i = M[8];
+    double det = a * (e * i - f * h) - b * (d * i - f * g) + cc * (d * h - e * g);
+    R[0] = (e * i - f * h) / det; R[1] = (cc * h - b * i) / det; R[2] = (b * f - cc * e) / det;
+    R[3] = (f * g - d * i) / det; R[4] = (a * i - cc * g) / det; R[5] = (cc * d - a * f) / det;
+    R[6] = (d * h - e * g) / det; R[7] = (b * g - a * h) / det; R[8] = (a * e - b * d) / det;
+}
+
+void cross(const double* a, const double* b, double* c) {
+    c[0] = a[1] * b[2] - a[2] * b[1]; c[1] = a[2] * b[0] - a[0] * b[2]; c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+ap_status setup_grid(ap::Ctx& c, const ap_box& box, std::vector<float4>& D) {
+    ap::GridDev& g = c.grid;
+    std::memcpy(g.h, box.h, sizeof(g.h));
+    std::memcpy(g.origin, box.origin, sizeof(g.origin));
+    double V, cr[3];
+    cross(g.h + 3, g.h + 6, cr);
+    V = g.h[0] * cr[0] + g.h[1] * cr[1] + g.h[2] * cr[2];
+    if (!(std::fabs(V) > 1e-9)) return set_err(c, AP_ERR_ARG, "box edge vectors are degenerate");
+    inv3(g.h, g.hinv);
+    double pw[3];
+    for (int d = 0; d < 3; ++d) {
+        const double* a = g.h + 3 * ((d + 1) % 3);
+        const double* b = g.h + 3 * ((d + 2) % 3);
+        cross(a, b, cr);
+        pw[d] = std::fabs(V) / std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+    }
+    long long ncell = 1;
+    for (int d = 0; d < 3; ++d) {
+        g.periodic[d] = box.periodic[d] ? 1 : 0;
+        int n = (int)std::floor(pw[d] / c.rc_list);
+        n = std::max(1, std::min(n, 1024));
+        g.nc[d] = n;
+        int S = 1;
+        if (g.periodic[d]) S = std::max(1, (int)std::ceil(c.rc_list * n / pw[d] - 1e-12));
+        if (S > 2) return set_err(c, AP_ERR_ARG, "box thinner than half the neighbour-list cutoff");
+        g.S[d] = S;
+        ncell *= n;
+        for (int q = 0; q < 3; ++q) g.cellvec[3 * d + q] = g.h[3 * d + q] / n;
+    }
+    if (ncell > (1ll << 26)) return set_err(c, AP_ERR_ARG, "cell grid too large");
+    g.ncell = (int)ncell;
+    g.ncode = (2 * g.S[0] + 1) * (2 * g.S[1] + 1) * (2 * g.S[2] + 1);
+    g.rlist2 = (float)(c.rc_list * c.rc_list);
+    D.resize(g.ncode);
+    const int w1 = 2 * g.S[1] + 1, w2 = 2 * g.S[2] + 1;
+    for (int code = 0; code < g.ncode; ++code) {
+        int o[3] = {code / (w1 * w2) - g.S[0], (code / w2) % w1 - g.S[1], code % w2 - g.S[2]};
+        double v[3];
+        for (int q = 0; q < 3; ++q) v[q] = o[0] * g.cellvec[q] + o[1] * g.cellvec[3 + q] + o[2] * g.cellvec[6 + q];
+        D[code] = make_float4((float)v[0], (float)v[1], (float)v[2], 0.f);
+    }
+    return AP_OK;
+}
+
+template <class T>
+ap_status dalloc(ap::Ctx& c, T** p, size_t count) {
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) { *p = nullptr; return cuda_check(c, e, "cudaMalloc"); }
+    return AP_OK;
+}
+
+void free_all(ap::Ctx& c) {
+    void* ps[] = {c.eam_d, c.eam64_d, c.ace_d, c.D, c.x, c.v, c.xb, c.f, c.pos4, c.uxi, c.w, c.e_emb, c.e_eam, c.e_ace,
+                  c.vir_eam, c.vir_ace, c.acc, c.fixed, c.w_fixed, c.cell, c.cell_count, c.cell_start,
+                  c.cell_atoms, c.nbr, c.nnbr, c.ace_list, c.flags, c.d_time, c.partials, c.totals, c.e_atom,
+                  c.pos_stage, c.f_stage};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    if (c.h_flags) cudaFreeHost(c.h_flags);
+    if (c.h_totals) cudaFreeHost(c.h_totals);
+    delete c.ace_h;
+}
+
+void to_soa(const double* aos, int n, std::vector<double>& soa) {
+    soa.resize(3 * (size_t)n);
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k) soa[(size_t)k * n + i] = aos[3 * (size_t)i + k];
+}
+
+// one AP force evaluation of the current positions (stages a1-a7)
+void run_forces(ap_ctx* xc, cudaStream_t s, float* out_aos) {
+    ap::Ctx& c = xc->c;
+    stage(xc, AP_STAGE_NEIGHBOR, s, [&] { return ap::launch_check(c, s) + ap::launch_rebuild(c, s); });
+    stage(xc, AP_STAGE_PREPARE, s, [&] { return ap::launch_prepare(c, s); });
+    stage(xc, AP_STAGE_NEIGHBOR, s, [&] { return ap::launch_build(c, s, 0); });
+    stage(xc, AP_STAGE_EAM_DENSITY, s, [&] { return ap::launch_eam_density(c, s); });
+    stage(xc, AP_STAGE_EAM_FORCE, s, [&] { return ap::launch_eam_force(c, s); });
+    stage(xc, AP_STAGE_ACE, s, [&] { return ap::launch_ace(c, s); });
+    stage(xc, AP_STAGE_BLEND, s, [&] { return ap::launch_blend(c, s, out_aos); });
+    c.forces_valid = true;
+    c.energy_fresh = false;
+}
+
+// FP64 energies of the last force evaluation, once
+void ensure_energy(ap_ctx* xc, cudaStream_t s) {
+    ap::Ctx& c = xc->c;
+    if (c.energy_fresh) return;
+    c.launches += ap::launch_energy64(c, s);
+    c.energy_fresh = true;
+}
+
+ap_status read_flags(ap::Ctx& c, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(c.h_flags, c.flags, sizeof(int) * ap::kFlagCount, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_check(c, e, "synchronise");
+    int err = c.h_flags[ap::kFlagErr];
+    if (err & ap::kErrDomain)
+        return set_err(c, AP_ERR_DOMAIN, "domain error (phi2 <= 1e-3, rho < 0 or non-finite) at atom " + std::to_string(c.h_flags[ap::kFlagBad]));
+    if (err & (ap::kErrCapacity | ap::kErrAceCapacity)) {
+        // grow the list capacity; the next evaluation rebuilds
+        int need = c.h_flags[ap::kFlagMaxNbr];
+        std::string m = "neighbour capacity exceeded (" + std::to_string(need) + " > " + std::to_string(c.cap) + ")";
+        if (err & ap::kErrCapacity) {
+            int cap = ((int)(need * 1.25) + 8 + 3) & ~3;
+            int* nb = nullptr;
+            if (cudaMalloc((void**)&nb, (size_t)cap * c.n * sizeof(int)) == cudaSuccess) {
+                cudaFree(c.nbr);
+                c.nbr = nb;
+                c.cap = cap;
+            }
+        }
+        int zero[2] = {1, 0};
+        cudaMemcpy(&c.flags[ap::kFlagRebuild], &zero[0], sizeof(int), cudaMemcpyHostToDevice);
+        cudaMemcpy(&c.flags[ap::kFlagErr], &zero[1], sizeof(int), cudaMemcpyHostToDevice);
+        c.forces_valid = false;
+        return set_err(c, AP_ERR_CAPACITY, m);
+    }
+    return AP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ap_version(void) { return AP_API_VERSION; }
+
+size_t ap_footprint_bytes(const ap_potential* pot, int n_atoms, double ace_fraction) {
+    (void)ace_fraction;
+    double rl = 6.5;
+    if (pot) {
+        double rc = 0.0;
+        for (int k = 0; k < pot->eam_n_phi && k < 32; ++k) rc = std::max(rc, pot->eam_phi_d[k]);
+        rc = std::max(rc, pot->ace_rc);
+        rl = rc + (pot->skin > 0 ? pot->skin : 1.0);
+    }
+    // neighbour capacity at a metallic density of 0.09 atoms / A^3, with margin
+    double cap = 1.3 * 4.18879 * rl * rl * rl * 0.09 + 16;
+    size_t per_atom = (size_t)(cap * 4) + 3 * 8 * 3 + 16 + 3 * 4 + 4 * 3 + 8 * 3 + 4 * 12 + 3 * 8 + 4 * 5 + 16;
+    return (size_t)n_atoms * per_atom + sizeof(ap::AceDev) + sizeof(ap::EamDev) + (8u << 20);
+}
+
+ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* region, const ap_indenter* ind,
+                  int n, const double* pos, const double* vel, const unsigned char* fixed, void* stream,
+                  ap_ctx** out) {
+    if (!out) return AP_ERR_ARG;
+    *out = nullptr;
+    if (!pot || !box || !pos || n < 1 || n > ap::kMaxAtoms) { g_init_err = "ap_init: missing argument or bad atom count"; return AP_ERR_ARG; }
+    if (!(pot->mass_amu > 0.0) || !(pot->skin >= 0.0)) { g_init_err = "ap_init: mass must be > 0 and skin >= 0"; return AP_ERR_ARG; }
+    if (pot->ace_precision != AP_ACE_FP32) { g_init_err = "ap_init: this build evaluates A_nlm in FP32 only"; return AP_ERR_ARG; }
+    ap_ctx* xc = new (std::nothrow) ap_ctx();
+    if (!xc) return AP_ERR_OOM;
+    ap::Ctx& c = xc->c;
+    c.n = n;
+    c.mass = pot->mass_amu;
+    c.skin = pot->skin;
+    c.ace_prec = pot->ace_precision;
+    c.stream = (cudaStream_t)stream;
+    ap_status st = AP_OK;
+    auto fail = [&](ap_status s2) {
+        g_init_err = c.err;
+        free_all(c);
+        delete xc;
+        return s2;
+    };
+    if (cudaGetDevice(&c.dev) != cudaSuccess) { c.err = "no CUDA device"; return fail(AP_ERR_CUDA); }
+    std::string err;
+    if (ap::build_eam_tables(*pot, c.eam_h, c.eam64_h, err)) { c.err = err; return fail(AP_ERR_ARG); }
+    c.ace_h = new (std::nothrow) ap::AceDev();
+    if (!c.ace_h) { c.err = "host allocation"; return fail(AP_ERR_OOM); }
+    if (ap::build_ace_tables(*pot, *c.ace_h, err)) { c.err = err; return fail(AP_ERR_ARG); }
+    c.ace_c1_0 = pot->ace_c1_0;
+    static int gaunt_done_dev = -1;
+    if (gaunt_done_dev != c.dev) {
+        std::vector<float> g(ap::kNG);
+        if (ap::gaunt_values(g.data(), err)) { c.err = err; return fail(AP_ERR_ARG); }
+        ap::upload_gaunt(g.data());
+        gaunt_done_dev = c.dev;
+    }
+    c.rc_eam = c.eam_h.rc;
+    c.rc_ace = pot->ace_rc;
+    c.rc_list = std::max(c.rc_eam, c.rc_ace) + c.skin;
+    std::vector<float4> D;
+    if ((st = setup_grid(c, *box, D)) != AP_OK) return fail(st);
+
+    // region and indenter
+    ap::DynDev& dy = c.dyn;
+    std::memset(&dy, 0, sizeof(dy));
+    c.region_kind = region ? region->kind : AP_REGION_NONE;
+    dy.reg_kind = c.region_kind;
+    if (region) {
+        if (region->kind < 0 || region->kind > AP_REGION_CONST) { c.err = "bad region kind"; return fail(AP_ERR_ARG); }
+        for (int k = 0; k < 3; ++k) dy.reg_c0[k] = region->center[k];
+        dy.r_in = region->r_in;
+        dy.r_sw = region->r_switch;
+        dy.w_const = region->w_const;
+        dy.follow = region->follow_indenter;
+        if (region->kind == AP_REGION_SPHERE && !(region->r_switch > 0.0 && region->r_in >= 0.0)) { c.err = "sphere needs r_in >= 0, r_switch > 0"; return fail(AP_ERR_ARG); }
+        if (region->kind == AP_REGION_CONST && !(region->w_const >= 0.0 && region->w_const <= 1.0)) { c.err = "w_const must lie in [0, 1]"; return fail(AP_ERR_ARG); }
+        if (region->kind == AP_REGION_EXPLICIT && !region->w_explicit) { c.err = "explicit region needs w_explicit"; return fail(AP_ERR_ARG); }
+    }
+    if (ind && ind->enabled) {
+        dy.ind_on = 1;
+        for (int k = 0; k < 3; ++k) { dy.ind_c0[k] = ind->center0[k]; dy.ind_vel[k] = ind->vel[k]; dy.ind_dir[k] = ind->dir[k]; }
+        dy.R = ind->R;
+        dy.K = ind->K;
+    }
+
+    // device memory
+    const size_t N = (size_t)n;
+    c.nred = (n + ap::kRedBlock - 1) / ap::kRedBlock;
+    if ((st = dalloc(c, &c.eam_d, 1)) || (st = dalloc(c, &c.eam64_d, 1)) || (st = dalloc(c, &c.ace_d, 1)) || (st = dalloc(c, &c.D, D.size())) ||
+        (st = dalloc(c, &c.x, 3 * N)) || (st = dalloc(c, &c.v, 3 * N)) || (st = dalloc(c, &c.xb, 3 * N)) ||
+        (st = dalloc(c, &c.f, 3 * N)) || (st = dalloc(c, &c.pos4, N)) || (st = dalloc(c, &c.uxi, N)) ||
+        (st = dalloc(c, &c.w, N)) || (st = dalloc(c, &c.e_emb, N)) || (st = dalloc(c, &c.e_eam, N)) ||
+        (st = dalloc(c, &c.e_ace, N)) || (st = dalloc(c, &c.vir_eam, 6 * N)) || (st = dalloc(c, &c.vir_ace, 6 * N)) ||
+        (st = dalloc(c, &c.acc, 3 * N)) || (st = dalloc(c, &c.fixed, N)) || (st = dalloc(c, &c.w_fixed, N)) ||
+        (st = dalloc(c, &c.cell, N)) || (st = dalloc(c, &c.cell_count, (size_t)c.grid.ncell)) ||
+        (st = dalloc(c, &c.cell_start, (size_t)c.grid.ncell + 1)) || (st = dalloc(c, &c.cell_atoms, N)) ||
+        (st = dalloc(c, &c.nnbr, N)) || (st = dalloc(c, &c.ace_list, N)) || (st = dalloc(c, &c.flags, ap::kFlagCount)) ||
+        (st = dalloc(c, &c.d_time, 1)) || (st = dalloc(c, &c.partials, (size_t)c.nred * 10)) ||
+        (st = dalloc(c, &c.totals, 16)) || (st = dalloc(c, &c.e_atom, N)))
+        return fail(st);
+    if (cudaMallocHost((void**)&c.h_flags, sizeof(int) * ap::kFlagCount) != cudaSuccess ||
+        cudaMallocHost((void**)&c.h_totals, sizeof(double) * 16) != cudaSuccess) {
+        c.err = "pinned host allocation";
+        return fail(AP_ERR_OOM);
+    }
+    std::vector<double> soa;
+    to_soa(pos, n, soa);
+    cudaError_t e = cudaSuccess;
+    auto cp = [&](void* dst, const void* src, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    cp(c.eam_d, &c.eam_h, sizeof(ap::EamDev));
+    cp(c.eam64_d, &c.eam64_h, sizeof(ap::EamDev64));
+    cp(c.ace_d, c.ace_h, sizeof(ap::AceDev));
+    cp(c.D, D.data(), D.size() * sizeof(float4));
+    cp(c.x, soa.data(), 3 * N * sizeof(double));
+    cp(c.xb, soa.data(), 3 * N * sizeof(double));
+    if (vel) { to_soa(vel, n, soa); cp(c.v, soa.data(), 3 * N * sizeof(double)); }
+    else if (e == cudaSuccess) e = cudaMemset(c.v, 0, 3 * N * sizeof(double));
+    if (fixed) cp(c.fixed, fixed, N);
+    else if (e == cudaSuccess) e = cudaMemset(c.fixed, 0, N);
+    if (region && region->kind == AP_REGION_EXPLICIT) {
+        for (int i = 0; i < n; ++i)
+            if (!(region->w_explicit[i] >= 0.0 && region->w_explicit[i] <= 1.0)) { c.err = "explicit weights must lie in [0, 1]"; return fail(AP_ERR_ARG); }
+        cp(c.w_fixed, region->w_explicit, N * sizeof(double));
+    }
+    if (e == cudaSuccess) e = cudaMemset(c.acc, 0, 3 * N * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(c.cell_count, 0, (size_t)c.grid.ncell * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c.flags, 0, ap::kFlagCount * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c.d_time, 0, sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(c.vir_ace, 0, 6 * N * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(c.e_ace, 0, N * sizeof(float));
+    int one = 1;
+    cp(&c.flags[ap::kFlagRebuild], &one, sizeof(int));
+    if (e != cudaSuccess) { cuda_check(c, e, "ap_init upload"); return fail(AP_ERR_CUDA); }
+
+    // size the neighbour capacity from a counting pass over the first binning
+    cudaStream_t s = c.stream;
+    c.launches += ap::launch_rebuild(c, s);
+    c.launches += ap::launch_prepare(c, s);
+    c.launches += ap::launch_build(c, s, 1);
+    e = cudaMemcpyAsync(c.h_flags, c.flags, sizeof(int) * ap::kFlagCount, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) { cuda_check(c, e, "ap_init neighbour sizing"); return fail(AP_ERR_CUDA); }
+    int need = c.h_flags[ap::kFlagMaxNbr];
+    c.cap = std::max(8, ((int)(need * 1.25) + 8 + 3) & ~3);
+    if ((st = dalloc(c, &c.nbr, (size_t)c.cap * N))) return fail(st);
+    c.rebuilds = 0;
+    *out = xc;
+    return AP_OK;
+}
+
+ap_status ap_compute_forces(ap_ctx* xc, const double* d_pos, float* d_force, void* stream) {
+    if (!xc) return AP_ERR_ARG;
+    ap::Ctx& c = xc->c;
+    cudaStream_t s = pick(xc, stream);
+    if (d_pos) c.launches += ap::launch_pos_in(c, s, d_pos);
+    run_forces(xc, s, d_force);
+    return cuda_check(c, cudaGetLastError(), "ap_compute_forces");
+}
+
+ap_status ap_compute_forces_host(ap_ctx* xc, const double* h_pos, float* h_force, double* h_energy, void* stream) {
+    if (!xc) return AP_ERR_ARG;
+    ap::Ctx& c = xc->c;
+    cudaStream_t s = pick(xc, stream);
+    const size_t N = (size_t)c.n;
+    ap_status st;
+    if (!c.pos_stage && ((st = dalloc(c, &c.pos_stage, 3 * N)) || (st = dalloc(c, &c.f_stage, 3 * N)))) return st;
+    cudaError_t e = cudaSuccess;
+    if (h_pos) {
+        e = cudaMemcpyAsync(c.pos_stage, h_pos, 3 * N * sizeof(double), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_check(c, e, "ap_compute_forces_host H2D");
+        c.launches += ap::launch_pos_in(c, s, c.pos_stage);
+    }
+    run_forces(xc, s, c.f_stage);
+    if (h_energy) {
+        ensure_energy(xc, s);
+        c.launches += ap::launch_reduce(c, s, 0);
+    }
+    if (h_force) e = cudaMemcpyAsync(h_force, c.f_stage, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && h_energy) e = cudaMemcpyAsync(c.h_totals, c.totals, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_check(c, e, "ap_compute_forces_host D2H");
+    if ((st = read_flags(c, s))) return st;
+    if (h_energy) *h_energy = c.h_totals[0] + c.h_totals[1];
+    return AP_OK;
+}
+
+ap_status ap_step(ap_ctx* xc, int n_steps, double dt, void* stream) {
+    if (!xc || n_steps < 0 || !(dt > 0.0)) return AP_ERR_ARG;
+    ap::Ctx& c = xc->c;
+    cudaStream_t s = pick(xc, stream);
+    if (!c.forces_valid) run_forces(xc, s, nullptr);
+    for (int k = 0; k < n_steps; ++k) {
+        stage(xc, AP_STAGE_INTEGRATE, s, [&] { return ap::launch_kick_drift(c, s, dt, 1); });
+        run_forces(xc, s, nullptr);
+        stage(xc, AP_STAGE_INTEGRATE, s, [&] { return ap::launch_kick(c, s, dt); });
+        c.t += dt;
+        c.step += 1;
+    }
+    return cuda_check(c, cudaGetLastError(), "ap_step");
+}
+
+ap_status ap_energy(ap_ctx* xc, ap_report* out, double* d_e_atom) {
+    if (!xc || !out) return AP_ERR_ARG;
+    ap::Ctx& c = xc->c;
+    cudaStream_t s = c.stream;
+    if (!c.forces_valid) run_forces(xc, s, nullptr);
+    ensure_energy(xc, s);
+    c.launches += ap::launch_reduce(c, s, 1);
+    cudaError_t e = cudaMemcpyAsync(c.h_totals, c.totals, 10 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && d_e_atom)
+        e = cudaMemcpyAsync(d_e_atom, c.e_atom, (size_t)c.n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_check(c, e, "ap_energy");
+    ap_status st = read_flags(c, s);
+    std::memset(out, 0, sizeof(*out));
+    const double* T = c.h_totals;
+    out->e_pot = T[0];
+    out->e_ind = T[1];
+    out->e_total = T[0] + T[1];
+    for (int k = 0; k < 6; ++k) out->virial[k] = T[2 + k];
+    out->load = T[8];
+    out->e_kin = T[9];
+    out->time_fs = c.t;
+    out->step = c.step;
+    out->n_ace = c.h_flags[ap::kFlagNAce];
+    out->n_atoms = c.n;
+    return st;
+}
+
+ap_status ap_check(ap_ctx* xc) {
+    if (!xc) return AP_ERR_ARG;
+    return read_flags(xc->c, xc->c.stream);
+}
+
+ap_status ap_get_state(ap_ctx* xc, double* x, double* v, double* t) {
+    if (!xc) return AP_ERR_ARG;
+    ap::Ctx& c = xc->c;
+    const size_t N = (size_t)c.n;
+    std::vector<double> tmp(3 * N);
+    for (int which = 0; which < 2; ++which) {
+        double* dst = which == 0 ? x : v;
+        if (!dst) continue;
+        cudaError_t e = cudaMemcpyAsync(tmp.data(), which == 0 ? c.x : c.v, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c.stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+        if (e != cudaSuccess) return cuda_check(c, e, "ap_get_state");
+        for (size_t i = 0; i < N; ++i)
+            for (int k = 0; k < 3; ++k) dst[3 * i + k] = tmp[(size_t)k * N + i];
+    }
+    if (t) *t = c.t;
+    return AP_OK;
+}
+
+ap_status ap_set_state(ap_ctx* xc, const double* x, const double* v, double t) {
+    if (!xc) return AP_ERR_ARG;
+    ap::Ctx& c = xc->c;
+    const size_t N = (size_t)c.n;
+    std::vector<double> soa;
+    cudaError_t e = cudaStreamSynchronize(c.stream);
+    if (x && e == cudaSuccess) { to_soa(x, c.n, soa); e = cudaMemcpy(c.x, soa.data(), 3 * N * sizeof(double), cudaMemcpyHostToDevice); }
+    if (v && e == cudaSuccess) { to_soa(v, c.n, soa); e = cudaMemcpy(c.v, soa.data(), 3 * N * sizeof(double), cudaMemcpyHostToDevice); }
+    int one = 1;
+    if (e == cudaSuccess) e = cudaMemcpy(&c.flags[ap::kFlagRebuild], &one, sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c.d_time, &t, sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_check(c, e, "ap_set_state");
+    c.t = t;
+    c.forces_valid = false;
+    return AP_OK;
+}
+
+ap_status ap_get_forces(ap_ctx* xc, float* f) {
+    if (!xc || !f) return AP_ERR_ARG;
+    ap::Ctx& c = xc->c;
+    const size_t N = (size_t)c.n;
+    std::vector<float> tmp(3 * N);
+    cudaError_t e = cudaMemcpyAsync(tmp.data(), c.f, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "ap_get_forces");
+    for (size_t i = 0; i < N; ++i)
+        for (int k = 0; k < 3; ++k) f[3 * i + k] = tmp[(size_t)k * N + i];
+    return AP_OK;
+}
+
+ap_status ap_get_weights(ap_ctx* xc, double* w) {
+    if (!xc || !w) return AP_ERR_ARG;
+    ap::Ctx& c = xc->c;
+    std::vector<float> tmp((size_t)c.n);
+    cudaError_t e = cudaMemcpyAsync(tmp.data(), c.w, (size_t)c.n * sizeof(float), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "ap_get_weights");
+    for (int i = 0; i < c.n; ++i) w[i] = tmp[i];
+    return AP_OK;
+}
+
+ap_status ap_set_weights(ap_ctx* xc, const double* w) {
+    if (!xc || !w) return AP_ERR_ARG;
+    ap::Ctx& c = xc->c;
+    if (c.region_kind != AP_REGION_EXPLICIT) return set_err(c, AP_ERR_STATE, "weights are explicit only for AP_REGION_EXPLICIT");
+    for (int i = 0; i < c.n; ++i)
+        if (!(w[i] >= 0.0 && w[i] <= 1.0)) return set_err(c, AP_ERR_ARG, "weights must lie in [0, 1]");
+    cudaError_t e = cudaStreamSynchronize(c.stream);
+    if (e == cudaSuccess) e = cudaMemcpy(c.w_fixed, w, (size_t)c.n * sizeof(double), cudaMemcpyHostToDevice);
+    c.forces_valid = false;
+    return cuda_check(c, e, "ap_set_weights");
+}
+
+ap_status ap_profile(ap_ctx* xc, int enable) {
+    if (!xc) return AP_ERR_ARG;
+    xc->c.prof = enable != 0;
+    return AP_OK;
+}
+
+ap_status ap_profile_read(ap_ctx* xc, double* ms, long long* launches) {
+    if (!xc) return AP_ERR_ARG;
+    drain_events(xc);
+    for (int k = 0; k < AP_NSTAGE; ++k) {
+        if (ms) ms[k] = xc->c.stage_ms[k];
+        if (launches) launches[k] = xc->c.stage_n[k];
+        xc->c.stage_ms[k] = 0.0;
+        xc->c.stage_n[k] = 0;
+    }
+    return AP_OK;
+}
+
+long long ap_launch_count(const ap_ctx* xc) { return xc ? xc->c.launches : 0; }
+
+ap_status ap_neighbor_info(ap_ctx* xc, int* capacity, long long* rebuilds) {
+    if (!xc) return AP_ERR_ARG;
+    ap_status st = read_flags(xc->c, xc->c.stream);
+    if (capacity) *capacity = xc->c.cap;
+    if (rebuilds) *rebuilds = xc->c.h_flags[ap::kFlagRebuilds] - 1;   // the sizing pass at ap_init is not counted
+    return st;
+}
+
+const char* ap_last_error(const ap_ctx* xc) { return xc ? xc->c.err.c_str() : g_init_err.c_str(); }
+
+void ap_destroy(ap_ctx* xc) {
+    if (!xc) return;
+    cudaStreamSynchronize(xc->c.stream);
+    drain_events(xc);
+    for (cudaEvent_t e : xc->free_ev) cudaEventDestroy(e);
+    free_all(xc->c);
+    delete xc;
+}
+
+ap_status ap_gaunt_real(int l1, int m1, int l2, int m2, int l3, int m3, double* out) {
+    if (!out || l1 < 0 || l2 < 0 || l3 < 0 || l1 > 4 || l2 > 4 || l3 > 4) return AP_ERR_ARG;
+    if (std::abs(m1) > l1 || std::abs(m2) > l2 || std::abs(m3) > l3) return AP_ERR_ARG;
+    *out = ap::gaunt_real_racah(l1, m1, l2, m2, l3, m3);
+    return AP_OK;
+}
+
+ap_status ap_eam_table_eval(const ap_potential* pot, int which, double r, double* f, double* df) {
+    if (!pot || !f || !df || (which != 0 && which != 1)) return AP_ERR_ARG;
+    return (ap_status)ap::eam_table_eval_fp64(*pot, which, r, f, df);
+}
+
+}  // extern "C"

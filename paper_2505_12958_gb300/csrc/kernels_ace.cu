@@ -1,0 +1,604 @@
+// kernels_ace.cu -- ACE pass of the AP force evaluation (Sec. 2.2.2, Eq. energy_ace).
+//
+// One warp per atom of the compacted list (w_i > 0), persistent grid.  Per atom:
+//   1. neighbours within the ACE cutoff are gathered from the full list into shared
+//      memory (r_ij from FP32 cell-relative positions);
+//   2. the atomic base A_nlm = (1/nref) sum_j g_n(r_ij) Y_lm(rhat_ij) (8 x 25) is formed
+//      from a shared-memory tile of g and Y (lane = (l, m), 8 accumulators);
+//   3. phi_p = c_p0 + sum_v c_p[v] B_v, p = 1, 2 (B: one, two and three A factors), with
+//      lanes over the 64 (n1, n2) pairs: three-factor products are evaluated as
+//      P[m3] = sum G A_n1 A_n2 (compile-time Gaunt pattern, operands in registers), then
+//      contracted with A_n3 and the coefficient tensor;
+//   4. the adjoint dE/dA with the combined coefficients c1 + c2 / (2 sqrt(phi2)):
+//      gradients with respect to the first two factors from the (n1, n2) mapping,
+//      with respect to the third from an (n1, n3) mapping; lane partial sums are
+//      reduced with butterfly shuffles in a fixed order;
+//   5. pair forces f_ij = dE_i/dr_ij = (1/nref) sum dE/dA_nlm grad(g_n Y_lm), weighted by
+//      w_i, are added to atom j (minus) and atom i (plus) through 64-bit fixed-point
+//      atomics (2^-40 eV/A resolution), whose integer sums do not depend on order.
+// E_i^ACE is stored without the constant c1_0, which the blend adds in FP64.
+#include <utility>
+
+#include "ap_internal.h"
+
+namespace ap {
+
+__constant__ float c_gaunt[kNG];
+
+void upload_gaunt(const float* g) { cudaMemcpyToSymbol(c_gaunt, g, sizeof(float) * kNG); }
+
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kTile = 32;
+
+struct WarpSmem {
+    float A[kNmax * kApad];
+    float dA[kNmax * kApad];
+    float dAT[kNLM][kNmax];
+    float4 nb[kAceNbrCap];
+    int nbj[kAceNbrCap];
+    float tileY[kTile][kNLM];
+    float tileG[kTile][kNmax];
+};
+
+// ---------------------------------------------------------------------------------
+// radial basis g_n = T_n(2r/rc - 1) fc(r), fc = (1 + cos(pi r/rc))/2, and dg_n/dr
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ void radial(float r, float rc, float* g, float* dg) {
+    const float x = 2.0f * r / rc - 1.0f, dx = 2.0f / rc;
+    float sn, cs;
+    sincospif(r / rc, &sn, &cs);
+    const float fc = 0.5f * (1.0f + cs), dfc = -0.5f * 3.14159265358979f / rc * sn;
+    float T0 = 1.0f, T1 = x, D0 = 0.0f, D1 = 1.0f;
+    g[0] = fc; dg[0] = dfc;
+    g[1] = x * fc; dg[1] = dx * fc + x * dfc;
+#pragma unroll
+    for (int n = 2; n < kNmax; ++n) {
+        float T2 = 2.0f * x * T1 - T0;
+        float D2 = 2.0f * T1 + 2.0f * x * D1 - D0;
+        g[n] = T2 * fc;
+        dg[n] = D2 * dx * fc + T2 * dfc;
+        T0 = T1; T1 = T2; D0 = D1; D1 = D2;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// real orthonormal spherical harmonics as homogeneous Cartesian polynomials S_lm
+// evaluated at the unit vector (x, y, z); index l*l + l + m
+// ---------------------------------------------------------------------------------
+#define YC0 0.28209479177387814f
+#define YC1 0.4886025119029199f
+#define YC2A 1.0925484305920792f
+#define YC2B 0.31539156525252005f
+#define YC2C 0.5462742152960396f
+#define YC3A 0.5900435899266435f
+#define YC3B 2.890611442640554f
+#define YC3C 0.45704579946446574f
+#define YC3D 0.3731763325901154f
+#define YC3E 1.445305721320277f
+#define YC4A 2.5033429417967046f
+#define YC4B 1.7701307697799304f
+#define YC4C 0.9461746957575601f
+#define YC4D 0.6690465435572892f
+#define YC4E 0.10578554691520431f
+#define YC4F 0.47308734787878004f
+#define YC4G 0.6258357354491761f
+
+__device__ __forceinline__ void ylm(float x, float y, float z, float* Y) {
+    const float x2 = x * x, y2 = y * y, z2 = z * z, r2 = x2 + y2 + z2;
+    Y[0] = YC0;
+    Y[1] = YC1 * y; Y[2] = YC1 * z; Y[3] = YC1 * x;
+    Y[4] = YC2A * x * y; Y[5] = YC2A * y * z; Y[6] = YC2B * (2.0f * z2 - x2 - y2); Y[7] = YC2A * x * z;
+    Y[8] = YC2C * (x2 - y2);
+    Y[9] = YC3A * y * (3.0f * x2 - y2); Y[10] = YC3B * x * y * z; Y[11] = YC3C * y * (4.0f * z2 - x2 - y2);
+    Y[12] = YC3D * z * (2.0f * z2 - 3.0f * x2 - 3.0f * y2); Y[13] = YC3C * x * (4.0f * z2 - x2 - y2);
+    Y[14] = YC3E * z * (x2 - y2); Y[15] = YC3A * x * (x2 - 3.0f * y2);
+    Y[16] = YC4A * x * y * (x2 - y2); Y[17] = YC4B * y * z * (3.0f * x2 - y2);
+    Y[18] = YC4C * x * y * (6.0f * z2 - x2 - y2); Y[19] = YC4D * y * z * (4.0f * z2 - 3.0f * x2 - 3.0f * y2);
+    Y[20] = YC4E * (35.0f * z2 * z2 - 30.0f * z2 * r2 + 3.0f * r2 * r2);
+    Y[21] = YC4D * x * z * (4.0f * z2 - 3.0f * x2 - 3.0f * y2); Y[22] = YC4F * (x2 - y2) * (6.0f * z2 - x2 - y2);
+    Y[23] = YC4B * x * z * (x2 - 3.0f * y2); Y[24] = YC4G * (x2 * x2 - 6.0f * x2 * y2 + y2 * y2);
+}
+
+// f += a * grad S_lm (Cartesian gradient of the homogeneous polynomial) for all lm,
+// s += (b - l a / r) S_lm, with a_lm, b_lm supplied by the functor.
+template <class AB>
+__device__ __forceinline__ void force_terms(float x, float y, float z, float rinv, AB ab, float& s, float& gx, float& gy,
+                                            float& gz) {
+    const float x2 = x * x, y2 = y * y, z2 = z * z, r2 = x2 + y2 + z2;
+    float a, b;
+#define TERM(LM, L, SV, GX, GY, GZ)            \
+    ab(LM, a, b);                              \
+    s = fmaf(b - (float)(L) * a * rinv, (SV), s); \
+    gx = fmaf(a, (GX), gx);                    \
+    gy = fmaf(a, (GY), gy);                    \
+    gz = fmaf(a, (GZ), gz);
+    TERM(0, 0, YC0, 0.f, 0.f, 0.f)
+    TERM(1, 1, YC1 * y, 0.f, YC1, 0.f)
+    TERM(2, 1, YC1 * z, 0.f, 0.f, YC1)
+    TERM(3, 1, YC1 * x, YC1, 0.f, 0.f)
+    TERM(4, 2, YC2A * x * y, YC2A * y, YC2A * x, 0.f)
+    TERM(5, 2, YC2A * y * z, 0.f, YC2A * z, YC2A * y)
+    TERM(6, 2, YC2B * (2.0f * z2 - x2 - y2), -2.0f * YC2B * x, -2.0f * YC2B * y, 4.0f * YC2B * z)
+    TERM(7, 2, YC2A * x * z, YC2A * z, 0.f, YC2A * x)
+    TERM(8, 2, YC2C * (x2 - y2), 2.0f * YC2C * x, -2.0f * YC2C * y, 0.f)
+    TERM(9, 3, YC3A * y * (3.0f * x2 - y2), 6.0f * YC3A * x * y, 3.0f * YC3A * (x2 - y2), 0.f)
+    TERM(10, 3, YC3B * x * y * z, YC3B * y * z, YC3B * x * z, YC3B * x * y)
+    TERM(11, 3, YC3C * y * (4.0f * z2 - x2 - y2), -2.0f * YC3C * x * y, YC3C * (4.0f * z2 - x2 - 3.0f * y2),
+         8.0f * YC3C * y * z)
+    TERM(12, 3, YC3D * z * (2.0f * z2 - 3.0f * x2 - 3.0f * y2), -6.0f * YC3D * x * z, -6.0f * YC3D * y * z,
+         YC3D * (6.0f * z2 - 3.0f * x2 - 3.0f * y2))
+    TERM(13, 3, YC3C * x * (4.0f * z2 - x2 - y2), YC3C * (4.0f * z2 - 3.0f * x2 - y2), -2.0f * YC3C * x * y,
+         8.0f * YC3C * x * z)
+    TERM(14, 3, YC3E * z * (x2 - y2), 2.0f * YC3E * x * z, -2.0f * YC3E * y * z, YC3E * (x2 - y2))
+    TERM(15, 3, YC3A * x * (x2 - 3.0f * y2), 3.0f * YC3A * (x2 - y2), -6.0f * YC3A * x * y, 0.f)
+    TERM(16, 4, YC4A * x * y * (x2 - y2), YC4A * y * (3.0f * x2 - y2), YC4A * x * (x2 - 3.0f * y2), 0.f)
+    TERM(17, 4, YC4B * y * z * (3.0f * x2 - y2), 6.0f * YC4B * x * y * z, 3.0f * YC4B * z * (x2 - y2),
+         YC4B * y * (3.0f * x2 - y2))
+    TERM(18, 4, YC4C * x * y * (6.0f * z2 - x2 - y2), YC4C * y * (6.0f * z2 - 3.0f * x2 - y2),
+         YC4C * x * (6.0f * z2 - x2 - 3.0f * y2), 12.0f * YC4C * x * y * z)
+    TERM(19, 4, YC4D * y * z * (4.0f * z2 - 3.0f * x2 - 3.0f * y2), -6.0f * YC4D * x * y * z,
+         YC4D * z * (4.0f * z2 - 3.0f * x2 - 9.0f * y2), YC4D * y * (12.0f * z2 - 3.0f * x2 - 3.0f * y2))
+    TERM(20, 4, YC4E * (35.0f * z2 * z2 - 30.0f * z2 * r2 + 3.0f * r2 * r2), 12.0f * YC4E * x * (r2 - 5.0f * z2),
+         12.0f * YC4E * y * (r2 - 5.0f * z2), 16.0f * YC4E * z * (5.0f * z2 - 3.0f * r2))
+    TERM(21, 4, YC4D * x * z * (4.0f * z2 - 3.0f * x2 - 3.0f * y2), YC4D * z * (4.0f * z2 - 9.0f * x2 - 3.0f * y2),
+         -6.0f * YC4D * x * y * z, YC4D * x * (12.0f * z2 - 3.0f * x2 - 3.0f * y2))
+    TERM(22, 4, YC4F * (x2 - y2) * (6.0f * z2 - x2 - y2), YC4F * x * (12.0f * z2 - 4.0f * x2),
+         YC4F * y * (4.0f * y2 - 12.0f * z2), 12.0f * YC4F * z * (x2 - y2))
+    TERM(23, 4, YC4B * x * z * (x2 - 3.0f * y2), 3.0f * YC4B * z * (x2 - y2), -6.0f * YC4B * x * y * z,
+         YC4B * x * (x2 - 3.0f * y2))
+    TERM(24, 4, YC4G * (x2 * x2 - 6.0f * x2 * y2 + y2 * y2), 4.0f * YC4G * x * (x2 - 3.0f * y2),
+         4.0f * YC4G * y * (y2 - 3.0f * x2), 0.f)
+#undef TERM
+}
+
+// ---------------------------------------------------------------------------------
+// three-factor products, one l-triple at a time, operands in registers
+// ---------------------------------------------------------------------------------
+template <int T>
+struct Tri {
+    static constexpr int L1 = tri_l(T, 0), L2 = tri_l(T, 1), L3 = tri_l(T, 2);
+    static constexpr int W1 = 2 * L1 + 1, W2 = 2 * L2 + 1, W3 = 2 * L3 + 1;
+    static constexpr int N = tri_count(T), OFF = tri_offset(T);
+    static constexpr int B1 = lblk(L1), B2 = lblk(L2), B3 = lblk(L3);
+    template <int E> static constexpr int m1() { return pat_entry(L1, L2, L3, E, 0) + L1; }
+    template <int E> static constexpr int m2() { return pat_entry(L1, L2, L3, E, 1) + L2; }
+    template <int E> static constexpr int m3() { return pat_entry(L1, L2, L3, E, 2) + L3; }
+};
+
+template <int T, int E>
+__device__ __forceinline__ void ent_p(float* P, const float* A1, const float* A2) {
+    using R = Tri<T>;
+    P[R::template m3<E>()] = fmaf(c_gaunt[R::OFF + E] * A1[R::template m1<E>()], A2[R::template m2<E>()],
+                                  P[R::template m3<E>()]);
+}
+template <int T, int... E>
+__device__ __forceinline__ void all_p(float* P, const float* A1, const float* A2, std::integer_sequence<int, E...>) {
+    (ent_p<T, E>(P, A1, A2), ...);
+}
+
+template <int T, int E>
+__device__ __forceinline__ void ent_x(float* d1, float* d2, const float* A1, const float* A2, const float* Q) {
+    using R = Tri<T>;
+    const float u = c_gaunt[R::OFF + E] * Q[R::template m3<E>()];
+    d1[R::template m1<E>()] = fmaf(u, A2[R::template m2<E>()], d1[R::template m1<E>()]);
+    d2[R::template m2<E>()] = fmaf(u, A1[R::template m1<E>()], d2[R::template m2<E>()]);
+}
+template <int T, int... E>
+__device__ __forceinline__ void all_x(float* d1, float* d2, const float* A1, const float* A2, const float* Q,
+                                      std::integer_sequence<int, E...>) {
+    (ent_x<T, E>(d1, d2, A1, A2, Q), ...);
+}
+
+template <int T, int E>
+__device__ __forceinline__ void ent_y(float* d3, const float* A1, const float* Tm) {
+    using R = Tri<T>;
+    d3[R::template m3<E>()] = fmaf(c_gaunt[R::OFF + E] * A1[R::template m1<E>()], Tm[R::template m2<E>()],
+                                   d3[R::template m3<E>()]);
+}
+template <int T, int... E>
+__device__ __forceinline__ void all_y(float* d3, const float* A1, const float* Tm, std::integer_sequence<int, E...>) {
+    (ent_y<T, E>(d3, A1, Tm), ...);
+}
+
+template <int W>
+__device__ __forceinline__ void load_row(float* dst, const float* src) {
+#pragma unroll
+    for (int k = 0; k < W; ++k) dst[k] = src[k];
+}
+
+// sum_k P[k] * row[k] over a 16-byte aligned shared-memory row
+template <int W>
+__device__ __forceinline__ float dot_row(const float* P, const float* row) {
+    float r = 0.0f;
+#pragma unroll
+    for (int k = 0; k < W; k += 4) {
+        float4 v = *reinterpret_cast<const float4*>(row + k);
+        r = fmaf(P[k], v.x, r);
+        if (k + 1 < W) r = fmaf(P[k + 1], v.y, r);
+        if (k + 2 < W) r = fmaf(P[k + 2], v.z, r);
+        if (k + 3 < W) r = fmaf(P[k + 3], v.w, r);
+    }
+    return r;
+}
+
+template <int T>
+__device__ __forceinline__ void nu3_forward(const float* As, const AceDev& C, int lane, float& p1, float& p2) {
+    using R = Tri<T>;
+#pragma unroll
+    for (int pp = 0; pp < 2; ++pp) {
+        const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
+        float A1[R::W1], A2[R::W2], P[R::W3];
+        load_row<R::W1>(A1, As + n1 * kApad + R::B1);
+        load_row<R::W2>(A2, As + n2 * kApad + R::B2);
+#pragma unroll
+        for (int k = 0; k < R::W3; ++k) P[k] = 0.0f;
+        all_p<T>(P, A1, A2, std::make_integer_sequence<int, R::N>{});
+        const float* c1 = C.c3[0][T][q];
+        const float* c2 = C.c3[1][T][q];
+        float s1 = 0.0f, s2 = 0.0f;
+#pragma unroll
+        for (int n3 = 0; n3 < kNmax; ++n3) {
+            const float r = dot_row<R::W3>(P, As + n3 * kApad + R::B3);
+            s1 = fmaf(c1[n3], r, s1);
+            s2 = fmaf(c2[n3], r, s2);
+        }
+        p1 += s1;
+        p2 += s2;
+    }
+}
+
+template <int T>
+__device__ __forceinline__ void nu3_adjoint(const float* As, float* dAs, const AceDev& C, float s, int lane) {
+    using R = Tri<T>;
+    // (n1, n2) mapping: gradients with respect to the first and second factor
+    float d2[R::W2];
+#pragma unroll
+    for (int k = 0; k < R::W2; ++k) d2[k] = 0.0f;
+#pragma unroll
+    for (int pp = 0; pp < 2; ++pp) {
+        const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
+        float A1[R::W1], A2[R::W2], Q[R::W3], d1[R::W1], ce[kNmax];
+        load_row<R::W1>(A1, As + n1 * kApad + R::B1);
+        load_row<R::W2>(A2, As + n2 * kApad + R::B2);
+#pragma unroll
+        for (int k = 0; k < kNmax; ++k) ce[k] = fmaf(s, C.c3[1][T][q][k], C.c3[0][T][q][k]);
+#pragma unroll
+        for (int m = 0; m < R::W3; ++m) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int n3 = 0; n3 < kNmax; ++n3) acc = fmaf(ce[n3], As[n3 * kApad + R::B3 + m], acc);
+            Q[m] = acc;
+        }
+#pragma unroll
+        for (int k = 0; k < R::W1; ++k) d1[k] = 0.0f;
+        all_x<T>(d1, d2, A1, A2, Q, std::make_integer_sequence<int, R::N>{});
+#pragma unroll
+        for (int k = 0; k < R::W1; ++k) {
+            float v = d1[k];
+            v += __shfl_xor_sync(0xffffffffu, v, 1);
+            v += __shfl_xor_sync(0xffffffffu, v, 2);
+            v += __shfl_xor_sync(0xffffffffu, v, 4);
+            d1[k] = v;
+        }
+        if ((lane & 7) == 0) {
+#pragma unroll
+            for (int k = 0; k < R::W1; ++k) dAs[n1 * kApad + R::B1 + k] += d1[k];
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int k = 0; k < R::W2; ++k) {
+        float v = d2[k];
+        v += __shfl_xor_sync(0xffffffffu, v, 8);
+        v += __shfl_xor_sync(0xffffffffu, v, 16);
+        d2[k] = v;
+    }
+    if (lane < 8) {
+#pragma unroll
+        for (int k = 0; k < R::W2; ++k) dAs[lane * kApad + R::B2 + k] += d2[k];
+    }
+    __syncwarp();
+    // (n1, n3) mapping: gradient with respect to the third factor
+    float d3[R::W3];
+#pragma unroll
+    for (int k = 0; k < R::W3; ++k) d3[k] = 0.0f;
+#pragma unroll
+    for (int pp = 0; pp < 2; ++pp) {
+        const int q = lane + 32 * pp, n1 = q >> 3, n3 = q & 7;
+        float A1[R::W1], Tm[R::W2], ce[kNmax];
+        load_row<R::W1>(A1, As + n1 * kApad + R::B1);
+#pragma unroll
+        for (int n2 = 0; n2 < kNmax; ++n2) ce[n2] = fmaf(s, C.c3[1][T][n1 * 8 + n2][n3], C.c3[0][T][n1 * 8 + n2][n3]);
+#pragma unroll
+        for (int m = 0; m < R::W2; ++m) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int n2 = 0; n2 < kNmax; ++n2) acc = fmaf(ce[n2], As[n2 * kApad + R::B2 + m], acc);
+            Tm[m] = acc;
+        }
+        all_y<T>(d3, A1, Tm, std::make_integer_sequence<int, R::N>{});
+    }
+#pragma unroll
+    for (int k = 0; k < R::W3; ++k) {
+        float v = d3[k];
+        v += __shfl_xor_sync(0xffffffffu, v, 8);
+        v += __shfl_xor_sync(0xffffffffu, v, 16);
+        d3[k] = v;
+    }
+    if (lane < 8) {
+#pragma unroll
+        for (int k = 0; k < R::W3; ++k) dAs[lane * kApad + R::B3 + k] += d3[k];
+    }
+    __syncwarp();
+}
+
+template <int... T>
+__device__ __forceinline__ void nu3_forward_all(const float* As, const AceDev& C, int lane, float& p1, float& p2,
+                                                std::integer_sequence<int, T...>) {
+    (nu3_forward<T>(As, C, lane, p1, p2), ...);
+}
+template <int... T>
+__device__ __forceinline__ void nu3_adjoint_all(const float* As, float* dAs, const AceDev& C, float s, int lane,
+                                                std::integer_sequence<int, T...>) {
+    (nu3_adjoint<T>(As, dAs, C, s, lane), ...);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void fix_add(unsigned long long* p, float v) {
+    long long q = __float2ll_rn(v * 1099511627776.0f);
+    atomicAdd(p, (unsigned long long)q);
+}
+
+__global__ void __launch_bounds__(kWarps * 32, 1)
+k_ace(const float4* __restrict__ pos4, const int* __restrict__ nbr, const int* __restrict__ nnbr, int n,
+      const float4* __restrict__ Dtab, int ncode, const AceDev* __restrict__ tab, const int* __restrict__ ace_list,
+      const float* __restrict__ wv, int* __restrict__ flags, float* __restrict__ e_ace, float* __restrict__ vir,
+      unsigned long long* __restrict__ acc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AceDev& C = *reinterpret_cast<AceDev*>(smem_raw);
+    float4* Ds = reinterpret_cast<float4*>(smem_raw + sizeof(AceDev));
+    WarpSmem* WS = reinterpret_cast<WarpSmem*>(smem_raw + sizeof(AceDev) + 128 * sizeof(float4));
+    {
+        const int4* src = reinterpret_cast<const int4*>(tab);
+        int4* dst = reinterpret_cast<int4*>(smem_raw);
+        for (int k = threadIdx.x; k < (int)(sizeof(AceDev) / 16); k += blockDim.x) dst[k] = src[k];
+        for (int k = threadIdx.x; k < ncode; k += blockDim.x) Ds[k] = Dtab[k];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpSmem& S = WS[warp];
+    const float rc = C.rc, rc2 = rc * rc, nrefi = C.nref_inv;
+    const int n_ace = flags[kFlagNAce];
+    // lane -> (l, m) for the 25 lanes that own an A column
+    int lam_l = 0;
+    if (lane >= 1) lam_l = 1;
+    if (lane >= 4) lam_l = 2;
+    if (lane >= 9) lam_l = 3;
+    if (lane >= 16) lam_l = 4;
+    const int lam_pad = lblk(lam_l) + (lane - lam_l * lam_l);
+
+    for (int a = blockIdx.x * kWarps + warp; a < n_ace; a += gridDim.x * kWarps) {
+        const int i = ace_list[a];
+        const float4 p = pos4[i];
+        const float wi = wv[i];
+        const int m = nnbr[i];
+        // 1. neighbours within the ACE cutoff
+        int cnt = 0;
+        for (int k0 = 0; k0 < m; k0 += 32) {
+            const int k = k0 + lane;
+            bool in = false;
+            float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+            int j = 0;
+            if (k < m) {
+                const int e = nbr[(size_t)k * n + i];
+                j = e & kNbrMask;
+                const float4 d = Ds[(unsigned)e >> kNbrShift];
+                const float4 q = pos4[j];
+                dx = q.x + d.x - p.x; dy = q.y + d.y - p.y; dz = q.z + d.z - p.z;
+                r2 = dx * dx + dy * dy + dz * dz;
+                in = r2 < rc2 && r2 > 0.0f;
+            }
+            const unsigned bm = __ballot_sync(0xffffffffu, in);
+            const int pos = cnt + __popc(bm & ((1u << lane) - 1u));
+            if (in && pos < kAceNbrCap) { S.nb[pos] = make_float4(dx, dy, dz, sqrtf(r2)); S.nbj[pos] = j; }
+            cnt += __popc(bm);
+        }
+        if (cnt > kAceNbrCap) {
+            if (lane == 0) { atomicOr(&flags[kFlagErr], kErrAceCapacity); flags[kFlagBad] = i; }
+            continue;
+        }
+        __syncwarp();
+        // 2. atomic base
+        float accA[kNmax];
+#pragma unroll
+        for (int q = 0; q < kNmax; ++q) accA[q] = 0.0f;
+        for (int t0 = 0; t0 < cnt; t0 += kTile) {
+            const int jj = t0 + lane;
+            if (jj < cnt) {
+                const float4 v = S.nb[jj];
+                const float ri = 1.0f / v.w;
+                float g[kNmax], dg[kNmax], Y[kNLM];
+                radial(v.w, rc, g, dg);
+                ylm(v.x * ri, v.y * ri, v.z * ri, Y);
+#pragma unroll
+                for (int q = 0; q < kNmax; ++q) S.tileG[lane][q] = g[q];
+#pragma unroll
+                for (int q = 0; q < kNLM; ++q) S.tileY[lane][q] = Y[q];
+            }
+            __syncwarp();
+            const int nt = min(kTile, cnt - t0);
+            if (lane < kNLM) {
+                for (int jj2 = 0; jj2 < nt; ++jj2) {
+                    const float y = S.tileY[jj2][lane];
+                    const float4 g0 = *reinterpret_cast<const float4*>(&S.tileG[jj2][0]);
+                    const float4 g1 = *reinterpret_cast<const float4*>(&S.tileG[jj2][4]);
+                    accA[0] = fmaf(y, g0.x, accA[0]); accA[1] = fmaf(y, g0.y, accA[1]);
+                    accA[2] = fmaf(y, g0.z, accA[2]); accA[3] = fmaf(y, g0.w, accA[3]);
+                    accA[4] = fmaf(y, g1.x, accA[4]); accA[5] = fmaf(y, g1.y, accA[5]);
+                    accA[6] = fmaf(y, g1.z, accA[6]); accA[7] = fmaf(y, g1.w, accA[7]);
+                }
+            }
+            __syncwarp();
+        }
+        for (int k = lane; k < kNmax * kApad; k += 32) { S.A[k] = 0.0f; S.dA[k] = 0.0f; }
+        __syncwarp();
+        if (lane < kNLM) {
+#pragma unroll
+            for (int q = 0; q < kNmax; ++q) S.A[q * kApad + lam_pad] = accA[q] * nrefi;
+        }
+        __syncwarp();
+        // 3. the two densities
+        float p1 = 0.0f, p2 = 0.0f;
+        if (lane < kNmax) {
+            const float a0 = S.A[lane * kApad];
+            p1 = C.c1[0][lane] * a0;
+            p2 = C.c1[1][lane] * a0;
+        }
+#pragma unroll
+        for (int l = 0; l <= kLmax; ++l) {
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp) {
+                const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
+                float mm = 0.0f;
+#pragma unroll
+                for (int k = 0; k < 2 * l + 1; ++k)
+                    mm = fmaf(S.A[n1 * kApad + lblk(l) + k], S.A[n2 * kApad + lblk(l) + k], mm);
+                p1 = fmaf(C.c2[0][l][q], mm, p1);
+                p2 = fmaf(C.c2[1][l][q], mm, p2);
+            }
+        }
+        nu3_forward_all(S.A, C, lane, p1, p2, std::make_integer_sequence<int, kNT>{});
+        p1 = warp_sum(p1);
+        p2 = warp_sum(p2);
+        const float phi2 = C.c2_0 + p2;
+        if (!(phi2 > 1e-3f) || !(p1 == p1)) {
+            if (lane == 0) { atomicOr(&flags[kFlagErr], kErrDomain); flags[kFlagBad] = i; e_ace[i] = __int_as_float(0x7fc00000); }
+            continue;
+        }
+        const float sq = sqrtf(phi2);
+        const float E = p1 + sq;
+        const float s = 0.5f / sq;
+        // 4. adjoint dE/dA
+        if (lane < kNmax) S.dA[lane * kApad] += fmaf(s, C.c1[1][lane], C.c1[0][lane]);
+        __syncwarp();
+#pragma unroll
+        for (int l = 0; l <= kLmax; ++l) {
+            constexpr int WM = 9;
+            float d2[WM];
+#pragma unroll
+            for (int k = 0; k < WM; ++k) d2[k] = 0.0f;
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp) {
+                const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
+                const float c = fmaf(s, C.c2[1][l][q], C.c2[0][l][q]);
+                float d1[WM];
+#pragma unroll
+                for (int k = 0; k < 2 * l + 1; ++k) {
+                    const float a1 = S.A[n1 * kApad + lblk(l) + k], a2 = S.A[n2 * kApad + lblk(l) + k];
+                    d1[k] = c * a2;
+                    d2[k] = fmaf(c, a1, d2[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < 2 * l + 1; ++k) {
+                    float v = d1[k];
+                    v += __shfl_xor_sync(0xffffffffu, v, 1);
+                    v += __shfl_xor_sync(0xffffffffu, v, 2);
+                    v += __shfl_xor_sync(0xffffffffu, v, 4);
+                    d1[k] = v;
+                }
+                if ((lane & 7) == 0) {
+#pragma unroll
+                    for (int k = 0; k < 2 * l + 1; ++k) S.dA[n1 * kApad + lblk(l) + k] += d1[k];
+                }
+                __syncwarp();
+            }
+#pragma unroll
+            for (int k = 0; k < 2 * l + 1; ++k) {
+                float v = d2[k];
+                v += __shfl_xor_sync(0xffffffffu, v, 8);
+                v += __shfl_xor_sync(0xffffffffu, v, 16);
+                d2[k] = v;
+            }
+            if (lane < 8) {
+#pragma unroll
+                for (int k = 0; k < 2 * l + 1; ++k) S.dA[lane * kApad + lblk(l) + k] += d2[k];
+            }
+            __syncwarp();
+        }
+        nu3_adjoint_all(S.A, S.dA, C, s, lane, std::make_integer_sequence<int, kNT>{});
+        if (lane < kNLM) {
+#pragma unroll
+            for (int q = 0; q < kNmax; ++q) S.dAT[lane][q] = S.dA[q * kApad + lam_pad];
+        }
+        __syncwarp();
+        // 5. pair forces
+        float fsx = 0.f, fsy = 0.f, fsz = 0.f;
+        float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f, v4 = 0.f, v5 = 0.f;
+        for (int t0 = 0; t0 < cnt; t0 += 32) {
+            const int jj = t0 + lane;
+            if (jj < cnt) {
+                const float4 v = S.nb[jj];
+                const int j = S.nbj[jj];
+                const float ri = 1.0f / v.w;
+                const float ux = v.x * ri, uy = v.y * ri, uz = v.z * ri;
+                float g[kNmax], dg[kNmax];
+                radial(v.w, rc, g, dg);
+                float sc = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+                auto ab = [&](int lm, float& aa, float& bb) {
+                    const float4 d0 = *reinterpret_cast<const float4*>(&S.dAT[lm][0]);
+                    const float4 d1 = *reinterpret_cast<const float4*>(&S.dAT[lm][4]);
+                    aa = d0.x * g[0] + d0.y * g[1] + d0.z * g[2] + d0.w * g[3] + d1.x * g[4] + d1.y * g[5] + d1.z * g[6] + d1.w * g[7];
+                    bb = d0.x * dg[0] + d0.y * dg[1] + d0.z * dg[2] + d0.w * dg[3] + d1.x * dg[4] + d1.y * dg[5] + d1.z * dg[6] + d1.w * dg[7];
+                };
+                force_terms(ux, uy, uz, ri, ab, sc, gx, gy, gz);
+                const float fx = nrefi * (sc * ux + gx * ri) * wi;
+                const float fy = nrefi * (sc * uy + gy * ri) * wi;
+                const float fz = nrefi * (sc * uz + gz * ri) * wi;
+                fix_add(&acc[j], -fx);
+                fix_add(&acc[(size_t)n + j], -fy);
+                fix_add(&acc[(size_t)2 * n + j], -fz);
+                fsx += fx; fsy += fy; fsz += fz;
+                v0 -= v.x * fx; v1 -= v.y * fy; v2 -= v.z * fz;
+                v3 -= 0.5f * (v.x * fy + v.y * fx); v4 -= 0.5f * (v.x * fz + v.z * fx); v5 -= 0.5f * (v.y * fz + v.z * fy);
+            }
+        }
+        fsx = warp_sum(fsx); fsy = warp_sum(fsy); fsz = warp_sum(fsz);
+        v0 = warp_sum(v0); v1 = warp_sum(v1); v2 = warp_sum(v2);
+        v3 = warp_sum(v3); v4 = warp_sum(v4); v5 = warp_sum(v5);
+        if (lane == 0) {
+            fix_add(&acc[i], fsx);
+            fix_add(&acc[(size_t)n + i], fsy);
+            fix_add(&acc[(size_t)2 * n + i], fsz);
+            e_ace[i] = E;
+            vir[i] = v0; vir[n + i] = v1; vir[2 * n + i] = v2; vir[3 * n + i] = v3; vir[4 * n + i] = v4; vir[5 * n + i] = v5;
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+size_t ace_smem_bytes() { return sizeof(AceDev) + 128 * sizeof(float4) + kWarps * sizeof(WarpSmem); }
+
+int launch_ace(Ctx& c, cudaStream_t s) {
+    static int configured = -1;
+    const size_t smem = ace_smem_bytes();
+    if (configured != c.dev) {
+        cudaFuncSetAttribute(k_ace, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        configured = c.dev;
+    }
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c.dev);
+    k_ace<<<nsm, kWarps * 32, smem, s>>>(c.pos4, c.nbr, c.nnbr, c.n, c.D, c.grid.ncode, c.ace_d, c.ace_list, c.w,
+                                         c.flags, c.e_ace, c.vir_ace, c.acc);
+    return 1;
+}
+
+}  // namespace ap

@@ -1,0 +1,242 @@
+// kernels_md.cu -- blend, indenter, reductions and velocity-Verlet integration.
+//
+// Blend (Sec. 2.2.3, Eq. energy_hyb with w = 1 - lambda): E_i = w_i E_i^ACE + (1 - w_i)
+// E_i^EAM.  The EAM and ACE force shares already carry their weights; a position-
+// dependent weight adds -grad w_i (E_i^ACE - E_i^EAM).  Indenter (Sec. 2.1, Eq.
+// V_indenter): V = K/3 (R - d)^3 for d < R, F = K (R - d)^2 (r - c)/d; load (Sec. 3.1,
+// Eq. P_ind) = sum F . dir.  Totals are summed per block in FP64 and then by one block
+// in a fixed order, so they are reproducible run to run.
+#include "ap_internal.h"
+
+namespace ap {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kFtm = 0.0096485332;      // 1 eV/(Angstrom amu) in Angstrom/fs^2
+constexpr int kNP = 10;                     // e_pot, e_ind, vir[6], load, spare
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
+    return s;                               // valid on thread 0
+}
+
+__device__ __forceinline__ void min_image(const GridDev& g, double* d) {
+    double s[3];
+    for (int k = 0; k < 3; ++k) s[k] = d[0] * g.hinv[k] + d[1] * g.hinv[3 + k] + d[2] * g.hinv[6 + k];
+    for (int k = 0; k < 3; ++k)
+        if (g.periodic[k]) {
+            double m = floor(s[k] + 0.5);
+            for (int q = 0; q < 3; ++q) d[q] -= m * g.h[3 * k + q];
+        }
+}
+
+__global__ void k_pos_in(const double* __restrict__ pos, int n, double* __restrict__ x) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    x[i] = pos[3 * i];
+    x[n + i] = pos[3 * i + 1];
+    x[2 * n + i] = pos[3 * i + 2];
+}
+
+__global__ void __launch_bounds__(kRedBlock) k_blend(
+    const double* __restrict__ x, int n, const GridDev g, const DynDev dy, const double* __restrict__ tptr,
+    const float* __restrict__ wv, float* __restrict__ f, unsigned long long* __restrict__ acc,
+    const float* __restrict__ e_ace, const double* __restrict__ e_eam, double c1_0,
+    const float* __restrict__ vir_eam, const float* __restrict__ vir_ace, double* __restrict__ e_atom,
+    double* __restrict__ partials, float* __restrict__ out_aos, int* __restrict__ flags) {
+    __shared__ double sh[32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc_e = 0.0, acc_i = 0.0, acc_l = 0.0, vv[6] = {0, 0, 0, 0, 0, 0};
+    if (i < n) {
+        const double wi = wv[i], ui = 1.0 - wi;
+        double F[3];
+        for (int k = 0; k < 3; ++k) {
+            const long long q = (long long)acc[(size_t)k * n + i];
+            acc[(size_t)k * n + i] = 0ull;
+            F[k] = (double)f[(size_t)k * n + i] + (double)q * (1.0 / kFixScale);
+        }
+        const double eA = wi > 0.0 ? c1_0 + (double)e_ace[i] : 0.0;
+        const double eE = ui > 0.0 ? e_eam[i] : 0.0;
+        const double Ei = wi * eA + ui * eE;
+        const double r[3] = {x[i], x[n + i], x[2 * n + i]};
+        const double t = *tptr;
+        if (dy.reg_kind == AP_REGION_SPHERE && wi > 0.0 && wi < 1.0) {
+            double d[3];
+            for (int k = 0; k < 3; ++k) d[k] = r[k] - (dy.reg_c0[k] - (dy.follow ? dy.ind_vel[k] * t : 0.0));
+            min_image(g, d);
+            const double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            if (dist > dy.r_in && dist < dy.r_in + dy.r_sw) {
+                const double ds = -0.5 * kPi / dy.r_sw * sin(kPi * (dist - dy.r_in) / dy.r_sw);
+                const double de = eA - eE;
+                for (int k = 0; k < 3; ++k) F[k] -= ds * d[k] / dist * de;
+            }
+        }
+        double V = 0.0;
+        if (dy.ind_on) {
+            double d[3];
+            for (int k = 0; k < 3; ++k) d[k] = r[k] - (dy.ind_c0[k] - dy.ind_vel[k] * t);
+            min_image(g, d);
+            const double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            if (dist < dy.R && dist > 0.0) {
+                const double h = dy.R - dist;
+                V = dy.K * h * h * h / 3.0;
+                double fl = 0.0;
+                for (int k = 0; k < 3; ++k) {
+                    const double fi = dy.K * h * h * d[k] / dist;
+                    F[k] += fi;
+                    fl += fi * dy.ind_dir[k];
+                }
+                acc_l = fl;
+            }
+        }
+        for (int k = 0; k < 3; ++k) f[(size_t)k * n + i] = (float)F[k];
+        if (out_aos)
+            for (int k = 0; k < 3; ++k) out_aos[3 * (size_t)i + k] = (float)F[k];
+        e_atom[i] = Ei + V;
+        acc_e = Ei;
+        acc_i = V;
+        for (int k = 0; k < 6; ++k) vv[k] = (double)vir_eam[(size_t)k * n + i] + (wi > 0.0 ? (double)vir_ace[(size_t)k * n + i] : 0.0);
+        if (!(Ei == Ei) || !(F[0] == F[0]) || !(F[1] == F[1]) || !(F[2] == F[2])) {
+            atomicOr(&flags[kFlagErr], kErrDomain);
+            flags[kFlagBad] = i;
+        }
+    }
+    double* out = partials + (size_t)blockIdx.x * kNP;
+    double s;
+    s = block_sum(acc_e, sh); if (threadIdx.x == 0) out[0] = s;
+    s = block_sum(acc_i, sh); if (threadIdx.x == 0) out[1] = s;
+    for (int k = 0; k < 6; ++k) { s = block_sum(vv[k], sh); if (threadIdx.x == 0) out[2 + k] = s; }
+    s = block_sum(acc_l, sh); if (threadIdx.x == 0) out[8] = s;
+}
+
+// energies only (after the FP64 EAM energy pass): per-atom E_i + V_ind and the two
+// energy partial sums; forces, virial and load partials stay those of k_blend
+__global__ void __launch_bounds__(kRedBlock) k_energy_blend(
+    const double* __restrict__ x, int n, const GridDev g, const DynDev dy, const double* __restrict__ tptr,
+    const float* __restrict__ wv, const float* __restrict__ e_ace, const double* __restrict__ e_eam, double c1_0,
+    double* __restrict__ e_atom, double* __restrict__ partials) {
+    __shared__ double sh[32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc_e = 0.0, acc_i = 0.0;
+    if (i < n) {
+        const double wi = wv[i], ui = 1.0 - wi;
+        const double Ei = (wi > 0.0 ? wi * (c1_0 + (double)e_ace[i]) : 0.0) + (ui > 0.0 ? ui * e_eam[i] : 0.0);
+        double V = 0.0;
+        if (dy.ind_on) {
+            const double t = *tptr;
+            double d[3];
+            for (int k = 0; k < 3; ++k) d[k] = x[(size_t)k * n + i] - (dy.ind_c0[k] - dy.ind_vel[k] * t);
+            min_image(g, d);
+            const double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            if (dist < dy.R && dist > 0.0) {
+                const double h = dy.R - dist;
+                V = dy.K * h * h * h / 3.0;
+            }
+        }
+        e_atom[i] = Ei + V;
+        acc_e = Ei;
+        acc_i = V;
+    }
+    double* out = partials + (size_t)blockIdx.x * kNP;
+    double s = block_sum(acc_e, sh);
+    if (threadIdx.x == 0) out[0] = s;
+    s = block_sum(acc_i, sh);
+    if (threadIdx.x == 0) out[1] = s;
+}
+
+__global__ void __launch_bounds__(kRedBlock) k_kinetic(const double* __restrict__ v, const unsigned char* __restrict__ fixed,
+                                                       int n, double mass, double* __restrict__ partials) {
+    __shared__ double sh[32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double ke = 0.0;
+    if (i < n) {
+        const double a = v[i], b = v[n + i], c = v[2 * n + i];
+        ke = 0.5 * mass * (a * a + b * b + c * c) / kFtm;
+    }
+    double s = block_sum(ke, sh);
+    if (threadIdx.x == 0) partials[(size_t)blockIdx.x * kNP + 9] = s;
+}
+
+__global__ void k_reduce(const double* __restrict__ partials, int nblk, double* __restrict__ totals, int with_ke) {
+    __shared__ double sh[32];
+    for (int k = 0; k < kNP; ++k) {
+        if (k == 9 && !with_ke) continue;
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nblk; b += blockDim.x) v += partials[(size_t)b * kNP + k];
+        double s = block_sum(v, sh);
+        if (threadIdx.x == 0) totals[k] = s;
+    }
+}
+
+__global__ void k_kick_drift(double* __restrict__ x, double* __restrict__ v, const float* __restrict__ f,
+                             const unsigned char* __restrict__ fixed, int n, double hdta, double dt,
+                             double* __restrict__ tptr) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *tptr += dt;
+    if (i >= n || fixed[i]) return;
+    for (int k = 0; k < 3; ++k) {
+        double vk = v[(size_t)k * n + i] + hdta * (double)f[(size_t)k * n + i];
+        v[(size_t)k * n + i] = vk;
+        x[(size_t)k * n + i] += dt * vk;
+    }
+}
+
+__global__ void k_kick(double* __restrict__ v, const float* __restrict__ f, const unsigned char* __restrict__ fixed,
+                       int n, double hdta) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || fixed[i]) return;
+    for (int k = 0; k < 3; ++k) v[(size_t)k * n + i] += hdta * (double)f[(size_t)k * n + i];
+}
+
+}  // namespace
+
+int launch_pos_in(Ctx& c, cudaStream_t s, const double* pos) {
+    k_pos_in<<<(c.n + 255) / 256, 256, 0, s>>>(pos, c.n, c.x);
+    return 1;
+}
+
+int launch_blend(Ctx& c, cudaStream_t s, float* out_aos) {
+    k_blend<<<c.nred, kRedBlock, 0, s>>>(c.x, c.n, c.grid, c.dyn, c.d_time, c.w, c.f, c.acc, c.e_ace, c.e_eam,
+                                         c.ace_c1_0, c.vir_eam, c.vir_ace, c.e_atom,
+                                         c.partials, out_aos, c.flags);
+    return 1;
+}
+
+int launch_eam_energy64(Ctx& c, cudaStream_t s);
+
+int launch_energy64(Ctx& c, cudaStream_t s) {
+    int k = launch_eam_energy64(c, s);
+    k_energy_blend<<<c.nred, kRedBlock, 0, s>>>(c.x, c.n, c.grid, c.dyn, c.d_time, c.w, c.e_ace, c.e_eam, c.ace_c1_0,
+                                                c.e_atom, c.partials);
+    return k + 1;
+}
+
+int launch_reduce(Ctx& c, cudaStream_t s, int with_kinetic) {
+    int k = 0;
+    if (with_kinetic) {
+        k_kinetic<<<c.nred, kRedBlock, 0, s>>>(c.v, c.fixed, c.n, c.mass, c.partials);
+        ++k;
+    }
+    k_reduce<<<1, 1024, 0, s>>>(c.partials, c.nred, c.totals, with_kinetic);
+    return k + 1;
+}
+
+int launch_kick_drift(Ctx& c, cudaStream_t s, double dt, int) {
+    k_kick_drift<<<(c.n + 255) / 256, 256, 0, s>>>(c.x, c.v, c.f, c.fixed, c.n, 0.5 * dt * kFtm / c.mass, dt, c.d_time);
+    return 1;
+}
+
+int launch_kick(Ctx& c, cudaStream_t s, double dt) {
+    k_kick<<<(c.n + 255) / 256, 256, 0, s>>>(c.v, c.f, c.fixed, c.n, 0.5 * dt * kFtm / c.mass);
+    return 1;
+}
+
+}  // namespace ap

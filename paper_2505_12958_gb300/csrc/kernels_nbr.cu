@@ -1,0 +1,249 @@
+// kernels_nbr.cu -- cell binning, neighbour list, per-step preparation.
+//
+// The neighbour list is a full list (each pair appears from both sides) within
+// r_list = max(EAM cutoff, ACE cutoff) + skin, stored column-major nbr[k * n + i]
+// so that thread-per-atom kernels read it coalesced.  An entry packs the neighbour
+// index j with the code of the cell offset o (per edge -S..S) it was found in; the
+// pair vector is then x_rel_j + D[code] - x_rel_i in FP32, where x_rel is the position
+// relative to the atom's own cell origin.  This keeps every FP32 operand below the
+// cell size (a few Angstrom), so forming r_ij costs no FP64 work per pair.
+// The list is rebuilt only when some atom moved more than skin/2 since the last build;
+// each rebuild kernel reads that device flag and returns at once when it is clear, so
+// no host synchronisation is needed per step.  Cells keep their atoms in index order
+// (insertion sort after the atomic scatter), which makes the list, and therefore every
+// FP32 summation order, deterministic.
+#include "ap_internal.h"
+
+namespace ap {
+
+namespace {
+
+__device__ __forceinline__ void cell_coords(const GridDev& g, int c, int* cc) {
+    cc[2] = c % g.nc[2];
+    int r = c / g.nc[2];
+    cc[1] = r % g.nc[1];
+    cc[0] = r / g.nc[1];
+}
+
+__global__ void k_check(const double* __restrict__ x, const double* __restrict__ xb, int n, double lim2,
+                        int* flags) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) flags[kFlagNAce] = 0;
+    if (i >= n) return;
+    double dx = x[i] - xb[i], dy = x[n + i] - xb[n + i], dz = x[2 * n + i] - xb[2 * n + i];
+    if (dx * dx + dy * dy + dz * dz > lim2) flags[kFlagRebuild] = 1;
+}
+
+__global__ void k_wrap_bin(double* __restrict__ x, double* __restrict__ xb, int n, const GridDev g,
+                           int* __restrict__ cell, int* __restrict__ cell_count, int* __restrict__ flags) {
+    if (flags[kFlagRebuild] == 0) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) flags[kFlagRebuilds] += 1;
+    if (i >= n) return;
+    double r[3] = {x[i], x[n + i], x[2 * n + i]};
+    double d[3] = {r[0] - g.origin[0], r[1] - g.origin[1], r[2] - g.origin[2]};
+    double s[3];
+    for (int k = 0; k < 3; ++k) s[k] = d[0] * g.hinv[k] + d[1] * g.hinv[3 + k] + d[2] * g.hinv[6 + k];
+    int c[3];
+    for (int k = 0; k < 3; ++k) {
+        if (g.periodic[k]) {
+            double m = floor(s[k]);
+            if (m != 0.0) {
+                for (int q = 0; q < 3; ++q) r[q] -= m * g.h[3 * k + q];
+                s[k] -= m;
+            }
+        }
+        int ck = (int)floor(s[k] * g.nc[k]);
+        c[k] = ck < 0 ? 0 : (ck >= g.nc[k] ? g.nc[k] - 1 : ck);
+    }
+    for (int q = 0; q < 3; ++q) { x[q * n + i] = r[q]; xb[q * n + i] = r[q]; }
+    int ci = (c[0] * g.nc[1] + c[1]) * g.nc[2] + c[2];
+    cell[i] = ci;
+    atomicAdd(&cell_count[ci], 1);
+}
+
+// exclusive scan of cell_count into cell_start (one block); the counters are cleared so
+// that the scatter can reuse them as fill pointers
+__global__ void k_scan(int* __restrict__ cell_count, int* __restrict__ cell_start, int ncell,
+                       const int* __restrict__ flags) {
+    if (flags[kFlagRebuild] == 0) return;
+    __shared__ int part[1024];
+    int tid = threadIdx.x, nt = blockDim.x;
+    int per = (ncell + nt - 1) / nt;
+    int b = tid * per, e = min(b + per, ncell);
+    int s = 0;
+    for (int c = b; c < e; ++c) s += cell_count[c];
+    part[tid] = s;
+    __syncthreads();
+    for (int off = 1; off < nt; off <<= 1) {
+        int v = tid >= off ? part[tid - off] : 0;
+        __syncthreads();
+        part[tid] += v;
+        __syncthreads();
+    }
+    int run = part[tid] - s;
+    for (int c = b; c < e; ++c) {
+        cell_start[c] = run;
+        run += cell_count[c];
+        cell_count[c] = 0;
+    }
+    if (tid == nt - 1) cell_start[ncell] = part[nt - 1];
+}
+
+__global__ void k_scatter(const int* __restrict__ cell, int n, const int* __restrict__ cell_start,
+                          int* __restrict__ fill, int* __restrict__ cell_atoms, const int* __restrict__ flags) {
+    if (flags[kFlagRebuild] == 0) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = cell[i];
+    int slot = atomicAdd(&fill[c], 1);
+    cell_atoms[cell_start[c] + slot] = i;
+}
+
+// order each cell's atoms by index and clear the per-cell counters for the next build
+__global__ void k_sort_cells(int* __restrict__ cell_atoms, const int* __restrict__ cell_start, int* __restrict__ fill,
+                             int ncell, const int* __restrict__ flags) {
+    if (flags[kFlagRebuild] == 0) return;
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    int b = cell_start[c], e = cell_start[c + 1];
+    for (int p = b + 1; p < e; ++p) {
+        int v = cell_atoms[p];
+        int q = p - 1;
+        while (q >= b && cell_atoms[q] > v) { cell_atoms[q + 1] = cell_atoms[q]; --q; }
+        cell_atoms[q + 1] = v;
+    }
+    fill[c] = 0;
+}
+
+// per step: FP32 cell-relative positions, ACE weights, compaction of w > 0
+__global__ void k_prepare(const double* __restrict__ x, int n, const GridDev g, const DynDev dy,
+                          const double* __restrict__ tptr, const int* __restrict__ cell,
+                          const double* __restrict__ w_fixed, float4* __restrict__ pos4, float* __restrict__ wout,
+                          int* __restrict__ ace_list, int* __restrict__ flags) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double w = 0.0;
+    if (i < n) {
+        double r[3] = {x[i], x[n + i], x[2 * n + i]};
+        int cc[3];
+        cell_coords(g, cell[i], cc);
+        double o[3];
+        for (int q = 0; q < 3; ++q)
+            o[q] = g.origin[q] + cc[0] * g.cellvec[q] + cc[1] * g.cellvec[3 + q] + cc[2] * g.cellvec[6 + q];
+        if (dy.reg_kind == AP_REGION_CONST) {
+            w = dy.w_const;
+        } else if (dy.reg_kind == AP_REGION_EXPLICIT) {
+            w = w_fixed[i];
+        } else if (dy.reg_kind == AP_REGION_SPHERE) {
+            double t = *tptr;
+            double d[3];
+            for (int q = 0; q < 3; ++q) d[q] = r[q] - (dy.reg_c0[q] - (dy.follow ? dy.ind_vel[q] * t : 0.0));
+            double s[3];
+            for (int k = 0; k < 3; ++k) s[k] = d[0] * g.hinv[k] + d[1] * g.hinv[3 + k] + d[2] * g.hinv[6 + k];
+            for (int k = 0; k < 3; ++k)
+                if (g.periodic[k]) {
+                    double m = floor(s[k] + 0.5);
+                    for (int q = 0; q < 3; ++q) d[q] -= m * g.h[3 * k + q];
+                }
+            double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            if (dist < dy.r_in) w = 1.0;
+            else if (dist >= dy.r_in + dy.r_sw) w = 0.0;
+            else w = 0.5 * (1.0 + cos(3.14159265358979323846 * (dist - dy.r_in) / dy.r_sw));
+        }
+        pos4[i] = make_float4((float)(r[0] - o[0]), (float)(r[1] - o[1]), (float)(r[2] - o[2]), (float)(1.0 - w));
+        wout[i] = (float)w;
+    }
+    // warp-aggregated compaction of the atoms that need ACE
+    bool need = (i < n) && (w > 0.0);
+    unsigned mask = __ballot_sync(0xffffffffu, need);
+    if (mask) {
+        int lane = threadIdx.x & 31;
+        int leader = __ffs(mask) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&flags[kFlagNAce], __popc(mask));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (need) ace_list[base + __popc(mask & ((1u << lane) - 1u))] = i;
+    }
+}
+
+__global__ void k_build(const float4* __restrict__ pos4, const int* __restrict__ cell, int n, const GridDev g,
+                        const float4* __restrict__ Dtab, const int* __restrict__ cell_start,
+                        const int* __restrict__ cell_atoms, int* __restrict__ nbr, int* __restrict__ nnbr, int cap,
+                        int* __restrict__ flags, int count_only) {
+    if (!count_only && flags[kFlagRebuild] == 0) return;
+    __shared__ float4 D[125];
+    for (int k = threadIdx.x; k < g.ncode; k += blockDim.x) D[k] = Dtab[k];
+    __syncthreads();
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 p = pos4[i];
+    int cc[3];
+    cell_coords(g, cell[i], cc);
+    int cnt = 0;
+    const int w1 = 2 * g.S[1] + 1, w2 = 2 * g.S[2] + 1;
+    for (int code = 0; code < g.ncode; ++code) {
+        int o[3] = {code / (w1 * w2) - g.S[0], (code / w2) % w1 - g.S[1], code % w2 - g.S[2]};
+        int nc[3];
+        bool ok = true;
+        for (int k = 0; k < 3; ++k) {
+            int v = cc[k] + o[k];
+            if (g.periodic[k]) {
+                v %= g.nc[k];
+                if (v < 0) v += g.nc[k];
+            } else if (v < 0 || v >= g.nc[k]) {
+                ok = false;
+            }
+            nc[k] = v;
+        }
+        if (!ok) continue;
+        bool self_cell = (o[0] == 0 && o[1] == 0 && o[2] == 0);
+        int cn = (nc[0] * g.nc[1] + nc[1]) * g.nc[2] + nc[2];
+        float4 d = D[code];
+        for (int q = cell_start[cn], e = cell_start[cn + 1]; q < e; ++q) {
+            int j = cell_atoms[q];
+            if (self_cell && j == i) continue;
+            float4 pj = pos4[j];
+            float dx = pj.x + d.x - p.x, dy = pj.y + d.y - p.y, dz = pj.z + d.z - p.z;
+            if (dx * dx + dy * dy + dz * dz < g.rlist2) {
+                if (!count_only && cnt < cap) nbr[(size_t)cnt * n + i] = j | (code << kNbrShift);
+                ++cnt;
+            }
+        }
+    }
+    if (!count_only) {
+        nnbr[i] = cnt < cap ? cnt : cap;
+        if (cnt > cap) atomicOr(&flags[kFlagErr], kErrCapacity);
+    }
+    atomicMax(&flags[kFlagMaxNbr], cnt);
+}
+
+}  // namespace
+
+int launch_check(Ctx& c, cudaStream_t s) {
+    double lim = 0.5 * c.skin;
+    k_check<<<(c.n + 255) / 256, 256, 0, s>>>(c.x, c.xb, c.n, lim * lim, c.flags);
+    return 1;
+}
+
+int launch_rebuild(Ctx& c, cudaStream_t s) {
+    int nb = (c.n + 255) / 256;
+    k_wrap_bin<<<nb, 256, 0, s>>>(c.x, c.xb, c.n, c.grid, c.cell, c.cell_count, c.flags);
+    k_scan<<<1, 1024, 0, s>>>(c.cell_count, c.cell_start, c.grid.ncell, c.flags);
+    k_scatter<<<nb, 256, 0, s>>>(c.cell, c.n, c.cell_start, c.cell_count, c.cell_atoms, c.flags);
+    k_sort_cells<<<(c.grid.ncell + 255) / 256, 256, 0, s>>>(c.cell_atoms, c.cell_start, c.cell_count, c.grid.ncell, c.flags);
+    return 4;
+}
+
+int launch_prepare(Ctx& c, cudaStream_t s) {
+    k_prepare<<<(c.n + 255) / 256, 256, 0, s>>>(c.x, c.n, c.grid, c.dyn, c.d_time, c.cell, c.w_fixed, c.pos4, c.w,
+                                               c.ace_list, c.flags);
+    return 1;
+}
+
+int launch_build(Ctx& c, cudaStream_t s, int count_only) {
+    k_build<<<(c.n + 127) / 128, 128, 0, s>>>(c.pos4, c.cell, c.n, c.grid, c.D, c.cell_start, c.cell_atoms, c.nbr,
+                                             c.nnbr, c.cap, c.flags, count_only);
+    return 1;
+}
+
+}  // namespace ap

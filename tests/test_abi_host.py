@@ -1,0 +1,84 @@
+"""CPU checks of the CUDA library's boundary and host logic (no GPU compute).
+
+The library must load, export every function include/ap.h declares, and its host-side
+table generators must agree with the oracle's independent routes: the Racah-formula
+Gaunt coefficients with the oracle's quadrature, the FP64 re-expanded EAM polynomials
+with the oracle's direct evaluation of the Appendix B forms.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import synth
+
+
+@pytest.fixture(scope="module")
+def apl():
+    import paper_2505_12958_gb300 as ap
+    ap.build()
+    return ap
+
+
+def test_library_exports_every_declared_symbol(apl):
+    from paper_2505_12958_gb300 import _capi
+    names = _capi.header_symbols()
+    assert len(names) >= 20
+    L = C.CDLL(_capi.LIBPATH)
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    assert _capi.lib().ap_version() == 1
+
+
+def test_gaunt_racah_matches_oracle_quadrature(apl, orc):
+    worst = 0.0
+    for l1 in range(5):
+        for l2 in range(5):
+            for l3 in range(5):
+                for m1 in range(-l1, l1 + 1):
+                    for m2 in range(-l2, l2 + 1):
+                        for m3 in range(-l3, l3 + 1):
+                            a = apl.gaunt_real(l1, m1, l2, m2, l3, m3)
+                            b = orc.gaunt(l1, m1, l2, m2, l3, m3)
+                            worst = max(worst, abs(a - b))
+    assert worst < 1e-13
+
+
+@pytest.mark.parametrize("species", ["W", "Cu"])
+def test_eam_tables_match_oracle_forms(apl, orc, species):
+    eam = synth.eam_potential(species)
+    r = np.concatenate([np.linspace(0.5, 6.0, 1500), [2.74451, 2.74456, 2.7445, 2.7446, 2.46396652011306, 1.10002200044,
+                                                    2.10004200084, 4.9, 5.45078]])
+    ref = orc.eam_funcs(eam, r)
+    for k, rr in enumerate(r):
+        f, df = apl.eam_table_eval(eam, 0, rr)
+        scale = max(1.0, abs(ref[k, 0]))
+        assert abs(f - ref[k, 0]) < 1e-10 * scale and abs(df - ref[k, 1]) < 1e-9 * max(1.0, abs(ref[k, 1])), (rr, f, ref[k])
+        f, df = apl.eam_table_eval(eam, 1, rr)
+        assert abs(f - ref[k, 2]) < 1e-12 and abs(df - ref[k, 3]) < 1e-11, (rr, f, ref[k])
+
+
+def test_init_rejects_bad_arguments_without_a_gpu(apl):
+    # ap_init validates before touching the device: a missing position array is AP_ERR_ARG
+    from paper_2505_12958_gb300 import _capi
+    c = synth.configs.w_bulk(3)
+    p, keep = apl.potential_struct(c["eam"], c["ace"], c["mass"])
+    b = _capi.Box()
+    h = C.c_void_p()
+    st = _capi.lib().ap_init(C.byref(p), C.byref(b), None, None, 10, None, None, None, None, C.byref(h))
+    assert st == _capi.AP_ERR_ARG
+    p.ace_precision = 7
+    x = np.zeros((10, 3))
+    st = _capi.lib().ap_init(C.byref(p), C.byref(b), None, None, 10, x.ctypes.data_as(_capi.PD), None, None,
+                             None, C.byref(h))
+    assert st == _capi.AP_ERR_ARG
+    assert len(_capi.lib().ap_last_error(None)) > 0
+
+
+def test_footprint_estimate_scales_with_atoms(apl):
+    from paper_2505_12958_gb300 import _capi
+    c = synth.configs.w_bulk(3)
+    p, keep = apl.potential_struct(c["eam"], c["ace"], c["mass"])
+    a = _capi.lib().ap_footprint_bytes(C.byref(p), 1000, 0.1)
+    b = _capi.lib().ap_footprint_bytes(C.byref(p), 2000, 0.1)
+    assert 0 < a < b and 300_000 < (b - a) < 2_000_000

@@ -1,0 +1,224 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (FP32 forces, spec bar): max per-atom |dF| <= 1e-4 eV/A and
+|dE_total| / N <= 1e-6 eV.  Per-atom energies carry FP32 rounding of O(1e-6) relative
+and are checked at 2e-5 eV.  ACE-only cases are also checked relative to the force
+scale (max |dF| <= 1e-5 max |F| + 1e-6), so that the bar is not met trivially.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+FTOL, ETOL, EATOM = 1e-4, 1e-6, 2e-5
+
+
+@pytest.fixture(scope="module")
+def apl():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("the gpu tests need a CUDA device")
+    import paper_2505_12958_gb300 as ap
+    ap.build()
+    torch.cuda.init()
+    return ap
+
+
+def ctx_of(ap, c, region="cfg", indenter="cfg", skin=1.0, x=None, fixed="cfg"):
+    reg = c["region"] if region == "cfg" else region
+    ind = c["indenter"] if indenter == "cfg" else indenter
+    fx = c["fixed"] if fixed == "cfg" else fixed
+    return ap.APContext(c["eam"], c["ace"], c["box"], c["x"] if x is None else x, c["v"], fx, reg, ind,
+                        c["ind_vel"], c["mass"], skin)
+
+
+def compare(ap, orc, c, region="cfg", indenter="cfg", rel_ace=False, skin=1.0):
+    reg = c["region"] if region == "cfg" else region
+    ind = c["indenter"] if indenter == "cfg" else indenter
+    ref = orc.evaluate(c["x"], c["box"], c["eam"], c["ace"], reg, ind)
+    assert ref["status"] == 0
+    with ctx_of(ap, c, region, indenter, skin) as ctx:
+        ctx.compute_forces()
+        rep = ctx.energy()
+        F = ctx.forces().astype(np.float64)
+        w = ctx.weights()
+        import torch
+        ea = torch.empty(len(c["x"]), dtype=torch.float64, device="cuda")
+        ctx.energy(e_atom=ea)
+        ea = ea.cpu().numpy()
+    n = len(c["x"])
+    dF = np.abs(F - ref["forces"]).max()
+    assert dF <= FTOL, (dF, np.abs(ref["forces"]).max())
+    if rel_ace:
+        assert dF <= 1e-5 * np.abs(ref["forces"]).max() + 1e-6, (dF, np.abs(ref["forces"]).max())
+    assert abs(rep["e_total"] - ref["e_total"]) / n <= ETOL, (rep["e_total"], ref["e_total"])
+    assert np.abs(ea - ref["e_atom"]).max() <= EATOM
+    assert rep["n_ace"] == ref["n_ace"]
+    assert np.abs(w - ref["w"]).max() < 1e-6
+    assert abs(rep["load"] - ref["load"]) <= 1e-4 * max(1.0, abs(ref["load"]))
+    # per-atom virials are sums of ~50 FP32 pair terms of up to ~10 eV that largely cancel; in
+    # near-identical environments their rounding is coherent, ~1e-7 of each term, so the bound
+    # is 1e-5 eV per atom (plus 2e-5 relative)
+    vtol = 2e-5 * np.abs(ref["virial"]).max() + 1e-5 * n
+    assert np.abs(rep["virial"] - ref["virial"]).max() <= vtol, (rep["virial"], ref["virial"])
+    return dF, ref
+
+
+def test_cu_bulk_ap_sphere(apl, orc):
+    c = synth.configs.cu_bulk()
+    compare(apl, orc, c)
+
+
+def test_cu_bulk_pure_eam_and_pure_ace(apl, orc):
+    c = synth.configs.cu_bulk(ncell=6)
+    compare(apl, orc, c, region=None)
+    compare(apl, orc, c, region={"kind": "const", "w": 1.0}, rel_ace=True)
+
+
+def test_w_bulk_ap_ragged(apl, orc):
+    c = synth.configs.w_bulk(ncell=5, r_in=3.0, r_sw=3.0)      # 250 atoms
+    compare(apl, orc, c)
+    compare(apl, orc, c, region={"kind": "const", "w": 1.0}, rel_ace=True)
+
+
+def test_w_slab_with_indenter_and_fixed_layers(apl, orc):
+    c = synth.configs.w_slab(ncell=12, nz=8, r_in=8.0, r_sw=4.0, R=10.0, penetration=1.5)
+    dF, ref = compare(apl, orc, c)
+    assert ref["load"] > 0 and ref["n_ace"] > 50
+
+
+def test_small_triclinic_cells_with_many_images(apl, orc):
+    for seed in (1, 2):
+        c = synth.configs.strained_w_cell(2, seed=seed, vacancy=0.0)     # 16 atoms, box ~ 6.3 A < r_list
+        compare(apl, orc, c, region=None)
+        compare(apl, orc, c, region={"kind": "const", "w": 0.6})
+    c = synth.configs.strained_w_cell(4, seed=3)                            # vacancies, ragged count
+    compare(apl, orc, c, region={"kind": "const", "w": 0.35})
+
+
+def test_perfect_lattices_with_commensurate_cell_grids(apl, orc):
+    # every equivalent atom repeats the same FP32 rounding here; the energies come from the
+    # FP64 energy pass, so the 1e-6 eV/atom bar holds without thermal noise
+    for c in (synth.configs.w_bulk(ncell=6, sigma=0.0, r_in=4.0), synth.configs.cu_bulk(ncell=6, sigma=0.0, r_in=5.0)):
+        compare(apl, orc, c, region=None)
+        compare(apl, orc, c)
+
+
+def test_explicit_weights(apl, orc):
+    c = synth.configs.cu_bulk(ncell=4)
+    w = np.random.default_rng(0).uniform(0, 1, len(c["x"]))
+    w[::3] = 0.0
+    w[1::7] = 1.0
+    compare(apl, orc, c, region={"kind": "explicit", "w": w})
+
+
+def test_isolated_atom_and_pair(apl, orc):
+    box = {"h": np.diag([40.0] * 3).ravel(), "origin": (0, 0, 0), "periodic": (0, 0, 0)}
+    c = synth.configs.w_bulk(3)
+    c["box"] = box
+    c["x"] = np.array([[20.0, 20.0, 20.0]])
+    c["v"] = np.zeros((1, 3)); c["fixed"] = np.zeros(1, np.uint8)
+    compare(apl, orc, c, region={"kind": "const", "w": 0.5})
+    c["x"] = np.array([[20.0, 20.0, 20.0], [22.5, 21.0, 19.2]])
+    c["v"] = np.zeros((2, 3)); c["fixed"] = np.zeros(2, np.uint8)
+    compare(apl, orc, c, region={"kind": "const", "w": 0.5})
+
+
+def test_device_and_host_entry_points_agree(apl, orc):
+    import torch
+    c = synth.configs.w_bulk(ncell=4, r_in=2.0, r_sw=3.0)
+    with ctx_of(apl, c) as ctx:
+        pos = torch.tensor(c["x"], dtype=torch.float64, device="cuda")
+        out = torch.empty((len(c["x"]), 3), dtype=torch.float32, device="cuda")
+        ctx.compute_forces(pos, out)
+        torch.cuda.synchronize()
+        f_dev = out.cpu().numpy()
+        f_host, e_host = ctx.compute_forces_host(c["x"])
+        e_rep = ctx.energy()["e_total"]
+    assert np.array_equal(f_dev, f_host)
+    assert e_host == e_rep
+
+
+def test_results_are_bitwise_reproducible(apl):
+    c = synth.configs.cu_bulk(ncell=6)
+    out = []
+    for _ in range(2):
+        with ctx_of(apl, c) as ctx:
+            ctx.compute_forces()
+            out.append((ctx.forces(), ctx.energy()["e_total"]))
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+
+
+def test_domain_error_is_reported(apl):
+    c = synth.configs.w_bulk(ncell=3)
+    c["ace"] = dict(c["ace"]); c["ace"]["c2_0"] = -5.0
+    with ctx_of(apl, c, region={"kind": "const", "w": 1.0}) as ctx:
+        ctx.compute_forces()
+        with pytest.raises(apl.APError) as e:
+            ctx.energy()
+        assert e.value.status == -4
+
+
+def test_md_matches_oracle_velocity_verlet(apl, orc):
+    c = synth.configs.w_slab(ncell=8, nz=6, r_in=6.0, r_sw=3.0, R=8.0, penetration=1.0, temperature=600.0)
+    nsteps = 20
+    xo, vo, ep, ek, st = orc.md(c["x"], c["v"], c["box"], c["eam"], c["ace"], c["region"], c["indenter"],
+                                c["ind_vel"], c["fixed"], c["mass"], 1.0, nsteps)
+    assert st == 0
+    with ctx_of(apl, c) as ctx:
+        ctx.step(nsteps, 1.0)
+        rep = ctx.energy()
+        x, v, t = ctx.get_state()
+    L = np.asarray(c["box"]["h"]).reshape(3, 3)
+    d = x - xo
+    for k in range(2):                         # periodic x, y: compare modulo the box
+        d[:, k] -= np.round(d[:, k] / L[k, k]) * L[k, k]
+    assert np.abs(d).max() < 1e-6
+    assert np.abs(v - vo).max() < 1e-6
+    n = len(x)
+    assert abs(rep["e_pot"] + rep["e_ind"] - ep[-1]) / n < 1e-6
+    assert abs(rep["e_kin"] - ek[-1]) / n < 1e-6
+    assert abs(t - nsteps) < 1e-12
+
+
+def test_nve_energy_conservation_on_gpu(apl):
+    c = synth.configs.w_bulk(ncell=6, r_in=4.0, r_sw=3.0)
+    c["v"] = synth.lattice.maxwell_velocities(len(c["x"]), 300.0, c["mass"], 5)
+    with ctx_of(apl, c) as ctx:
+        e0 = ctx.energy()
+        E0 = e0["e_total"] + e0["e_kin"]
+        worst = 0.0
+        for _ in range(10):
+            ctx.step(50, 1.0)
+            r = ctx.energy()
+            worst = max(worst, abs(r["e_total"] + r["e_kin"] - E0))
+    assert worst / len(c["x"]) < 2e-4
+
+
+@pytest.mark.parametrize("nsample", [96])
+def test_w_indentation_slab_full_size_sampled(apl, orc, nsample):
+    """128,000-atom W slab (the timed workload) at t = 0: sampled atoms against the oracle."""
+    c = synth.configs.w_slab()
+    with ctx_of(apl, c) as ctx:
+        ctx.compute_forces()
+        rep = ctx.energy()
+        F = ctx.forces().astype(np.float64)
+        w = ctx.weights()
+    x = c["x"]
+    reg = c["region"]
+    d = np.linalg.norm(x - np.array(reg["center"]), axis=1)
+    di = np.linalg.norm(x - np.array(c["indenter"]["center"]), axis=1)
+    rng = np.random.default_rng(11)
+    groups = [np.where(d < reg["r_in"])[0], np.where((d >= reg["r_in"]) & (d < reg["r_in"] + reg["r_sw"]))[0],
+              np.where(d >= reg["r_in"] + reg["r_sw"])[0], np.where(di < c["indenter"]["R"])[0],
+              np.where(c["fixed"] > 0)[0]]
+    sample = np.unique(np.concatenate([rng.choice(g, size=min(len(g), nsample // 5), replace=False) for g in groups]))
+    pi, pj, _ = orc.neighbors(x, c["box"], 5.46)
+    centers = np.unique(np.concatenate([sample, pj[np.isin(pi, sample)]]))
+    ref = orc.evaluate(x, c["box"], c["eam"], c["ace"], reg, c["indenter"], centers=centers)
+    assert np.abs(F[sample] - ref["forces"][sample]).max() <= FTOL
+    assert np.abs(w[sample] - ref["w"][sample]).max() < 1e-6
+    assert rep["n_ace"] == 21241
+    assert rep["load"] > 0
