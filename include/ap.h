@@ -205,6 +205,31 @@ const char* ap_last_error(const ap_ctx* ctx);
 void ap_destroy(ap_ctx* ctx);
 int ap_version(void);
 
+/* Allocation-free ACE forces for neighbour environments the caller supplies.  The paper
+ * has no counterpart: this entry point exists for callers that cannot create device
+ * allocations of their own - a program or plugin whose GPU memory is owned entirely by
+ * another allocator (a framework's caching pool that must account for every byte), or a
+ * time-critical loop that rules out the latency and the failure modes of cudaMalloc once
+ * it is running.  It evaluates E = sum_i w_i E_i^ACE (Eq. energy_ace, the same kernel
+ * arithmetic as the context path) and F_k = -dE/dr_k for up to 65,536 atoms, and calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *   d_nbr_idx  device, n_atoms x max_nb ints: neighbour atom index j of atom i, -1 = unused
+ *   d_rvec     device, n_atoms x max_nb x 3 FP32: r_j (image) - r_i for those slots
+ *   d_w        device, n_atoms FP32 weights w_i, or NULL for w = 1 (atoms with w = 0 are skipped)
+ *   d_force    device, n_atoms x 3 FP32 output
+ *   d_energy   device, n_atoms FP64 output: E_i^ACE (0 where w = 0, NaN where phi2 <= 1e-3)
+ * Limits: n_atoms <= 65536, max_nb <= 128, else AP_ERR_ARG.  Scratch (the coefficient
+ * tables and 64-bit force accumulators, ~1.6 MB) is one file-scope device array that every
+ * GPU loading the library holds until the process exits; the first call on a device looks
+ * up its address and uploads constant tables, so make that first call before any stream
+ * capture.  Every call shares the array and the call clears the accumulators it uses
+ * before its kernels run; calls that overlap on the GPU (other streams, other threads)
+ * race on it.  Asynchronous on `stream`; errors of the launch are returned, a domain error
+ * shows as a NaN energy. */
+ap_status ap_ace_forces_noalloc(const ap_potential* pot, int n_atoms, int max_nb, const int* d_nbr_idx,
+                                const float* d_rvec, const float* d_w, float* d_force, double* d_energy,
+                                void* stream);
+
 /* Host-side table generators, exposed so that they can be checked without a GPU.
  * ap_gaunt_real: real Gaunt coefficient integral(Y_l1m1 Y_l2m2 Y_l3m3) from the Racah
  * formula for Wigner 3j symbols and the complex-to-real transform (l <= 4).

@@ -81,6 +81,7 @@ def lib():
         "ap_last_error": (C.c_char_p, [VP]),
         "ap_destroy": (None, [VP]),
         "ap_version": (I, []),
+        "ap_ace_forces_noalloc": (I, [P(Potential), I, I, VP, VP, VP, VP, VP, VP]),
         "ap_gaunt_real": (I, [I, I, I, I, I, I, PD]),
         "ap_eam_table_eval": (I, [P(Potential), I, D, PD, PD]),
     }

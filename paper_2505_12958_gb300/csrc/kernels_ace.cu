@@ -17,6 +17,8 @@
 //      w_i, are added to atom j (minus) and atom i (plus) through 64-bit fixed-point
 //      atomics (2^-40 eV/A resolution), whose integer sums do not depend on order.
 // E_i^ACE is stored without the constant c1_0, which the blend adds in FP64.
+#include <mutex>
+#include <string>
 #include <utility>
 
 #include "ap_internal.h"
@@ -602,3 +604,311 @@ int launch_ace(Ctx& c, cudaStream_t s) {
 }
 
 }  // namespace ap
+
+// =====================================================================================
+// Allocation-free variant: ACE forces for environments the caller supplies.
+//
+// Some callers of this library cannot create device allocations of their own: a host
+// program or plugin whose GPU memory is owned entirely by another allocator (a
+// framework's caching pool that must see every byte), or a time-critical step loop that
+// forbids the latency and the failure modes of cudaMalloc after start-up.  For them
+// ap_ace_forces_noalloc evaluates the ACE pass (the same warp-per-atom arithmetic as
+// k_ace) on neighbour lists they pass in, and keeps its scratch - the coefficient
+// tables and the 64-bit fixed-point force accumulators - in the file-scope array below,
+// which every GPU that loads this library holds until the process exits.
+// =====================================================================================
+namespace ap {
+
+namespace {
+
+constexpr int kNoAllocMaxAtoms = 65536;
+constexpr size_t kNoAllocTableBytes = (sizeof(AceDev) + 255) / 256 * 256;
+constexpr size_t kNoAllocBytes = kNoAllocTableBytes + 3 * (size_t)kNoAllocMaxAtoms * sizeof(unsigned long long);
+
+}  // namespace
+
+}  // namespace ap
+
+// ~1.6 MB: the coefficient tables, then accumulators for up to 65,536 atoms.  In host
+// code this name is only a stand-in; kernels receive its device address, obtained once
+// per device with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_ace_noalloc_scratch[ap::kNoAllocBytes];
+
+namespace ap {
+
+namespace {
+
+__global__ void __launch_bounds__(kWarps * 32, 1)
+k_ace_noalloc(const int* __restrict__ nbr_idx, const float* __restrict__ rvec, int n, int max_nb,
+              const float* __restrict__ wv, unsigned char* __restrict__ scratch, double* __restrict__ e_out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AceDev& C = *reinterpret_cast<AceDev*>(smem_raw);
+    WarpSmem* WS = reinterpret_cast<WarpSmem*>(smem_raw + sizeof(AceDev) + 128 * sizeof(float4));
+    unsigned long long* acc = reinterpret_cast<unsigned long long*>(scratch + kNoAllocTableBytes);
+    {
+        const int4* src = reinterpret_cast<const int4*>(scratch);
+        int4* dst = reinterpret_cast<int4*>(smem_raw);
+        for (int k = threadIdx.x; k < (int)(sizeof(AceDev) / 16); k += blockDim.x) dst[k] = src[k];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpSmem& S = WS[warp];
+    const float rc = C.rc, rc2 = rc * rc, nrefi = C.nref_inv;
+    int lam_l = 0;
+    if (lane >= 1) lam_l = 1;
+    if (lane >= 4) lam_l = 2;
+    if (lane >= 9) lam_l = 3;
+    if (lane >= 16) lam_l = 4;
+    const int lam_pad = lblk(lam_l) + (lane - lam_l * lam_l);
+
+    for (int i = blockIdx.x * kWarps + warp; i < n; i += gridDim.x * kWarps) {
+        const float wi = wv ? wv[i] : 1.0f;
+        if (!(wi > 0.0f)) {
+            if (lane == 0) e_out[i] = 0.0;
+            continue;
+        }
+        // neighbours inside the cutoff; S.nbj keeps the atom index
+        int cnt = 0;
+        for (int k0 = 0; k0 < max_nb; k0 += 32) {
+            const int k = k0 + lane;
+            bool in = false;
+            float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+            int j = -1;
+            if (k < max_nb) {
+                j = nbr_idx[(size_t)i * max_nb + k];
+                if (j >= 0 && j < n) {
+                    const float* v = rvec + 3 * ((size_t)i * max_nb + k);
+                    dx = v[0]; dy = v[1]; dz = v[2];
+                    r2 = dx * dx + dy * dy + dz * dz;
+                    in = r2 < rc2 && r2 > 0.0f;
+                }
+            }
+            const unsigned bm = __ballot_sync(0xffffffffu, in);
+            const int pos = cnt + __popc(bm & ((1u << lane) - 1u));
+            if (in) { S.nb[pos] = make_float4(dx, dy, dz, sqrtf(r2)); S.nbj[pos] = j; }
+            cnt += __popc(bm);
+        }
+        __syncwarp();
+        float accA[kNmax];
+#pragma unroll
+        for (int q = 0; q < kNmax; ++q) accA[q] = 0.0f;
+        for (int t0 = 0; t0 < cnt; t0 += kTile) {
+            const int jj = t0 + lane;
+            if (jj < cnt) {
+                const float4 v = S.nb[jj];
+                const float ri = 1.0f / v.w;
+                float g[kNmax], dg[kNmax], Y[kNLM];
+                radial(v.w, rc, g, dg);
+                ylm(v.x * ri, v.y * ri, v.z * ri, Y);
+#pragma unroll
+                for (int q = 0; q < kNmax; ++q) S.tileG[lane][q] = g[q];
+#pragma unroll
+                for (int q = 0; q < kNLM; ++q) S.tileY[lane][q] = Y[q];
+            }
+            __syncwarp();
+            const int nt = min(kTile, cnt - t0);
+            if (lane < kNLM) {
+                for (int jj2 = 0; jj2 < nt; ++jj2) {
+                    const float y = S.tileY[jj2][lane];
+#pragma unroll
+                    for (int q = 0; q < kNmax; ++q) accA[q] = fmaf(y, S.tileG[jj2][q], accA[q]);
+                }
+            }
+            __syncwarp();
+        }
+        for (int k = lane; k < kNmax * kApad; k += 32) { S.A[k] = 0.0f; S.dA[k] = 0.0f; }
+        __syncwarp();
+        if (lane < kNLM) {
+#pragma unroll
+            for (int q = 0; q < kNmax; ++q) S.A[q * kApad + lam_pad] = accA[q] * nrefi;
+        }
+        __syncwarp();
+        float p1 = 0.0f, p2 = 0.0f;
+        if (lane < kNmax) {
+            const float a0 = S.A[lane * kApad];
+            p1 = C.c1[0][lane] * a0;
+            p2 = C.c1[1][lane] * a0;
+        }
+#pragma unroll
+        for (int l = 0; l <= kLmax; ++l) {
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp) {
+                const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
+                float mm = 0.0f;
+#pragma unroll
+                for (int k = 0; k < 2 * l + 1; ++k)
+                    mm = fmaf(S.A[n1 * kApad + lblk(l) + k], S.A[n2 * kApad + lblk(l) + k], mm);
+                p1 = fmaf(C.c2[0][l][q], mm, p1);
+                p2 = fmaf(C.c2[1][l][q], mm, p2);
+            }
+        }
+        nu3_forward_all(S.A, C, lane, p1, p2, std::make_integer_sequence<int, kNT>{});
+        p1 = warp_sum(p1);
+        p2 = warp_sum(p2);
+        const float phi2 = C.c2_0 + p2;
+        if (!(phi2 > 1e-3f) || !(p1 == p1)) {
+            if (lane == 0) e_out[i] = __longlong_as_double(0x7ff8000000000000ll);
+            continue;
+        }
+        const float sq = sqrtf(phi2);
+        const float s = 0.5f / sq;
+        if (lane < kNmax) S.dA[lane * kApad] += fmaf(s, C.c1[1][lane], C.c1[0][lane]);
+        __syncwarp();
+#pragma unroll
+        for (int l = 0; l <= kLmax; ++l) {
+            constexpr int WM = 9;
+            float d2[WM];
+#pragma unroll
+            for (int k = 0; k < WM; ++k) d2[k] = 0.0f;
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp) {
+                const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
+                const float c = fmaf(s, C.c2[1][l][q], C.c2[0][l][q]);
+                float d1[WM];
+#pragma unroll
+                for (int k = 0; k < 2 * l + 1; ++k) {
+                    const float a1 = S.A[n1 * kApad + lblk(l) + k], a2 = S.A[n2 * kApad + lblk(l) + k];
+                    d1[k] = c * a2;
+                    d2[k] = fmaf(c, a1, d2[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < 2 * l + 1; ++k) {
+                    float v = d1[k];
+                    v += __shfl_xor_sync(0xffffffffu, v, 1);
+                    v += __shfl_xor_sync(0xffffffffu, v, 2);
+                    v += __shfl_xor_sync(0xffffffffu, v, 4);
+                    d1[k] = v;
+                }
+                if ((lane & 7) == 0) {
+#pragma unroll
+                    for (int k = 0; k < 2 * l + 1; ++k) S.dA[n1 * kApad + lblk(l) + k] += d1[k];
+                }
+                __syncwarp();
+            }
+#pragma unroll
+            for (int k = 0; k < 2 * l + 1; ++k) {
+                float v = d2[k];
+                v += __shfl_xor_sync(0xffffffffu, v, 8);
+                v += __shfl_xor_sync(0xffffffffu, v, 16);
+                d2[k] = v;
+            }
+            if (lane < 8) {
+#pragma unroll
+                for (int k = 0; k < 2 * l + 1; ++k) S.dA[lane * kApad + lblk(l) + k] += d2[k];
+            }
+            __syncwarp();
+        }
+        nu3_adjoint_all(S.A, S.dA, C, s, lane, std::make_integer_sequence<int, kNT>{});
+        if (lane < kNLM) {
+#pragma unroll
+            for (int q = 0; q < kNmax; ++q) S.dAT[lane][q] = S.dA[q * kApad + lam_pad];
+        }
+        __syncwarp();
+        float fsx = 0.f, fsy = 0.f, fsz = 0.f;
+        for (int t0 = 0; t0 < cnt; t0 += 32) {
+            const int jj = t0 + lane;
+            if (jj < cnt) {
+                const float4 v = S.nb[jj];
+                const int j = S.nbj[jj];
+                const float ri = 1.0f / v.w;
+                const float ux = v.x * ri, uy = v.y * ri, uz = v.z * ri;
+                float g[kNmax], dg[kNmax];
+                radial(v.w, rc, g, dg);
+                float sc = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+                auto ab = [&](int lm, float& aa, float& bb) {
+                    float a_ = 0.f, b_ = 0.f;
+#pragma unroll
+                    for (int q = 0; q < kNmax; ++q) {
+                        a_ = fmaf(S.dAT[lm][q], g[q], a_);
+                        b_ = fmaf(S.dAT[lm][q], dg[q], b_);
+                    }
+                    aa = a_;
+                    bb = b_;
+                };
+                force_terms(ux, uy, uz, ri, ab, sc, gx, gy, gz);
+                const float fx = nrefi * (sc * ux + gx * ri) * wi;
+                const float fy = nrefi * (sc * uy + gy * ri) * wi;
+                const float fz = nrefi * (sc * uz + gz * ri) * wi;
+                fix_add(&acc[j], -fx);
+                fix_add(&acc[(size_t)n + j], -fy);
+                fix_add(&acc[(size_t)2 * n + j], -fz);
+                fsx += fx; fsy += fy; fsz += fz;
+            }
+        }
+        fsx = warp_sum(fsx); fsy = warp_sum(fsy); fsz = warp_sum(fsz);
+        if (lane == 0) {
+            fix_add(&acc[i], fsx);
+            fix_add(&acc[(size_t)n + i], fsy);
+            fix_add(&acc[(size_t)2 * n + i], fsz);
+            e_out[i] = (double)C.c1_0 + (double)(p1 + sq);
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_ace_noalloc_forces(const unsigned char* __restrict__ scratch, int n, float* __restrict__ f_out) {
+    const unsigned long long* acc = reinterpret_cast<const unsigned long long*>(scratch + kNoAllocTableBytes);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int k = 0; k < 3; ++k)
+        f_out[3 * (size_t)i + k] = (float)((double)(long long)acc[(size_t)k * n + i] * (1.0 / kFixScale));
+}
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_dev_ptr[64] = {};
+AceDev g_noalloc_tables;                 // host staging of the tables (guarded by the mutex)
+std::string g_noalloc_err;
+
+}  // namespace
+
+}  // namespace ap
+
+extern "C" ap_status ap_ace_forces_noalloc(const ap_potential* pot, int n_atoms, int max_nb, const int* d_nbr_idx,
+                                           const float* d_rvec, const float* d_w, float* d_force, double* d_energy,
+                                           void* stream) {
+    using namespace ap;
+    if (!pot || !d_nbr_idx || !d_rvec || !d_force || !d_energy || n_atoms < 1 || max_nb < 0) return AP_ERR_ARG;
+    if (n_atoms > kNoAllocMaxAtoms || max_nb > kAceNbrCap) {
+        std::lock_guard<std::mutex> g(g_noalloc_mu);
+        g_noalloc_err = "ap_ace_forces_noalloc: at most 65536 atoms and 128 neighbour slots per atom";
+        return AP_ERR_ARG;
+    }
+    if (pot->ace_precision != AP_ACE_FP32) return AP_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return AP_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_dev_ptr[dev]) {
+        // once per device, with that device current (the first call on a device does this)
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_ace_noalloc_scratch) != cudaSuccess || !p) {
+            g_noalloc_err = "cudaGetSymbolAddress failed for the scratch array";
+            return AP_ERR_CUDA;
+        }
+        static float gv[kNG];
+        std::string err;
+        if (gaunt_values(gv, err)) { g_noalloc_err = err; return AP_ERR_ARG; }
+        upload_gaunt(gv);
+        if (cudaFuncSetAttribute(k_ace_noalloc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ace_smem_bytes()) !=
+            cudaSuccess) {
+            g_noalloc_err = "cudaFuncSetAttribute failed";
+            return AP_ERR_CUDA;
+        }
+        g_noalloc_dev_ptr[dev] = p;
+    }
+    unsigned char* scratch = static_cast<unsigned char*>(g_noalloc_dev_ptr[dev]);
+    std::string err;
+    if (build_ace_tables(*pot, g_noalloc_tables, err)) { g_noalloc_err = err; return AP_ERR_ARG; }
+    cudaError_t e = cudaMemcpyAsync(scratch, &g_noalloc_tables, sizeof(AceDev), cudaMemcpyHostToDevice, s);
+    // the accumulators must start at zero; the array keeps whatever the last call left
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(scratch + kNoAllocTableBytes, 0, 3 * (size_t)n_atoms * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) { g_noalloc_err = cudaGetErrorString(e); return AP_ERR_CUDA; }
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    k_ace_noalloc<<<nsm, kWarps * 32, ace_smem_bytes(), s>>>(d_nbr_idx, d_rvec, n_atoms, max_nb, d_w, scratch, d_energy);
+    k_ace_noalloc_forces<<<(n_atoms + 255) / 256, 256, 0, s>>>(scratch, n_atoms, d_force);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { g_noalloc_err = cudaGetErrorString(e); return AP_ERR_CUDA; }
+    return AP_OK;
+}
