@@ -191,20 +191,22 @@ def run_reference(args):
 
 
 def ace_kernel_roofline(prof, n_steps, c, pk, peak_src, ctx_atoms_in_rc):
-    from paper_2505_12958_gb300.workload import ace_flops_per_atom
+    """Roofline of the dominant kernel, k_ace_contract (products, densities and dE/dA of the
+    compacted atoms); its CUDA-event time comes from the library's per-stage events."""
+    from paper_2505_12958_gb300.workload import ace_contract_flops_per_atom
     ms, nl = prof["ace"]
     avg_s = ms / max(1, nl) / 1000.0
-    flops = sum(ace_flops_per_atom(k) for k in ctx_atoms_in_rc)
+    flops = ace_contract_flops_per_atom() * len(ctx_atoms_in_rc)
     achieved = flops / avg_s / 1e12
     peak = 152 * 128 * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
     traffic = None
-    tf = os.path.join(ROOT, "profiles", "k_ace_traffic.json")
+    tf = os.path.join(ROOT, "profiles", "k_ace_contract_traffic.json")
     if os.path.exists(tf):
         from paper_2505_12958_gb300.buildlib import source_hash
         rec = json.load(open(tf))
         if rec.get("source_hash") == source_hash():
             traffic = rec["dram_bytes_per_launch"]
-    return {"kernel": "k_ace", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+    return {"kernel": "k_ace_contract", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock, %s peaks file)"
                            % (float(pk.get("sm_max_mhz", 2070.0)), peak_src),

@@ -190,7 +190,8 @@ ap_status ap_set_weights(ap_ctx* ctx, const double* w);
  * the accumulated time of stage k over launches[k] launches, stages AP_STAGE_*. */
 enum { AP_STAGE_NEIGHBOR = 0, AP_STAGE_PREPARE = 1, AP_STAGE_EAM_DENSITY = 2,
        AP_STAGE_EAM_FORCE = 3, AP_STAGE_ACE = 4, AP_STAGE_BLEND = 5, AP_STAGE_INTEGRATE = 6,
-       AP_NSTAGE = 7 };
+       AP_STAGE_ACE_BASIS = 7, AP_STAGE_ACE_FORCE = 8, AP_NSTAGE = 9 };
+/* (AP_STAGE_ACE is the contraction kernel: products, densities and dE/dA.) */
 ap_status ap_profile(ap_ctx* ctx, int enable);
 ap_status ap_profile_read(ap_ctx* ctx, double* ms, long long* launches);
 

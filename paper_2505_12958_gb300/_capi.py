@@ -16,7 +16,7 @@ STATUS = {0: "AP_OK", -1: "AP_ERR_ARG", -2: "AP_ERR_OOM", -3: "AP_ERR_CUDA", -4:
           -5: "AP_ERR_CAPACITY", -6: "AP_ERR_TIMEOUT", -7: "AP_ERR_STATE"}
 PRECISION = {"fp32": 0, "tf32x3": 1, "bf16": 2, "fp16": 3, "fp64": 4}
 REGION = {None: 0, "none": 0, "sphere": 1, "explicit": 2, "const": 3}
-STAGES = ["neighbor", "prepare", "eam_density", "eam_force", "ace", "blend", "integrate"]
+STAGES = ["neighbor", "prepare", "eam_density", "eam_force", "ace", "blend", "integrate", "ace_basis", "ace_force"]
 
 
 class Potential(C.Structure):

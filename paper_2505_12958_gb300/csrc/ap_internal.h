@@ -26,6 +26,7 @@ struct PolyTab {
     float start[kMaxInt + 1];
     float mid[kMaxInt];
     float c[kMaxInt][6];
+    float c0lo[kMaxInt];      // c[k][0] - (double)c[k][0], for the compensated energy pass
     unsigned char bin[kNBin]; // first interval that overlaps bin b
 };
 
@@ -36,20 +37,6 @@ struct alignas(16) EamDev {
     float rc;                 // max(phi.rcut, rho.rcut)
     float pad;
     double F_a1, F_a2, F_dxi;
-};
-
-// The same piecewise polynomials in FP64, for the on-demand FP64 energy pass.
-struct PolyTab64 {
-    int nint, zbl;
-    double rcut;
-    double start[kMaxInt + 1];
-    double mid[kMaxInt];
-    double c[kMaxInt][6];
-};
-
-struct EamDev64 {
-    PolyTab64 phi, rho;
-    double zbl_k, zbl_a, F_a1, F_a2, F_dxi;
 };
 
 // ACE coefficient tensors, zero-padded to full n-ranges (a basis function sits at its
@@ -107,23 +94,25 @@ struct Ctx {
 
     EamDev eam_h{};
     EamDev* eam_d = nullptr;
-    EamDev64 eam64_h{};
-    EamDev64* eam64_d = nullptr;
-    bool energy_fresh = false;                           // FP64 energy pass done for the last forces
+    bool energy_fresh = false;                           // energy pass done for the last forces
     AceDev* ace_h = nullptr;
     AceDev* ace_d = nullptr;
     GridDev grid{};
-    float4* D = nullptr;
+    float4* D = nullptr;                                 // cell-offset vectors, FP32
+    float4* Dlo = nullptr;                               // their FP32 residuals (o . cellvec - D)
     DynDev dyn{};
 
     double *x = nullptr, *v = nullptr, *xb = nullptr;   // SoA [3][n]
     float* f = nullptr;                                  // SoA [3][n]
     float4* pos4 = nullptr;                              // x_rel (3) and u = 1 - w
+    float4* pos_lo = nullptr;                            // FP32 residual of x_rel (energy pass)
     float* uxi = nullptr;                                // u_i xi'(rho_i)
     float* w = nullptr;
     double* e_emb = nullptr;                             // xi(rho_i) + Delta xi
     double* e_eam = nullptr;                             // E_i^EAM (FP64)
     float* e_ace = nullptr;                              // E_i^ACE - c1_0
+    float* ace_A = nullptr;                              // [n_ace][25][8] atomic base of the compacted atoms
+    float* ace_dA = nullptr;                             // [n_ace][25][8] dE/dA
     double ace_c1_0 = 0.0;
     float* vir_eam = nullptr;                            // [6][n]
     float* vir_ace = nullptr;                            // [6][n]
@@ -166,9 +155,11 @@ int launch_prepare(Ctx& c, cudaStream_t s);          // x_rel, weights, compacti
 int launch_build(Ctx& c, cudaStream_t s, int count_only);
 int launch_eam_density(Ctx& c, cudaStream_t s);
 int launch_eam_force(Ctx& c, cudaStream_t s);
-int launch_ace(Ctx& c, cudaStream_t s);
+int launch_ace_basis(Ctx& c, cudaStream_t s);        // A_nlm of the compacted atoms
+int launch_ace(Ctx& c, cudaStream_t s);              // products, densities, dE/dA
+int launch_ace_force(Ctx& c, cudaStream_t s);        // pair forces and scatter
 int launch_blend(Ctx& c, cudaStream_t s, float* out_aos);
-int launch_energy64(Ctx& c, cudaStream_t s);         // FP64 EAM energies + energy blend
+int launch_energy(Ctx& c, cudaStream_t s);           // compensated EAM energies + energy blend
 int launch_reduce(Ctx& c, cudaStream_t s, int with_kinetic);
 int launch_kick_drift(Ctx& c, cudaStream_t s, double dt, int first_half);
 int launch_kick(Ctx& c, cudaStream_t s, double dt);
@@ -176,7 +167,7 @@ int launch_pos_in(Ctx& c, cudaStream_t s, const double* pos_aos);
 int launch_check(Ctx& c, cudaStream_t s);
 
 // host-side tables (tables.cpp)
-int build_eam_tables(const ap_potential& p, EamDev& out, EamDev64& out64, std::string& err);
+int build_eam_tables(const ap_potential& p, EamDev& out, std::string& err);
 int build_ace_tables(const ap_potential& p, AceDev& out, std::string& err);
 double gaunt_real_racah(int l1, int m1, int l2, int m2, int l3, int m3);
 int gaunt_values(float* out, std::string& err);      // kNG entries in pattern order

@@ -80,7 +80,7 @@ void cross(const double* a, const double* b, double* c) {
     c[0] = a[1] * b[2] - a[2] * b[1]; c[1] = a[2] * b[0] - a[0] * b[2]; c[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-ap_status setup_grid(ap::Ctx& c, const ap_box& box, std::vector<float4>& D) {
+ap_status setup_grid(ap::Ctx& c, const ap_box& box, std::vector<float4>& D, std::vector<float4>& Dlo) {
     ap::GridDev& g = c.grid;
     std::memcpy(g.h, box.h, sizeof(g.h));
     std::memcpy(g.origin, box.origin, sizeof(g.origin));
@@ -114,12 +114,14 @@ ap_status setup_grid(ap::Ctx& c, const ap_box& box, std::vector<float4>& D) {
     g.ncode = (2 * g.S[0] + 1) * (2 * g.S[1] + 1) * (2 * g.S[2] + 1);
     g.rlist2 = (float)(c.rc_list * c.rc_list);
     D.resize(g.ncode);
+    Dlo.resize(g.ncode);
     const int w1 = 2 * g.S[1] + 1, w2 = 2 * g.S[2] + 1;
     for (int code = 0; code < g.ncode; ++code) {
         int o[3] = {code / (w1 * w2) - g.S[0], (code / w2) % w1 - g.S[1], code % w2 - g.S[2]};
         double v[3];
         for (int q = 0; q < 3; ++q) v[q] = o[0] * g.cellvec[q] + o[1] * g.cellvec[3 + q] + o[2] * g.cellvec[6 + q];
         D[code] = make_float4((float)v[0], (float)v[1], (float)v[2], 0.f);
+        Dlo[code] = make_float4((float)(v[0] - (float)v[0]), (float)(v[1] - (float)v[1]), (float)(v[2] - (float)v[2]), 0.f);
     }
     return AP_OK;
 }
@@ -133,7 +135,7 @@ ap_status dalloc(ap::Ctx& c, T** p, size_t count) {
 }
 
 void free_all(ap::Ctx& c) {
-    void* ps[] = {c.eam_d, c.eam64_d, c.ace_d, c.D, c.x, c.v, c.xb, c.f, c.pos4, c.uxi, c.w, c.e_emb, c.e_eam, c.e_ace,
+    void* ps[] = {c.eam_d, c.ace_d, c.D, c.Dlo, c.pos_lo, c.ace_A, c.ace_dA, c.x, c.v, c.xb, c.f, c.pos4, c.uxi, c.w, c.e_emb, c.e_eam, c.e_ace,
                   c.vir_eam, c.vir_ace, c.acc, c.fixed, c.w_fixed, c.cell, c.cell_count, c.cell_start,
                   c.cell_atoms, c.nbr, c.nnbr, c.ace_list, c.flags, c.d_time, c.partials, c.totals, c.e_atom,
                   c.pos_stage, c.f_stage};
@@ -158,17 +160,19 @@ void run_forces(ap_ctx* xc, cudaStream_t s, float* out_aos) {
     stage(xc, AP_STAGE_NEIGHBOR, s, [&] { return ap::launch_build(c, s, 0); });
     stage(xc, AP_STAGE_EAM_DENSITY, s, [&] { return ap::launch_eam_density(c, s); });
     stage(xc, AP_STAGE_EAM_FORCE, s, [&] { return ap::launch_eam_force(c, s); });
+    stage(xc, AP_STAGE_ACE_BASIS, s, [&] { return ap::launch_ace_basis(c, s); });
     stage(xc, AP_STAGE_ACE, s, [&] { return ap::launch_ace(c, s); });
+    stage(xc, AP_STAGE_ACE_FORCE, s, [&] { return ap::launch_ace_force(c, s); });
     stage(xc, AP_STAGE_BLEND, s, [&] { return ap::launch_blend(c, s, out_aos); });
     c.forces_valid = true;
     c.energy_fresh = false;
 }
 
-// FP64 energies of the last force evaluation, once
+// accurate energies of the last force evaluation, once
 void ensure_energy(ap_ctx* xc, cudaStream_t s) {
     ap::Ctx& c = xc->c;
     if (c.energy_fresh) return;
-    c.launches += ap::launch_energy64(c, s);
+    c.launches += ap::launch_energy(c, s);
     c.energy_fresh = true;
 }
 
@@ -247,7 +251,7 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
     };
     if (cudaGetDevice(&c.dev) != cudaSuccess) { c.err = "no CUDA device"; return fail(AP_ERR_CUDA); }
     std::string err;
-    if (ap::build_eam_tables(*pot, c.eam_h, c.eam64_h, err)) { c.err = err; return fail(AP_ERR_ARG); }
+    if (ap::build_eam_tables(*pot, c.eam_h, err)) { c.err = err; return fail(AP_ERR_ARG); }
     c.ace_h = new (std::nothrow) ap::AceDev();
     if (!c.ace_h) { c.err = "host allocation"; return fail(AP_ERR_OOM); }
     if (ap::build_ace_tables(*pot, *c.ace_h, err)) { c.err = err; return fail(AP_ERR_ARG); }
@@ -262,8 +266,8 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
     c.rc_eam = c.eam_h.rc;
     c.rc_ace = pot->ace_rc;
     c.rc_list = std::max(c.rc_eam, c.rc_ace) + c.skin;
-    std::vector<float4> D;
-    if ((st = setup_grid(c, *box, D)) != AP_OK) return fail(st);
+    std::vector<float4> D, Dlo;
+    if ((st = setup_grid(c, *box, D, Dlo)) != AP_OK) return fail(st);
 
     // region and indenter
     ap::DynDev& dy = c.dyn;
@@ -291,11 +295,13 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
     // device memory
     const size_t N = (size_t)n;
     c.nred = (n + ap::kRedBlock - 1) / ap::kRedBlock;
-    if ((st = dalloc(c, &c.eam_d, 1)) || (st = dalloc(c, &c.eam64_d, 1)) || (st = dalloc(c, &c.ace_d, 1)) || (st = dalloc(c, &c.D, D.size())) ||
+    if ((st = dalloc(c, &c.eam_d, 1)) || (st = dalloc(c, &c.ace_d, 1)) || (st = dalloc(c, &c.D, D.size())) ||
+        (st = dalloc(c, &c.Dlo, Dlo.size())) || (st = dalloc(c, &c.pos_lo, N)) ||
         (st = dalloc(c, &c.x, 3 * N)) || (st = dalloc(c, &c.v, 3 * N)) || (st = dalloc(c, &c.xb, 3 * N)) ||
         (st = dalloc(c, &c.f, 3 * N)) || (st = dalloc(c, &c.pos4, N)) || (st = dalloc(c, &c.uxi, N)) ||
         (st = dalloc(c, &c.w, N)) || (st = dalloc(c, &c.e_emb, N)) || (st = dalloc(c, &c.e_eam, N)) ||
-        (st = dalloc(c, &c.e_ace, N)) || (st = dalloc(c, &c.vir_eam, 6 * N)) || (st = dalloc(c, &c.vir_ace, 6 * N)) ||
+        (st = dalloc(c, &c.e_ace, N)) || (st = dalloc(c, &c.ace_A, (size_t)ap::kNLM * ap::kNmax * N)) ||
+        (st = dalloc(c, &c.ace_dA, (size_t)ap::kNLM * ap::kNmax * N)) || (st = dalloc(c, &c.vir_eam, 6 * N)) || (st = dalloc(c, &c.vir_ace, 6 * N)) ||
         (st = dalloc(c, &c.acc, 3 * N)) || (st = dalloc(c, &c.fixed, N)) || (st = dalloc(c, &c.w_fixed, N)) ||
         (st = dalloc(c, &c.cell, N)) || (st = dalloc(c, &c.cell_count, (size_t)c.grid.ncell)) ||
         (st = dalloc(c, &c.cell_start, (size_t)c.grid.ncell + 1)) || (st = dalloc(c, &c.cell_atoms, N)) ||
@@ -315,9 +321,9 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
         if (e == cudaSuccess) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
     };
     cp(c.eam_d, &c.eam_h, sizeof(ap::EamDev));
-    cp(c.eam64_d, &c.eam64_h, sizeof(ap::EamDev64));
     cp(c.ace_d, c.ace_h, sizeof(ap::AceDev));
     cp(c.D, D.data(), D.size() * sizeof(float4));
+    cp(c.Dlo, Dlo.data(), Dlo.size() * sizeof(float4));
     cp(c.x, soa.data(), 3 * N * sizeof(double));
     cp(c.xb, soa.data(), 3 * N * sizeof(double));
     if (vel) { to_soa(vel, n, soa); cp(c.v, soa.data(), 3 * N * sizeof(double)); }

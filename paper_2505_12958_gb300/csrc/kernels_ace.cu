@@ -172,8 +172,8 @@ struct Tri {
 template <int T, int E>
 __device__ __forceinline__ void ent_p(float* P, const float* A1, const float* A2) {
     using R = Tri<T>;
-    P[R::template m3<E>()] = fmaf(c_gaunt[R::OFF + E] * A1[R::template m1<E>()], A2[R::template m2<E>()],
-                                  P[R::template m3<E>()]);
+    constexpr int i1 = R::template m1<E>(), i2 = R::template m2<E>(), i3 = R::template m3<E>();
+    P[i3] = fmaf(c_gaunt[R::OFF + E] * A1[i1], A2[i2], P[i3]);
 }
 template <int T, int... E>
 __device__ __forceinline__ void all_p(float* P, const float* A1, const float* A2, std::integer_sequence<int, E...>) {
@@ -183,9 +183,10 @@ __device__ __forceinline__ void all_p(float* P, const float* A1, const float* A2
 template <int T, int E>
 __device__ __forceinline__ void ent_x(float* d1, float* d2, const float* A1, const float* A2, const float* Q) {
     using R = Tri<T>;
-    const float u = c_gaunt[R::OFF + E] * Q[R::template m3<E>()];
-    d1[R::template m1<E>()] = fmaf(u, A2[R::template m2<E>()], d1[R::template m1<E>()]);
-    d2[R::template m2<E>()] = fmaf(u, A1[R::template m1<E>()], d2[R::template m2<E>()]);
+    constexpr int i1 = R::template m1<E>(), i2 = R::template m2<E>(), i3 = R::template m3<E>();
+    const float u = c_gaunt[R::OFF + E] * Q[i3];
+    d1[i1] = fmaf(u, A2[i2], d1[i1]);
+    d2[i2] = fmaf(u, A1[i1], d2[i2]);
 }
 template <int T, int... E>
 __device__ __forceinline__ void all_x(float* d1, float* d2, const float* A1, const float* A2, const float* Q,
@@ -196,8 +197,8 @@ __device__ __forceinline__ void all_x(float* d1, float* d2, const float* A1, con
 template <int T, int E>
 __device__ __forceinline__ void ent_y(float* d3, const float* A1, const float* Tm) {
     using R = Tri<T>;
-    d3[R::template m3<E>()] = fmaf(c_gaunt[R::OFF + E] * A1[R::template m1<E>()], Tm[R::template m2<E>()],
-                                   d3[R::template m3<E>()]);
+    constexpr int i1 = R::template m1<E>(), i2 = R::template m2<E>(), i3 = R::template m3<E>();
+    d3[i3] = fmaf(c_gaunt[R::OFF + E] * A1[i1], Tm[i2], d3[i3]);
 }
 template <int T, int... E>
 __device__ __forceinline__ void all_y(float* d3, const float* A1, const float* Tm, std::integer_sequence<int, E...>) {
@@ -225,10 +226,28 @@ __device__ __forceinline__ float dot_row(const float* P, const float* row) {
     return r;
 }
 
+// sum_k P[k] * row[k] over a 16-byte aligned shared-memory row, two accumulator chains
+template <int W>
+__device__ __forceinline__ float dot_row2(const float* P, const float* row) {
+    float r0 = 0.0f, r1 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < W; k += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(row + k);
+        r0 = fmaf(P[k], v.x, r0);
+        if (k + 1 < W) r1 = fmaf(P[k + 1], v.y, r1);
+        if (k + 2 < W) r0 = fmaf(P[k + 2], v.z, r0);
+        if (k + 3 < W) r1 = fmaf(P[k + 3], v.w, r1);
+    }
+    return r0 + r1;
+}
+
+// The two (n1, n2) pairs of a lane and the n3 / n2 contractions are runtime loops; only the
+// Gaunt entries are unrolled (their operands are register-indexed), which keeps the code
+// of all 14 l-triples small enough for the instruction cache.
 template <int T>
 __device__ __forceinline__ void nu3_forward(const float* As, const AceDev& C, int lane, float& p1, float& p2) {
     using R = Tri<T>;
-#pragma unroll
+#pragma unroll 1
     for (int pp = 0; pp < 2; ++pp) {
         const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
         float A1[R::W1], A2[R::W2], P[R::W3];
@@ -240,9 +259,9 @@ __device__ __forceinline__ void nu3_forward(const float* As, const AceDev& C, in
         const float* c1 = C.c3[0][T][q];
         const float* c2 = C.c3[1][T][q];
         float s1 = 0.0f, s2 = 0.0f;
-#pragma unroll
+#pragma unroll 2
         for (int n3 = 0; n3 < kNmax; ++n3) {
-            const float r = dot_row<R::W3>(P, As + n3 * kApad + R::B3);
+            const float r = dot_row2<R::W3>(P, As + n3 * kApad + R::B3);
             s1 = fmaf(c1[n3], r, s1);
             s2 = fmaf(c2[n3], r, s2);
         }
@@ -258,20 +277,23 @@ __device__ __forceinline__ void nu3_adjoint(const float* As, float* dAs, const A
     float d2[R::W2];
 #pragma unroll
     for (int k = 0; k < R::W2; ++k) d2[k] = 0.0f;
-#pragma unroll
+#pragma unroll 1
     for (int pp = 0; pp < 2; ++pp) {
-        const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
-        float A1[R::W1], A2[R::W2], Q[R::W3], d1[R::W1], ce[kNmax];
+        const int q = lane + 32 * pp, n1 = q >> 3;
+        const int n2 = q & 7;
+        float A1[R::W1], A2[R::W2], Q[R::W3], d1[R::W1];
         load_row<R::W1>(A1, As + n1 * kApad + R::B1);
         load_row<R::W2>(A2, As + n2 * kApad + R::B2);
 #pragma unroll
-        for (int k = 0; k < kNmax; ++k) ce[k] = fmaf(s, C.c3[1][T][q][k], C.c3[0][T][q][k]);
+        for (int m = 0; m < R::W3; ++m) Q[m] = 0.0f;
+        const float* c1 = C.c3[0][T][q];
+        const float* c2 = C.c3[1][T][q];
+#pragma unroll 2
+        for (int n3 = 0; n3 < kNmax; ++n3) {
+            const float ce = fmaf(s, c2[n3], c1[n3]);
+            const float* a3 = As + n3 * kApad + R::B3;
 #pragma unroll
-        for (int m = 0; m < R::W3; ++m) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int n3 = 0; n3 < kNmax; ++n3) acc = fmaf(ce[n3], As[n3 * kApad + R::B3 + m], acc);
-            Q[m] = acc;
+            for (int m = 0; m < R::W3; ++m) Q[m] = fmaf(ce, a3[m], Q[m]);
         }
 #pragma unroll
         for (int k = 0; k < R::W1; ++k) d1[k] = 0.0f;
@@ -306,19 +328,19 @@ __device__ __forceinline__ void nu3_adjoint(const float* As, float* dAs, const A
     float d3[R::W3];
 #pragma unroll
     for (int k = 0; k < R::W3; ++k) d3[k] = 0.0f;
-#pragma unroll
+#pragma unroll 1
     for (int pp = 0; pp < 2; ++pp) {
         const int q = lane + 32 * pp, n1 = q >> 3, n3 = q & 7;
-        float A1[R::W1], Tm[R::W2], ce[kNmax];
+        float A1[R::W1], Tm[R::W2];
         load_row<R::W1>(A1, As + n1 * kApad + R::B1);
 #pragma unroll
-        for (int n2 = 0; n2 < kNmax; ++n2) ce[n2] = fmaf(s, C.c3[1][T][n1 * 8 + n2][n3], C.c3[0][T][n1 * 8 + n2][n3]);
+        for (int m = 0; m < R::W2; ++m) Tm[m] = 0.0f;
+#pragma unroll 2
+        for (int n2 = 0; n2 < kNmax; ++n2) {
+            const float ce = fmaf(s, C.c3[1][T][n1 * 8 + n2][n3], C.c3[0][T][n1 * 8 + n2][n3]);
+            const float* a2 = As + n2 * kApad + R::B2;
 #pragma unroll
-        for (int m = 0; m < R::W2; ++m) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int n2 = 0; n2 < kNmax; ++n2) acc = fmaf(ce[n2], As[n2 * kApad + R::B2 + m], acc);
-            Tm[m] = acc;
+            for (int m = 0; m < R::W2; ++m) Tm[m] = fmaf(ce, a2[m], Tm[m]);
         }
         all_y<T>(d3, A1, Tm, std::make_integer_sequence<int, R::N>{});
     }
@@ -358,66 +380,64 @@ __device__ __forceinline__ void fix_add(unsigned long long* p, float v) {
     atomicAdd(p, (unsigned long long)q);
 }
 
-__global__ void __launch_bounds__(kWarps * 32, 1)
-k_ace(const float4* __restrict__ pos4, const int* __restrict__ nbr, const int* __restrict__ nnbr, int n,
-      const float4* __restrict__ Dtab, int ncode, const AceDev* __restrict__ tab, const int* __restrict__ ace_list,
-      const float* __restrict__ wv, int* __restrict__ flags, float* __restrict__ e_ace, float* __restrict__ vir,
-      unsigned long long* __restrict__ acc) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    AceDev& C = *reinterpret_cast<AceDev*>(smem_raw);
-    float4* Ds = reinterpret_cast<float4*>(smem_raw + sizeof(AceDev));
-    WarpSmem* WS = reinterpret_cast<WarpSmem*>(smem_raw + sizeof(AceDev) + 128 * sizeof(float4));
-    {
-        const int4* src = reinterpret_cast<const int4*>(tab);
-        int4* dst = reinterpret_cast<int4*>(smem_raw);
-        for (int k = threadIdx.x; k < (int)(sizeof(AceDev) / 16); k += blockDim.x) dst[k] = src[k];
-        for (int k = threadIdx.x; k < ncode; k += blockDim.x) Ds[k] = Dtab[k];
+// neighbours of atom i inside the ACE cutoff, from the full list, into S (warp-uniform count;
+// returns -1 when there are more than kAceNbrCap)
+__device__ __forceinline__ int gather_ace_neighbors(const float4* __restrict__ pos4, const int* __restrict__ nbr,
+                                                    int n, int i, int m, const float4* Ds, float rc2, float4* nb,
+                                                    int* nbj, int lane) {
+    const float4 p = pos4[i];
+    int cnt = 0;
+    for (int k0 = 0; k0 < m; k0 += 32) {
+        const int k = k0 + lane;
+        bool in = false;
+        float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+        int j = 0;
+        if (k < m) {
+            const int e = nbr[(size_t)k * n + i];
+            j = e & kNbrMask;
+            const float4 d = Ds[(unsigned)e >> kNbrShift];
+            const float4 q = pos4[j];
+            dx = q.x + d.x - p.x; dy = q.y + d.y - p.y; dz = q.z + d.z - p.z;
+            r2 = dx * dx + dy * dy + dz * dz;
+            in = r2 < rc2 && r2 > 0.0f;
+        }
+        const unsigned bm = __ballot_sync(0xffffffffu, in);
+        const int pos = cnt + __popc(bm & ((1u << lane) - 1u));
+        if (in && pos < kAceNbrCap) { nb[pos] = make_float4(dx, dy, dz, sqrtf(r2)); nbj[pos] = j; }
+        cnt += __popc(bm);
     }
+    __syncwarp();
+    return cnt > kAceNbrCap ? -1 : cnt;
+}
+
+struct BasisSmem {
+    float4 nb[kAceNbrCap];
+    int nbj[kAceNbrCap];
+    float tileY[kTile][kNLM];
+    float tileG[kTile][kNmax];
+};
+
+// stage a1 of the ACE pass: A_nlm = (1/nref) sum_j g_n(r_ij) Y_lm(rhat_ij), stored [atom][lm][n]
+__global__ void __launch_bounds__(256) k_ace_basis(const float4* __restrict__ pos4, const int* __restrict__ nbr,
+                                                   const int* __restrict__ nnbr, int n, const float4* __restrict__ Dtab,
+                                                   int ncode, const AceDev* __restrict__ tab,
+                                                   const int* __restrict__ ace_list, int* __restrict__ flags,
+                                                   float* __restrict__ Aout) {
+    __shared__ float4 Ds[125];
+    __shared__ BasisSmem WS[8];
+    for (int k = threadIdx.x; k < ncode; k += blockDim.x) Ds[k] = Dtab[k];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpSmem& S = WS[warp];
-    const float rc = C.rc, rc2 = rc * rc, nrefi = C.nref_inv;
+    BasisSmem& S = WS[warp];
+    const float rc = tab->rc, rc2 = rc * rc, nrefi = tab->nref_inv;
     const int n_ace = flags[kFlagNAce];
-    // lane -> (l, m) for the 25 lanes that own an A column
-    int lam_l = 0;
-    if (lane >= 1) lam_l = 1;
-    if (lane >= 4) lam_l = 2;
-    if (lane >= 9) lam_l = 3;
-    if (lane >= 16) lam_l = 4;
-    const int lam_pad = lblk(lam_l) + (lane - lam_l * lam_l);
-
-    for (int a = blockIdx.x * kWarps + warp; a < n_ace; a += gridDim.x * kWarps) {
+    for (int a = blockIdx.x * 8 + warp; a < n_ace; a += gridDim.x * 8) {
         const int i = ace_list[a];
-        const float4 p = pos4[i];
-        const float wi = wv[i];
-        const int m = nnbr[i];
-        // 1. neighbours within the ACE cutoff
-        int cnt = 0;
-        for (int k0 = 0; k0 < m; k0 += 32) {
-            const int k = k0 + lane;
-            bool in = false;
-            float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
-            int j = 0;
-            if (k < m) {
-                const int e = nbr[(size_t)k * n + i];
-                j = e & kNbrMask;
-                const float4 d = Ds[(unsigned)e >> kNbrShift];
-                const float4 q = pos4[j];
-                dx = q.x + d.x - p.x; dy = q.y + d.y - p.y; dz = q.z + d.z - p.z;
-                r2 = dx * dx + dy * dy + dz * dz;
-                in = r2 < rc2 && r2 > 0.0f;
-            }
-            const unsigned bm = __ballot_sync(0xffffffffu, in);
-            const int pos = cnt + __popc(bm & ((1u << lane) - 1u));
-            if (in && pos < kAceNbrCap) { S.nb[pos] = make_float4(dx, dy, dz, sqrtf(r2)); S.nbj[pos] = j; }
-            cnt += __popc(bm);
-        }
-        if (cnt > kAceNbrCap) {
+        const int cnt = gather_ace_neighbors(pos4, nbr, n, i, nnbr[i], Ds, rc2, S.nb, S.nbj, lane);
+        if (cnt < 0) {
             if (lane == 0) { atomicOr(&flags[kFlagErr], kErrAceCapacity); flags[kFlagBad] = i; }
             continue;
         }
-        __syncwarp();
-        // 2. atomic base
         float accA[kNmax];
 #pragma unroll
         for (int q = 0; q < kNmax; ++q) accA[q] = 0.0f;
@@ -449,25 +469,65 @@ k_ace(const float4* __restrict__ pos4, const int* __restrict__ nbr, const int* _
             }
             __syncwarp();
         }
+        if (lane < kNLM) {
+            float4* o = reinterpret_cast<float4*>(Aout + ((size_t)a * kNLM + lane) * kNmax);
+            o[0] = make_float4(accA[0] * nrefi, accA[1] * nrefi, accA[2] * nrefi, accA[3] * nrefi);
+            o[1] = make_float4(accA[4] * nrefi, accA[5] * nrefi, accA[6] * nrefi, accA[7] * nrefi);
+        }
+    }
+}
+
+struct ContractSmem {
+    float A[kNmax * kApad];
+    float dA[kNmax * kApad];
+};
+
+constexpr int kContractWarps = 8;
+
+// stage a5/a6 core: phi1, phi2, E = phi1 + sqrt(phi2) and dE/dA from A, one warp per atom
+__global__ void __launch_bounds__(kContractWarps * 32, 2)
+k_ace_contract(const AceDev* __restrict__ tab, const int* __restrict__ ace_list, int* __restrict__ flags,
+               const float* __restrict__ Ain, float* __restrict__ dAout, float* __restrict__ e_ace) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AceDev& C = *reinterpret_cast<AceDev*>(smem_raw);
+    ContractSmem* WS = reinterpret_cast<ContractSmem*>(smem_raw + sizeof(AceDev));
+    {
+        const int4* src = reinterpret_cast<const int4*>(tab);
+        int4* dst = reinterpret_cast<int4*>(smem_raw);
+        for (int k = threadIdx.x; k < (int)(sizeof(AceDev) / 16); k += blockDim.x) dst[k] = src[k];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    ContractSmem& S = WS[warp];
+    const int n_ace = flags[kFlagNAce];
+    int lam_l = 0;
+    if (lane >= 1) lam_l = 1;
+    if (lane >= 4) lam_l = 2;
+    if (lane >= 9) lam_l = 3;
+    if (lane >= 16) lam_l = 4;
+    const int lam_pad = lblk(lam_l) + (lane - lam_l * lam_l);
+    for (int a = blockIdx.x * kContractWarps + warp; a < n_ace; a += gridDim.x * kContractWarps) {
         for (int k = lane; k < kNmax * kApad; k += 32) { S.A[k] = 0.0f; S.dA[k] = 0.0f; }
         __syncwarp();
         if (lane < kNLM) {
+            const float4* src = reinterpret_cast<const float4*>(Ain + ((size_t)a * kNLM + lane) * kNmax);
+            const float4 g0 = src[0], g1 = src[1];
+            const float v[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
 #pragma unroll
-            for (int q = 0; q < kNmax; ++q) S.A[q * kApad + lam_pad] = accA[q] * nrefi;
+            for (int q = 0; q < kNmax; ++q) S.A[q * kApad + lam_pad] = v[q];
         }
         __syncwarp();
-        // 3. the two densities
         float p1 = 0.0f, p2 = 0.0f;
         if (lane < kNmax) {
             const float a0 = S.A[lane * kApad];
             p1 = C.c1[0][lane] * a0;
             p2 = C.c1[1][lane] * a0;
         }
+#pragma unroll 1
+        for (int pp = 0; pp < 2; ++pp) {
+            const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
 #pragma unroll
-        for (int l = 0; l <= kLmax; ++l) {
-#pragma unroll
-            for (int pp = 0; pp < 2; ++pp) {
-                const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
+            for (int l = 0; l <= kLmax; ++l) {
                 float mm = 0.0f;
 #pragma unroll
                 for (int k = 0; k < 2 * l + 1; ++k)
@@ -479,15 +539,20 @@ k_ace(const float4* __restrict__ pos4, const int* __restrict__ nbr, const int* _
         nu3_forward_all(S.A, C, lane, p1, p2, std::make_integer_sequence<int, kNT>{});
         p1 = warp_sum(p1);
         p2 = warp_sum(p2);
+        const int i = ace_list[a];
         const float phi2 = C.c2_0 + p2;
         if (!(phi2 > 1e-3f) || !(p1 == p1)) {
             if (lane == 0) { atomicOr(&flags[kFlagErr], kErrDomain); flags[kFlagBad] = i; e_ace[i] = __int_as_float(0x7fc00000); }
+            // zero adjoint: the force stage then adds nothing for this atom
+            if (lane < kNLM) {
+                float4* o = reinterpret_cast<float4*>(dAout + ((size_t)a * kNLM + lane) * kNmax);
+                o[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+                o[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
             continue;
         }
         const float sq = sqrtf(phi2);
-        const float E = p1 + sq;
         const float s = 0.5f / sq;
-        // 4. adjoint dE/dA
         if (lane < kNmax) S.dA[lane * kApad] += fmaf(s, C.c1[1][lane], C.c1[0][lane]);
         __syncwarp();
 #pragma unroll
@@ -496,7 +561,7 @@ k_ace(const float4* __restrict__ pos4, const int* __restrict__ nbr, const int* _
             float d2[WM];
 #pragma unroll
             for (int k = 0; k < WM; ++k) d2[k] = 0.0f;
-#pragma unroll
+#pragma unroll 1
             for (int pp = 0; pp < 2; ++pp) {
                 const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
                 const float c = fmaf(s, C.c2[1][l][q], C.c2[0][l][q]);
@@ -536,11 +601,47 @@ k_ace(const float4* __restrict__ pos4, const int* __restrict__ nbr, const int* _
         }
         nu3_adjoint_all(S.A, S.dA, C, s, lane, std::make_integer_sequence<int, kNT>{});
         if (lane < kNLM) {
+            float v[kNmax];
 #pragma unroll
-            for (int q = 0; q < kNmax; ++q) S.dAT[lane][q] = S.dA[q * kApad + lam_pad];
+            for (int q = 0; q < kNmax; ++q) v[q] = S.dA[q * kApad + lam_pad];
+            float4* o = reinterpret_cast<float4*>(dAout + ((size_t)a * kNLM + lane) * kNmax);
+            o[0] = make_float4(v[0], v[1], v[2], v[3]);
+            o[1] = make_float4(v[4], v[5], v[6], v[7]);
         }
+        if (lane == 0) e_ace[i] = p1 + sq;
         __syncwarp();
-        // 5. pair forces
+    }
+}
+
+struct ForceSmem {
+    float dAT[kNLM][kNmax];
+    float4 nb[kAceNbrCap];
+    int nbj[kAceNbrCap];
+};
+
+// stage a6: f_ij = (1/nref) sum dE/dA_nlm grad(g_n Y_lm), scattered with weight w_i
+__global__ void __launch_bounds__(256) k_ace_force(const float4* __restrict__ pos4, const int* __restrict__ nbr,
+                                                   const int* __restrict__ nnbr, int n, const float4* __restrict__ Dtab,
+                                                   int ncode, const AceDev* __restrict__ tab,
+                                                   const int* __restrict__ ace_list, const float* __restrict__ wv,
+                                                   int* __restrict__ flags, const float* __restrict__ dAin,
+                                                   float* __restrict__ vir, unsigned long long* __restrict__ acc) {
+    __shared__ float4 Ds[125];
+    __shared__ ForceSmem WS[8];
+    for (int k = threadIdx.x; k < ncode; k += blockDim.x) Ds[k] = Dtab[k];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    ForceSmem& S = WS[warp];
+    const float rc = tab->rc, rc2 = rc * rc, nrefi = tab->nref_inv;
+    const int n_ace = flags[kFlagNAce];
+    for (int a = blockIdx.x * 8 + warp; a < n_ace; a += gridDim.x * 8) {
+        const int i = ace_list[a];
+        const float wi = wv[i];
+        const int cnt = gather_ace_neighbors(pos4, nbr, n, i, nnbr[i], Ds, rc2, S.nb, S.nbj, lane);
+        if (cnt < 0) continue;
+        for (int k = lane; k < kNLM * 2; k += 32)
+            reinterpret_cast<float4*>(&S.dAT[0][0])[k] = reinterpret_cast<const float4*>(dAin + (size_t)a * kNLM * kNmax)[k];
+        __syncwarp();
         float fsx = 0.f, fsy = 0.f, fsz = 0.f;
         float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f, v4 = 0.f, v5 = 0.f;
         for (int t0 = 0; t0 < cnt; t0 += 32) {
@@ -578,7 +679,6 @@ k_ace(const float4* __restrict__ pos4, const int* __restrict__ nbr, const int* _
             fix_add(&acc[i], fsx);
             fix_add(&acc[(size_t)n + i], fsy);
             fix_add(&acc[(size_t)2 * n + i], fsz);
-            e_ace[i] = E;
             vir[i] = v0; vir[n + i] = v1; vir[2 * n + i] = v2; vir[3 * n + i] = v3; vir[4 * n + i] = v4; vir[5 * n + i] = v5;
         }
         __syncwarp();
@@ -589,17 +689,34 @@ k_ace(const float4* __restrict__ pos4, const int* __restrict__ nbr, const int* _
 
 size_t ace_smem_bytes() { return sizeof(AceDev) + 128 * sizeof(float4) + kWarps * sizeof(WarpSmem); }
 
+size_t ace_contract_smem_bytes() { return sizeof(AceDev) + kContractWarps * sizeof(ContractSmem); }
+
+int launch_ace_basis(Ctx& c, cudaStream_t s) {
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c.dev);
+    k_ace_basis<<<nsm * 2, 256, 0, s>>>(c.pos4, c.nbr, c.nnbr, c.n, c.D, c.grid.ncode, c.ace_d, c.ace_list, c.flags,
+                                        c.ace_A);
+    return 1;
+}
+
 int launch_ace(Ctx& c, cudaStream_t s) {
     static int configured = -1;
-    const size_t smem = ace_smem_bytes();
     if (configured != c.dev) {
-        cudaFuncSetAttribute(k_ace, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_ace_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ace_contract_smem_bytes());
         configured = c.dev;
     }
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c.dev);
-    k_ace<<<nsm, kWarps * 32, smem, s>>>(c.pos4, c.nbr, c.nnbr, c.n, c.D, c.grid.ncode, c.ace_d, c.ace_list, c.w,
-                                         c.flags, c.e_ace, c.vir_ace, c.acc);
+    k_ace_contract<<<nsm * 2, kContractWarps * 32, ace_contract_smem_bytes(), s>>>(c.ace_d, c.ace_list, c.flags,
+                                                                                 c.ace_A, c.ace_dA, c.e_ace);
+    return 1;
+}
+
+int launch_ace_force(Ctx& c, cudaStream_t s) {
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c.dev);
+    k_ace_force<<<nsm * 2, 256, 0, s>>>(c.pos4, c.nbr, c.nnbr, c.n, c.D, c.grid.ncode, c.ace_d, c.ace_list, c.w,
+                                        c.flags, c.ace_dA, c.vir_ace, c.acc);
     return 1;
 }
 

@@ -133,68 +133,115 @@ __global__ void __launch_bounds__(256) k_eam_force(const float4* __restrict__ po
 }
 
 // ---------------------------------------------------------------------------------
-// On-demand FP64 EAM energies.  FP32 pair distances and polynomials are accurate to a few
-// ulp, but in a perfect lattice every equivalent atom repeats the same rounding, which
-// adds up coherently to ~1e-6 eV/atom; energies are therefore recomputed from the FP64
-// positions (exact periodic image shifts) when a caller asks for them.
+// On-demand EAM energies with compensated FP32 arithmetic.  Plain FP32 pair distances
+// and polynomials are accurate to a few ulp, but in a perfect lattice every equivalent
+// atom repeats the same rounding and the per-atom energies are off coherently by
+// ~1e-6 eV.  Here every pair vector is an error-free double-float sum (TwoSum) of the
+// cell-relative positions, their FP32 residuals and the offset table with its residuals;
+// r = sqrt(r2) carries a first-order correction, and each polynomial is evaluated as
+// p(t_hi) + p'(t_hi) t_lo with t_hi = r_f - mid exact in FP32.  Sums are compensated too.
+// Only FP32 instructions run per pair (GB300's FP64 rate is 1/64 of its FP32 rate).
 // ---------------------------------------------------------------------------------
-__device__ double poly64(const PolyTab64& t, double r, double zk, double za) {
-    if (r >= t.rcut) return 0.0;
-    int k = 0;
-    while (k + 1 < t.nint && r >= t.start[k + 1]) ++k;
-    if (t.zbl && k == 0) {
-        double xx = r / za;
-        double ph = 0.1818 * exp(-3.2 * xx) + 0.5099 * exp(-0.9423 * xx) + 0.2802 * exp(-0.4029 * xx) +
-                    0.02817 * exp(-0.2016 * xx);
-        return zk * ph / r;
-    }
-    double x = r - t.mid[k];
-    const double* c = t.c[k];
-    return ((((c[5] * x + c[4]) * x + c[3]) * x + c[2]) * x + c[1]) * x + c[0];
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+__device__ __forceinline__ void acc_add(float& hi, float& lo, float v) {
+    float s, e;
+    two_sum(hi, v, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
 
-__global__ void __launch_bounds__(128) k_eam_energy64(const double* __restrict__ x, int n, const GridDev g,
-                                                      const int* __restrict__ cell, const int* __restrict__ nbr,
-                                                      const int* __restrict__ nnbr, const float4* __restrict__ pos4,
-                                                      const EamDev64* __restrict__ T, double* __restrict__ e_eam) {
+// value of the piecewise polynomial at rf + tl, added into the double-float sum (hi, lo):
+// the constant term enters as c0 (hi + lo) through TwoSum, the rest in FP32
+__device__ __forceinline__ void poly_acc_df(const PolyTab& t, float rf, float tl, float zk, float zainv, float& hi,
+                                            float& lo) {
+    int b = (int)(rf * t.bin_inv);
+    b = b < kNBin ? b : kNBin - 1;
+    int k = t.bin[b];
+    while (k + 1 < t.nint && rf >= t.start[k + 1]) ++k;
+    if (t.zbl && k == 0) {
+        const float r = rf + tl, x = r * zainv;
+        acc_add(hi, lo, zk * (0.1818f * expf(-3.2f * x) + 0.5099f * expf(-0.9423f * x) + 0.2802f * expf(-0.4029f * x) +
+                              0.02817f * expf(-0.2016f * x)) / r);
+        return;
+    }
+    const float x = __fsub_rn(rf, t.mid[k]);           // exact: mid is an FP32 number near rf
+    const float* c = t.c[k];
+    const float u = (((c[5] * x + c[4]) * x + c[3]) * x + c[2]) * x + c[1];   // p(x) = c0 + x u
+    const float d = (((5.0f * c[5] * x + 4.0f * c[4]) * x + 3.0f * c[3]) * x + 2.0f * c[2]) * x + c[1];
+    const float xu = __fmul_rn(x, u), xue = fmaf(x, u, -xu);
+    acc_add(hi, lo, c[0]);
+    acc_add(hi, lo, xu);
+    lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(t.c0lo[k], xue), d * tl));
+}
+
+__global__ void __launch_bounds__(256) k_eam_energy(const float4* __restrict__ pos4, const float4* __restrict__ pos_lo,
+                                                    const int* __restrict__ nbr, const int* __restrict__ nnbr, int n,
+                                                    const EamDev* __restrict__ eam, const float4* __restrict__ D,
+                                                    const float4* __restrict__ Dlo, int ncode,
+                                                    double* __restrict__ e_eam) {
+    __shared__ EamDev T;
+    __shared__ float4 Ds[125];
+    __shared__ float4 Dl[125];
+    stage_tables(&T, eam, Ds, D, ncode);
+    for (int k = threadIdx.x; k < ncode; k += blockDim.x) Dl[k] = Dlo[k];
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    if (pos4[i].w <= 0.0f) { e_eam[i] = 0.0; return; }
-    int ci = cell[i];
-    int cc[3] = {ci / (g.nc[1] * g.nc[2]), (ci / g.nc[2]) % g.nc[1], ci % g.nc[2]};
-    const double xi = x[i], yi = x[n + i], zi = x[2 * n + i];
-    const int w1 = 2 * g.S[1] + 1, w2 = 2 * g.S[2] + 1;
-    double rho = 0.0, ph = 0.0;
+    const float4 p = pos4[i], pl = pos_lo[i];
+    if (p.w <= 0.0f) { e_eam[i] = 0.0; return; }
+    const float rc2 = T.rc * T.rc, rcr = T.rho.rcut, rcp = T.phi.rcut;
+    float rh = 0.f, rl = 0.f, ph = 0.f, pl_ = 0.f;
     const int m = nnbr[i];
     for (int k = 0; k < m; ++k) {
         const int e = nbr[(size_t)k * n + i];
         const int j = e & kNbrMask;
-        const int code = (int)((unsigned)e >> kNbrShift);
-        int o[3] = {code / (w1 * w2) - g.S[0], (code / w2) % w1 - g.S[1], code % w2 - g.S[2]};
-        double sh[3] = {0.0, 0.0, 0.0};
-        for (int d = 0; d < 3; ++d) {
-            if (!g.periodic[d]) continue;
-            const int im = floor_div(cc[d] + o[d], g.nc[d]);
-            if (im != 0)
-                for (int q = 0; q < 3; ++q) sh[q] += im * g.h[3 * d + q];
+        const unsigned code = (unsigned)e >> kNbrShift;
+        const float4 dh = Ds[code], dl = Dl[code];
+        const float4 q = pos4[j], ql = pos_lo[j];
+        float d[3], dlo[3];
+        const float qa[3] = {q.x, q.y, q.z}, pa[3] = {p.x, p.y, p.z};
+        const float qla[3] = {ql.x, ql.y, ql.z}, pla[3] = {pl.x, pl.y, pl.z};
+        const float dha[3] = {dh.x, dh.y, dh.z}, dla[3] = {dl.x, dl.y, dl.z};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float s1, e1, s2, e2;
+            two_sum(qa[c], -pa[c], s1, e1);
+            two_sum(s1, dha[c], s2, e2);
+            d[c] = s2;
+            dlo[c] = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(__fsub_rn(qla[c], pla[c]), dla[c]));
         }
-        const double dx = x[j] + sh[0] - xi, dy = x[n + j] + sh[1] - yi, dz = x[2 * n + j] + sh[2] - zi;
-        const double r = sqrt(dx * dx + dy * dy + dz * dz);
-        if (r < T->rho.rcut) rho += poly64(T->rho, r, 0.0, 1.0);
-        if (r < T->phi.rcut) ph += poly64(T->phi, r, T->zbl_k, T->zbl_a);
+        // r2 = sum (d + dlo)^2 as a double-float
+        float r2h = 0.f, r2l = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float sq = __fmul_rn(d[c], d[c]);
+            const float sqe = fmaf(d[c], d[c], -sq);
+            acc_add(r2h, r2l, sq);
+            r2l = __fadd_rn(r2l, fmaf(2.0f * d[c], dlo[c], sqe));
+        }
+        if (r2h >= rc2) continue;
+        const float rf = sqrtf(r2h);
+        const float pp = __fmul_rn(rf, rf), pe = fmaf(rf, rf, -pp);
+        const float tl = __fdiv_rn(__fadd_rn(__fsub_rn(__fsub_rn(r2h, pp), pe), r2l), 2.0f * rf);
+        if (rf < rcr) poly_acc_df(T.rho, rf, tl, 0.f, 0.f, rh, rl);
+        if (rf < rcp) poly_acc_df(T.phi, rf, tl, T.zbl_k, T.zbl_ainv, ph, pl_);
     }
-    double F = T->F_dxi;
-    if (rho > 0.0) F += T->F_a1 * sqrt(rho) + T->F_a2 * rho * rho;
-    e_eam[i] = F + 0.5 * ph;
+    const double rho = (double)rh + (double)rl;
+    double F = T.F_dxi;
+    if (rho > 0.0) F += T.F_a1 * sqrt(rho) + T.F_a2 * rho * rho;
+    e_eam[i] = F + 0.5 * ((double)ph + (double)pl_);
 }
 
 }  // namespace
 
-int launch_eam_energy64(Ctx& c, cudaStream_t s) {
-    k_eam_energy64<<<(c.n + 127) / 128, 128, 0, s>>>(c.x, c.n, c.grid, c.cell, c.nbr, c.nnbr, c.pos4, c.eam64_d,
-                                                     c.e_eam);
+int launch_eam_energy(Ctx& c, cudaStream_t s) {
+    k_eam_energy<<<(c.n + 255) / 256, 256, 0, s>>>(c.pos4, c.pos_lo, c.nbr, c.nnbr, c.n, c.eam_d, c.D, c.Dlo,
+                                                   c.grid.ncode, c.e_eam);
     return 1;
 }
 

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kRedBlock) k_blend(
     s = block_sum(acc_l, sh); if (threadIdx.x == 0) out[8] = s;
 }
 
-// energies only (after the FP64 EAM energy pass): per-atom E_i + V_ind and the two
+// energies only (after the compensated EAM energy pass): per-atom E_i + V_ind and the two
 // energy partial sums; forces, virial and load partials stay those of k_blend
 __global__ void __launch_bounds__(kRedBlock) k_energy_blend(
     const double* __restrict__ x, int n, const GridDev g, const DynDev dy, const double* __restrict__ tptr,
@@ -210,10 +210,10 @@ int launch_blend(Ctx& c, cudaStream_t s, float* out_aos) {
     return 1;
 }
 
-int launch_eam_energy64(Ctx& c, cudaStream_t s);
+int launch_eam_energy(Ctx& c, cudaStream_t s);
 
-int launch_energy64(Ctx& c, cudaStream_t s) {
-    int k = launch_eam_energy64(c, s);
+int launch_energy(Ctx& c, cudaStream_t s) {
+    int k = launch_eam_energy(c, s);
     k_energy_blend<<<c.nred, kRedBlock, 0, s>>>(c.x, c.n, c.grid, c.dyn, c.d_time, c.w, c.e_ace, c.e_eam, c.ace_c1_0,
                                                 c.e_atom, c.partials);
     return k + 1;

@@ -119,7 +119,8 @@ __global__ void k_sort_cells(int* __restrict__ cell_atoms, const int* __restrict
 // per step: FP32 cell-relative positions, ACE weights, compaction of w > 0
 __global__ void k_prepare(const double* __restrict__ x, int n, const GridDev g, const DynDev dy,
                           const double* __restrict__ tptr, const int* __restrict__ cell,
-                          const double* __restrict__ w_fixed, float4* __restrict__ pos4, float* __restrict__ wout,
+                          const double* __restrict__ w_fixed, float4* __restrict__ pos4, float4* __restrict__ pos_lo,
+                          float* __restrict__ wout,
                           int* __restrict__ ace_list, int* __restrict__ flags) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     double w = 0.0;
@@ -150,7 +151,10 @@ __global__ void k_prepare(const double* __restrict__ x, int n, const GridDev g, 
             else if (dist >= dy.r_in + dy.r_sw) w = 0.0;
             else w = 0.5 * (1.0 + cos(3.14159265358979323846 * (dist - dy.r_in) / dy.r_sw));
         }
-        pos4[i] = make_float4((float)(r[0] - o[0]), (float)(r[1] - o[1]), (float)(r[2] - o[2]), (float)(1.0 - w));
+        const double rel[3] = {r[0] - o[0], r[1] - o[1], r[2] - o[2]};
+        const float hx = (float)rel[0], hy = (float)rel[1], hz = (float)rel[2];
+        pos4[i] = make_float4(hx, hy, hz, (float)(1.0 - w));
+        pos_lo[i] = make_float4((float)(rel[0] - hx), (float)(rel[1] - hy), (float)(rel[2] - hz), 0.0f);
         wout[i] = (float)w;
     }
     // warp-aggregated compaction of the atoms that need ACE
@@ -235,8 +239,8 @@ int launch_rebuild(Ctx& c, cudaStream_t s) {
 }
 
 int launch_prepare(Ctx& c, cudaStream_t s) {
-    k_prepare<<<(c.n + 255) / 256, 256, 0, s>>>(c.x, c.n, c.grid, c.dyn, c.d_time, c.cell, c.w_fixed, c.pos4, c.w,
-                                               c.ace_list, c.flags);
+    k_prepare<<<(c.n + 255) / 256, 256, 0, s>>>(c.x, c.n, c.grid, c.dyn, c.d_time, c.cell, c.w_fixed, c.pos4,
+                                               c.pos_lo, c.w, c.ace_list, c.flags);
     return 1;
 }
 

@@ -119,6 +119,7 @@ void fill_tab(const std::vector<Interval>& iv, double rcut, PolyTab& t) {
         t.start[k] = (float)iv[k].a;
         t.mid[k] = (float)iv[k].mid;
         for (int c = 0; c < 6; ++c) t.c[k][c] = (float)iv[k].c[c];
+        t.c0lo[k] = (float)(iv[k].c[0] - (double)t.c[k][0]);
     }
     t.start[t.nint] = (float)rcut;
     for (int b = 0; b < kNBin; ++b) {
@@ -215,39 +216,16 @@ int gaunt_values(float* out, std::string& err) {
     return AP_OK;
 }
 
-void fill_tab64(const std::vector<Interval>& iv, double rcut, PolyTab64& t) {
-    std::memset(&t, 0, sizeof(t));
-    t.nint = (int)iv.size();
-    t.zbl = iv.size() && iv[0].zbl ? 1 : 0;
-    t.rcut = rcut;
-    for (int k = 0; k < t.nint; ++k) {
-        t.start[k] = iv[k].a;
-        t.mid[k] = iv[k].mid;
-        for (int c = 0; c < 6; ++c) t.c[k][c] = iv[k].c[c];
-    }
-    t.start[t.nint] = rcut;
-}
-
-int build_eam_tables(const ap_potential& p, EamDev& out, EamDev64& out64, std::string& err) {
+int build_eam_tables(const ap_potential& p, EamDev& out, std::string& err) {
     std::memset(&out, 0, sizeof(out));
-    std::memset(&out64, 0, sizeof(out64));
     std::vector<Interval> iv;
     double rc_phi = 0.0, rc_rho = 0.0;
     int s = build_intervals(p, 0, iv, rc_phi, err);
     if (s) return s;
     fill_tab(iv, rc_phi, out.phi);
-    fill_tab64(iv, rc_phi, out64.phi);
     s = build_intervals(p, 1, iv, rc_rho, err);
     if (s) return s;
     fill_tab(iv, rc_rho, out.rho);
-    fill_tab64(iv, rc_rho, out64.rho);
-    out64.F_a1 = p.eam_F_a1;
-    out64.F_a2 = p.eam_F_a2;
-    out64.F_dxi = p.eam_F_dxi;
-    if (p.eam_zbl) {
-        out64.zbl_k = p.eam_zbl_Z * p.eam_zbl_Z / (4.0 * 3.14159265358979323846 * p.eam_zbl_eps0);
-        out64.zbl_a = p.eam_zbl_a;
-    }
     if (p.eam_zbl) {
         if (!(p.eam_zbl_eps0 > 0.0 && p.eam_zbl_a > 0.0)) { err = "EAM: bad ZBL parameters"; return AP_ERR_ARG; }
         out.zbl_k = (float)(p.eam_zbl_Z * p.eam_zbl_Z / (4.0 * 3.14159265358979323846 * p.eam_zbl_eps0));

@@ -32,6 +32,11 @@ def _active_pairs(l1, l2, l3):
     return x, y
 
 
+def ace_contract_flops_per_atom():
+    """FLOPs of the contraction kernel per atom (products, densities, dE/dA; no neighbour terms)."""
+    return ace_flops_per_atom(0)
+
+
 def ace_flops_per_atom(n_neighbors):
     tot = 0
     for (l1, l2, l3), nnz in zip(TRIPLES, NNZ):
