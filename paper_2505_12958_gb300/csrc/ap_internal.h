@@ -42,7 +42,8 @@ struct alignas(16) EamDev {
 // ACE coefficient tensors, zero-padded to full n-ranges (a basis function sits at its
 // sorted (n, l) position; the other orderings carry zero).
 struct AceDev {
-    float c3[2][kNT][64][8];  // [density][l-triple][n1 * 8 + n2][n3]
+    float c3[2][kNT][8][65];  // [density][l-triple][n3][n1 * 8 + n2], row padded to 65 floats so that
+                              // both lane mappings of the contraction read it without bank conflicts
     float c2[2][5][64];       // [density][l][n1 * 8 + n2]
     float c1[2][8];           // [density][n]
     float c1_0, c2_0, nref_inv, rc;
@@ -62,6 +63,8 @@ struct GridDev {
     int ncode;                // (2 S0 + 1)(2 S1 + 1)(2 S2 + 1) <= 125
     int ncell;
     float rlist2;
+    int ortho;                // edge vectors along x, y, z
+    double L[3], Linv[3];     // edge lengths (orthorhombic boxes)
 };
 
 struct DynDev {               // time-dependent geometry; time is read from device memory

@@ -110,6 +110,11 @@ ap_status setup_grid(ap::Ctx& c, const ap_box& box, std::vector<float4>& D, std:
         for (int q = 0; q < 3; ++q) g.cellvec[3 * d + q] = g.h[3 * d + q] / n;
     }
     if (ncell > (1ll << 26)) return set_err(c, AP_ERR_ARG, "cell grid too large");
+    g.ortho = (g.h[1] == 0.0 && g.h[2] == 0.0 && g.h[3] == 0.0 && g.h[5] == 0.0 && g.h[6] == 0.0 && g.h[7] == 0.0) ? 1 : 0;
+    for (int d = 0; d < 3; ++d) {
+        g.L[d] = g.h[4 * d];
+        g.Linv[d] = 1.0 / g.h[4 * d];
+    }
     g.ncell = (int)ncell;
     g.ncode = (2 * g.S[0] + 1) * (2 * g.S[1] + 1) * (2 * g.S[2] + 1);
     g.rlist2 = (float)(c.rc_list * c.rc_list);
@@ -233,7 +238,7 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
     *out = nullptr;
     if (!pot || !box || !pos || n < 1 || n > ap::kMaxAtoms) { g_init_err = "ap_init: missing argument or bad atom count"; return AP_ERR_ARG; }
     if (!(pot->mass_amu > 0.0) || !(pot->skin >= 0.0)) { g_init_err = "ap_init: mass must be > 0 and skin >= 0"; return AP_ERR_ARG; }
-    if (pot->ace_precision != AP_ACE_FP32) { g_init_err = "ap_init: this build evaluates A_nlm in FP32 only"; return AP_ERR_ARG; }
+    if (pot->ace_precision < AP_ACE_FP32 || pot->ace_precision > AP_ACE_FP64) { g_init_err = "ap_init: unknown ace_precision"; return AP_ERR_ARG; }
     ap_ctx* xc = new (std::nothrow) ap_ctx();
     if (!xc) return AP_ERR_OOM;
     ap::Ctx& c = xc->c;

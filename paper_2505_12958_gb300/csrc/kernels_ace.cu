@@ -17,6 +17,10 @@
 //      w_i, are added to atom j (minus) and atom i (plus) through 64-bit fixed-point
 //      atomics (2^-40 eV/A resolution), whose integer sums do not depend on order.
 // E_i^ACE is stored without the constant c1_0, which the blend adds in FP64.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cstdint>
 #include <mutex>
 #include <string>
 #include <utility>
@@ -256,14 +260,14 @@ __device__ __forceinline__ void nu3_forward(const float* As, const AceDev& C, in
 #pragma unroll
         for (int k = 0; k < R::W3; ++k) P[k] = 0.0f;
         all_p<T>(P, A1, A2, std::make_integer_sequence<int, R::N>{});
-        const float* c1 = C.c3[0][T][q];
-        const float* c2 = C.c3[1][T][q];
+        const float* c1 = &C.c3[0][T][0][q];
+        const float* c2 = &C.c3[1][T][0][q];
         float s1 = 0.0f, s2 = 0.0f;
 #pragma unroll 2
         for (int n3 = 0; n3 < kNmax; ++n3) {
             const float r = dot_row2<R::W3>(P, As + n3 * kApad + R::B3);
-            s1 = fmaf(c1[n3], r, s1);
-            s2 = fmaf(c2[n3], r, s2);
+            s1 = fmaf(c1[n3 * 65], r, s1);
+            s2 = fmaf(c2[n3 * 65], r, s2);
         }
         p1 += s1;
         p2 += s2;
@@ -286,11 +290,11 @@ __device__ __forceinline__ void nu3_adjoint(const float* As, float* dAs, const A
         load_row<R::W2>(A2, As + n2 * kApad + R::B2);
 #pragma unroll
         for (int m = 0; m < R::W3; ++m) Q[m] = 0.0f;
-        const float* c1 = C.c3[0][T][q];
-        const float* c2 = C.c3[1][T][q];
+        const float* c1 = &C.c3[0][T][0][q];
+        const float* c2 = &C.c3[1][T][0][q];
 #pragma unroll 2
         for (int n3 = 0; n3 < kNmax; ++n3) {
-            const float ce = fmaf(s, c2[n3], c1[n3]);
+            const float ce = fmaf(s, c2[n3 * 65], c1[n3 * 65]);
             const float* a3 = As + n3 * kApad + R::B3;
 #pragma unroll
             for (int m = 0; m < R::W3; ++m) Q[m] = fmaf(ce, a3[m], Q[m]);
@@ -337,7 +341,7 @@ __device__ __forceinline__ void nu3_adjoint(const float* As, float* dAs, const A
         for (int m = 0; m < R::W2; ++m) Tm[m] = 0.0f;
 #pragma unroll 2
         for (int n2 = 0; n2 < kNmax; ++n2) {
-            const float ce = fmaf(s, C.c3[1][T][n1 * 8 + n2][n3], C.c3[0][T][n1 * 8 + n2][n3]);
+            const float ce = fmaf(s, C.c3[1][T][n3][n1 * 8 + n2], C.c3[0][T][n3][n1 * 8 + n2]);
             const float* a2 = As + n2 * kApad + R::B2;
 #pragma unroll
             for (int m = 0; m < R::W2; ++m) Tm[m] = fmaf(ce, a2[m], Tm[m]);
@@ -417,7 +421,55 @@ struct BasisSmem {
     float tileG[kTile][kNmax];
 };
 
-// stage a1 of the ACE pass: A_nlm = (1/nref) sum_j g_n(r_ij) Y_lm(rhat_ij), stored [atom][lm][n]
+// ---------------------------------------------------------------------------------
+// A = Y^T g on tensor cores (mma.sync; M = (l, m) padded to 32, N = n = 8, K = neighbours).
+// Fragment layouts of the PTX m16n8k8 (tf32) and m16n8k16 (bf16 / f16) shapes, with
+// g = lane / 4 and t = lane % 4.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float* d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+template <int MODE>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    if (MODE == AP_ACE_TC_BF16) {
+        __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<uint32_t*>(&v);
+    } else {
+        __half2 v = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<uint32_t*>(&v);
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void mma_16bit(float* d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                          uint32_t b1) {
+    if (MODE == AP_ACE_TC_BF16)
+        asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                     : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                     : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+    else
+        asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                     : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                     : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// element (row lm, column j) of the A operand Y^T; rows 25..31 are padding
+__device__ __forceinline__ float yt(const BasisSmem& S, int lm, int j) { return lm < kNLM ? S.tileY[j][lm] : 0.0f; }
+
+// stage a1 of the ACE pass: A_nlm = (1/nref) sum_j g_n(r_ij) Y_lm(rhat_ij), stored [atom][lm][n].
+// MODE (AP_ACE_*) sets the precision of the contraction over neighbours: FP32 FMA, tensor
+// cores (3xTF32 split, BF16 or FP16 inputs; FP32 accumulation), or FP64 accumulation.
+template <int MODE>
 __global__ void __launch_bounds__(256) k_ace_basis(const float4* __restrict__ pos4, const int* __restrict__ nbr,
                                                    const int* __restrict__ nnbr, int n, const float4* __restrict__ Dtab,
                                                    int ncode, const AceDev* __restrict__ tab,
@@ -428,6 +480,7 @@ __global__ void __launch_bounds__(256) k_ace_basis(const float4* __restrict__ po
     for (int k = threadIdx.x; k < ncode; k += blockDim.x) Ds[k] = Dtab[k];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gq = lane >> 2, tq = lane & 3;
     BasisSmem& S = WS[warp];
     const float rc = tab->rc, rc2 = rc * rc, nrefi = tab->nref_inv;
     const int n_ace = flags[kFlagNAce];
@@ -439,40 +492,115 @@ __global__ void __launch_bounds__(256) k_ace_basis(const float4* __restrict__ po
             continue;
         }
         float accA[kNmax];
+        double accD[MODE == AP_ACE_FP64 ? kNmax : 1];
+        float acc_tc[2][4];
 #pragma unroll
         for (int q = 0; q < kNmax; ++q) accA[q] = 0.0f;
+#pragma unroll
+        for (int q = 0; q < (MODE == AP_ACE_FP64 ? kNmax : 1); ++q) accD[q] = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc_tc[q >> 2][q & 3] = 0.0f;
         for (int t0 = 0; t0 < cnt; t0 += kTile) {
             const int jj = t0 + lane;
+            float g[kNmax], dg[kNmax], Y[kNLM];
             if (jj < cnt) {
                 const float4 v = S.nb[jj];
                 const float ri = 1.0f / v.w;
-                float g[kNmax], dg[kNmax], Y[kNLM];
                 radial(v.w, rc, g, dg);
                 ylm(v.x * ri, v.y * ri, v.z * ri, Y);
+            } else {
 #pragma unroll
-                for (int q = 0; q < kNmax; ++q) S.tileG[lane][q] = g[q];
+                for (int q = 0; q < kNmax; ++q) g[q] = 0.0f;
 #pragma unroll
-                for (int q = 0; q < kNLM; ++q) S.tileY[lane][q] = Y[q];
+                for (int q = 0; q < kNLM; ++q) Y[q] = 0.0f;
             }
+#pragma unroll
+            for (int q = 0; q < kNmax; ++q) S.tileG[lane][q] = g[q];
+#pragma unroll
+            for (int q = 0; q < kNLM; ++q) S.tileY[lane][q] = Y[q];
             __syncwarp();
             const int nt = min(kTile, cnt - t0);
-            if (lane < kNLM) {
-                for (int jj2 = 0; jj2 < nt; ++jj2) {
-                    const float y = S.tileY[jj2][lane];
-                    const float4 g0 = *reinterpret_cast<const float4*>(&S.tileG[jj2][0]);
-                    const float4 g1 = *reinterpret_cast<const float4*>(&S.tileG[jj2][4]);
-                    accA[0] = fmaf(y, g0.x, accA[0]); accA[1] = fmaf(y, g0.y, accA[1]);
-                    accA[2] = fmaf(y, g0.z, accA[2]); accA[3] = fmaf(y, g0.w, accA[3]);
-                    accA[4] = fmaf(y, g1.x, accA[4]); accA[5] = fmaf(y, g1.y, accA[5]);
-                    accA[6] = fmaf(y, g1.z, accA[6]); accA[7] = fmaf(y, g1.w, accA[7]);
+            if (MODE == AP_ACE_FP32 || MODE == AP_ACE_FP64) {
+                if (lane < kNLM) {
+                    for (int jj2 = 0; jj2 < nt; ++jj2) {
+                        const float y = S.tileY[jj2][lane];
+                        const float4 g0 = *reinterpret_cast<const float4*>(&S.tileG[jj2][0]);
+                        const float4 g1 = *reinterpret_cast<const float4*>(&S.tileG[jj2][4]);
+                        const float gg[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+                        if (MODE == AP_ACE_FP64) {
+#pragma unroll
+                            for (int q = 0; q < kNmax; ++q) accD[q] = fma((double)y, (double)gg[q], accD[q]);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < kNmax; ++q) accA[q] = fmaf(y, gg[q], accA[q]);
+                        }
+                    }
+                }
+            } else if (MODE == AP_ACE_TC_TF32X3) {
+#pragma unroll
+                for (int k0 = 0; k0 < kTile; k0 += 8) {
+                    const float bv0 = S.tileG[k0 + tq][gq], bv1 = S.tileG[k0 + tq + 4][gq];
+                    const uint32_t bh0 = to_tf32(bv0), bh1 = to_tf32(bv1);
+                    const uint32_t bl0 = to_tf32(bv0 - __uint_as_float(bh0)), bl1 = to_tf32(bv1 - __uint_as_float(bh1));
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt) {
+                        const int m0 = 16 * mt;
+                        const float av[4] = {yt(S, m0 + gq, k0 + tq), yt(S, m0 + gq + 8, k0 + tq),
+                                             yt(S, m0 + gq, k0 + tq + 4), yt(S, m0 + gq + 8, k0 + tq + 4)};
+                        uint32_t ah[4], al[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            ah[q] = to_tf32(av[q]);
+                            al[q] = to_tf32(av[q] - __uint_as_float(ah[q]));
+                        }
+                        mma_tf32(acc_tc[mt], al[0], al[1], al[2], al[3], bh0, bh1);
+                        mma_tf32(acc_tc[mt], ah[0], ah[1], ah[2], ah[3], bl0, bl1);
+                        mma_tf32(acc_tc[mt], ah[0], ah[1], ah[2], ah[3], bh0, bh1);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int k0 = 0; k0 < kTile; k0 += 16) {
+                    const uint32_t b0 = pack2<MODE>(S.tileG[k0 + 2 * tq][gq], S.tileG[k0 + 2 * tq + 1][gq]);
+                    const uint32_t b1 = pack2<MODE>(S.tileG[k0 + 2 * tq + 8][gq], S.tileG[k0 + 2 * tq + 9][gq]);
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt) {
+                        const int r0 = 16 * mt + gq, r1 = r0 + 8, c0 = k0 + 2 * tq;
+                        const uint32_t a0 = pack2<MODE>(yt(S, r0, c0), yt(S, r0, c0 + 1));
+                        const uint32_t a1 = pack2<MODE>(yt(S, r1, c0), yt(S, r1, c0 + 1));
+                        const uint32_t a2 = pack2<MODE>(yt(S, r0, c0 + 8), yt(S, r0, c0 + 9));
+                        const uint32_t a3 = pack2<MODE>(yt(S, r1, c0 + 8), yt(S, r1, c0 + 9));
+                        mma_16bit<MODE>(acc_tc[mt], a0, a1, a2, a3, b0, b1);
+                    }
                 }
             }
             __syncwarp();
         }
-        if (lane < kNLM) {
-            float4* o = reinterpret_cast<float4*>(Aout + ((size_t)a * kNLM + lane) * kNmax);
-            o[0] = make_float4(accA[0] * nrefi, accA[1] * nrefi, accA[2] * nrefi, accA[3] * nrefi);
-            o[1] = make_float4(accA[4] * nrefi, accA[5] * nrefi, accA[6] * nrefi, accA[7] * nrefi);
+        if (MODE == AP_ACE_FP32 || MODE == AP_ACE_FP64) {
+            if (lane < kNLM) {
+                if (MODE == AP_ACE_FP64) {
+#pragma unroll
+                    for (int q = 0; q < kNmax; ++q) accA[q] = (float)(accD[q] * (double)nrefi);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < kNmax; ++q) accA[q] *= nrefi;
+                }
+                float4* o = reinterpret_cast<float4*>(Aout + ((size_t)a * kNLM + lane) * kNmax);
+                o[0] = make_float4(accA[0], accA[1], accA[2], accA[3]);
+                o[1] = make_float4(accA[4], accA[5], accA[6], accA[7]);
+            }
+        } else {
+            // D fragment: (row g, cols 2t, 2t+1) and (row g + 8, same cols) of each 16-row tile
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const int r0 = 16 * mt + gq, r1 = r0 + 8;
+                if (r0 < kNLM)
+                    *reinterpret_cast<float2*>(Aout + ((size_t)a * kNLM + r0) * kNmax + 2 * tq) =
+                        make_float2(acc_tc[mt][0] * nrefi, acc_tc[mt][1] * nrefi);
+                if (r1 < kNLM)
+                    *reinterpret_cast<float2*>(Aout + ((size_t)a * kNLM + r1) * kNmax + 2 * tq) =
+                        make_float2(acc_tc[mt][2] * nrefi, acc_tc[mt][3] * nrefi);
+            }
         }
     }
 }
@@ -694,8 +822,15 @@ size_t ace_contract_smem_bytes() { return sizeof(AceDev) + kContractWarps * size
 int launch_ace_basis(Ctx& c, cudaStream_t s) {
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c.dev);
-    k_ace_basis<<<nsm * 2, 256, 0, s>>>(c.pos4, c.nbr, c.nnbr, c.n, c.D, c.grid.ncode, c.ace_d, c.ace_list, c.flags,
-                                        c.ace_A);
+#define AP_BASIS_ARGS c.pos4, c.nbr, c.nnbr, c.n, c.D, c.grid.ncode, c.ace_d, c.ace_list, c.flags, c.ace_A
+    switch (c.ace_prec) {
+        case AP_ACE_TC_TF32X3: k_ace_basis<AP_ACE_TC_TF32X3><<<nsm * 2, 256, 0, s>>>(AP_BASIS_ARGS); break;
+        case AP_ACE_TC_BF16: k_ace_basis<AP_ACE_TC_BF16><<<nsm * 2, 256, 0, s>>>(AP_BASIS_ARGS); break;
+        case AP_ACE_TC_FP16: k_ace_basis<AP_ACE_TC_FP16><<<nsm * 2, 256, 0, s>>>(AP_BASIS_ARGS); break;
+        case AP_ACE_FP64: k_ace_basis<AP_ACE_FP64><<<nsm * 2, 256, 0, s>>>(AP_BASIS_ARGS); break;
+        default: k_ace_basis<AP_ACE_FP32><<<nsm * 2, 256, 0, s>>>(AP_BASIS_ARGS); break;
+    }
+#undef AP_BASIS_ARGS
     return 1;
 }
 

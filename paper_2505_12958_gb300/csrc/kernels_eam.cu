@@ -18,6 +18,8 @@ __device__ __forceinline__ void poly_eval(const PolyTab& t, float r, float& f, f
     int b = (int)(r * t.bin_inv);
     b = b < kNBin ? b : kNBin - 1;
     int k = t.bin[b];
+    k += (k + 1 < t.nint && r >= t.start[k + 1]) ? 1 : 0;
+    k += (k + 1 < t.nint && r >= t.start[k + 1]) ? 1 : 0;
     while (k + 1 < t.nint && r >= t.start[k + 1]) ++k;
     if (t.zbl && k == 0) {
         // screened Coulomb: Z^2/(4 pi eps0 r) phi(r/a), phi = sum of four exponentials
@@ -61,19 +63,32 @@ __global__ void __launch_bounds__(256) k_eam_density(const float4* __restrict__ 
     if (u <= 0.0f) { uxi[i] = 0.0f; e_emb[i] = 0.0; return; }
     const float rc2 = T.rho.rcut * T.rho.rcut;
     float rho = 0.0f;
-    int m = nnbr[i];
-    for (int k = 0; k < m; ++k) {
-        int e = nbr[(size_t)k * n + i];
-        int j = e & kNbrMask;
-        float4 d = Ds[(unsigned)e >> kNbrShift];
-        float4 q = pos4[j];
-        float dx = q.x + d.x - p.x, dy = q.y + d.y - p.y, dz = q.z + d.z - p.z;
-        float r2 = dx * dx + dy * dy + dz * dz;
+    const int m = nnbr[i];
+    auto pair = [&](int e, const float4& q) {
+        const float4 d = Ds[(unsigned)e >> kNbrShift];
+        const float dx = q.x + d.x - p.x, dy = q.y + d.y - p.y, dz = q.z + d.z - p.z;
+        const float r2 = dx * dx + dy * dy + dz * dz;
         if (r2 < rc2) {
             float f, df;
             poly_eval(T.rho, sqrtf(r2), f, df, 0.0f, 0.0f);
             rho += f;
         }
+    };
+    // four list entries at a time: their gathers are independent and overlap in flight
+    int k = 0;
+    for (; k + 4 <= m; k += 4) {
+        int e[4];
+        float4 q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) e[u] = nbr[(size_t)(k + u) * n + i];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) q[u] = pos4[e[u] & kNbrMask];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) pair(e[u], q[u]);
+    }
+    for (; k < m; ++k) {
+        const int e = nbr[(size_t)k * n + i];
+        pair(e, pos4[e & kNbrMask]);
     }
     double R = rho, F, dF;
     if (R > 0.0) {
@@ -104,28 +119,45 @@ __global__ void __launch_bounds__(256) k_eam_force(const float4* __restrict__ po
     const float rc2 = T.rc * T.rc, rcr = T.rho.rcut, rcp = T.phi.rcut;
     float fx = 0.f, fy = 0.f, fz = 0.f, eph = 0.f;
     float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f, v4 = 0.f, v5 = 0.f;
-    int m = nnbr[i];
-    for (int k = 0; k < m; ++k) {
-        int e = nbr[(size_t)k * n + i];
-        int j = e & kNbrMask;
-        float4 d = Ds[(unsigned)e >> kNbrShift];
-        float4 q = pos4[j];
-        float dx = q.x + d.x - p.x, dy = q.y + d.y - p.y, dz = q.z + d.z - p.z;
-        float r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 >= rc2) continue;
-        float us = ui + q.w;
-        if (us <= 0.0f) continue;              // both atoms fully ACE
-        float r = sqrtf(r2), ri = 1.0f / r;
+    const int m = nnbr[i];
+    auto pair = [&](int e, const float4& q, float xj) {
+        const float4 d = Ds[(unsigned)e >> kNbrShift];
+        const float dx = q.x + d.x - p.x, dy = q.y + d.y - p.y, dz = q.z + d.z - p.z;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float us = ui + q.w;
+        if (r2 >= rc2 || us <= 0.0f) return;   // beyond the cutoff, or both atoms fully ACE
+        const float r = sqrtf(r2), ri = 1.0f / r;
         float zf = 0.f, dz_ = 0.f, pf = 0.f, dp = 0.f;
         if (r < rcr) poly_eval(T.rho, r, zf, dz_, 0.f, 0.f);
         if (r < rcp) poly_eval(T.phi, r, pf, dp, T.zbl_k, T.zbl_ainv);
-        float c = (xi + uxi[j]) * dz_ + 0.5f * us * dp;
-        float cr = c * ri;
+        const float c = (xi + xj) * dz_ + 0.5f * us * dp;
+        const float cr = c * ri;
         fx += cr * dx; fy += cr * dy; fz += cr * dz;
         eph += pf;
-        float s = -0.5f * cr;
+        const float s = -0.5f * cr;
         v0 += s * dx * dx; v1 += s * dy * dy; v2 += s * dz * dz;
         v3 += s * dx * dy; v4 += s * dx * dz; v5 += s * dy * dz;
+    };
+    int k = 0;
+    for (; k + 4 <= m; k += 4) {
+        int e[4];
+        float4 q[4];
+        float xj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) e[u] = nbr[(size_t)(k + u) * n + i];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = e[u] & kNbrMask;
+            q[u] = pos4[j];
+            xj[u] = uxi[j];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) pair(e[u], q[u], xj[u]);
+    }
+    for (; k < m; ++k) {
+        const int e = nbr[(size_t)k * n + i];
+        const int j = e & kNbrMask;
+        pair(e, pos4[j], uxi[j]);
     }
     f[i] = fx; f[n + i] = fy; f[2 * n + i] = fz;
     e_eam[i] = ui > 0.0f ? e_emb[i] + 0.5 * (double)eph : 0.0;

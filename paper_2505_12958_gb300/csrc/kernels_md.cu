@@ -7,6 +7,7 @@
 // Eq. P_ind) = sum F . dir.  Totals are summed per block in FP64 and then by one block
 // in a fixed order, so they are reproducible run to run.
 #include "ap_internal.h"
+#include "geom.cuh"
 
 namespace ap {
 
@@ -28,16 +29,6 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return s;                               // valid on thread 0
 }
 
-__device__ __forceinline__ void min_image(const GridDev& g, double* d) {
-    double s[3];
-    for (int k = 0; k < 3; ++k) s[k] = d[0] * g.hinv[k] + d[1] * g.hinv[3 + k] + d[2] * g.hinv[6 + k];
-    for (int k = 0; k < 3; ++k)
-        if (g.periodic[k]) {
-            double m = floor(s[k] + 0.5);
-            for (int q = 0; q < 3; ++q) d[q] -= m * g.h[3 * k + q];
-        }
-}
-
 __global__ void k_pos_in(const double* __restrict__ pos, int n, double* __restrict__ x) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -46,65 +37,88 @@ __global__ void k_pos_in(const double* __restrict__ pos, int n, double* __restri
     x[2 * n + i] = pos[3 * i + 2];
 }
 
+// per step: F_i = F_i^EAM (carries u) + ACE sum (carries w) - grad w_i (E^ACE - E^EAM) + F_ind
 __global__ void __launch_bounds__(kRedBlock) k_blend(
     const double* __restrict__ x, int n, const GridDev g, const DynDev dy, const double* __restrict__ tptr,
     const float* __restrict__ wv, float* __restrict__ f, unsigned long long* __restrict__ acc,
-    const float* __restrict__ e_ace, const double* __restrict__ e_eam, double c1_0,
+    const float* __restrict__ e_ace, const double* __restrict__ e_eam, double c1_0, float* __restrict__ out_aos,
+    int* __restrict__ flags) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float wi = wv[i];
+    float F[3];
+    for (int k = 0; k < 3; ++k) {
+        const long long q = (long long)acc[(size_t)k * n + i];
+        acc[(size_t)k * n + i] = 0ull;
+        F[k] = f[(size_t)k * n + i] + (float)((double)q * (1.0 / kFixScale));
+    }
+    const bool trans = dy.reg_kind == AP_REGION_SPHERE && wi > 0.0f && wi < 1.0f;
+    if (trans || dy.ind_on) {
+        const double t = *tptr;
+        const double r[3] = {x[i], x[n + i], x[2 * n + i]};
+        if (trans) {
+            double d[3];
+            for (int k = 0; k < 3; ++k) d[k] = r[k] - (dy.reg_c0[k] - (dy.follow ? dy.ind_vel[k] * t : 0.0));
+            min_image_vec(g, d);
+            const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            float dS;
+            switch_weight(d2, dy.r_in, dy.r_sw, &dS);
+            const float de = (float)((c1_0 + (double)e_ace[i]) - e_eam[i]);
+            const float gi = dS * de * rsqrtf((float)d2);
+            for (int k = 0; k < 3; ++k) F[k] -= gi * (float)d[k];
+        }
+        if (dy.ind_on) {
+            double d[3];
+            for (int k = 0; k < 3; ++k) d[k] = r[k] - (dy.ind_c0[k] - dy.ind_vel[k] * t);
+            min_image_vec(g, d);
+            const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (d2 < dy.R * dy.R && d2 > 0.0) {
+                const double dist = sqrt(d2), h = dy.R - dist, c = dy.K * h * h / dist;
+                for (int k = 0; k < 3; ++k) F[k] += (float)(c * d[k]);
+            }
+        }
+    }
+    for (int k = 0; k < 3; ++k) f[(size_t)k * n + i] = F[k];
+    if (out_aos)
+        for (int k = 0; k < 3; ++k) out_aos[3 * (size_t)i + k] = F[k];
+    if (!(F[0] == F[0]) || !(F[1] == F[1]) || !(F[2] == F[2])) {
+        atomicOr(&flags[kFlagErr], kErrDomain);
+        flags[kFlagBad] = i;
+    }
+}
+
+// on request: per-atom E_i + V_ind, and block sums of the energies, the virial and the load
+__global__ void __launch_bounds__(kRedBlock) k_energy_blend(
+    const double* __restrict__ x, int n, const GridDev g, const DynDev dy, const double* __restrict__ tptr,
+    const float* __restrict__ wv, const float* __restrict__ e_ace, const double* __restrict__ e_eam, double c1_0,
     const float* __restrict__ vir_eam, const float* __restrict__ vir_ace, double* __restrict__ e_atom,
-    double* __restrict__ partials, float* __restrict__ out_aos, int* __restrict__ flags) {
+    double* __restrict__ partials, int* __restrict__ flags) {
     __shared__ double sh[32];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double acc_e = 0.0, acc_i = 0.0, acc_l = 0.0, vv[6] = {0, 0, 0, 0, 0, 0};
     if (i < n) {
         const double wi = wv[i], ui = 1.0 - wi;
-        double F[3];
-        for (int k = 0; k < 3; ++k) {
-            const long long q = (long long)acc[(size_t)k * n + i];
-            acc[(size_t)k * n + i] = 0ull;
-            F[k] = (double)f[(size_t)k * n + i] + (double)q * (1.0 / kFixScale);
-        }
-        const double eA = wi > 0.0 ? c1_0 + (double)e_ace[i] : 0.0;
-        const double eE = ui > 0.0 ? e_eam[i] : 0.0;
-        const double Ei = wi * eA + ui * eE;
-        const double r[3] = {x[i], x[n + i], x[2 * n + i]};
-        const double t = *tptr;
-        if (dy.reg_kind == AP_REGION_SPHERE && wi > 0.0 && wi < 1.0) {
-            double d[3];
-            for (int k = 0; k < 3; ++k) d[k] = r[k] - (dy.reg_c0[k] - (dy.follow ? dy.ind_vel[k] * t : 0.0));
-            min_image(g, d);
-            const double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-            if (dist > dy.r_in && dist < dy.r_in + dy.r_sw) {
-                const double ds = -0.5 * kPi / dy.r_sw * sin(kPi * (dist - dy.r_in) / dy.r_sw);
-                const double de = eA - eE;
-                for (int k = 0; k < 3; ++k) F[k] -= ds * d[k] / dist * de;
-            }
-        }
+        const double Ei = (wi > 0.0 ? wi * (c1_0 + (double)e_ace[i]) : 0.0) + (ui > 0.0 ? ui * e_eam[i] : 0.0);
         double V = 0.0;
         if (dy.ind_on) {
+            const double t = *tptr;
             double d[3];
-            for (int k = 0; k < 3; ++k) d[k] = r[k] - (dy.ind_c0[k] - dy.ind_vel[k] * t);
-            min_image(g, d);
-            const double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-            if (dist < dy.R && dist > 0.0) {
-                const double h = dy.R - dist;
+            for (int k = 0; k < 3; ++k) d[k] = x[(size_t)k * n + i] - (dy.ind_c0[k] - dy.ind_vel[k] * t);
+            min_image_vec(g, d);
+            const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (d2 < dy.R * dy.R && d2 > 0.0) {
+                const double dist = sqrt(d2), h = dy.R - dist;
                 V = dy.K * h * h * h / 3.0;
-                double fl = 0.0;
-                for (int k = 0; k < 3; ++k) {
-                    const double fi = dy.K * h * h * d[k] / dist;
-                    F[k] += fi;
-                    fl += fi * dy.ind_dir[k];
-                }
-                acc_l = fl;
+                const double c = dy.K * h * h / dist;
+                acc_l = c * (d[0] * dy.ind_dir[0] + d[1] * dy.ind_dir[1] + d[2] * dy.ind_dir[2]);
             }
         }
-        for (int k = 0; k < 3; ++k) f[(size_t)k * n + i] = (float)F[k];
-        if (out_aos)
-            for (int k = 0; k < 3; ++k) out_aos[3 * (size_t)i + k] = (float)F[k];
         e_atom[i] = Ei + V;
         acc_e = Ei;
         acc_i = V;
-        for (int k = 0; k < 6; ++k) vv[k] = (double)vir_eam[(size_t)k * n + i] + (wi > 0.0 ? (double)vir_ace[(size_t)k * n + i] : 0.0);
-        if (!(Ei == Ei) || !(F[0] == F[0]) || !(F[1] == F[1]) || !(F[2] == F[2])) {
+        for (int k = 0; k < 6; ++k)
+            vv[k] = (double)vir_eam[(size_t)k * n + i] + (wi > 0.0 ? (double)vir_ace[(size_t)k * n + i] : 0.0);
+        if (!(Ei == Ei)) {
             atomicOr(&flags[kFlagErr], kErrDomain);
             flags[kFlagBad] = i;
         }
@@ -115,41 +129,6 @@ __global__ void __launch_bounds__(kRedBlock) k_blend(
     s = block_sum(acc_i, sh); if (threadIdx.x == 0) out[1] = s;
     for (int k = 0; k < 6; ++k) { s = block_sum(vv[k], sh); if (threadIdx.x == 0) out[2 + k] = s; }
     s = block_sum(acc_l, sh); if (threadIdx.x == 0) out[8] = s;
-}
-
-// energies only (after the compensated EAM energy pass): per-atom E_i + V_ind and the two
-// energy partial sums; forces, virial and load partials stay those of k_blend
-__global__ void __launch_bounds__(kRedBlock) k_energy_blend(
-    const double* __restrict__ x, int n, const GridDev g, const DynDev dy, const double* __restrict__ tptr,
-    const float* __restrict__ wv, const float* __restrict__ e_ace, const double* __restrict__ e_eam, double c1_0,
-    double* __restrict__ e_atom, double* __restrict__ partials) {
-    __shared__ double sh[32];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double acc_e = 0.0, acc_i = 0.0;
-    if (i < n) {
-        const double wi = wv[i], ui = 1.0 - wi;
-        const double Ei = (wi > 0.0 ? wi * (c1_0 + (double)e_ace[i]) : 0.0) + (ui > 0.0 ? ui * e_eam[i] : 0.0);
-        double V = 0.0;
-        if (dy.ind_on) {
-            const double t = *tptr;
-            double d[3];
-            for (int k = 0; k < 3; ++k) d[k] = x[(size_t)k * n + i] - (dy.ind_c0[k] - dy.ind_vel[k] * t);
-            min_image(g, d);
-            const double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-            if (dist < dy.R && dist > 0.0) {
-                const double h = dy.R - dist;
-                V = dy.K * h * h * h / 3.0;
-            }
-        }
-        e_atom[i] = Ei + V;
-        acc_e = Ei;
-        acc_i = V;
-    }
-    double* out = partials + (size_t)blockIdx.x * kNP;
-    double s = block_sum(acc_e, sh);
-    if (threadIdx.x == 0) out[0] = s;
-    s = block_sum(acc_i, sh);
-    if (threadIdx.x == 0) out[1] = s;
 }
 
 __global__ void __launch_bounds__(kRedBlock) k_kinetic(const double* __restrict__ v, const unsigned char* __restrict__ fixed,
@@ -205,8 +184,7 @@ int launch_pos_in(Ctx& c, cudaStream_t s, const double* pos) {
 
 int launch_blend(Ctx& c, cudaStream_t s, float* out_aos) {
     k_blend<<<c.nred, kRedBlock, 0, s>>>(c.x, c.n, c.grid, c.dyn, c.d_time, c.w, c.f, c.acc, c.e_ace, c.e_eam,
-                                         c.ace_c1_0, c.vir_eam, c.vir_ace, c.e_atom,
-                                         c.partials, out_aos, c.flags);
+                                         c.ace_c1_0, out_aos, c.flags);
     return 1;
 }
 
@@ -215,7 +193,7 @@ int launch_eam_energy(Ctx& c, cudaStream_t s);
 int launch_energy(Ctx& c, cudaStream_t s) {
     int k = launch_eam_energy(c, s);
     k_energy_blend<<<c.nred, kRedBlock, 0, s>>>(c.x, c.n, c.grid, c.dyn, c.d_time, c.w, c.e_ace, c.e_eam, c.ace_c1_0,
-                                                c.e_atom, c.partials);
+                                                c.vir_eam, c.vir_ace, c.e_atom, c.partials, c.flags);
     return k + 1;
 }
 

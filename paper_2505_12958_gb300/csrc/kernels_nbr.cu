@@ -13,6 +13,7 @@
 // (insertion sort after the atomic scatter), which makes the list, and therefore every
 // FP32 summation order, deterministic.
 #include "ap_internal.h"
+#include "geom.cuh"
 
 namespace ap {
 
@@ -136,20 +137,12 @@ __global__ void k_prepare(const double* __restrict__ x, int n, const GridDev g, 
         } else if (dy.reg_kind == AP_REGION_EXPLICIT) {
             w = w_fixed[i];
         } else if (dy.reg_kind == AP_REGION_SPHERE) {
-            double t = *tptr;
+            const double t = *tptr;
             double d[3];
             for (int q = 0; q < 3; ++q) d[q] = r[q] - (dy.reg_c0[q] - (dy.follow ? dy.ind_vel[q] * t : 0.0));
-            double s[3];
-            for (int k = 0; k < 3; ++k) s[k] = d[0] * g.hinv[k] + d[1] * g.hinv[3 + k] + d[2] * g.hinv[6 + k];
-            for (int k = 0; k < 3; ++k)
-                if (g.periodic[k]) {
-                    double m = floor(s[k] + 0.5);
-                    for (int q = 0; q < 3; ++q) d[q] -= m * g.h[3 * k + q];
-                }
-            double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-            if (dist < dy.r_in) w = 1.0;
-            else if (dist >= dy.r_in + dy.r_sw) w = 0.0;
-            else w = 0.5 * (1.0 + cos(3.14159265358979323846 * (dist - dy.r_in) / dy.r_sw));
+            min_image_vec(g, d);
+            float dS;
+            w = switch_weight(d[0] * d[0] + d[1] * d[1] + d[2] * d[2], dy.r_in, dy.r_sw, &dS);
         }
         const double rel[3] = {r[0] - o[0], r[1] - o[1], r[2] - o[2]};
         const float hx = (float)rel[0], hy = (float)rel[1], hz = (float)rel[2];

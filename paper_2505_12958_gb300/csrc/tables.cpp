@@ -301,7 +301,7 @@ int build_ace_tables(const ap_potential& p, AceDev& out, std::string& err) {
                     err = "ACE: unsupported l-triple";
                     return AP_ERR_ARG;
                 }
-                out.c3[d][t][key[0][1] * 8 + key[1][1]][key[2][1]] += (float)c;
+                out.c3[d][t][key[2][1]][key[0][1] * 8 + key[1][1]] += (float)c;
             } else {
                 err = "ACE: only nu = 1, 2, 3 (body order <= 4) are built";
                 return AP_ERR_ARG;
