@@ -164,8 +164,16 @@ ap_status ap_compute_forces_host(ap_ctx* ctx, const double* h_pos, float* h_forc
 
 /* n_steps velocity-Verlet steps of dt_fs on the library-owned positions and velocities.
  * Fixed atoms keep x and v.  The indenter (and a following region) advance with time.
- * Asynchronous. */
+ * On a stream other than the legacy default stream (and with profiling off) one step is
+ * captured once as a CUDA graph and replayed.  Asynchronous. */
 ap_status ap_step(ap_ctx* ctx, int n_steps, double dt_fs, void* stream);
+
+/* Serving form: n_steps[k] velocity-Verlet steps (dt_fs) for each of n_ctx independent
+ * contexts, each issued on its own context's stream (give every context its own
+ * non-blocking stream at ap_init and the steps of different contexts overlap on the
+ * device).  A context's results do not depend on which others are stepped with it.
+ * Asynchronous; returns the first error. */
+ap_status ap_step_batch(ap_ctx* const* ctxs, const int* n_steps, int n_ctx, double dt_fs);
 
 /* Totals of the last force evaluation; d_e_atom (device, n FP64, nullable) receives
  * the per-atom energies E_i + V_ind(r_i).  Synchronises; returns sticky device errors. */
@@ -179,6 +187,10 @@ ap_status ap_get_state(ap_ctx* ctx, double* x, double* v, double* t_fs);
 /* Replace positions / velocities (host, n x 3, either may be NULL) and time; forces a
  * neighbour rebuild and a fresh force evaluation before the next step. */
 ap_status ap_set_state(ap_ctx* ctx, const double* x, const double* v, double t_fs);
+/* Replace the box (e.g. a strained cell); positions are not changed.  The cell grid and
+ * the neighbour list are rebuilt by the next evaluation.  AP_ERR_ARG if the new box is
+ * thinner than half the list cutoff.  Synchronises. */
+ap_status ap_set_box(ap_ctx* ctx, const ap_box* box);
 /* Host copy of the last forces (n x 3 FP32). */
 ap_status ap_get_forces(ap_ctx* ctx, float* f);
 /* Host copy of the current weights w_i (n FP64). */

@@ -20,7 +20,7 @@ from . import _capi
 from ._capi import PRECISION, REGION, STAGES, STATUS
 
 __all__ = ["APContext", "APError", "build", "PRECISION", "STAGES", "potential_struct", "gaunt_real",
-           "eam_table_eval"]
+           "eam_table_eval", "step_batch"]
 
 
 class APError(RuntimeError):
@@ -154,6 +154,7 @@ class APContext:
             raise APError(st, L.ap_last_error(None).decode())
         self._h = h
         self._L = L
+        self.stream = stream          # kept alive for the context's lifetime
 
     def _chk(self, st):
         if st != 0:
@@ -214,6 +215,11 @@ class APContext:
         self._chk(self._L.ap_set_state(self._h, None if xx is None else xx.ctypes.data_as(_capi.PD),
                                        None if vv is None else vv.ctypes.data_as(_capi.PD), float(t)))
 
+    def set_box(self, box):
+        """Replace the box (dict with h, origin, periodic); the next evaluation re-bins."""
+        b = _box_struct(box)
+        self._chk(self._L.ap_set_box(self._h, C.byref(b)))
+
     def profile(self, enable=True):
         self._chk(self._L.ap_profile(self._h, int(enable)))
 
@@ -249,6 +255,18 @@ class APContext:
 
     def __exit__(self, *a):
         self.close()
+
+
+def step_batch(ctxs, n_steps, dt):
+    """n_steps[k] MD steps for each context ctxs[k], each on its own stream (ap_step_batch)."""
+    L = _capi.lib()
+    k = len(ctxs)
+    hs = (C.c_void_p * k)(*[c._h.value for c in ctxs])
+    ns = (C.c_int * k)(*[int(s) for s in n_steps])
+    st = L.ap_step_batch(hs, ns, k, float(dt))
+    if st != 0:
+        msgs = "; ".join(L.ap_last_error(c._h).decode() for c in ctxs)
+        raise APError(st, msgs)
 
 
 def gaunt_real(l1, m1, l2, m2, l3, m3):

@@ -66,11 +66,13 @@ def lib():
         "ap_compute_forces": (I, [VP, VP, VP, VP]),
         "ap_compute_forces_host": (I, [VP, PD, PF, PD, VP]),
         "ap_step": (I, [VP, I, D, VP]),
+        "ap_step_batch": (I, [C.POINTER(VP), PI, I, D]),
         "ap_energy": (I, [VP, P(Report), VP]),
         "ap_check": (I, [VP]),
         "ap_get_state": (I, [VP, PD, PD, PD]),
         "ap_set_state": (I, [VP, PD, PD, D]),
         "ap_get_forces": (I, [VP, PF]),
+        "ap_set_box": (I, [VP, P(Box)]),
         "ap_get_weights": (I, [VP, PD]),
         "ap_set_weights": (I, [VP, PD]),
         "ap_profile": (I, [VP, I]),

@@ -135,6 +135,8 @@ struct Ctx {
     double* pos_stage = nullptr;                         // n x 3 host-transfer staging
     float* f_stage = nullptr;                            // n x 3 host-transfer staging
     int nred = 0;
+    int ncell_cap = 0;                                   // allocated length of the cell arrays
+    long long layout_gen = 0;                            // bumped when kernel arguments change
 
     int* h_flags = nullptr;                              // pinned
     double* h_totals = nullptr;                          // pinned

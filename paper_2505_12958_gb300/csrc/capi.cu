@@ -16,6 +16,12 @@ struct ap_ctx {
     struct Pending { int stage; cudaEvent_t a, b; };
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> free_ev;
+    // one captured MD step (kick-drift, force evaluation, kick), replayed by ap_step
+    cudaGraphExec_t step_exec = nullptr;
+    cudaStream_t step_stream = nullptr;
+    double step_dt = 0.0;
+    long long step_kernels = 0;
+    long long step_gen = -1;
 };
 
 namespace {
@@ -52,6 +58,11 @@ void stage(ap_ctx* x, int st, cudaStream_t s, F&& launch) {
     c.launches += launch();
     cudaEventRecord(b, s);
     x->pending.push_back({st, a, b});
+}
+
+void drop_step_graph(ap_ctx* x) {
+    if (x->step_exec) cudaGraphExecDestroy(x->step_exec);
+    x->step_exec = nullptr;
 }
 
 void drain_events(ap_ctx* x) {
@@ -131,11 +142,25 @@ ap_status setup_grid(ap::Ctx& c, const ap_box& box, std::vector<float4>& D, std:
     return AP_OK;
 }
 
+// Context memory comes from the device's stream-ordered pool on the context's stream, so
+// creating and destroying contexts (e.g. requests of a serving loop) never synchronises
+// the whole device; freed blocks stay cached in the pool up to a release threshold.
+void pool_setup(int dev) {
+    static int done = -1;
+    if (done == dev) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        unsigned long long thr = 8ull << 30;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done = dev;
+}
+
 template <class T>
 ap_status dalloc(ap::Ctx& c, T** p, size_t count) {
     if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
-    if (e != cudaSuccess) { *p = nullptr; return cuda_check(c, e, "cudaMalloc"); }
+    cudaError_t e = cudaMallocAsync((void**)p, count * sizeof(T), c.stream);
+    if (e != cudaSuccess) { *p = nullptr; return cuda_check(c, e, "cudaMallocAsync"); }
     return AP_OK;
 }
 
@@ -145,7 +170,8 @@ void free_all(ap::Ctx& c) {
                   c.cell_atoms, c.nbr, c.nnbr, c.ace_list, c.flags, c.d_time, c.partials, c.totals, c.e_atom,
                   c.pos_stage, c.f_stage};
     for (void* p : ps)
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, c.stream);
+    cudaStreamSynchronize(c.stream);
     if (c.h_flags) cudaFreeHost(c.h_flags);
     if (c.h_totals) cudaFreeHost(c.h_totals);
     delete c.ace_h;
@@ -195,15 +221,17 @@ ap_status read_flags(ap::Ctx& c, cudaStream_t s) {
         if (err & ap::kErrCapacity) {
             int cap = ((int)(need * 1.25) + 8 + 3) & ~3;
             int* nb = nullptr;
-            if (cudaMalloc((void**)&nb, (size_t)cap * c.n * sizeof(int)) == cudaSuccess) {
-                cudaFree(c.nbr);
+            if (cudaMallocAsync((void**)&nb, (size_t)cap * c.n * sizeof(int), c.stream) == cudaSuccess) {
+                cudaFreeAsync(c.nbr, c.stream);
                 c.nbr = nb;
                 c.cap = cap;
+                c.layout_gen += 1;
             }
         }
         int zero[2] = {1, 0};
-        cudaMemcpy(&c.flags[ap::kFlagRebuild], &zero[0], sizeof(int), cudaMemcpyHostToDevice);
-        cudaMemcpy(&c.flags[ap::kFlagErr], &zero[1], sizeof(int), cudaMemcpyHostToDevice);
+        cudaMemcpyAsync(&c.flags[ap::kFlagRebuild], &zero[0], sizeof(int), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(&c.flags[ap::kFlagErr], &zero[1], sizeof(int), cudaMemcpyHostToDevice, s);
+        cudaStreamSynchronize(s);
         c.forces_valid = false;
         return set_err(c, AP_ERR_CAPACITY, m);
     }
@@ -255,6 +283,7 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
         return s2;
     };
     if (cudaGetDevice(&c.dev) != cudaSuccess) { c.err = "no CUDA device"; return fail(AP_ERR_CUDA); }
+    pool_setup(c.dev);
     std::string err;
     if (ap::build_eam_tables(*pot, c.eam_h, err)) { c.err = err; return fail(AP_ERR_ARG); }
     c.ace_h = new (std::nothrow) ap::AceDev();
@@ -300,8 +329,8 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
     // device memory
     const size_t N = (size_t)n;
     c.nred = (n + ap::kRedBlock - 1) / ap::kRedBlock;
-    if ((st = dalloc(c, &c.eam_d, 1)) || (st = dalloc(c, &c.ace_d, 1)) || (st = dalloc(c, &c.D, D.size())) ||
-        (st = dalloc(c, &c.Dlo, Dlo.size())) || (st = dalloc(c, &c.pos_lo, N)) ||
+    if ((st = dalloc(c, &c.eam_d, 1)) || (st = dalloc(c, &c.ace_d, 1)) || (st = dalloc(c, &c.D, 125)) ||
+        (st = dalloc(c, &c.Dlo, 125)) || (st = dalloc(c, &c.pos_lo, N)) ||
         (st = dalloc(c, &c.x, 3 * N)) || (st = dalloc(c, &c.v, 3 * N)) || (st = dalloc(c, &c.xb, 3 * N)) ||
         (st = dalloc(c, &c.f, 3 * N)) || (st = dalloc(c, &c.pos4, N)) || (st = dalloc(c, &c.uxi, N)) ||
         (st = dalloc(c, &c.w, N)) || (st = dalloc(c, &c.e_emb, N)) || (st = dalloc(c, &c.e_eam, N)) ||
@@ -314,6 +343,7 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
         (st = dalloc(c, &c.d_time, 1)) || (st = dalloc(c, &c.partials, (size_t)c.nred * 10)) ||
         (st = dalloc(c, &c.totals, 16)) || (st = dalloc(c, &c.e_atom, N)))
         return fail(st);
+    c.ncell_cap = c.grid.ncell;
     if (cudaMallocHost((void**)&c.h_flags, sizeof(int) * ap::kFlagCount) != cudaSuccess ||
         cudaMallocHost((void**)&c.h_totals, sizeof(double) * 16) != cudaSuccess) {
         c.err = "pinned host allocation";
@@ -323,7 +353,10 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
     to_soa(pos, n, soa);
     cudaError_t e = cudaSuccess;
     auto cp = [&](void* dst, const void* src, size_t bytes) {
-        if (e == cudaSuccess) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c.stream);
+    };
+    auto zero = [&](void* dst, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMemsetAsync(dst, 0, bytes, c.stream);
     };
     cp(c.eam_d, &c.eam_h, sizeof(ap::EamDev));
     cp(c.ace_d, c.ace_h, sizeof(ap::AceDev));
@@ -332,20 +365,23 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
     cp(c.x, soa.data(), 3 * N * sizeof(double));
     cp(c.xb, soa.data(), 3 * N * sizeof(double));
     if (vel) { to_soa(vel, n, soa); cp(c.v, soa.data(), 3 * N * sizeof(double)); }
-    else if (e == cudaSuccess) e = cudaMemset(c.v, 0, 3 * N * sizeof(double));
+    else zero(c.v, 3 * N * sizeof(double));
     if (fixed) cp(c.fixed, fixed, N);
-    else if (e == cudaSuccess) e = cudaMemset(c.fixed, 0, N);
+    else zero(c.fixed, N);
     if (region && region->kind == AP_REGION_EXPLICIT) {
         for (int i = 0; i < n; ++i)
             if (!(region->w_explicit[i] >= 0.0 && region->w_explicit[i] <= 1.0)) { c.err = "explicit weights must lie in [0, 1]"; return fail(AP_ERR_ARG); }
         cp(c.w_fixed, region->w_explicit, N * sizeof(double));
     }
-    if (e == cudaSuccess) e = cudaMemset(c.acc, 0, 3 * N * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemset(c.cell_count, 0, (size_t)c.grid.ncell * sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(c.flags, 0, ap::kFlagCount * sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(c.d_time, 0, sizeof(double));
-    if (e == cudaSuccess) e = cudaMemset(c.vir_ace, 0, 6 * N * sizeof(float));
-    if (e == cudaSuccess) e = cudaMemset(c.e_ace, 0, N * sizeof(float));
+    zero(c.acc, 3 * N * sizeof(unsigned long long));
+    zero(c.cell_count, (size_t)c.grid.ncell * sizeof(int));
+    zero(c.flags, ap::kFlagCount * sizeof(int));
+    zero(c.d_time, sizeof(double));
+    zero(c.vir_ace, 6 * N * sizeof(float));
+    zero(c.e_ace, N * sizeof(float));
+    zero(c.e_eam, N * sizeof(double));
+    zero(c.e_emb, N * sizeof(double));
+    zero(c.vir_eam, 6 * N * sizeof(float));
     int one = 1;
     cp(&c.flags[ap::kFlagRebuild], &one, sizeof(int));
     if (e != cudaSuccess) { cuda_check(c, e, "ap_init upload"); return fail(AP_ERR_CUDA); }
@@ -402,19 +438,65 @@ ap_status ap_compute_forces_host(ap_ctx* xc, const double* h_pos, float* h_force
     return AP_OK;
 }
 
+bool capturable(cudaStream_t s) {
+    return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
+}
+
 ap_status ap_step(ap_ctx* xc, int n_steps, double dt, void* stream) {
     if (!xc || n_steps < 0 || !(dt > 0.0)) return AP_ERR_ARG;
     ap::Ctx& c = xc->c;
     cudaStream_t s = pick(xc, stream);
     if (!c.forces_valid) run_forces(xc, s, nullptr);
-    for (int k = 0; k < n_steps; ++k) {
-        stage(xc, AP_STAGE_INTEGRATE, s, [&] { return ap::launch_kick_drift(c, s, dt, 1); });
+    if (c.prof || !capturable(s) || n_steps == 0) {
+        for (int k = 0; k < n_steps; ++k) {
+            stage(xc, AP_STAGE_INTEGRATE, s, [&] { return ap::launch_kick_drift(c, s, dt, 1); });
+            run_forces(xc, s, nullptr);
+            stage(xc, AP_STAGE_INTEGRATE, s, [&] { return ap::launch_kick(c, s, dt); });
+            c.t += dt;
+            c.step += 1;
+        }
+        return cuda_check(c, cudaGetLastError(), "ap_step");
+    }
+    if (xc->step_exec && (xc->step_stream != s || xc->step_dt != dt || xc->step_gen != c.layout_gen)) drop_step_graph(xc);
+    if (!xc->step_exec) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_check(c, e, "ap_step capture");
+        const long long before = c.launches;
+        c.launches += ap::launch_kick_drift(c, s, dt, 1);
         run_forces(xc, s, nullptr);
-        stage(xc, AP_STAGE_INTEGRATE, s, [&] { return ap::launch_kick(c, s, dt); });
+        c.launches += ap::launch_kick(c, s, dt);
+        xc->step_kernels = c.launches - before;
+        c.launches = before;
+        e = cudaStreamEndCapture(s, &g);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&xc->step_exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) { xc->step_exec = nullptr; return cuda_check(c, e, "ap_step graph"); }
+        xc->step_stream = s;
+        xc->step_dt = dt;
+        xc->step_gen = c.layout_gen;
+    }
+    for (int k = 0; k < n_steps; ++k) {
+        cudaError_t e = cudaGraphLaunch(xc->step_exec, s);
+        if (e != cudaSuccess) return cuda_check(c, e, "ap_step launch");
+        c.launches += xc->step_kernels;
         c.t += dt;
         c.step += 1;
     }
-    return cuda_check(c, cudaGetLastError(), "ap_step");
+    c.forces_valid = true;
+    c.energy_fresh = false;
+    return AP_OK;
+}
+
+ap_status ap_step_batch(ap_ctx* const* ctxs, const int* n_steps, int n_ctx, double dt) {
+    if (!ctxs || !n_steps || n_ctx < 0) return AP_ERR_ARG;
+    ap_status first = AP_OK;
+    for (int k = 0; k < n_ctx; ++k) {
+        if (!ctxs[k]) return AP_ERR_ARG;
+        ap_status st = ap_step(ctxs[k], n_steps[k], dt, nullptr);
+        if (st != AP_OK && first == AP_OK) first = st;
+    }
+    return first;
 }
 
 ap_status ap_energy(ap_ctx* xc, ap_report* out, double* d_e_atom) {
@@ -473,14 +555,51 @@ ap_status ap_set_state(ap_ctx* xc, const double* x, const double* v, double t) {
     const size_t N = (size_t)c.n;
     std::vector<double> soa;
     cudaError_t e = cudaStreamSynchronize(c.stream);
-    if (x && e == cudaSuccess) { to_soa(x, c.n, soa); e = cudaMemcpy(c.x, soa.data(), 3 * N * sizeof(double), cudaMemcpyHostToDevice); }
-    if (v && e == cudaSuccess) { to_soa(v, c.n, soa); e = cudaMemcpy(c.v, soa.data(), 3 * N * sizeof(double), cudaMemcpyHostToDevice); }
+    std::vector<double> soa_v;
+    if (x && e == cudaSuccess) { to_soa(x, c.n, soa); e = cudaMemcpyAsync(c.x, soa.data(), 3 * N * sizeof(double), cudaMemcpyHostToDevice, c.stream); }
+    if (v && e == cudaSuccess) { to_soa(v, c.n, soa_v); e = cudaMemcpyAsync(c.v, soa_v.data(), 3 * N * sizeof(double), cudaMemcpyHostToDevice, c.stream); }
     int one = 1;
-    if (e == cudaSuccess) e = cudaMemcpy(&c.flags[ap::kFlagRebuild], &one, sizeof(int), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(c.d_time, &t, sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&c.flags[ap::kFlagRebuild], &one, sizeof(int), cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c.d_time, &t, sizeof(double), cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
     if (e != cudaSuccess) return cuda_check(c, e, "ap_set_state");
     c.t = t;
     c.forces_valid = false;
+    return AP_OK;
+}
+
+ap_status ap_set_box(ap_ctx* xc, const ap_box* box) {
+    if (!xc || !box) return AP_ERR_ARG;
+    ap::Ctx& c = xc->c;
+    cudaError_t e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "ap_set_box");
+    const ap::GridDev old = c.grid;
+    std::vector<float4> D, Dlo;
+    ap_status st = setup_grid(c, *box, D, Dlo);
+    if (st != AP_OK) { c.grid = old; return st; }
+    if (c.grid.ncell > c.ncell_cap) {
+        int *cc = nullptr, *cs = nullptr;
+        if (cudaMallocAsync((void**)&cc, (size_t)c.grid.ncell * sizeof(int), c.stream) != cudaSuccess ||
+            cudaMallocAsync((void**)&cs, ((size_t)c.grid.ncell + 1) * sizeof(int), c.stream) != cudaSuccess) {
+            if (cc) cudaFreeAsync(cc, c.stream);
+            c.grid = old;
+            return set_err(c, AP_ERR_OOM, "ap_set_box: cell arrays");
+        }
+        cudaFreeAsync(c.cell_count, c.stream);
+        cudaFreeAsync(c.cell_start, c.stream);
+        c.cell_count = cc;
+        c.cell_start = cs;
+        c.ncell_cap = c.grid.ncell;
+    }
+    e = cudaMemsetAsync(c.cell_count, 0, (size_t)c.grid.ncell * sizeof(int), c.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c.D, D.data(), D.size() * sizeof(float4), cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c.Dlo, Dlo.data(), Dlo.size() * sizeof(float4), cudaMemcpyHostToDevice, c.stream);
+    int one = 1;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&c.flags[ap::kFlagRebuild], &one, sizeof(int), cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "ap_set_box");
+    c.forces_valid = false;
+    c.layout_gen += 1;
     return AP_OK;
 }
 
@@ -515,7 +634,8 @@ ap_status ap_set_weights(ap_ctx* xc, const double* w) {
     for (int i = 0; i < c.n; ++i)
         if (!(w[i] >= 0.0 && w[i] <= 1.0)) return set_err(c, AP_ERR_ARG, "weights must lie in [0, 1]");
     cudaError_t e = cudaStreamSynchronize(c.stream);
-    if (e == cudaSuccess) e = cudaMemcpy(c.w_fixed, w, (size_t)c.n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c.w_fixed, w, (size_t)c.n * sizeof(double), cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
     c.forces_valid = false;
     return cuda_check(c, e, "ap_set_weights");
 }
@@ -553,6 +673,7 @@ const char* ap_last_error(const ap_ctx* xc) { return xc ? xc->c.err.c_str() : g_
 void ap_destroy(ap_ctx* xc) {
     if (!xc) return;
     cudaStreamSynchronize(xc->c.stream);
+    drop_step_graph(xc);
     drain_events(xc);
     for (cudaEvent_t e : xc->free_ev) cudaEventDestroy(e);
     free_all(xc->c);

@@ -245,6 +245,19 @@ __device__ __forceinline__ float dot_row2(const float* P, const float* row) {
     return r0 + r1;
 }
 
+// Q[k] += ce * row[k] over a 16-byte aligned shared-memory row (one broadcast load per 4 FMA)
+template <int W>
+__device__ __forceinline__ void axpy_row(float* Q, float ce, const float* row) {
+#pragma unroll
+    for (int k = 0; k < W; k += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(row + k);
+        Q[k] = fmaf(ce, v.x, Q[k]);
+        if (k + 1 < W) Q[k + 1] = fmaf(ce, v.y, Q[k + 1]);
+        if (k + 2 < W) Q[k + 2] = fmaf(ce, v.z, Q[k + 2]);
+        if (k + 3 < W) Q[k + 3] = fmaf(ce, v.w, Q[k + 3]);
+    }
+}
+
 // The two (n1, n2) pairs of a lane and the n3 / n2 contractions are runtime loops; only the
 // Gaunt entries are unrolled (their operands are register-indexed), which keeps the code
 // of all 14 l-triples small enough for the instruction cache.
@@ -295,9 +308,7 @@ __device__ __forceinline__ void nu3_adjoint(const float* As, float* dAs, const A
 #pragma unroll 2
         for (int n3 = 0; n3 < kNmax; ++n3) {
             const float ce = fmaf(s, c2[n3 * 65], c1[n3 * 65]);
-            const float* a3 = As + n3 * kApad + R::B3;
-#pragma unroll
-            for (int m = 0; m < R::W3; ++m) Q[m] = fmaf(ce, a3[m], Q[m]);
+            axpy_row<R::W3>(Q, ce, As + n3 * kApad + R::B3);
         }
 #pragma unroll
         for (int k = 0; k < R::W1; ++k) d1[k] = 0.0f;
@@ -342,9 +353,7 @@ __device__ __forceinline__ void nu3_adjoint(const float* As, float* dAs, const A
 #pragma unroll 2
         for (int n2 = 0; n2 < kNmax; ++n2) {
             const float ce = fmaf(s, C.c3[1][T][n3][n1 * 8 + n2], C.c3[0][T][n3][n1 * 8 + n2]);
-            const float* a2 = As + n2 * kApad + R::B2;
-#pragma unroll
-            for (int m = 0; m < R::W2; ++m) Tm[m] = fmaf(ce, a2[m], Tm[m]);
+            axpy_row<R::W2>(Tm, ce, As + n2 * kApad + R::B2);
         }
         all_y<T>(d3, A1, Tm, std::make_integer_sequence<int, R::N>{});
     }

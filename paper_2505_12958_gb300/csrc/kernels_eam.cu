@@ -4,39 +4,58 @@
 // 1/2 sum_j Phi(r_ij)], rho_i = sum_j zeta(r_ij).  Its negative gradient on atom i is
 //   F_i = sum_j [ (u_i xi'(rho_i) + u_j xi'(rho_j)) zeta'(r_ij) + (u_i + u_j)/2 Phi'(r_ij) ] rhat_ij,
 // evaluated from i's side over the full list, so no atomics are needed and the sum
-// order is fixed.  Two passes: density (rho, xi, u xi' per atom), then forces, per-atom
-// energies and the per-atom virial -1/2 sum_j c_ij r_ij (x) rhat_ij.  The embedding
-// function is evaluated in FP64 (one square root per atom); pair terms are FP32
-// piecewise polynomials from the host tables.
+// order is fixed.  Per step two passes: density (rho, xi, u xi' per atom), then forces.
+// On request a third pass gives accurate per-atom energies and the per-atom virial
+// -1/2 sum_j c_ij r_ij (x) rhat_ij.  The embedding function is evaluated in FP64 (one
+// square root per atom); pair terms are FP32 piecewise polynomials from the host tables.
 #include "ap_internal.h"
 
 namespace ap {
 
 namespace {
 
-__device__ __forceinline__ void poly_eval(const PolyTab& t, float r, float& f, float& df, float zk, float zainv) {
+// interval of r: the bin table gives the interval at the bin start; at most two knots
+// (the W pair potential's 5e-5 A wide interval) can fall inside one bin
+__device__ __forceinline__ int poly_interval(const PolyTab& t, float r) {
     int b = (int)(r * t.bin_inv);
     b = b < kNBin ? b : kNBin - 1;
     int k = t.bin[b];
     k += (k + 1 < t.nint && r >= t.start[k + 1]) ? 1 : 0;
     k += (k + 1 < t.nint && r >= t.start[k + 1]) ? 1 : 0;
     while (k + 1 < t.nint && r >= t.start[k + 1]) ++k;
+    return k;
+}
+
+// screened Coulomb: Z^2/(4 pi eps0 r) phi(r/a), phi = sum of four exponentials
+__device__ __forceinline__ void zbl_eval(float r, float zk, float zainv, float& f, float& df) {
+    const float x = r * zainv;
+    const float e0 = 0.1818f * expf(-3.2f * x), e1 = 0.5099f * expf(-0.9423f * x);
+    const float e2 = 0.2802f * expf(-0.4029f * x), e3 = 0.02817f * expf(-0.2016f * x);
+    const float ph = e0 + e1 + e2 + e3;
+    const float dph = -(3.2f * e0 + 0.9423f * e1 + 0.4029f * e2 + 0.2016f * e3);
+    const float ri = 1.0f / r;
+    f = zk * ph * ri;
+    df = zk * (dph * zainv * ri - ph * ri * ri);
+}
+
+// value (VAL) and/or derivative (DER) of the piecewise polynomial at r; all intervals are
+// cubic except the quintic bridge of a table with the ZBL core (interval 1)
+template <bool VAL, bool DER>
+__device__ __forceinline__ void poly_eval(const PolyTab& t, float r, float& f, float& df, float zk, float zainv) {
+    const int k = poly_interval(t, r);
     if (t.zbl && k == 0) {
-        // screened Coulomb: Z^2/(4 pi eps0 r) phi(r/a), phi = sum of four exponentials
-        float x = r * zainv;
-        float e0 = 0.1818f * expf(-3.2f * x), e1 = 0.5099f * expf(-0.9423f * x);
-        float e2 = 0.2802f * expf(-0.4029f * x), e3 = 0.02817f * expf(-0.2016f * x);
-        float ph = e0 + e1 + e2 + e3;
-        float dph = -(3.2f * e0 + 0.9423f * e1 + 0.4029f * e2 + 0.2016f * e3);
-        float ri = 1.0f / r;
-        f = zk * ph * ri;
-        df = zk * (dph * zainv * ri - ph * ri * ri);
+        zbl_eval(r, zk, zainv, f, df);
         return;
     }
-    float x = r - t.mid[k];
+    const float x = r - t.mid[k];
     const float* c = t.c[k];
-    f = ((((c[5] * x + c[4]) * x + c[3]) * x + c[2]) * x + c[1]) * x + c[0];
-    df = (((5.0f * c[5] * x + 4.0f * c[4]) * x + 3.0f * c[3]) * x + 2.0f * c[2]) * x + c[1];
+    if (t.zbl && k == 1) {
+        if (VAL) f = ((((c[5] * x + c[4]) * x + c[3]) * x + c[2]) * x + c[1]) * x + c[0];
+        if (DER) df = (((5.0f * c[5] * x + 4.0f * c[4]) * x + 3.0f * c[3]) * x + 2.0f * c[2]) * x + c[1];
+    } else {
+        if (VAL) f = ((c[3] * x + c[2]) * x + c[1]) * x + c[0];
+        if (DER) df = (3.0f * c[3] * x + 2.0f * c[2]) * x + c[1];
+    }
 }
 
 __device__ __forceinline__ void stage_tables(EamDev* sm, const EamDev* __restrict__ gm, float4* Ds,
@@ -70,7 +89,7 @@ __global__ void __launch_bounds__(256) k_eam_density(const float4* __restrict__ 
         const float r2 = dx * dx + dy * dy + dz * dz;
         if (r2 < rc2) {
             float f, df;
-            poly_eval(T.rho, sqrtf(r2), f, df, 0.0f, 0.0f);
+            poly_eval<true, false>(T.rho, sqrtf(r2), f, df, 0.0f, 0.0f);
             rho += f;
         }
     };
@@ -104,21 +123,25 @@ __global__ void __launch_bounds__(256) k_eam_density(const float4* __restrict__ 
     e_emb[i] = F;
 }
 
+// per step: EAM forces.  The pair value Phi is needed only for the FP32 estimate of E_i^EAM
+// that the weight-gradient force of transition atoms (0 < w < 1) uses; exact energies and
+// the virial come from the on-request energy pass.
 __global__ void __launch_bounds__(256) k_eam_force(const float4* __restrict__ pos4, const int* __restrict__ nbr,
                                                    const int* __restrict__ nnbr, int n, const EamDev* __restrict__ eam,
                                                    const float4* __restrict__ D, int ncode, const float* __restrict__ uxi,
-                                                   const double* __restrict__ e_emb, float* __restrict__ f,
-                                                   double* __restrict__ e_eam, float* __restrict__ vir) {
+                                                   const double* __restrict__ e_emb, const float* __restrict__ wv,
+                                                   float* __restrict__ f, double* __restrict__ e_eam) {
     __shared__ EamDev T;
     __shared__ float4 Ds[125];
     stage_tables(&T, eam, Ds, D, ncode);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float4 p = pos4[i];
+    const float4 p = pos4[i];
     const float ui = p.w, xi = uxi[i];
+    const float wi = wv[i];
+    const bool want_e = wi > 0.0f && wi < 1.0f;   // the same test as the blend's weight-gradient term
     const float rc2 = T.rc * T.rc, rcr = T.rho.rcut, rcp = T.phi.rcut;
     float fx = 0.f, fy = 0.f, fz = 0.f, eph = 0.f;
-    float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f, v4 = 0.f, v5 = 0.f;
     const int m = nnbr[i];
     auto pair = [&](int e, const float4& q, float xj) {
         const float4 d = Ds[(unsigned)e >> kNbrShift];
@@ -128,15 +151,14 @@ __global__ void __launch_bounds__(256) k_eam_force(const float4* __restrict__ po
         if (r2 >= rc2 || us <= 0.0f) return;   // beyond the cutoff, or both atoms fully ACE
         const float r = sqrtf(r2), ri = 1.0f / r;
         float zf = 0.f, dz_ = 0.f, pf = 0.f, dp = 0.f;
-        if (r < rcr) poly_eval(T.rho, r, zf, dz_, 0.f, 0.f);
-        if (r < rcp) poly_eval(T.phi, r, pf, dp, T.zbl_k, T.zbl_ainv);
-        const float c = (xi + xj) * dz_ + 0.5f * us * dp;
-        const float cr = c * ri;
+        if (r < rcr) poly_eval<false, true>(T.rho, r, zf, dz_, 0.f, 0.f);
+        if (r < rcp) {
+            if (want_e) poly_eval<true, true>(T.phi, r, pf, dp, T.zbl_k, T.zbl_ainv);
+            else poly_eval<false, true>(T.phi, r, pf, dp, T.zbl_k, T.zbl_ainv);
+        }
+        const float cr = ((xi + xj) * dz_ + 0.5f * us * dp) * ri;
         fx += cr * dx; fy += cr * dy; fz += cr * dz;
         eph += pf;
-        const float s = -0.5f * cr;
-        v0 += s * dx * dx; v1 += s * dy * dy; v2 += s * dz * dz;
-        v3 += s * dx * dy; v4 += s * dx * dz; v5 += s * dy * dz;
     };
     int k = 0;
     for (; k + 4 <= m; k += 4) {
@@ -160,8 +182,7 @@ __global__ void __launch_bounds__(256) k_eam_force(const float4* __restrict__ po
         pair(e, pos4[j], uxi[j]);
     }
     f[i] = fx; f[n + i] = fy; f[2 * n + i] = fz;
-    e_eam[i] = ui > 0.0f ? e_emb[i] + 0.5 * (double)eph : 0.0;
-    vir[i] = v0; vir[n + i] = v1; vir[2 * n + i] = v2; vir[3 * n + i] = v3; vir[4 * n + i] = v4; vir[5 * n + i] = v5;
+    if (want_e) e_eam[i] = e_emb[i] + 0.5 * (double)eph;
 }
 
 // ---------------------------------------------------------------------------------
@@ -215,7 +236,8 @@ __global__ void __launch_bounds__(256) k_eam_energy(const float4* __restrict__ p
                                                     const int* __restrict__ nbr, const int* __restrict__ nnbr, int n,
                                                     const EamDev* __restrict__ eam, const float4* __restrict__ D,
                                                     const float4* __restrict__ Dlo, int ncode,
-                                                    double* __restrict__ e_eam) {
+                                                    const float* __restrict__ uxi, double* __restrict__ e_eam,
+                                                    float* __restrict__ vir) {
     __shared__ EamDev T;
     __shared__ float4 Ds[125];
     __shared__ float4 Dl[125];
@@ -225,9 +247,11 @@ __global__ void __launch_bounds__(256) k_eam_energy(const float4* __restrict__ p
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float4 p = pos4[i], pl = pos_lo[i];
-    if (p.w <= 0.0f) { e_eam[i] = 0.0; return; }
+    const float ui = p.w, xi = uxi[i];
+    const bool own = ui > 0.0f;               // the atom has an EAM energy share
     const float rc2 = T.rc * T.rc, rcr = T.rho.rcut, rcp = T.phi.rcut;
     float rh = 0.f, rl = 0.f, ph = 0.f, pl_ = 0.f;
+    float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f, v4 = 0.f, v5 = 0.f;
     const int m = nnbr[i];
     for (int k = 0; k < m; ++k) {
         const int e = nbr[(size_t)k * n + i];
@@ -257,12 +281,26 @@ __global__ void __launch_bounds__(256) k_eam_energy(const float4* __restrict__ p
             r2l = __fadd_rn(r2l, fmaf(2.0f * d[c], dlo[c], sqe));
         }
         if (r2h >= rc2) continue;
+        const float us = ui + q.w;
+        if (us <= 0.0f) continue;
         const float rf = sqrtf(r2h);
+        {
+            // virial -1/2 c_ij r_ij (x) rhat_ij with the bond coefficient of the force pass
+            float zf, dz_ = 0.f, pf, dp = 0.f;
+            if (rf < rcr) poly_eval<false, true>(T.rho, rf, zf, dz_, 0.f, 0.f);
+            if (rf < rcp) poly_eval<false, true>(T.phi, rf, pf, dp, T.zbl_k, T.zbl_ainv);
+            const float sc = -0.5f * ((xi + uxi[j]) * dz_ + 0.5f * us * dp) / rf;
+            v0 += sc * d[0] * d[0]; v1 += sc * d[1] * d[1]; v2 += sc * d[2] * d[2];
+            v3 += sc * d[0] * d[1]; v4 += sc * d[0] * d[2]; v5 += sc * d[1] * d[2];
+        }
+        if (!own) continue;
         const float pp = __fmul_rn(rf, rf), pe = fmaf(rf, rf, -pp);
         const float tl = __fdiv_rn(__fadd_rn(__fsub_rn(__fsub_rn(r2h, pp), pe), r2l), 2.0f * rf);
         if (rf < rcr) poly_acc_df(T.rho, rf, tl, 0.f, 0.f, rh, rl);
         if (rf < rcp) poly_acc_df(T.phi, rf, tl, T.zbl_k, T.zbl_ainv, ph, pl_);
     }
+    vir[i] = v0; vir[n + i] = v1; vir[2 * n + i] = v2; vir[3 * n + i] = v3; vir[4 * n + i] = v4; vir[5 * n + i] = v5;
+    if (!own) { e_eam[i] = 0.0; return; }
     const double rho = (double)rh + (double)rl;
     double F = T.F_dxi;
     if (rho > 0.0) F += T.F_a1 * sqrt(rho) + T.F_a2 * rho * rho;
@@ -273,7 +311,7 @@ __global__ void __launch_bounds__(256) k_eam_energy(const float4* __restrict__ p
 
 int launch_eam_energy(Ctx& c, cudaStream_t s) {
     k_eam_energy<<<(c.n + 255) / 256, 256, 0, s>>>(c.pos4, c.pos_lo, c.nbr, c.nnbr, c.n, c.eam_d, c.D, c.Dlo,
-                                                   c.grid.ncode, c.e_eam);
+                                                   c.grid.ncode, c.uxi, c.e_eam, c.vir_eam);
     return 1;
 }
 
@@ -285,7 +323,7 @@ int launch_eam_density(Ctx& c, cudaStream_t s) {
 
 int launch_eam_force(Ctx& c, cudaStream_t s) {
     k_eam_force<<<(c.n + 255) / 256, 256, 0, s>>>(c.pos4, c.nbr, c.nnbr, c.n, c.eam_d, c.D, c.grid.ncode, c.uxi,
-                                                 c.e_emb, c.f, c.e_eam, c.vir_eam);
+                                                 c.e_emb, c.w, c.f, c.e_eam);
     return 1;
 }
 

@@ -97,3 +97,93 @@ def strained_w_cell(ncell, seed, strain=0.02, vacancy=0.01, sigma=0.1, a=3.165):
     h = (np.diag([ncell * a] * 3) @ F.T).ravel()
     box = {"h": h, "origin": np.zeros(3), "periodic": (1, 1, 1)}
     return _bundle("W", x, np.zeros_like(x), box, np.zeros(len(x), dtype=np.uint8), None, None, None)
+
+
+# ---------------------------------------------------------------------------------------
+# serving workload: independent structures of uneven size arriving as a Poisson stream
+# ---------------------------------------------------------------------------------------
+_SPEC = {"Cu": ("fcc", 3.615), "W": ("bcc", 3.165)}
+
+
+def _cells_for(n_target, atoms_per_cell, aspect=(1, 1, 1)):
+    k = max(1.0, (n_target / atoms_per_cell / (aspect[0] * aspect[1] * aspect[2])) ** (1.0 / 3.0))
+    return [max(2, int(round(k * a))) for a in aspect]
+
+
+def _oriented_110(species, nx, ny, nz):
+    """Orthorhombic cell with x || [1-10], y || [001], z || [110] (periodic lengths exact)."""
+    kind, a = _SPEC[species]
+    lat = fcc if kind == "fcc" else bcc
+    px = a / np.sqrt(2) if kind == "fcc" else a * np.sqrt(2)
+    pz = a / np.sqrt(2) if kind == "fcc" else a * np.sqrt(2) / 2
+    Lx, Ly, Lz = nx * px, ny * a, nz * pz
+    m = int(np.ceil(max(Lx, Ly, Lz) / a)) + 2
+    x = lat(a, 2 * m, 2 * m, 2 * m) - m * a
+    ex = np.array([1.0, -1.0, 0.0]) / np.sqrt(2)
+    ey = np.array([0.0, 0.0, 1.0])
+    ez = np.array([1.0, 1.0, 0.0]) / np.sqrt(2)
+    y = np.stack([x @ ex, x @ ey, x @ ez], axis=1)
+    eps = 1e-6
+    keep = (y[:, 0] >= -eps) & (y[:, 0] < Lx - eps) & (y[:, 1] >= -eps) & (y[:, 1] < Ly - eps) & \
+           (y[:, 2] >= -eps) & (y[:, 2] < Lz - eps)
+    return y[keep], (Lx, Ly, Lz)
+
+
+def serving_request(rid, rng):
+    """One request: structure, weight region, steps.  Sizes log-uniform 64..50,000 atoms."""
+    species = "Cu" if rng.random() < 0.5 else "W"
+    kind, a = _SPEC[species]
+    per_cell = 4 if kind == "fcc" else 2
+    lat = fcc if kind == "fcc" else bcc
+    n_target = int(np.exp(rng.uniform(np.log(64), np.log(50000))))
+    geom = ["bulk", "vacancy", "surface001", "surface110", "indented"][rng.integers(5)]
+    vac = 10.0
+    if geom in ("bulk", "vacancy"):
+        c = _cells_for(n_target, per_cell)
+        x = lat(a, *c)
+        L = np.array(c, dtype=float) * a
+        box = orthorhombic_box(*L, (1, 1, 1))
+        if geom == "vacancy":
+            x = np.delete(x, rng.integers(len(x)), axis=0)
+    elif geom == "surface110":
+        px = a / np.sqrt(2) if kind == "fcc" else a * np.sqrt(2)
+        pz = a / np.sqrt(2) if kind == "fcc" else a * np.sqrt(2) / 2
+        k = max(2, int(round((n_target / (per_cell * (px / a) * (pz / a) * 2)) ** (1 / 3))))
+        x, (Lx, Ly, Lz) = _oriented_110(species, k, k, 2 * k)
+        box = orthorhombic_box(Lx, Ly, Lz + 2 * vac, (1, 1, 0), origin=(0.0, 0.0, -vac))
+    else:
+        c = _cells_for(n_target, per_cell, (1, 1, 1))
+        x = lat(a, *c)
+        L = np.array(c, dtype=float) * a
+        box = orthorhombic_box(L[0], L[1], L[2] + 2 * vac, (1, 1, 0), origin=(0.0, 0.0, -vac))
+        if geom == "indented":
+            z_top = x[:, 2].max()
+            tip = np.array([L[0] / 2, L[1] / 2, z_top + 0.6 * L[0]])
+            x = x[np.linalg.norm(x - tip, axis=1) > 0.6 * L[0] + 0.5 * a]
+    T = rng.uniform(0.0, 1000.0)
+    mass = float(eam_potential(species)["mass_amu"])
+    x = x + rng.normal(0.0, 0.1 * np.sqrt(T / 1000.0), size=x.shape)
+    v = maxwell_velocities(len(x), T, mass, int(rng.integers(1 << 30)))
+    h = np.asarray(box["h"]).reshape(3, 3)
+    center = box["origin"] + 0.5 * np.diag(h)
+    if box["periodic"][2] == 0:
+        center[2] = x[:, 2].max()
+    frac = rng.uniform(0.0, 1.0)
+    r_in = frac ** (1.0 / 3.0) * 0.5 * float(np.linalg.norm(np.diag(h)[:2] if box["periodic"][2] == 0 else np.diag(h)))
+    region = {"kind": "sphere", "center": tuple(center), "r_in": r_in, "r_sw": 2.0}
+    req = _bundle(species, x, v, box, np.zeros(len(x), dtype=np.uint8), region, None, None)
+    req.update({"id": rid, "geometry": geom, "temperature": T, "ace_fraction_target": frac,
+                "n_steps": int(rng.integers(1, 101))})
+    return req
+
+
+def serving_requests(n, seed=1005, rate_per_s=50.0):
+    """n requests with Poisson arrival times (seconds from 0) at rate_per_s."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate_per_s, size=n))
+    out = []
+    for k in range(n):
+        r = serving_request(k, rng)
+        r["arrival_s"] = float(t[k])
+        out.append(r)
+    return out

@@ -1,0 +1,72 @@
+"""The autograd form: backward of the AP energy against the oracle's analytic forces and
+virial and against central finite differences, on strained triclinic W cells with
+vacancies and noise (the differentiation workload), for FP64 and FP32 inputs.
+
+Finite differences of the library energy are noise-limited: each energy carries FP32
+rounding of ~1e-7 eV per affected atom, so h = 1e-3 A gives ~5e-4 eV/A of noise (h = 1e-4 A
+would give ~5e-3); the analytic checks against the oracle hold the 1e-4 eV/A bar.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def apl():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("needs a CUDA device")
+    import paper_2505_12958_gb300 as ap
+    ap.build()
+    return ap
+
+
+@pytest.mark.parametrize("ncell,seed,dtype", [(4, 1, "float64"), (5, 2, "float64"), (6, 3, "float32")])
+def test_backward_matches_oracle_and_finite_differences(apl, orc, ncell, seed, dtype):
+    import torch
+    from paper_2505_12958_gb300.autograd import ap_energy
+    c = synth.configs.strained_w_cell(ncell, seed=seed)
+    reg = {"kind": "const", "w": 0.5}
+    ref = orc.evaluate(c["x"], c["box"], c["eam"], c["ace"], reg)
+    td = getattr(torch, dtype)
+    n = len(c["x"])
+    with apl.APContext(c["eam"], c["ace"], c["box"], c["x"], None, None, reg, None, None, c["mass"]) as ctx:
+        x = torch.tensor(c["x"], dtype=td, device="cuda", requires_grad=True)
+        eps = torch.zeros((3, 3), dtype=td, device="cuda", requires_grad=True)
+        E = ap_energy(x, eps, ctx, c["box"])
+        E.backward()
+        gx = x.grad.double().cpu().numpy()
+        gs = eps.grad.double().cpu().numpy()
+        # analytic: -dE/dx = oracle forces; -dE/deps = oracle virial
+        xr = x.detach().double().cpu().numpy() if dtype == "float32" else c["x"]
+        ref = orc.evaluate(xr, c["box"], c["eam"], c["ace"], reg)
+        assert np.abs(-gx - ref["forces"]).max() <= 1e-4
+        assert abs(E.item() - ref["e_total"]) / n <= (1e-6 if dtype == "float64" else 1e-5)
+        v = ref["virial"]
+        W = np.array([[v[0], v[3], v[4]], [v[3], v[1], v[5]], [v[4], v[5], v[2]]])
+        assert np.abs(-gs - W).max() <= 2e-5 * np.abs(W).max() + 1e-5 * n
+        # central differences of the library energy (taken in FP64: an FP32 total energy of
+        # ~5e3 eV has a resolution of ~5e-4 eV)
+        h = 1e-3
+        x64 = x.detach().double()
+        e64 = eps.detach().double()
+        rng = np.random.default_rng(seed)
+        for i in rng.choice(n, size=3, replace=False):
+            for k in range(3):
+                xp = x64.clone(); xp[i, k] += h
+                xm = x64.clone(); xm[i, k] -= h
+                e_p = ap_energy(xp, e64, ctx, c["box"]).item()
+                e_m = ap_energy(xm, e64, ctx, c["box"]).item()
+                assert abs((e_p - e_m) / (2 * h) - gx[i, k]) <= 2e-3
+        hs = 1e-5
+        for a, b in ((0, 0), (1, 2)):
+            d = torch.zeros((3, 3), dtype=torch.float64, device="cuda")
+            d[a, b] = d[b, a] = hs
+            e_p = ap_energy(x64, d, ctx, c["box"]).item()
+            e_m = ap_energy(x64, -d, ctx, c["box"]).item()
+            fd = (e_p - e_m) / (2 * hs)
+            an = gs[a, b] + (gs[b, a] if a != b else 0.0)
+            assert abs(fd - an) <= 1e-3 * max(1.0, abs(an)) + 0.05
