@@ -21,6 +21,8 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the serving run keeps dozens of streams busy; let them map to separate hardware queues
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 import numpy as np  # noqa: E402
 
@@ -213,6 +215,44 @@ def ace_kernel_roofline(prof, n_steps, c, pk, peak_src, ctx_atoms_in_rc):
             "algorithmic_flops_per_launch": int(flops), "avg_launch_ms": avg_s * 1000.0}
 
 
+def serving_bench(torch, n_req, seed=1005, load=0.7, chunk=8, max_active=64):
+    """Continuous-batching server on a Poisson stream of uneven Cu/W requests.
+
+    The saturated throughput comes from a closed-loop run (all requests waiting at t = 0);
+    the open-loop rate is then `load` x that throughput / mean request work (atom-steps),
+    and latency (arrival to final state, forces and energy on the host) is taken there."""
+    from paper_2505_12958_gb300.serve import Server, percentile_ms
+    t = time.perf_counter()
+    reqs = synth.configs.serving_requests(n_req, seed=seed, rate_per_s=1.0)
+    gen_s = time.perf_counter() - t
+    base = [r["arrival_s"] for r in reqs]
+    work = np.array([len(r["x"]) * r["n_steps"] for r in reqs], dtype=np.float64)
+    Server(keep_arrays=False, chunk=chunk, max_active=max_active).run(reqs[:8], realtime=False)   # warm-up
+    torch.cuda.synchronize()
+    sat = Server(keep_arrays=False, chunk=chunk, max_active=max_active)
+    res = sat.run(reqs, realtime=False)
+    makespan = max(r.done_s for r in res)
+    sat_rate = work.sum() / makespan
+    rate = load * sat_rate / work.mean()
+    for r, b in zip(reqs, base):
+        r["arrival_s"] = b / rate
+    srv = Server(keep_arrays=False, chunk=chunk, max_active=max_active)
+    res = srv.run(reqs, realtime=True)
+    span = max(r.done_s for r in res) - min(r.arrival_s for r in res)
+    lat = np.array([r.latency_s for r in res])
+    return {"requests": n_req, "seed": seed, "mean_atoms": float(np.mean([len(r["x"]) for r in reqs])),
+            "mean_steps": float(np.mean([r["n_steps"] for r in reqs])),
+            "saturated_atom_steps_per_s": sat_rate, "saturated_requests_per_s": n_req / makespan,
+            "load": load, "arrival_rate_per_s": rate, "atom_steps_per_s": work.sum() / span,
+            "p50_latency_ms": percentile_ms(res, 50), "p99_latency_ms": percentile_ms(res, 99),
+            "mean_latency_ms": float(lat.mean() * 1e3), "max_latency_ms": float(lat.max() * 1e3),
+            "peak_active": srv.peak_active, "chunk_steps": chunk, "max_active": max_active,
+            "generation_s": gen_s,
+            "workload": "Cu/W 50/50; bulk, vacancy, (001) and (110) surfaces, indented; 64-50,000 atoms "
+                        "log-uniform; 0-1000 K; ACE fraction U(0,1) via the sphere radius; 1-100 steps; "
+                        "Poisson arrivals; latency = arrival to final state/forces/energy on the host"}
+
+
 def neighbors_in_ace_cutoff(c):
     """Neighbour counts within the ACE cutoff of the atoms with w > 0 (host, for the flop count)."""
     from scipy.spatial import cKDTree
@@ -232,14 +272,25 @@ def neighbors_in_ace_cutoff(c):
 def main():
     ap_ = argparse.ArgumentParser()
     ap_.add_argument("--gpus", type=int, default=1)
-    ap_.add_argument("--steps", type=int, default=200)
+    ap_.add_argument("--steps", type=int, default=1000)
     ap_.add_argument("--warmup", type=int, default=10)
     ap_.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap_.add_argument("--no-cpu-baseline", action="store_true")
     ap_.add_argument("--variants", default="ace,eam", help="extra single-potential runs (comma list or 'none')")
+    ap_.add_argument("--serve-requests", type=int, default=300,
+                     help="requests in the serving run reported beside the metric (0: skip)")
+    ap_.add_argument("--mode", default="ap", choices=["ap", "serve"],
+                     help="ap: the metric line; serve: only the serving run, as its own line")
     args = ap_.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "serve":
+        import torch
+        import paper_2505_12958_gb300 as ap
+        ap.build()
+        out = serving_bench(torch, args.serve_requests)
+        print(json.dumps({"mode": "serve", **out}, default=_jsonable), flush=True)
+        return
 
     import torch
     import paper_2505_12958_gb300 as ap
@@ -315,6 +366,8 @@ def main():
                                  "ms_per_step": sum(msv) / kk}
         cv.close()
 
+    serving = serving_bench(torch, args.serve_requests) if args.serve_requests > 0 else None
+
     if rank != 0:
         return
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -325,6 +378,8 @@ def main():
             "p50_ms_per_step": float(np.percentile(ms, 50)), "p99_ms_per_step": float(np.percentile(ms, 99)),
             "stage_ms_per_step": stage_ms, "gpu_launches": launches, "clocks": clocks, "e2e": e2e, "roofline": roof,
             "wall_s_timed_region": wall}
+    if serving is not None:
+        line["serving"] = serving
     line.update(extra)
     if "ace_only" in extra:
         line["ap_vs_ace_speedup"] = value / extra["ace_only"]["value"]

@@ -175,6 +175,12 @@ ap_status ap_step(ap_ctx* ctx, int n_steps, double dt_fs, void* stream);
  * Asynchronous; returns the first error. */
 ap_status ap_step_batch(ap_ctx* const* ctxs, const int* n_steps, int n_ctx, double dt_fs);
 
+/* Serving form of ap_compute_forces: one AP force evaluation of the library-owned
+ * positions of each of n_ctx contexts, each on its own context's stream.  Arguments are
+ * checked before anything is launched (AP_ERR_ARG for a NULL entry).  Asynchronous;
+ * returns the first error. */
+ap_status ap_compute_forces_batch(ap_ctx* const* ctxs, int n_ctx);
+
 /* Totals of the last force evaluation; d_e_atom (device, n FP64, nullable) receives
  * the per-atom energies E_i + V_ind(r_i).  Synchronises; returns sticky device errors. */
 ap_status ap_energy(ap_ctx* ctx, ap_report* out, double* d_e_atom);
@@ -211,8 +217,14 @@ ap_status ap_profile_read(ap_ctx* ctx, double* ms, long long* launches);
 long long ap_launch_count(const ap_ctx* ctx);
 /* Neighbour-list capacity per atom and the number of list rebuilds so far. */
 ap_status ap_neighbor_info(ap_ctx* ctx, int* capacity, long long* rebuilds);
-/* Device bytes a context of n atoms needs (an upper estimate). */
+/* Device bytes a context of n atoms needs: an upper estimate for structures of metallic
+ * density (at most 0.1 atoms / A^3 inside the list sphere) whose binning grid has at most
+ * one cell per atom.  ace_fraction is accepted for callers that know it; the ACE arrays
+ * are sized for every atom because the region may move.  No device access. */
 size_t ap_footprint_bytes(const ap_potential* pot, int n_atoms, double ace_fraction);
+/* Device bytes ctx holds right now (its stream-ordered allocations, including any
+ * capacity growth); 0 for NULL. */
+size_t ap_memory_bytes(const ap_ctx* ctx);
 /* Text of the last error of ctx (or of the last failed ap_init when ctx is NULL). */
 const char* ap_last_error(const ap_ctx* ctx);
 void ap_destroy(ap_ctx* ctx);

@@ -548,8 +548,12 @@ static void region_weight(const or_region* reg, int i, const or_system* sys, con
     double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     if (r < reg->r_in) { *w = 1.0; return; }
     if (r >= reg->r_in + reg->r_sw) { *w = 0.0; return; }
+    /* S = (1 + cos a)/2, written as cos^2(a/2): the same function, but positive for every
+     * r < r_in + r_sw in floating point, so that the compaction rule w > 0 selects exactly
+     * the atoms inside the outer radius */
     double a = M_PI * (r - reg->r_in) / reg->r_sw;
-    *w = 0.5 * (1.0 + cos(a));
+    double ch = cos(0.5 * a);
+    *w = ch * ch;
     double ds = -0.5 * M_PI / reg->r_sw * sin(a);
     for (int k = 0; k < 3; ++k) gw[k] = ds * d[k] / r;
 }

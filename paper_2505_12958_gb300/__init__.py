@@ -20,7 +20,7 @@ from . import _capi
 from ._capi import PRECISION, REGION, STAGES, STATUS
 
 __all__ = ["APContext", "APError", "build", "PRECISION", "STAGES", "potential_struct", "gaunt_real",
-           "eam_table_eval", "step_batch"]
+           "eam_table_eval", "step_batch", "compute_forces_batch", "footprint_bytes"]
 
 
 class APError(RuntimeError):
@@ -229,6 +229,10 @@ class APContext:
         self._chk(self._L.ap_profile_read(self._h, ms, nl))
         return {s: (ms[k], nl[k]) for k, s in enumerate(STAGES)}
 
+    def memory_bytes(self):
+        """Device bytes this context holds (ap_memory_bytes)."""
+        return int(self._L.ap_memory_bytes(self._h))
+
     @property
     def launch_count(self):
         return int(self._L.ap_launch_count(self._h))
@@ -267,6 +271,24 @@ def step_batch(ctxs, n_steps, dt):
     if st != 0:
         msgs = "; ".join(L.ap_last_error(c._h).decode() for c in ctxs)
         raise APError(st, msgs)
+
+
+def compute_forces_batch(ctxs):
+    """One force evaluation for each context, each on its own stream (ap_compute_forces_batch)."""
+    L = _capi.lib()
+    k = len(ctxs)
+    hs = (C.c_void_p * k)(*[c._h.value for c in ctxs])
+    st = L.ap_compute_forces_batch(hs, k)
+    if st != 0:
+        raise APError(st, "; ".join(L.ap_last_error(c._h).decode() for c in ctxs))
+
+
+def footprint_bytes(eam, ace, n_atoms, mass=1.0, skin=1.0, ace_fraction=1.0):
+    """Upper estimate of the device bytes a context of n_atoms needs (ap_footprint_bytes)."""
+    pot, keep = potential_struct(eam, ace, mass, skin)
+    nb = int(_capi.lib().ap_footprint_bytes(C.byref(pot), int(n_atoms), float(ace_fraction)))
+    del keep
+    return nb
 
 
 def gaunt_real(l1, m1, l2, m2, l3, m3):

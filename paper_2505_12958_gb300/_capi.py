@@ -67,6 +67,8 @@ def lib():
         "ap_compute_forces_host": (I, [VP, PD, PF, PD, VP]),
         "ap_step": (I, [VP, I, D, VP]),
         "ap_step_batch": (I, [C.POINTER(VP), PI, I, D]),
+        "ap_compute_forces_batch": (I, [C.POINTER(VP), I]),
+        "ap_memory_bytes": (C.c_size_t, [VP]),
         "ap_energy": (I, [VP, P(Report), VP]),
         "ap_check": (I, [VP]),
         "ap_get_state": (I, [VP, PD, PD, PD]),

@@ -141,6 +141,7 @@ struct Ctx {
     int* h_flags = nullptr;                              // pinned
     double* h_totals = nullptr;                          // pinned
     long long launches = 0, rebuilds = 0, step = 0;
+    size_t dev_bytes = 0;                                // device bytes this context holds
     double t = 0.0;
     bool forces_valid = false;
     std::string err;

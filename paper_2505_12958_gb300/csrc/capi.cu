@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -161,7 +162,35 @@ ap_status dalloc(ap::Ctx& c, T** p, size_t count) {
     if (count == 0) count = 1;
     cudaError_t e = cudaMallocAsync((void**)p, count * sizeof(T), c.stream);
     if (e != cudaSuccess) { *p = nullptr; return cuda_check(c, e, "cudaMallocAsync"); }
+    c.dev_bytes += count * sizeof(T);
     return AP_OK;
+}
+
+// Pinned host slots for each context's flag and total read-backs.  cudaFreeHost waits for
+// the whole device, which would stall every other context's stream whenever one context
+// is destroyed, so slots are recycled for the lifetime of the process instead.
+constexpr size_t kPinnedSlot = 256;                     // 16 doubles of totals + flags
+static_assert(16 * sizeof(double) + ap::kFlagCount * sizeof(int) <= kPinnedSlot, "pinned slot");
+std::mutex g_pinned_mu;
+std::vector<char*> g_pinned_free;
+
+char* pinned_take() {
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    if (g_pinned_free.empty()) {
+        char* block = nullptr;
+        const int per = 256;
+        if (cudaMallocHost((void**)&block, kPinnedSlot * per) != cudaSuccess) return nullptr;
+        for (int k = per - 1; k >= 0; --k) g_pinned_free.push_back(block + kPinnedSlot * k);
+    }
+    char* p = g_pinned_free.back();
+    g_pinned_free.pop_back();
+    return p;
+}
+
+void pinned_give(char* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    g_pinned_free.push_back(p);
 }
 
 void free_all(ap::Ctx& c) {
@@ -172,8 +201,10 @@ void free_all(ap::Ctx& c) {
     for (void* p : ps)
         if (p) cudaFreeAsync(p, c.stream);
     cudaStreamSynchronize(c.stream);
-    if (c.h_flags) cudaFreeHost(c.h_flags);
-    if (c.h_totals) cudaFreeHost(c.h_totals);
+    pinned_give((char*)c.h_totals);
+    c.h_totals = nullptr;
+    c.h_flags = nullptr;
+    c.dev_bytes = 0;
     delete c.ace_h;
 }
 
@@ -223,6 +254,7 @@ ap_status read_flags(ap::Ctx& c, cudaStream_t s) {
             int* nb = nullptr;
             if (cudaMallocAsync((void**)&nb, (size_t)cap * c.n * sizeof(int), c.stream) == cudaSuccess) {
                 cudaFreeAsync(c.nbr, c.stream);
+                c.dev_bytes += ((size_t)cap - (size_t)c.cap) * c.n * sizeof(int);
                 c.nbr = nb;
                 c.cap = cap;
                 c.layout_gen += 1;
@@ -245,7 +277,7 @@ extern "C" {
 int ap_version(void) { return AP_API_VERSION; }
 
 size_t ap_footprint_bytes(const ap_potential* pot, int n_atoms, double ace_fraction) {
-    (void)ace_fraction;
+    (void)ace_fraction;   // the ACE arrays are sized for every atom (the region moves)
     double rl = 6.5;
     if (pot) {
         double rc = 0.0;
@@ -253,11 +285,21 @@ size_t ap_footprint_bytes(const ap_potential* pot, int n_atoms, double ace_fract
         rc = std::max(rc, pot->ace_rc);
         rl = rc + (pot->skin > 0 ? pot->skin : 1.0);
     }
-    // neighbour capacity at a metallic density of 0.09 atoms / A^3, with margin
-    double cap = 1.3 * 4.18879 * rl * rl * rl * 0.09 + 16;
-    size_t per_atom = (size_t)(cap * 4) + 3 * 8 * 3 + 16 + 3 * 4 + 4 * 3 + 8 * 3 + 4 * 12 + 3 * 8 + 4 * 5 + 16;
-    return (size_t)n_atoms * per_atom + sizeof(ap::AceDev) + sizeof(ap::EamDev) + (8u << 20);
+    // neighbour capacity: the list sphere at 0.1 atoms / A^3 (denser than any metal here),
+    // with the 25 % margin and rounding the context applies
+    const double need = 4.18879 * rl * rl * rl * 0.1;
+    const size_t cap = (size_t)(need * 1.25 + 8 + 4);
+    // per-atom arrays allocated by ap_init (and the host-transfer staging buffers)
+    const size_t per_atom = 16 + 3 * 8 * 3 + 3 * 4 + 16 + 4 + 4 + 8 + 8 + 4 +
+                            2 * sizeof(float) * ap::kNLM * ap::kNmax + 2 * 6 * 4 + 3 * 8 + 1 + 8 +
+                            4 + 4 + 4 + 4 + 8 + 3 * 8 + 3 * 4 + cap * 4;
+    const size_t cells = 2 * sizeof(int) * ((size_t)n_atoms + 1);   // cell count/start (<= 1 per atom)
+    const size_t nred = (size_t)(n_atoms + ap::kRedBlock - 1) / ap::kRedBlock + 1;
+    return (size_t)n_atoms * per_atom + cells + nred * 10 * 8 + 2 * 125 * 16 + sizeof(ap::AceDev) +
+           sizeof(ap::EamDev) + (1u << 16);
 }
+
+size_t ap_memory_bytes(const ap_ctx* xc) { return xc ? xc->c.dev_bytes : 0; }
 
 ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* region, const ap_indenter* ind,
                   int n, const double* pos, const double* vel, const unsigned char* fixed, void* stream,
@@ -290,12 +332,16 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
     if (!c.ace_h) { c.err = "host allocation"; return fail(AP_ERR_OOM); }
     if (ap::build_ace_tables(*pot, *c.ace_h, err)) { c.err = err; return fail(AP_ERR_ARG); }
     c.ace_c1_0 = pot->ace_c1_0;
-    static int gaunt_done_dev = -1;
-    if (gaunt_done_dev != c.dev) {
-        std::vector<float> g(ap::kNG);
-        if (ap::gaunt_values(g.data(), err)) { c.err = err; return fail(AP_ERR_ARG); }
-        ap::upload_gaunt(g.data());
-        gaunt_done_dev = c.dev;
+    {
+        static std::mutex mu;
+        static std::vector<int> done;
+        std::lock_guard<std::mutex> lk(mu);
+        if (std::find(done.begin(), done.end(), c.dev) == done.end()) {
+            std::vector<float> g(ap::kNG);
+            if (ap::gaunt_values(g.data(), err)) { c.err = err; return fail(AP_ERR_ARG); }
+            ap::upload_gaunt(g.data());
+            done.push_back(c.dev);
+        }
     }
     c.rc_eam = c.eam_h.rc;
     c.rc_ace = pot->ace_rc;
@@ -344,8 +390,10 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
         (st = dalloc(c, &c.totals, 16)) || (st = dalloc(c, &c.e_atom, N)))
         return fail(st);
     c.ncell_cap = c.grid.ncell;
-    if (cudaMallocHost((void**)&c.h_flags, sizeof(int) * ap::kFlagCount) != cudaSuccess ||
-        cudaMallocHost((void**)&c.h_totals, sizeof(double) * 16) != cudaSuccess) {
+    if (char* slot = pinned_take()) {
+        c.h_totals = (double*)slot;
+        c.h_flags = (int*)(slot + 16 * sizeof(double));
+    } else {
         c.err = "pinned host allocation";
         return fail(AP_ERR_OOM);
     }
@@ -489,11 +537,24 @@ ap_status ap_step(ap_ctx* xc, int n_steps, double dt, void* stream) {
 }
 
 ap_status ap_step_batch(ap_ctx* const* ctxs, const int* n_steps, int n_ctx, double dt) {
-    if (!ctxs || !n_steps || n_ctx < 0) return AP_ERR_ARG;
+    if (!ctxs || !n_steps || n_ctx < 0 || !(dt > 0.0)) return AP_ERR_ARG;
+    for (int k = 0; k < n_ctx; ++k)
+        if (!ctxs[k] || n_steps[k] < 0) return AP_ERR_ARG;
     ap_status first = AP_OK;
     for (int k = 0; k < n_ctx; ++k) {
-        if (!ctxs[k]) return AP_ERR_ARG;
         ap_status st = ap_step(ctxs[k], n_steps[k], dt, nullptr);
+        if (st != AP_OK && first == AP_OK) first = st;
+    }
+    return first;
+}
+
+ap_status ap_compute_forces_batch(ap_ctx* const* ctxs, int n_ctx) {
+    if (!ctxs || n_ctx < 0) return AP_ERR_ARG;
+    for (int k = 0; k < n_ctx; ++k)
+        if (!ctxs[k]) return AP_ERR_ARG;
+    ap_status first = AP_OK;
+    for (int k = 0; k < n_ctx; ++k) {
+        ap_status st = ap_compute_forces(ctxs[k], nullptr, nullptr, nullptr);
         if (st != AP_OK && first == AP_OK) first = st;
     }
     return first;
@@ -587,6 +648,7 @@ ap_status ap_set_box(ap_ctx* xc, const ap_box* box) {
         }
         cudaFreeAsync(c.cell_count, c.stream);
         cudaFreeAsync(c.cell_start, c.stream);
+        c.dev_bytes += 2 * ((size_t)c.grid.ncell - (size_t)c.ncell_cap) * sizeof(int);
         c.cell_count = cc;
         c.cell_start = cs;
         c.ncell_cap = c.grid.ncell;

@@ -1,8 +1,9 @@
 // geom.cuh -- distances to the fixed-zone centre and to the indenter, and the weight switch.
 //
 // FP64 is kept to the few operations whose rounding would show (the difference of absolute
-// coordinates, its square, and d^2 - r_in^2); the switch itself is evaluated in FP32 from an
-// argument formed as (d^2 - r_in^2) / (d + r_in), so w carries FP32 relative precision.
+// coordinates, its square, and the distances to the two shell radii); the switch itself is
+// evaluated in FP32 from arguments formed as (d^2 - r^2) / (d + r), so w and 1 - w both carry
+// FP32 relative precision.
 #pragma once
 
 #include "ap_internal.h"
@@ -25,19 +26,22 @@ __device__ __forceinline__ void min_image_vec(const GridDev& g, double* d) {
         }
 }
 
-// cosine switch S(d) = 1 (d < r_in), (1 + cos(pi (d - r_in)/r_sw))/2, 0 (d >= r_in + r_sw),
-// from d2 = d^2; *dS receives dS/dd (0 outside the shell)
-__device__ __forceinline__ float switch_weight(double d2, double r_in, double r_sw, float* dS) {
+// cosine switch S(d) = 1 (d < r_in), (1 + cos(pi a))/2 with a = (d - r_in)/r_sw, 0 (d >= r_in +
+// r_sw), from d2 = d^2.  S is evaluated as cos^2(pi a/2) = sin^2(pi b/2), b = (r_in + r_sw - d)/r_sw,
+// and 1 - S as sin^2(pi a/2): both keep FP32 relative precision at their small ends, so S > 0
+// for every d < r_in + r_sw, the compaction rule.  *u receives 1 - S, *dS receives dS/dd.
+__device__ __forceinline__ float switch_weight(double d2, double r_in, double r_sw, float* u, float* dS) {
     *dS = 0.0f;
-    if (d2 < r_in * r_in) return 1.0f;
+    if (d2 < r_in * r_in) { *u = 0.0f; return 1.0f; }
     const double ro = r_in + r_sw;
-    if (d2 >= ro * ro) return 0.0f;
-    const float dist = sqrtf((float)d2);
-    const float x = (float)((d2 - r_in * r_in) / ((double)dist + r_in) / r_sw);   // (d - r_in)/r_sw
-    float sn, cs;
-    sincospif(x, &sn, &cs);
-    *dS = -0.5f * 3.14159265358979f / (float)r_sw * sn;
-    return 0.5f * (1.0f + cs);
+    if (d2 >= ro * ro) { *u = 1.0f; return 0.0f; }
+    const double dist = sqrt(d2);
+    const float a = (float)((d2 - r_in * r_in) / (dist + r_in) / r_sw);   // (d - r_in)/r_sw
+    const float b = (float)((ro * ro - d2) / (dist + ro) / r_sw);         // (r_in + r_sw - d)/r_sw
+    const float sa = sinpif(0.5f * a), sb = sinpif(0.5f * b);
+    *u = sa * sa;
+    *dS = -3.14159265358979f / (float)r_sw * sa * sb;                   // -(pi/2r_sw) sin(pi a)
+    return sb * sb;
 }
 
 }  // namespace ap

@@ -61,8 +61,8 @@ __global__ void __launch_bounds__(kRedBlock) k_blend(
             for (int k = 0; k < 3; ++k) d[k] = r[k] - (dy.reg_c0[k] - (dy.follow ? dy.ind_vel[k] * t : 0.0));
             min_image_vec(g, d);
             const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-            float dS;
-            switch_weight(d2, dy.r_in, dy.r_sw, &dS);
+            float uS, dS;
+            switch_weight(d2, dy.r_in, dy.r_sw, &uS, &dS);
             const float de = (float)((c1_0 + (double)e_ace[i]) - e_eam[i]);
             const float gi = dS * de * rsqrtf((float)d2);
             for (int k = 0; k < 3; ++k) F[k] -= gi * (float)d[k];
@@ -90,14 +90,15 @@ __global__ void __launch_bounds__(kRedBlock) k_blend(
 // on request: per-atom E_i + V_ind, and block sums of the energies, the virial and the load
 __global__ void __launch_bounds__(kRedBlock) k_energy_blend(
     const double* __restrict__ x, int n, const GridDev g, const DynDev dy, const double* __restrict__ tptr,
-    const float* __restrict__ wv, const float* __restrict__ e_ace, const double* __restrict__ e_eam, double c1_0,
+    const float* __restrict__ wv, const float4* __restrict__ pos4, const float* __restrict__ e_ace,
+    const double* __restrict__ e_eam, double c1_0,
     const float* __restrict__ vir_eam, const float* __restrict__ vir_ace, double* __restrict__ e_atom,
     double* __restrict__ partials, int* __restrict__ flags) {
     __shared__ double sh[32];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double acc_e = 0.0, acc_i = 0.0, acc_l = 0.0, vv[6] = {0, 0, 0, 0, 0, 0};
     if (i < n) {
-        const double wi = wv[i], ui = 1.0 - wi;
+        const double wi = wv[i], ui = pos4[i].w;         // both weights at FP32 relative precision
         const double Ei = (wi > 0.0 ? wi * (c1_0 + (double)e_ace[i]) : 0.0) + (ui > 0.0 ? ui * e_eam[i] : 0.0);
         double V = 0.0;
         if (dy.ind_on) {
@@ -192,7 +193,7 @@ int launch_eam_energy(Ctx& c, cudaStream_t s);
 
 int launch_energy(Ctx& c, cudaStream_t s) {
     int k = launch_eam_energy(c, s);
-    k_energy_blend<<<c.nred, kRedBlock, 0, s>>>(c.x, c.n, c.grid, c.dyn, c.d_time, c.w, c.e_ace, c.e_eam, c.ace_c1_0,
+    k_energy_blend<<<c.nred, kRedBlock, 0, s>>>(c.x, c.n, c.grid, c.dyn, c.d_time, c.w, c.pos4, c.e_ace, c.e_eam, c.ace_c1_0,
                                                 c.vir_eam, c.vir_ace, c.e_atom, c.partials, c.flags);
     return k + 1;
 }

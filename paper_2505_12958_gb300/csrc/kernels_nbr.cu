@@ -125,6 +125,7 @@ __global__ void k_prepare(const double* __restrict__ x, int n, const GridDev g, 
                           int* __restrict__ ace_list, int* __restrict__ flags) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     double w = 0.0;
+    float u = 1.0f;
     if (i < n) {
         double r[3] = {x[i], x[n + i], x[2 * n + i]};
         int cc[3];
@@ -134,19 +135,21 @@ __global__ void k_prepare(const double* __restrict__ x, int n, const GridDev g, 
             o[q] = g.origin[q] + cc[0] * g.cellvec[q] + cc[1] * g.cellvec[3 + q] + cc[2] * g.cellvec[6 + q];
         if (dy.reg_kind == AP_REGION_CONST) {
             w = dy.w_const;
+            u = (float)(1.0 - w);
         } else if (dy.reg_kind == AP_REGION_EXPLICIT) {
             w = w_fixed[i];
+            u = (float)(1.0 - w);
         } else if (dy.reg_kind == AP_REGION_SPHERE) {
             const double t = *tptr;
             double d[3];
             for (int q = 0; q < 3; ++q) d[q] = r[q] - (dy.reg_c0[q] - (dy.follow ? dy.ind_vel[q] * t : 0.0));
             min_image_vec(g, d);
             float dS;
-            w = switch_weight(d[0] * d[0] + d[1] * d[1] + d[2] * d[2], dy.r_in, dy.r_sw, &dS);
+            w = switch_weight(d[0] * d[0] + d[1] * d[1] + d[2] * d[2], dy.r_in, dy.r_sw, &u, &dS);
         }
         const double rel[3] = {r[0] - o[0], r[1] - o[1], r[2] - o[2]};
         const float hx = (float)rel[0], hy = (float)rel[1], hz = (float)rel[2];
-        pos4[i] = make_float4(hx, hy, hz, (float)(1.0 - w));
+        pos4[i] = make_float4(hx, hy, hz, u);
         pos_lo[i] = make_float4((float)(rel[0] - hx), (float)(rel[1] - hy), (float)(rel[2] - hz), 0.0f);
         wout[i] = (float)w;
     }

@@ -57,6 +57,16 @@ double cubic_value(const double* amp, const double* d, int n, double r) {
 // shared by every pair of the interval would bias all densities and energies alike).
 double fp32_exact(double v) { return (double)(float)v; }
 
+// Intervals longer than kMaxPiece are split into equal pieces, each re-expanded about its
+// own midpoint: over a long interval the FP32 Horner terms c_k t^k grow far beyond the value
+// they sum to (a cubic over [0, 2.8] A evaluated at 2.5 A), and their rounding, not the
+// function, sets the error of every pair energy and density.
+constexpr double kMaxPiece = 0.25;
+
+int pieces(double a, double b) { return std::max(1, (int)std::ceil((b - a) / kMaxPiece - 1e-9)); }
+
+double piece_edge(double a, double b, int m, int j) { return j == m ? b : a + (b - a) * j / m; }
+
 double binom(int m, int k) {
     double b = 1.0;
     for (int i = 1; i <= k; ++i) b = b * (m - k + i) / i;
@@ -78,11 +88,16 @@ int build_intervals(const ap_potential& p, int which, std::vector<Interval>& out
         Interval z{};
         z.a = 0.0; z.b = p.eam_r_lo; z.mid = 0.5 * z.b; z.zbl = 1;
         out.push_back(z);
-        Interval q{};
-        q.a = p.eam_r_lo; q.b = p.eam_r_hi; q.mid = fp32_exact(0.5 * (q.a + q.b));
-        for (int k = 0; k <= 5; ++k)
-            for (int m = k; m <= 5; ++m) q.c[k] += p.eam_b[m] * binom(m, k) * std::pow(q.mid, m - k);
-        out.push_back(q);
+        const int m_pieces = pieces(p.eam_r_lo, p.eam_r_hi);
+        for (int j = 0; j < m_pieces; ++j) {
+            Interval q{};
+            q.a = piece_edge(p.eam_r_lo, p.eam_r_hi, m_pieces, j);
+            q.b = piece_edge(p.eam_r_lo, p.eam_r_hi, m_pieces, j + 1);
+            q.mid = fp32_exact(0.5 * (q.a + q.b));
+            for (int k = 0; k <= 5; ++k)
+                for (int m = k; m <= 5; ++m) q.c[k] += p.eam_b[m] * binom(m, k) * std::pow(q.mid, m - k);
+            out.push_back(q);
+        }
         r0 = p.eam_r_hi;
     }
     if (which == 1 && p.eam_rho_rclamp > 0.0) {
@@ -100,10 +115,15 @@ int build_intervals(const ap_potential& p, int which, std::vector<Interval>& out
     for (double k : ks)
         if (k > r0 && k > br.back()) br.push_back(k);
     for (size_t k = 0; k + 1 < br.size(); ++k) {
-        Interval q{};
-        q.a = br[k]; q.b = br[k + 1]; q.mid = fp32_exact(0.5 * (q.a + q.b));
-        cubic_expand(amp, d, n, q.b, q.mid, q.c);
-        out.push_back(q);
+        const int m_pieces = pieces(br[k], br[k + 1]);
+        for (int j = 0; j < m_pieces; ++j) {
+            Interval q{};
+            q.a = piece_edge(br[k], br[k + 1], m_pieces, j);
+            q.b = piece_edge(br[k], br[k + 1], m_pieces, j + 1);
+            q.mid = fp32_exact(0.5 * (q.a + q.b));
+            cubic_expand(amp, d, n, br[k + 1], q.mid, q.c);
+            out.push_back(q);
+        }
     }
     if ((int)out.size() > kMaxInt) { err = "EAM: too many intervals"; return AP_ERR_ARG; }
     return AP_OK;

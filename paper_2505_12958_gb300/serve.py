@@ -1,0 +1,160 @@
+"""Serving form: many independent structures stepped concurrently on one GPU.
+
+Continuous batching over whole MD requests.  Each admitted request gets its own context
+(`APContext`) on its own non-blocking stream.  In every scheduling pass the server issues
+one chunk of velocity-Verlet steps for each active request in a single `ap_step_batch`
+call, so the replayed step graphs of different requests overlap on the device.  Requests
+join at any pass once their device footprint (`ap_footprint_bytes`) fits the memory budget
+(first come, first served, no overtaking) and leave as soon as their last chunk has
+completed, which the server learns from a CUDA event without blocking the others.
+
+Latency runs from a request's arrival to the moment its final positions, velocities,
+forces and energy are readable on the host.  A request's results do not depend on what it
+is batched with: every kernel is deterministic and contexts share no device state.
+"""
+import collections
+import time
+
+import numpy as np
+import torch
+
+from . import APContext, footprint_bytes, step_batch
+
+__all__ = ["Server", "Result", "percentile_ms"]
+
+
+class Result:
+    __slots__ = ("id", "n_atoms", "n_steps", "n_ace", "arrival_s", "admit_s", "done_s", "energy",
+                 "x", "v", "forces", "memory_bytes", "footprint_bytes")
+
+    @property
+    def latency_s(self):
+        return self.done_s - self.arrival_s
+
+
+class _Active:
+    __slots__ = ("req", "ctx", "stream", "left", "events", "foot", "admit_s")
+
+
+class Server:
+    """Continuous-batching MD server on the current CUDA device.
+
+    mem_budget   device bytes the active contexts may hold (default: 80 % of free memory)
+    chunk        MD steps issued per request per scheduling pass
+    max_active   cap on concurrently active requests
+    inflight     chunks a request may have queued on its stream at once
+    keep_arrays  keep final x, v, forces in each Result (else only the energy report)
+    """
+
+    def __init__(self, mem_budget=None, chunk=8, dt=1.0, max_active=64, inflight=2, precision="fp32",
+                 keep_arrays=True):
+        if mem_budget is None:
+            free, _ = torch.cuda.mem_get_info()
+            mem_budget = int(0.8 * free)
+        self.mem_budget = int(mem_budget)
+        self.chunk = int(chunk)
+        self.dt = float(dt)
+        self.max_active = int(max_active)
+        self.inflight = int(inflight)
+        self.precision = precision
+        self.keep_arrays = keep_arrays
+        self._streams = []
+        self.used = 0
+        self.peak_used = 0
+        self.peak_active = 0
+        self.passes = 0
+
+    def _stream(self):
+        return self._streams.pop() if self._streams else torch.cuda.Stream()
+
+    def _admit(self, req, foot, now):
+        a = _Active()
+        a.req, a.foot, a.admit_s = req, foot, now
+        a.stream = self._stream()
+        a.ctx = APContext(req["eam"], req["ace"], req["box"], req["x"], req["v"], req["fixed"], req["region"],
+                          req.get("indenter"), req.get("ind_vel"), req["mass"], precision=self.precision,
+                          stream=a.stream)
+        a.left = int(req["n_steps"])
+        a.events = collections.deque()
+        self.used += foot
+        self.peak_used = max(self.peak_used, self.used)
+        return a
+
+    def _retire(self, a, t0):
+        r = Result()
+        q = a.req
+        r.id, r.n_atoms, r.n_steps = q["id"], len(q["x"]), int(q["n_steps"])
+        r.arrival_s, r.admit_s = q["arrival_s"], a.admit_s
+        r.energy = a.ctx.energy()
+        r.n_ace = r.energy["n_ace"]
+        if self.keep_arrays:
+            r.x, r.v, _ = a.ctx.get_state()
+            r.forces = a.ctx.forces()
+        else:
+            r.x = r.v = r.forces = None
+        r.memory_bytes = a.ctx.memory_bytes()
+        r.footprint_bytes = a.foot
+        r.done_s = time.perf_counter() - t0
+        a.ctx.close()
+        self._streams.append(a.stream)
+        self.used -= a.foot
+        return r
+
+    def run(self, requests, realtime=True):
+        """Serve `requests` (dicts with x, v, box, ..., n_steps, arrival_s).  With realtime,
+        request k becomes visible at its arrival_s after the start; otherwise all are
+        visible at once (closed loop, for the saturated throughput).  Returns the Results in
+        completion order."""
+        reqs = sorted(requests, key=lambda r: r["arrival_s"])
+        if not realtime:
+            reqs = [dict(r, arrival_s=0.0) for r in reqs]
+        feet = [footprint_bytes(r["eam"], r["ace"], len(r["x"]), r["mass"]) for r in reqs]
+        k_next = 0
+        queue = collections.deque()
+        active = []
+        done = []
+        t0 = time.perf_counter()
+        while k_next < len(reqs) or queue or active:
+            now = time.perf_counter() - t0
+            while k_next < len(reqs) and reqs[k_next]["arrival_s"] <= now:
+                queue.append((reqs[k_next], feet[k_next]))
+                k_next += 1
+            # admission: first come, first served while the footprint fits
+            while queue and len(active) < self.max_active:
+                q, foot = queue[0]
+                if active and self.used + foot > self.mem_budget:
+                    break
+                queue.popleft()
+                active.append(self._admit(q, foot, time.perf_counter() - t0))
+            self.peak_active = max(self.peak_active, len(active))
+            # retire finished requests; trim completed chunk events
+            still = []
+            for a in active:
+                while a.events and a.events[0].query():
+                    a.events.popleft()
+                if a.left == 0 and not a.events:
+                    done.append(self._retire(a, t0))
+                else:
+                    still.append(a)
+            active = still
+            # one chunk for every request with room in its stream queue
+            batch = [a for a in active if a.left > 0 and len(a.events) < self.inflight]
+            if batch:
+                ks = [min(self.chunk, a.left) for a in batch]
+                step_batch([a.ctx for a in batch], ks, self.dt)
+                for a, k in zip(batch, ks):
+                    a.left -= k
+                    ev = torch.cuda.Event()
+                    ev.record(a.stream)
+                    a.events.append(ev)
+                self.passes += 1
+            else:
+                # nothing to issue: wait for a completion or the next arrival
+                nxt = reqs[k_next]["arrival_s"] - (time.perf_counter() - t0) if k_next < len(reqs) else 1.0
+                time.sleep(min(max(nxt, 0.0), 5e-5) if active else max(nxt, 0.0))
+        return done
+
+
+def percentile_ms(results, q):
+    lat = np.array([r.latency_s for r in results]) * 1e3
+    return float(np.percentile(lat, q)) if len(lat) else float("nan")

@@ -129,14 +129,21 @@ def _oriented_110(species, nx, ny, nz):
     return y[keep], (Lx, Ly, Lz)
 
 
-def serving_request(rid, rng):
-    """One request: structure, weight region, steps.  Sizes log-uniform 64..50,000 atoms."""
-    species = "Cu" if rng.random() < 0.5 else "W"
+GEOMETRIES = ("bulk", "vacancy", "surface001", "surface110", "indented")
+
+
+def serving_request(rid, rng, species=None, geometry=None, n_target=None):
+    """One request: structure, weight region, steps.  Sizes log-uniform 64..50,000 atoms,
+    species Cu/W 50/50, geometry uniform over GEOMETRIES (any of the three may be fixed)."""
+    sp = "Cu" if rng.random() < 0.5 else "W"
+    species = sp if species is None else species
     kind, a = _SPEC[species]
     per_cell = 4 if kind == "fcc" else 2
     lat = fcc if kind == "fcc" else bcc
-    n_target = int(np.exp(rng.uniform(np.log(64), np.log(50000))))
-    geom = ["bulk", "vacancy", "surface001", "surface110", "indented"][rng.integers(5)]
+    nt = int(np.exp(rng.uniform(np.log(64), np.log(50000))))
+    n_target = nt if n_target is None else n_target
+    g = GEOMETRIES[rng.integers(5)]
+    geom = g if geometry is None else geometry
     vac = 10.0
     if geom in ("bulk", "vacancy"):
         c = _cells_for(n_target, per_cell)

@@ -10,7 +10,16 @@ parametrisations are not printed), so the synthetic ACE is stated here:
   phi1 carries B_0 with c1_0 chosen so that E^ACE of the perfect lattice equals E^EAM
   there (the role the energy offset Delta xi plays in Appendix B, Eq. tungsten_F_up),
   which keeps the weight-gradient force -grad w (E^ACE - E^EAM) small.
-The offset is computed with the oracle only.
+With every coefficient random the perfect lattices are dynamically unstable (the dynamical
+matrix has negative eigenvalues down to -5.5 eV/A^2 for Cu and -0.7 for W; MD runs away
+within ~100 fs).  The 188 phi1 coefficients of the one- and two-factor functions (nu <= 2)
+are therefore fitted: linear least squares that matches the pure-ACE force constants to
+the species' EAM force constants on an 8^3 q-grid (4x4x4 supercell), with a ridge term
+pulling each coefficient toward its seeded random value (weight lam = 1, relative to the
+design matrix norm).  D(q) is linear in phi1's coefficients, so each column is one force-
+constant evaluation with a unit coefficient.  The three-factor coefficients and all of
+phi2 stay as drawn.
+The fits and the offset are computed with the oracle only.
 """
 import json
 import os
@@ -23,14 +32,53 @@ sys.path.insert(0, os.path.join(HERE, "..", ".."))
 import oracle  # noqa: E402
 import synth  # noqa: E402
 from synth.lattice import bcc, fcc  # noqa: E402
+from synth.params.lattice_dynamics import dynamical, force_constants, min_eigenvalue, q_grid  # noqa: E402
 
 SPEC = {"Cu": (fcc, 3.615, 4), "W": (bcc, 3.165, 5)}
 NREF, C2_0, RC = 1.5, 2.0, 5.0
+LAM = 1.0
+
+
+def fit_pair_and_two_factor(sp):
+    """phi1 coefficients of the nu <= 2 functions (see the module docstring)."""
+    ace = synth.ace_potential(sp)
+    reg = {"kind": "const", "w": 1.0}
+    nfit = int((ace["idx"][:, 0] <= 2).sum())
+    PhiE, R, L = force_constants(sp, eam=synth.eam_potential(sp))
+    q = q_grid(L, 8)
+    DE = dynamical(PhiE, R, q)
+    base = dict(ace, c1=ace["c1"].copy())
+    base["c1"][:nfit] = 0.0
+    Pb, _, _ = force_constants(sp, ace=base, region=reg)
+    Db = dynamical(Pb, R, q)
+    cols = []
+    for k in range(nfit):
+        unit = dict(base, c1=base["c1"].copy())
+        unit["c1"][k] = 1.0
+        Pk, _, _ = force_constants(sp, ace=unit, region=reg)
+        cols.append((dynamical(Pk, R, q) - Db).ravel())
+    M = np.stack(cols, axis=1)
+    drawn = ace["c1"][:nfit]
+    sc = np.sqrt(LAM) * np.linalg.norm(M) / np.sqrt(nfit)
+    c, *_ = np.linalg.lstsq(np.vstack([M, sc * np.eye(nfit)]), np.concatenate([(DE - Db).ravel(), sc * drawn]),
+                            rcond=None)
+    fitted = dict(base, c1=base["c1"].copy())
+    fitted["c1"][:nfit] = c
+    Pf, _, _ = force_constants(sp, ace=fitted, region=reg)
+    info = {"n_fitted": nfit, "ridge_lam": LAM, "rms_shift_from_drawn": float(np.sqrt(np.mean((c - drawn) ** 2))),
+            "min_dynamical_eigenvalue_eV_A2": min_eigenvalue(Pf, R, L),
+            "min_dynamical_eigenvalue_drawn_eV_A2": min_eigenvalue(*force_constants(sp, ace=ace, region=reg))}
+    return [round(float(v), 12) for v in c], info
 
 
 def main():
     out = {"_source": __doc__.strip().splitlines()[0] + " (make_ace_synth.py)"}
     base = {sp: {"rc": RC, "nref": NREF, "c1_0": 0.0, "c2_0": C2_0} for sp in SPEC}
+    with open(os.path.join(HERE, "ace_synth.json"), "w") as f:
+        json.dump(base, f)
+    for sp in SPEC:
+        base[sp]["c1_fit"], base[sp]["c1_fit_info"] = fit_pair_and_two_factor(sp)
+        print(sp, base[sp]["c1_fit_info"], flush=True)
     with open(os.path.join(HERE, "ace_synth.json"), "w") as f:
         json.dump(base, f)
     for sp, (lat, a, n) in SPEC.items():
@@ -40,7 +88,8 @@ def main():
         ra = oracle.evaluate(x, box, ace=ace, region={"kind": "const", "w": 1.0})
         re = oracle.evaluate(x, box, eam=synth.eam_potential(sp))
         off = (re["e_total"] - ra["e_total"]) / len(x)
-        out[sp] = {"rc": RC, "nref": NREF, "c1_0": round(off, 8), "c2_0": C2_0, "lattice_a": a}
+        out[sp] = {"rc": RC, "nref": NREF, "c1_0": round(off, 8), "c2_0": C2_0, "lattice_a": a,
+                   "c1_fit_info": base[sp]["c1_fit_info"], "c1_fit": base[sp]["c1_fit"]}
     with open(os.path.join(HERE, "ace_synth.json"), "w") as f:
         json.dump(out, f, indent=1)
     print(json.dumps(out, indent=1))

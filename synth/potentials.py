@@ -46,13 +46,19 @@ def ace_basis(nmax=8, lmax=4):
 
 
 def ace_potential(species, seed=None, nmax=8, lmax=4, sigma=0.1):
-    """Synthetic ACE: stated basis, cutoff and normalisation; seeded N(0, sigma^2) coefficients."""
+    """Synthetic ACE: stated basis, cutoff and normalisation; seeded N(0, sigma^2) coefficients,
+    except the phi1 coefficients of the nu <= 2 functions, which params/ace_synth.json holds
+    (fitted so that the perfect lattice is dynamically stable; see make_ace_synth.py)."""
     with open(os.path.join(PARAMS, "ace_synth.json")) as f:
         spec = json.load(f)[species]
     idx = ace_basis(nmax, lmax)
     rng = np.random.default_rng(ACE_SEEDS[species] if seed is None else seed)
     c1 = rng.normal(0.0, sigma, size=len(idx))
     c2 = rng.normal(0.0, sigma, size=len(idx))
+    if seed is None and "c1_fit" in spec:
+        # the phi1 coefficients of the nu <= 2 functions, fitted for dynamical stability
+        fit = np.asarray(spec["c1_fit"], dtype=np.float64)
+        c1[:len(fit)] = fit
     return {
         "species": species,
         "rc": float(spec["rc"]),

@@ -61,7 +61,10 @@ def test_backward_matches_oracle_and_finite_differences(apl, orc, ncell, seed, d
                 e_p = ap_energy(xp, e64, ctx, c["box"]).item()
                 e_m = ap_energy(xm, e64, ctx, c["box"]).item()
                 assert abs((e_p - e_m) / (2 * h) - gx[i, k]) <= 2e-3
-        hs = 1e-5
+        # strain differences: E carries ~1e-5-1e-4 eV of FP32 rounding per evaluation, so hs is
+        # kept large enough for that noise to stay below ~0.1 eV after the division, while the
+        # O(hs^2) truncation (third strain derivative ~1e5 eV) stays at ~1e-2 eV
+        hs = 5e-4
         for a, b in ((0, 0), (1, 2)):
             d = torch.zeros((3, 3), dtype=torch.float64, device="cuda")
             d[a, b] = d[b, a] = hs
@@ -69,4 +72,4 @@ def test_backward_matches_oracle_and_finite_differences(apl, orc, ncell, seed, d
             e_m = ap_energy(x64, -d, ctx, c["box"]).item()
             fd = (e_p - e_m) / (2 * hs)
             an = gs[a, b] + (gs[b, a] if a != b else 0.0)
-            assert abs(fd - an) <= 1e-3 * max(1.0, abs(an)) + 0.05
+            assert abs(fd - an) <= 1e-3 * max(1.0, abs(an)) + 0.1

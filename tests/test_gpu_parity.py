@@ -114,6 +114,24 @@ def test_explicit_weights(apl, orc):
     compare(apl, orc, c, region={"kind": "explicit", "w": w})
 
 
+def test_weights_at_the_shell_edges(apl, orc):
+    """Atoms placed a micrometre-fraction inside and outside both shell radii: the GPU's w (and
+    the compaction w > 0) must agree with the oracle's, including w ~ 1e-15 at the outer edge."""
+    c = synth.configs.cu_bulk(ncell=6, r_in=5.0, r_sw=2.5)
+    ctr = np.asarray(c["region"]["center"])
+    r_in, ro = 5.0, 7.5
+    targets = [ro - 1e-3, ro - 1e-5, ro - 1e-7, ro + 1e-7, r_in + 1e-7, r_in + 1e-5, r_in - 1e-7]
+    x = c["x"].copy()
+    d = np.linalg.norm(x - ctr, axis=1)
+    used = set()
+    for t in targets:
+        k = next(k for k in np.argsort(np.abs(d - t)) if k not in used)
+        used.add(k)
+        x[k] = ctr + (x[k] - ctr) * (t / d[k])
+    c["x"] = x
+    compare(apl, orc, c)
+
+
 def test_isolated_atom_and_pair(apl, orc):
     box = {"h": np.diag([40.0] * 3).ravel(), "origin": (0, 0, 0), "periodic": (0, 0, 0)}
     c = synth.configs.w_bulk(3)

@@ -36,6 +36,38 @@ def test_weight_limits_reduce_to_pure_potentials(orc):
     assert z["n_ace"] == 0 and o["n_ace"] == len(x)
 
 
+def test_sphere_weight_closed_form_and_compaction(orc):
+    """w = (1 + cos(pi (d - r_in)/r_sw))/2 in the shell, 1 inside, 0 outside (Sec. 2.2.3 with the
+    cosine transition); checked against sin^2(pi (r_in + r_sw - d)/(2 r_sw)), the same function
+    written from the outer radius, and the compaction count w > 0 equals #{d < r_in + r_sw},
+    including atoms a nanometre-fraction inside the outer radius."""
+    r_in, r_sw = 10.0, 3.0
+    ro = r_in + r_sw
+    d = np.concatenate([[0.0, 3.0, 9.999], np.linspace(r_in, ro, 31)[1:-1],
+                        [ro - 1e-3, ro - 1e-6, ro - 1e-9, ro, ro + 1e-9, 14.0, 20.0]])
+    k = np.arange(len(d)) + 0.5
+    th, ph = np.arccos(1 - 2 * k / len(d)), np.pi * (1 + 5 ** 0.5) * k
+    u = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], axis=1)
+    c = np.array([50.0, 50.0, 50.0])
+    x = c + d[:, None] * u
+    box = {"h": np.diag([100.0] * 3).ravel(), "origin": (0, 0, 0), "periodic": (0, 0, 0)}
+    reg = {"kind": "sphere", "center": tuple(c), "r_in": r_in, "r_sw": r_sw}
+    r = orc.evaluate(x, box, synth.eam_potential("W"), synth.ace_potential("W"), reg)
+    dd = np.linalg.norm(x - c, axis=1)
+    ref = np.where(dd < r_in, 1.0, np.where(dd >= ro, 0.0, np.sin(0.5 * np.pi * (ro - dd) / r_sw) ** 2))
+    shell = (dd >= r_in) & (dd < ro)
+    # away from the outer radius: relative agreement; within 1e-6 A of it w ~ 1e-13 and below,
+    # where any FP64 evaluation carries the rounding of d itself: positive and tiny
+    far = shell & (ro - dd > 1e-6)
+    assert np.allclose(r["w"][far], ref[far], rtol=1e-7, atol=0.0)
+    edge = shell & ~far
+    assert edge.sum() >= 2 and (r["w"][edge] > 0).all() and (r["w"][edge] < 1e-12).all()
+    assert np.array_equal(r["w"][~shell], ref[~shell])
+    mid = shell & (dd - r_in > 0.1) & (ro - dd > 0.1)
+    assert np.allclose(r["w"][mid], 0.5 * (1 + np.cos(np.pi * (dd[mid] - r_in) / r_sw)), rtol=1e-12)
+    assert r["n_ace"] == int((dd < ro).sum()) and (r["w"][dd < ro] > 0).all()
+
+
 def test_energy_and_forces_are_linear_in_constant_weights(orc):
     x, box, eam, ace, L = _small("Cu", 3)
     e = orc.evaluate(x, box, eam=eam)
