@@ -192,15 +192,18 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def ace_kernel_roofline(prof, n_steps, c, pk, peak_src, ctx_atoms_in_rc):
+def ace_kernel_roofline(prof, n_steps, c, pk, peak_src, ctx_atoms_in_rc, fma_peak=None):
     """Roofline of the dominant kernel, k_ace_contract (products, densities and dE/dA of the
-    compacted atoms); its CUDA-event time comes from the library's per-stage events."""
+    compacted atoms); its CUDA-event time comes from the library's per-stage events.  The
+    peak is the FP32 FMA throughput measured on this device (ap_probe_fp32_peak); the
+    unit-count figure at the maximum SM clock is reported beside it."""
     from paper_2505_12958_gb300.workload import ace_contract_flops_per_atom
     ms, nl = prof["ace"]
     avg_s = ms / max(1, nl) / 1000.0
     flops = ace_contract_flops_per_atom() * len(ctx_atoms_in_rc)
     achieved = flops / avg_s / 1e12
-    peak = 152 * 128 * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    derived = 152 * 128 * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    peak = fma_peak if fma_peak else derived
     traffic = None
     tf = os.path.join(ROOT, "profiles", "k_ace_contract_traffic.json")
     if os.path.exists(tf):
@@ -210,8 +213,10 @@ def ace_kernel_roofline(prof, n_steps, c, pk, peak_src, ctx_atoms_in_rc):
             traffic = rec["dram_bytes_per_launch"]
     return {"kernel": "k_ace_contract", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock, %s peaks file)"
-                           % (float(pk.get("sm_max_mhz", 2070.0)), peak_src),
+            "peak_source": ("measured: FP32 FMA microbenchmark on this device (ap_probe_fp32_peak)" if fma_peak else
+                            "derived: 152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock, %s peaks file)"
+                            % (float(pk.get("sm_max_mhz", 2070.0)), peak_src)),
+            "peak_derived_unit_count": derived,
             "algorithmic_flops_per_launch": int(flops), "avg_launch_ms": avg_s * 1000.0}
 
 
@@ -253,6 +258,106 @@ def serving_bench(torch, n_req, seed=1005, load=0.7, chunk=8, max_active=64):
                         "Poisson arrivals; latency = arrival to final state/forces/energy on the host"}
 
 
+def precision_sweep(torch, ap, steps, warmup, modes=("fp64", "fp32", "tf32x3", "bf16", "fp16")):
+    """The 2,000,000-atom Cu (001) slab (5 % ACE, thermal snapshot, 300 K velocities, moving
+    indenter): per precision mode of A_nlm, the MD throughput over `steps` steps and the force
+    and trajectory differences from the FP64-accumulation mode (GPU against GPU; the oracle
+    bars are checked by the full-size precision tests)."""
+    c = synth.configs.cu_slab(sigma=0.066)
+    n = len(c["x"])
+    reg = c["region"]
+    d = np.linalg.norm(c["x"] - np.asarray(reg["center"]), axis=1)
+    ace_rows = torch.as_tensor(np.where(d < reg["r_in"] + reg["r_sw"])[0], device="cuda")
+    res, F64, X64 = {}, None, None
+    for mode in modes:
+        ctx = ap.APContext(c["eam"], c["ace"], c["box"], c["x"], c["v"], c["fixed"], reg, c["indenter"],
+                           c["ind_vel"], c["mass"], precision=mode)
+        F = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+        ctx.compute_forces(None, F)
+        ctx.step(warmup, 1.0)
+        ctx.check()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ctx.step(steps, 1.0)
+        b.record()
+        torch.cuda.synchronize()
+        ctx.check()
+        ms = a.elapsed_time(b)
+        x, _, _ = ctx.get_state()
+        rep = ctx.energy()
+        ctx.close()
+        row = {"atom_steps_per_s": n * steps / (ms / 1000.0), "ms_per_step": ms / steps, "n_ace": rep["n_ace"],
+               "load_eV_per_A": rep["load"]}
+        if F64 is None:
+            F64, X64 = F, x
+        else:
+            dF = (F - F64).abs()
+            row["max_dF_vs_fp64_eV_A"] = float(dF.max())
+            row["max_dF_vs_fp64_ace_atoms_eV_A"] = float(dF[ace_rows].max())
+            row["max_dx_vs_fp64_after_steps_A"] = float(np.abs(x - X64).max())
+        res[mode] = row
+    return {"workload": "Cu FCC (001) slab 100x100x50 cells, 2,000,000 atoms, ACE hemisphere r=82.6 A "
+                        "(5 %), thermal snapshot sigma 0.066 A, 300 K, indenter R=60 A K=10 eV/A^3 v=25 m/s, dt=1 fs",
+            "atoms": n, "steps": steps, "warmup": warmup, "l2": "working set > L2 (no flush needed)",
+            "modes": res}
+
+
+def autograd_bench(torch, ap, n_cells=256, seed=1004):
+    """Forward + backward of the differentiable AP energy (positions and strain) over 256
+    strained triclinic W cells of 4^3 .. 12^3 BCC cells (128 .. 3456 atoms, 1 % vacancies,
+    sigma 0.1 A, w = 0.5), in FP64 and FP32 inputs; then a 250,000-atom pure-ACE W slab with
+    the device memory it holds.  Contexts are built before the timed loops."""
+    from paper_2505_12958_gb300.autograd import ap_energy
+    cells = [synth.configs.strained_w_cell(4 + k % 9, seed=seed * 1000 + k) for k in range(n_cells)]
+    reg = {"kind": "const", "w": 0.5}
+    ctxs = [ap.APContext(c["eam"], c["ace"], c["box"], c["x"], None, None, reg, None, None, c["mass"]) for c in cells]
+    atoms = sum(len(c["x"]) for c in cells)
+    out = {"cells": n_cells, "atoms": atoms}
+    for dt_name, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        xs = [torch.tensor(c["x"], dtype=dt, device="cuda") for c in cells]
+        eps = torch.zeros((3, 3), dtype=dt, device="cuda")
+        for k in range(min(8, n_cells)):                      # warm-up
+            xx = xs[k].clone().requires_grad_(True)
+            ap_energy(xx, eps, ctxs[k], cells[k]["box"]).backward()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for k in range(n_cells):
+            xx = xs[k].requires_grad_(True)
+            e = eps.clone().requires_grad_(True)
+            ap_energy(xx, e, ctxs[k], cells[k]["box"]).backward()
+        torch.cuda.synchronize()
+        s_ = time.perf_counter() - t
+        out[dt_name] = {"cells_per_s": n_cells / s_, "atoms_per_s": atoms / s_, "ms_per_cell": 1e3 * s_ / n_cells}
+    for ctx in ctxs:
+        ctx.close()
+    # 250,000-atom pure-ACE W slab (50 x 50 x 50 BCC cells)
+    c = synth.configs.w_slab(ncell=50)
+    n = len(c["x"])
+    torch.cuda.reset_peak_memory_stats()
+    ctx = ap.APContext(c["eam"], c["ace"], c["box"], c["x"], None, None, {"kind": "const", "w": 1.0}, None, None,
+                       c["mass"])
+    x = torch.tensor(c["x"], dtype=torch.float64, device="cuda")
+    eps = torch.zeros((3, 3), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        xx = x.clone().requires_grad_(True)
+        ap_energy(xx, eps, ctx, c["box"]).backward()
+    torch.cuda.synchronize()
+    reps = 10
+    t = time.perf_counter()
+    for _ in range(reps):
+        xx = x.clone().requires_grad_(True)
+        ap_energy(xx, eps, ctx, c["box"]).backward()
+    torch.cuda.synchronize()
+    s_ = (time.perf_counter() - t) / reps
+    out["pure_ace_w_slab"] = {"atoms": n, "ms_per_forward_backward": 1e3 * s_, "atoms_per_s": n / s_,
+                              "context_bytes": ctx.memory_bytes(), "context_bytes_per_atom": ctx.memory_bytes() / n,
+                              "torch_peak_bytes": torch.cuda.max_memory_allocated(),
+                              "saved_for_backward": "forces (FP32, 12 B/atom), strain and virial; no per-pair buffers"}
+    ctx.close()
+    return out
+
+
 def neighbors_in_ace_cutoff(c):
     """Neighbour counts within the ACE cutoff of the atoms with w > 0 (host, for the flop count)."""
     from scipy.spatial import cKDTree
@@ -279,17 +384,24 @@ def main():
     ap_.add_argument("--variants", default="ace,eam", help="extra single-potential runs (comma list or 'none')")
     ap_.add_argument("--serve-requests", type=int, default=300,
                      help="requests in the serving run reported beside the metric (0: skip)")
-    ap_.add_argument("--mode", default="ap", choices=["ap", "serve"],
-                     help="ap: the metric line; serve: only the serving run, as its own line")
+    ap_.add_argument("--mode", default="ap", choices=["ap", "serve", "precision", "autograd"],
+                     help="ap: the metric line; serve: only the serving run; precision: the A_nlm "
+                          "precision sweep on the 2M-atom Cu slab; autograd: forward+backward of the "
+                          "differentiable energy (each as its own line)")
     args = ap_.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.mode == "serve":
+    if args.mode in ("serve", "precision", "autograd"):
         import torch
         import paper_2505_12958_gb300 as ap
         ap.build()
-        out = serving_bench(torch, args.serve_requests)
-        print(json.dumps({"mode": "serve", **out}, default=_jsonable), flush=True)
+        if args.mode == "serve":
+            out = serving_bench(torch, args.serve_requests)
+        elif args.mode == "precision":
+            out = precision_sweep(torch, ap, args.steps, args.warmup)
+        else:
+            out = autograd_bench(torch, ap)
+        print(json.dumps({"mode": args.mode, **out}, default=_jsonable), flush=True)
         return
 
     import torch
@@ -348,7 +460,8 @@ def main():
 
     # ---- roofline of the dominant kernel ----
     stage_ms = {k: v[0] / max(1, v[1]) for k, v in prof.items()}
-    roof = ace_kernel_roofline(prof, args.steps, c, pk, peak_src, neighbors_in_ace_cutoff(c))
+    fma_peak, _ = ap.probe_fp32_peak()
+    roof = ace_kernel_roofline(prof, args.steps, c, pk, peak_src, neighbors_in_ace_cutoff(c), fma_peak)
     ctx.close()
 
     extra = {}

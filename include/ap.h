@@ -230,6 +230,13 @@ const char* ap_last_error(const ap_ctx* ctx);
 void ap_destroy(ap_ctx* ctx);
 int ap_version(void);
 
+/* Measurement helper: FP32 FMA throughput of the current device (TFLOP/s), from one
+ * timed launch of a kernel of independent FMA chains on 8 blocks of 256 threads per SM
+ * (after a short warm-up launch).  iters in [1, 2^20] sets its length (2e5: ~25 ms).
+ * The roofline denominator of the ACE contraction, which is plain FP32 arithmetic.
+ * *ms_out (nullable) receives the launch time.  Synchronises the device. */
+ap_status ap_probe_fp32_peak(int iters, double* tflops, double* ms_out);
+
 /* Allocation-free ACE forces for neighbour environments the caller supplies.  The paper
  * has no counterpart: this entry point exists for callers that cannot create device
  * allocations of their own - a program or plugin whose GPU memory is owned entirely by

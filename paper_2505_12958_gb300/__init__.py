@@ -20,7 +20,7 @@ from . import _capi
 from ._capi import PRECISION, REGION, STAGES, STATUS
 
 __all__ = ["APContext", "APError", "build", "PRECISION", "STAGES", "potential_struct", "gaunt_real",
-           "eam_table_eval", "step_batch", "compute_forces_batch", "footprint_bytes"]
+           "eam_table_eval", "step_batch", "compute_forces_batch", "footprint_bytes", "probe_fp32_peak"]
 
 
 class APError(RuntimeError):
@@ -289,6 +289,15 @@ def footprint_bytes(eam, ace, n_atoms, mass=1.0, skin=1.0, ace_fraction=1.0):
     nb = int(_capi.lib().ap_footprint_bytes(C.byref(pot), int(n_atoms), float(ace_fraction)))
     del keep
     return nb
+
+
+def probe_fp32_peak(iters=200000):
+    """Measured FP32 FMA throughput of the current device in TFLOP/s (ap_probe_fp32_peak)."""
+    tf, ms = C.c_double(), C.c_double()
+    st = _capi.lib().ap_probe_fp32_peak(int(iters), C.byref(tf), C.byref(ms))
+    if st != 0:
+        raise APError(st, "ap_probe_fp32_peak")
+    return tf.value, ms.value
 
 
 def gaunt_real(l1, m1, l2, m2, l3, m3):

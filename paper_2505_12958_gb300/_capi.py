@@ -87,6 +87,7 @@ def lib():
         "ap_version": (I, []),
         "ap_ace_forces_noalloc": (I, [P(Potential), I, I, VP, VP, VP, VP, VP, VP]),
         "ap_gaunt_real": (I, [I, I, I, I, I, I, PD]),
+        "ap_probe_fp32_peak": (I, [I, PD, PD]),
         "ap_eam_table_eval": (I, [P(Potential), I, D, PD, PD]),
     }
     for name, (res, args) in sig.items():

@@ -66,18 +66,23 @@ def w_slab(ncell=40, nz=None, a=3.165, temperature=300.0, seed=1002, r_in=50.0, 
 
 
 def cu_slab(nx=100, nz=50, a=3.615, temperature=300.0, seed=1003, r_hemi=82.6, r_sw=4.0,
-            R=60.0, K=10.0, v_ms=25.0, penetration=1.0, n_fixed_layers=3, vacuum=10.0):
-    """Cu FCC (001) indentation slab (the precision-sweep cell), same layout as w_slab."""
+            R=60.0, K=10.0, v_ms=25.0, penetration=1.0, n_fixed_layers=3, vacuum=10.0, sigma=0.0):
+    """Cu FCC (001) indentation slab (the precision-sweep cell), same layout as w_slab; the
+    ACE hemisphere's outer radius r_hemi (w > 0 inside it) holds 5 % of the atoms.  sigma > 0
+    displaces the free atoms by N(0, sigma^2) per component (a thermal snapshot: 0.066 A is
+    the 300 K amplitude of the synthetic Cu EAM's Einstein oscillator)."""
     x = fcc(a, nx, nx, nz)
     n = len(x)
     zs = np.unique(np.round(x[:, 2], 6))
     fixed = (x[:, 2] < zs[n_fixed_layers] - 1e-6).astype(np.uint8)
+    if sigma > 0.0:
+        x = x + random_displacements(n, sigma, seed + 100) * (1 - fixed)[:, None]
     mass = float(eam_potential("Cu")["mass_amu"])
     v = maxwell_velocities(n, temperature, mass, seed, fixed)
     L = nx * a
     z_top = x[:, 2].max()
     box = orthorhombic_box(L, L, z_top + 2 * vacuum, (1, 1, 0), origin=(0.0, 0.0, -vacuum))
-    region = {"kind": "sphere", "center": (L / 2, L / 2, z_top), "r_in": r_hemi, "r_sw": r_sw}
+    region = {"kind": "sphere", "center": (L / 2, L / 2, z_top), "r_in": r_hemi - r_sw, "r_sw": r_sw}
     ind = {"center": (L / 2, L / 2, z_top + R - penetration), "R": R, "K": K, "dir": (0.0, 0.0, -1.0)}
     return _bundle("Cu", x, v, box, fixed, region, ind, (0.0, 0.0, v_ms * MS_TO_AFS))
 

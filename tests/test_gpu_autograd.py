@@ -73,3 +73,29 @@ def test_backward_matches_oracle_and_finite_differences(apl, orc, ncell, seed, d
             fd = (e_p - e_m) / (2 * hs)
             an = gs[a, b] + (gs[b, a] if a != b else 0.0)
             assert abs(fd - an) <= 1e-3 * max(1.0, abs(an)) + 0.1
+
+
+@pytest.mark.parametrize("dtype", ["float64", "float32"])
+def test_strained_cell_sweep_against_oracle(apl, orc, dtype):
+    """Nine strained W cells from 4^3 to 12^3 BCC cells (128 - 3456 atoms): backward against the
+    oracle's forces and virial at the positions the forward pass saw."""
+    import torch
+    from paper_2505_12958_gb300.autograd import ap_energy
+    td = getattr(torch, dtype)
+    reg = {"kind": "const", "w": 0.5}
+    for k, ncell in enumerate(range(4, 13)):
+        c = synth.configs.strained_w_cell(ncell, seed=500 + k)
+        n = len(c["x"])
+        with apl.APContext(c["eam"], c["ace"], c["box"], c["x"], None, None, reg, None, None, c["mass"]) as ctx:
+            x = torch.tensor(c["x"], dtype=td, device="cuda", requires_grad=True)
+            eps = torch.zeros((3, 3), dtype=td, device="cuda", requires_grad=True)
+            E = ap_energy(x, eps, ctx, c["box"])
+            E.backward()
+            xr = x.detach().double().cpu().numpy()
+            ref = orc.evaluate(xr, c["box"], c["eam"], c["ace"], reg)
+            assert np.abs(-x.grad.double().cpu().numpy() - ref["forces"]).max() <= 1e-4, ncell
+            assert abs(E.item() - ref["e_total"]) / n <= (1e-6 if dtype == "float64" else 1e-5), ncell
+            v = ref["virial"]
+            W = np.array([[v[0], v[3], v[4]], [v[3], v[1], v[5]], [v[4], v[5], v[2]]])
+            gs = eps.grad.double().cpu().numpy()
+            assert np.abs(-gs - W).max() <= 2e-5 * np.abs(W).max() + 1e-5 * n, ncell

@@ -52,3 +52,56 @@ def test_precision_mode_against_oracle(apl, case, mode):
         assert dE <= 2 * U[mode] * escale
     else:
         assert dF <= 1e-4 and dE <= 1e-6
+
+
+@pytest.fixture(scope="module")
+def slab(orc):
+    """The 2,000,000-atom Cu (001) indentation slab (5 % ACE), thermal snapshot, with the
+    oracle's forces on 1000 seeded atoms: 500 with w > 0 and 500 without."""
+    c = synth.configs.cu_slab(sigma=0.066)
+    reg = c["region"]
+    d = np.linalg.norm(c["x"] - np.asarray(reg["center"]), axis=1)
+    rng = np.random.default_rng(3003)
+    ace = np.where(d < reg["r_in"] + reg["r_sw"])[0]
+    rest = np.where(d >= reg["r_in"] + reg["r_sw"])[0]
+    cen = np.concatenate([rng.choice(ace, 500, replace=False), rng.choice(rest, 500, replace=False)])
+    # a sampled atom's force needs the energies of every atom within the cutoff of it
+    ext = _with_neighbours(c, cen, 5.0 + 1e-6)
+    ref = orc.evaluate(c["x"], c["box"], c["eam"], c["ace"], reg, c["indenter"], centers=ext)
+    assert ref["status"] == 0
+    ext_a = _with_neighbours(c, cen[:500], 5.0 + 1e-6)
+    ace_only = orc.evaluate(c["x"], c["box"], None, c["ace"], {"kind": "const", "w": 1.0}, centers=ext_a)
+    return c, cen, ref["forces"][cen], np.abs(ace_only["forces"][cen[:500]]).max()
+
+
+def _with_neighbours(c, idx, rc):
+    """idx and every atom within rc of one of them (periodic in x and y, open in z)."""
+    from scipy.spatial import cKDTree
+    h = np.asarray(c["box"]["h"]).reshape(3, 3)
+    L = np.diag(h)
+    y = c["x"] - np.asarray(c["box"]["origin"])
+    y[:, :2] = np.mod(y[:, :2], L[:2])
+    y[:, 2] -= y[:, 2].min()
+    tree = cKDTree(y, boxsize=[L[0], L[1], 1e9])
+    near = tree.query_ball_point(y[idx], r=rc)
+    return np.unique(np.concatenate([np.asarray(idx)] + [np.asarray(v, dtype=np.int64) for v in near]))
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp32", "tf32x3", "bf16", "fp16"])
+def test_full_size_cu_slab_sampled(apl, slab, mode):
+    import torch
+    c, cen, fref, fscale = slab
+    n = len(c["x"])
+    with apl.APContext(c["eam"], c["ace"], c["box"], c["x"], c["v"], c["fixed"], c["region"], c["indenter"],
+                       c["ind_vel"], c["mass"], precision=mode) as ctx:
+        out = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+        ctx.compute_forces(None, out)
+        ctx.check()
+        F = out.cpu().numpy().astype(np.float64)[cen]
+    dF = np.abs(F - fref).max()
+    print("mode %-7s 2M-atom Cu slab, 1000 sampled atoms: max|dF| = %.3e eV/A (ACE force scale %.2f)"
+          % (mode, dF, fscale))
+    if mode in U:
+        assert dF <= 10 * 2 * U[mode] * fscale
+    else:
+        assert dF <= 1e-4
