@@ -207,9 +207,9 @@ def ace_kernel_roofline(prof, n_steps, c, pk, peak_src, ctx_atoms_in_rc, fma_pea
     traffic = None
     tf = os.path.join(ROOT, "profiles", "k_ace_contract_traffic.json")
     if os.path.exists(tf):
-        from paper_2505_12958_gb300.buildlib import source_hash
+        from paper_2505_12958_gb300.buildlib import CONTRACT_FILES, source_hash
         rec = json.load(open(tf))
-        if rec.get("source_hash") == source_hash():
+        if rec.get("source_hash") == source_hash(CONTRACT_FILES):
             traffic = rec["dram_bytes_per_launch"]
     return {"kernel": "k_ace_contract", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,

@@ -33,11 +33,20 @@ def _deps():
     return sources() + glob.glob(os.path.join(CSRC, "*.h")) + [os.path.join(INCLUDE, "ap.h"), __file__]
 
 
-def source_hash():
-    """Hash of the CUDA sources and headers (tags profile records to the code they measured)."""
+# the files that define the ACE contraction kernel (k_ace_contract)
+CONTRACT_FILES = ("kernels_ace.cu", "ace_pattern.h", "ap_internal.h")
+
+
+def source_hash(names=None):
+    """Hash of the CUDA sources and headers, or of the named csrc files only (tags profile
+    records to the code they measured)."""
     import hashlib
     h = hashlib.sha256()
-    for p in sorted(sources() + glob.glob(os.path.join(CSRC, "*.h")) + [os.path.join(INCLUDE, "ap.h")]):
+    files = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
+        [os.path.join(INCLUDE, "ap.h")]
+    if names is not None:
+        files = [os.path.join(CSRC, n) for n in names]
+    for p in sorted(files):
         h.update(os.path.basename(p).encode())
         h.update(open(p, "rb").read())
     return h.hexdigest()[:16]
