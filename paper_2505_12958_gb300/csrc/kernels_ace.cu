@@ -1,22 +1,24 @@
 // kernels_ace.cu -- ACE pass of the AP force evaluation (Sec. 2.2.2, Eq. energy_ace).
 //
-// One warp per atom of the compacted list (w_i > 0), persistent grid.  Per atom:
-//   1. neighbours within the ACE cutoff are gathered from the full list into shared
-//      memory (r_ij from FP32 cell-relative positions);
-//   2. the atomic base A_nlm = (1/nref) sum_j g_n(r_ij) Y_lm(rhat_ij) (8 x 25) is formed
-//      from a shared-memory tile of g and Y (lane = (l, m), 8 accumulators);
-//   3. phi_p = c_p0 + sum_v c_p[v] B_v, p = 1, 2 (B: one, two and three A factors), with
-//      lanes over the 64 (n1, n2) pairs: three-factor products are evaluated as
-//      P[m3] = sum G A_n1 A_n2 (compile-time Gaunt pattern, operands in registers), then
-//      contracted with A_n3 and the coefficient tensor;
-//   4. the adjoint dE/dA with the combined coefficients c1 + c2 / (2 sqrt(phi2)):
-//      gradients with respect to the first two factors from the (n1, n2) mapping,
-//      with respect to the third from an (n1, n3) mapping; lane partial sums are
-//      reduced with butterfly shuffles in a fixed order;
-//   5. pair forces f_ij = dE_i/dr_ij = (1/nref) sum dE/dA_nlm grad(g_n Y_lm), weighted by
-//      w_i, are added to atom j (minus) and atom i (plus) through 64-bit fixed-point
-//      atomics (2^-40 eV/A resolution), whose integer sums do not depend on order.
-// E_i^ACE is stored without the constant c1_0, which the blend adds in FP64.
+// Three kernels per step, one warp per atom of the compacted list (w_i > 0), persistent grids:
+//   k_ace_basis<MODE>  neighbours within the ACE cutoff are gathered from the full list
+//                      (r_ij from FP32 cell-relative positions); g_n(r_ij), Y_lm(rhat_ij) and
+//                      A_nlm = (1/nref) sum_j g_n Y_lm (8 x 25) in the precision MODE
+//                      (FP32 FMA, 3xTF32 / BF16 / FP16 mma.sync, or FP64 accumulation);
+//                      A is written [atom][lm][n].
+//   k_ace_contract     phi_p = c_p0 + sum_v c_p[v] B_v, p = 1, 2 (B: one, two and three A
+//                      factors) with lanes over the 64 (n1, n2) pairs; three-factor products
+//                      as P[m3] = sum G A_n1 A_n2 (compile-time Gaunt pattern, operands in
+//                      registers) contracted with A_n3 and the coefficient tensor; then the
+//                      adjoint dE/dA with the combined coefficients c1 + c2 / (2 sqrt(phi2)):
+//                      first and second factors from the (n1, n2) mapping, the third from an
+//                      (n1, n3) mapping, lane partial sums reduced by butterfly shuffles in a
+//                      fixed order.  Writes dE/dA and E_i^ACE.
+//   k_ace_force        f_ij = dE_i/dr_ij = (1/nref) sum dE/dA_nlm grad(g_n Y_lm), weighted by
+//                      w_i, added to atom j (minus) and atom i (plus) through 64-bit fixed-point
+//                      atomics (2^-40 eV/A resolution), whose integer sums do not depend on order.
+// E_i^ACE is stored without the constant c1_0, which the blend adds in FP64.  The allocation-
+// free entry point at the end of the file runs the same arithmetic in one kernel.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
