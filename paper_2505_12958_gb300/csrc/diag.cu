@@ -2,7 +2,7 @@
 // denominator of the ACE contraction (plain FP32 arithmetic, no tensor cores).
 #include <cuda_runtime.h>
 
-#include "../../include/ap.h"
+#include "ap.h"
 
 namespace {
 

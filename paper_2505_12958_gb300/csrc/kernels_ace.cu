@@ -37,6 +37,16 @@ void upload_gaunt(const float* g) { cudaMemcpyToSymbol(c_gaunt, g, sizeof(float)
 
 namespace {
 
+// unroll factors of the contraction loops (tuning constants; results do not depend on them)
+#ifndef AP_N3_UNROLL
+#define AP_N3_UNROLL 2
+#endif
+#ifndef AP_PP_UNROLL
+#define AP_PP_UNROLL 1
+#endif
+constexpr int kN3Unroll = AP_N3_UNROLL;
+constexpr int kPPUnroll = AP_PP_UNROLL;
+
 constexpr int kWarps = 8;
 constexpr int kTile = 32;
 
@@ -266,7 +276,7 @@ __device__ __forceinline__ void axpy_row(float* Q, float ce, const float* row) {
 template <int T>
 __device__ __forceinline__ void nu3_forward(const float* As, const AceDev& C, int lane, float& p1, float& p2) {
     using R = Tri<T>;
-#pragma unroll 1
+#pragma unroll kPPUnroll
     for (int pp = 0; pp < 2; ++pp) {
         const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
         float A1[R::W1], A2[R::W2], P[R::W3];
@@ -278,7 +288,7 @@ __device__ __forceinline__ void nu3_forward(const float* As, const AceDev& C, in
         const float* c1 = &C.c3[0][T][0][q];
         const float* c2 = &C.c3[1][T][0][q];
         float s1 = 0.0f, s2 = 0.0f;
-#pragma unroll 2
+#pragma unroll kN3Unroll
         for (int n3 = 0; n3 < kNmax; ++n3) {
             const float r = dot_row2<R::W3>(P, As + n3 * kApad + R::B3);
             s1 = fmaf(c1[n3 * 65], r, s1);
@@ -296,7 +306,7 @@ __device__ __forceinline__ void nu3_adjoint(const float* As, float* dAs, const A
     float d2[R::W2];
 #pragma unroll
     for (int k = 0; k < R::W2; ++k) d2[k] = 0.0f;
-#pragma unroll 1
+#pragma unroll kPPUnroll
     for (int pp = 0; pp < 2; ++pp) {
         const int q = lane + 32 * pp, n1 = q >> 3;
         const int n2 = q & 7;
@@ -307,7 +317,7 @@ __device__ __forceinline__ void nu3_adjoint(const float* As, float* dAs, const A
         for (int m = 0; m < R::W3; ++m) Q[m] = 0.0f;
         const float* c1 = &C.c3[0][T][0][q];
         const float* c2 = &C.c3[1][T][0][q];
-#pragma unroll 2
+#pragma unroll kN3Unroll
         for (int n3 = 0; n3 < kNmax; ++n3) {
             const float ce = fmaf(s, c2[n3 * 65], c1[n3 * 65]);
             axpy_row<R::W3>(Q, ce, As + n3 * kApad + R::B3);
@@ -345,14 +355,14 @@ __device__ __forceinline__ void nu3_adjoint(const float* As, float* dAs, const A
     float d3[R::W3];
 #pragma unroll
     for (int k = 0; k < R::W3; ++k) d3[k] = 0.0f;
-#pragma unroll 1
+#pragma unroll kPPUnroll
     for (int pp = 0; pp < 2; ++pp) {
         const int q = lane + 32 * pp, n1 = q >> 3, n3 = q & 7;
         float A1[R::W1], Tm[R::W2];
         load_row<R::W1>(A1, As + n1 * kApad + R::B1);
 #pragma unroll
         for (int m = 0; m < R::W2; ++m) Tm[m] = 0.0f;
-#pragma unroll 2
+#pragma unroll kN3Unroll
         for (int n2 = 0; n2 < kNmax; ++n2) {
             const float ce = fmaf(s, C.c3[1][T][n3][n1 * 8 + n2], C.c3[0][T][n3][n1 * 8 + n2]);
             axpy_row<R::W2>(Tm, ce, As + n2 * kApad + R::B2);
