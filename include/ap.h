@@ -265,8 +265,11 @@ ap_status ap_ace_forces_noalloc(const ap_potential* pot, int n_atoms, int max_nb
 /* Host-side table generators, exposed so that they can be checked without a GPU.
  * ap_gaunt_real: real Gaunt coefficient integral(Y_l1m1 Y_l2m2 Y_l3m3) from the Racah
  * formula for Wigner 3j symbols and the complex-to-real transform (l <= 4).
- * ap_eam_table_eval: the piecewise polynomials the kernels evaluate (which = 0: Phi,
- * 1: zeta), re-expanded in FP64 about each interval's midpoint, evaluated in FP64. */
+ * ap_eam_table_eval: the pair functions of Appendix B as the kernels hold them: the merged
+ * piecewise-polynomial partition re-expanded in FP64 about each segment midpoint and
+ * evaluated in FP64 (which = 0: Phi, 1: zeta), or the FP32 device table read through the
+ * kernels' own segment lookup and evaluated in FP32 on the host (which = 2: Phi, 3: zeta).
+ * Zero at and beyond each function's cutoff. */
 ap_status ap_gaunt_real(int l1, int m1, int l2, int m2, int l3, int m3, double* out);
 ap_status ap_eam_table_eval(const ap_potential* pot, int which, double r, double* f, double* df);
 

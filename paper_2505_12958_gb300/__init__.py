@@ -310,7 +310,8 @@ def gaunt_real(l1, m1, l2, m2, l3, m3):
 
 
 def eam_table_eval(eam, which, r, mass=1.0):
-    """The library's host-side piecewise-polynomial EAM table, evaluated in FP64."""
+    """The library's EAM pair table: which 0 (Phi) / 1 (zeta) from the FP64 segments, 2 / 3 from the
+    FP32 device table through the kernels' segment lookup (ap_eam_table_eval)."""
     dummy_ace = {"idx": np.zeros((0, 7), np.int32), "c1": np.zeros(0), "c2": np.zeros(0), "rc": 5.0,
                  "nref": 1.0, "nmax": 8, "lmax": 4, "c1_0": 0.0, "c2_0": 1.0}
     p, keep = potential_struct(eam, dummy_ace, mass)

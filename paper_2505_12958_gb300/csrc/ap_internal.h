@@ -15,27 +15,40 @@ namespace ap {
 // EAM functions as piecewise polynomials (degree <= 5) in t = r - mid on each interval.
 // Built on the host in FP64 from the Appendix B forms, evaluated on the device in FP32.
 // ---------------------------------------------------------------------------------
-constexpr int kMaxInt = 40;
 constexpr int kNBin = 256;
 
-struct PolyTab {
-    int nint;                 // intervals [start[k], start[k+1]), k < nint
-    int zbl;                  // 1: interval 0 is the screened-Coulomb (ZBL) form
-    float rcut;               // zero at and beyond rcut
-    float bin_inv;            // kNBin / rcut
-    float start[kMaxInt + 1];
-    float mid[kMaxInt];
-    float c[kMaxInt][6];
-    float c0lo[kMaxInt];      // c[k][0] - (double)c[k][0], for the compensated energy pass
-    unsigned char bin[kNBin]; // first interval that overlaps bin b
+// EAM pair functions zeta(r) and Phi(r) on one merged partition of [0, rc): the union of
+// both functions' knots (and of r_lo, r_hi, r_cut^rho), split into pieces of at most
+// 0.25 A.  On each segment zeta is a cubic and Phi a cubic, the quintic bridge or the ZBL
+// form, expanded in FP64 on the host about the segment midpoint (an FP32 number) and
+// stored in FP32 with the constant terms' residuals for the compensated energy pass.
+constexpr int kMaxSeg = 48;
+constexpr int kSegCubic = 0, kSegQuintic = 1, kSegZbl = 2;   // kinds of the Phi piece
+
+struct EamSeg {
+    float4 q0;                // (mid, zeta c1, zeta c2, zeta c3)
+    float4 q1;                // (Phi c1, Phi c2, Phi c3, Phi c0)
+    float4 q2;                // (zeta c0, zeta c0 residual, Phi c0 residual, kind)
+    float4 q3;                // (Phi c4, Phi c5, 0, 0): the quintic bridge only
+};
+
+// r in bin b = (int)(r * bin_inv) lies in segment k + (r >= s1) + (r >= s2); special is set
+// when one of those segments has a non-cubic Phi piece
+struct EamBin {
+    int k;
+    float s1, s2;
+    int special;
 };
 
 struct alignas(16) EamDev {
-    PolyTab phi, rho;
+    EamSeg seg[kMaxSeg];
+    EamBin bin[kNBin];
+    int nseg, pad0;
+    float rc_rho, rc_phi;     // zeta and Phi vanish at and beyond these
+    float rc;                 // max of the two
+    float bin_inv;            // kNBin / rc
     float zbl_k;              // Z^2 / (4 pi eps0), eV Angstrom
     float zbl_ainv;           // 1 / a_ZBL
-    float rc;                 // max(phi.rcut, rho.rcut)
-    float pad;
     double F_a1, F_a2, F_dxi;
 };
 
@@ -177,8 +190,9 @@ int build_eam_tables(const ap_potential& p, EamDev& out, std::string& err);
 int build_ace_tables(const ap_potential& p, AceDev& out, std::string& err);
 double gaunt_real_racah(int l1, int m1, int l2, int m2, int l3, int m3);
 int gaunt_values(float* out, std::string& err);      // kNG entries in pattern order
-double poly_eval_host(const PolyTab& t, const double* coef64, double r, double* df);
-int eam_table_eval_fp64(const ap_potential& p, int which, double r, double* f, double* df);
+// which = 0: Phi, 1: zeta from the FP64 segments; 2: Phi, 3: zeta from the FP32 device
+// table through the kernels' own segment lookup (eam_table.h)
+int eam_table_eval(const ap_potential& p, int which, double r, double* f, double* df);
 void upload_gaunt(const float* g);                   // kernels_ace.cu
 
 }  // namespace ap

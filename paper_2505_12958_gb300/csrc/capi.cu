@@ -750,8 +750,8 @@ ap_status ap_gaunt_real(int l1, int m1, int l2, int m2, int l3, int m3, double* 
 }
 
 ap_status ap_eam_table_eval(const ap_potential* pot, int which, double r, double* f, double* df) {
-    if (!pot || !f || !df || (which != 0 && which != 1)) return AP_ERR_ARG;
-    return (ap_status)ap::eam_table_eval_fp64(*pot, which, r, f, df);
+    if (!pot || !f || !df || which < 0 || which > 3) return AP_ERR_ARG;
+    return (ap_status)ap::eam_table_eval(*pot, which, r, f, df);
 }
 
 }  // extern "C"

@@ -26,6 +26,7 @@
 #include <mutex>
 #include <string>
 #include <utility>
+#include <vector>
 
 #include "ap_internal.h"
 
@@ -840,18 +841,40 @@ size_t ace_smem_bytes() { return sizeof(AceDev) + 128 * sizeof(float4) + kWarps 
 
 size_t ace_contract_smem_bytes() { return sizeof(AceDev) + kContractWarps * sizeof(ContractSmem); }
 
+// Persistent grids: as many resident blocks per SM as the kernel's registers and shared
+// memory allow (the gather kernels are latency-bound, so every resident warp helps),
+// computed once per kernel and device.
+template <class K>
+int persistent_blocks(K kernel, int dev, int threads, size_t smem) {
+    struct Entry { const void* k; int dev, threads; size_t smem; int blocks; };
+    static std::mutex mu;
+    static std::vector<Entry> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    for (const Entry& e : cache)
+        if (e.k == (const void*)kernel && e.dev == dev && e.threads == threads && e.smem == smem) return e.blocks;
+    int nsm = 0, per = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
+    const int blocks = nsm * (per > 0 ? per : 1);
+    cache.push_back({(const void*)kernel, dev, threads, smem, blocks});
+    return blocks;
+}
+
+template <int MODE>
+void launch_basis_mode(Ctx& c, cudaStream_t s) {
+    const int nb = persistent_blocks(k_ace_basis<MODE>, c.dev, 256, 0);
+    k_ace_basis<MODE><<<nb, 256, 0, s>>>(c.pos4, c.nbr, c.nnbr, c.n, c.D, c.grid.ncode, c.ace_d, c.ace_list, c.flags,
+                                         c.ace_A);
+}
+
 int launch_ace_basis(Ctx& c, cudaStream_t s) {
-    int nsm = 0;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c.dev);
-#define AP_BASIS_ARGS c.pos4, c.nbr, c.nnbr, c.n, c.D, c.grid.ncode, c.ace_d, c.ace_list, c.flags, c.ace_A
     switch (c.ace_prec) {
-        case AP_ACE_TC_TF32X3: k_ace_basis<AP_ACE_TC_TF32X3><<<nsm * 2, 256, 0, s>>>(AP_BASIS_ARGS); break;
-        case AP_ACE_TC_BF16: k_ace_basis<AP_ACE_TC_BF16><<<nsm * 2, 256, 0, s>>>(AP_BASIS_ARGS); break;
-        case AP_ACE_TC_FP16: k_ace_basis<AP_ACE_TC_FP16><<<nsm * 2, 256, 0, s>>>(AP_BASIS_ARGS); break;
-        case AP_ACE_FP64: k_ace_basis<AP_ACE_FP64><<<nsm * 2, 256, 0, s>>>(AP_BASIS_ARGS); break;
-        default: k_ace_basis<AP_ACE_FP32><<<nsm * 2, 256, 0, s>>>(AP_BASIS_ARGS); break;
+        case AP_ACE_TC_TF32X3: launch_basis_mode<AP_ACE_TC_TF32X3>(c, s); break;
+        case AP_ACE_TC_BF16: launch_basis_mode<AP_ACE_TC_BF16>(c, s); break;
+        case AP_ACE_TC_FP16: launch_basis_mode<AP_ACE_TC_FP16>(c, s); break;
+        case AP_ACE_FP64: launch_basis_mode<AP_ACE_FP64>(c, s); break;
+        default: launch_basis_mode<AP_ACE_FP32>(c, s); break;
     }
-#undef AP_BASIS_ARGS
     return 1;
 }
 
@@ -869,9 +892,8 @@ int launch_ace(Ctx& c, cudaStream_t s) {
 }
 
 int launch_ace_force(Ctx& c, cudaStream_t s) {
-    int nsm = 0;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c.dev);
-    k_ace_force<<<nsm * 2, 256, 0, s>>>(c.pos4, c.nbr, c.nnbr, c.n, c.D, c.grid.ncode, c.ace_d, c.ace_list, c.w,
+    const int nb = persistent_blocks(k_ace_force, c.dev, 256, 0);
+    k_ace_force<<<nb, 256, 0, s>>>(c.pos4, c.nbr, c.nnbr, c.n, c.D, c.grid.ncode, c.ace_d, c.ace_list, c.w,
                                         c.flags, c.ace_dA, c.vir_ace, c.acc);
     return 1;
 }

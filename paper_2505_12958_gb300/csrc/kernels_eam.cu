@@ -9,54 +9,11 @@
 // -1/2 sum_j c_ij r_ij (x) rhat_ij.  The embedding function is evaluated in FP64 (one
 // square root per atom); pair terms are FP32 piecewise polynomials from the host tables.
 #include "ap_internal.h"
+#include "eam_table.h"
 
 namespace ap {
 
 namespace {
-
-// interval of r: the bin table gives the interval at the bin start; at most two knots
-// (the W pair potential's 5e-5 A wide interval) can fall inside one bin
-__device__ __forceinline__ int poly_interval(const PolyTab& t, float r) {
-    int b = (int)(r * t.bin_inv);
-    b = b < kNBin ? b : kNBin - 1;
-    int k = t.bin[b];
-    k += (k + 1 < t.nint && r >= t.start[k + 1]) ? 1 : 0;
-    k += (k + 1 < t.nint && r >= t.start[k + 1]) ? 1 : 0;
-    while (k + 1 < t.nint && r >= t.start[k + 1]) ++k;
-    return k;
-}
-
-// screened Coulomb: Z^2/(4 pi eps0 r) phi(r/a), phi = sum of four exponentials
-__device__ __forceinline__ void zbl_eval(float r, float zk, float zainv, float& f, float& df) {
-    const float x = r * zainv;
-    const float e0 = 0.1818f * expf(-3.2f * x), e1 = 0.5099f * expf(-0.9423f * x);
-    const float e2 = 0.2802f * expf(-0.4029f * x), e3 = 0.02817f * expf(-0.2016f * x);
-    const float ph = e0 + e1 + e2 + e3;
-    const float dph = -(3.2f * e0 + 0.9423f * e1 + 0.4029f * e2 + 0.2016f * e3);
-    const float ri = 1.0f / r;
-    f = zk * ph * ri;
-    df = zk * (dph * zainv * ri - ph * ri * ri);
-}
-
-// value (VAL) and/or derivative (DER) of the piecewise polynomial at r; all intervals are
-// cubic except the quintic bridge of a table with the ZBL core (interval 1)
-template <bool VAL, bool DER>
-__device__ __forceinline__ void poly_eval(const PolyTab& t, float r, float& f, float& df, float zk, float zainv) {
-    const int k = poly_interval(t, r);
-    if (t.zbl && k == 0) {
-        zbl_eval(r, zk, zainv, f, df);
-        return;
-    }
-    const float x = r - t.mid[k];
-    const float* c = t.c[k];
-    if (t.zbl && k == 1) {
-        if (VAL) f = ((((c[5] * x + c[4]) * x + c[3]) * x + c[2]) * x + c[1]) * x + c[0];
-        if (DER) df = (((5.0f * c[5] * x + 4.0f * c[4]) * x + 3.0f * c[3]) * x + 2.0f * c[2]) * x + c[1];
-    } else {
-        if (VAL) f = ((c[3] * x + c[2]) * x + c[1]) * x + c[0];
-        if (DER) df = (3.0f * c[3] * x + 2.0f * c[2]) * x + c[1];
-    }
-}
 
 __device__ __forceinline__ void stage_tables(EamDev* sm, const EamDev* __restrict__ gm, float4* Ds,
                                              const float4* __restrict__ D, int ncode) {
@@ -80,18 +37,14 @@ __global__ void __launch_bounds__(256) k_eam_density(const float4* __restrict__ 
     float4 p = pos4[i];
     float u = p.w;
     if (u <= 0.0f) { uxi[i] = 0.0f; e_emb[i] = 0.0; return; }
-    const float rc2 = T.rho.rcut * T.rho.rcut;
+    const float rc2 = T.rc_rho * T.rc_rho;
     float rho = 0.0f;
     const int m = nnbr[i];
     auto pair = [&](int e, const float4& q) {
         const float4 d = Ds[(unsigned)e >> kNbrShift];
         const float dx = q.x + d.x - p.x, dy = q.y + d.y - p.y, dz = q.z + d.z - p.z;
         const float r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 < rc2) {
-            float f, df;
-            poly_eval<true, false>(T.rho, sqrtf(r2), f, df, 0.0f, 0.0f);
-            rho += f;
-        }
+        if (r2 < rc2) rho += eam_zeta(T, sqrtf(r2));
     };
     // four list entries at a time: their gathers are independent and overlap in flight
     int k = 0;
@@ -140,7 +93,7 @@ __global__ void __launch_bounds__(256) k_eam_force(const float4* __restrict__ po
     const float ui = p.w, xi = uxi[i];
     const float wi = wv[i];
     const bool want_e = wi > 0.0f && wi < 1.0f;   // the same test as the blend's weight-gradient term
-    const float rc2 = T.rc * T.rc, rcr = T.rho.rcut, rcp = T.phi.rcut;
+    const float rc2 = T.rc * T.rc;
     float fx = 0.f, fy = 0.f, fz = 0.f, eph = 0.f;
     const int m = nnbr[i];
     auto pair = [&](int e, const float4& q, float xj) {
@@ -150,12 +103,9 @@ __global__ void __launch_bounds__(256) k_eam_force(const float4* __restrict__ po
         const float us = ui + q.w;
         if (r2 >= rc2 || us <= 0.0f) return;   // beyond the cutoff, or both atoms fully ACE
         const float r = sqrtf(r2), ri = 1.0f / r;
-        float zf = 0.f, dz_ = 0.f, pf = 0.f, dp = 0.f;
-        if (r < rcr) poly_eval<false, true>(T.rho, r, zf, dz_, 0.f, 0.f);
-        if (r < rcp) {
-            if (want_e) poly_eval<true, true>(T.phi, r, pf, dp, T.zbl_k, T.zbl_ainv);
-            else poly_eval<false, true>(T.phi, r, pf, dp, T.zbl_k, T.zbl_ainv);
-        }
+        float dz_, dp, pf = 0.f;
+        if (want_e) eam_pair_der<true>(T, r, dz_, dp, pf);
+        else eam_pair_der<false>(T, r, dz_, dp, pf);
         const float cr = ((xi + xj) * dz_ + 0.5f * us * dp) * ri;
         fx += cr * dx; fy += cr * dy; fz += cr * dz;
         eph += pf;
@@ -208,28 +158,40 @@ __device__ __forceinline__ void acc_add(float& hi, float& lo, float v) {
     lo = __fadd_rn(lo, e);
 }
 
-// value of the piecewise polynomial at rf + tl, added into the double-float sum (hi, lo):
-// the constant term enters as c0 (hi + lo) through TwoSum, the rest in FP32
-__device__ __forceinline__ void poly_acc_df(const PolyTab& t, float rf, float tl, float zk, float zainv, float& hi,
-                                            float& lo) {
-    int b = (int)(rf * t.bin_inv);
-    b = b < kNBin ? b : kNBin - 1;
-    int k = t.bin[b];
-    while (k + 1 < t.nint && rf >= t.start[k + 1]) ++k;
-    if (t.zbl && k == 0) {
-        const float r = rf + tl, x = r * zainv;
-        acc_add(hi, lo, zk * (0.1818f * expf(-3.2f * x) + 0.5099f * expf(-0.9423f * x) + 0.2802f * expf(-0.4029f * x) +
-                              0.02817f * expf(-0.2016f * x)) / r);
-        return;
+// zeta and Phi at rf + tl (FP32 rf, first-order correction tl), each added into its
+// double-float sum: the constant terms enter as c0 (hi + lo) through TwoSum, the rest in FP32
+__device__ __forceinline__ void pair_acc_df(const EamDev& T, float rf, float tl, bool with_z, float& zh, float& zl,
+                                            float& ph, float& pl) {
+    int sp;
+    const int k = eam_seg(T, rf, sp);
+    const EamSeg& g = T.seg[k];
+    const float4 q0 = g.q0, q1 = g.q1, q2 = g.q2;
+    const float x = __fsub_rn(rf, q0.x);            // exact: mid is an FP32 number near rf
+    if (with_z) {
+        const float u = fmaf(fmaf(q0.w, x, q0.z), x, q0.y);
+        const float d = fmaf(fmaf(3.0f * q0.w, x, 2.0f * q0.z), x, q0.y);
+        const float xu = __fmul_rn(x, u), xue = fmaf(x, u, -xu);
+        acc_add(zh, zl, q2.x);
+        acc_add(zh, zl, xu);
+        zl = __fadd_rn(zl, __fadd_rn(__fadd_rn(q2.y, xue), d * tl));
     }
-    const float x = __fsub_rn(rf, t.mid[k]);           // exact: mid is an FP32 number near rf
-    const float* c = t.c[k];
-    const float u = (((c[5] * x + c[4]) * x + c[3]) * x + c[2]) * x + c[1];   // p(x) = c0 + x u
-    const float d = (((5.0f * c[5] * x + 4.0f * c[4]) * x + 3.0f * c[3]) * x + 2.0f * c[2]) * x + c[1];
+    float c4 = 0.0f, c5 = 0.0f;
+    if (sp) {
+        const int kind = (int)q2.w;
+        if (kind == kSegZbl) {
+            const float r = rf + tl, xr = r * T.zbl_ainv;
+            acc_add(ph, pl, T.zbl_k * (0.1818f * expf(-3.2f * xr) + 0.5099f * expf(-0.9423f * xr) +
+                                       0.2802f * expf(-0.4029f * xr) + 0.02817f * expf(-0.2016f * xr)) / r);
+            return;
+        }
+        if (kind == kSegQuintic) { c4 = g.q3.x; c5 = g.q3.y; }
+    }
+    const float u = fmaf(fmaf(fmaf(fmaf(c5, x, c4), x, q1.z), x, q1.y), x, q1.x);
+    const float d = fmaf(fmaf(fmaf(fmaf(5.0f * c5, x, 4.0f * c4), x, 3.0f * q1.z), x, 2.0f * q1.y), x, q1.x);
     const float xu = __fmul_rn(x, u), xue = fmaf(x, u, -xu);
-    acc_add(hi, lo, c[0]);
-    acc_add(hi, lo, xu);
-    lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(t.c0lo[k], xue), d * tl));
+    acc_add(ph, pl, q1.w);
+    acc_add(ph, pl, xu);
+    pl = __fadd_rn(pl, __fadd_rn(__fadd_rn(q2.z, xue), d * tl));
 }
 
 __global__ void __launch_bounds__(256) k_eam_energy(const float4* __restrict__ pos4, const float4* __restrict__ pos_lo,
@@ -249,7 +211,7 @@ __global__ void __launch_bounds__(256) k_eam_energy(const float4* __restrict__ p
     const float4 p = pos4[i], pl = pos_lo[i];
     const float ui = p.w, xi = uxi[i];
     const bool own = ui > 0.0f;               // the atom has an EAM energy share
-    const float rc2 = T.rc * T.rc, rcr = T.rho.rcut, rcp = T.phi.rcut;
+    const float rc2 = T.rc * T.rc, rcr = T.rc_rho;
     float rh = 0.f, rl = 0.f, ph = 0.f, pl_ = 0.f;
     float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f, v4 = 0.f, v5 = 0.f;
     const int m = nnbr[i];
@@ -286,9 +248,8 @@ __global__ void __launch_bounds__(256) k_eam_energy(const float4* __restrict__ p
         const float rf = sqrtf(r2h);
         {
             // virial -1/2 c_ij r_ij (x) rhat_ij with the bond coefficient of the force pass
-            float zf, dz_ = 0.f, pf, dp = 0.f;
-            if (rf < rcr) poly_eval<false, true>(T.rho, rf, zf, dz_, 0.f, 0.f);
-            if (rf < rcp) poly_eval<false, true>(T.phi, rf, pf, dp, T.zbl_k, T.zbl_ainv);
+            float dz_, dp, pf;
+            eam_pair_der<false>(T, rf, dz_, dp, pf);
             const float sc = -0.5f * ((xi + uxi[j]) * dz_ + 0.5f * us * dp) / rf;
             v0 += sc * d[0] * d[0]; v1 += sc * d[1] * d[1]; v2 += sc * d[2] * d[2];
             v3 += sc * d[0] * d[1]; v4 += sc * d[0] * d[2]; v5 += sc * d[1] * d[2];
@@ -296,8 +257,7 @@ __global__ void __launch_bounds__(256) k_eam_energy(const float4* __restrict__ p
         if (!own) continue;
         const float pp = __fmul_rn(rf, rf), pe = fmaf(rf, rf, -pp);
         const float tl = __fdiv_rn(__fadd_rn(__fsub_rn(__fsub_rn(r2h, pp), pe), r2l), 2.0f * rf);
-        if (rf < rcr) poly_acc_df(T.rho, rf, tl, 0.f, 0.f, rh, rl);
-        if (rf < rcp) poly_acc_df(T.phi, rf, tl, T.zbl_k, T.zbl_ainv, ph, pl_);
+        pair_acc_df(T, rf, tl, rf < rcr, rh, rl, ph, pl_);
     }
     vir[i] = v0; vir[n + i] = v1; vir[2 * n + i] = v2; vir[3 * n + i] = v3; vir[4 * n + i] = v4; vir[5 * n + i] = v5;
     if (!own) { e_eam[i] = 0.0; return; }

@@ -19,16 +19,11 @@
 #include <vector>
 
 #include "ap_internal.h"
+#include "eam_table.h"
 
 namespace ap {
 
 namespace {
-
-struct Interval {
-    double a, b, mid;
-    double c[6];
-    int zbl;
-};
 
 // sum_i a_i (d_i - r)^3 over the knots with d_i >= b, expanded in t = r - mid
 void cubic_expand(const double* amp, const double* d, int n, double b, double mid, double* c) {
@@ -73,81 +68,73 @@ double binom(int m, int k) {
     return b;
 }
 
-int build_intervals(const ap_potential& p, int which, std::vector<Interval>& out, double& rcut, std::string& err) {
-    out.clear();
-    const double* amp = which == 0 ? p.eam_phi_a : p.eam_rho_a;
-    const double* d = which == 0 ? p.eam_phi_d : p.eam_rho_d;
-    int n = which == 0 ? p.eam_n_phi : p.eam_n_rho;
-    if (n < 1 || n > (which == 0 ? 32 : 16)) { err = "EAM: bad number of knots"; return AP_ERR_ARG; }
+// One segment of the merged partition, in FP64: zeta cubic, Phi cubic / quintic / ZBL.
+struct Seg {
+    double a, b, mid;
+    double z[4];
+    double f[6];
+    int kind;
+};
+
+int check_knots(const double* amp, const double* d, int n, int nmax, double& rcut, std::string& err) {
+    (void)amp;
+    if (n < 1 || n > nmax) { err = "EAM: bad number of knots"; return AP_ERR_ARG; }
     rcut = 0.0;
     for (int i = 0; i < n; ++i) rcut = std::max(rcut, d[i]);
     if (!(rcut > 0.0) || rcut > 20.0) { err = "EAM: knot radii must lie in (0, 20] Angstrom"; return AP_ERR_ARG; }
-    double r0 = 0.0;
-    if (which == 0 && p.eam_zbl) {
-        if (!(p.eam_r_lo > 0.0 && p.eam_r_hi > p.eam_r_lo && p.eam_r_hi < rcut)) { err = "EAM: bad r_lo/r_hi"; return AP_ERR_ARG; }
-        Interval z{};
-        z.a = 0.0; z.b = p.eam_r_lo; z.mid = 0.5 * z.b; z.zbl = 1;
-        out.push_back(z);
-        const int m_pieces = pieces(p.eam_r_lo, p.eam_r_hi);
-        for (int j = 0; j < m_pieces; ++j) {
-            Interval q{};
-            q.a = piece_edge(p.eam_r_lo, p.eam_r_hi, m_pieces, j);
-            q.b = piece_edge(p.eam_r_lo, p.eam_r_hi, m_pieces, j + 1);
-            q.mid = fp32_exact(0.5 * (q.a + q.b));
-            for (int k = 0; k <= 5; ++k)
-                for (int m = k; m <= 5; ++m) q.c[k] += p.eam_b[m] * binom(m, k) * std::pow(q.mid, m - k);
-            out.push_back(q);
-        }
-        r0 = p.eam_r_hi;
-    }
-    if (which == 1 && p.eam_rho_rclamp > 0.0) {
-        if (p.eam_rho_rclamp >= rcut) { err = "EAM: r_cut^rho beyond the density cutoff"; return AP_ERR_ARG; }
-        Interval q{};
-        q.a = 0.0; q.b = p.eam_rho_rclamp; q.mid = 0.5 * q.b;
-        q.c[0] = cubic_value(amp, d, n, p.eam_rho_rclamp);
-        out.push_back(q);
-        r0 = p.eam_rho_rclamp;
-    }
-    std::vector<double> br;
-    br.push_back(r0);
-    std::vector<double> ks(d, d + n);
-    std::sort(ks.begin(), ks.end());
-    for (double k : ks)
-        if (k > r0 && k > br.back()) br.push_back(k);
-    for (size_t k = 0; k + 1 < br.size(); ++k) {
-        const int m_pieces = pieces(br[k], br[k + 1]);
-        for (int j = 0; j < m_pieces; ++j) {
-            Interval q{};
-            q.a = piece_edge(br[k], br[k + 1], m_pieces, j);
-            q.b = piece_edge(br[k], br[k + 1], m_pieces, j + 1);
-            q.mid = fp32_exact(0.5 * (q.a + q.b));
-            cubic_expand(amp, d, n, br[k + 1], q.mid, q.c);
-            out.push_back(q);
-        }
-    }
-    if ((int)out.size() > kMaxInt) { err = "EAM: too many intervals"; return AP_ERR_ARG; }
     return AP_OK;
 }
 
-void fill_tab(const std::vector<Interval>& iv, double rcut, PolyTab& t) {
-    std::memset(&t, 0, sizeof(t));
-    t.nint = (int)iv.size();
-    t.zbl = iv.size() && iv[0].zbl ? 1 : 0;
-    t.rcut = (float)rcut;
-    t.bin_inv = (float)(kNBin / rcut);
-    for (int k = 0; k < t.nint; ++k) {
-        t.start[k] = (float)iv[k].a;
-        t.mid[k] = (float)iv[k].mid;
-        for (int c = 0; c < 6; ++c) t.c[k][c] = (float)iv[k].c[c];
-        t.c0lo[k] = (float)(iv[k].c[0] - (double)t.c[k][0]);
+// The merged partition of [0, rc): breakpoints of both functions, pieces of <= kMaxPiece.
+int build_segments(const ap_potential& p, std::vector<Seg>& out, double& rc_rho, double& rc_phi, std::string& err) {
+    out.clear();
+    int s;
+    if ((s = check_knots(p.eam_phi_a, p.eam_phi_d, p.eam_n_phi, 32, rc_phi, err))) return s;
+    if ((s = check_knots(p.eam_rho_a, p.eam_rho_d, p.eam_n_rho, 16, rc_rho, err))) return s;
+    const double rc = std::max(rc_phi, rc_rho);
+    std::vector<double> br = {0.0, rc_rho, rc_phi};
+    for (int i = 0; i < p.eam_n_phi; ++i) br.push_back(p.eam_phi_d[i]);
+    for (int i = 0; i < p.eam_n_rho; ++i) br.push_back(p.eam_rho_d[i]);
+    if (p.eam_zbl) {
+        if (!(p.eam_r_lo > 0.0 && p.eam_r_hi > p.eam_r_lo && p.eam_r_hi < rc_phi)) { err = "EAM: bad r_lo/r_hi"; return AP_ERR_ARG; }
+        br.push_back(p.eam_r_lo);
+        br.push_back(p.eam_r_hi);
     }
-    t.start[t.nint] = (float)rcut;
-    for (int b = 0; b < kNBin; ++b) {
-        float r = (float)b / t.bin_inv;
-        int k = 0;
-        while (k + 1 < t.nint && r >= t.start[k + 1]) ++k;
-        t.bin[b] = (unsigned char)k;
+    const double clamp = p.eam_rho_rclamp;
+    if (clamp > 0.0) {
+        if (clamp >= rc_rho) { err = "EAM: r_cut^rho beyond the density cutoff"; return AP_ERR_ARG; }
+        br.push_back(clamp);
     }
+    std::sort(br.begin(), br.end());
+    br.erase(std::unique(br.begin(), br.end()), br.end());
+    const double zclamp = clamp > 0.0 ? cubic_value(p.eam_rho_a, p.eam_rho_d, p.eam_n_rho, clamp) : 0.0;
+    for (size_t k = 0; k + 1 < br.size() && br[k] < rc; ++k) {
+        const int m = pieces(br[k], br[k + 1]);
+        for (int j = 0; j < m; ++j) {
+            Seg g{};
+            g.a = piece_edge(br[k], br[k + 1], m, j);
+            g.b = piece_edge(br[k], br[k + 1], m, j + 1);
+            g.mid = fp32_exact(0.5 * (g.a + g.b));
+            if (clamp > 0.0 && g.b <= clamp) g.z[0] = zclamp;
+            else if (g.a < rc_rho) {
+                double c[6];
+                cubic_expand(p.eam_rho_a, p.eam_rho_d, p.eam_n_rho, g.b, g.mid, c);
+                for (int q = 0; q < 4; ++q) g.z[q] = c[q];
+            }
+            if (p.eam_zbl && g.b <= p.eam_r_lo) {
+                g.kind = kSegZbl;
+            } else if (p.eam_zbl && g.b <= p.eam_r_hi) {
+                g.kind = kSegQuintic;
+                for (int q = 0; q <= 5; ++q)
+                    for (int e = q; e <= 5; ++e) g.f[q] += p.eam_b[e] * binom(e, q) * std::pow(g.mid, e - q);
+            } else if (g.a < rc_phi) {
+                cubic_expand(p.eam_phi_a, p.eam_phi_d, p.eam_n_phi, g.b, g.mid, g.f);
+            }
+            out.push_back(g);
+        }
+    }
+    if ((int)out.size() > kMaxSeg) { err = "EAM: too many table segments"; return AP_ERR_ARG; }
+    return AP_OK;
 }
 
 double fact(int n) {
@@ -238,37 +225,86 @@ int gaunt_values(float* out, std::string& err) {
 
 int build_eam_tables(const ap_potential& p, EamDev& out, std::string& err) {
     std::memset(&out, 0, sizeof(out));
-    std::vector<Interval> iv;
-    double rc_phi = 0.0, rc_rho = 0.0;
-    int s = build_intervals(p, 0, iv, rc_phi, err);
+    std::vector<Seg> sg;
+    double rc_rho = 0.0, rc_phi = 0.0;
+    int s = build_segments(p, sg, rc_rho, rc_phi, err);
     if (s) return s;
-    fill_tab(iv, rc_phi, out.phi);
-    s = build_intervals(p, 1, iv, rc_rho, err);
-    if (s) return s;
-    fill_tab(iv, rc_rho, out.rho);
     if (p.eam_zbl) {
         if (!(p.eam_zbl_eps0 > 0.0 && p.eam_zbl_a > 0.0)) { err = "EAM: bad ZBL parameters"; return AP_ERR_ARG; }
         out.zbl_k = (float)(p.eam_zbl_Z * p.eam_zbl_Z / (4.0 * 3.14159265358979323846 * p.eam_zbl_eps0));
         out.zbl_ainv = (float)(1.0 / p.eam_zbl_a);
     }
-    out.rc = (float)std::max(rc_phi, rc_rho);
+    const double rc = std::max(rc_rho, rc_phi);
+    out.nseg = (int)sg.size();
+    out.rc_rho = (float)rc_rho;
+    out.rc_phi = (float)rc_phi;
+    out.rc = (float)rc;
+    out.bin_inv = (float)(kNBin / rc);
+    for (int k = 0; k < out.nseg; ++k) {
+        const Seg& g = sg[k];
+        EamSeg& e = out.seg[k];
+        const float z0 = (float)g.z[0], f0 = (float)g.f[0];
+        e.q0 = make_float4((float)g.mid, (float)g.z[1], (float)g.z[2], (float)g.z[3]);
+        e.q1 = make_float4((float)g.f[1], (float)g.f[2], (float)g.f[3], f0);
+        e.q2 = make_float4(z0, (float)(g.z[0] - (double)z0), (float)(g.f[0] - (double)f0), (float)g.kind);
+        e.q3 = make_float4((float)g.f[4], (float)g.f[5], 0.0f, 0.0f);
+    }
+    // bin b holds every FP32 r with (int)(r * bin_inv) == b; its range is widened by 1 % on
+    // both sides so that rounding of that product cannot land r outside the record
+    const double binw = rc / kNBin;
+    for (int b = 0; b < kNBin; ++b) {
+        const double lo = std::max(0.0, (b - 0.01) * binw), hi = (b + 1.01) * binw;
+        int k = 0;
+        while (k + 1 < out.nseg && sg[k + 1].a <= lo) ++k;
+        EamBin& e = out.bin[b];
+        e.k = k;
+        e.s1 = e.s2 = INFINITY;
+        e.special = sg[k].kind != kSegCubic;
+        if (k + 1 < out.nseg && sg[k + 1].a < hi) {
+            e.s1 = (float)sg[k + 1].a;
+            e.special |= sg[k + 1].kind != kSegCubic;
+            if (k + 2 < out.nseg && sg[k + 2].a < hi) {
+                e.s2 = (float)sg[k + 2].a;
+                e.special |= sg[k + 2].kind != kSegCubic;
+                if (k + 3 < out.nseg && sg[k + 3].a < hi) { err = "EAM: more than two knots in one table bin"; return AP_ERR_ARG; }
+            }
+        }
+    }
+    // The device compares r >= (float)start.  Where a start is not an FP32 number the boundary
+    // moves by less than one ulp; the adjacent pieces join with continuous value and first
+    // derivative (knots of the cubic sums, the bridge joins, the piece splits), so either
+    // piece is correct there to rounding.
     out.F_a1 = p.eam_F_a1;
     out.F_a2 = p.eam_F_a2;
     out.F_dxi = p.eam_F_dxi;
     return AP_OK;
 }
 
-int eam_table_eval_fp64(const ap_potential& p, int which, double r, double* f, double* df) {
-    std::vector<Interval> iv;
-    double rcut = 0.0;
+int eam_table_eval(const ap_potential& p, int which, double r, double* f, double* df) {
+    *f = 0.0;
+    *df = 0.0;
     std::string err;
-    int s = build_intervals(p, which, iv, rcut, err);
+    if (which >= 2) {
+        EamDev T;
+        int s = build_eam_tables(p, T, err);
+        if (s) return s;
+        const float rf = (float)r;
+        if (!(rf < (which == 2 ? T.rc_phi : T.rc_rho)) || rf < 0.0f) return AP_OK;
+        float dz, dp, pf;
+        eam_pair_der<true>(T, rf, dz, dp, pf);
+        if (which == 2) { *f = pf; *df = dp; }
+        else { *f = eam_zeta(T, rf); *df = dz; }
+        return AP_OK;
+    }
+    std::vector<Seg> sg;
+    double rc_rho = 0.0, rc_phi = 0.0;
+    int s = build_segments(p, sg, rc_rho, rc_phi, err);
     if (s) return s;
-    *f = 0.0; *df = 0.0;
-    if (r >= rcut) return AP_OK;
+    if (r < 0.0 || r >= (which == 0 ? rc_phi : rc_rho)) return AP_OK;
     size_t k = 0;
-    while (k + 1 < iv.size() && r >= iv[k + 1].a) ++k;
-    if (iv[k].zbl) {
+    while (k + 1 < sg.size() && r >= sg[k + 1].a) ++k;
+    const Seg& g = sg[k];
+    if (which == 0 && g.kind == kSegZbl) {
         const double c[4] = {0.1818, 0.5099, 0.2802, 0.02817};
         const double e[4] = {3.2, 0.9423, 0.4029, 0.2016};
         double kz = p.eam_zbl_Z * p.eam_zbl_Z / (4.0 * 3.14159265358979323846 * p.eam_zbl_eps0);
@@ -278,10 +314,13 @@ int eam_table_eval_fp64(const ap_potential& p, int which, double r, double* f, d
         *df = kz * (dph / p.eam_zbl_a / r - ph / (r * r));
         return AP_OK;
     }
-    double t = r - iv[k].mid, v = 0.0, dv = 0.0;
-    for (int c = 5; c >= 0; --c) v = v * t + iv[k].c[c];
-    for (int c = 5; c >= 1; --c) dv = dv * t + c * iv[k].c[c];
-    *f = v; *df = dv;
+    const double* c = which == 0 ? g.f : g.z;
+    const int deg = which == 0 ? 5 : 3;
+    double t = r - g.mid, v = 0.0, dv = 0.0;
+    for (int q = deg; q >= 0; --q) v = v * t + c[q];
+    for (int q = deg; q >= 1; --q) dv = dv * t + q * c[q];
+    *f = v;
+    *df = dv;
     return AP_OK;
 }
 

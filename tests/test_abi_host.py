@@ -83,3 +83,30 @@ def test_footprint_estimate_scales_with_atoms(apl):
     b = _capi.lib().ap_footprint_bytes(C.byref(p), 2000, 0.1)
     # per atom: the two [25][8] FP32 ACE arrays (1600 B), the list rows and ~300 B of state
     assert 0 < a < b and 2_000_000 < (b - a) < 4_000_000
+
+
+@pytest.mark.parametrize("species", ["W", "Cu"])
+def test_fp32_device_table_lookup_matches_oracle(apl, orc, species):
+    """The FP32 table the kernels read, through their own segment lookup (one bin record and
+    two compares), on a dense grid and a few ulp either side of every breakpoint."""
+    eam = synth.eam_potential(species)
+    knots = list(eam["phi_d"]) + list(eam["rho_d"])
+    if eam.get("zbl"):
+        knots += [eam["r_lo"], eam["r_hi"]]
+    if eam.get("rho_rclamp", 0.0) > 0.0:
+        knots.append(eam["rho_rclamp"])
+    rng = np.random.default_rng(7)
+    r = [np.linspace(0.6, 5.5, 4000), rng.uniform(0.6, 5.5, 2000)]
+    for d in knots:
+        f = np.float32(d)
+        r.append(np.array([np.nextafter(f, np.float32(0) if k < 0 else np.float32(10), dtype=np.float32)
+                           if k else f for k in (-1, 0, 1)], dtype=np.float64))
+    r = np.unique(np.concatenate(r).astype(np.float32).astype(np.float64))
+    ref = orc.eam_funcs(eam, r)
+    for k, rr in enumerate(r):
+        f, df = apl.eam_table_eval(eam, 2, rr)
+        assert abs(f - ref[k, 0]) <= 2e-6 * max(1.0, abs(ref[k, 0])), (rr, f, ref[k, 0])
+        assert abs(df - ref[k, 1]) <= 2e-5 * max(1.0, abs(ref[k, 1])), (rr, df, ref[k, 1])
+        f, df = apl.eam_table_eval(eam, 3, rr)
+        assert abs(f - ref[k, 2]) <= 2e-6 * max(1.0, abs(ref[k, 2])), (rr, f, ref[k, 2])
+        assert abs(df - ref[k, 3]) <= 2e-5 * max(1.0, abs(ref[k, 3])), (rr, df, ref[k, 3])
