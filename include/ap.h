@@ -204,8 +204,13 @@ ap_status ap_get_weights(ap_ctx* ctx, double* w);
 /* Replace explicit weights (AP_REGION_EXPLICIT contexts only; host, n). */
 ap_status ap_set_weights(ap_ctx* ctx, const double* w);
 
-/* Per-stage CUDA-event timing of later calls (enable = 1) and its readout: ms[k] is
- * the accumulated time of stage k over launches[k] launches, stages AP_STAGE_*. */
+/* Per-stage CUDA-event timing of later calls and its readout: enable = 1 brackets every
+ * stage with a pair of events (about 2.5 us per stage on the stream), enable = 2 only the
+ * ACE contraction stage (the dominant kernel, for its roofline at negligible cost),
+ * enable = 0 stops.  Stepping with profiling on uses plain launches, not the captured
+ * graph.  ms[k] is the accumulated time of stage k over launches[k] launches, stages
+ * AP_STAGE_*; reading drains the pending events (synchronises).  AP_ERR_ARG for other
+ * values of enable. */
 enum { AP_STAGE_NEIGHBOR = 0, AP_STAGE_PREPARE = 1, AP_STAGE_EAM_DENSITY = 2,
        AP_STAGE_EAM_FORCE = 3, AP_STAGE_ACE = 4, AP_STAGE_BLEND = 5, AP_STAGE_INTEGRATE = 6,
        AP_STAGE_ACE_BASIS = 7, AP_STAGE_ACE_FORCE = 8, AP_NSTAGE = 9 };

@@ -159,7 +159,7 @@ struct Ctx {
     bool forces_valid = false;
     std::string err;
 
-    bool prof = false;
+    int prof = 0;                                        // 0 off, 1 every stage, 2 the ACE contraction only
     cudaEvent_t ev[2] = {nullptr, nullptr};
     double stage_ms[AP_NSTAGE] = {0};
     long long stage_n[AP_NSTAGE] = {0};

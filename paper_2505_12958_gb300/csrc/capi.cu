@@ -53,7 +53,7 @@ cudaEvent_t get_event(ap_ctx* x) {
 template <class F>
 void stage(ap_ctx* x, int st, cudaStream_t s, F&& launch) {
     ap::Ctx& c = x->c;
-    if (!c.prof) { c.launches += launch(); return; }
+    if (!c.prof || (c.prof == 2 && st != AP_STAGE_ACE)) { c.launches += launch(); return; }
     cudaEvent_t a = get_event(x), b = get_event(x);
     cudaEventRecord(a, s);
     c.launches += launch();
@@ -704,7 +704,8 @@ ap_status ap_set_weights(ap_ctx* xc, const double* w) {
 
 ap_status ap_profile(ap_ctx* xc, int enable) {
     if (!xc) return AP_ERR_ARG;
-    xc->c.prof = enable != 0;
+    if (enable < 0 || enable > 2) return AP_ERR_ARG;
+    xc->c.prof = enable;
     return AP_OK;
 }
 

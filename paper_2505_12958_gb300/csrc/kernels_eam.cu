@@ -15,6 +15,17 @@ namespace ap {
 
 namespace {
 
+// list entries whose gathers are issued together per thread, and the block size of the
+// thread-per-atom EAM kernels (tuning constants; results do not depend on them)
+#ifndef AP_EAM_BATCH
+#define AP_EAM_BATCH 4
+#endif
+#ifndef AP_EAM_BLOCK
+#define AP_EAM_BLOCK 128
+#endif
+constexpr int kEamBatch = AP_EAM_BATCH;
+constexpr int kEamBlock = AP_EAM_BLOCK;
+
 __device__ __forceinline__ void stage_tables(EamDev* sm, const EamDev* __restrict__ gm, float4* Ds,
                                              const float4* __restrict__ D, int ncode) {
     const int4* src = reinterpret_cast<const int4*>(gm);
@@ -24,7 +35,7 @@ __device__ __forceinline__ void stage_tables(EamDev* sm, const EamDev* __restric
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) k_eam_density(const float4* __restrict__ pos4, const int* __restrict__ nbr,
+__global__ void __launch_bounds__(kEamBlock) k_eam_density(const float4* __restrict__ pos4, const int* __restrict__ nbr,
                                                      const int* __restrict__ nnbr, int n, const EamDev* __restrict__ eam,
                                                      const float4* __restrict__ D, int ncode, float* __restrict__ uxi,
                                                      double* __restrict__ e_emb, int* __restrict__ flags) {
@@ -48,15 +59,15 @@ __global__ void __launch_bounds__(256) k_eam_density(const float4* __restrict__ 
     };
     // four list entries at a time: their gathers are independent and overlap in flight
     int k = 0;
-    for (; k + 4 <= m; k += 4) {
-        int e[4];
-        float4 q[4];
+    for (; k + kEamBatch <= m; k += kEamBatch) {
+        int e[kEamBatch];
+        float4 q[kEamBatch];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) e[u] = nbr[(size_t)(k + u) * n + i];
+        for (int u = 0; u < kEamBatch; ++u) e[u] = nbr[(size_t)(k + u) * n + i];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) q[u] = pos4[e[u] & kNbrMask];
+        for (int u = 0; u < kEamBatch; ++u) q[u] = pos4[e[u] & kNbrMask];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) pair(e[u], q[u]);
+        for (int u = 0; u < kEamBatch; ++u) pair(e[u], q[u]);
     }
     for (; k < m; ++k) {
         const int e = nbr[(size_t)k * n + i];
@@ -79,7 +90,7 @@ __global__ void __launch_bounds__(256) k_eam_density(const float4* __restrict__ 
 // per step: EAM forces.  The pair value Phi is needed only for the FP32 estimate of E_i^EAM
 // that the weight-gradient force of transition atoms (0 < w < 1) uses; exact energies and
 // the virial come from the on-request energy pass.
-__global__ void __launch_bounds__(256) k_eam_force(const float4* __restrict__ pos4, const int* __restrict__ nbr,
+__global__ void __launch_bounds__(kEamBlock) k_eam_force(const float4* __restrict__ pos4, const int* __restrict__ nbr,
                                                    const int* __restrict__ nnbr, int n, const EamDev* __restrict__ eam,
                                                    const float4* __restrict__ D, int ncode, const float* __restrict__ uxi,
                                                    const double* __restrict__ e_emb, const float* __restrict__ wv,
@@ -111,20 +122,20 @@ __global__ void __launch_bounds__(256) k_eam_force(const float4* __restrict__ po
         eph += pf;
     };
     int k = 0;
-    for (; k + 4 <= m; k += 4) {
-        int e[4];
-        float4 q[4];
-        float xj[4];
+    for (; k + kEamBatch <= m; k += kEamBatch) {
+        int e[kEamBatch];
+        float4 q[kEamBatch];
+        float xj[kEamBatch];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) e[u] = nbr[(size_t)(k + u) * n + i];
+        for (int u = 0; u < kEamBatch; ++u) e[u] = nbr[(size_t)(k + u) * n + i];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kEamBatch; ++u) {
             const int j = e[u] & kNbrMask;
             q[u] = pos4[j];
             xj[u] = uxi[j];
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) pair(e[u], q[u], xj[u]);
+        for (int u = 0; u < kEamBatch; ++u) pair(e[u], q[u], xj[u]);
     }
     for (; k < m; ++k) {
         const int e = nbr[(size_t)k * n + i];
@@ -276,13 +287,13 @@ int launch_eam_energy(Ctx& c, cudaStream_t s) {
 }
 
 int launch_eam_density(Ctx& c, cudaStream_t s) {
-    k_eam_density<<<(c.n + 255) / 256, 256, 0, s>>>(c.pos4, c.nbr, c.nnbr, c.n, c.eam_d, c.D, c.grid.ncode, c.uxi,
+    k_eam_density<<<(c.n + kEamBlock - 1) / kEamBlock, kEamBlock, 0, s>>>(c.pos4, c.nbr, c.nnbr, c.n, c.eam_d, c.D, c.grid.ncode, c.uxi,
                                                    c.e_emb, c.flags);
     return 1;
 }
 
 int launch_eam_force(Ctx& c, cudaStream_t s) {
-    k_eam_force<<<(c.n + 255) / 256, 256, 0, s>>>(c.pos4, c.nbr, c.nnbr, c.n, c.eam_d, c.D, c.grid.ncode, c.uxi,
+    k_eam_force<<<(c.n + kEamBlock - 1) / kEamBlock, kEamBlock, 0, s>>>(c.pos4, c.nbr, c.nnbr, c.n, c.eam_d, c.D, c.grid.ncode, c.uxi,
                                                  c.e_emb, c.w, c.f, c.e_eam);
     return 1;
 }
