@@ -78,6 +78,7 @@ struct GridDev {
     float rlist2;
     int ortho;                // edge vectors along x, y, z
     double L[3], Linv[3];     // edge lengths (orthorhombic boxes)
+    float Lf[3], Linvf[3];    // the same in FP32 (pre-tests only)
 };
 
 struct DynDev {               // time-dependent geometry; time is read from device memory
@@ -89,6 +90,10 @@ struct DynDev {               // time-dependent geometry; time is read from devi
     int pad;
     double ind_c0[3], ind_vel[3], ind_dir[3];
     double R, K;
+    // FP32 pre-tests (orthorhombic boxes): below reg_in2_lo an atom is surely inside the
+    // inner radius, above reg_out2_hi surely outside the shell, above ind_R2_hi surely
+    // outside the indenter; squared radii with a 1e-5 relative margin
+    float reg_in2_lo, reg_out2_hi, ind_R2_hi, pad2;
 };
 
 enum : int { kFlagRebuild = 0, kFlagNAce = 1, kFlagErr = 2, kFlagBad = 3, kFlagMaxNbr = 4, kFlagRebuilds = 5, kFlagCount = 8 };

@@ -17,8 +17,10 @@ struct ap_ctx {
     struct Pending { int stage; cudaEvent_t a, b; };
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> free_ev;
-    // one captured MD step (kick-drift, force evaluation, kick), replayed by ap_step
+    // captured MD steps (kick-drift, force evaluation, kick), replayed by ap_step: one step,
+    // and kStepBlock steps in one graph for long runs (one launch instead of kStepBlock)
     cudaGraphExec_t step_exec = nullptr;
+    cudaGraphExec_t block_exec = nullptr;
     cudaStream_t step_stream = nullptr;
     double step_dt = 0.0;
     long long step_kernels = 0;
@@ -49,11 +51,30 @@ cudaEvent_t get_event(ap_ctx* x) {
     return e;
 }
 
+// fold the completed stage events at the front of the pending list into the totals and
+// recycle them (no waiting), so that long profiled runs create no new events
+void drain_ready(ap_ctx* x) {
+    ap::Ctx& c = x->c;
+    size_t k = 0;
+    for (; k < x->pending.size(); ++k) {
+        auto& p = x->pending[k];
+        if (cudaEventQuery(p.b) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        c.stage_ms[p.stage] += ms;
+        c.stage_n[p.stage] += 1;
+        x->free_ev.push_back(p.a);
+        x->free_ev.push_back(p.b);
+    }
+    x->pending.erase(x->pending.begin(), x->pending.begin() + k);
+}
+
 // run one stage; with profiling on, bracket it with events on the same stream
 template <class F>
 void stage(ap_ctx* x, int st, cudaStream_t s, F&& launch) {
     ap::Ctx& c = x->c;
     if (!c.prof || (c.prof == 2 && st != AP_STAGE_ACE)) { c.launches += launch(); return; }
+    if (x->pending.size() >= 64) drain_ready(x);
     cudaEvent_t a = get_event(x), b = get_event(x);
     cudaEventRecord(a, s);
     c.launches += launch();
@@ -61,9 +82,13 @@ void stage(ap_ctx* x, int st, cudaStream_t s, F&& launch) {
     x->pending.push_back({st, a, b});
 }
 
+constexpr int kStepBlock = 8;
+
 void drop_step_graph(ap_ctx* x) {
     if (x->step_exec) cudaGraphExecDestroy(x->step_exec);
+    if (x->block_exec) cudaGraphExecDestroy(x->block_exec);
     x->step_exec = nullptr;
+    x->block_exec = nullptr;
 }
 
 void drain_events(ap_ctx* x) {
@@ -126,6 +151,8 @@ ap_status setup_grid(ap::Ctx& c, const ap_box& box, std::vector<float4>& D, std:
     for (int d = 0; d < 3; ++d) {
         g.L[d] = g.h[4 * d];
         g.Linv[d] = 1.0 / g.h[4 * d];
+        g.Lf[d] = (float)g.L[d];
+        g.Linvf[d] = (float)g.Linv[d];
     }
     g.ncell = (int)ncell;
     g.ncode = (2 * g.S[0] + 1) * (2 * g.S[1] + 1) * (2 * g.S[2] + 1);
@@ -371,6 +398,12 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
         dy.R = ind->R;
         dy.K = ind->K;
     }
+    {
+        const double ri = dy.r_in * (1.0 - 1e-5), ro = (dy.r_in + dy.r_sw) * (1.0 + 1e-5), rr = dy.R * (1.0 + 1e-5);
+        dy.reg_in2_lo = (float)(ri * ri);
+        dy.reg_out2_hi = (float)(ro * ro);
+        dy.ind_R2_hi = (float)(rr * rr);
+    }
 
     // device memory
     const size_t N = (size_t)n;
@@ -506,30 +539,46 @@ ap_status ap_step(ap_ctx* xc, int n_steps, double dt, void* stream) {
         return cuda_check(c, cudaGetLastError(), "ap_step");
     }
     if (xc->step_exec && (xc->step_stream != s || xc->step_dt != dt || xc->step_gen != c.layout_gen)) drop_step_graph(xc);
-    if (!xc->step_exec) {
+    // capture k steps on s as one graph
+    auto capture = [&](int k, cudaGraphExec_t* out) -> cudaError_t {
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return cuda_check(c, e, "ap_step capture");
+        if (e != cudaSuccess) return e;
         const long long before = c.launches;
-        c.launches += ap::launch_kick_drift(c, s, dt, 1);
-        run_forces(xc, s, nullptr);
-        c.launches += ap::launch_kick(c, s, dt);
-        xc->step_kernels = c.launches - before;
+        for (int q = 0; q < k; ++q) {
+            c.launches += ap::launch_kick_drift(c, s, dt, 1);
+            run_forces(xc, s, nullptr);
+            c.launches += ap::launch_kick(c, s, dt);
+        }
+        xc->step_kernels = (c.launches - before) / k;
         c.launches = before;
         e = cudaStreamEndCapture(s, &g);
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&xc->step_exec, g, 0);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
         if (g) cudaGraphDestroy(g);
-        if (e != cudaSuccess) { xc->step_exec = nullptr; return cuda_check(c, e, "ap_step graph"); }
+        if (e != cudaSuccess) *out = nullptr;
+        return e;
+    };
+    if (!xc->step_exec) {
+        cudaError_t e = capture(1, &xc->step_exec);
+        if (e != cudaSuccess) return cuda_check(c, e, "ap_step graph");
         xc->step_stream = s;
         xc->step_dt = dt;
         xc->step_gen = c.layout_gen;
     }
-    for (int k = 0; k < n_steps; ++k) {
-        cudaError_t e = cudaGraphLaunch(xc->step_exec, s);
+    if (n_steps >= kStepBlock && !xc->block_exec) {
+        cudaError_t e = capture(kStepBlock, &xc->block_exec);
+        if (e != cudaSuccess) return cuda_check(c, e, "ap_step graph");
+    }
+    int left = n_steps;
+    while (left > 0) {
+        const bool block = left >= kStepBlock && xc->block_exec;
+        const int k = block ? kStepBlock : 1;
+        cudaError_t e = cudaGraphLaunch(block ? xc->block_exec : xc->step_exec, s);
         if (e != cudaSuccess) return cuda_check(c, e, "ap_step launch");
-        c.launches += xc->step_kernels;
-        c.t += dt;
-        c.step += 1;
+        c.launches += xc->step_kernels * k;
+        c.t += dt * k;
+        c.step += k;
+        left -= k;
     }
     c.forces_valid = true;
     c.energy_fresh = false;

@@ -70,11 +70,13 @@ __global__ void __launch_bounds__(kRedBlock) k_blend(
         if (dy.ind_on) {
             double d[3];
             for (int k = 0; k < 3; ++k) d[k] = r[k] - (dy.ind_c0[k] - dy.ind_vel[k] * t);
-            min_image_vec(g, d);
-            const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-            if (d2 < dy.R * dy.R && d2 > 0.0) {
-                const double dist = sqrt(d2), h = dy.R - dist, c = dy.K * h * h / dist;
-                for (int k = 0; k < 3; ++k) F[k] += (float)(c * d[k]);
+            if (!g.ortho || min_image_d2_f32(g, d) < dy.ind_R2_hi) {
+                min_image_vec(g, d);
+                const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                if (d2 < dy.R * dy.R && d2 > 0.0) {
+                    const double dist = sqrt(d2), h = dy.R - dist, c = dy.K * h * h / dist;
+                    for (int k = 0; k < 3; ++k) F[k] += (float)(c * d[k]);
+                }
             }
         }
     }

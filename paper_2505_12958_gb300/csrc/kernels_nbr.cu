@@ -131,8 +131,12 @@ __global__ void k_prepare(const double* __restrict__ x, int n, const GridDev g, 
         int cc[3];
         cell_coords(g, cell[i], cc);
         double o[3];
-        for (int q = 0; q < 3; ++q)
-            o[q] = g.origin[q] + cc[0] * g.cellvec[q] + cc[1] * g.cellvec[3 + q] + cc[2] * g.cellvec[6 + q];
+        if (g.ortho) {
+            for (int q = 0; q < 3; ++q) o[q] = g.origin[q] + cc[q] * g.cellvec[4 * q];
+        } else {
+            for (int q = 0; q < 3; ++q)
+                o[q] = g.origin[q] + cc[0] * g.cellvec[q] + cc[1] * g.cellvec[3 + q] + cc[2] * g.cellvec[6 + q];
+        }
         if (dy.reg_kind == AP_REGION_CONST) {
             w = dy.w_const;
             u = (float)(1.0 - w);
@@ -143,9 +147,18 @@ __global__ void k_prepare(const double* __restrict__ x, int n, const GridDev g, 
             const double t = *tptr;
             double d[3];
             for (int q = 0; q < 3; ++q) d[q] = r[q] - (dy.reg_c0[q] - (dy.follow ? dy.ind_vel[q] * t : 0.0));
-            min_image_vec(g, d);
-            float dS;
-            w = switch_weight(d[0] * d[0] + d[1] * d[1] + d[2] * d[2], dy.r_in, dy.r_sw, &u, &dS);
+            const float d2f = g.ortho ? min_image_d2_f32(g, d) : -1.0f;
+            if (d2f >= 0.0f && d2f < dy.reg_in2_lo) {
+                w = 1.0;
+                u = 0.0f;
+            } else if (d2f > dy.reg_out2_hi) {
+                w = 0.0;
+                u = 1.0f;
+            } else {
+                min_image_vec(g, d);
+                float dS;
+                w = switch_weight(d[0] * d[0] + d[1] * d[1] + d[2] * d[2], dy.r_in, dy.r_sw, &u, &dS);
+            }
         }
         const double rel[3] = {r[0] - o[0], r[1] - o[1], r[2] - o[2]};
         const float hx = (float)rel[0], hy = (float)rel[1], hz = (float)rel[2];
