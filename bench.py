@@ -360,6 +360,34 @@ def autograd_bench(torch, ap, n_cells=256, seed=1004):
     return out
 
 
+def csp_timing(torch, ap, c, reps=20):
+    """CSP-driven weights on the timed workload: one CSP evaluation (ap_csp_accumulate) and
+    one weight update (ap_csp_update_weights, block average, zone, spatial spread), CUDA
+    events on the launch stream; the paper updates the weights every 110 steps."""
+    n = len(c["x"])
+    reg = c["region"]
+    p = {"n_nb": 14, "rc": 3.8, "zone_center": reg["center"], "zone_r": reg["r_in"]}
+    ctx = ap.APContext(c["eam"], c["ace"], c["box"], c["x"], c["v"], c["fixed"], {"kind": "explicit", "w": np.zeros(n)},
+                       c["indenter"], c["ind_vel"], c["mass"])
+    ctx.step(3, 1.0)
+    ctx.csp_accumulate(p)
+    ctx.csp_update_weights(p)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        ctx.csp_accumulate(p)
+    b.record()
+    torch.cuda.synchronize()
+    acc_ms = a.elapsed_time(b) / reps
+    t = time.perf_counter()
+    ns = ctx.csp_update_weights(p)
+    upd_ms = 1e3 * (time.perf_counter() - t)
+    ctx.close()
+    return {"atoms": n, "csp_ms": acc_ms, "update_ms_incl_sync": upd_ms, "seeds": ns,
+            "per_step_share_at_every_step": acc_ms / 1.0, "n_nb": 14, "rc": 3.8}
+
+
 def neighbors_in_ace_cutoff(c):
     """Neighbour counts within the ACE cutoff of the atoms with w > 0 (host, for the flop count)."""
     from scipy.spatial import cKDTree
@@ -486,6 +514,7 @@ def main():
         cv.close()
 
     serving = serving_bench(torch, args.serve_requests) if args.serve_requests > 0 else None
+    csp = csp_timing(torch, ap, c)
 
     if rank != 0:
         return
@@ -502,6 +531,8 @@ def main():
             "wall_s_timed_region": wall}
     if serving is not None:
         line["serving"] = serving
+    csp["per_step_share_at_every_step"] = csp["csp_ms"] / line["ms_per_step"]
+    line["csp_weights"] = csp
     line.update(extra)
     if "ace_only" in extra:
         line["ap_vs_ace_speedup"] = value / extra["ace_only"]["value"]

@@ -181,6 +181,35 @@ ap_status ap_step_batch(ap_ctx* const* ctxs, const int* n_steps, int n_ctx, doub
  * returns the first error. */
 ap_status ap_compute_forces_batch(ap_ctx* const* ctxs, int n_ctx);
 
+/* CSP-driven switching weights (Sec. 2.2.3, the switching function of Appendix B with
+ * the parameters of Tab. model_parameters_tungsten).  The centro-symmetry parameter of atom
+ * i is the sum of the n_nb/2 smallest |R_j + R_k|^2 over pairs of its n_nb nearest
+ * neighbours within rc (fewer than n_nb there: a surface atom).  ap_csp_accumulate adds the
+ * CSP of the current positions to per-atom block sums (d_csp: optional device copy, n FP32,
+ * -1 for surface atoms); ap_csp_update_weights turns the block averages into weights and
+ * starts a new block (the paper averages over 110 steps):
+ *   w0 = clamp((CSP - csp_lo) / (csp_hi - csp_lo), 0, 1);  w0 = 1 inside the precise zone
+ *   (|r - zone_center| < zone_r, nearest image); w0 = 0 for surface atoms outside it;
+ *   w_i = max_j w0_j T(|r_ij|), T = 1 for r <= r_lo, cos^2(pi (r - r_lo) / (2 (r_hi - r_lo)))
+ *   below r_hi, 0 beyond; the stored weight changes only where |w_new - w| >= dlam_min.
+ * The w0 map, the spatial form and the hysteresis are this library's readings (the paper
+ * names the parameters; the map is in its cited AP work).  The context must use
+ * AP_REGION_EXPLICIT; the weights act from the next force evaluation.  rc must not exceed
+ * the neighbour-list cutoff.  *n_seeds (nullable) receives the number of atoms with w0 > 0.
+ * AP_ERR_ARG on bad parameters, AP_ERR_STATE for a non-explicit context or an empty block.
+ * ap_csp_update_weights synchronises. */
+typedef struct {
+    int n_nb;                  /* 12 (FCC) or 14 (BCC: the first two shells) */
+    double rc;                 /* CSP neighbour cutoff, between shells n_nb and n_nb + 1 (A) */
+    double csp_lo, csp_hi;     /* A^2 (the paper: 1.5, 1.6) */
+    double r_lo, r_hi;         /* spatial transition (A; the paper: 4, 12) */
+    double dlam_min;           /* smallest applied change of a weight (the paper: 0.01) */
+    double zone_center[3];     /* precise zone, w0 = 1 inside */
+    double zone_r;
+} ap_csp_params;
+ap_status ap_csp_accumulate(ap_ctx* ctx, const ap_csp_params* p, float* d_csp);
+ap_status ap_csp_update_weights(ap_ctx* ctx, const ap_csp_params* p, int* n_seeds);
+
 /* Totals of the last force evaluation; d_e_atom (device, n FP64, nullable) receives
  * the per-atom energies E_i + V_ind(r_i).  Synchronises; returns sticky device errors. */
 ap_status ap_energy(ap_ctx* ctx, ap_report* out, double* d_e_atom);
@@ -199,7 +228,8 @@ ap_status ap_set_state(ap_ctx* ctx, const double* x, const double* v, double t_f
 ap_status ap_set_box(ap_ctx* ctx, const ap_box* box);
 /* Host copy of the last forces (n x 3 FP32). */
 ap_status ap_get_forces(ap_ctx* ctx, float* f);
-/* Host copy of the current weights w_i (n FP64). */
+/* Host copy of the weights w_i (n FP64) of the last force evaluation; weights set by
+ * ap_set_weights or ap_csp_update_weights appear after the next evaluation. */
 ap_status ap_get_weights(ap_ctx* ctx, double* w);
 /* Replace explicit weights (AP_REGION_EXPLICIT contexts only; host, n). */
 ap_status ap_set_weights(ap_ctx* ctx, const double* w);

@@ -95,6 +95,8 @@ def lib():
         L.or_md.argtypes = [C.POINTER(System), C.POINTER(EAM), C.POINTER(ACE), C.POINTER(Region),
                             C.POINTER(Indenter), PD, I, PU8, D, D, I, I, PD, PD, PD, PD]
         L.or_num_threads.restype = I
+        L.or_csp.restype = I
+        L.or_csp.argtypes = [C.POINTER(System), I, D, PD, PI]
         _lib = L
     return _lib
 
@@ -321,6 +323,63 @@ def md(x, v, box, eam, ace, region, indenter, ind_vel, fixed, mass, dt, nsteps,
                  int(nsteps), int(nthreads), _pd(x), _pd(v), _pd(ep), _pd(ek))
     del rkeep
     return x, v, ep, ek, st
+
+
+def csp(x, box, n_nb, rc):
+    """Centro-symmetry parameter per atom (or_csp): the sum of the n_nb/2 smallest
+    |R_j + R_k|^2 over pairs of the n_nb nearest neighbours within rc; -1 for atoms with
+    fewer than n_nb neighbours there.  Returns (csp, coordination within rc)."""
+    L = lib()
+    sysd, xk = make_system(x, box)
+    n = sysd.n
+    out = np.zeros(n)
+    coord = np.zeros(n, dtype=np.int32)
+    st = L.or_csp(C.byref(sysd), int(n_nb), float(rc), _pd(out), coord.ctypes.data_as(PI))
+    del xk
+    if st != 0:
+        raise ValueError("or_csp: bad arguments")
+    return out, coord
+
+
+def csp_weights(x, box, csp_blocks, p, w_old):
+    """CSP-driven switching weights (the switching function of Appendix B, Sec. 2.2.3), the
+    library's stated reading written out with numpy:
+      block average of the CSP evaluations of each atom (csp_blocks: list of per-atom CSP
+      arrays, -1 = surface); an atom is a surface atom when more than half of them are -1
+      (or all); w0 = clamp((avg - csp_lo)/(csp_hi - csp_lo), 0, 1); w0 = 1 inside the zone
+      |r - zone_center| < zone_r (nearest image); w0 = 0 for surface atoms outside it;
+      w_i = max_j w0_j T(|r_ij|) over all j (itself included) and every periodic image,
+      T = 1 for r <= r_lo, cos^2(pi (r - r_lo) / (2 (r_hi - r_lo))) below r_hi, else 0;
+      w_i keeps its old value unless |w_new - w_old| >= dlam_min.
+    Returns (w, w0)."""
+    x = _f64(x).reshape(-1, 3)
+    n = len(x)
+    blocks = np.asarray(csp_blocks, dtype=np.float64).reshape(-1, n)
+    under = (blocks < 0).sum(axis=0)
+    nacc = blocks.shape[0]
+    with np.errstate(invalid="ignore", divide="ignore"):
+        avg = np.where(blocks < 0, 0.0, blocks).sum(axis=0) / (nacc - under)
+    t = (avg - p["csp_lo"]) / (p["csp_hi"] - p["csp_lo"])
+    w0 = np.clip(np.nan_to_num(t, nan=0.0), 0.0, 1.0)
+    surface = (2 * under > nacc) | (under == nacc)
+    w0[surface] = 0.0
+    h = np.asarray(box["h"], dtype=np.float64).reshape(3, 3)
+    d = x - np.asarray(p["zone_center"], dtype=np.float64)
+    s = d @ np.linalg.inv(h)
+    for k in range(3):
+        if box["periodic"][k]:
+            s[:, k] -= np.floor(s[:, k] + 0.5)
+    d = s @ h
+    zone = (d * d).sum(axis=1) < p["zone_r"] ** 2
+    w0[zone] = 1.0
+    w = w0.copy()
+    pi, pj, rv = neighbors(x, box, p["r_hi"])
+    r = np.sqrt((rv * rv).sum(axis=1))
+    T = np.where(r <= p["r_lo"], 1.0, np.cos(0.5 * np.pi * (r - p["r_lo"]) / (p["r_hi"] - p["r_lo"])) ** 2)
+    T[r >= p["r_hi"]] = 0.0
+    np.maximum.at(w, pi, w0[pj] * T)
+    w_old = np.asarray(w_old, dtype=np.float64)
+    return np.where(np.abs(w - w_old) >= p["dlam_min"], w, w_old), w0
 
 
 def num_threads():

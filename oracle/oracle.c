@@ -763,3 +763,63 @@ int or_md(const or_system* sys0, const or_eam* eam, const or_ace* ace,
     free(F);
     return status;
 }
+
+/* ------------------------------------------------------------------------- */
+/* centro-symmetry parameter                                                   */
+/* ------------------------------------------------------------------------- */
+static int cmp_double(const void* a, const void* b) {
+    double x = *(const double*)a, y = *(const double*)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+typedef struct { double r2; double r[3]; } nbv_t;
+static int cmp_nbv(const void* a, const void* b) {
+    double x = ((const nbv_t*)a)->r2, y = ((const nbv_t*)b)->r2;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+int or_csp(const or_system* sys, int n_nb, double rc, double* csp, int* coord) {
+    if (n_nb < 2 || n_nb > 16 || (n_nb & 1) || !(rc > 0.0)) return -1;
+    grid_t G;
+    grid_build(&G, sys, rc);
+    const int N = sys->n;
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int i = 0; i < N; ++i) {
+        long m = grid_visit(&G, i, rc, NULL, NULL);
+        int* jj = (int*)malloc(sizeof(int) * (m > 0 ? m : 1));
+        double* rr = (double*)malloc(sizeof(double) * 3 * (m > 0 ? m : 1));
+        nlist_t L = {jj, rr, 0, m};
+        grid_visit(&G, i, rc, nl_push, &L);
+        if (coord) coord[i] = (int)m;
+        if (m < n_nb) {
+            csp[i] = -1.0;
+        } else {
+            /* the n_nb nearest */
+            nbv_t* v = (nbv_t*)malloc(sizeof(nbv_t) * m);
+            for (long q = 0; q < m; ++q) {
+                for (int k = 0; k < 3; ++k) v[q].r[k] = rr[3 * q + k];
+                v[q].r2 = rr[3 * q] * rr[3 * q] + rr[3 * q + 1] * rr[3 * q + 1] + rr[3 * q + 2] * rr[3 * q + 2];
+            }
+            qsort(v, (size_t)m, sizeof(nbv_t), cmp_nbv);
+            /* all pairs, the n_nb/2 smallest |R_j + R_k|^2 */
+            const int np = n_nb * (n_nb - 1) / 2;
+            double* ps = (double*)malloc(sizeof(double) * np);
+            int c = 0;
+            for (int a = 0; a < n_nb; ++a)
+                for (int b = a + 1; b < n_nb; ++b) {
+                    double s0 = v[a].r[0] + v[b].r[0], s1 = v[a].r[1] + v[b].r[1], s2 = v[a].r[2] + v[b].r[2];
+                    ps[c++] = s0 * s0 + s1 * s1 + s2 * s2;
+                }
+            qsort(ps, (size_t)np, sizeof(double), cmp_double);
+            double sum = 0.0;
+            for (int q = 0; q < n_nb / 2; ++q) sum += ps[q];
+            csp[i] = sum;
+            free(ps);
+            free(v);
+        }
+        free(jj);
+        free(rr);
+    }
+    grid_free(&G);
+    return 0;
+}

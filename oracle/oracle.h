@@ -135,6 +135,14 @@ int or_md(const or_system* sys, const or_eam* eam, const or_ace* ace,
           int region_follows, const unsigned char* fixed, double mass, double dt,
           int nsteps, int nthreads, double* x, double* v, double* epot, double* ekin);
 
+/* Centro-symmetry parameter, as the switching function of Appendix B uses it (Sec. 2.2.3):
+ * for atom i the n_nb nearest neighbours within rc (n_nb = 12 for FCC, 14 for BCC: the
+ * first two BCC shells), every pair (j, k) of them gives |R_j + R_k|^2, and the CSP is
+ * the sum of the n_nb/2 smallest.  An atom with fewer than n_nb neighbours within rc
+ * (a surface atom) gets -1.  coord (nullable) receives the neighbour count within rc.
+ * n_nb even, 2 <= n_nb <= 16.  Returns 0, or -1 on bad arguments. */
+int or_csp(const or_system* sys, int n_nb, double rc, double* csp, int* coord);
+
 int or_num_threads(void);
 
 #ifdef __cplusplus

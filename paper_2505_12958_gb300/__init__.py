@@ -230,6 +230,20 @@ class APContext:
         self._chk(self._L.ap_profile_read(self._h, ms, nl))
         return {s: (ms[k], nl[k]) for k, s in enumerate(STAGES)}
 
+    def csp_accumulate(self, params, out=None):
+        """Add the CSP of the current positions to the block sums (ap_csp_accumulate); out: an
+        optional (n,) float32 CUDA tensor receiving this evaluation's CSP (-1: surface atom)."""
+        p = csp_params(params)
+        self._chk(self._L.ap_csp_accumulate(self._h, C.byref(p), _ptr(out)))
+        return out
+
+    def csp_update_weights(self, params):
+        """Weights from the block-averaged CSP (ap_csp_update_weights); returns the seed count."""
+        p = csp_params(params)
+        ns = C.c_int()
+        self._chk(self._L.ap_csp_update_weights(self._h, C.byref(p), C.byref(ns)))
+        return ns.value
+
     def memory_bytes(self):
         """Device bytes this context holds (ap_memory_bytes)."""
         return int(self._L.ap_memory_bytes(self._h))
@@ -260,6 +274,27 @@ class APContext:
 
     def __exit__(self, *a):
         self.close()
+
+
+# switching-function parameters of Appendix B (Tab. model_parameters_tungsten)
+CSP_PAPER = {"csp_lo": 1.5, "csp_hi": 1.6, "r_lo": 4.0, "r_hi": 12.0, "dlam_min": 0.01, "n_avg": 110}
+
+
+def csp_params(d):
+    """ap_csp_params from a dict: n_nb, rc, zone_center, zone_r, and csp_lo, csp_hi, r_lo,
+    r_hi, dlam_min (defaults: the paper's values)."""
+    p = _capi.CspParams()
+    p.n_nb = int(d["n_nb"])
+    p.rc = float(d["rc"])
+    p.csp_lo = float(d.get("csp_lo", CSP_PAPER["csp_lo"]))
+    p.csp_hi = float(d.get("csp_hi", CSP_PAPER["csp_hi"]))
+    p.r_lo = float(d.get("r_lo", CSP_PAPER["r_lo"]))
+    p.r_hi = float(d.get("r_hi", CSP_PAPER["r_hi"]))
+    p.dlam_min = float(d.get("dlam_min", CSP_PAPER["dlam_min"]))
+    for k in range(3):
+        p.zone_center[k] = float(d.get("zone_center", (0.0, 0.0, 0.0))[k])
+    p.zone_r = float(d.get("zone_r", 0.0))
+    return p
 
 
 def step_batch(ctxs, n_steps, dt):

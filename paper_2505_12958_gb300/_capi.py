@@ -51,6 +51,12 @@ class Report(C.Structure):
 _lib = None
 
 
+class CspParams(C.Structure):
+    _fields_ = [("n_nb", C.c_int), ("rc", C.c_double), ("csp_lo", C.c_double), ("csp_hi", C.c_double),
+                ("r_lo", C.c_double), ("r_hi", C.c_double), ("dlam_min", C.c_double),
+                ("zone_center", C.c_double * 3), ("zone_r", C.c_double)]
+
+
 def lib():
     """Load libapforce.so; raise if it has not been built (there is no fallback path)."""
     global _lib
@@ -68,6 +74,8 @@ def lib():
         "ap_step": (I, [VP, I, D, VP]),
         "ap_step_batch": (I, [C.POINTER(VP), PI, I, D]),
         "ap_compute_forces_batch": (I, [C.POINTER(VP), I]),
+        "ap_csp_accumulate": (I, [VP, P(CspParams), VP]),
+        "ap_csp_update_weights": (I, [VP, P(CspParams), PI]),
         "ap_memory_bytes": (C.c_size_t, [VP]),
         "ap_energy": (I, [VP, P(Report), VP]),
         "ap_check": (I, [VP]),

@@ -70,6 +70,7 @@ struct GridDev {
     double h[9];              // edge vectors as rows
     double hinv[9];           // s = (r - origin) . hinv gives fractional coordinates
     double cellvec[9];        // h rows / n_d
+    double cw[3];             // perpendicular width of a cell along each edge
     int periodic[3];
     int nc[3];
     int S[3];
@@ -150,6 +151,11 @@ struct Ctx {
     double* partials = nullptr;
     double* totals = nullptr;                            // 16 doubles
     double* e_atom = nullptr;
+    double* csp_sum = nullptr;                           // CSP block sums (valid evaluations)
+    int* csp_under = nullptr;                            // evaluations that found a surface atom
+    float *csp_w0 = nullptr, *csp_wnew = nullptr;
+    int *csp_seeds = nullptr, *csp_nseed = nullptr;
+    int csp_nacc = 0;                                    // evaluations in the current block
     double* pos_stage = nullptr;                         // n x 3 host-transfer staging
     float* f_stage = nullptr;                            // n x 3 host-transfer staging
     int nred = 0;
@@ -188,6 +194,8 @@ int launch_reduce(Ctx& c, cudaStream_t s, int with_kinetic);
 int launch_kick_drift(Ctx& c, cudaStream_t s, double dt, int first_half);
 int launch_kick(Ctx& c, cudaStream_t s, double dt);
 int launch_pos_in(Ctx& c, cudaStream_t s, const double* pos_aos);
+int launch_csp(Ctx& c, cudaStream_t s, const ap_csp_params& P, float* d_csp);
+int launch_csp_weights(Ctx& c, cudaStream_t s, const ap_csp_params& P, int nacc, const int S[3]);
 int launch_check(Ctx& c, cudaStream_t s);
 
 // host-side tables (tables.cpp)

@@ -145,6 +145,7 @@ ap_status setup_grid(ap::Ctx& c, const ap_box& box, std::vector<float4>& D, std:
         g.S[d] = S;
         ncell *= n;
         for (int q = 0; q < 3; ++q) g.cellvec[3 * d + q] = g.h[3 * d + q] / n;
+        g.cw[d] = pw[d] / n;
     }
     if (ncell > (1ll << 26)) return set_err(c, AP_ERR_ARG, "cell grid too large");
     g.ortho = (g.h[1] == 0.0 && g.h[2] == 0.0 && g.h[3] == 0.0 && g.h[5] == 0.0 && g.h[6] == 0.0 && g.h[7] == 0.0) ? 1 : 0;
@@ -224,7 +225,7 @@ void free_all(ap::Ctx& c) {
     void* ps[] = {c.eam_d, c.ace_d, c.D, c.Dlo, c.pos_lo, c.ace_A, c.ace_dA, c.x, c.v, c.xb, c.f, c.pos4, c.uxi, c.w, c.e_emb, c.e_eam, c.e_ace,
                   c.vir_eam, c.vir_ace, c.acc, c.fixed, c.w_fixed, c.cell, c.cell_count, c.cell_start,
                   c.cell_atoms, c.nbr, c.nnbr, c.ace_list, c.flags, c.d_time, c.partials, c.totals, c.e_atom,
-                  c.pos_stage, c.f_stage};
+                  c.pos_stage, c.f_stage, c.csp_sum, c.csp_under, c.csp_w0, c.csp_wnew, c.csp_seeds, c.csp_nseed};
     for (void* p : ps)
         if (p) cudaFreeAsync(p, c.stream);
     cudaStreamSynchronize(c.stream);
@@ -607,6 +608,55 @@ ap_status ap_compute_forces_batch(ap_ctx* const* ctxs, int n_ctx) {
         if (st != AP_OK && first == AP_OK) first = st;
     }
     return first;
+}
+
+static ap_status check_csp(ap::Ctx& c, const ap_csp_params* p) {
+    if (!p || (p->n_nb != 12 && p->n_nb != 14)) return set_err(c, AP_ERR_ARG, "CSP: n_nb must be 12 or 14");
+    if (!(p->rc > 0.0 && p->rc <= c.rc_list)) return set_err(c, AP_ERR_ARG, "CSP: rc must lie in (0, neighbour-list cutoff]");
+    if (!(p->csp_hi > p->csp_lo) || !(p->r_hi > p->r_lo && p->r_lo >= 0.0) || !(p->dlam_min >= 0.0) || !(p->zone_r >= 0.0))
+        return set_err(c, AP_ERR_ARG, "CSP: need csp_hi > csp_lo, r_hi > r_lo >= 0, dlam_min >= 0, zone_r >= 0");
+    return AP_OK;
+}
+
+ap_status ap_csp_accumulate(ap_ctx* xc, const ap_csp_params* p, float* d_csp) {
+    if (!xc) return AP_ERR_ARG;
+    ap::Ctx& c = xc->c;
+    ap_status st;
+    if ((st = check_csp(c, p))) return st;
+    const size_t N = (size_t)c.n;
+    if (!c.csp_sum) {
+        if ((st = dalloc(c, &c.csp_sum, N)) || (st = dalloc(c, &c.csp_under, N)) || (st = dalloc(c, &c.csp_w0, N)) ||
+            (st = dalloc(c, &c.csp_wnew, N)) || (st = dalloc(c, &c.csp_seeds, N)) || (st = dalloc(c, &c.csp_nseed, 1)))
+            return st;
+        cudaMemsetAsync(c.csp_sum, 0, N * sizeof(double), c.stream);
+        cudaMemsetAsync(c.csp_under, 0, N * sizeof(int), c.stream);
+        c.csp_nacc = 0;
+    }
+    if (!c.forces_valid) run_forces(xc, c.stream, nullptr);   // positions and list of the current state
+    c.launches += ap::launch_csp(c, c.stream, *p, d_csp);
+    c.csp_nacc += 1;
+    return cuda_check(c, cudaGetLastError(), "ap_csp_accumulate");
+}
+
+ap_status ap_csp_update_weights(ap_ctx* xc, const ap_csp_params* p, int* n_seeds) {
+    if (!xc) return AP_ERR_ARG;
+    ap::Ctx& c = xc->c;
+    ap_status st;
+    if ((st = check_csp(c, p))) return st;
+    if (c.region_kind != AP_REGION_EXPLICIT) return set_err(c, AP_ERR_STATE, "CSP weights need an AP_REGION_EXPLICIT context");
+    if (!c.csp_sum || c.csp_nacc == 0) return set_err(c, AP_ERR_STATE, "CSP: no evaluation in the current block");
+    int S[3];
+    for (int k = 0; k < 3; ++k) S[k] = std::max(1, (int)std::ceil(p->r_hi / c.grid.cw[k] - 1e-12));
+    c.launches += ap::launch_csp_weights(c, c.stream, *p, c.csp_nacc, S);
+    c.csp_nacc = 0;
+    int ns = 0;
+    cudaError_t e = cudaMemcpyAsync(&c.h_flags[ap::kFlagCount - 1], c.csp_nseed, sizeof(int), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "ap_csp_update_weights");
+    ns = c.h_flags[ap::kFlagCount - 1];
+    if (n_seeds) *n_seeds = ns;
+    c.forces_valid = false;
+    return AP_OK;
 }
 
 ap_status ap_energy(ap_ctx* xc, ap_report* out, double* d_e_atom) {
