@@ -141,6 +141,8 @@ typedef struct {
     long long step;
     int n_ace;                   /* atoms with w > 0                                 */
     int n_atoms;
+    double e_thermostat;         /* Q xi^2 / 2 + N_f k_B T eta of the Nose-Hoover thermostat:
+                                    e_total + e_kin + e_thermostat is conserved (0 without) */
 } ap_report;
 
 /* Create a context on the current CUDA device: copies parameters and the host arrays
@@ -180,6 +182,24 @@ ap_status ap_step_batch(ap_ctx* const* ctxs, const int* n_steps, int n_ctx, doub
  * checked before anything is launched (AP_ERR_ARG for a NULL entry).  Asynchronous;
  * returns the first error. */
 ap_status ap_compute_forces_batch(ap_ctx* const* ctxs, int n_ctx);
+
+/* Thermostat of a group of atoms (Appendix A: during the indentation the central part of
+ * the slab is an NVT ensemble, Nose-Hoover with damping time gamma_T^NH = 0.1 ps at 300 K
+ * for W, 292 K for Cu).  One thermostat variable xi (chain length 1); before and after each
+ * velocity-Verlet step of ap_step a half step
+ *   xi += dt/4 G;  v_G *= exp(-xi dt/2);  eta += xi dt/2;  xi += dt/4 G,
+ *   G = (2 KE_G - N_f k_B T) / Q,  N_f = 3 |G|,  Q = N_f k_B T tau^2,
+ * all on the device (the step graph includes it).  group: host mask of n bytes (nonzero =
+ * thermostatted; fixed atoms are excluded), NULL = every free atom.  kind AP_THERMO_NONE
+ * removes the thermostat.  Resets xi and eta.  AP_ERR_ARG for t_target <= 0 or tau_fs <= 0.
+ * Synchronises. */
+enum { AP_THERMO_NONE = 0, AP_THERMO_NOSE_HOOVER = 1 };
+typedef struct {
+    int kind;
+    double t_target;           /* K */
+    double tau_fs;             /* damping time, fs (the paper: 100) */
+} ap_thermostat;
+ap_status ap_set_thermostat(ap_ctx* ctx, const ap_thermostat* t, const unsigned char* group);
 
 /* CSP-driven switching weights (Sec. 2.2.3, the switching function of Appendix B with
  * the parameters of Tab. model_parameters_tungsten).  The centro-symmetry parameter of atom

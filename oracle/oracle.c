@@ -823,3 +823,81 @@ int or_csp(const or_system* sys, int n_nb, double rc, double* csp, int* coord) {
     grid_free(&G);
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Nose-Hoover thermostat on a group                                           */
+/* ------------------------------------------------------------------------- */
+#define OR_KB 8.617333262e-5    /* Boltzmann constant, eV/K */
+
+static double group_ke(const double* v, const unsigned char* group, int N, double mass) {
+    double ke = 0.0;
+    for (int i = 0; i < N; ++i)
+        if (group[i])
+            for (int c = 0; c < 3; ++c) ke += 0.5 * mass * v[3 * i + c] * v[3 * i + c] / OR_FTM;
+    return ke;
+}
+
+/* one half step dt/2 of the thermostat: updates xi, eta and the group velocities */
+static void nh_half(double* v, const unsigned char* group, int N, double mass, double dt, double nfkt, double Q,
+                    double* xi, double* eta) {
+    double ke = group_ke(v, group, N, mass);
+    *xi += 0.25 * dt * (2.0 * ke - nfkt) / Q;
+    double s = exp(-0.5 * dt * (*xi));
+    for (int i = 0; i < N; ++i)
+        if (group[i])
+            for (int c = 0; c < 3; ++c) v[3 * i + c] *= s;
+    ke *= s * s;
+    *eta += 0.5 * dt * (*xi);
+    *xi += 0.25 * dt * (2.0 * ke - nfkt) / Q;
+}
+
+int or_md_nh(const or_system* sys0, const or_eam* eam, const or_ace* ace,
+             const or_region* reg0, const or_indenter* ind0, const double* ind_vel,
+             int region_follows, const unsigned char* fixed, const unsigned char* group,
+             double t_target, double tau, double mass, double dt, int nsteps, int nthreads,
+             double* x, double* v, double* epot, double* ekin, double* ethermo) {
+    const int N = sys0->n;
+    or_system sys = *sys0;
+    sys.x = x;
+    or_region reg;
+    or_indenter ind;
+    if (reg0) reg = *reg0;
+    if (ind0) ind = *ind0;
+    int ng = 0;
+    for (int i = 0; i < N; ++i) if (group[i] && !(fixed && fixed[i])) ++ng;
+    const double nfkt = 3.0 * ng * OR_KB * t_target, Q = nfkt * tau * tau;
+    unsigned char* g = (unsigned char*)malloc(N > 0 ? N : 1);
+    for (int i = 0; i < N; ++i) g[i] = group[i] && !(fixed && fixed[i]);
+    double xi = 0.0, eta = 0.0;
+    double* F = (double*)malloc(sizeof(double) * 3 * (N > 0 ? N : 1));
+    or_result res;
+    int status = or_evaluate(&sys, eam, ace, reg0 ? &reg : NULL, ind0 ? &ind : NULL, NULL, nthreads, F, NULL, NULL, NULL, NULL, &res);
+    double a = dt * OR_FTM / mass;
+    for (int k = 0; k <= nsteps; ++k) {
+        if (k > 0) {
+            if (ng > 0) nh_half(v, g, N, mass, dt, nfkt, Q, &xi, &eta);
+            for (int i = 0; i < N; ++i) {
+                if (fixed && fixed[i]) continue;
+                for (int c = 0; c < 3; ++c) { v[3 * i + c] += 0.5 * a * F[3 * i + c]; x[3 * i + c] += dt * v[3 * i + c]; }
+            }
+            if (ind0 && ind_vel) for (int c = 0; c < 3; ++c) ind.center[c] -= ind_vel[c] * dt;
+            if (reg0 && region_follows && ind_vel) for (int c = 0; c < 3; ++c) reg.center[c] -= ind_vel[c] * dt;
+            int s = or_evaluate(&sys, eam, ace, reg0 ? &reg : NULL, ind0 ? &ind : NULL, NULL, nthreads, F, NULL, NULL, NULL, NULL, &res);
+            if (s != 0 && status == 0) status = s;
+            for (int i = 0; i < N; ++i) {
+                if (fixed && fixed[i]) continue;
+                for (int c = 0; c < 3; ++c) v[3 * i + c] += 0.5 * a * F[3 * i + c];
+            }
+            if (ng > 0) nh_half(v, g, N, mass, dt, nfkt, Q, &xi, &eta);
+        }
+        double ke = 0.0;
+        for (int i = 0; i < N; ++i)
+            for (int c = 0; c < 3; ++c) ke += 0.5 * mass * v[3 * i + c] * v[3 * i + c] / OR_FTM;
+        if (epot) epot[k] = res.e_total;
+        if (ekin) ekin[k] = ke;
+        if (ethermo) ethermo[k] = 0.5 * Q * xi * xi + nfkt * eta;
+    }
+    free(F);
+    free(g);
+    return status;
+}

@@ -143,6 +143,21 @@ int or_md(const or_system* sys, const or_eam* eam, const or_ace* ace,
  * n_nb even, 2 <= n_nb <= 16.  Returns 0, or -1 on bad arguments. */
 int or_csp(const or_system* sys, int n_nb, double rc, double* csp, int* coord);
 
+/* Velocity Verlet with a Nose-Hoover thermostat on a group of atoms (Appendix A: the
+ * central part of the slab is simulated as NVT during the indentation, Nose-Hoover with
+ * damping time tau = gamma_T^NH).  One thermostat variable xi (chain length 1), integrated
+ * by the time-reversible split: before and after each velocity-Verlet step a half step
+ *   xi += dt/4 G;  v_G *= exp(-xi dt/2);  eta += xi dt/2;  xi += dt/4 G,
+ * G = (2 KE_G - N_f k_B T) / Q,  N_f = 3 |G|,  Q = N_f k_B T tau^2  (tau in fs).
+ * group: 0/1 mask (fixed atoms are never in it).  Writes per step k (0..nsteps) epot,
+ * ekin (all atoms) and ethermo = Q xi^2 / 2 + N_f k_B T eta, so that epot + ekin +
+ * ethermo is conserved.  Other arguments as or_md. */
+int or_md_nh(const or_system* sys, const or_eam* eam, const or_ace* ace,
+             const or_region* reg, const or_indenter* ind, const double* ind_vel,
+             int region_follows, const unsigned char* fixed, const unsigned char* group,
+             double t_target, double tau, double mass, double dt, int nsteps, int nthreads,
+             double* x, double* v, double* epot, double* ekin, double* ethermo);
+
 int or_num_threads(void);
 
 #ifdef __cplusplus

@@ -183,7 +183,7 @@ class APContext:
         self._chk(self._L.ap_energy(self._h, C.byref(r), _ptr(e_atom)))
         return {"e_total": r.e_total, "e_pot": r.e_pot, "e_ind": r.e_ind, "e_kin": r.e_kin,
                 "virial": np.array(r.virial[:]), "load": r.load, "time_fs": r.time_fs, "step": r.step,
-                "n_ace": r.n_ace, "n_atoms": r.n_atoms}
+                "n_ace": r.n_ace, "n_atoms": r.n_atoms, "e_thermostat": r.e_thermostat}
 
     def check(self):
         self._chk(self._L.ap_check(self._h))
@@ -229,6 +229,17 @@ class APContext:
         nl = (C.c_longlong * len(STAGES))()
         self._chk(self._L.ap_profile_read(self._h, ms, nl))
         return {s: (ms[k], nl[k]) for k, s in enumerate(STAGES)}
+
+    def set_thermostat(self, t_target=None, tau_fs=100.0, group=None):
+        """Nose-Hoover thermostat on `group` (host mask, None = all free atoms) at t_target K
+        with damping time tau_fs (ap_set_thermostat); t_target None removes it."""
+        t = _capi.Thermostat()
+        t.kind = 0 if t_target is None else 1
+        t.t_target = float(t_target or 0.0)
+        t.tau_fs = float(tau_fs)
+        g = None if group is None else np.ascontiguousarray(group, dtype=np.uint8)
+        self._chk(self._L.ap_set_thermostat(self._h, C.byref(t),
+                                            None if g is None else g.ctypes.data_as(C.POINTER(C.c_ubyte))))
 
     def csp_accumulate(self, params, out=None):
         """Add the CSP of the current positions to the block sums (ap_csp_accumulate); out: an

@@ -45,10 +45,14 @@ class Indenter(C.Structure):
 
 class Report(C.Structure):
     _fields_ = [("e_total", D), ("e_pot", D), ("e_ind", D), ("e_kin", D), ("virial", D * 6),
-                ("load", D), ("time_fs", D), ("step", LL), ("n_ace", I), ("n_atoms", I)]
+                ("load", D), ("time_fs", D), ("step", LL), ("n_ace", I), ("n_atoms", I), ("e_thermostat", D)]
 
 
 _lib = None
+
+
+class Thermostat(C.Structure):
+    _fields_ = [("kind", C.c_int), ("t_target", C.c_double), ("tau_fs", C.c_double)]
 
 
 class CspParams(C.Structure):
@@ -75,6 +79,7 @@ def lib():
         "ap_step_batch": (I, [C.POINTER(VP), PI, I, D]),
         "ap_compute_forces_batch": (I, [C.POINTER(VP), I]),
         "ap_csp_accumulate": (I, [VP, P(CspParams), VP]),
+        "ap_set_thermostat": (I, [VP, P(Thermostat), C.POINTER(C.c_ubyte)]),
         "ap_csp_update_weights": (I, [VP, P(CspParams), PI]),
         "ap_memory_bytes": (C.c_size_t, [VP]),
         "ap_energy": (I, [VP, P(Report), VP]),

@@ -156,6 +156,11 @@ struct Ctx {
     float *csp_w0 = nullptr, *csp_wnew = nullptr;
     int *csp_seeds = nullptr, *csp_nseed = nullptr;
     int csp_nacc = 0;                                    // evaluations in the current block
+    int thermo_kind = 0;                                 // AP_THERMO_*
+    double nh_nfkt = 0.0, nh_Q = 0.0;                    // N_f k_B T (eV) and Q (eV fs^2)
+    unsigned char* thermo_group = nullptr;
+    double* nh_state = nullptr;                          // xi (1/fs), eta, velocity scale of the last half step
+    double* nh_partials = nullptr;                       // [nred] group kinetic energies
     double* pos_stage = nullptr;                         // n x 3 host-transfer staging
     float* f_stage = nullptr;                            // n x 3 host-transfer staging
     int nred = 0;
@@ -193,6 +198,7 @@ int launch_energy(Ctx& c, cudaStream_t s);           // compensated EAM energies
 int launch_reduce(Ctx& c, cudaStream_t s, int with_kinetic);
 int launch_kick_drift(Ctx& c, cudaStream_t s, double dt, int first_half);
 int launch_kick(Ctx& c, cudaStream_t s, double dt);
+int launch_nh_half(Ctx& c, cudaStream_t s, double dt);
 int launch_pos_in(Ctx& c, cudaStream_t s, const double* pos_aos);
 int launch_csp(Ctx& c, cudaStream_t s, const ap_csp_params& P, float* d_csp);
 int launch_csp_weights(Ctx& c, cudaStream_t s, const ap_csp_params& P, int nacc, const int S[3]);

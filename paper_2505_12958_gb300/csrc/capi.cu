@@ -225,7 +225,8 @@ void free_all(ap::Ctx& c) {
     void* ps[] = {c.eam_d, c.ace_d, c.D, c.Dlo, c.pos_lo, c.ace_A, c.ace_dA, c.x, c.v, c.xb, c.f, c.pos4, c.uxi, c.w, c.e_emb, c.e_eam, c.e_ace,
                   c.vir_eam, c.vir_ace, c.acc, c.fixed, c.w_fixed, c.cell, c.cell_count, c.cell_start,
                   c.cell_atoms, c.nbr, c.nnbr, c.ace_list, c.flags, c.d_time, c.partials, c.totals, c.e_atom,
-                  c.pos_stage, c.f_stage, c.csp_sum, c.csp_under, c.csp_w0, c.csp_wnew, c.csp_seeds, c.csp_nseed};
+                  c.pos_stage, c.f_stage, c.csp_sum, c.csp_under, c.csp_w0, c.csp_wnew, c.csp_seeds, c.csp_nseed,
+                  c.thermo_group, c.nh_state, c.nh_partials};
     for (void* p : ps)
         if (p) cudaFreeAsync(p, c.stream);
     cudaStreamSynchronize(c.stream);
@@ -531,9 +532,11 @@ ap_status ap_step(ap_ctx* xc, int n_steps, double dt, void* stream) {
     if (!c.forces_valid) run_forces(xc, s, nullptr);
     if (c.prof || !capturable(s) || n_steps == 0) {
         for (int k = 0; k < n_steps; ++k) {
+            if (c.thermo_kind) stage(xc, AP_STAGE_INTEGRATE, s, [&] { return ap::launch_nh_half(c, s, dt); });
             stage(xc, AP_STAGE_INTEGRATE, s, [&] { return ap::launch_kick_drift(c, s, dt, 1); });
             run_forces(xc, s, nullptr);
             stage(xc, AP_STAGE_INTEGRATE, s, [&] { return ap::launch_kick(c, s, dt); });
+            if (c.thermo_kind) stage(xc, AP_STAGE_INTEGRATE, s, [&] { return ap::launch_nh_half(c, s, dt); });
             c.t += dt;
             c.step += 1;
         }
@@ -547,9 +550,11 @@ ap_status ap_step(ap_ctx* xc, int n_steps, double dt, void* stream) {
         if (e != cudaSuccess) return e;
         const long long before = c.launches;
         for (int q = 0; q < k; ++q) {
+            if (c.thermo_kind) c.launches += ap::launch_nh_half(c, s, dt);
             c.launches += ap::launch_kick_drift(c, s, dt, 1);
             run_forces(xc, s, nullptr);
             c.launches += ap::launch_kick(c, s, dt);
+            if (c.thermo_kind) c.launches += ap::launch_nh_half(c, s, dt);
         }
         xc->step_kernels = (c.launches - before) / k;
         c.launches = before;
@@ -610,6 +615,42 @@ ap_status ap_compute_forces_batch(ap_ctx* const* ctxs, int n_ctx) {
     return first;
 }
 
+ap_status ap_set_thermostat(ap_ctx* xc, const ap_thermostat* t, const unsigned char* group) {
+    if (!xc || !t) return AP_ERR_ARG;
+    ap::Ctx& c = xc->c;
+    if (t->kind != AP_THERMO_NONE && t->kind != AP_THERMO_NOSE_HOOVER) return set_err(c, AP_ERR_ARG, "unknown thermostat kind");
+    cudaError_t e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "ap_set_thermostat");
+    drop_step_graph(xc);
+    c.layout_gen += 1;                                   // the step graph changes shape
+    if (t->kind == AP_THERMO_NONE) { c.thermo_kind = 0; return AP_OK; }
+    if (!(t->t_target > 0.0) || !(t->tau_fs > 0.0)) return set_err(c, AP_ERR_ARG, "thermostat needs t_target > 0 and tau_fs > 0");
+    const size_t N = (size_t)c.n;
+    ap_status st;
+    if (!c.thermo_group &&
+        ((st = dalloc(c, &c.thermo_group, N)) || (st = dalloc(c, &c.nh_state, 4)) || (st = dalloc(c, &c.nh_partials, (size_t)c.nred))))
+        return st;
+    std::vector<unsigned char> fx(N), g(N);
+    e = cudaMemcpyAsync(fx.data(), c.fixed, N, cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "ap_set_thermostat");
+    long long ng = 0;
+    for (size_t i = 0; i < N; ++i) {
+        g[i] = (group ? group[i] != 0 : true) && !fx[i];
+        ng += g[i];
+    }
+    const double kB = 8.617333262e-5;
+    c.nh_nfkt = 3.0 * (double)ng * kB * t->t_target;
+    c.nh_Q = c.nh_nfkt * t->tau_fs * t->tau_fs;
+    const double zero[4] = {0.0, 0.0, 1.0, 0.0};
+    e = cudaMemcpyAsync(c.thermo_group, g.data(), N, cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c.nh_state, zero, sizeof(zero), cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "ap_set_thermostat");
+    c.thermo_kind = ng > 0 ? t->kind : 0;
+    return AP_OK;
+}
+
 static ap_status check_csp(ap::Ctx& c, const ap_csp_params* p) {
     if (!p || (p->n_nb != 12 && p->n_nb != 14)) return set_err(c, AP_ERR_ARG, "CSP: n_nb must be 12 or 14");
     if (!(p->rc > 0.0 && p->rc <= c.rc_list)) return set_err(c, AP_ERR_ARG, "CSP: rc must lie in (0, neighbour-list cutoff]");
@@ -667,6 +708,8 @@ ap_status ap_energy(ap_ctx* xc, ap_report* out, double* d_e_atom) {
     ensure_energy(xc, s);
     c.launches += ap::launch_reduce(c, s, 1);
     cudaError_t e = cudaMemcpyAsync(c.h_totals, c.totals, 10 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && c.thermo_kind)
+        e = cudaMemcpyAsync(c.h_totals + 12, c.nh_state, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && d_e_atom)
         e = cudaMemcpyAsync(d_e_atom, c.e_atom, (size_t)c.n * sizeof(double), cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return cuda_check(c, e, "ap_energy");
@@ -678,6 +721,7 @@ ap_status ap_energy(ap_ctx* xc, ap_report* out, double* d_e_atom) {
     out->e_total = T[0] + T[1];
     for (int k = 0; k < 6; ++k) out->virial[k] = T[2 + k];
     out->load = T[8];
+    out->e_thermostat = c.thermo_kind ? 0.5 * c.nh_Q * T[12] * T[12] + c.nh_nfkt * T[13] : 0.0;
     out->e_kin = T[9];
     out->time_fs = c.t;
     out->step = c.step;

@@ -178,7 +178,57 @@ __global__ void k_kick(double* __restrict__ v, const float* __restrict__ f, cons
     for (int k = 0; k < 3; ++k) v[(size_t)k * n + i] += hdta * (double)f[(size_t)k * n + i];
 }
 
+// Nose-Hoover half step on the group: block sums of the group's kinetic energy, one block
+// that advances xi and eta and computes the velocity scale, then the scaling
+__global__ void __launch_bounds__(kRedBlock) k_group_ke(const double* __restrict__ v,
+                                                        const unsigned char* __restrict__ group, int n, double mass,
+                                                        double* __restrict__ partials) {
+    __shared__ double sh[32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double ke = 0.0;
+    if (i < n && group[i]) {
+        const double a = v[i], b = v[n + i], c = v[2 * n + i];
+        ke = 0.5 * mass * (a * a + b * b + c * c) / kFtm;
+    }
+    const double s = block_sum(ke, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void k_nh_update(const double* __restrict__ partials, int nblk, double* __restrict__ st, double dt,
+                            double nfkt, double Q) {
+    __shared__ double sh[32];
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) v += partials[b];
+    double ke = block_sum(v, sh);
+    if (threadIdx.x == 0) {
+        double xi = st[0], eta = st[1];
+        xi += 0.25 * dt * (2.0 * ke - nfkt) / Q;
+        const double sc = exp(-0.5 * dt * xi);
+        ke *= sc * sc;
+        eta += 0.5 * dt * xi;
+        xi += 0.25 * dt * (2.0 * ke - nfkt) / Q;
+        st[0] = xi;
+        st[1] = eta;
+        st[2] = sc;
+    }
+}
+
+__global__ void k_scale_group(double* __restrict__ v, const unsigned char* __restrict__ group, int n,
+                              const double* __restrict__ st) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !group[i]) return;
+    const double sc = st[2];
+    for (int k = 0; k < 3; ++k) v[(size_t)k * n + i] *= sc;
+}
+
 }  // namespace
+
+int launch_nh_half(Ctx& c, cudaStream_t s, double dt) {
+    k_group_ke<<<c.nred, kRedBlock, 0, s>>>(c.v, c.thermo_group, c.n, c.mass, c.nh_partials);
+    k_nh_update<<<1, 1024, 0, s>>>(c.nh_partials, c.nred, c.nh_state, dt, c.nh_nfkt, c.nh_Q);
+    k_scale_group<<<(c.n + 255) / 256, 256, 0, s>>>(c.v, c.thermo_group, c.n, c.nh_state);
+    return 3;
+}
 
 int launch_pos_in(Ctx& c, cudaStream_t s, const double* pos) {
     k_pos_in<<<(c.n + 255) / 256, 256, 0, s>>>(pos, c.n, c.x);
