@@ -189,15 +189,25 @@ ap_status ap_compute_forces_batch(ap_ctx* const* ctxs, int n_ctx);
  * velocity-Verlet step of ap_step a half step
  *   xi += dt/4 G;  v_G *= exp(-xi dt/2);  eta += xi dt/2;  xi += dt/4 G,
  *   G = (2 KE_G - N_f k_B T) / Q,  N_f = 3 |G|,  Q = N_f k_B T tau^2,
- * all on the device (the step graph includes it).  group: host mask of n bytes (nonzero =
- * thermostatted; fixed atoms are excluded), NULL = every free atom.  kind AP_THERMO_NONE
- * removes the thermostat.  Resets xi and eta.  AP_ERR_ARG for t_target <= 0 or tau_fs <= 0.
- * Synchronises. */
-enum { AP_THERMO_NONE = 0, AP_THERMO_NOSE_HOOVER = 1 };
+ * all on the device (the step graph includes it).
+ * AP_THERMO_LANGEVIN (equilibration, Appendix A): after each force evaluation the group's
+ * forces get a drag -(m/tau) v (v of the half step) and a random force sqrt(2 m k_B T /
+ * (tau dt)) g per component; g is standard normal, by Box-Muller from Philox4x32-10 at
+ * counter (atom index, step since ap_set_thermostat, 0, 0) and key (seed low, seed high):
+ * u1 = (w0 + 1)/2^32, u2 = (w1 + 0.5)/2^32, g_x, g_y = sqrt(-2 ln u1) (cos, sin)(2 pi u2),
+ * g_z the cosine branch of (w2, w3).  With zero_every > 0 the centre-of-mass velocity of the
+ * free atoms is removed every zero_every steps after the final kick.
+ * group: host mask of n bytes (nonzero = thermostatted; fixed atoms are excluded), NULL =
+ * every free atom.  kind AP_THERMO_NONE removes the thermostat.  Resets the thermostat
+ * state.  AP_ERR_ARG for t_target <= 0 or tau_fs <= 0.  Synchronises. */
+enum { AP_THERMO_NONE = 0, AP_THERMO_NOSE_HOOVER = 1, AP_THERMO_LANGEVIN = 2 };
 typedef struct {
     int kind;
     double t_target;           /* K */
-    double tau_fs;             /* damping time, fs (the paper: 100) */
+    double tau_fs;             /* damping time, fs (the paper: 100 for Nose-Hoover; Langevin 100 - 10000) */
+    unsigned long long seed;   /* Langevin: key of the random numbers */
+    int zero_every;            /* Langevin: zero the centre-of-mass velocity of the free atoms
+                                  every zero_every steps (0: never; the paper: every 1 ps) */
 } ap_thermostat;
 ap_status ap_set_thermostat(ap_ctx* ctx, const ap_thermostat* t, const unsigned char* group);
 

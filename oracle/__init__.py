@@ -98,6 +98,12 @@ def lib():
         L.or_md_nh.restype = I
         L.or_md_nh.argtypes = [C.POINTER(System), C.POINTER(EAM), C.POINTER(ACE), C.POINTER(Region),
                                C.POINTER(Indenter), PD, I, PU8, PU8, D, D, D, D, I, I, PD, PD, PD, PD, PD]
+        L.or_philox4x32_10.restype = None
+        L.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint), C.POINTER(C.c_uint), C.POINTER(C.c_uint)]
+        L.or_md_langevin.restype = I
+        L.or_md_langevin.argtypes = [C.POINTER(System), C.POINTER(EAM), C.POINTER(ACE), C.POINTER(Region),
+                                     C.POINTER(Indenter), PD, I, PU8, PU8, D, D, C.c_ulonglong, I, D, D, I, I,
+                                     PD, PD, PD, PD]
         L.or_csp.restype = I
         L.or_csp.argtypes = [C.POINTER(System), I, D, PD, PI]
         _lib = L
@@ -352,6 +358,42 @@ def md_nh(x, v, box, eam, ace, region, indenter, ind_vel, fixed, group, t_target
                     _pd(x), _pd(v), _pd(ep), _pd(ek), _pd(et))
     del rkeep
     return x, v, ep, ek, et, st
+
+
+def philox4x32_10(ctr, key):
+    """The four 32-bit words of Philox4x32-10 at counter ctr (4 words) and key (2 words)."""
+    L = lib()
+    c = (C.c_uint * 4)(*[int(v) & 0xffffffff for v in ctr])
+    k = (C.c_uint * 2)(*[int(v) & 0xffffffff for v in key])
+    o = (C.c_uint * 4)()
+    L.or_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def md_langevin(x, v, box, eam, ace, region, indenter, ind_vel, fixed, group, t_target, tau, seed, zero_every,
+                mass, dt, nsteps, region_follows=False, nthreads=0):
+    """Velocity Verlet with a Langevin thermostat on `group` (or_md_langevin).  Returns
+    (x, v, epot[nsteps+1], ekin[nsteps+1], status)."""
+    L = lib()
+    x = _f64(x).reshape(-1, 3).copy()
+    v = _f64(v).reshape(-1, 3).copy()
+    sysd, _ = make_system(x, box)
+    sysd.x = _pd(x)
+    e = make_eam(eam)
+    a = make_ace(ace)
+    r, rkeep = make_region(region)
+    ind = make_indenter(indenter)
+    iv = _f64(ind_vel if ind_vel is not None else np.zeros(3))
+    fx = np.ascontiguousarray(fixed, dtype=np.uint8) if fixed is not None else None
+    gr = np.ascontiguousarray(group, dtype=np.uint8)
+    ep, ek = np.zeros(nsteps + 1), np.zeros(nsteps + 1)
+    st = L.or_md_langevin(C.byref(sysd), _ptr(e, EAM), C.byref(a.s) if a else C.POINTER(ACE)(), _ptr(r, Region),
+                          _ptr(ind, Indenter), _pd(iv), int(region_follows),
+                          fx.ctypes.data_as(PU8) if fx is not None else PU8(), gr.ctypes.data_as(PU8),
+                          float(t_target), float(tau), int(seed), int(zero_every), float(mass), float(dt),
+                          int(nsteps), int(nthreads), _pd(x), _pd(v), _pd(ep), _pd(ek))
+    del rkeep
+    return x, v, ep, ek, st
 
 
 def csp(x, box, n_nb, rc):

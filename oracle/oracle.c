@@ -901,3 +901,100 @@ int or_md_nh(const or_system* sys0, const or_eam* eam, const or_ace* ace,
     free(g);
     return status;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10 and the Langevin thermostat                                   */
+/* ------------------------------------------------------------------------- */
+void or_philox4x32_10(const unsigned int* ctr, const unsigned int* key, unsigned int* out) {
+    unsigned int c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    unsigned int k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        unsigned long long p0 = (unsigned long long)0xD2511F53u * c0;
+        unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c2;
+        unsigned int hi0 = (unsigned int)(p0 >> 32), lo0 = (unsigned int)p0;
+        unsigned int hi1 = (unsigned int)(p1 >> 32), lo1 = (unsigned int)p1;
+        unsigned int n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static void gauss3(int i, int step, unsigned long long seed, double* g) {
+    unsigned int ctr[4] = {(unsigned int)i, (unsigned int)step, 0u, 0u};
+    unsigned int key[2] = {(unsigned int)(seed & 0xffffffffu), (unsigned int)(seed >> 32)};
+    unsigned int w[4];
+    or_philox4x32_10(ctr, key, w);
+    const double two32 = 4294967296.0;
+    double u1 = ((double)w[0] + 1.0) / two32, u2 = ((double)w[1] + 0.5) / two32;
+    double r = sqrt(-2.0 * log(u1));
+    g[0] = r * cos(2.0 * M_PI * u2);
+    g[1] = r * sin(2.0 * M_PI * u2);
+    double u3 = ((double)w[2] + 1.0) / two32, u4 = ((double)w[3] + 0.5) / two32;
+    g[2] = sqrt(-2.0 * log(u3)) * cos(2.0 * M_PI * u4);
+}
+
+int or_md_langevin(const or_system* sys0, const or_eam* eam, const or_ace* ace,
+                   const or_region* reg0, const or_indenter* ind0, const double* ind_vel,
+                   int region_follows, const unsigned char* fixed, const unsigned char* group,
+                   double t_target, double tau, unsigned long long seed, int zero_every,
+                   double mass, double dt, int nsteps, int nthreads,
+                   double* x, double* v, double* epot, double* ekin) {
+    const int N = sys0->n;
+    or_system sys = *sys0;
+    sys.x = x;
+    or_region reg;
+    or_indenter ind;
+    if (reg0) reg = *reg0;
+    if (ind0) ind = *ind0;
+    double* F = (double*)malloc(sizeof(double) * 3 * (N > 0 ? N : 1));
+    or_result res;
+    int status = or_evaluate(&sys, eam, ace, reg0 ? &reg : NULL, ind0 ? &ind : NULL, NULL, nthreads, F, NULL, NULL, NULL, NULL, &res);
+    const double a = dt * OR_FTM / mass;
+    /* drag and random force in eV/A: m v / tau with m in amu, v in A/fs -> / OR_FTM */
+    const double drag = mass / (tau * OR_FTM);
+    const double sig = sqrt(2.0 * mass * OR_KB * t_target / (tau * dt * OR_FTM));
+    for (int k = 0; k <= nsteps; ++k) {
+        if (k > 0) {
+            for (int i = 0; i < N; ++i) {
+                if (fixed && fixed[i]) continue;
+                for (int c = 0; c < 3; ++c) { v[3 * i + c] += 0.5 * a * F[3 * i + c]; x[3 * i + c] += dt * v[3 * i + c]; }
+            }
+            if (ind0 && ind_vel) for (int c = 0; c < 3; ++c) ind.center[c] -= ind_vel[c] * dt;
+            if (reg0 && region_follows && ind_vel) for (int c = 0; c < 3; ++c) reg.center[c] -= ind_vel[c] * dt;
+            int s = or_evaluate(&sys, eam, ace, reg0 ? &reg : NULL, ind0 ? &ind : NULL, NULL, nthreads, F, NULL, NULL, NULL, NULL, &res);
+            if (s != 0 && status == 0) status = s;
+            for (int i = 0; i < N; ++i) {
+                if (!group[i] || (fixed && fixed[i])) continue;
+                double g[3];
+                gauss3(i, k, seed, g);
+                for (int c = 0; c < 3; ++c) F[3 * i + c] += -drag * v[3 * i + c] + sig * g[c];
+            }
+            for (int i = 0; i < N; ++i) {
+                if (fixed && fixed[i]) continue;
+                for (int c = 0; c < 3; ++c) v[3 * i + c] += 0.5 * a * F[3 * i + c];
+            }
+            if (zero_every > 0 && k % zero_every == 0) {
+                double vc[3] = {0, 0, 0};
+                int nf = 0;
+                for (int i = 0; i < N; ++i) {
+                    if (fixed && fixed[i]) continue;
+                    for (int c = 0; c < 3; ++c) vc[c] += v[3 * i + c];
+                    ++nf;
+                }
+                if (nf > 0)
+                    for (int i = 0; i < N; ++i) {
+                        if (fixed && fixed[i]) continue;
+                        for (int c = 0; c < 3; ++c) v[3 * i + c] -= vc[c] / nf;
+                    }
+            }
+        }
+        double ke = 0.0;
+        for (int i = 0; i < N; ++i)
+            for (int c = 0; c < 3; ++c) ke += 0.5 * mass * v[3 * i + c] * v[3 * i + c] / OR_FTM;
+        if (epot) epot[k] = res.e_total;
+        if (ekin) ekin[k] = ke;
+    }
+    free(F);
+    return status;
+}

@@ -158,6 +158,27 @@ int or_md_nh(const or_system* sys, const or_eam* eam, const or_ace* ace,
              double t_target, double tau, double mass, double dt, int nsteps, int nthreads,
              double* x, double* v, double* epot, double* ekin, double* ethermo);
 
+/* Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
+ * the 4-word multiply-xor round with the published multipliers and Weyl key increments.
+ * out[4] = philox4x32_10(ctr[4], key[2]). */
+void or_philox4x32_10(const unsigned int* ctr, const unsigned int* key, unsigned int* out);
+
+/* Velocity Verlet with a Langevin thermostat on a group (Appendix A: equilibration steps 1
+ * and 3, damping time gamma^L): after each force evaluation the group's forces get a drag
+ * -(m / tau) v (v of the half step) and a random force sqrt(2 m k_B T / (tau dt)) g per
+ * component, g a standard normal number.  The normal numbers of atom i at step s (1-based)
+ * come from philox4x32_10(ctr = (i, s, 0, 0), key = (seed_lo, seed_hi)) by Box-Muller:
+ * u1 = (w0 + 1) / 2^32, u2 = (w1 + 0.5) / 2^32, g_x = sqrt(-2 ln u1) cos(2 pi u2),
+ * g_y = sqrt(-2 ln u1) sin(2 pi u2); g_z from (w2, w3) the same way (its cosine branch).
+ * zero_every > 0: every zero_every steps the centre-of-mass velocity of the free atoms is
+ * subtracted from them (the momentum zeroing of Appendix A).  Other arguments as or_md. */
+int or_md_langevin(const or_system* sys, const or_eam* eam, const or_ace* ace,
+                   const or_region* reg, const or_indenter* ind, const double* ind_vel,
+                   int region_follows, const unsigned char* fixed, const unsigned char* group,
+                   double t_target, double tau, unsigned long long seed, int zero_every,
+                   double mass, double dt, int nsteps, int nthreads,
+                   double* x, double* v, double* epot, double* ekin);
+
 int or_num_threads(void);
 
 #ifdef __cplusplus

@@ -230,13 +230,16 @@ class APContext:
         self._chk(self._L.ap_profile_read(self._h, ms, nl))
         return {s: (ms[k], nl[k]) for k, s in enumerate(STAGES)}
 
-    def set_thermostat(self, t_target=None, tau_fs=100.0, group=None):
-        """Nose-Hoover thermostat on `group` (host mask, None = all free atoms) at t_target K
-        with damping time tau_fs (ap_set_thermostat); t_target None removes it."""
+    def set_thermostat(self, t_target=None, tau_fs=100.0, group=None, kind="nose-hoover", seed=0, zero_every=0):
+        """Thermostat on `group` (host mask, None = all free atoms) at t_target K with damping
+        time tau_fs (ap_set_thermostat): kind "nose-hoover" or "langevin" (seed, zero_every);
+        t_target None removes it."""
         t = _capi.Thermostat()
-        t.kind = 0 if t_target is None else 1
+        t.kind = 0 if t_target is None else {"nose-hoover": 1, "langevin": 2}[kind]
         t.t_target = float(t_target or 0.0)
         t.tau_fs = float(tau_fs)
+        t.seed = int(seed)
+        t.zero_every = int(zero_every)
         g = None if group is None else np.ascontiguousarray(group, dtype=np.uint8)
         self._chk(self._L.ap_set_thermostat(self._h, C.byref(t),
                                             None if g is None else g.ctypes.data_as(C.POINTER(C.c_ubyte))))

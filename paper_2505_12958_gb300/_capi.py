@@ -52,7 +52,8 @@ _lib = None
 
 
 class Thermostat(C.Structure):
-    _fields_ = [("kind", C.c_int), ("t_target", C.c_double), ("tau_fs", C.c_double)]
+    _fields_ = [("kind", C.c_int), ("t_target", C.c_double), ("tau_fs", C.c_double), ("seed", C.c_ulonglong),
+                ("zero_every", C.c_int)]
 
 
 class CspParams(C.Structure):

@@ -104,6 +104,7 @@ constexpr int kNbrShift = 25;               // neighbour entry = j | code << 25
 constexpr int kNbrMask = (1 << kNbrShift) - 1;
 constexpr int kMaxAtoms = (1 << kNbrShift) - 1;
 constexpr double kFixScale = 1099511627776.0;   // 2^40: fixed-point scale of ACE force sums
+constexpr double kFtm = 0.0096485332;           // 1 eV/(Angstrom amu) in Angstrom/fs^2
 constexpr int kAceNbrCap = 128;                 // neighbours within the ACE cutoff per atom
 constexpr int kRedBlock = 256;
 
@@ -161,6 +162,12 @@ struct Ctx {
     unsigned char* thermo_group = nullptr;
     double* nh_state = nullptr;                          // xi (1/fs), eta, velocity scale of the last half step
     double* nh_partials = nullptr;                       // [nred] group kinetic energies
+    double lv_drag = 0.0, lv_sig = 0.0;                  // Langevin drag (eV fs/A^2) and noise amplitude (eV/A)
+    unsigned long long lv_seed = 0;
+    long long lv_base = 0;                               // step count at ap_set_thermostat
+    int lv_zero_every = 0;
+    long long* d_step = nullptr;                         // device step counter (advanced by k_kick_drift)
+    double* com = nullptr;                               // [4 nred + 4] momentum-zeroing partials and result
     double* pos_stage = nullptr;                         // n x 3 host-transfer staging
     float* f_stage = nullptr;                            // n x 3 host-transfer staging
     int nred = 0;
@@ -199,6 +206,8 @@ int launch_reduce(Ctx& c, cudaStream_t s, int with_kinetic);
 int launch_kick_drift(Ctx& c, cudaStream_t s, double dt, int first_half);
 int launch_kick(Ctx& c, cudaStream_t s, double dt);
 int launch_nh_half(Ctx& c, cudaStream_t s, double dt);
+int launch_langevin(Ctx& c, cudaStream_t s, double dt);
+int launch_zero_momentum(Ctx& c, cudaStream_t s);
 int launch_pos_in(Ctx& c, cudaStream_t s, const double* pos_aos);
 int launch_csp(Ctx& c, cudaStream_t s, const ap_csp_params& P, float* d_csp);
 int launch_csp_weights(Ctx& c, cudaStream_t s, const ap_csp_params& P, int nacc, const int S[3]);

@@ -226,7 +226,7 @@ void free_all(ap::Ctx& c) {
                   c.vir_eam, c.vir_ace, c.acc, c.fixed, c.w_fixed, c.cell, c.cell_count, c.cell_start,
                   c.cell_atoms, c.nbr, c.nnbr, c.ace_list, c.flags, c.d_time, c.partials, c.totals, c.e_atom,
                   c.pos_stage, c.f_stage, c.csp_sum, c.csp_under, c.csp_w0, c.csp_wnew, c.csp_seeds, c.csp_nseed,
-                  c.thermo_group, c.nh_state, c.nh_partials};
+                  c.thermo_group, c.nh_state, c.nh_partials, c.d_step, c.com};
     for (void* p : ps)
         if (p) cudaFreeAsync(p, c.stream);
     cudaStreamSynchronize(c.stream);
@@ -422,7 +422,7 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
         (st = dalloc(c, &c.cell_start, (size_t)c.grid.ncell + 1)) || (st = dalloc(c, &c.cell_atoms, N)) ||
         (st = dalloc(c, &c.nnbr, N)) || (st = dalloc(c, &c.ace_list, N)) || (st = dalloc(c, &c.flags, ap::kFlagCount)) ||
         (st = dalloc(c, &c.d_time, 1)) || (st = dalloc(c, &c.partials, (size_t)c.nred * 10)) ||
-        (st = dalloc(c, &c.totals, 16)) || (st = dalloc(c, &c.e_atom, N)))
+        (st = dalloc(c, &c.totals, 16)) || (st = dalloc(c, &c.e_atom, N)) || (st = dalloc(c, &c.d_step, 1)))
         return fail(st);
     c.ncell_cap = c.grid.ncell;
     if (char* slot = pinned_take()) {
@@ -460,6 +460,7 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
     zero(c.cell_count, (size_t)c.grid.ncell * sizeof(int));
     zero(c.flags, ap::kFlagCount * sizeof(int));
     zero(c.d_time, sizeof(double));
+    zero(c.d_step, sizeof(long long));
     zero(c.vir_ace, 6 * N * sizeof(float));
     zero(c.e_ace, N * sizeof(float));
     zero(c.e_eam, N * sizeof(double));
@@ -521,6 +522,22 @@ ap_status ap_compute_forces_host(ap_ctx* xc, const double* h_pos, float* h_force
     return AP_OK;
 }
 
+// the integration kernels around a force pass: part 0 before it (thermostat half step,
+// kick-drift), part 1 after it (Langevin forces, kick, thermostat half step, momentum zeroing)
+int step_kernels(ap::Ctx& c, cudaStream_t s, double dt, int part) {
+    int k = 0;
+    if (part == 0) {
+        if (c.thermo_kind == AP_THERMO_NOSE_HOOVER) k += ap::launch_nh_half(c, s, dt);
+        k += ap::launch_kick_drift(c, s, dt, 1);
+        return k;
+    }
+    if (c.thermo_kind == AP_THERMO_LANGEVIN) k += ap::launch_langevin(c, s, dt);
+    k += ap::launch_kick(c, s, dt);
+    if (c.thermo_kind == AP_THERMO_NOSE_HOOVER) k += ap::launch_nh_half(c, s, dt);
+    if (c.thermo_kind == AP_THERMO_LANGEVIN && c.lv_zero_every > 0) k += ap::launch_zero_momentum(c, s);
+    return k;
+}
+
 bool capturable(cudaStream_t s) {
     return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
 }
@@ -532,11 +549,9 @@ ap_status ap_step(ap_ctx* xc, int n_steps, double dt, void* stream) {
     if (!c.forces_valid) run_forces(xc, s, nullptr);
     if (c.prof || !capturable(s) || n_steps == 0) {
         for (int k = 0; k < n_steps; ++k) {
-            if (c.thermo_kind) stage(xc, AP_STAGE_INTEGRATE, s, [&] { return ap::launch_nh_half(c, s, dt); });
-            stage(xc, AP_STAGE_INTEGRATE, s, [&] { return ap::launch_kick_drift(c, s, dt, 1); });
+            stage(xc, AP_STAGE_INTEGRATE, s, [&] { return step_kernels(c, s, dt, 0); });
             run_forces(xc, s, nullptr);
-            stage(xc, AP_STAGE_INTEGRATE, s, [&] { return ap::launch_kick(c, s, dt); });
-            if (c.thermo_kind) stage(xc, AP_STAGE_INTEGRATE, s, [&] { return ap::launch_nh_half(c, s, dt); });
+            stage(xc, AP_STAGE_INTEGRATE, s, [&] { return step_kernels(c, s, dt, 1); });
             c.t += dt;
             c.step += 1;
         }
@@ -550,11 +565,9 @@ ap_status ap_step(ap_ctx* xc, int n_steps, double dt, void* stream) {
         if (e != cudaSuccess) return e;
         const long long before = c.launches;
         for (int q = 0; q < k; ++q) {
-            if (c.thermo_kind) c.launches += ap::launch_nh_half(c, s, dt);
-            c.launches += ap::launch_kick_drift(c, s, dt, 1);
+            c.launches += step_kernels(c, s, dt, 0);
             run_forces(xc, s, nullptr);
-            c.launches += ap::launch_kick(c, s, dt);
-            if (c.thermo_kind) c.launches += ap::launch_nh_half(c, s, dt);
+            c.launches += step_kernels(c, s, dt, 1);
         }
         xc->step_kernels = (c.launches - before) / k;
         c.launches = before;
@@ -618,7 +631,9 @@ ap_status ap_compute_forces_batch(ap_ctx* const* ctxs, int n_ctx) {
 ap_status ap_set_thermostat(ap_ctx* xc, const ap_thermostat* t, const unsigned char* group) {
     if (!xc || !t) return AP_ERR_ARG;
     ap::Ctx& c = xc->c;
-    if (t->kind != AP_THERMO_NONE && t->kind != AP_THERMO_NOSE_HOOVER) return set_err(c, AP_ERR_ARG, "unknown thermostat kind");
+    if (t->kind != AP_THERMO_NONE && t->kind != AP_THERMO_NOSE_HOOVER && t->kind != AP_THERMO_LANGEVIN)
+        return set_err(c, AP_ERR_ARG, "unknown thermostat kind");
+    if (t->kind == AP_THERMO_LANGEVIN && t->zero_every < 0) return set_err(c, AP_ERR_ARG, "zero_every must be >= 0");
     cudaError_t e = cudaStreamSynchronize(c.stream);
     if (e != cudaSuccess) return cuda_check(c, e, "ap_set_thermostat");
     drop_step_graph(xc);
@@ -628,7 +643,8 @@ ap_status ap_set_thermostat(ap_ctx* xc, const ap_thermostat* t, const unsigned c
     const size_t N = (size_t)c.n;
     ap_status st;
     if (!c.thermo_group &&
-        ((st = dalloc(c, &c.thermo_group, N)) || (st = dalloc(c, &c.nh_state, 4)) || (st = dalloc(c, &c.nh_partials, (size_t)c.nred))))
+        ((st = dalloc(c, &c.thermo_group, N)) || (st = dalloc(c, &c.nh_state, 4)) || (st = dalloc(c, &c.nh_partials, (size_t)c.nred)) ||
+         (st = dalloc(c, &c.com, 4 * (size_t)c.nred + 4))))
         return st;
     std::vector<unsigned char> fx(N), g(N);
     e = cudaMemcpyAsync(fx.data(), c.fixed, N, cudaMemcpyDeviceToHost, c.stream);
@@ -642,6 +658,12 @@ ap_status ap_set_thermostat(ap_ctx* xc, const ap_thermostat* t, const unsigned c
     const double kB = 8.617333262e-5;
     c.nh_nfkt = 3.0 * (double)ng * kB * t->t_target;
     c.nh_Q = c.nh_nfkt * t->tau_fs * t->tau_fs;
+    // Langevin: drag m/tau and noise sqrt(2 m k_B T / (tau dt)) in eV/A (dt enters at the step)
+    c.lv_drag = c.mass / (t->tau_fs * ap::kFtm);
+    c.lv_sig = 2.0 * c.mass * kB * t->t_target / (t->tau_fs * ap::kFtm);   // / dt, sqrt at the step
+    c.lv_seed = t->seed;
+    c.lv_zero_every = t->zero_every;
+    c.lv_base = c.step;
     const double zero[4] = {0.0, 0.0, 1.0, 0.0};
     e = cudaMemcpyAsync(c.thermo_group, g.data(), N, cudaMemcpyHostToDevice, c.stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c.nh_state, zero, sizeof(zero), cudaMemcpyHostToDevice, c.stream);

@@ -6,6 +6,9 @@
 // V_indenter): V = K/3 (R - d)^3 for d < R, F = K (R - d)^2 (r - c)/d; load (Sec. 3.1,
 // Eq. P_ind) = sum F . dir.  Totals are summed per block in FP64 and then by one block
 // in a fixed order, so they are reproducible run to run.
+#include <cmath>
+#include <cstdint>
+
 #include "ap_internal.h"
 #include "geom.cuh"
 
@@ -14,7 +17,6 @@ namespace ap {
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
-constexpr double kFtm = 0.0096485332;      // 1 eV/(Angstrom amu) in Angstrom/fs^2
 constexpr int kNP = 10;                     // e_pot, e_ind, vir[6], load, spare
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -160,9 +162,9 @@ __global__ void k_reduce(const double* __restrict__ partials, int nblk, double* 
 
 __global__ void k_kick_drift(double* __restrict__ x, double* __restrict__ v, const float* __restrict__ f,
                              const unsigned char* __restrict__ fixed, int n, double hdta, double dt,
-                             double* __restrict__ tptr) {
+                             double* __restrict__ tptr, long long* __restrict__ step) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) *tptr += dt;
+    if (i == 0) { *tptr += dt; *step += 1; }
     if (i >= n || fixed[i]) return;
     for (int k = 0; k < 3; ++k) {
         double vk = v[(size_t)k * n + i] + hdta * (double)f[(size_t)k * n + i];
@@ -221,7 +223,93 @@ __global__ void k_scale_group(double* __restrict__ v, const unsigned char* __res
     for (int k = 0; k < 3; ++k) v[(size_t)k * n + i] *= sc;
 }
 
+// Philox4x32-10 (Salmon et al., SC'11): ten multiply-xor rounds with Weyl key increments
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    }
+}
+
+// Langevin drag and random force on the group, added to the forces of this step
+__global__ void k_langevin(const double* __restrict__ v, float* __restrict__ f, const unsigned char* __restrict__ group,
+                           int n, const long long* __restrict__ step, long long base, unsigned long long seed,
+                           double drag, double sig) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !group[i]) return;
+    uint32_t w[4] = {(uint32_t)i, (uint32_t)(*step - base), 0u, 0u};
+    philox4x32_10(w, (uint32_t)(seed & 0xffffffffull), (uint32_t)(seed >> 32));
+    const double two32 = 4294967296.0, tpi = 6.283185307179586476925;
+    const double r1 = sqrt(-2.0 * log(((double)w[0] + 1.0) / two32)), a1 = tpi * (((double)w[1] + 0.5) / two32);
+    const double r2 = sqrt(-2.0 * log(((double)w[2] + 1.0) / two32)), a2 = tpi * (((double)w[3] + 0.5) / two32);
+    const double g[3] = {r1 * cos(a1), r1 * sin(a1), r2 * cos(a2)};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const size_t q = (size_t)k * n + i;
+        f[q] = (float)((double)f[q] - drag * v[q] + sig * g[k]);
+    }
+}
+
+// momentum zeroing every `every` steps: block sums of the free atoms' velocities, their mean,
+// the subtraction
+__global__ void __launch_bounds__(kRedBlock) k_com_partial(const double* __restrict__ v,
+                                                           const unsigned char* __restrict__ fixed, int n,
+                                                           const long long* __restrict__ step, long long base, int every,
+                                                           double* __restrict__ part) {
+    if ((*step - base) % every != 0) return;
+    __shared__ double sh[32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool on = i < n && !fixed[i];
+    double q[4] = {on ? v[i] : 0.0, on ? v[n + i] : 0.0, on ? v[2 * n + i] : 0.0, on ? 1.0 : 0.0};
+    for (int k = 0; k < 4; ++k) {
+        const double s = block_sum(q[k], sh);
+        if (threadIdx.x == 0) part[4 * blockIdx.x + k] = s;
+    }
+}
+
+__global__ void k_com_final(const double* __restrict__ part, int nblk, const long long* __restrict__ step,
+                            long long base, int every, double* __restrict__ com) {
+    __shared__ double sh[32];
+    const bool go = (*step - base) % every == 0;
+    double tot[4];
+    for (int k = 0; k < 4; ++k) {
+        double v = 0.0;
+        if (go)
+            for (int b = threadIdx.x; b < nblk; b += blockDim.x) v += part[4 * b + k];
+        tot[k] = block_sum(v, sh);
+    }
+    if (threadIdx.x == 0) {
+        const bool any = go && tot[3] > 0.0;
+        for (int k = 0; k < 3; ++k) com[k] = any ? tot[k] / tot[3] : 0.0;
+        com[3] = any ? 1.0 : 0.0;
+    }
+}
+
+__global__ void k_sub_com(double* __restrict__ v, const unsigned char* __restrict__ fixed, int n,
+                          const double* __restrict__ com) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || fixed[i] || com[3] == 0.0) return;
+    for (int k = 0; k < 3; ++k) v[(size_t)k * n + i] -= com[k];
+}
+
 }  // namespace
+
+int launch_langevin(Ctx& c, cudaStream_t s, double dt) {
+    k_langevin<<<(c.n + 255) / 256, 256, 0, s>>>(c.v, c.f, c.thermo_group, c.n, c.d_step, c.lv_base, c.lv_seed,
+                                                 c.lv_drag, std::sqrt(c.lv_sig / dt));
+    return 1;
+}
+
+int launch_zero_momentum(Ctx& c, cudaStream_t s) {
+    k_com_partial<<<c.nred, kRedBlock, 0, s>>>(c.v, c.fixed, c.n, c.d_step, c.lv_base, c.lv_zero_every, c.com);
+    k_com_final<<<1, 1024, 0, s>>>(c.com, c.nred, c.d_step, c.lv_base, c.lv_zero_every, c.com + 4 * (size_t)c.nred);
+    k_sub_com<<<(c.n + 255) / 256, 256, 0, s>>>(c.v, c.fixed, c.n, c.com + 4 * (size_t)c.nred);
+    return 3;
+}
 
 int launch_nh_half(Ctx& c, cudaStream_t s, double dt) {
     k_group_ke<<<c.nred, kRedBlock, 0, s>>>(c.v, c.thermo_group, c.n, c.mass, c.nh_partials);
@@ -261,7 +349,8 @@ int launch_reduce(Ctx& c, cudaStream_t s, int with_kinetic) {
 }
 
 int launch_kick_drift(Ctx& c, cudaStream_t s, double dt, int) {
-    k_kick_drift<<<(c.n + 255) / 256, 256, 0, s>>>(c.x, c.v, c.f, c.fixed, c.n, 0.5 * dt * kFtm / c.mass, dt, c.d_time);
+    k_kick_drift<<<(c.n + 255) / 256, 256, 0, s>>>(c.x, c.v, c.f, c.fixed, c.n, 0.5 * dt * kFtm / c.mass, dt, c.d_time,
+                                                    c.d_step);
     return 1;
 }
 

@@ -88,3 +88,42 @@ def test_graph_replay_with_thermostat_is_bitwise_equal(apl):
         xb, vb, _ = b.get_state()
         assert np.array_equal(xa, xb) and np.array_equal(va, vb)
         assert a.energy()["e_thermostat"] == b.energy()["e_thermostat"]
+
+
+def test_langevin_md_matches_oracle(apl, orc):
+    """Langevin forces from the counter-based generator, momentum zeroing every 5 steps:
+    the same trajectory as the oracle's, which draws its normal numbers from its own
+    implementation of the same generator."""
+    c, group = _slab()
+    nsteps = 20
+    xo, vo, ep, ek, st = orc.md_langevin(c["x"], c["v"], c["box"], c["eam"], c["ace"], c["region"], c["indenter"],
+                                         c["ind_vel"], c["fixed"], group, 300.0, 100.0, 12345678901, 5, c["mass"],
+                                         1.0, nsteps)
+    assert st == 0
+    with _ctx(apl, c) as ctx:
+        ctx.set_thermostat(300.0, 100.0, group, kind="langevin", seed=12345678901, zero_every=5)
+        ctx.step(nsteps, 1.0)
+        rep = ctx.energy()
+        x, v, _ = ctx.get_state()
+    L = np.asarray(c["box"]["h"]).reshape(3, 3)
+    d = x - xo
+    for k in range(2):
+        d[:, k] -= np.round(d[:, k] / L[k, k]) * L[k, k]
+    n = len(x)
+    assert np.abs(d).max() < 1e-6 and np.abs(v - vo).max() < 1e-6
+    assert abs(rep["e_kin"] - ek[-1]) / n < 1e-6
+    free = c["fixed"] == 0
+    assert np.abs(v[free].sum(axis=0)).max() < 1e-9        # step 20 zeroed the momentum
+
+
+def test_langevin_graph_replay_is_bitwise_equal(apl):
+    import torch
+    c, group = _slab()
+    with _ctx(apl, c) as a, _ctx(apl, c, stream=torch.cuda.Stream()) as b:
+        for ctx in (a, b):
+            ctx.set_thermostat(500.0, 50.0, group, kind="langevin", seed=99, zero_every=3)
+            ctx.step(19, 1.0)
+        b.check()
+        xa, va, _ = a.get_state()
+        xb, vb, _ = b.get_state()
+        assert np.array_equal(xa, xb) and np.array_equal(va, vb)
