@@ -414,6 +414,8 @@ def main():
     ap_.add_argument("--variants", default="ace,eam", help="extra single-potential runs (comma list or 'none')")
     ap_.add_argument("--serve-requests", type=int, default=300,
                      help="requests in the serving run reported beside the metric (0: skip)")
+    ap_.add_argument("--serve-chunk", type=int, default=8, help="MD steps per request per scheduling pass")
+    ap_.add_argument("--serve-active", type=int, default=64, help="cap on concurrently active requests")
     ap_.add_argument("--mode", default="ap", choices=["ap", "serve", "precision", "autograd"],
                      help="ap: the metric line; serve: only the serving run; precision: the A_nlm "
                           "precision sweep on the 2M-atom Cu slab; autograd: forward+backward of the "
@@ -426,7 +428,7 @@ def main():
         import paper_2505_12958_gb300 as ap
         ap.build()
         if args.mode == "serve":
-            out = serving_bench(torch, args.serve_requests)
+            out = serving_bench(torch, args.serve_requests, chunk=args.serve_chunk, max_active=args.serve_active)
         elif args.mode == "precision":
             out = precision_sweep(torch, ap, args.steps, args.warmup)
         else:
@@ -513,7 +515,8 @@ def main():
                                  "ms_per_step": sum(msv) / kk}
         cv.close()
 
-    serving = serving_bench(torch, args.serve_requests) if args.serve_requests > 0 else None
+    serving = (serving_bench(torch, args.serve_requests, chunk=args.serve_chunk, max_active=args.serve_active)
+               if args.serve_requests > 0 else None)
     csp = csp_timing(torch, ap, c)
 
     if rank != 0:
