@@ -19,6 +19,14 @@ pulling each coefficient toward its seeded random value (weight lam = 1, relativ
 design matrix norm).  D(q) is linear in phi1's coefficients, so each column is one force-
 constant evaluation with a unit coefficient.  The three-factor coefficients and all of
 phi2 stay as drawn.
+Force constants alone leave the Cu (001) surface unstable in pure-ACE MD under an indenter
+(the top layer collapses within a few hundred steps).  For Cu the same least-squares problem
+therefore also matches the pure-ACE forces to the EAM forces on five distorted structures
+(thermally displaced bulk at 0, -4 % and +3 % strain, and two displaced (001) slabs with
+free surfaces): F(c) is linear in phi1's coefficients too, so each column is one force
+evaluation with a unit coefficient.  Both blocks of rows are divided by their Frobenius
+norms, the force block carries the weight FORCE_WEIGHT; W, whose pure-ACE surface is stable,
+keeps weight 0 and its force-constant-only fit.
 The fits and the offset are computed with the oracle only.
 """
 import json
@@ -37,10 +45,31 @@ from synth.params.lattice_dynamics import dynamical, force_constants, min_eigenv
 SPEC = {"Cu": (fcc, 3.615, 4), "W": (bcc, 3.165, 5)}
 NREF, C2_0, RC = 1.5, 2.0, 5.0
 LAM = 1.0
+FORCE_WEIGHT = {"Cu": 1.0, "W": 0.0}
+TRAIN = [(0.0, 0.10, False), (-0.04, 0.08, False), (0.03, 0.08, False), (0.0, 0.10, True), (0.0, 0.15, True)]
+
+
+def training_configs(sp):
+    """(x, box) of the force-matching structures: (strain, displacement sigma in A, slab)."""
+    lat, a0, n = SPEC[sp]
+    out = []
+    for k, (strain, sigma, slab) in enumerate(TRAIN):
+        a = a0 * (1.0 + strain)
+        x = lat(a, n, n, n)
+        x = x + np.random.default_rng(500 + k).normal(0.0, sigma, size=x.shape)
+        if slab:
+            box = {"h": np.diag([n * a, n * a, n * a + 20.0]).ravel(), "origin": (0.0, 0.0, -10.0),
+                   "periodic": (1, 1, 0)}
+        else:
+            box = {"h": np.diag([n * a] * 3).ravel(), "origin": (0.0, 0.0, 0.0), "periodic": (1, 1, 1)}
+        out.append((x, box))
+    return out
 
 
 def fit_pair_and_two_factor(sp):
-    """phi1 coefficients of the nu <= 2 functions (see the module docstring)."""
+    """phi1 coefficients of the nu <= 2 functions (see the module docstring): rows of
+    force constants (scaled by 1/||M_D||), of forces for Cu (FORCE_WEIGHT/||M_F||), and the
+    ridge sqrt(LAM/nfit) (c - drawn)."""
     ace = synth.ace_potential(sp)
     reg = {"kind": "const", "w": 1.0}
     nfit = int((ace["idx"][:, 0] <= 2).sum())
@@ -57,15 +86,37 @@ def fit_pair_and_two_factor(sp):
         unit["c1"][k] = 1.0
         Pk, _, _ = force_constants(sp, ace=unit, region=reg)
         cols.append((dynamical(Pk, R, q) - Db).ravel())
-    M = np.stack(cols, axis=1)
+    MD = np.stack(cols, axis=1)
+    tD = (DE - Db).ravel()
     drawn = ace["c1"][:nfit]
-    sc = np.sqrt(LAM) * np.linalg.norm(M) / np.sqrt(nfit)
-    c, *_ = np.linalg.lstsq(np.vstack([M, sc * np.eye(nfit)]), np.concatenate([(DE - Db).ravel(), sc * drawn]),
-                            rcond=None)
+    alpha = FORCE_WEIGHT[sp]
+    sr = np.sqrt(LAM / nfit)
+    nD = np.linalg.norm(MD)
+    A, b = [MD / nD], [tD / nD]
+    if alpha > 0:
+        fcols, tF = [], []
+        for x, box in training_configs(sp):
+            fb = oracle.evaluate(x, box, ace=base, region=reg)["forces"]
+            fe = oracle.evaluate(x, box, eam=synth.eam_potential(sp))["forces"]
+            tF.append((fe - fb).ravel())
+            cf = []
+            for k in range(nfit):
+                unit = dict(base, c1=base["c1"].copy())
+                unit["c1"][k] = 1.0
+                cf.append((oracle.evaluate(x, box, ace=unit, region=reg)["forces"] - fb).ravel())
+            fcols.append(np.stack(cf, axis=1))
+        MF, tF = np.vstack(fcols), np.concatenate(tF)
+        nF = np.linalg.norm(MF)
+        A.append(alpha * MF / nF)
+        b.append(alpha * tF / nF)
+    A.append(sr * np.eye(nfit))
+    b.append(sr * drawn)
+    c, *_ = np.linalg.lstsq(np.vstack(A), np.concatenate(b), rcond=None)
     fitted = dict(base, c1=base["c1"].copy())
     fitted["c1"][:nfit] = c
     Pf, _, _ = force_constants(sp, ace=fitted, region=reg)
-    info = {"n_fitted": nfit, "ridge_lam": LAM, "rms_shift_from_drawn": float(np.sqrt(np.mean((c - drawn) ** 2))),
+    info = {"n_fitted": nfit, "ridge_lam": LAM, "force_weight": alpha,
+            "rms_shift_from_drawn": float(np.sqrt(np.mean((c - drawn) ** 2))),
             "min_dynamical_eigenvalue_eV_A2": min_eigenvalue(Pf, R, L),
             "min_dynamical_eigenvalue_drawn_eV_A2": min_eigenvalue(*force_constants(sp, ace=ace, region=reg))}
     return [round(float(v), 12) for v in c], info

@@ -43,3 +43,19 @@ def test_cu_eam_zone_boundary_phonons(orc):
     for k, nu in thz.items():
         nu_got = np.sqrt(got[k] / (p["mass_amu"] * AMU_THZ2)) / (2 * np.pi)
         assert abs(nu_got - nu) / nu < 0.1, (k, nu_got, nu)
+
+
+def test_cu_ace_surface_forces_follow_the_eam(orc):
+    """The Cu ACE is also fitted to EAM forces on distorted bulk and (001) slabs, so on a
+    displaced slab that the fit never saw its pure-ACE forces track the EAM forces: a
+    surface that pure ACE pulls apart (the failure that fit prevents) gives errors of the
+    order of the forces themselves."""
+    from synth.lattice import fcc, random_displacements
+    a = 3.615
+    x = fcc(a, 5, 5, 4)
+    x = x + random_displacements(len(x), 0.1, 909)
+    box = {"h": np.diag([5 * a, 5 * a, 4 * a + 20.0]).ravel(), "origin": (0.0, 0.0, -10.0), "periodic": (1, 1, 0)}
+    fa = orc.evaluate(x, box, ace=synth.ace_potential("Cu"), region={"kind": "const", "w": 1.0})["forces"]
+    fe = orc.evaluate(x, box, eam=synth.eam_potential("Cu"))["forces"]
+    rms = lambda f: np.sqrt(np.mean(f ** 2))            # noqa: E731
+    assert rms(fa - fe) < 0.3 * rms(fe), (rms(fa - fe), rms(fe))
