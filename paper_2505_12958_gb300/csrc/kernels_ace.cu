@@ -222,10 +222,18 @@ __device__ __forceinline__ void all_y(float* d3, const float* A1, const float* T
     (ent_y<T, E>(d3, A1, Tm), ...);
 }
 
+// the first W entries of a 16-byte aligned row of A, in 128-bit loads (the padding of each
+// l-block covers the rounding up to a multiple of 4)
 template <int W>
 __device__ __forceinline__ void load_row(float* dst, const float* src) {
 #pragma unroll
-    for (int k = 0; k < W; ++k) dst[k] = src[k];
+    for (int k = 0; k < W; k += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(src + k);
+        dst[k] = v.x;
+        if (k + 1 < W) dst[k + 1] = v.y;
+        if (k + 2 < W) dst[k + 2] = v.z;
+        if (k + 3 < W) dst[k + 3] = v.w;
+    }
 }
 
 // sum_k P[k] * row[k] over a 16-byte aligned shared-memory row
@@ -274,58 +282,77 @@ __device__ __forceinline__ void axpy_row(float* Q, float ce, const float* row) {
 // The two (n1, n2) pairs of a lane and the n3 / n2 contractions are runtime loops; only the
 // Gaunt entries are unrolled (their operands are register-indexed), which keeps the code
 // of all 14 l-triples small enough for the instruction cache.
+
+// forward of one (n1, n2) pair: P[m3] = sum G A_n1 A_n2, then sum_n3 c_p[n1 n2 n3] P . A_n3
 template <int T>
-__device__ __forceinline__ void nu3_forward(const float* As, const AceDev& C, int lane, float& p1, float& p2) {
+__device__ __forceinline__ void nu3_forward_pair(const float* As, const AceDev& C, int n1, int n2, float& p1,
+                                                 float& p2) {
     using R = Tri<T>;
-#pragma unroll kPPUnroll
-    for (int pp = 0; pp < 2; ++pp) {
-        const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
-        float A1[R::W1], A2[R::W2], P[R::W3];
-        load_row<R::W1>(A1, As + n1 * kApad + R::B1);
-        load_row<R::W2>(A2, As + n2 * kApad + R::B2);
+    const int q = n1 * 8 + n2;
+    float A1[R::W1], A2[R::W2], P[R::W3];
+    load_row<R::W1>(A1, As + n1 * kApad + R::B1);
+    load_row<R::W2>(A2, As + n2 * kApad + R::B2);
 #pragma unroll
-        for (int k = 0; k < R::W3; ++k) P[k] = 0.0f;
-        all_p<T>(P, A1, A2, std::make_integer_sequence<int, R::N>{});
-        const float* c1 = &C.c3[0][T][0][q];
-        const float* c2 = &C.c3[1][T][0][q];
-        float s1 = 0.0f, s2 = 0.0f;
+    for (int k = 0; k < R::W3; ++k) P[k] = 0.0f;
+    all_p<T>(P, A1, A2, std::make_integer_sequence<int, R::N>{});
+    const float* c1 = &C.c3[0][T][0][q];
+    const float* c2 = &C.c3[1][T][0][q];
+    float s1 = 0.0f, s2 = 0.0f;
 #pragma unroll kN3Unroll
-        for (int n3 = 0; n3 < kNmax; ++n3) {
-            const float r = dot_row2<R::W3>(P, As + n3 * kApad + R::B3);
-            s1 = fmaf(c1[n3 * 65], r, s1);
-            s2 = fmaf(c2[n3 * 65], r, s2);
-        }
-        p1 += s1;
-        p2 += s2;
+    for (int n3 = 0; n3 < kNmax; ++n3) {
+        const float r = dot_row2<R::W3>(P, As + n3 * kApad + R::B3);
+        s1 = fmaf(c1[n3 * 65], r, s1);
+        s2 = fmaf(c2[n3 * 65], r, s2);
     }
+    p1 += s1;
+    p2 += s2;
 }
 
 template <int T>
-__device__ __forceinline__ void nu3_adjoint(const float* As, float* dAs, const AceDev& C, float s, int lane) {
+__device__ __forceinline__ void nu3_forward(const float* As, const AceDev& C, int lane, float& p1, float& p2) {
+#pragma unroll kPPUnroll
+    for (int pp = 0; pp < 2; ++pp) {
+        const int q = lane + 32 * pp;
+        nu3_forward_pair<T>(As, C, q >> 3, q & 7, p1, p2);
+    }
+}
+
+// adjoint of one (n1, n2) pair with respect to its first two factors:
+// Q[m3] = sum_n3 (c1 + s c2)[n1 n2 n3] A_n3, then d1 += G Q A_n2, d2 += G Q A_n1
+template <int T>
+__device__ __forceinline__ void nu3_adjoint_x_pair(const float* As, const AceDev& C, float s, int n1, int n2,
+                                                   float* d1, float* d2) {
     using R = Tri<T>;
-    // (n1, n2) mapping: gradients with respect to the first and second factor
+    const int q = n1 * 8 + n2;
+    float A1[R::W1], A2[R::W2], Q[R::W3];
+    load_row<R::W1>(A1, As + n1 * kApad + R::B1);
+    load_row<R::W2>(A2, As + n2 * kApad + R::B2);
+#pragma unroll
+    for (int m = 0; m < R::W3; ++m) Q[m] = 0.0f;
+    const float* c1 = &C.c3[0][T][0][q];
+    const float* c2 = &C.c3[1][T][0][q];
+#pragma unroll kN3Unroll
+    for (int n3 = 0; n3 < kNmax; ++n3) {
+        const float ce = fmaf(s, c2[n3 * 65], c1[n3 * 65]);
+        axpy_row<R::W3>(Q, ce, As + n3 * kApad + R::B3);
+    }
+    all_x<T>(d1, d2, A1, A2, Q, std::make_integer_sequence<int, R::N>{});
+}
+
+// (n1, n2) mapping: gradients with respect to the first and second factor
+template <int T>
+__device__ __forceinline__ void nu3_adjoint_x(const float* As, float* dAs, const AceDev& C, float s, int lane) {
+    using R = Tri<T>;
     float d2[R::W2];
 #pragma unroll
     for (int k = 0; k < R::W2; ++k) d2[k] = 0.0f;
 #pragma unroll kPPUnroll
     for (int pp = 0; pp < 2; ++pp) {
         const int q = lane + 32 * pp, n1 = q >> 3;
-        const int n2 = q & 7;
-        float A1[R::W1], A2[R::W2], Q[R::W3], d1[R::W1];
-        load_row<R::W1>(A1, As + n1 * kApad + R::B1);
-        load_row<R::W2>(A2, As + n2 * kApad + R::B2);
-#pragma unroll
-        for (int m = 0; m < R::W3; ++m) Q[m] = 0.0f;
-        const float* c1 = &C.c3[0][T][0][q];
-        const float* c2 = &C.c3[1][T][0][q];
-#pragma unroll kN3Unroll
-        for (int n3 = 0; n3 < kNmax; ++n3) {
-            const float ce = fmaf(s, c2[n3 * 65], c1[n3 * 65]);
-            axpy_row<R::W3>(Q, ce, As + n3 * kApad + R::B3);
-        }
+        float d1[R::W1];
 #pragma unroll
         for (int k = 0; k < R::W1; ++k) d1[k] = 0.0f;
-        all_x<T>(d1, d2, A1, A2, Q, std::make_integer_sequence<int, R::N>{});
+        nu3_adjoint_x_pair<T>(As, C, s, n1, q & 7, d1, d2);
 #pragma unroll
         for (int k = 0; k < R::W1; ++k) {
             float v = d1[k];
@@ -352,7 +379,12 @@ __device__ __forceinline__ void nu3_adjoint(const float* As, float* dAs, const A
         for (int k = 0; k < R::W2; ++k) dAs[lane * kApad + R::B2 + k] += d2[k];
     }
     __syncwarp();
-    // (n1, n3) mapping: gradient with respect to the third factor
+}
+
+// (n1, n3) mapping: gradient with respect to the third factor
+template <int T>
+__device__ __forceinline__ void nu3_adjoint_y(const float* As, float* dAs, const AceDev& C, float s, int lane) {
+    using R = Tri<T>;
     float d3[R::W3];
 #pragma unroll
     for (int k = 0; k < R::W3; ++k) d3[k] = 0.0f;
@@ -384,6 +416,98 @@ __device__ __forceinline__ void nu3_adjoint(const float* As, float* dAs, const A
     __syncwarp();
 }
 
+template <int T>
+__device__ __forceinline__ void nu3_adjoint(const float* As, float* dAs, const AceDev& C, float s, int lane) {
+    nu3_adjoint_x<T>(As, dAs, C, s, lane);
+    nu3_adjoint_y<T>(As, dAs, C, s, lane);
+}
+
+// ---------------------------------------------------------------------------------
+// l-triples with l1 = l2 carry only the (n1 <= n2) pairs, 36 of the 64 (the coefficients
+// of the others are zero).  k_ace_contract evaluates 32 of them in one lane pass and
+// leaves the four diagonal pairs (4,4) ... (7,7) to "diagonal units": one warp runs one
+// triple's diagonal pairs for all eight atoms of the block, lane (slot, k) = (lane / 4,
+// lane % 4) taking atom slot's pair (4 + k, 4 + k).
+// ---------------------------------------------------------------------------------
+constexpr int kDiag = 6;                       // l-triples with l1 = l2
+__host__ __device__ constexpr int diag_triple(int u) {   // (0,0,0) (1,1,2) (2,2,2) (2,2,4) (3,3,4) (4,4,4)
+    return u == 0 ? 0 : u == 1 ? 5 : u == 2 ? 8 : u == 3 ? 9 : u == 4 ? 12 : 13;
+}
+
+// folded lane mapping of the (n1 <= n2) pairs: lane (a, b) = (lane / 8, lane % 8) takes
+// (a, b) when b >= a (every pair of rows 0-3) and (7 - a, 7 - b) otherwise (the
+// off-diagonal pairs of rows 4-7)
+__device__ __forceinline__ void folded_pair(int lane, int& n1, int& n2, bool& lo) {
+    const int a = lane >> 3, b = lane & 7;
+    lo = b >= a;
+    n1 = lo ? a : 7 - a;
+    n2 = lo ? b : 7 - b;
+}
+
+template <int T>
+__device__ __forceinline__ void nu3_forward_main(const float* As, const AceDev& C, int lane, float& p1, float& p2) {
+    using R = Tri<T>;
+    if constexpr (R::L1 == R::L2) {
+        int n1, n2;
+        bool lo;
+        folded_pair(lane, n1, n2, lo);
+        nu3_forward_pair<T>(As, C, n1, n2, p1, p2);
+    } else {
+        nu3_forward<T>(As, C, lane, p1, p2);
+    }
+}
+
+// first- and second-factor gradients of the folded pass.  Both go to the same l-block.
+// Row sums: d1 of group a (8 lanes) belongs to row a (lo lanes) or 7 - a (hi lanes); d2 of
+// column b (4 lanes) to row b (lo) or 7 - b (hi).  Lane (a, b) with a = min(b, 7 - b)
+// gathers everything of row b and is its only writer.
+template <int T>
+__device__ __forceinline__ void nu3_adjoint_x_folded(const float* As, float* dAs, const AceDev& C, float s, int lane) {
+    using R = Tri<T>;
+    static_assert(R::L1 == R::L2, "folded pass needs l1 = l2");
+    constexpr int W = R::W1;
+    int n1, n2;
+    bool lo;
+    folded_pair(lane, n1, n2, lo);
+    float d1[W], d2[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) { d1[k] = 0.0f; d2[k] = 0.0f; }
+    nu3_adjoint_x_pair<T>(As, C, s, n1, n2, d1, d2);
+    const int b = lane & 7;
+    const bool low_row = b < 4;
+    const bool owner = (lane >> 3) == (low_row ? b : 7 - b);
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        float u = lo ? d1[k] : 0.0f, v = lo ? 0.0f : d1[k];
+        float x = lo ? d2[k] : 0.0f, y = lo ? 0.0f : d2[k];
+        u += __shfl_xor_sync(0xffffffffu, u, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        u += __shfl_xor_sync(0xffffffffu, u, 2);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        u += __shfl_xor_sync(0xffffffffu, u, 4);
+        v += __shfl_xor_sync(0xffffffffu, v, 4);
+        x += __shfl_xor_sync(0xffffffffu, x, 8);
+        y += __shfl_xor_sync(0xffffffffu, y, 8);
+        x += __shfl_xor_sync(0xffffffffu, x, 16);
+        y += __shfl_xor_sync(0xffffffffu, y, 16);
+        y = __shfl_xor_sync(0xffffffffu, y, 7);       // column 7 - b's hi sum belongs to row b
+        d1[k] = (low_row ? u : v) + x + y;
+    }
+    if (owner) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) dAs[b * kApad + R::B1 + k] += d1[k];
+    }
+    __syncwarp();
+}
+
+template <int T>
+__device__ __forceinline__ void nu3_adjoint_main(const float* As, float* dAs, const AceDev& C, float s, int lane) {
+    using R = Tri<T>;
+    if constexpr (R::L1 == R::L2) nu3_adjoint_x_folded<T>(As, dAs, C, s, lane);
+    else nu3_adjoint_x<T>(As, dAs, C, s, lane);
+    nu3_adjoint_y<T>(As, dAs, C, s, lane);
+}
+
 template <int... T>
 __device__ __forceinline__ void nu3_forward_all(const float* As, const AceDev& C, int lane, float& p1, float& p2,
                                                 std::integer_sequence<int, T...>) {
@@ -393,6 +517,17 @@ template <int... T>
 __device__ __forceinline__ void nu3_adjoint_all(const float* As, float* dAs, const AceDev& C, float s, int lane,
                                                 std::integer_sequence<int, T...>) {
     (nu3_adjoint<T>(As, dAs, C, s, lane), ...);
+}
+
+template <int... T>
+__device__ __forceinline__ void nu3_forward_main_all(const float* As, const AceDev& C, int lane, float& p1, float& p2,
+                                                     std::integer_sequence<int, T...>) {
+    (nu3_forward_main<T>(As, C, lane, p1, p2), ...);
+}
+template <int... T>
+__device__ __forceinline__ void nu3_adjoint_main_all(const float* As, float* dAs, const AceDev& C, float s, int lane,
+                                                     std::integer_sequence<int, T...>) {
+    (nu3_adjoint_main<T>(As, dAs, C, s, lane), ...);
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -627,24 +762,113 @@ __global__ void __launch_bounds__(256) k_ace_basis(const float4* __restrict__ po
     }
 }
 
+// 2368 bytes: the 64-byte pad puts the A of neighbouring warps 4 bank groups apart, so a
+// diagonal unit's lanes (8 atoms, one row each) read without bank conflicts
 struct ContractSmem {
     float A[kNmax * kApad];
     float dA[kNmax * kApad];
+    float pad[16];
 };
 
-constexpr int kContractWarps = 8;
+constexpr int kContractWarps = 8;              // atoms of the block per iteration (one per warp)
 
-// stage a5/a6 core: phi1, phi2, E = phi1 + sqrt(phi2) and dE/dA from A, one warp per atom
+// block-shared state of the diagonal units
+struct DiagSmem {
+    float pm[kContractWarps][2];               // phi1, phi2 sums of each warp's own passes
+    float lf[kDiag][kContractWarps][2];        // diagonal-unit sums per l1 = l2 triple and atom
+    float ldA[kContractWarps][4][kApad + 1];   // diagonal-unit gradients, rows n = 4..7 (odd stride:
+                                               // the 32 lanes of a unit write 32 different banks)
+};
+
+static_assert(sizeof(AceDev) % 16 == 0 && sizeof(ContractSmem) % 128 == 64, "A rows 16-byte aligned, warps 4 bank groups apart");
+
+// phi1, phi2 sums of atom slot, in a fixed order (every reader computes the same bits)
+__device__ __forceinline__ float2 phi_sums(const DiagSmem& D, int slot) {
+    float p1 = D.pm[slot][0], p2 = D.pm[slot][1];
+#pragma unroll
+    for (int u = 0; u < kDiag; ++u) {
+        p1 += D.lf[u][slot][0];
+        p2 += D.lf[u][slot][1];
+    }
+    return make_float2(p1, p2);
+}
+
+__device__ __forceinline__ bool phi_ok(const AceDev& C, float2 P) { return C.c2_0 + P.y > 1e-3f && P.x == P.x; }
+
+// forward of the diagonal pairs of triple diag_triple(U) for the 8 atoms of the block
+template <int U>
+__device__ __forceinline__ void diag_forward(const ContractSmem* WS, const AceDev& C, DiagSmem& D, int lane) {
+    const int slot = lane >> 2, n = 4 + (lane & 3);
+    float p1 = 0.0f, p2 = 0.0f;
+    nu3_forward_pair<diag_triple(U)>(WS[slot].A, C, n, n, p1, p2);
+    p1 += __shfl_xor_sync(0xffffffffu, p1, 1);
+    p2 += __shfl_xor_sync(0xffffffffu, p2, 1);
+    p1 += __shfl_xor_sync(0xffffffffu, p1, 2);
+    p2 += __shfl_xor_sync(0xffffffffu, p2, 2);
+    if ((lane & 3) == 0) { D.lf[U][slot][0] = p1; D.lf[U][slot][1] = p2; }
+}
+
+// first- and second-factor gradients of the diagonal pairs (both land in row n) for the
+// 8 atoms of the block, added to the block's diagonal-unit rows
+template <int U>
+__device__ __forceinline__ void diag_adjoint(const ContractSmem* WS, const AceDev& C, DiagSmem& D, int lane) {
+    constexpr int T = diag_triple(U);
+    using R = Tri<T>;
+    const int slot = lane >> 2, k = lane & 3, n = 4 + k;
+    const float2 P = phi_sums(D, slot);
+    const float s = phi_ok(C, P) ? 0.5f / sqrtf(C.c2_0 + P.y) : 0.0f;
+    float d1[R::W1], d2[R::W2];
+#pragma unroll
+    for (int m = 0; m < R::W1; ++m) { d1[m] = 0.0f; d2[m] = 0.0f; }
+    nu3_adjoint_x_pair<T>(WS[slot].A, C, s, n, n, d1, d2);
+#pragma unroll
+    for (int m = 0; m < R::W1; ++m) D.ldA[slot][k][R::B1 + m] += d1[m] + d2[m];
+}
+
+// Warp w runs these units.  The two l = 2 triples write the same rows of ldA, so one warp
+// runs both adjoint units.
+__device__ __forceinline__ void diag_forward_units(const ContractSmem* WS, const AceDev& C, DiagSmem& D, int warp,
+                                                   int lane) {
+    switch (warp) {
+        case 0: diag_forward<5>(WS, C, D, lane); break;
+        case 1: diag_forward<4>(WS, C, D, lane); break;
+        case 2: diag_forward<3>(WS, C, D, lane); break;
+        case 3: diag_forward<2>(WS, C, D, lane); break;
+        case 4: diag_forward<1>(WS, C, D, lane); break;
+        case 5: diag_forward<0>(WS, C, D, lane); break;
+        default: break;
+    }
+}
+
+__device__ __forceinline__ void diag_adjoint_units(const ContractSmem* WS, const AceDev& C, DiagSmem& D, int warp,
+                                                   int lane) {
+    switch (warp) {
+        case 0: diag_adjoint<5>(WS, C, D, lane); break;
+        case 1: diag_adjoint<4>(WS, C, D, lane); break;
+        case 2: diag_adjoint<3>(WS, C, D, lane); __syncwarp(); diag_adjoint<2>(WS, C, D, lane); break;
+        case 3: diag_adjoint<1>(WS, C, D, lane); break;
+        case 4: diag_adjoint<0>(WS, C, D, lane); break;
+        default: break;
+    }
+}
+
+// stage a5/a6 core: phi1, phi2, E = phi1 + sqrt(phi2) and dE/dA from A.  The block works on
+// 8 atoms at a time, one per warp; the diagonal units of the l1 = l2 triples run between
+// block barriers (their sums are needed before the adjoint, their gradients before the
+// write-out).
 __global__ void __launch_bounds__(kContractWarps * 32, 2)
 k_ace_contract(const AceDev* __restrict__ tab, const int* __restrict__ ace_list, int* __restrict__ flags,
                const float* __restrict__ Ain, float* __restrict__ dAout, float* __restrict__ e_ace) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     AceDev& C = *reinterpret_cast<AceDev*>(smem_raw);
     ContractSmem* WS = reinterpret_cast<ContractSmem*>(smem_raw + sizeof(AceDev));
+    DiagSmem& D = *reinterpret_cast<DiagSmem*>(smem_raw + sizeof(AceDev) + kContractWarps * sizeof(ContractSmem));
     {
         const int4* src = reinterpret_cast<const int4*>(tab);
         int4* dst = reinterpret_cast<int4*>(smem_raw);
         for (int k = threadIdx.x; k < (int)(sizeof(AceDev) / 16); k += blockDim.x) dst[k] = src[k];
+        float* z = &D.ldA[0][0][0];
+        for (int k = threadIdx.x; k < kContractWarps * 4 * (kApad + 1); k += blockDim.x) z[k] = 0.0f;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -656,17 +880,29 @@ k_ace_contract(const AceDev* __restrict__ tab, const int* __restrict__ ace_list,
     if (lane >= 9) lam_l = 3;
     if (lane >= 16) lam_l = 4;
     const int lam_pad = lblk(lam_l) + (lane - lam_l * lam_l);
-    for (int a = blockIdx.x * kContractWarps + warp; a < n_ace; a += gridDim.x * kContractWarps) {
-        for (int k = lane; k < kNmax * kApad; k += 32) { S.A[k] = 0.0f; S.dA[k] = 0.0f; }
-        __syncwarp();
+    // the padding of S.A stays zero; each iteration writes only the (l, m) entries
+    for (int k = lane; k < kNmax * kApad; k += 32) S.A[k] = 0.0f;
+    // A of this warp's next atom, loaded a phase ahead of its use
+    float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
+    {
+        const int a0 = blockIdx.x * kContractWarps + warp;
+        if (a0 < n_ace && lane < kNLM) {
+            const float4* src = reinterpret_cast<const float4*>(Ain + ((size_t)a0 * kNLM + lane) * kNmax);
+            g0 = src[0];
+            g1 = src[1];
+        }
+    }
+    // the loop bound is uniform over the block: every warp reaches every barrier
+    for (int base = blockIdx.x * kContractWarps; base < n_ace; base += gridDim.x * kContractWarps) {
+        const int a = base + warp;
+        const bool act = a < n_ace;
+        for (int k = lane; k < kNmax * kApad; k += 32) S.dA[k] = 0.0f;
         if (lane < kNLM) {
-            const float4* src = reinterpret_cast<const float4*>(Ain + ((size_t)a * kNLM + lane) * kNmax);
-            const float4 g0 = src[0], g1 = src[1];
             const float v[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
 #pragma unroll
-            for (int q = 0; q < kNmax; ++q) S.A[q * kApad + lam_pad] = v[q];
+            for (int q = 0; q < kNmax; ++q) S.A[q * kApad + lam_pad] = act ? v[q] : 0.0f;
         }
-        __syncwarp();
+        __syncthreads();                                   // every atom's A is visible
         float p1 = 0.0f, p2 = 0.0f;
         if (lane < kNmax) {
             const float a0 = S.A[lane * kApad];
@@ -686,79 +922,103 @@ k_ace_contract(const AceDev* __restrict__ tab, const int* __restrict__ ace_list,
                 p2 = fmaf(C.c2[1][l][q], mm, p2);
             }
         }
-        nu3_forward_all(S.A, C, lane, p1, p2, std::make_integer_sequence<int, kNT>{});
+        nu3_forward_main_all(S.A, C, lane, p1, p2, std::make_integer_sequence<int, kNT>{});
         p1 = warp_sum(p1);
         p2 = warp_sum(p2);
-        const int i = ace_list[a];
-        const float phi2 = C.c2_0 + p2;
-        if (!(phi2 > 1e-3f) || !(p1 == p1)) {
-            if (lane == 0) { atomicOr(&flags[kFlagErr], kErrDomain); flags[kFlagBad] = i; e_ace[i] = __int_as_float(0x7fc00000); }
-            // zero adjoint: the force stage then adds nothing for this atom
-            if (lane < kNLM) {
-                float4* o = reinterpret_cast<float4*>(dAout + ((size_t)a * kNLM + lane) * kNmax);
-                o[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-                o[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lane == 0) { D.pm[warp][0] = p1; D.pm[warp][1] = p2; }
+        diag_forward_units(WS, C, D, warp, lane);
+        __syncthreads();                                   // every sum of the block is visible
+        {
+            const int an = a + gridDim.x * kContractWarps;
+            if (an < n_ace && lane < kNLM) {
+                const float4* src = reinterpret_cast<const float4*>(Ain + ((size_t)an * kNLM + lane) * kNmax);
+                g0 = src[0];
+                g1 = src[1];
             }
-            continue;
         }
-        const float sq = sqrtf(phi2);
-        const float s = 0.5f / sq;
-        if (lane < kNmax) S.dA[lane * kApad] += fmaf(s, C.c1[1][lane], C.c1[0][lane]);
-        __syncwarp();
+        const float2 P = phi_sums(D, warp);
+        const bool ok = phi_ok(C, P);
+        const float sq = ok ? sqrtf(C.c2_0 + P.y) : 0.0f;
+        if (ok) {
+            const float s = 0.5f / sq;
+            if (lane < kNmax) S.dA[lane * kApad] += fmaf(s, C.c1[1][lane], C.c1[0][lane]);
+            __syncwarp();
 #pragma unroll
-        for (int l = 0; l <= kLmax; ++l) {
-            constexpr int WM = 9;
-            float d2[WM];
+            for (int l = 0; l <= kLmax; ++l) {
+                constexpr int WM = 9;
+                float d2[WM];
 #pragma unroll
-            for (int k = 0; k < WM; ++k) d2[k] = 0.0f;
+                for (int k = 0; k < WM; ++k) d2[k] = 0.0f;
 #pragma unroll 1
-            for (int pp = 0; pp < 2; ++pp) {
-                const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
-                const float c = fmaf(s, C.c2[1][l][q], C.c2[0][l][q]);
-                float d1[WM];
+                for (int pp = 0; pp < 2; ++pp) {
+                    const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
+                    const float c = fmaf(s, C.c2[1][l][q], C.c2[0][l][q]);
+                    float d1[WM];
 #pragma unroll
-                for (int k = 0; k < 2 * l + 1; ++k) {
-                    const float a1 = S.A[n1 * kApad + lblk(l) + k], a2 = S.A[n2 * kApad + lblk(l) + k];
-                    d1[k] = c * a2;
-                    d2[k] = fmaf(c, a1, d2[k]);
+                    for (int k = 0; k < 2 * l + 1; ++k) {
+                        const float a1 = S.A[n1 * kApad + lblk(l) + k], a2 = S.A[n2 * kApad + lblk(l) + k];
+                        d1[k] = c * a2;
+                        d2[k] = fmaf(c, a1, d2[k]);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 2 * l + 1; ++k) {
+                        float v = d1[k];
+                        v += __shfl_xor_sync(0xffffffffu, v, 1);
+                        v += __shfl_xor_sync(0xffffffffu, v, 2);
+                        v += __shfl_xor_sync(0xffffffffu, v, 4);
+                        d1[k] = v;
+                    }
+                    if ((lane & 7) == 0) {
+#pragma unroll
+                        for (int k = 0; k < 2 * l + 1; ++k) S.dA[n1 * kApad + lblk(l) + k] += d1[k];
+                    }
+                    __syncwarp();
                 }
 #pragma unroll
                 for (int k = 0; k < 2 * l + 1; ++k) {
-                    float v = d1[k];
-                    v += __shfl_xor_sync(0xffffffffu, v, 1);
-                    v += __shfl_xor_sync(0xffffffffu, v, 2);
-                    v += __shfl_xor_sync(0xffffffffu, v, 4);
-                    d1[k] = v;
+                    float v = d2[k];
+                    v += __shfl_xor_sync(0xffffffffu, v, 8);
+                    v += __shfl_xor_sync(0xffffffffu, v, 16);
+                    d2[k] = v;
                 }
-                if ((lane & 7) == 0) {
+                if (lane < 8) {
 #pragma unroll
-                    for (int k = 0; k < 2 * l + 1; ++k) S.dA[n1 * kApad + lblk(l) + k] += d1[k];
+                    for (int k = 0; k < 2 * l + 1; ++k) S.dA[lane * kApad + lblk(l) + k] += d2[k];
                 }
                 __syncwarp();
             }
-#pragma unroll
-            for (int k = 0; k < 2 * l + 1; ++k) {
-                float v = d2[k];
-                v += __shfl_xor_sync(0xffffffffu, v, 8);
-                v += __shfl_xor_sync(0xffffffffu, v, 16);
-                d2[k] = v;
-            }
-            if (lane < 8) {
-#pragma unroll
-                for (int k = 0; k < 2 * l + 1; ++k) S.dA[lane * kApad + lblk(l) + k] += d2[k];
-            }
-            __syncwarp();
+            nu3_adjoint_main_all(S.A, S.dA, C, s, lane, std::make_integer_sequence<int, kNT>{});
         }
-        nu3_adjoint_all(S.A, S.dA, C, s, lane, std::make_integer_sequence<int, kNT>{});
-        if (lane < kNLM) {
-            float v[kNmax];
-#pragma unroll
-            for (int q = 0; q < kNmax; ++q) v[q] = S.dA[q * kApad + lam_pad];
-            float4* o = reinterpret_cast<float4*>(dAout + ((size_t)a * kNLM + lane) * kNmax);
-            o[0] = make_float4(v[0], v[1], v[2], v[3]);
-            o[1] = make_float4(v[4], v[5], v[6], v[7]);
+        diag_adjoint_units(WS, C, D, warp, lane);
+        __syncthreads();                                   // every diagonal gradient is in ldA
+        for (int e = lane; e < 4 * kApad; e += 32) {
+            const int r = e / kApad, m = e - r * kApad;
+            S.dA[(4 + r) * kApad + m] += D.ldA[warp][r][m];
+            D.ldA[warp][r][m] = 0.0f;
         }
-        if (lane == 0) e_ace[i] = p1 + sq;
+        __syncwarp();
+        if (act) {
+            const int i = ace_list[a];
+            if (!ok) {
+                if (lane == 0) { atomicOr(&flags[kFlagErr], kErrDomain); flags[kFlagBad] = i; e_ace[i] = __int_as_float(0x7fc00000); }
+                // zero adjoint: the force stage then adds nothing for this atom
+                if (lane < kNLM) {
+                    float4* o = reinterpret_cast<float4*>(dAout + ((size_t)a * kNLM + lane) * kNmax);
+                    o[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    o[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            } else {
+                if (lane < kNLM) {
+                    float v[kNmax];
+#pragma unroll
+                    for (int q = 0; q < kNmax; ++q) v[q] = S.dA[q * kApad + lam_pad];
+                    float4* o = reinterpret_cast<float4*>(dAout + ((size_t)a * kNLM + lane) * kNmax);
+                    o[0] = make_float4(v[0], v[1], v[2], v[3]);
+                    o[1] = make_float4(v[4], v[5], v[6], v[7]);
+                }
+                if (lane == 0) e_ace[i] = P.x + sq;
+            }
+        }
         __syncwarp();
     }
 }
@@ -839,7 +1099,9 @@ __global__ void __launch_bounds__(256) k_ace_force(const float4* __restrict__ po
 
 size_t ace_smem_bytes() { return sizeof(AceDev) + 128 * sizeof(float4) + kWarps * sizeof(WarpSmem); }
 
-size_t ace_contract_smem_bytes() { return sizeof(AceDev) + kContractWarps * sizeof(ContractSmem); }
+size_t ace_contract_smem_bytes() {
+    return sizeof(AceDev) + kContractWarps * sizeof(ContractSmem) + sizeof(DiagSmem);
+}
 
 // Persistent grids: as many resident blocks per SM as the kernel's registers and shared
 // memory allow (the gather kernels are latency-bound, so every resident warp helps),
