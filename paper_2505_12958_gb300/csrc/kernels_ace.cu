@@ -425,14 +425,12 @@ __device__ __forceinline__ void nu3_adjoint(const float* As, float* dAs, const A
 // ---------------------------------------------------------------------------------
 // l-triples with l1 = l2 carry only the (n1 <= n2) pairs, 36 of the 64 (the coefficients
 // of the others are zero).  k_ace_contract evaluates 32 of them in one lane pass and
-// leaves the four diagonal pairs (4,4) ... (7,7) to "diagonal units": one warp runs one
+// leaves the four diagonal pairs (4,4) ... (7,7) to "diagonal units": one warp of the
+// block (the triple's unit warp) runs a second trip through the same code that takes the
 // triple's diagonal pairs for all eight atoms of the block, lane (slot, k) = (lane / 4,
 // lane % 4) taking atom slot's pair (4 + k, 4 + k).
 // ---------------------------------------------------------------------------------
 constexpr int kDiag = 6;                       // l-triples with l1 = l2
-__host__ __device__ constexpr int diag_triple(int u) {   // (0,0,0) (1,1,2) (2,2,2) (2,2,4) (3,3,4) (4,4,4)
-    return u == 0 ? 0 : u == 1 ? 5 : u == 2 ? 8 : u == 3 ? 9 : u == 4 ? 12 : 13;
-}
 
 // folded lane mapping of the (n1 <= n2) pairs: lane (a, b) = (lane / 8, lane % 8) takes
 // (a, b) when b >= a (every pair of rows 0-3) and (7 - a, 7 - b) otherwise (the
@@ -444,14 +442,76 @@ __device__ __forceinline__ void folded_pair(int lane, int& n1, int& n2, bool& lo
     n2 = lo ? b : 7 - b;
 }
 
+// 2368 bytes: the 64-byte pad puts the A of neighbouring warps 4 bank groups apart, so a
+// diagonal unit's lanes (8 atoms, one row each) read without bank conflicts
+struct ContractSmem {
+    float A[kNmax * kApad];
+    float dA[kNmax * kApad];
+    float pad[16];
+};
+
+constexpr int kContractWarps = 8;              // atoms of the block per iteration (one per warp)
+
+// block-shared state of the diagonal units
+struct DiagSmem {
+    float pm[kContractWarps][2];               // phi1, phi2 sums of each warp's own passes
+    float lf[kDiag][kContractWarps][2];        // diagonal-unit sums per l1 = l2 triple and atom
+    float ldA[kContractWarps][4][kApad + 1];   // diagonal-unit gradients, rows n = 4..7 (odd stride:
+                                               // the 32 lanes of a unit write 32 different banks)
+};
+
+static_assert(sizeof(AceDev) % 16 == 0 && sizeof(ContractSmem) % 128 == 64,
+              "A rows 16-byte aligned, warps 4 bank groups apart");
+
+// phi1, phi2 sums of atom slot, in a fixed order (every reader computes the same bits)
+__device__ __forceinline__ float2 phi_sums(const DiagSmem& D, int slot) {
+    float p1 = D.pm[slot][0], p2 = D.pm[slot][1];
+#pragma unroll
+    for (int u = 0; u < kDiag; ++u) {
+        p1 += D.lf[u][slot][0];
+        p2 += D.lf[u][slot][1];
+    }
+    return make_float2(p1, p2);
+}
+
+__device__ __forceinline__ bool phi_ok(const AceDev& C, float2 P) { return C.c2_0 + P.y > 1e-3f && P.x == P.x; }
+
+// unit index u of the l1 = l2 triples (0,0,0) (1,1,2) (2,2,2) (2,2,4) (3,3,4) (4,4,4), and the
+// warp that runs unit u; the two l = 2 triples write the same rows of ldA and share a warp
+__host__ __device__ constexpr int diag_unit_of(int t) {
+    return t == 0 ? 0 : t == 5 ? 1 : t == 8 ? 2 : t == 9 ? 3 : t == 12 ? 4 : 5;
+}
+__host__ __device__ constexpr int diag_warp(int u) { return u == 5 ? 0 : u == 4 ? 1 : u == 3 || u == 2 ? 2 : u == 1 ? 3 : 4; }
+
+// phi sums of the forward: an l1 = l2 triple's folded pass, and on its unit warp a second
+// trip through the same code for the diagonal pairs of the block's 8 atoms (lane (slot, k)
+// = (lane / 4, lane % 4) takes atom slot's pair (4 + k, 4 + k))
 template <int T>
-__device__ __forceinline__ void nu3_forward_main(const float* As, const AceDev& C, int lane, float& p1, float& p2) {
+__device__ __forceinline__ void nu3_forward_main(const ContractSmem* WS, const float* As, const AceDev& C, DiagSmem& D,
+                                                 int warp, int lane, float& p1, float& p2) {
     using R = Tri<T>;
     if constexpr (R::L1 == R::L2) {
+        constexpr int U = diag_unit_of(T);
         int n1, n2;
         bool lo;
         folded_pair(lane, n1, n2, lo);
-        nu3_forward_pair<T>(As, C, n1, n2, p1, p2);
+        const int slot = lane >> 2, nd = 4 + (lane & 3);
+        const int trips = warp == diag_warp(U) ? 2 : 1;
+#pragma unroll 1
+        for (int t = 0; t < trips; ++t) {
+            float a1 = 0.0f, a2 = 0.0f;
+            nu3_forward_pair<T>(t ? WS[slot].A : As, C, t ? nd : n1, t ? nd : n2, a1, a2);
+            if (t == 0) {
+                p1 += a1;
+                p2 += a2;
+            } else {
+                a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
+                a2 += __shfl_xor_sync(0xffffffffu, a2, 1);
+                a1 += __shfl_xor_sync(0xffffffffu, a1, 2);
+                a2 += __shfl_xor_sync(0xffffffffu, a2, 2);
+                if ((lane & 3) == 0) { D.lf[U][slot][0] = a1; D.lf[U][slot][1] = a2; }
+            }
+        }
     } else {
         nu3_forward<T>(As, C, lane, p1, p2);
     }
@@ -461,49 +521,66 @@ __device__ __forceinline__ void nu3_forward_main(const float* As, const AceDev& 
 // Row sums: d1 of group a (8 lanes) belongs to row a (lo lanes) or 7 - a (hi lanes); d2 of
 // column b (4 lanes) to row b (lo) or 7 - b (hi).  Lane (a, b) with a = min(b, 7 - b)
 // gathers everything of row b and is its only writer.
+// On the triple's unit warp a second trip through the same code takes the diagonal pairs
+// of the block's 8 atoms, each lane with its atom's scale s, and adds their gradients
+// (both to row n) to the block's ldA rows.
 template <int T>
-__device__ __forceinline__ void nu3_adjoint_x_folded(const float* As, float* dAs, const AceDev& C, float s, int lane) {
+__device__ __forceinline__ void nu3_adjoint_x_folded(const ContractSmem* WS, const float* As, float* dAs,
+                                                     const AceDev& C, DiagSmem& D, float s, float s_slot, int warp,
+                                                     int lane) {
     using R = Tri<T>;
     static_assert(R::L1 == R::L2, "folded pass needs l1 = l2");
     constexpr int W = R::W1;
+    constexpr int U = diag_unit_of(T);
     int n1, n2;
     bool lo;
     folded_pair(lane, n1, n2, lo);
-    float d1[W], d2[W];
+    const int slot = lane >> 2, kd = lane & 3, nd = 4 + kd;
+    const int trips = warp == diag_warp(U) ? 2 : 1;
+#pragma unroll 1
+    for (int t = 0; t < trips; ++t) {
+        float d1[W], d2[W];
 #pragma unroll
-    for (int k = 0; k < W; ++k) { d1[k] = 0.0f; d2[k] = 0.0f; }
-    nu3_adjoint_x_pair<T>(As, C, s, n1, n2, d1, d2);
-    const int b = lane & 7;
-    const bool low_row = b < 4;
-    const bool owner = (lane >> 3) == (low_row ? b : 7 - b);
+        for (int k = 0; k < W; ++k) { d1[k] = 0.0f; d2[k] = 0.0f; }
+        nu3_adjoint_x_pair<T>(t ? WS[slot].A : As, C, t ? s_slot : s, t ? nd : n1, t ? nd : n2, d1, d2);
+        if (t) {
 #pragma unroll
-    for (int k = 0; k < W; ++k) {
-        float u = lo ? d1[k] : 0.0f, v = lo ? 0.0f : d1[k];
-        float x = lo ? d2[k] : 0.0f, y = lo ? 0.0f : d2[k];
-        u += __shfl_xor_sync(0xffffffffu, u, 1);
-        v += __shfl_xor_sync(0xffffffffu, v, 1);
-        u += __shfl_xor_sync(0xffffffffu, u, 2);
-        v += __shfl_xor_sync(0xffffffffu, v, 2);
-        u += __shfl_xor_sync(0xffffffffu, u, 4);
-        v += __shfl_xor_sync(0xffffffffu, v, 4);
-        x += __shfl_xor_sync(0xffffffffu, x, 8);
-        y += __shfl_xor_sync(0xffffffffu, y, 8);
-        x += __shfl_xor_sync(0xffffffffu, x, 16);
-        y += __shfl_xor_sync(0xffffffffu, y, 16);
-        y = __shfl_xor_sync(0xffffffffu, y, 7);       // column 7 - b's hi sum belongs to row b
-        d1[k] = (low_row ? u : v) + x + y;
+            for (int m = 0; m < W; ++m) D.ldA[slot][kd][R::B1 + m] += d1[m] + d2[m];
+        } else {
+            const int b = lane & 7;
+            const bool low_row = b < 4;
+            const bool owner = (lane >> 3) == (low_row ? b : 7 - b);
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                float u = lo ? d1[k] : 0.0f, v = lo ? 0.0f : d1[k];
+                float x = lo ? d2[k] : 0.0f, y = lo ? 0.0f : d2[k];
+                u += __shfl_xor_sync(0xffffffffu, u, 1);
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                u += __shfl_xor_sync(0xffffffffu, u, 2);
+                v += __shfl_xor_sync(0xffffffffu, v, 2);
+                u += __shfl_xor_sync(0xffffffffu, u, 4);
+                v += __shfl_xor_sync(0xffffffffu, v, 4);
+                x += __shfl_xor_sync(0xffffffffu, x, 8);
+                y += __shfl_xor_sync(0xffffffffu, y, 8);
+                x += __shfl_xor_sync(0xffffffffu, x, 16);
+                y += __shfl_xor_sync(0xffffffffu, y, 16);
+                y = __shfl_xor_sync(0xffffffffu, y, 7);       // column 7 - b's hi sum belongs to row b
+                d1[k] = (low_row ? u : v) + x + y;
+            }
+            if (owner) {
+#pragma unroll
+                for (int k = 0; k < W; ++k) dAs[b * kApad + R::B1 + k] += d1[k];
+            }
+            __syncwarp();
+        }
     }
-    if (owner) {
-#pragma unroll
-        for (int k = 0; k < W; ++k) dAs[b * kApad + R::B1 + k] += d1[k];
-    }
-    __syncwarp();
 }
 
 template <int T>
-__device__ __forceinline__ void nu3_adjoint_main(const float* As, float* dAs, const AceDev& C, float s, int lane) {
+__device__ __forceinline__ void nu3_adjoint_main(const ContractSmem* WS, const float* As, float* dAs, const AceDev& C,
+                                                 DiagSmem& D, float s, float s_slot, int warp, int lane) {
     using R = Tri<T>;
-    if constexpr (R::L1 == R::L2) nu3_adjoint_x_folded<T>(As, dAs, C, s, lane);
+    if constexpr (R::L1 == R::L2) nu3_adjoint_x_folded<T>(WS, As, dAs, C, D, s, s_slot, warp, lane);
     else nu3_adjoint_x<T>(As, dAs, C, s, lane);
     nu3_adjoint_y<T>(As, dAs, C, s, lane);
 }
@@ -520,14 +597,16 @@ __device__ __forceinline__ void nu3_adjoint_all(const float* As, float* dAs, con
 }
 
 template <int... T>
-__device__ __forceinline__ void nu3_forward_main_all(const float* As, const AceDev& C, int lane, float& p1, float& p2,
+__device__ __forceinline__ void nu3_forward_main_all(const ContractSmem* WS, const float* As, const AceDev& C,
+                                                     DiagSmem& D, int warp, int lane, float& p1, float& p2,
                                                      std::integer_sequence<int, T...>) {
-    (nu3_forward_main<T>(As, C, lane, p1, p2), ...);
+    (nu3_forward_main<T>(WS, As, C, D, warp, lane, p1, p2), ...);
 }
 template <int... T>
-__device__ __forceinline__ void nu3_adjoint_main_all(const float* As, float* dAs, const AceDev& C, float s, int lane,
-                                                     std::integer_sequence<int, T...>) {
-    (nu3_adjoint_main<T>(As, dAs, C, s, lane), ...);
+__device__ __forceinline__ void nu3_adjoint_main_all(const ContractSmem* WS, const float* As, float* dAs,
+                                                     const AceDev& C, DiagSmem& D, float s, float s_slot, int warp,
+                                                     int lane, std::integer_sequence<int, T...>) {
+    (nu3_adjoint_main<T>(WS, As, dAs, C, D, s, s_slot, warp, lane), ...);
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -762,100 +841,11 @@ __global__ void __launch_bounds__(256) k_ace_basis(const float4* __restrict__ po
     }
 }
 
-// 2368 bytes: the 64-byte pad puts the A of neighbouring warps 4 bank groups apart, so a
-// diagonal unit's lanes (8 atoms, one row each) read without bank conflicts
-struct ContractSmem {
-    float A[kNmax * kApad];
-    float dA[kNmax * kApad];
-    float pad[16];
-};
-
-constexpr int kContractWarps = 8;              // atoms of the block per iteration (one per warp)
-
-// block-shared state of the diagonal units
-struct DiagSmem {
-    float pm[kContractWarps][2];               // phi1, phi2 sums of each warp's own passes
-    float lf[kDiag][kContractWarps][2];        // diagonal-unit sums per l1 = l2 triple and atom
-    float ldA[kContractWarps][4][kApad + 1];   // diagonal-unit gradients, rows n = 4..7 (odd stride:
-                                               // the 32 lanes of a unit write 32 different banks)
-};
-
-static_assert(sizeof(AceDev) % 16 == 0 && sizeof(ContractSmem) % 128 == 64, "A rows 16-byte aligned, warps 4 bank groups apart");
-
-// phi1, phi2 sums of atom slot, in a fixed order (every reader computes the same bits)
-__device__ __forceinline__ float2 phi_sums(const DiagSmem& D, int slot) {
-    float p1 = D.pm[slot][0], p2 = D.pm[slot][1];
-#pragma unroll
-    for (int u = 0; u < kDiag; ++u) {
-        p1 += D.lf[u][slot][0];
-        p2 += D.lf[u][slot][1];
-    }
-    return make_float2(p1, p2);
-}
-
-__device__ __forceinline__ bool phi_ok(const AceDev& C, float2 P) { return C.c2_0 + P.y > 1e-3f && P.x == P.x; }
-
-// forward of the diagonal pairs of triple diag_triple(U) for the 8 atoms of the block
-template <int U>
-__device__ __forceinline__ void diag_forward(const ContractSmem* WS, const AceDev& C, DiagSmem& D, int lane) {
-    const int slot = lane >> 2, n = 4 + (lane & 3);
-    float p1 = 0.0f, p2 = 0.0f;
-    nu3_forward_pair<diag_triple(U)>(WS[slot].A, C, n, n, p1, p2);
-    p1 += __shfl_xor_sync(0xffffffffu, p1, 1);
-    p2 += __shfl_xor_sync(0xffffffffu, p2, 1);
-    p1 += __shfl_xor_sync(0xffffffffu, p1, 2);
-    p2 += __shfl_xor_sync(0xffffffffu, p2, 2);
-    if ((lane & 3) == 0) { D.lf[U][slot][0] = p1; D.lf[U][slot][1] = p2; }
-}
-
-// first- and second-factor gradients of the diagonal pairs (both land in row n) for the
-// 8 atoms of the block, added to the block's diagonal-unit rows
-template <int U>
-__device__ __forceinline__ void diag_adjoint(const ContractSmem* WS, const AceDev& C, DiagSmem& D, int lane) {
-    constexpr int T = diag_triple(U);
-    using R = Tri<T>;
-    const int slot = lane >> 2, k = lane & 3, n = 4 + k;
-    const float2 P = phi_sums(D, slot);
-    const float s = phi_ok(C, P) ? 0.5f / sqrtf(C.c2_0 + P.y) : 0.0f;
-    float d1[R::W1], d2[R::W2];
-#pragma unroll
-    for (int m = 0; m < R::W1; ++m) { d1[m] = 0.0f; d2[m] = 0.0f; }
-    nu3_adjoint_x_pair<T>(WS[slot].A, C, s, n, n, d1, d2);
-#pragma unroll
-    for (int m = 0; m < R::W1; ++m) D.ldA[slot][k][R::B1 + m] += d1[m] + d2[m];
-}
-
-// Warp w runs these units.  The two l = 2 triples write the same rows of ldA, so one warp
-// runs both adjoint units.
-__device__ __forceinline__ void diag_forward_units(const ContractSmem* WS, const AceDev& C, DiagSmem& D, int warp,
-                                                   int lane) {
-    switch (warp) {
-        case 0: diag_forward<5>(WS, C, D, lane); break;
-        case 1: diag_forward<4>(WS, C, D, lane); break;
-        case 2: diag_forward<3>(WS, C, D, lane); break;
-        case 3: diag_forward<2>(WS, C, D, lane); break;
-        case 4: diag_forward<1>(WS, C, D, lane); break;
-        case 5: diag_forward<0>(WS, C, D, lane); break;
-        default: break;
-    }
-}
-
-__device__ __forceinline__ void diag_adjoint_units(const ContractSmem* WS, const AceDev& C, DiagSmem& D, int warp,
-                                                   int lane) {
-    switch (warp) {
-        case 0: diag_adjoint<5>(WS, C, D, lane); break;
-        case 1: diag_adjoint<4>(WS, C, D, lane); break;
-        case 2: diag_adjoint<3>(WS, C, D, lane); __syncwarp(); diag_adjoint<2>(WS, C, D, lane); break;
-        case 3: diag_adjoint<1>(WS, C, D, lane); break;
-        case 4: diag_adjoint<0>(WS, C, D, lane); break;
-        default: break;
-    }
-}
-
 // stage a5/a6 core: phi1, phi2, E = phi1 + sqrt(phi2) and dE/dA from A.  The block works on
-// 8 atoms at a time, one per warp; the diagonal units of the l1 = l2 triples run between
-// block barriers (their sums are needed before the adjoint, their gradients before the
-// write-out).
+// 8 atoms at a time, one per warp, in three barrier-separated phases: the forward (after
+// every atom's A is in shared memory, since the diagonal units read all of them), the
+// adjoint (after every phi sum is complete, since the units need each atom's scale), and
+// the write-out (after the units' gradients are in ldA).
 __global__ void __launch_bounds__(kContractWarps * 32, 2)
 k_ace_contract(const AceDev* __restrict__ tab, const int* __restrict__ ace_list, int* __restrict__ flags,
                const float* __restrict__ Ain, float* __restrict__ dAout, float* __restrict__ e_ace) {
@@ -922,11 +912,10 @@ k_ace_contract(const AceDev* __restrict__ tab, const int* __restrict__ ace_list,
                 p2 = fmaf(C.c2[1][l][q], mm, p2);
             }
         }
-        nu3_forward_main_all(S.A, C, lane, p1, p2, std::make_integer_sequence<int, kNT>{});
+        nu3_forward_main_all(WS, S.A, C, D, warp, lane, p1, p2, std::make_integer_sequence<int, kNT>{});
         p1 = warp_sum(p1);
         p2 = warp_sum(p2);
         if (lane == 0) { D.pm[warp][0] = p1; D.pm[warp][1] = p2; }
-        diag_forward_units(WS, C, D, warp, lane);
         __syncthreads();                                   // every sum of the block is visible
         {
             const int an = a + gridDim.x * kContractWarps;
@@ -939,8 +928,13 @@ k_ace_contract(const AceDev* __restrict__ tab, const int* __restrict__ ace_list,
         const float2 P = phi_sums(D, warp);
         const bool ok = phi_ok(C, P);
         const float sq = ok ? sqrtf(C.c2_0 + P.y) : 0.0f;
-        if (ok) {
-            const float s = 0.5f / sq;
+        // the scale of atom slot lane / 4, for the diagonal trips of this warp
+        const float2 Ps = phi_sums(D, lane >> 2);
+        const float s_slot = phi_ok(C, Ps) ? 0.5f / sqrtf(C.c2_0 + Ps.y) : 0.0f;
+        {
+            // an atom outside the domain runs with s = 0 (its results are discarded); its warp
+            // may carry a diagonal trip for the other atoms
+            const float s = ok ? 0.5f / sq : 0.0f;
             if (lane < kNmax) S.dA[lane * kApad] += fmaf(s, C.c1[1][lane], C.c1[0][lane]);
             __syncwarp();
 #pragma unroll
@@ -987,9 +981,8 @@ k_ace_contract(const AceDev* __restrict__ tab, const int* __restrict__ ace_list,
                 }
                 __syncwarp();
             }
-            nu3_adjoint_main_all(S.A, S.dA, C, s, lane, std::make_integer_sequence<int, kNT>{});
+            nu3_adjoint_main_all(WS, S.A, S.dA, C, D, s, s_slot, warp, lane, std::make_integer_sequence<int, kNT>{});
         }
-        diag_adjoint_units(WS, C, D, warp, lane);
         __syncthreads();                                   // every diagonal gradient is in ldA
         for (int e = lane; e < 4 * kApad; e += 32) {
             const int r = e / kApad, m = e - r * kApad;
