@@ -10,6 +10,7 @@
 // square root per atom); pair terms are FP32 piecewise polynomials from the host tables.
 #include "ap_internal.h"
 #include "eam_table.h"
+#include "geom.cuh"
 
 namespace ap {
 
@@ -205,6 +206,21 @@ __device__ __forceinline__ void pair_acc_df(const EamDev& T, float rf, float tl,
     pl = __fadd_rn(pl, __fadd_rn(__fadd_rn(q2.z, xue), d * tl));
 }
 
+// the FP32 residual of x_rel for the energy pass: the FP64 difference x - cell origin that
+// k_prepare rounded to FP32, minus that FP32 value
+__global__ void k_pos_lo(const double* __restrict__ x, int n, const GridDev g, const int* __restrict__ cell,
+                         const float4* __restrict__ pos4, float4* __restrict__ pos_lo) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int cc[3];
+    cell_coords(g, cell[i], cc);
+    double o[3];
+    cell_origin(g, cc, o);
+    const float4 p = pos4[i];
+    pos_lo[i] = make_float4((float)((x[i] - o[0]) - (double)p.x), (float)((x[n + i] - o[1]) - (double)p.y),
+                            (float)((x[2 * (size_t)n + i] - o[2]) - (double)p.z), 0.0f);
+}
+
 __global__ void __launch_bounds__(256) k_eam_energy(const float4* __restrict__ pos4, const float4* __restrict__ pos_lo,
                                                     const int* __restrict__ nbr, const int* __restrict__ nnbr, int n,
                                                     const EamDev* __restrict__ eam, const float4* __restrict__ D,
@@ -281,9 +297,10 @@ __global__ void __launch_bounds__(256) k_eam_energy(const float4* __restrict__ p
 }  // namespace
 
 int launch_eam_energy(Ctx& c, cudaStream_t s) {
+    k_pos_lo<<<(c.n + 255) / 256, 256, 0, s>>>(c.x, c.n, c.grid, c.cell, c.pos4, c.pos_lo);
     k_eam_energy<<<(c.n + 255) / 256, 256, 0, s>>>(c.pos4, c.pos_lo, c.nbr, c.nnbr, c.n, c.eam_d, c.D, c.Dlo,
                                                    c.grid.ncode, c.uxi, c.e_eam, c.vir_eam);
-    return 1;
+    return 2;
 }
 
 int launch_eam_density(Ctx& c, cudaStream_t s) {

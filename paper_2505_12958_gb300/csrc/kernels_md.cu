@@ -42,9 +42,25 @@ __global__ void k_pos_in(const double* __restrict__ pos, int n, double* __restri
 // per step: F_i = F_i^EAM (carries u) + ACE sum (carries w) - grad w_i (E^ACE - E^EAM) + F_ind
 __global__ void __launch_bounds__(kRedBlock) k_blend(
     const double* __restrict__ x, int n, const GridDev g, const DynDev dy, const double* __restrict__ tptr,
+    const float4* __restrict__ pos4, const int* __restrict__ cell,
     const float* __restrict__ wv, float* __restrict__ f, unsigned long long* __restrict__ acc,
     const float* __restrict__ e_ace, const double* __restrict__ e_eam, double c1_0, float* __restrict__ out_aos,
     int* __restrict__ flags) {
+    // FP64 runs at 1/64 of the FP32 rate on this GPU.  Positions are taken in FP32 from the
+    // cell origin and x_rel (absolute error ~1e-5 A) for the indenter pre-test, inside its
+    // margin, and for the weight-gradient force of the switching shell, whose relative error
+    // of ~1e-6 stays far below the force bar; only atoms near the tip read FP64 positions.
+    __shared__ float sh[12];         // box origin, cell edges, tip centre and zone centre at time t
+    if (threadIdx.x == 0 && g.ortho) {
+        const double t = *tptr;
+        for (int q = 0; q < 3; ++q) {
+            sh[q] = (float)g.origin[q];
+            sh[3 + q] = (float)g.cellvec[4 * q];
+            sh[6 + q] = (float)(dy.ind_c0[q] - dy.ind_vel[q] * t);
+            sh[9 + q] = (float)(dy.reg_c0[q] - (dy.follow ? dy.ind_vel[q] * t : 0.0));
+        }
+    }
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float wi = wv[i];
@@ -52,13 +68,44 @@ __global__ void __launch_bounds__(kRedBlock) k_blend(
     for (int k = 0; k < 3; ++k) {
         const long long q = (long long)acc[(size_t)k * n + i];
         acc[(size_t)k * n + i] = 0ull;
-        F[k] = f[(size_t)k * n + i] + (float)((double)q * (1.0 / kFixScale));
+        // q 2^-40 without FP64 instructions: q = hi 2^32 + lo, lo in [0, 2^32); hi 2^-8 is
+        // exact in FP32 for forces below 2^16 eV/A and the sum is rounded once
+        const int hi = (int)(q >> 32);
+        const unsigned lo = (unsigned)(q & 0xffffffffll);
+        F[k] = f[(size_t)k * n + i] + fmaf((float)hi, 0x1p-8f, (float)lo * 0x1p-40f);
     }
     const bool trans = dy.reg_kind == AP_REGION_SPHERE && wi > 0.0f && wi < 1.0f;
-    if (trans || dy.ind_on) {
+    bool near_tip = dy.ind_on;
+    if (g.ortho && (trans || near_tip)) {
+        const float4 p = pos4[i];
+        int cc[3];
+        cell_coords(g, cell[i], cc);
+        float xf[3];
+        xf[0] = fmaf((float)cc[0], sh[3], sh[0]) + p.x;
+        xf[1] = fmaf((float)cc[1], sh[4], sh[1]) + p.y;
+        xf[2] = fmaf((float)cc[2], sh[5], sh[2]) + p.z;
+        if (near_tip) {
+            const float d[3] = {xf[0] - sh[6], xf[1] - sh[7], xf[2] - sh[8]};
+            near_tip = min_image_d2_f32v(g, d) < dy.ind_R2_hi;
+        }
+        if (trans) {
+            float d[3] = {xf[0] - sh[9], xf[1] - sh[10], xf[2] - sh[11]};
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                if (g.periodic[k]) d[k] = fmaf(-g.Lf[k], rintf(d[k] * g.Linvf[k]), d[k]);
+            const float d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2], dist = sqrtf(d2);
+            const float rin = (float)dy.r_in, rsw = (float)dy.r_sw;
+            const float a = fminf(fmaxf((dist - rin) / rsw, 0.0f), 1.0f);
+            const float dS = -3.14159265358979f / rsw * sinpif(0.5f * a) * cospif(0.5f * a);
+            const float de = (float)((c1_0 + (double)e_ace[i]) - e_eam[i]);
+            const float gi = dS * de / dist;
+            for (int k = 0; k < 3; ++k) F[k] -= gi * d[k];
+        }
+    }
+    if ((trans && !g.ortho) || near_tip) {
         const double t = *tptr;
         const double r[3] = {x[i], x[n + i], x[2 * n + i]};
-        if (trans) {
+        if (trans && !g.ortho) {
             double d[3];
             for (int k = 0; k < 3; ++k) d[k] = r[k] - (dy.reg_c0[k] - (dy.follow ? dy.ind_vel[k] * t : 0.0));
             min_image_vec(g, d);
@@ -69,16 +116,14 @@ __global__ void __launch_bounds__(kRedBlock) k_blend(
             const float gi = dS * de * rsqrtf((float)d2);
             for (int k = 0; k < 3; ++k) F[k] -= gi * (float)d[k];
         }
-        if (dy.ind_on) {
+        if (near_tip) {
             double d[3];
             for (int k = 0; k < 3; ++k) d[k] = r[k] - (dy.ind_c0[k] - dy.ind_vel[k] * t);
-            if (!g.ortho || min_image_d2_f32(g, d) < dy.ind_R2_hi) {
-                min_image_vec(g, d);
-                const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                if (d2 < dy.R * dy.R && d2 > 0.0) {
-                    const double dist = sqrt(d2), h = dy.R - dist, c = dy.K * h * h / dist;
-                    for (int k = 0; k < 3; ++k) F[k] += (float)(c * d[k]);
-                }
+            min_image_vec(g, d);
+            const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (d2 < dy.R * dy.R && d2 > 0.0) {
+                const double dist = sqrt(d2), h = dy.R - dist, c = dy.K * h * h / dist;
+                for (int k = 0; k < 3; ++k) F[k] += (float)(c * d[k]);
             }
         }
     }
@@ -324,8 +369,8 @@ int launch_pos_in(Ctx& c, cudaStream_t s, const double* pos) {
 }
 
 int launch_blend(Ctx& c, cudaStream_t s, float* out_aos) {
-    k_blend<<<c.nred, kRedBlock, 0, s>>>(c.x, c.n, c.grid, c.dyn, c.d_time, c.w, c.f, c.acc, c.e_ace, c.e_eam,
-                                         c.ace_c1_0, out_aos, c.flags);
+    k_blend<<<c.nred, kRedBlock, 0, s>>>(c.x, c.n, c.grid, c.dyn, c.d_time, c.pos4, c.cell, c.w, c.f, c.acc, c.e_ace,
+                                         c.e_eam, c.ace_c1_0, out_aos, c.flags);
     return 1;
 }
 

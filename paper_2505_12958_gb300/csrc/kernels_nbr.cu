@@ -19,13 +19,6 @@ namespace ap {
 
 namespace {
 
-__device__ __forceinline__ void cell_coords(const GridDev& g, int c, int* cc) {
-    cc[2] = c % g.nc[2];
-    int r = c / g.nc[2];
-    cc[1] = r % g.nc[1];
-    cc[0] = r / g.nc[1];
-}
-
 __global__ void k_check(const double* __restrict__ x, const double* __restrict__ xb, int n, double lim2,
                         int* flags) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -117,57 +110,71 @@ __global__ void k_sort_cells(int* __restrict__ cell_atoms, const int* __restrict
     fill[c] = 0;
 }
 
-// per step: FP32 cell-relative positions, ACE weights, compaction of w > 0
+// Per step: x_rel = x - cell origin as FP32 (the force kernels' coordinates), the weight
+// w_i of the fixed zone, and the compaction of the atoms with w > 0.  FP64 runs at 1/64 of
+// the FP32 rate on this GPU, so the region test is first taken in FP32 from the cell origin
+// and x_rel (absolute error ~1e-5 A, far inside the pre-test margins); only atoms the FP32
+// test cannot place (the switching shell and its edges) take the FP64 path.  The FP32
+// residual of x_rel is formed on demand, for the energy pass (k_pos_lo).
 __global__ void k_prepare(const double* __restrict__ x, int n, const GridDev g, const DynDev dy,
                           const double* __restrict__ tptr, const int* __restrict__ cell,
-                          const double* __restrict__ w_fixed, float4* __restrict__ pos4, float4* __restrict__ pos_lo,
-                          float* __restrict__ wout,
-                          int* __restrict__ ace_list, int* __restrict__ flags) {
+                          const double* __restrict__ w_fixed, float4* __restrict__ pos4,
+                          float* __restrict__ wout, int* __restrict__ ace_list, int* __restrict__ flags) {
+    __shared__ float sh[9];          // box origin, cell edges (orthorhombic), zone centre at time t
+    if (threadIdx.x == 0 && dy.reg_kind == AP_REGION_SPHERE && g.ortho) {
+        const double t = *tptr;
+        for (int q = 0; q < 3; ++q) {
+            sh[q] = (float)g.origin[q];
+            sh[3 + q] = (float)g.cellvec[4 * q];
+            sh[6 + q] = (float)(dy.reg_c0[q] - (dy.follow ? dy.ind_vel[q] * t : 0.0));
+        }
+    }
+    __syncthreads();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double w = 0.0;
-    float u = 1.0f;
+    float wf = 0.0f;
+    bool need = false;                 // w > 0, decided in the precision w is given in
     if (i < n) {
         double r[3] = {x[i], x[n + i], x[2 * n + i]};
         int cc[3];
         cell_coords(g, cell[i], cc);
         double o[3];
-        if (g.ortho) {
-            for (int q = 0; q < 3; ++q) o[q] = g.origin[q] + cc[q] * g.cellvec[4 * q];
-        } else {
-            for (int q = 0; q < 3; ++q)
-                o[q] = g.origin[q] + cc[0] * g.cellvec[q] + cc[1] * g.cellvec[3 + q] + cc[2] * g.cellvec[6 + q];
-        }
+        cell_origin(g, cc, o);
+        const float hx = (float)(r[0] - o[0]), hy = (float)(r[1] - o[1]), hz = (float)(r[2] - o[2]);
+        float u = 1.0f;
         if (dy.reg_kind == AP_REGION_CONST) {
-            w = dy.w_const;
-            u = (float)(1.0 - w);
+            wf = (float)dy.w_const;
+            u = (float)(1.0 - dy.w_const);
+            need = dy.w_const > 0.0;
         } else if (dy.reg_kind == AP_REGION_EXPLICIT) {
-            w = w_fixed[i];
+            const double w = w_fixed[i];
+            wf = (float)w;
             u = (float)(1.0 - w);
+            need = w > 0.0;
         } else if (dy.reg_kind == AP_REGION_SPHERE) {
-            const double t = *tptr;
-            double d[3];
-            for (int q = 0; q < 3; ++q) d[q] = r[q] - (dy.reg_c0[q] - (dy.follow ? dy.ind_vel[q] * t : 0.0));
-            const float d2f = g.ortho ? min_image_d2_f32(g, d) : -1.0f;
+            float d2f = -1.0f;
+            if (g.ortho) {
+                const float h[3] = {hx, hy, hz};
+                float d[3];
+                for (int q = 0; q < 3; ++q) d[q] = (fmaf((float)cc[q], sh[3 + q], sh[q]) - sh[6 + q]) + h[q];
+                d2f = min_image_d2_f32v(g, d);
+            }
             if (d2f >= 0.0f && d2f < dy.reg_in2_lo) {
-                w = 1.0;
+                wf = 1.0f;
                 u = 0.0f;
-            } else if (d2f > dy.reg_out2_hi) {
-                w = 0.0;
-                u = 1.0f;
-            } else {
+            } else if (!(d2f > dy.reg_out2_hi)) {
+                const double t = *tptr;
+                double d[3];
+                for (int q = 0; q < 3; ++q) d[q] = r[q] - (dy.reg_c0[q] - (dy.follow ? dy.ind_vel[q] * t : 0.0));
                 min_image_vec(g, d);
                 float dS;
-                w = switch_weight(d[0] * d[0] + d[1] * d[1] + d[2] * d[2], dy.r_in, dy.r_sw, &u, &dS);
+                wf = switch_weight(d[0] * d[0] + d[1] * d[1] + d[2] * d[2], dy.r_in, dy.r_sw, &u, &dS);
             }
+            need = wf > 0.0f;
         }
-        const double rel[3] = {r[0] - o[0], r[1] - o[1], r[2] - o[2]};
-        const float hx = (float)rel[0], hy = (float)rel[1], hz = (float)rel[2];
         pos4[i] = make_float4(hx, hy, hz, u);
-        pos_lo[i] = make_float4((float)(rel[0] - hx), (float)(rel[1] - hy), (float)(rel[2] - hz), 0.0f);
-        wout[i] = (float)w;
+        wout[i] = wf;
     }
     // warp-aggregated compaction of the atoms that need ACE
-    bool need = (i < n) && (w > 0.0);
     unsigned mask = __ballot_sync(0xffffffffu, need);
     if (mask) {
         int lane = threadIdx.x & 31;
@@ -248,8 +255,8 @@ int launch_rebuild(Ctx& c, cudaStream_t s) {
 }
 
 int launch_prepare(Ctx& c, cudaStream_t s) {
-    k_prepare<<<(c.n + 255) / 256, 256, 0, s>>>(c.x, c.n, c.grid, c.dyn, c.d_time, c.cell, c.w_fixed, c.pos4,
-                                               c.pos_lo, c.w, c.ace_list, c.flags);
+    k_prepare<<<(c.n + 255) / 256, 256, 0, s>>>(c.x, c.n, c.grid, c.dyn, c.d_time, c.cell, c.w_fixed, c.pos4, c.w,
+                                               c.ace_list, c.flags);
     return 1;
 }
 
