@@ -31,6 +31,32 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return s;                               // valid on thread 0
 }
 
+// NV sums over a block of kRedBlock threads in a fixed order (each value added once: FP64
+// adds run at 1/64 of the FP32 rate on this GPU, so no butterfly that repeats them on every
+// lane); red holds NV * (kRedBlock + 1) doubles.  Thread k < NV returns sum k.
+template <int NV>
+__device__ __forceinline__ double block_sums(const double* v, double* red) {
+    constexpr int kChunks = kRedBlock / 32;
+    const int t = threadIdx.x;
+    for (int k = 0; k < NV; ++k) red[k * (kRedBlock + 1) + t] = v[k];
+    __syncthreads();
+    double part = 0.0;
+    if (t < NV * kChunks) {
+        const double* r = red + (t / kChunks) * (kRedBlock + 1) + 32 * (t % kChunks);
+        part = r[0];
+        for (int q = 1; q < 32; ++q) part += r[q];
+    }
+    __syncthreads();
+    if (t < NV * kChunks) red[t] = part;
+    __syncthreads();
+    double s = 0.0;
+    if (t < NV) {
+        s = red[t * kChunks];
+        for (int c = 1; c < kChunks; ++c) s += red[t * kChunks + c];
+    }
+    return s;
+}
+
 __global__ void k_pos_in(const double* __restrict__ pos, int n, double* __restrict__ x) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -139,18 +165,39 @@ __global__ void __launch_bounds__(kRedBlock) k_blend(
 // on request: per-atom E_i + V_ind, and block sums of the energies, the virial and the load
 __global__ void __launch_bounds__(kRedBlock) k_energy_blend(
     const double* __restrict__ x, int n, const GridDev g, const DynDev dy, const double* __restrict__ tptr,
-    const float* __restrict__ wv, const float4* __restrict__ pos4, const float* __restrict__ e_ace,
-    const double* __restrict__ e_eam, double c1_0,
+    const float* __restrict__ wv, const float4* __restrict__ pos4, const int* __restrict__ cell,
+    const float* __restrict__ e_ace, const double* __restrict__ e_eam, double c1_0,
     const float* __restrict__ vir_eam, const float* __restrict__ vir_ace, double* __restrict__ e_atom,
     double* __restrict__ partials, int* __restrict__ flags) {
-    __shared__ double sh[32];
+    __shared__ double red[9 * (kRedBlock + 1)];
+    __shared__ float sh[9];          // box origin, cell edges (orthorhombic), tip centre at time t
+    if (threadIdx.x == 0 && dy.ind_on && g.ortho) {
+        const double t = *tptr;
+        for (int q = 0; q < 3; ++q) {
+            sh[q] = (float)g.origin[q];
+            sh[3 + q] = (float)g.cellvec[4 * q];
+            sh[6 + q] = (float)(dy.ind_c0[q] - dy.ind_vel[q] * t);
+        }
+    }
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double acc_e = 0.0, acc_i = 0.0, acc_l = 0.0, vv[6] = {0, 0, 0, 0, 0, 0};
+    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};     // E, V_ind, virial (6), load
     if (i < n) {
-        const double wi = wv[i], ui = pos4[i].w;         // both weights at FP32 relative precision
+        const float4 p = pos4[i];
+        const double wi = wv[i], ui = p.w;              // both weights at FP32 relative precision
         const double Ei = (wi > 0.0 ? wi * (c1_0 + (double)e_ace[i]) : 0.0) + (ui > 0.0 ? ui * e_eam[i] : 0.0);
         double V = 0.0;
-        if (dy.ind_on) {
+        bool near_tip = dy.ind_on;
+        if (near_tip && g.ortho) {
+            // FP32 pre-test (positions to ~1e-5 A, inside the margin of ind_R2_hi)
+            int cc[3];
+            cell_coords(g, cell[i], cc);
+            const float h[3] = {p.x, p.y, p.z};
+            float d[3];
+            for (int q = 0; q < 3; ++q) d[q] = (fmaf((float)cc[q], sh[3 + q], sh[q]) - sh[6 + q]) + h[q];
+            near_tip = min_image_d2_f32v(g, d) < dy.ind_R2_hi;
+        }
+        if (near_tip) {
             const double t = *tptr;
             double d[3];
             for (int k = 0; k < 3; ++k) d[k] = x[(size_t)k * n + i] - (dy.ind_c0[k] - dy.ind_vel[k] * t);
@@ -160,25 +207,22 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_blend(
                 const double dist = sqrt(d2), h = dy.R - dist;
                 V = dy.K * h * h * h / 3.0;
                 const double c = dy.K * h * h / dist;
-                acc_l = c * (d[0] * dy.ind_dir[0] + d[1] * dy.ind_dir[1] + d[2] * dy.ind_dir[2]);
+                acc[8] = c * (d[0] * dy.ind_dir[0] + d[1] * dy.ind_dir[1] + d[2] * dy.ind_dir[2]);
             }
         }
         e_atom[i] = Ei + V;
-        acc_e = Ei;
-        acc_i = V;
+        acc[0] = Ei;
+        acc[1] = V;
+        // per-atom virial: the FP32 sum of the two parts (relative error ~6e-8 per atom)
         for (int k = 0; k < 6; ++k)
-            vv[k] = (double)vir_eam[(size_t)k * n + i] + (wi > 0.0 ? (double)vir_ace[(size_t)k * n + i] : 0.0);
+            acc[2 + k] = (double)(vir_eam[(size_t)k * n + i] + (wi > 0.0 ? vir_ace[(size_t)k * n + i] : 0.0f));
         if (!(Ei == Ei)) {
             atomicOr(&flags[kFlagErr], kErrDomain);
             flags[kFlagBad] = i;
         }
     }
-    double* out = partials + (size_t)blockIdx.x * kNP;
-    double s;
-    s = block_sum(acc_e, sh); if (threadIdx.x == 0) out[0] = s;
-    s = block_sum(acc_i, sh); if (threadIdx.x == 0) out[1] = s;
-    for (int k = 0; k < 6; ++k) { s = block_sum(vv[k], sh); if (threadIdx.x == 0) out[2 + k] = s; }
-    s = block_sum(acc_l, sh); if (threadIdx.x == 0) out[8] = s;
+    const double s = block_sums<9>(acc, red);
+    if (threadIdx.x < 9) partials[(size_t)blockIdx.x * kNP + threadIdx.x] = s;
 }
 
 __global__ void __launch_bounds__(kRedBlock) k_kinetic(const double* __restrict__ v, const unsigned char* __restrict__ fixed,
@@ -194,15 +238,14 @@ __global__ void __launch_bounds__(kRedBlock) k_kinetic(const double* __restrict_
     if (threadIdx.x == 0) partials[(size_t)blockIdx.x * kNP + 9] = s;
 }
 
-__global__ void k_reduce(const double* __restrict__ partials, int nblk, double* __restrict__ totals, int with_ke) {
-    __shared__ double sh[32];
-    for (int k = 0; k < kNP; ++k) {
-        if (k == 9 && !with_ke) continue;
-        double v = 0.0;
-        for (int b = threadIdx.x; b < nblk; b += blockDim.x) v += partials[(size_t)b * kNP + k];
-        double s = block_sum(v, sh);
-        if (threadIdx.x == 0) totals[k] = s;
-    }
+__global__ void __launch_bounds__(kRedBlock) k_reduce(const double* __restrict__ partials, int nblk,
+                                                        double* __restrict__ totals, int with_ke) {
+    __shared__ double red[kNP * (kRedBlock + 1)];
+    double v[kNP] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblk; b += kRedBlock)
+        for (int k = 0; k < kNP; ++k) v[k] += partials[(size_t)b * kNP + k];
+    const double s = block_sums<kNP>(v, red);
+    if (threadIdx.x < kNP && (threadIdx.x != 9 || with_ke)) totals[threadIdx.x] = s;
 }
 
 __global__ void k_kick_drift(double* __restrict__ x, double* __restrict__ v, const float* __restrict__ f,
@@ -378,8 +421,9 @@ int launch_eam_energy(Ctx& c, cudaStream_t s);
 
 int launch_energy(Ctx& c, cudaStream_t s) {
     int k = launch_eam_energy(c, s);
-    k_energy_blend<<<c.nred, kRedBlock, 0, s>>>(c.x, c.n, c.grid, c.dyn, c.d_time, c.w, c.pos4, c.e_ace, c.e_eam, c.ace_c1_0,
-                                                c.vir_eam, c.vir_ace, c.e_atom, c.partials, c.flags);
+    k_energy_blend<<<c.nred, kRedBlock, 0, s>>>(c.x, c.n, c.grid, c.dyn, c.d_time, c.w, c.pos4, c.cell, c.e_ace,
+                                                c.e_eam, c.ace_c1_0, c.vir_eam, c.vir_ace, c.e_atom, c.partials,
+                                                c.flags);
     return k + 1;
 }
 
@@ -389,7 +433,7 @@ int launch_reduce(Ctx& c, cudaStream_t s, int with_kinetic) {
         k_kinetic<<<c.nred, kRedBlock, 0, s>>>(c.v, c.fixed, c.n, c.mass, c.partials);
         ++k;
     }
-    k_reduce<<<1, 1024, 0, s>>>(c.partials, c.nred, c.totals, with_kinetic);
+    k_reduce<<<1, kRedBlock, 0, s>>>(c.partials, c.nred, c.totals, with_kinetic);
     return k + 1;
 }
 
