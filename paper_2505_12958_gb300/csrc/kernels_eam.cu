@@ -242,12 +242,9 @@ __global__ void __launch_bounds__(256) k_eam_energy(const float4* __restrict__ p
     float rh = 0.f, rl = 0.f, ph = 0.f, pl_ = 0.f;
     float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f, v4 = 0.f, v5 = 0.f;
     const int m = nnbr[i];
-    for (int k = 0; k < m; ++k) {
-        const int e = nbr[(size_t)k * n + i];
-        const int j = e & kNbrMask;
+    auto pair = [&](int e, const float4& q, const float4& ql, float xj) {
         const unsigned code = (unsigned)e >> kNbrShift;
         const float4 dh = Ds[code], dl = Dl[code];
-        const float4 q = pos4[j], ql = pos_lo[j];
         float d[3], dlo[3];
         const float qa[3] = {q.x, q.y, q.z}, pa[3] = {p.x, p.y, p.z};
         const float qla[3] = {ql.x, ql.y, ql.z}, pla[3] = {pl.x, pl.y, pl.z};
@@ -269,22 +266,46 @@ __global__ void __launch_bounds__(256) k_eam_energy(const float4* __restrict__ p
             acc_add(r2h, r2l, sq);
             r2l = __fadd_rn(r2l, fmaf(2.0f * d[c], dlo[c], sqe));
         }
-        if (r2h >= rc2) continue;
+        if (r2h >= rc2) return;
         const float us = ui + q.w;
-        if (us <= 0.0f) continue;
+        if (us <= 0.0f) return;
         const float rf = sqrtf(r2h);
         {
             // virial -1/2 c_ij r_ij (x) rhat_ij with the bond coefficient of the force pass
             float dz_, dp, pf;
             eam_pair_der<false>(T, rf, dz_, dp, pf);
-            const float sc = -0.5f * ((xi + uxi[j]) * dz_ + 0.5f * us * dp) / rf;
+            const float sc = -0.5f * ((xi + xj) * dz_ + 0.5f * us * dp) / rf;
             v0 += sc * d[0] * d[0]; v1 += sc * d[1] * d[1]; v2 += sc * d[2] * d[2];
             v3 += sc * d[0] * d[1]; v4 += sc * d[0] * d[2]; v5 += sc * d[1] * d[2];
         }
-        if (!own) continue;
+        if (!own) return;
         const float pp = __fmul_rn(rf, rf), pe = fmaf(rf, rf, -pp);
         const float tl = __fdiv_rn(__fadd_rn(__fsub_rn(__fsub_rn(r2h, pp), pe), r2l), 2.0f * rf);
         pair_acc_df(T, rf, tl, rf < rcr, rh, rl, ph, pl_);
+    };
+    // kEamBatch list entries at a time: their gathers are independent and overlap in flight
+    // (the pairs are still added in list order)
+    int k = 0;
+    for (; k + kEamBatch <= m; k += kEamBatch) {
+        int e[kEamBatch];
+        float4 q[kEamBatch], ql[kEamBatch];
+        float xj[kEamBatch];
+#pragma unroll
+        for (int b = 0; b < kEamBatch; ++b) e[b] = nbr[(size_t)(k + b) * n + i];
+#pragma unroll
+        for (int b = 0; b < kEamBatch; ++b) {
+            const int j = e[b] & kNbrMask;
+            q[b] = pos4[j];
+            ql[b] = pos_lo[j];
+            xj[b] = uxi[j];
+        }
+#pragma unroll
+        for (int b = 0; b < kEamBatch; ++b) pair(e[b], q[b], ql[b], xj[b]);
+    }
+    for (; k < m; ++k) {
+        const int e = nbr[(size_t)k * n + i];
+        const int j = e & kNbrMask;
+        pair(e, pos4[j], pos_lo[j], uxi[j]);
     }
     vir[i] = v0; vir[n + i] = v1; vir[2 * n + i] = v2; vir[3 * n + i] = v3; vir[4 * n + i] = v4; vir[5 * n + i] = v5;
     if (!own) { e_eam[i] = 0.0; return; }
