@@ -186,51 +186,76 @@ __global__ void k_prepare(const double* __restrict__ x, int n, const GridDev g, 
     }
 }
 
-__global__ void k_build(const float4* __restrict__ pos4, const int* __restrict__ cell, int n, const GridDev g,
-                        const float4* __restrict__ Dtab, const int* __restrict__ cell_start,
-                        const int* __restrict__ cell_atoms, int* __restrict__ nbr, int* __restrict__ nnbr, int cap,
-                        int* __restrict__ flags, int count_only) {
+// Full neighbour list, r < r_list.  Each atom's entries are written in order of distance
+// band (kBands bands of r_list / kBands; within a band, in cell-scan order): the pair kernels
+// visit the k-th entries of neighbouring atoms together, and with band-ordered lists those
+// sit at similar distances, so the lanes of a warp mostly read the same pair-table segment.
+// Two passes over the candidate cells: counts per band, then placement.
+constexpr int kBands = 16;
+constexpr int kBuildBlock = 128;
+
+__global__ void __launch_bounds__(kBuildBlock) k_build(const float4* __restrict__ pos4, const int* __restrict__ cell,
+                                                       int n, const GridDev g, const float4* __restrict__ Dtab,
+                                                       const int* __restrict__ cell_start,
+                                                       const int* __restrict__ cell_atoms, int* __restrict__ nbr,
+                                                       int* __restrict__ nnbr, int cap, int* __restrict__ flags,
+                                                       int count_only) {
     if (!count_only && flags[kFlagRebuild] == 0) return;
     __shared__ float4 D[125];
+    __shared__ int band_at[kBands][kBuildBlock];      // counts, then running write positions
     for (int k = threadIdx.x; k < g.ncode; k += blockDim.x) D[k] = Dtab[k];
+    for (int b = 0; b < kBands; ++b) band_at[b][threadIdx.x] = 0;
     __syncthreads();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float4 p = pos4[i];
     int cc[3];
     cell_coords(g, cell[i], cc);
-    int cnt = 0;
+    const float bscale = (float)kBands * rsqrtf(g.rlist2);
     const int w1 = 2 * g.S[1] + 1, w2 = 2 * g.S[2] + 1;
-    for (int code = 0; code < g.ncode; ++code) {
-        int o[3] = {code / (w1 * w2) - g.S[0], (code / w2) % w1 - g.S[1], code % w2 - g.S[2]};
-        int nc[3];
-        bool ok = true;
-        for (int k = 0; k < 3; ++k) {
-            int v = cc[k] + o[k];
-            if (g.periodic[k]) {
-                v %= g.nc[k];
-                if (v < 0) v += g.nc[k];
-            } else if (v < 0 || v >= g.nc[k]) {
-                ok = false;
+    // visit(e, band) for every candidate inside r_list, in a fixed cell-scan order
+    auto scan = [&](auto&& visit) {
+        for (int code = 0; code < g.ncode; ++code) {
+            int o[3] = {code / (w1 * w2) - g.S[0], (code / w2) % w1 - g.S[1], code % w2 - g.S[2]};
+            int nc[3];
+            bool ok = true;
+            for (int k = 0; k < 3; ++k) {
+                int v = cc[k] + o[k];
+                if (g.periodic[k]) {
+                    v %= g.nc[k];
+                    if (v < 0) v += g.nc[k];
+                } else if (v < 0 || v >= g.nc[k]) {
+                    ok = false;
+                }
+                nc[k] = v;
             }
-            nc[k] = v;
-        }
-        if (!ok) continue;
-        bool self_cell = (o[0] == 0 && o[1] == 0 && o[2] == 0);
-        int cn = (nc[0] * g.nc[1] + nc[1]) * g.nc[2] + nc[2];
-        float4 d = D[code];
-        for (int q = cell_start[cn], e = cell_start[cn + 1]; q < e; ++q) {
-            int j = cell_atoms[q];
-            if (self_cell && j == i) continue;
-            float4 pj = pos4[j];
-            float dx = pj.x + d.x - p.x, dy = pj.y + d.y - p.y, dz = pj.z + d.z - p.z;
-            if (dx * dx + dy * dy + dz * dz < g.rlist2) {
-                if (!count_only && cnt < cap) nbr[(size_t)cnt * n + i] = j | (code << kNbrShift);
-                ++cnt;
+            if (!ok) continue;
+            bool self_cell = (o[0] == 0 && o[1] == 0 && o[2] == 0);
+            int cn = (nc[0] * g.nc[1] + nc[1]) * g.nc[2] + nc[2];
+            float4 d = D[code];
+            for (int q = cell_start[cn], e = cell_start[cn + 1]; q < e; ++q) {
+                int j = cell_atoms[q];
+                if (self_cell && j == i) continue;
+                float4 pj = pos4[j];
+                float dx = pj.x + d.x - p.x, dy = pj.y + d.y - p.y, dz = pj.z + d.z - p.z;
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 < g.rlist2) visit(j | (code << kNbrShift), min(kBands - 1, (int)(sqrtf(r2) * bscale)));
             }
         }
-    }
+    };
+    int cnt = 0;
+    scan([&](int, int b) { ++cnt; ++band_at[b][threadIdx.x]; });
     if (!count_only) {
+        int run = 0;
+        for (int b = 0; b < kBands; ++b) {
+            const int c = band_at[b][threadIdx.x];
+            band_at[b][threadIdx.x] = run;
+            run += c;
+        }
+        scan([&](int e, int b) {
+            const int at = band_at[b][threadIdx.x]++;
+            if (at < cap) nbr[(size_t)at * n + i] = e;
+        });
         nnbr[i] = cnt < cap ? cnt : cap;
         if (cnt > cap) atomicOr(&flags[kFlagErr], kErrCapacity);
     }
@@ -261,7 +286,7 @@ int launch_prepare(Ctx& c, cudaStream_t s) {
 }
 
 int launch_build(Ctx& c, cudaStream_t s, int count_only) {
-    k_build<<<(c.n + 127) / 128, 128, 0, s>>>(c.pos4, c.cell, c.n, c.grid, c.D, c.cell_start, c.cell_atoms, c.nbr,
+    k_build<<<(c.n + kBuildBlock - 1) / kBuildBlock, kBuildBlock, 0, s>>>(c.pos4, c.cell, c.n, c.grid, c.D, c.cell_start, c.cell_atoms, c.nbr,
                                              c.nnbr, c.cap, c.flags, count_only);
     return 1;
 }
