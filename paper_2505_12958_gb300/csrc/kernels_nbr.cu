@@ -202,8 +202,15 @@ __global__ void __launch_bounds__(kBuildBlock) k_build(const float4* __restrict_
                                                        int count_only) {
     if (!count_only && flags[kFlagRebuild] == 0) return;
     __shared__ float4 D[125];
+    __shared__ char4 O[125];                          // cell offset of each code (no divisions in the scan)
     __shared__ int band_at[kBands][kBuildBlock];      // counts, then running write positions
-    for (int k = threadIdx.x; k < g.ncode; k += blockDim.x) D[k] = Dtab[k];
+    {
+        const int w1 = 2 * g.S[1] + 1, w2 = 2 * g.S[2] + 1;
+        for (int k = threadIdx.x; k < g.ncode; k += blockDim.x) {
+            D[k] = Dtab[k];
+            O[k] = make_char4((char)(k / (w1 * w2) - g.S[0]), (char)((k / w2) % w1 - g.S[1]), (char)(k % w2 - g.S[2]), 0);
+        }
+    }
     for (int b = 0; b < kBands; ++b) band_at[b][threadIdx.x] = 0;
     __syncthreads();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -212,34 +219,60 @@ __global__ void __launch_bounds__(kBuildBlock) k_build(const float4* __restrict_
     int cc[3];
     cell_coords(g, cell[i], cc);
     const float bscale = (float)kBands * rsqrtf(g.rlist2);
-    const int w1 = 2 * g.S[1] + 1, w2 = 2 * g.S[2] + 1;
-    // visit(e, band) for every candidate inside r_list, in a fixed cell-scan order
+    // visit(e, band) for every candidate inside r_list, in a fixed cell-scan order.  The scan
+    // is a chain of dependent loads (cell range, atom index, position): the ranges of four
+    // cells, and then the indices and positions of up to four atoms of a cell, are loaded
+    // together.
     auto scan = [&](auto&& visit) {
-        for (int code = 0; code < g.ncode; ++code) {
-            int o[3] = {code / (w1 * w2) - g.S[0], (code / w2) % w1 - g.S[1], code % w2 - g.S[2]};
-            int nc[3];
-            bool ok = true;
-            for (int k = 0; k < 3; ++k) {
-                int v = cc[k] + o[k];
-                if (g.periodic[k]) {
-                    v %= g.nc[k];
-                    if (v < 0) v += g.nc[k];
-                } else if (v < 0 || v >= g.nc[k]) {
-                    ok = false;
+        for (int c0 = 0; c0 < g.ncode; c0 += 4) {
+            int beg[4], end[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                beg[u] = end[u] = 0;
+                const int code = c0 + u;
+                if (code >= g.ncode) continue;
+                const char4 oc = O[code];
+                const int o[3] = {oc.x, oc.y, oc.z};
+                int nc[3];
+                bool ok = true;
+                for (int k = 0; k < 3; ++k) {
+                    int v = cc[k] + o[k];             // |o| <= S <= 2: at most two wraps
+                    if (g.periodic[k]) {
+                        while (v < 0) v += g.nc[k];
+                        while (v >= g.nc[k]) v -= g.nc[k];
+                    } else if (v < 0 || v >= g.nc[k]) {
+                        ok = false;
+                    }
+                    nc[k] = v;
                 }
-                nc[k] = v;
+                if (!ok) continue;
+                const int cn = (nc[0] * g.nc[1] + nc[1]) * g.nc[2] + nc[2];
+                beg[u] = cell_start[cn];
+                end[u] = cell_start[cn + 1];
             }
-            if (!ok) continue;
-            bool self_cell = (o[0] == 0 && o[1] == 0 && o[2] == 0);
-            int cn = (nc[0] * g.nc[1] + nc[1]) * g.nc[2] + nc[2];
-            float4 d = D[code];
-            for (int q = cell_start[cn], e = cell_start[cn + 1]; q < e; ++q) {
-                int j = cell_atoms[q];
-                if (self_cell && j == i) continue;
-                float4 pj = pos4[j];
-                float dx = pj.x + d.x - p.x, dy = pj.y + d.y - p.y, dz = pj.z + d.z - p.z;
-                const float r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 < g.rlist2) visit(j | (code << kNbrShift), min(kBands - 1, (int)(sqrtf(r2) * bscale)));
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int code = c0 + u;
+                if (beg[u] >= end[u]) continue;
+                const bool self_cell = O[code].x == 0 && O[code].y == 0 && O[code].z == 0;
+                const float4 d = D[code];
+                for (int q0 = beg[u]; q0 < end[u]; q0 += 4) {
+                    int jj[4];
+                    float4 pj[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) jj[t] = q0 + t < end[u] ? cell_atoms[q0 + t] : -1;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        if (jj[t] >= 0) pj[t] = pos4[jj[t]];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int j = jj[t];
+                        if (j < 0 || (self_cell && j == i)) continue;
+                        const float dx = pj[t].x + d.x - p.x, dy = pj[t].y + d.y - p.y, dz = pj[t].z + d.z - p.z;
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        if (r2 < g.rlist2) visit(j | (code << kNbrShift), min(kBands - 1, (int)(sqrtf(r2) * bscale)));
+                    }
+                }
             }
         }
     };
