@@ -14,6 +14,9 @@
 
 struct ap_ctx {
     ap::Ctx c;
+    // the fixed-size device buffers of the context, carved from one allocation
+    char* arena = nullptr;
+    size_t arena_bytes = 0;
     struct Pending { int stage; cudaEvent_t a, b; };
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> free_ev;
@@ -221,20 +224,53 @@ void pinned_give(char* p) {
     g_pinned_free.push_back(p);
 }
 
-void free_all(ap::Ctx& c) {
+void free_all(ap_ctx* xc) {
+    ap::Ctx& c = xc->c;
     void* ps[] = {c.eam_d, c.ace_d, c.D, c.Dlo, c.pos_lo, c.ace_A, c.ace_dA, c.x, c.v, c.xb, c.f, c.pos4, c.uxi, c.w, c.e_emb, c.e_eam, c.e_ace,
                   c.vir_eam, c.vir_ace, c.acc, c.fixed, c.w_fixed, c.cell, c.cell_count, c.cell_start,
                   c.cell_atoms, c.nbr, c.nnbr, c.ace_list, c.flags, c.d_time, c.partials, c.totals, c.e_atom,
                   c.pos_stage, c.f_stage, c.csp_sum, c.csp_under, c.csp_w0, c.csp_wnew, c.csp_seeds, c.csp_nseed,
                   c.thermo_group, c.nh_state, c.nh_partials, c.d_step, c.com};
-    for (void* p : ps)
-        if (p) cudaFreeAsync(p, c.stream);
+    for (void* p : ps) {
+        const bool carved = xc->arena && (char*)p >= xc->arena && (char*)p < xc->arena + xc->arena_bytes;
+        if (p && !carved) cudaFreeAsync(p, c.stream);
+    }
+    if (xc->arena) cudaFreeAsync(xc->arena, c.stream);
+    xc->arena = nullptr;
+    xc->arena_bytes = 0;
     cudaStreamSynchronize(c.stream);
     pinned_give((char*)c.h_totals);
     c.h_totals = nullptr;
     c.h_flags = nullptr;
     c.dev_bytes = 0;
     delete c.ace_h;
+}
+
+// Fixed-size buffers of a context: the sizes are gathered first, then one stream-ordered
+// allocation is carved into 256-byte aligned pieces (an allocation call costs ~10 us, and a
+// context has some 30 such buffers).
+struct ArenaPlan {
+    struct Item { void** p; size_t bytes; };
+    std::vector<Item> items;
+    template <class T>
+    void add(T** p, size_t count) { items.push_back({(void**)p, (count ? count : 1) * sizeof(T)}); }
+};
+
+ap_status arena_commit(ap_ctx* xc, const ArenaPlan& plan) {
+    ap::Ctx& c = xc->c;
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    size_t total = 0;
+    for (const auto& it : plan.items) total += up(it.bytes);
+    cudaError_t e = cudaMallocAsync((void**)&xc->arena, total, c.stream);
+    if (e != cudaSuccess) { xc->arena = nullptr; return cuda_check(c, e, "cudaMallocAsync"); }
+    xc->arena_bytes = total;
+    size_t off = 0;
+    for (const auto& it : plan.items) {
+        *it.p = xc->arena + off;
+        off += up(it.bytes);
+    }
+    c.dev_bytes += total;
+    return AP_OK;
 }
 
 void to_soa(const double* aos, int n, std::vector<double>& soa) {
@@ -349,7 +385,7 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
     ap_status st = AP_OK;
     auto fail = [&](ap_status s2) {
         g_init_err = c.err;
-        free_all(c);
+        free_all(xc);
         delete xc;
         return s2;
     };
@@ -410,20 +446,23 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
     // device memory
     const size_t N = (size_t)n;
     c.nred = (n + ap::kRedBlock - 1) / ap::kRedBlock;
-    if ((st = dalloc(c, &c.eam_d, 1)) || (st = dalloc(c, &c.ace_d, 1)) || (st = dalloc(c, &c.D, 125)) ||
-        (st = dalloc(c, &c.Dlo, 125)) || (st = dalloc(c, &c.pos_lo, N)) ||
-        (st = dalloc(c, &c.x, 3 * N)) || (st = dalloc(c, &c.v, 3 * N)) || (st = dalloc(c, &c.xb, 3 * N)) ||
-        (st = dalloc(c, &c.f, 3 * N)) || (st = dalloc(c, &c.pos4, N)) || (st = dalloc(c, &c.uxi, N)) ||
-        (st = dalloc(c, &c.w, N)) || (st = dalloc(c, &c.e_emb, N)) || (st = dalloc(c, &c.e_eam, N)) ||
-        (st = dalloc(c, &c.e_ace, N)) || (st = dalloc(c, &c.ace_A, (size_t)ap::kNLM * ap::kNmax * N)) ||
-        (st = dalloc(c, &c.ace_dA, (size_t)ap::kNLM * ap::kNmax * N)) || (st = dalloc(c, &c.vir_eam, 6 * N)) || (st = dalloc(c, &c.vir_ace, 6 * N)) ||
-        (st = dalloc(c, &c.acc, 3 * N)) || (st = dalloc(c, &c.fixed, N)) || (st = dalloc(c, &c.w_fixed, N)) ||
-        (st = dalloc(c, &c.cell, N)) || (st = dalloc(c, &c.cell_count, (size_t)c.grid.ncell)) ||
-        (st = dalloc(c, &c.cell_start, (size_t)c.grid.ncell + 1)) || (st = dalloc(c, &c.cell_atoms, N)) ||
-        (st = dalloc(c, &c.nnbr, N)) || (st = dalloc(c, &c.ace_list, N)) || (st = dalloc(c, &c.flags, ap::kFlagCount)) ||
-        (st = dalloc(c, &c.d_time, 1)) || (st = dalloc(c, &c.partials, (size_t)c.nred * 10)) ||
-        (st = dalloc(c, &c.totals, 16)) || (st = dalloc(c, &c.e_atom, N)) || (st = dalloc(c, &c.d_step, 1)))
-        return fail(st);
+    {
+        ArenaPlan plan;
+        plan.add(&c.eam_d, 1); plan.add(&c.ace_d, 1); plan.add(&c.D, 125); plan.add(&c.Dlo, 125);
+        plan.add(&c.pos_lo, N); plan.add(&c.x, 3 * N); plan.add(&c.v, 3 * N); plan.add(&c.xb, 3 * N);
+        plan.add(&c.f, 3 * N); plan.add(&c.pos4, N); plan.add(&c.uxi, N); plan.add(&c.w, N);
+        plan.add(&c.e_emb, N); plan.add(&c.e_eam, N); plan.add(&c.e_ace, N);
+        plan.add(&c.ace_A, (size_t)ap::kNLM * ap::kNmax * N); plan.add(&c.ace_dA, (size_t)ap::kNLM * ap::kNmax * N);
+        plan.add(&c.vir_eam, 6 * N); plan.add(&c.vir_ace, 6 * N); plan.add(&c.acc, 3 * N); plan.add(&c.fixed, N);
+        plan.add(&c.w_fixed, N); plan.add(&c.cell, N); plan.add(&c.cell_atoms, N); plan.add(&c.nnbr, N);
+        plan.add(&c.ace_list, N); plan.add(&c.flags, ap::kFlagCount); plan.add(&c.d_time, 1);
+        plan.add(&c.partials, (size_t)c.nred * 10); plan.add(&c.totals, 16); plan.add(&c.e_atom, N);
+        plan.add(&c.d_step, 1);
+        // the cell arrays grow with the box (ap_set_box): allocated on their own
+        if ((st = arena_commit(xc, plan)) || (st = dalloc(c, &c.cell_count, (size_t)c.grid.ncell)) ||
+            (st = dalloc(c, &c.cell_start, (size_t)c.grid.ncell + 1)))
+            return fail(st);
+    }
     c.ncell_cap = c.grid.ncell;
     if (char* slot = pinned_take()) {
         c.h_totals = (double*)slot;
@@ -904,7 +943,7 @@ void ap_destroy(ap_ctx* xc) {
     drop_step_graph(xc);
     drain_events(xc);
     for (cudaEvent_t e : xc->free_ev) cudaEventDestroy(e);
-    free_all(xc->c);
+    free_all(xc);
     delete xc;
 }
 

@@ -13,6 +13,7 @@
 //  * ACE coefficient tensors: the basis table's coefficients placed at the sorted
 //    (n, l) position of each product.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -325,6 +326,15 @@ int eam_table_eval(const ap_potential& p, int which, double r, double* f, double
 }
 
 int build_ace_tables(const ap_potential& p, AceDev& out, std::string& err) {
+    // l-triple index of sorted (l1, l2, l3), -1 where none (a lookup: a context build visits
+    // every three-factor function twice)
+    static const auto tri_lut = [] {
+        std::array<std::array<std::array<int, kLmax + 1>, kLmax + 1>, kLmax + 1> lut{};
+        for (int a = 0; a <= kLmax; ++a)
+            for (int b = 0; b <= kLmax; ++b)
+                for (int c = 0; c <= kLmax; ++c) lut[a][b][c] = tri_index(a, b, c);
+        return lut;
+    }();
     std::memset(&out, 0, sizeof(out));
     if (p.ace_nmax != kNmax || p.ace_lmax != kLmax) { err = "ACE: only n_max = 8, l_max = 4 are built"; return AP_ERR_ARG; }
     if (!(p.ace_rc > 0.0) || !(p.ace_nref > 0.0)) { err = "ACE: rc and nref must be positive"; return AP_ERR_ARG; }
@@ -352,7 +362,7 @@ int build_ace_tables(const ap_potential& p, AceDev& out, std::string& err) {
                     for (int j = i + 1; j < 3; ++j)
                         if (key[j][0] < key[i][0] || (key[j][0] == key[i][0] && key[j][1] < key[i][1]))
                             for (int z = 0; z < 2; ++z) std::swap(key[i][z], key[j][z]);
-                int t = tri_index(key[0][0], key[1][0], key[2][0]);
+                int t = tri_lut[key[0][0]][key[1][0]][key[2][0]];
                 if (t < 0) {
                     int l1 = key[0][0], l2 = key[1][0], l3 = key[2][0];
                     bool zero = ((l1 + l2 + l3) & 1) || l3 > l1 + l2 || l3 < std::abs(l1 - l2);
