@@ -184,46 +184,67 @@ struct Tri {
     template <int E> static constexpr int m1() { return pat_entry(L1, L2, L3, E, 0) + L1; }
     template <int E> static constexpr int m2() { return pat_entry(L1, L2, L3, E, 1) + L2; }
     template <int E> static constexpr int m3() { return pat_entry(L1, L2, L3, E, 2) + L3; }
+    // the entries are ordered by (m1, m2, m3), so those sharing (m1, m2) are consecutive
+    template <int E> static constexpr bool first12() {
+        return E == 0 || pat_entry(L1, L2, L3, E, 0) != pat_entry(L1, L2, L3, E - 1, 0) ||
+               pat_entry(L1, L2, L3, E, 1) != pat_entry(L1, L2, L3, E - 1, 1);
+    }
+    template <int E> static constexpr bool last12() {
+        return E == N - 1 || pat_entry(L1, L2, L3, E, 0) != pat_entry(L1, L2, L3, E + 1, 0) ||
+               pat_entry(L1, L2, L3, E, 1) != pat_entry(L1, L2, L3, E + 1, 1);
+    }
 };
 
+// Entries sharing (m1, m2) share the product of their two factors:
+//   P[m3]  += G A1[m1] A2[m2]          t = A1[m1] A2[m2] once per (m1, m2)
+//   d1[m1] += G Q[m3] A2[m2], d2[m2] += G Q[m3] A1[m1]
+//                                       u = sum G Q[m3] over the (m1, m2) group
+//   d3[m3] += G A1[m1] Tm[m2]          t = A1[m1] Tm[m2] once per (m1, m2)
 template <int T, int E>
-__device__ __forceinline__ void ent_p(float* P, const float* A1, const float* A2) {
+__device__ __forceinline__ void ent_p(float* P, const float* A1, const float* A2, float& t) {
     using R = Tri<T>;
     constexpr int i1 = R::template m1<E>(), i2 = R::template m2<E>(), i3 = R::template m3<E>();
-    P[i3] = fmaf(c_gaunt[R::OFF + E] * A1[i1], A2[i2], P[i3]);
+    if constexpr (R::template first12<E>()) t = A1[i1] * A2[i2];
+    P[i3] = fmaf(c_gaunt[R::OFF + E], t, P[i3]);
 }
 template <int T, int... E>
 __device__ __forceinline__ void all_p(float* P, const float* A1, const float* A2, std::integer_sequence<int, E...>) {
-    (ent_p<T, E>(P, A1, A2), ...);
+    float t = 0.0f;
+    (ent_p<T, E>(P, A1, A2, t), ...);
 }
 
 template <int T, int E>
-__device__ __forceinline__ void ent_x(float* d1, float* d2, const float* A1, const float* A2, const float* Q) {
+__device__ __forceinline__ void ent_x(float* d1, float* d2, const float* A1, const float* A2, const float* Q,
+                                      float& u) {
     using R = Tri<T>;
     constexpr int i1 = R::template m1<E>(), i2 = R::template m2<E>(), i3 = R::template m3<E>();
-    const float u = c_gaunt[R::OFF + E] * Q[i3];
-    d1[i1] = fmaf(u, A2[i2], d1[i1]);
-    d2[i2] = fmaf(u, A1[i1], d2[i2]);
+    if constexpr (R::template first12<E>()) u = c_gaunt[R::OFF + E] * Q[i3];
+    else u = fmaf(c_gaunt[R::OFF + E], Q[i3], u);
+    if constexpr (R::template last12<E>()) {
+        d1[i1] = fmaf(u, A2[i2], d1[i1]);
+        d2[i2] = fmaf(u, A1[i1], d2[i2]);
+    }
 }
 template <int T, int... E>
 __device__ __forceinline__ void all_x(float* d1, float* d2, const float* A1, const float* A2, const float* Q,
                                       std::integer_sequence<int, E...>) {
-    (ent_x<T, E>(d1, d2, A1, A2, Q), ...);
+    float u = 0.0f;
+    (ent_x<T, E>(d1, d2, A1, A2, Q, u), ...);
 }
 
 template <int T, int E>
-__device__ __forceinline__ void ent_y(float* d3, const float* A1, const float* Tm) {
+__device__ __forceinline__ void ent_y(float* d3, const float* A1, const float* Tm, float& t) {
     using R = Tri<T>;
     constexpr int i1 = R::template m1<E>(), i2 = R::template m2<E>(), i3 = R::template m3<E>();
-    d3[i3] = fmaf(c_gaunt[R::OFF + E] * A1[i1], Tm[i2], d3[i3]);
+    if constexpr (R::template first12<E>()) t = A1[i1] * Tm[i2];
+    d3[i3] = fmaf(c_gaunt[R::OFF + E], t, d3[i3]);
 }
 template <int T, int... E>
 __device__ __forceinline__ void all_y(float* d3, const float* A1, const float* Tm, std::integer_sequence<int, E...>) {
-    (ent_y<T, E>(d3, A1, Tm), ...);
+    float t = 0.0f;
+    (ent_y<T, E>(d3, A1, Tm, t), ...);
 }
 
-// the first W entries of a 16-byte aligned row of A, in 128-bit loads (the padding of each
-// l-block covers the rounding up to a multiple of 4)
 template <int W>
 __device__ __forceinline__ void load_row(float* dst, const float* src) {
 #pragma unroll
