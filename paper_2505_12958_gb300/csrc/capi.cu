@@ -280,9 +280,12 @@ void to_soa(const double* aos, int n, std::vector<double>& soa) {
 }
 
 // one AP force evaluation of the current positions (stages a1-a7)
-void run_forces(ap_ctx* xc, cudaStream_t s, float* out_aos) {
+// one force evaluation; after_drift: the kick-drift kernel of this step already took the
+// neighbour-list displacement test (positions change only there between evaluations of a
+// step loop), so the separate check is left out
+void run_forces(ap_ctx* xc, cudaStream_t s, float* out_aos, bool after_drift = false) {
     ap::Ctx& c = xc->c;
-    stage(xc, AP_STAGE_NEIGHBOR, s, [&] { return ap::launch_check(c, s) + ap::launch_rebuild(c, s); });
+    stage(xc, AP_STAGE_NEIGHBOR, s, [&] { return (after_drift ? 0 : ap::launch_check(c, s)) + ap::launch_rebuild(c, s); });
     stage(xc, AP_STAGE_PREPARE, s, [&] { return ap::launch_prepare(c, s); });
     stage(xc, AP_STAGE_NEIGHBOR, s, [&] { return ap::launch_build(c, s, 0); });
     stage(xc, AP_STAGE_EAM_DENSITY, s, [&] { return ap::launch_eam_density(c, s); });
@@ -589,7 +592,7 @@ ap_status ap_step(ap_ctx* xc, int n_steps, double dt, void* stream) {
     if (c.prof || !capturable(s) || n_steps == 0) {
         for (int k = 0; k < n_steps; ++k) {
             stage(xc, AP_STAGE_INTEGRATE, s, [&] { return step_kernels(c, s, dt, 0); });
-            run_forces(xc, s, nullptr);
+            run_forces(xc, s, nullptr, true);
             stage(xc, AP_STAGE_INTEGRATE, s, [&] { return step_kernels(c, s, dt, 1); });
             c.t += dt;
             c.step += 1;
@@ -605,7 +608,7 @@ ap_status ap_step(ap_ctx* xc, int n_steps, double dt, void* stream) {
         const long long before = c.launches;
         for (int q = 0; q < k; ++q) {
             c.launches += step_kernels(c, s, dt, 0);
-            run_forces(xc, s, nullptr);
+            run_forces(xc, s, nullptr, true);
             c.launches += step_kernels(c, s, dt, 1);
         }
         xc->step_kernels = (c.launches - before) / k;
