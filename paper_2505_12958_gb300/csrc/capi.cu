@@ -282,8 +282,9 @@ void to_soa(const double* aos, int n, std::vector<double>& soa) {
 // one AP force evaluation of the current positions (stages a1-a7)
 // one force evaluation; after_drift: the kick-drift kernel of this step already took the
 // neighbour-list displacement test (positions change only there between evaluations of a
-// step loop), so the separate check is left out
-void run_forces(ap_ctx* xc, cudaStream_t s, float* out_aos, bool after_drift = false) {
+// step loop), so the separate check is left out; kick_dt > 0: the blend kernel also applies
+// the step's second half kick
+void run_forces(ap_ctx* xc, cudaStream_t s, float* out_aos, bool after_drift = false, double kick_dt = 0.0) {
     ap::Ctx& c = xc->c;
     stage(xc, AP_STAGE_NEIGHBOR, s, [&] { return (after_drift ? 0 : ap::launch_check(c, s)) + ap::launch_rebuild(c, s); });
     stage(xc, AP_STAGE_PREPARE, s, [&] { return ap::launch_prepare(c, s); });
@@ -293,7 +294,7 @@ void run_forces(ap_ctx* xc, cudaStream_t s, float* out_aos, bool after_drift = f
     stage(xc, AP_STAGE_ACE_BASIS, s, [&] { return ap::launch_ace_basis(c, s); });
     stage(xc, AP_STAGE_ACE, s, [&] { return ap::launch_ace(c, s); });
     stage(xc, AP_STAGE_ACE_FORCE, s, [&] { return ap::launch_ace_force(c, s); });
-    stage(xc, AP_STAGE_BLEND, s, [&] { return ap::launch_blend(c, s, out_aos); });
+    stage(xc, AP_STAGE_BLEND, s, [&] { return ap::launch_blend(c, s, out_aos, kick_dt); });
     c.forces_valid = true;
     c.energy_fresh = false;
 }
@@ -564,6 +565,10 @@ ap_status ap_compute_forces_host(ap_ctx* xc, const double* h_pos, float* h_force
     return AP_OK;
 }
 
+// the second half kick runs inside the force pass's blend kernel unless Langevin forces are
+// added between them
+bool kick_in_blend(const ap::Ctx& c) { return c.thermo_kind != AP_THERMO_LANGEVIN; }
+
 // the integration kernels around a force pass: part 0 before it (thermostat half step,
 // kick-drift), part 1 after it (Langevin forces, kick, thermostat half step, momentum zeroing)
 int step_kernels(ap::Ctx& c, cudaStream_t s, double dt, int part) {
@@ -574,7 +579,7 @@ int step_kernels(ap::Ctx& c, cudaStream_t s, double dt, int part) {
         return k;
     }
     if (c.thermo_kind == AP_THERMO_LANGEVIN) k += ap::launch_langevin(c, s, dt);
-    k += ap::launch_kick(c, s, dt);
+    if (!kick_in_blend(c)) k += ap::launch_kick(c, s, dt);
     if (c.thermo_kind == AP_THERMO_NOSE_HOOVER) k += ap::launch_nh_half(c, s, dt);
     if (c.thermo_kind == AP_THERMO_LANGEVIN && c.lv_zero_every > 0) k += ap::launch_zero_momentum(c, s);
     return k;
@@ -592,7 +597,7 @@ ap_status ap_step(ap_ctx* xc, int n_steps, double dt, void* stream) {
     if (c.prof || !capturable(s) || n_steps == 0) {
         for (int k = 0; k < n_steps; ++k) {
             stage(xc, AP_STAGE_INTEGRATE, s, [&] { return step_kernels(c, s, dt, 0); });
-            run_forces(xc, s, nullptr, true);
+            run_forces(xc, s, nullptr, true, kick_in_blend(c) ? dt : 0.0);
             stage(xc, AP_STAGE_INTEGRATE, s, [&] { return step_kernels(c, s, dt, 1); });
             c.t += dt;
             c.step += 1;
@@ -608,7 +613,7 @@ ap_status ap_step(ap_ctx* xc, int n_steps, double dt, void* stream) {
         const long long before = c.launches;
         for (int q = 0; q < k; ++q) {
             c.launches += step_kernels(c, s, dt, 0);
-            run_forces(xc, s, nullptr, true);
+            run_forces(xc, s, nullptr, true, kick_in_blend(c) ? dt : 0.0);
             c.launches += step_kernels(c, s, dt, 1);
         }
         xc->step_kernels = (c.launches - before) / k;

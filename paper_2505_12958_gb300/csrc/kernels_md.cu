@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kRedBlock) k_blend(
     const float4* __restrict__ pos4, const int* __restrict__ cell,
     const float* __restrict__ wv, float* __restrict__ f, unsigned long long* __restrict__ acc,
     const float* __restrict__ e_ace, const double* __restrict__ e_eam, double c1_0, float* __restrict__ out_aos,
-    int* __restrict__ flags) {
+    int* __restrict__ flags, double hdta, const unsigned char* __restrict__ fixed, double* __restrict__ v) {
     // FP64 runs at 1/64 of the FP32 rate on this GPU.  Positions are taken in FP32 from the
     // cell origin and x_rel (absolute error ~1e-5 A) for the indenter pre-test, inside its
     // margin, and for the weight-gradient force of the switching shell, whose relative error
@@ -156,6 +156,10 @@ __global__ void __launch_bounds__(kRedBlock) k_blend(
     for (int k = 0; k < 3; ++k) f[(size_t)k * n + i] = F[k];
     if (out_aos)
         for (int k = 0; k < 3; ++k) out_aos[3 * (size_t)i + k] = F[k];
+    // the second half kick of a velocity-Verlet step, when nothing else adds to F before it
+    // (the same arithmetic as k_kick)
+    if (hdta != 0.0 && !fixed[i])
+        for (int k = 0; k < 3; ++k) v[(size_t)k * n + i] += hdta * (double)F[k];
     if (!(F[0] == F[0]) || !(F[1] == F[1]) || !(F[2] == F[2])) {
         atomicOr(&flags[kFlagErr], kErrDomain);
         flags[kFlagBad] = i;
@@ -420,9 +424,10 @@ int launch_pos_in(Ctx& c, cudaStream_t s, const double* pos) {
     return 1;
 }
 
-int launch_blend(Ctx& c, cudaStream_t s, float* out_aos) {
+int launch_blend(Ctx& c, cudaStream_t s, float* out_aos, double kick_dt) {
+    const double hdta = kick_dt > 0.0 ? 0.5 * kick_dt * kFtm / c.mass : 0.0;
     k_blend<<<c.nred, kRedBlock, 0, s>>>(c.x, c.n, c.grid, c.dyn, c.d_time, c.pos4, c.cell, c.w, c.f, c.acc, c.e_ace,
-                                         c.e_eam, c.ace_c1_0, out_aos, c.flags);
+                                         c.e_eam, c.ace_c1_0, out_aos, c.flags, hdta, c.fixed, c.v);
     return 1;
 }
 
