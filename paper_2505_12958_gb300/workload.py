@@ -1,20 +1,21 @@
 """Work accounting for roofline figures (host-side bookkeeping, no physics).
 
-ACE, per atom of the compacted list (Sec. 2.2.2, Eq. energy_ace), for the factored
-evaluation the kernel uses.  FLOPs count an FMA as 2.  Only (n, n') pairs that carry a
-structurally nonzero coefficient are counted: for an l-triple with l1 = l2 the first two
-factors are ordered (n1 <= n2), for l2 = l3 the last two (n2 <= n3).
+ACE, per atom of the compacted list (Sec. 2.2.2, Eq. energy_ace): the arithmetic that the
+factored evaluation cannot avoid.  FLOPs count an FMA as 2.  Only index combinations with a
+structurally nonzero coefficient are counted: an l-triple with l1 = l2 has ordered first
+factors (n1 <= n2), one with l2 = l3 ordered last factors (n2 <= n3), so each triple has
+512, 288 or 120 (n1, n2, n3) combinations.  The real-Gaunt pattern of each triple has nnz
+entries in g12 groups sharing (m1, m2), and the product of the two factors of a group is
+formed once.
 
-  per l-triple t and active (n1, n2) pair, forward:   P = sum G A A      3 nnz_t
-                                                      R = P . A_n3       16 W3
-                                                      phi1, phi2         32
-  adjoint, (n1, n2) mapping:                          c1 + s c2          16
-                                                      Q = c . A_n3       16 W3
-                                                      dA1, dA2           5 nnz_t
-  adjoint, (n1, n3) mapping:                          c1 + s c2          16
-                                                      T = c . A_n2       16 W2
-                                                      dA3                3 nnz_t
-  two-factor terms: 64 pairs x 25 x 2 (forward) + 64 x 25 x 4 (adjoint) + 64 x 5 x 8
+  per active (n1, n2) pair, forward:    P = sum G A A          g12 + 2 nnz
+  per (n1, n2, n3) combination:         r = P . A_n3, phi1, phi2   2 W3 + 4
+  adjoint, per combination:             c1 + s c2, Q = c . A_n3     2 + 2 W3
+          per active (n1, n2) pair:     dA1, dA2               2 nnz + 3 g12
+  adjoint, per combination:             c1 + s c2, T = c . A_n2     2 + 2 W2
+          per active (n1, n3) pair:     dA3                    g12 + 2 nnz
+  two-factor terms over the 36 pairs n1 <= n2 and each l: W_l FMA and two densities
+  forward, W_l FMA plus one coefficient FMA and W_l multiplies adjoint; one-factor terms.
   per neighbour inside the cutoff: A = g Y (400), basis values (~100), pair force
   (25 x (32 + 10) + radial 40, ~1090).
 """
@@ -23,29 +24,41 @@ from .csrc_constants import NNZ, TRIPLES
 PER_NEIGHBOR_FLOPS = 400 + 100 + 25 * 42 + 40
 
 
-def _active_pairs(l1, l2, l3):
-    x = 36 if l1 == l2 else 64
-    if l1 == l2 and l2 == l3:
-        y = 36
-    else:
-        y = 64
-    return x, y
+def _pattern(l1, l2, l3):
+    """(m1, m2, m3) entries of a triple's real-Gaunt pattern (an even number of negative m,
+    the largest |m| the sum of the other two)."""
+    out = []
+    for m1 in range(-l1, l1 + 1):
+        for m2 in range(-l2, l2 + 1):
+            for m3 in range(-l3, l3 + 1):
+                a = sorted((abs(m1), abs(m2), abs(m3)))
+                if ((m1 < 0) + (m2 < 0) + (m3 < 0)) % 2 == 0 and a[2] == a[0] + a[1]:
+                    out.append((m1, m2, m3))
+    return out
 
 
 def ace_contract_flops_per_atom():
-    """FLOPs of the contraction kernel per atom (products, densities, dE/dA; no neighbour terms)."""
+    """FLOPs of the contraction per atom (products, densities, dE/dA; no neighbour terms)."""
     return ace_flops_per_atom(0)
 
 
 def ace_flops_per_atom(n_neighbors):
     tot = 0
     for (l1, l2, l3), nnz in zip(TRIPLES, NNZ):
+        pat = _pattern(l1, l2, l3)
+        assert len(pat) == nnz
+        g12 = len({(a, b) for a, b, _ in pat})
         w2, w3 = 2 * l2 + 1, 2 * l3 + 1
-        px, py = _active_pairs(l1, l2, l3)
-        tot += px * (3 * nnz + 16 * w3 + 32)
-        tot += px * (16 + 16 * w3 + 5 * nnz)
-        tot += py * (16 + 16 * w2 + 3 * nnz)
-    tot += 64 * 25 * 2 + 64 * 25 * 4 + 64 * 5 * 8
+        combos = [(n1, n2, n3) for n1 in range(8) for n2 in range(8) for n3 in range(8)
+                  if (l1 != l2 or n1 <= n2) and (l2 != l3 or n2 <= n3)]
+        px = len({(a, b) for a, b, _ in combos})
+        py = len({(a, c) for a, _, c in combos})
+        t3 = len(combos)
+        tot += px * (g12 + 2 * nnz) + t3 * (2 * w3 + 4)
+        tot += t3 * (2 + 2 * w3) + px * (2 * nnz + 3 * g12)
+        tot += t3 * (2 + 2 * w2) + py * (g12 + 2 * nnz)
+    tot += 36 * sum(2 * (2 * l + 1) + 4 for l in range(5)) + 36 * sum(2 + 3 * (2 * l + 1) for l in range(5))
+    tot += 8 * 4 + 8 * 2
     return tot + PER_NEIGHBOR_FLOPS * n_neighbors
 
 

@@ -1,0 +1,32 @@
+"""The work count behind the contraction's roofline figure: its index combinations must be
+exactly the three-factor basis functions of the synthetic ACE, and its pattern sizes the
+real-Gaunt entries of each l-triple."""
+import numpy as np
+
+import synth
+from paper_2505_12958_gb300 import workload
+from paper_2505_12958_gb300.csrc_constants import NNZ, TRIPLES
+
+
+def test_counted_combinations_are_the_three_factor_functions():
+    idx = synth.ace_basis()
+    nu3 = idx[idx[:, 0] == 3]
+    # (l, n) sorted triples of the basis, grouped by l-triple
+    per_triple = {}
+    for row in nu3:
+        key = tuple(sorted([(row[2], row[1]), (row[4], row[3]), (row[6], row[5])]))
+        per_triple.setdefault(tuple(k[0] for k in key), set()).add(key)
+    for (l1, l2, l3) in TRIPLES:
+        combos = [(n1, n2, n3) for n1 in range(8) for n2 in range(8) for n3 in range(8)
+                  if (l1 != l2 or n1 <= n2) and (l2 != l3 or n2 <= n3)]
+        assert len(combos) == len(per_triple[(l1, l2, l3)])
+    assert sum(len(v) for v in per_triple.values()) == len(nu3) == 3976
+
+
+def test_pattern_sizes_and_total():
+    for (l1, l2, l3), nnz in zip(TRIPLES, NNZ):
+        assert len(workload._pattern(l1, l2, l3)) == nnz
+    assert sum(NNZ) == 418
+    f = workload.ace_contract_flops_per_atom()
+    assert f == 403704
+    assert workload.ace_flops_per_atom(10) == f + 10 * workload.PER_NEIGHBOR_FLOPS
