@@ -201,7 +201,7 @@ int launch_ace_basis(Ctx& c, cudaStream_t s);        // A_nlm of the compacted a
 int launch_ace(Ctx& c, cudaStream_t s);              // products, densities, dE/dA
 int launch_ace_force(Ctx& c, cudaStream_t s);        // pair forces and scatter
 int launch_blend(Ctx& c, cudaStream_t s, float* out_aos, double kick_dt = 0.0);   // kick_dt > 0: fused second half kick
-int launch_energy(Ctx& c, cudaStream_t s);           // compensated EAM energies + energy blend
+int launch_energy(Ctx& c, cudaStream_t s, bool virial = true);   // compensated EAM energies + energy blend (+ virial)
 int launch_reduce(Ctx& c, cudaStream_t s, int with_kinetic);
 int launch_kick_drift(Ctx& c, cudaStream_t s, double dt, int first_half);
 int launch_kick(Ctx& c, cudaStream_t s, double dt);

@@ -17,6 +17,8 @@ struct ap_ctx {
     // the fixed-size device buffers of the context, carved from one allocation
     char* arena = nullptr;
     size_t arena_bytes = 0;
+    // the fresh energies of the last force evaluation include the per-atom virial
+    bool energy_virial = false;
     struct Pending { int stage; cudaEvent_t a, b; };
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> free_ev;
@@ -300,11 +302,13 @@ void run_forces(ap_ctx* xc, cudaStream_t s, float* out_aos, bool after_drift = f
 }
 
 // accurate energies of the last force evaluation, once
-void ensure_energy(ap_ctx* xc, cudaStream_t s) {
+// (totals and per-atom energies; the per-atom virial only when asked for)
+void ensure_energy(ap_ctx* xc, cudaStream_t s, bool virial = true) {
     ap::Ctx& c = xc->c;
-    if (c.energy_fresh) return;
-    c.launches += ap::launch_energy(c, s);
+    if (c.energy_fresh && (xc->energy_virial || !virial)) return;
+    c.launches += ap::launch_energy(c, s, virial);
     c.energy_fresh = true;
+    xc->energy_virial = virial;
 }
 
 ap_status read_flags(ap::Ctx& c, cudaStream_t s) {
@@ -554,7 +558,7 @@ ap_status ap_compute_forces_host(ap_ctx* xc, const double* h_pos, float* h_force
     }
     run_forces(xc, s, c.f_stage);
     if (h_energy) {
-        ensure_energy(xc, s);
+        ensure_energy(xc, s, false);                    // the total energy only
         c.launches += ap::launch_reduce(c, s, 0);
     }
     if (h_force) e = cudaMemcpyAsync(h_force, c.f_stage, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, s);

@@ -221,6 +221,7 @@ __global__ void k_pos_lo(const double* __restrict__ x, int n, const GridDev g, c
                             (float)((x[2 * (size_t)n + i] - o[2]) - (double)p.z), 0.0f);
 }
 
+template <bool VIR>
 __global__ void __launch_bounds__(256) k_eam_energy(const float4* __restrict__ pos4, const float4* __restrict__ pos_lo,
                                                     const int* __restrict__ nbr, const int* __restrict__ nnbr, int n,
                                                     const EamDev* __restrict__ eam, const float4* __restrict__ D,
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(256) k_eam_energy(const float4* __restrict__ p
         const float us = ui + q.w;
         if (us <= 0.0f) return;
         const float rf = sqrtf(r2h);
-        {
+        if (VIR) {
             // virial -1/2 c_ij r_ij (x) rhat_ij with the bond coefficient of the force pass
             float dz_, dp, pf;
             eam_pair_der<false>(T, rf, dz_, dp, pf);
@@ -307,7 +308,9 @@ __global__ void __launch_bounds__(256) k_eam_energy(const float4* __restrict__ p
         const int j = e & kNbrMask;
         pair(e, pos4[j], pos_lo[j], uxi[j]);
     }
-    vir[i] = v0; vir[n + i] = v1; vir[2 * n + i] = v2; vir[3 * n + i] = v3; vir[4 * n + i] = v4; vir[5 * n + i] = v5;
+    if (VIR) {
+        vir[i] = v0; vir[n + i] = v1; vir[2 * n + i] = v2; vir[3 * n + i] = v3; vir[4 * n + i] = v4; vir[5 * n + i] = v5;
+    }
     if (!own) { e_eam[i] = 0.0; return; }
     const double rho = (double)rh + (double)rl;
     double F = T.F_dxi;
@@ -317,10 +320,14 @@ __global__ void __launch_bounds__(256) k_eam_energy(const float4* __restrict__ p
 
 }  // namespace
 
-int launch_eam_energy(Ctx& c, cudaStream_t s) {
+int launch_eam_energy(Ctx& c, cudaStream_t s, bool virial) {
     k_pos_lo<<<(c.n + 255) / 256, 256, 0, s>>>(c.x, c.n, c.grid, c.cell, c.pos4, c.pos_lo);
-    k_eam_energy<<<(c.n + 255) / 256, 256, 0, s>>>(c.pos4, c.pos_lo, c.nbr, c.nnbr, c.n, c.eam_d, c.D, c.Dlo,
-                                                   c.grid.ncode, c.uxi, c.e_eam, c.vir_eam);
+    if (virial)
+        k_eam_energy<true><<<(c.n + 255) / 256, 256, 0, s>>>(c.pos4, c.pos_lo, c.nbr, c.nnbr, c.n, c.eam_d, c.D,
+                                                             c.Dlo, c.grid.ncode, c.uxi, c.e_eam, c.vir_eam);
+    else
+        k_eam_energy<false><<<(c.n + 255) / 256, 256, 0, s>>>(c.pos4, c.pos_lo, c.nbr, c.nnbr, c.n, c.eam_d, c.D,
+                                                              c.Dlo, c.grid.ncode, c.uxi, c.e_eam, c.vir_eam);
     return 2;
 }
 

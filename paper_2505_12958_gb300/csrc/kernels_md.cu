@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_blend(
     const float* __restrict__ wv, const float4* __restrict__ pos4, const int* __restrict__ cell,
     const float* __restrict__ e_ace, const double* __restrict__ e_eam, double c1_0,
     const float* __restrict__ vir_eam, const float* __restrict__ vir_ace, double* __restrict__ e_atom,
-    double* __restrict__ partials, int* __restrict__ flags) {
+    double* __restrict__ partials, int* __restrict__ flags, int with_virial) {
     __shared__ double red[9 * (kRedBlock + 1)];
     __shared__ float sh[9];          // box origin, cell edges (orthorhombic), tip centre at time t
     if (threadIdx.x == 0 && dy.ind_on && g.ortho) {
@@ -218,8 +218,9 @@ __global__ void __launch_bounds__(kRedBlock) k_energy_blend(
         acc[0] = Ei;
         acc[1] = V;
         // per-atom virial: the FP32 sum of the two parts (relative error ~6e-8 per atom)
-        for (int k = 0; k < 6; ++k)
-            acc[2 + k] = (double)(vir_eam[(size_t)k * n + i] + (wi > 0.0 ? vir_ace[(size_t)k * n + i] : 0.0f));
+        if (with_virial)
+            for (int k = 0; k < 6; ++k)
+                acc[2 + k] = (double)(vir_eam[(size_t)k * n + i] + (wi > 0.0 ? vir_ace[(size_t)k * n + i] : 0.0f));
         if (!(Ei == Ei)) {
             atomicOr(&flags[kFlagErr], kErrDomain);
             flags[kFlagBad] = i;
@@ -431,13 +432,13 @@ int launch_blend(Ctx& c, cudaStream_t s, float* out_aos, double kick_dt) {
     return 1;
 }
 
-int launch_eam_energy(Ctx& c, cudaStream_t s);
+int launch_eam_energy(Ctx& c, cudaStream_t s, bool virial);
 
-int launch_energy(Ctx& c, cudaStream_t s) {
-    int k = launch_eam_energy(c, s);
+int launch_energy(Ctx& c, cudaStream_t s, bool virial) {
+    int k = launch_eam_energy(c, s, virial);
     k_energy_blend<<<c.nred, kRedBlock, 0, s>>>(c.x, c.n, c.grid, c.dyn, c.d_time, c.w, c.pos4, c.cell, c.e_ace,
                                                 c.e_eam, c.ace_c1_0, c.vir_eam, c.vir_ace, c.e_atom, c.partials,
-                                                c.flags);
+                                                c.flags, virial ? 1 : 0);
     return k + 1;
 }
 
