@@ -47,6 +47,10 @@ namespace {
 #endif
 constexpr int kN3Unroll = AP_N3_UNROLL;
 constexpr int kPPUnroll = AP_PP_UNROLL;
+#ifndef AP_J_UNROLL
+#define AP_J_UNROLL 1
+#endif
+constexpr int kJUnroll = AP_J_UNROLL;
 
 constexpr int kWarps = 8;
 constexpr int kTile = 32;
@@ -300,6 +304,38 @@ __device__ __forceinline__ void axpy_row(float* Q, float ce, const float* row) {
     }
 }
 
+// Pa . row and Pb . row over a 16-byte aligned shared-memory row: one broadcast load serves
+// both products; each keeps the two accumulator chains (even and odd k) of dot_row2
+template <int W>
+__device__ __forceinline__ void dot_row2_x2(const float* Pa, const float* Pb, const float* row, float& ra, float& rb) {
+    float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < W; k += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(row + k);
+        a0 = fmaf(Pa[k], v.x, a0);
+        b0 = fmaf(Pb[k], v.x, b0);
+        if (k + 1 < W) { a1 = fmaf(Pa[k + 1], v.y, a1); b1 = fmaf(Pb[k + 1], v.y, b1); }
+        if (k + 2 < W) { a0 = fmaf(Pa[k + 2], v.z, a0); b0 = fmaf(Pb[k + 2], v.z, b0); }
+        if (k + 3 < W) { a1 = fmaf(Pa[k + 3], v.w, a1); b1 = fmaf(Pb[k + 3], v.w, b1); }
+    }
+    ra = a0 + a1;
+    rb = b0 + b1;
+}
+
+// Qa[k] += ca * row[k], Qb[k] += cb * row[k]: one broadcast load per 8 FMA
+template <int W>
+__device__ __forceinline__ void axpy_row_x2(float* Qa, float* Qb, float ca, float cb, const float* row) {
+#pragma unroll
+    for (int k = 0; k < W; k += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(row + k);
+        Qa[k] = fmaf(ca, v.x, Qa[k]);
+        Qb[k] = fmaf(cb, v.x, Qb[k]);
+        if (k + 1 < W) { Qa[k + 1] = fmaf(ca, v.y, Qa[k + 1]); Qb[k + 1] = fmaf(cb, v.y, Qb[k + 1]); }
+        if (k + 2 < W) { Qa[k + 2] = fmaf(ca, v.z, Qa[k + 2]); Qb[k + 2] = fmaf(cb, v.z, Qb[k + 2]); }
+        if (k + 3 < W) { Qa[k + 3] = fmaf(ca, v.w, Qa[k + 3]); Qb[k + 3] = fmaf(cb, v.w, Qb[k + 3]); }
+    }
+}
+
 // The two (n1, n2) pairs of a lane and the n3 / n2 contractions are runtime loops; only the
 // Gaunt entries are unrolled (their operands are register-indexed), which keeps the code
 // of all 14 l-triples small enough for the instruction cache.
@@ -329,13 +365,65 @@ __device__ __forceinline__ void nu3_forward_pair(const float* As, const AceDev& 
     p2 += s2;
 }
 
+// forward of a lane's two pairs (n1, n2) and (n1 + 4, n2), one after the other
 template <int T>
-__device__ __forceinline__ void nu3_forward(const float* As, const AceDev& C, int lane, float& p1, float& p2) {
+__device__ __forceinline__ void nu3_forward_seq(const float* As, const AceDev& C, int lane, float& p1, float& p2) {
 #pragma unroll kPPUnroll
     for (int pp = 0; pp < 2; ++pp) {
         const int q = lane + 32 * pp;
         nu3_forward_pair<T>(As, C, q >> 3, q & 7, p1, p2);
     }
+}
+
+// the same two pairs together: they share the A_n2 row and every A_n3 row, so each
+// broadcast row load serves both (the contraction is bound by shared-memory bandwidth).
+// The sums keep the order of evaluating the pairs one after the other (identical bits).
+template <int T>
+__device__ __forceinline__ void nu3_forward_joint(const float* As, const AceDev& C, int lane, float& p1, float& p2) {
+    using R = Tri<T>;
+    const int n1 = lane >> 3, n2 = lane & 7, q = lane;
+    float Pa[R::W3], Pb[R::W3];
+    {
+        float A2[R::W2];
+        load_row<R::W2>(A2, As + n2 * kApad + R::B2);
+        // one copy of the unrolled Gaunt code for both pairs (instruction cache)
+#pragma unroll 1
+        for (int pp = 0; pp < 2; ++pp) {
+            float A1[R::W1];
+            load_row<R::W1>(A1, As + (n1 + 4 * pp) * kApad + R::B1);
+#pragma unroll
+            for (int k = 0; k < R::W3; ++k) Pb[k] = 0.0f;
+            all_p<T>(Pb, A1, A2, std::make_integer_sequence<int, R::N>{});
+            if (pp == 0) {
+#pragma unroll
+                for (int k = 0; k < R::W3; ++k) Pa[k] = Pb[k];
+            }
+        }
+    }
+    const float* c1 = &C.c3[0][T][0][q];
+    const float* c2 = &C.c3[1][T][0][q];
+    float a1 = 0.0f, a2 = 0.0f, b1 = 0.0f, b2 = 0.0f;
+#pragma unroll kJUnroll
+    for (int n3 = 0; n3 < kNmax; ++n3) {
+        float ra, rb;
+        dot_row2_x2<R::W3>(Pa, Pb, As + n3 * kApad + R::B3, ra, rb);
+        a1 = fmaf(c1[n3 * 65], ra, a1);
+        a2 = fmaf(c2[n3 * 65], ra, a2);
+        b1 = fmaf(c1[n3 * 65 + 32], rb, b1);
+        b2 = fmaf(c2[n3 * 65 + 32], rb, b2);
+    }
+    p1 += a1;
+    p2 += a2;
+    p1 += b1;
+    p2 += b2;
+}
+
+// joint where the two P rows fit the register budget of two blocks per SM (W3 <= 7; the
+// l3 = 4 triples would spill)
+template <int T>
+__device__ __forceinline__ void nu3_forward(const float* As, const AceDev& C, int lane, float& p1, float& p2) {
+    if constexpr (Tri<T>::W3 <= 7) nu3_forward_joint<T>(As, C, lane, p1, p2);
+    else nu3_forward_seq<T>(As, C, lane, p1, p2);
 }
 
 // adjoint of one (n1, n2) pair with respect to its first two factors:
@@ -360,20 +448,39 @@ __device__ __forceinline__ void nu3_adjoint_x_pair(const float* As, const AceDev
     all_x<T>(d1, d2, A1, A2, Q, std::make_integer_sequence<int, R::N>{});
 }
 
-// (n1, n2) mapping: gradients with respect to the first and second factor
+// (n1, n2) mapping: gradients with respect to the first and second factor.  A lane's two
+// pairs (n1, n2) and (n1 + 4, n2) run together: their Q rows share every A_n3 row load.
+// The sums keep the order of evaluating the pairs one after the other.
 template <int T>
 __device__ __forceinline__ void nu3_adjoint_x(const float* As, float* dAs, const AceDev& C, float s, int lane) {
     using R = Tri<T>;
+    const int n1 = lane >> 3, n2 = lane & 7, q = lane;
+    float Qa[R::W3], Qb[R::W3];
+#pragma unroll
+    for (int m = 0; m < R::W3; ++m) { Qa[m] = 0.0f; Qb[m] = 0.0f; }
+    const float* c1 = &C.c3[0][T][0][q];
+    const float* c2 = &C.c3[1][T][0][q];
+#pragma unroll kJUnroll
+    for (int n3 = 0; n3 < kNmax; ++n3) {
+        const float ca = fmaf(s, c2[n3 * 65], c1[n3 * 65]);
+        const float cb = fmaf(s, c2[n3 * 65 + 32], c1[n3 * 65 + 32]);
+        axpy_row_x2<R::W3>(Qa, Qb, ca, cb, As + n3 * kApad + R::B3);
+    }
     float d2[R::W2];
 #pragma unroll
     for (int k = 0; k < R::W2; ++k) d2[k] = 0.0f;
-#pragma unroll kPPUnroll
+#pragma unroll 1
     for (int pp = 0; pp < 2; ++pp) {
-        const int q = lane + 32 * pp, n1 = q >> 3;
-        float d1[R::W1];
+        const int r1 = n1 + 4 * pp;
+        float A1[R::W1], A2[R::W2], d1[R::W1];
+        load_row<R::W1>(A1, As + r1 * kApad + R::B1);
+        load_row<R::W2>(A2, As + n2 * kApad + R::B2);
 #pragma unroll
         for (int k = 0; k < R::W1; ++k) d1[k] = 0.0f;
-        nu3_adjoint_x_pair<T>(As, C, s, n1, q & 7, d1, d2);
+        float Qt[R::W3];
+#pragma unroll
+        for (int m = 0; m < R::W3; ++m) Qt[m] = pp ? Qb[m] : Qa[m];
+        all_x<T>(d1, d2, A1, A2, Qt, std::make_integer_sequence<int, R::N>{});
 #pragma unroll
         for (int k = 0; k < R::W1; ++k) {
             float v = d1[k];
@@ -384,7 +491,7 @@ __device__ __forceinline__ void nu3_adjoint_x(const float* As, float* dAs, const
         }
         if ((lane & 7) == 0) {
 #pragma unroll
-            for (int k = 0; k < R::W1; ++k) dAs[n1 * kApad + R::B1 + k] += d1[k];
+            for (int k = 0; k < R::W1; ++k) dAs[r1 * kApad + R::B1 + k] += d1[k];
         }
         __syncwarp();
     }
@@ -402,9 +509,10 @@ __device__ __forceinline__ void nu3_adjoint_x(const float* As, float* dAs, const
     __syncwarp();
 }
 
-// (n1, n3) mapping: gradient with respect to the third factor
+// (n1, n3) mapping: gradient with respect to the third factor; a lane's two pairs (n1, n3)
+// and (n1 + 4, n3) one after the other
 template <int T>
-__device__ __forceinline__ void nu3_adjoint_y(const float* As, float* dAs, const AceDev& C, float s, int lane) {
+__device__ __forceinline__ void nu3_adjoint_y_seq(const float* As, float* dAs, const AceDev& C, float s, int lane) {
     using R = Tri<T>;
     float d3[R::W3];
 #pragma unroll
@@ -435,6 +543,55 @@ __device__ __forceinline__ void nu3_adjoint_y(const float* As, float* dAs, const
         for (int k = 0; k < R::W3; ++k) dAs[lane * kApad + R::B3 + k] += d3[k];
     }
     __syncwarp();
+}
+
+// the same two pairs together: their Tm rows share every A_n2 row load (identical bits)
+template <int T>
+__device__ __forceinline__ void nu3_adjoint_y_joint(const float* As, float* dAs, const AceDev& C, float s, int lane) {
+    using R = Tri<T>;
+    const int n1 = lane >> 3, n3 = lane & 7;
+    float Ta[R::W2], Tb[R::W2];
+#pragma unroll
+    for (int m = 0; m < R::W2; ++m) { Ta[m] = 0.0f; Tb[m] = 0.0f; }
+    const float* c1 = &C.c3[0][T][n3][n1 * 8];
+    const float* c2 = &C.c3[1][T][n3][n1 * 8];
+#pragma unroll kJUnroll
+    for (int n2 = 0; n2 < kNmax; ++n2) {
+        const float ca = fmaf(s, c2[n2], c1[n2]);
+        const float cb = fmaf(s, c2[n2 + 32], c1[n2 + 32]);
+        axpy_row_x2<R::W2>(Ta, Tb, ca, cb, As + n2 * kApad + R::B2);
+    }
+    float d3[R::W3];
+#pragma unroll
+    for (int k = 0; k < R::W3; ++k) d3[k] = 0.0f;
+#pragma unroll 1
+    for (int pp = 0; pp < 2; ++pp) {
+        float A1[R::W1], Tt[R::W2];
+        load_row<R::W1>(A1, As + (n1 + 4 * pp) * kApad + R::B1);
+#pragma unroll
+        for (int m = 0; m < R::W2; ++m) Tt[m] = pp ? Tb[m] : Ta[m];
+        all_y<T>(d3, A1, Tt, std::make_integer_sequence<int, R::N>{});
+    }
+#pragma unroll
+    for (int k = 0; k < R::W3; ++k) {
+        float v = d3[k];
+        v += __shfl_xor_sync(0xffffffffu, v, 8);
+        v += __shfl_xor_sync(0xffffffffu, v, 16);
+        d3[k] = v;
+    }
+    if (lane < 8) {
+#pragma unroll
+        for (int k = 0; k < R::W3; ++k) dAs[lane * kApad + R::B3 + k] += d3[k];
+    }
+    __syncwarp();
+}
+
+// joint where the two Tm rows fit the register budget of two blocks per SM: W2 <= 5 (wider
+// rows measured slower or spilled)
+template <int T>
+__device__ __forceinline__ void nu3_adjoint_y(const float* As, float* dAs, const AceDev& C, float s, int lane) {
+    if constexpr (Tri<T>::W2 <= 5) nu3_adjoint_y_joint<T>(As, dAs, C, s, lane);
+    else nu3_adjoint_y_seq<T>(As, dAs, C, s, lane);
 }
 
 template <int T>
