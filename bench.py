@@ -113,15 +113,16 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def make_ctx(ap, c, region="cfg", skin=1.0):
+def make_ctx(ap, c, region="cfg", skin=1.0, stream=None):
     reg = c["region"] if region == "cfg" else region
     return ap.APContext(c["eam"], c["ace"], c["box"], c["x"], c["v"], c["fixed"], reg, c["indenter"], c["ind_vel"],
-                        c["mass"], skin)
+                        c["mass"], skin, stream=stream)
 
 
 def timed_steps(torch, ctx, steps, flush, profile=0):
     """Per-step device time (CUDA events on the launch stream), L2 flushed before each step.
-    profile: 0 none, 1 every stage bracketed by events, 2 only the ACE contraction kernel."""
+    profile: 0 none, 1 every stage bracketed by events, 2 only the ACE contraction kernel,
+    3 the ACE contraction kernel of one step in eight."""
     s = torch.cuda.current_stream()
     evs = []
     if profile:
@@ -219,7 +220,7 @@ def ace_kernel_roofline(prof, n_steps, c, pk, peak_src, ctx_atoms_in_rc, fma_pea
                             "derived: 152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock, %s peaks file)"
                             % (float(pk.get("sm_max_mhz", 2070.0)), peak_src)),
             "peak_derived_unit_count": derived,
-            "algorithmic_flops_per_launch": int(flops), "avg_launch_ms": avg_s * 1000.0}
+            "algorithmic_flops_per_launch": int(flops), "avg_launch_ms": avg_s * 1000.0, "timed_launches": nl}
 
 
 def serving_bench(torch, n_req, seed=1005, load=0.7, chunk=8, max_active=64):
@@ -455,14 +456,18 @@ def main():
         torch.cuda.synchronize()
 
     # ---- AP (the metric) ----
-    ctx = make_ctx(ap, c)
+    # the context steps on its own stream, where ap_step replays captured step graphs; the
+    # flushes and the timing events go to the same stream
+    ctx_stream = torch.cuda.Stream()
+    torch.cuda.set_stream(ctx_stream)
+    ctx = make_ctx(ap, c, stream=ctx_stream)
     ctx.step(args.warmup, 1.0)
     ctx.check()
     barrier()
     l0 = ctx.launch_count
     with Clocks(local) as clk:
         t0 = time.perf_counter()
-        ms, prof = timed_steps(torch, ctx, args.steps, flush, profile=2)
+        ms, prof = timed_steps(torch, ctx, args.steps, flush, profile=3)
         barrier()
         wall = time.perf_counter() - t0
     launches = ctx.launch_count - l0
@@ -504,7 +509,7 @@ def main():
     variants = [] if args.variants == "none" else args.variants.split(",")
     for name in variants:
         reg = {"kind": "const", "w": 1.0} if name == "ace" else None
-        cv = make_ctx(ap, c, region=reg)
+        cv = make_ctx(ap, c, region=reg, stream=ctx_stream)
         kk = max(5, args.steps // (8 if name == "ace" else 1))
         cv.step(3, 1.0)
         cv.check()
@@ -514,6 +519,8 @@ def main():
         extra[name + "_only"] = {"value": n * kk / (sum(msv) / 1000.0), "unit": UNIT, "steps": kk,
                                  "ms_per_step": sum(msv) / kk}
         cv.close()
+    torch.cuda.synchronize()
+    torch.cuda.set_stream(torch.cuda.default_stream())
 
     serving = (serving_bench(torch, args.serve_requests, chunk=args.serve_chunk, max_active=args.serve_active)
                if args.serve_requests > 0 else None)
@@ -525,11 +532,15 @@ def main():
             "ms_per_step": 1000.0 * dev_s / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 forces / f64 integration", "data": "synthetic",
             "config": {"workload": WORKLOAD, "atoms": n, "n_ace": rep["n_ace"], "parallelism": "replicas" if ws > 1 else "1 GPU",
-                       "l2": "flushed before every timed step (256 MB write)", "timing": "CUDA events per step on the launch stream"},
+                       "l2": "flushed before every timed step (256 MB write)",
+                       "timing": "CUDA events per step on the context's stream; each step replays a captured "
+                                 "step graph; in one step of eight the graph's event nodes around the ACE "
+                                 "contraction time that kernel"},
             "p50_ms_per_step": float(np.percentile(ms, 50)), "p99_ms_per_step": float(np.percentile(ms, 99)),
             "stage_ms_per_step": stage_ms,
             "stage_profile": "separate pass of %d steps with every stage bracketed by CUDA events "
-                             "(about 2.5 us per stage); the timed steps bracket only the ACE contraction" % k_stage,
+                             "(about 2.5 us per stage); in the timed steps only the ACE contraction of one step in "
+                             "eight is bracketed" % k_stage,
             "gpu_launches": launches, "clocks": clocks, "e2e": e2e, "roofline": roof,
             "wall_s_timed_region": wall}
     if serving is not None:

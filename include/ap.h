@@ -166,8 +166,14 @@ ap_status ap_compute_forces_host(ap_ctx* ctx, const double* h_pos, float* h_forc
 
 /* n_steps velocity-Verlet steps of dt_fs on the library-owned positions and velocities.
  * Fixed atoms keep x and v.  The indenter (and a following region) advance with time.
- * On a stream other than the legacy default stream (and with profiling off) one step is
- * captured once as a CUDA graph and replayed.  Asynchronous. */
+ * On a stream other than the legacy default stream one step (and a block of 8 steps) is
+ * captured once as a CUDA graph and replayed.  The neighbour-rebuild kernels sit in
+ * conditional nodes of the graph: the kick-drift kernel's displacement test sets the
+ * condition, and they run only on rebuild steps.  With only the ACE contraction profiled
+ * (ap_profile 2 or 3) one step at a time is replayed, the timed steps from a graph whose
+ * event-record nodes around the contraction are set to a fresh event pair each time; with every stage profiled (ap_profile 1),
+ * or on the legacy stream, steps are plain launches.  The results are the same bits on
+ * every path.  Asynchronous. */
 ap_status ap_step(ap_ctx* ctx, int n_steps, double dt_fs, void* stream);
 
 /* Serving form: n_steps[k] velocity-Verlet steps (dt_fs) for each of n_ctx independent
@@ -266,9 +272,11 @@ ap_status ap_set_weights(ap_ctx* ctx, const double* w);
 
 /* Per-stage CUDA-event timing of later calls and its readout: enable = 1 brackets every
  * stage with a pair of events (about 2.5 us per stage on the stream), enable = 2 only the
- * ACE contraction stage (the dominant kernel, for its roofline at negligible cost),
- * enable = 0 stops.  Stepping with profiling on uses plain launches, not the captured
- * graph.  ms[k] is the accumulated time of stage k over launches[k] launches, stages
+ * ACE contraction stage (the dominant kernel, for its roofline), enable = 3 the ACE
+ * contraction of one step in eight of ap_step's graph replays (the others replay the
+ * untimed step graph: two event-record nodes cost about 10 us per replayed step),
+ * enable = 0 stops.  Stepping with every stage profiled uses plain launches, not the
+ * captured graphs.  ms[k] is the accumulated time of stage k over launches[k] launches, stages
  * AP_STAGE_*; reading drains the pending events (synchronises).  AP_ERR_ARG for other
  * values of enable. */
 enum { AP_STAGE_NEIGHBOR = 0, AP_STAGE_PREPARE = 1, AP_STAGE_EAM_DENSITY = 2,
@@ -278,7 +286,8 @@ enum { AP_STAGE_NEIGHBOR = 0, AP_STAGE_PREPARE = 1, AP_STAGE_EAM_DENSITY = 2,
 ap_status ap_profile(ap_ctx* ctx, int enable);
 ap_status ap_profile_read(ap_ctx* ctx, double* ms, long long* launches);
 
-/* Number of kernels this context has launched since creation. */
+/* Number of kernels this context has launched since creation (those of the conditional
+ * rebuild nodes of a step graph, which run on rebuild steps only, are not counted). */
 long long ap_launch_count(const ap_ctx* ctx);
 /* Neighbour-list capacity per atom and the number of list rebuilds so far. */
 ap_status ap_neighbor_info(ap_ctx* ctx, int* capacity, long long* rebuilds);

@@ -221,7 +221,8 @@ class APContext:
         self._chk(self._L.ap_set_box(self._h, C.byref(b)))
 
     def profile(self, enable=True):
-        """Stage timing: True / 1 every stage, 2 the ACE contraction only, False / 0 off."""
+        """Stage timing: True / 1 every stage, 2 the ACE contraction only, 3 the ACE contraction
+        of one step in eight, False / 0 off."""
         self._chk(self._L.ap_profile(self._h, int(enable)))
 
     def profile_read(self):

@@ -30,6 +30,19 @@ struct ap_ctx {
     double step_dt = 0.0;
     long long step_kernels = 0;
     long long step_gen = -1;
+    // with only the ACE contraction timed: one step graph whose two event-record nodes
+    // around the contraction get a fresh event pair before every replay (ev_mark are the
+    // events recorded during capture, ev_node the nodes; the graph keeps the nodes valid)
+    cudaGraph_t timed_graph = nullptr;
+    cudaGraphExec_t timed_exec = nullptr;
+    cudaGraphNode_t ev_node[2] = {nullptr, nullptr};
+    cudaEvent_t ev_mark[2] = {nullptr, nullptr};
+    long long timed_kernels = 0;
+    long long timed_count = 0;                           // steps replayed in profiling mode 3
+    // captures the bodies of conditional nodes
+    cudaStream_t aux = nullptr;
+    cudaError_t cap_err = cudaSuccess;
+    const char* cap_where = "";                          // the capture call that failed
 };
 
 namespace {
@@ -65,7 +78,7 @@ void drain_ready(ap_ctx* x) {
         auto& p = x->pending[k];
         if (cudaEventQuery(p.b) != cudaSuccess) break;
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, p.a, p.b);
+        if (cudaEventElapsedTime(&ms, p.a, p.b) != cudaSuccess) break;
         c.stage_ms[p.stage] += ms;
         c.stage_n[p.stage] += 1;
         x->free_ev.push_back(p.a);
@@ -78,7 +91,7 @@ void drain_ready(ap_ctx* x) {
 template <class F>
 void stage(ap_ctx* x, int st, cudaStream_t s, F&& launch) {
     ap::Ctx& c = x->c;
-    if (!c.prof || (c.prof == 2 && st != AP_STAGE_ACE)) { c.launches += launch(); return; }
+    if (!c.prof || (c.prof >= 2 && st != AP_STAGE_ACE)) { c.launches += launch(); return; }
     if (x->pending.size() >= 64) drain_ready(x);
     cudaEvent_t a = get_event(x), b = get_event(x);
     cudaEventRecord(a, s);
@@ -90,10 +103,83 @@ void stage(ap_ctx* x, int st, cudaStream_t s, F&& launch) {
 constexpr int kStepBlock = 8;
 
 void drop_step_graph(ap_ctx* x) {
-    if (x->step_exec) cudaGraphExecDestroy(x->step_exec);
-    if (x->block_exec) cudaGraphExecDestroy(x->block_exec);
-    x->step_exec = nullptr;
-    x->block_exec = nullptr;
+    for (cudaGraphExec_t* g : {&x->step_exec, &x->block_exec, &x->timed_exec}) {
+        if (*g) cudaGraphExecDestroy(*g);
+        *g = nullptr;
+    }
+    if (x->timed_graph) cudaGraphDestroy(x->timed_graph);
+    x->timed_graph = nullptr;
+    x->ev_node[0] = x->ev_node[1] = nullptr;
+}
+
+// While s is being captured, for a step whose kick-drift kernel was captured with the
+// condition c.rb_cond: the prepare kernel, then one conditional node on that condition whose
+// body rebuilds the neighbour list (binning, prepare again on the new cells, list build).
+// Without the node the rebuild kernels would run every step and return at once; the first
+// prepare pass is wasted on rebuild steps only.  Returns the kernels that run on every
+// replay.
+int prepare_then_rebuild(ap_ctx* xc, cudaStream_t s) {
+    ap::Ctx& c = xc->c;
+    const int k = ap::launch_prepare(c, s);
+    const char* where = "capture info";
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd);
+    if (e == cudaSuccess && st != cudaStreamCaptureStatusActive) e = cudaErrorStreamCaptureInvalidated;
+    if (e == cudaSuccess && !xc->aux) {
+        where = "body stream";
+        e = cudaStreamCreateWithFlags(&xc->aux, cudaStreamNonBlocking);
+    }
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = c.rb_cond;
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    if (e == cudaSuccess) {
+        where = "conditional node";
+        e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &p);
+    }
+    if (e == cudaSuccess) {
+        where = "capture dependencies";
+        e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    }
+    if (e == cudaSuccess) {
+        where = "body capture";
+        e = cudaStreamBeginCaptureToGraph(xc->aux, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal);
+    }
+    if (e == cudaSuccess) {
+        ap::launch_rebuild(c, xc->aux);
+        ap::launch_prepare(c, xc->aux, true);
+        ap::launch_build(c, xc->aux, 0);
+        cudaGraph_t body = nullptr;
+        where = "body end";
+        e = cudaStreamEndCapture(xc->aux, &body);
+    }
+    if (e != cudaSuccess && xc->cap_err == cudaSuccess) {
+        xc->cap_err = e;
+        xc->cap_where = where;
+    }
+    return k;
+}
+
+// While s is being captured: a new condition for the next step (a conditional node takes a
+// handle of its own), set by that step's kick-drift kernel.  Its default at every replay
+// is 1, so a condition that were never set would run the rebuild body, whose kernels all
+// check the device flag themselves.
+void new_step_condition(ap_ctx* xc, cudaStream_t s) {
+    ap::Ctx& c = xc->c;
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&c.rb_cond, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess && xc->cap_err == cudaSuccess) {
+        xc->cap_err = e;
+        xc->cap_where = "condition handle";
+    }
 }
 
 void drain_events(ap_ctx* x) {
@@ -281,24 +367,38 @@ void to_soa(const double* aos, int n, std::vector<double>& soa) {
         for (int k = 0; k < 3; ++k) soa[(size_t)k * n + i] = aos[3 * (size_t)i + k];
 }
 
-// one AP force evaluation of the current positions (stages a1-a7)
-// one force evaluation; after_drift: the kick-drift kernel of this step already took the
+// one AP force evaluation of the current positions (stages a1-a7), in two parts around the
+// ACE contraction.  after_drift: the kick-drift kernel of this step already took the
 // neighbour-list displacement test (positions change only there between evaluations of a
-// step loop), so the separate check is left out; kick_dt > 0: the blend kernel also applies
-// the step's second half kick
-void run_forces(ap_ctx* xc, cudaStream_t s, float* out_aos, bool after_drift = false, double kick_dt = 0.0) {
+// step loop), so the separate check is left out; inside a step graph the rebuild launches
+// then sit in a conditional node on that kernel's decision.  kick_dt > 0: the blend kernel
+// also applies the step's second half kick.
+void run_forces_pre(ap_ctx* xc, cudaStream_t s, bool after_drift) {
     ap::Ctx& c = xc->c;
-    stage(xc, AP_STAGE_NEIGHBOR, s, [&] { return (after_drift ? 0 : ap::launch_check(c, s)) + ap::launch_rebuild(c, s); });
-    stage(xc, AP_STAGE_PREPARE, s, [&] { return ap::launch_prepare(c, s); });
-    stage(xc, AP_STAGE_NEIGHBOR, s, [&] { return ap::launch_build(c, s, 0); });
+    if (after_drift && c.rb_cond_on) {
+        stage(xc, AP_STAGE_PREPARE, s, [&] { return prepare_then_rebuild(xc, s); });
+    } else {
+        stage(xc, AP_STAGE_NEIGHBOR, s, [&] { return (after_drift ? 0 : ap::launch_check(c, s)) + ap::launch_rebuild(c, s); });
+        stage(xc, AP_STAGE_PREPARE, s, [&] { return ap::launch_prepare(c, s); });
+        stage(xc, AP_STAGE_NEIGHBOR, s, [&] { return ap::launch_build(c, s, 0); });
+    }
     stage(xc, AP_STAGE_EAM_DENSITY, s, [&] { return ap::launch_eam_density(c, s); });
     stage(xc, AP_STAGE_EAM_FORCE, s, [&] { return ap::launch_eam_force(c, s); });
     stage(xc, AP_STAGE_ACE_BASIS, s, [&] { return ap::launch_ace_basis(c, s); });
-    stage(xc, AP_STAGE_ACE, s, [&] { return ap::launch_ace(c, s); });
+}
+
+void run_forces_post(ap_ctx* xc, cudaStream_t s, float* out_aos, double kick_dt) {
+    ap::Ctx& c = xc->c;
     stage(xc, AP_STAGE_ACE_FORCE, s, [&] { return ap::launch_ace_force(c, s); });
     stage(xc, AP_STAGE_BLEND, s, [&] { return ap::launch_blend(c, s, out_aos, kick_dt); });
     c.forces_valid = true;
     c.energy_fresh = false;
+}
+
+void run_forces(ap_ctx* xc, cudaStream_t s, float* out_aos, bool after_drift = false, double kick_dt = 0.0) {
+    run_forces_pre(xc, s, after_drift);
+    stage(xc, AP_STAGE_ACE, s, [&] { return ap::launch_ace(xc->c, s); });
+    run_forces_post(xc, s, out_aos, kick_dt);
 }
 
 // accurate energies of the last force evaluation, once
@@ -589,6 +689,11 @@ int step_kernels(ap::Ctx& c, cudaStream_t s, double dt, int part) {
     return k;
 }
 
+ap_status graph_error(ap_ctx* xc, cudaError_t e) {
+    const std::string what = std::string("ap_step graph (") + xc->cap_where + ")";
+    return cuda_check(xc->c, e, what.c_str());
+}
+
 bool capturable(cudaStream_t s) {
     return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
 }
@@ -598,46 +703,153 @@ ap_status ap_step(ap_ctx* xc, int n_steps, double dt, void* stream) {
     ap::Ctx& c = xc->c;
     cudaStream_t s = pick(xc, stream);
     if (!c.forces_valid) run_forces(xc, s, nullptr);
-    if (c.prof || !capturable(s) || n_steps == 0) {
+    const double kick = kick_in_blend(c) ? dt : 0.0;
+    if (c.prof == 1 || !capturable(s) || n_steps == 0) {
         for (int k = 0; k < n_steps; ++k) {
             stage(xc, AP_STAGE_INTEGRATE, s, [&] { return step_kernels(c, s, dt, 0); });
-            run_forces(xc, s, nullptr, true, kick_in_blend(c) ? dt : 0.0);
+            run_forces(xc, s, nullptr, true, kick);
             stage(xc, AP_STAGE_INTEGRATE, s, [&] { return step_kernels(c, s, dt, 1); });
             c.t += dt;
             c.step += 1;
         }
         return cuda_check(c, cudaGetLastError(), "ap_step");
     }
-    if (xc->step_exec && (xc->step_stream != s || xc->step_dt != dt || xc->step_gen != c.layout_gen)) drop_step_graph(xc);
-    // capture k steps on s as one graph
-    auto capture = [&](int k, cudaGraphExec_t* out) -> cudaError_t {
+    if ((xc->step_exec || xc->timed_exec) &&
+        (xc->step_stream != s || xc->step_dt != dt || xc->step_gen != c.layout_gen))
+        drop_step_graph(xc);
+    // capture body() on s as one graph; with_cond: each captured step gets a rebuild
+    // condition that its kick-drift kernel sets; kernels = launches per replay; keep: the
+    // graph is handed back instead of destroyed
+    auto capture = [&](bool with_cond, cudaGraphExec_t* out, long long* kernels, auto&& body,
+                       cudaGraph_t* keep = nullptr) -> cudaError_t {
         cudaGraph_t g = nullptr;
+        xc->cap_err = cudaSuccess;
         cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return e;
+        xc->cap_where = "";
+        c.rb_cond_on = with_cond;
+        const int prof = c.prof;                         // no stage events inside a capture
+        c.prof = 0;
         const long long before = c.launches;
-        for (int q = 0; q < k; ++q) {
-            c.launches += step_kernels(c, s, dt, 0);
-            run_forces(xc, s, nullptr, true, kick_in_blend(c) ? dt : 0.0);
-            c.launches += step_kernels(c, s, dt, 1);
-        }
-        xc->step_kernels = (c.launches - before) / k;
+        body();
+        *kernels = c.launches - before;
         c.launches = before;
-        e = cudaStreamEndCapture(s, &g);
-        if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
-        if (g) cudaGraphDestroy(g);
+        c.prof = prof;
+        c.rb_cond_on = false;
+        const cudaError_t e2 = cudaStreamEndCapture(s, &g);
+        if (e == cudaSuccess && e2 != cudaSuccess) { e = e2; xc->cap_where = "end capture"; }
+        if (e == cudaSuccess) e = xc->cap_err;
+        if (e == cudaSuccess) {
+            e = cudaGraphInstantiate(out, g, 0);
+            if (e != cudaSuccess) xc->cap_where = "instantiate";
+        }
         if (e != cudaSuccess) *out = nullptr;
+        if (keep && e == cudaSuccess) *keep = g;
+        else if (g) cudaGraphDestroy(g);
         return e;
     };
-    if (!xc->step_exec) {
-        cudaError_t e = capture(1, &xc->step_exec);
-        if (e != cudaSuccess) return cuda_check(c, e, "ap_step graph");
+    auto tag = [&] {
         xc->step_stream = s;
         xc->step_dt = dt;
         xc->step_gen = c.layout_gen;
+    };
+    auto steps = [&](int k) {
+        return [&, k] {
+            for (int q = 0; q < k; ++q) {
+                new_step_condition(xc, s);
+                c.launches += step_kernels(c, s, dt, 0);
+                run_forces(xc, s, nullptr, true, kick);
+                c.launches += step_kernels(c, s, dt, 1);
+            }
+        };
+    };
+    if (c.prof >= 2) {
+        if (!xc->timed_exec) {
+            cudaError_t e = cudaSuccess;
+            for (int q = 0; q < 2 && e == cudaSuccess; ++q)
+                if (!xc->ev_mark[q]) e = cudaEventCreate(&xc->ev_mark[q]);
+            if (e == cudaSuccess)
+                e = capture(true, &xc->timed_exec, &xc->timed_kernels, [&] {
+                    new_step_condition(xc, s);
+                    c.launches += step_kernels(c, s, dt, 0);
+                    run_forces_pre(xc, s, true);
+                    cudaError_t r = cudaEventRecordWithFlags(xc->ev_mark[0], s, cudaEventRecordExternal);
+                    c.launches += ap::launch_ace(c, s);
+                    if (r == cudaSuccess) r = cudaEventRecordWithFlags(xc->ev_mark[1], s, cudaEventRecordExternal);
+                    if (r != cudaSuccess && xc->cap_err == cudaSuccess) {
+                        xc->cap_err = r;
+                        xc->cap_where = "event record";
+                    }
+                    run_forces_post(xc, s, nullptr, kick);
+                    c.launches += step_kernels(c, s, dt, 1);
+                }, &xc->timed_graph);
+            if (e == cudaSuccess) {
+                // the two event-record nodes of the capture
+                size_t nn = 0;
+                e = cudaGraphGetNodes(xc->timed_graph, nullptr, &nn);
+                std::vector<cudaGraphNode_t> nodes(nn);
+                if (e == cudaSuccess && nn) e = cudaGraphGetNodes(xc->timed_graph, nodes.data(), &nn);
+                for (size_t k = 0; k < nn && e == cudaSuccess; ++k) {
+                    cudaGraphNodeType t;
+                    e = cudaGraphNodeGetType(nodes[k], &t);
+                    if (e != cudaSuccess || t != cudaGraphNodeTypeEventRecord) continue;
+                    cudaEvent_t ev = nullptr;
+                    e = cudaGraphEventRecordNodeGetEvent(nodes[k], &ev);
+                    for (int q = 0; q < 2; ++q)
+                        if (ev == xc->ev_mark[q]) xc->ev_node[q] = nodes[k];
+                }
+                if (e == cudaSuccess && (!xc->ev_node[0] || !xc->ev_node[1])) {
+                    e = cudaErrorInvalidValue;
+                    xc->cap_where = "event nodes";
+                }
+            }
+            if (e != cudaSuccess) {
+                drop_step_graph(xc);
+                return graph_error(xc, e);
+            }
+            tag();
+        }
+        if (c.prof == 3 && !xc->step_exec) {
+            long long kernels = 0;
+            cudaError_t e = capture(true, &xc->step_exec, &kernels, steps(1));
+            if (e != cudaSuccess) return graph_error(xc, e);
+            xc->step_kernels = kernels;
+        }
+        for (int k = 0; k < n_steps; ++k) {
+            // mode 3: the other seven of eight steps replay the untimed step graph
+            if (c.prof == 3 && (xc->timed_count++ & 7) != 0) {
+                cudaError_t e = cudaGraphLaunch(xc->step_exec, s);
+                if (e != cudaSuccess) return cuda_check(c, e, "ap_step launch");
+                c.launches += xc->step_kernels;
+                c.t += dt;
+                c.step += 1;
+                continue;
+            }
+            if (xc->pending.size() >= 64) drain_ready(xc);
+            cudaEvent_t a = get_event(xc), b = get_event(xc);
+            cudaError_t e = cudaGraphExecEventRecordNodeSetEvent(xc->timed_exec, xc->ev_node[0], a);
+            if (e == cudaSuccess) e = cudaGraphExecEventRecordNodeSetEvent(xc->timed_exec, xc->ev_node[1], b);
+            if (e == cudaSuccess) e = cudaGraphLaunch(xc->timed_exec, s);
+            if (e != cudaSuccess) return cuda_check(c, e, "ap_step launch");
+            xc->pending.push_back({AP_STAGE_ACE, a, b});
+            c.launches += xc->timed_kernels;
+            c.t += dt;
+            c.step += 1;
+        }
+        c.forces_valid = true;
+        c.energy_fresh = false;
+        return AP_OK;
+    }
+    long long kernels = 0;
+    if (!xc->step_exec) {
+        cudaError_t e = capture(true, &xc->step_exec, &kernels, steps(1));
+        if (e != cudaSuccess) return graph_error(xc, e);
+        xc->step_kernels = kernels;
+        tag();
     }
     if (n_steps >= kStepBlock && !xc->block_exec) {
-        cudaError_t e = capture(kStepBlock, &xc->block_exec);
-        if (e != cudaSuccess) return cuda_check(c, e, "ap_step graph");
+        cudaError_t e = capture(true, &xc->block_exec, &kernels, steps(kStepBlock));
+        if (e != cudaSuccess) return graph_error(xc, e);
     }
     int left = n_steps;
     while (left > 0) {
@@ -920,8 +1132,9 @@ ap_status ap_set_weights(ap_ctx* xc, const double* w) {
 
 ap_status ap_profile(ap_ctx* xc, int enable) {
     if (!xc) return AP_ERR_ARG;
-    if (enable < 0 || enable > 2) return AP_ERR_ARG;
+    if (enable < 0 || enable > 3) return AP_ERR_ARG;
     xc->c.prof = enable;
+    xc->timed_count = 0;
     return AP_OK;
 }
 
@@ -953,6 +1166,9 @@ void ap_destroy(ap_ctx* xc) {
     if (!xc) return;
     cudaStreamSynchronize(xc->c.stream);
     drop_step_graph(xc);
+    if (xc->aux) cudaStreamDestroy(xc->aux);
+    for (cudaEvent_t e : xc->ev_mark)
+        if (e) cudaEventDestroy(e);
     drain_events(xc);
     for (cudaEvent_t e : xc->free_ev) cudaEventDestroy(e);
     free_all(xc);

@@ -32,7 +32,9 @@ __global__ void k_wrap_bin(double* __restrict__ x, double* __restrict__ xb, int 
                            int* __restrict__ cell, int* __restrict__ cell_count, int* __restrict__ flags) {
     if (flags[kFlagRebuild] == 0) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) flags[kFlagRebuilds] += 1;
+    // a prepare pass on the old cells may have compacted already (inside a step graph); the
+    // prepare pass after this rebuild counts afresh
+    if (i == 0) { flags[kFlagRebuilds] += 1; flags[kFlagNAce] = 0; }
     if (i >= n) return;
     double r[3] = {x[i], x[n + i], x[2 * n + i]};
     double d[3] = {r[0] - g.origin[0], r[1] - g.origin[1], r[2] - g.origin[2]};
@@ -119,7 +121,9 @@ __global__ void k_sort_cells(int* __restrict__ cell_atoms, const int* __restrict
 __global__ void k_prepare(const double* __restrict__ x, int n, const GridDev g, const DynDev dy,
                           const double* __restrict__ tptr, const int* __restrict__ cell,
                           const double* __restrict__ w_fixed, float4* __restrict__ pos4,
-                          float* __restrict__ wout, int* __restrict__ ace_list, int* __restrict__ flags) {
+                          float* __restrict__ wout, int* __restrict__ ace_list, int* __restrict__ flags,
+                          int only_if_rebuild) {
+    if (only_if_rebuild && flags[kFlagRebuild] == 0) return;      // uniform over the grid
     __shared__ float sh[9];          // box origin, cell edges (orthorhombic), zone centre at time t
     if (threadIdx.x == 0 && dy.reg_kind == AP_REGION_SPHERE && g.ortho) {
         const double t = *tptr;
@@ -312,9 +316,9 @@ int launch_rebuild(Ctx& c, cudaStream_t s) {
     return 4;
 }
 
-int launch_prepare(Ctx& c, cudaStream_t s) {
+int launch_prepare(Ctx& c, cudaStream_t s, bool only_if_rebuild) {
     k_prepare<<<(c.n + 255) / 256, 256, 0, s>>>(c.x, c.n, c.grid, c.dyn, c.d_time, c.cell, c.w_fixed, c.pos4, c.w,
-                                               c.ace_list, c.flags);
+                                               c.ace_list, c.flags, only_if_rebuild ? 1 : 0);
     return 1;
 }
 

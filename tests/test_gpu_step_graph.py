@@ -1,6 +1,7 @@
 """Replayed step graphs and batched stepping: a step captured as a CUDA graph on a
-non-blocking stream must give the same bits as the plain launch loop on the legacy stream,
-and a context stepped inside a batch the same bits as the context stepped alone."""
+non-blocking stream (its rebuild kernels in conditional nodes) must give the same bits as
+the plain launch loop on the legacy stream, and a context stepped inside a batch the same
+bits as the context stepped alone."""
 import numpy as np
 import pytest
 
@@ -50,6 +51,39 @@ def test_graph_replay_matches_plain_loop(apl):
         a.step(3, 0.5)
         b.step(3, 0.5)
         assert np.array_equal(a.get_state()[0], b.get_state()[0])
+
+
+def test_timed_step_graph_matches_plain_loop(apl):
+    """With only the ACE contraction timed, a step replays a graph whose event-record nodes
+    around the contraction get a fresh event pair each time; the rebuild kernels sit in a
+    conditional node."""
+    import torch
+    c = _hot_slab()
+    s = torch.cuda.Stream()
+    with _ctx(apl, c) as a, _ctx(apl, c, stream=s) as b:
+        a.step(30, 1.0)
+        b.profile(2)
+        b.step(30, 1.0)
+        prof = b.profile_read()
+        b.profile(0)
+        b.check()
+        assert prof["ace"][1] == 31                      # the initial forces, then one per step
+        assert 0.0 < prof["ace"][0] / 31 < 50.0          # ms per contraction of this small slab
+        xa, va, _ = a.get_state()
+        xb, vb, _ = b.get_state()
+        assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+        assert b.neighbor_info()[1] > 1 and a.neighbor_info() == b.neighbor_info()
+        # one timed step in eight, then the plain graph path: the same trajectory
+        b.profile(3)
+        b.step(16, 1.0)
+        prof = b.profile_read()
+        b.profile(0)
+        assert prof["ace"][1] == 2 and prof["ace"][0] > 0.0
+        b.step(10, 1.0)
+        a.step(26, 1.0)
+        b.check()
+        assert np.array_equal(a.get_state()[0], b.get_state()[0])
+        assert np.array_equal(a.get_state()[1], b.get_state()[1])
 
 
 def test_step_batch_alone_equals_mixed(apl):
