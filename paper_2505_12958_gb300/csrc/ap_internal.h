@@ -193,6 +193,27 @@ struct Ctx {
     long long stage_n[AP_NSTAGE] = {0};
 };
 
+#ifdef __CUDACC__
+// Inside a graph: the last block of the kernel that took the displacement test reads the
+// final rebuild flag and sets the graph's rebuild condition (one caller, picked by a ticket
+// counter that it resets).  Every thread of the grid must reach this call.
+__device__ __forceinline__ void publish_rebuild(int* flags, cudaGraphConditionalHandle rb) {
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&flags[kFlagTicket], 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const int r = atomicOr(&flags[kFlagRebuild], 0);
+        flags[kFlagTicket] = 0;
+        cudaGraphSetConditional(rb, r != 0 ? 1u : 0u);
+    }
+}
+#endif
+
 static_assert(sizeof(EamDev) % 16 == 0, "EamDev is staged in 16-byte words");
 static_assert(sizeof(AceDev) % 16 == 0, "AceDev is staged in 16-byte words");
 

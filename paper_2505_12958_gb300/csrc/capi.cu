@@ -39,6 +39,13 @@ struct ap_ctx {
     cudaEvent_t ev_mark[2] = {nullptr, nullptr};
     long long timed_kernels = 0;
     long long timed_count = 0;                           // steps replayed in profiling mode 3
+    // ap_compute_forces_host's kernels as one graph between its plain copies, captured per
+    // (stream, buffer layout, mode: bit 0 positions given, bit 1 energy asked)
+    cudaGraphExec_t host_exec = nullptr;
+    cudaStream_t host_stream = nullptr;
+    long long host_gen = -1;
+    int host_mode = -1;
+    long long host_kernels = 0;
     // captures the bodies of conditional nodes
     cudaStream_t aux = nullptr;
     cudaError_t cap_err = cudaSuccess;
@@ -103,7 +110,7 @@ void stage(ap_ctx* x, int st, cudaStream_t s, F&& launch) {
 constexpr int kStepBlock = 8;
 
 void drop_step_graph(ap_ctx* x) {
-    for (cudaGraphExec_t* g : {&x->step_exec, &x->block_exec, &x->timed_exec}) {
+    for (cudaGraphExec_t* g : {&x->step_exec, &x->block_exec, &x->timed_exec, &x->host_exec}) {
         if (*g) cudaGraphExecDestroy(*g);
         *g = nullptr;
     }
@@ -180,6 +187,50 @@ void new_step_condition(ap_ctx* xc, cudaStream_t s) {
         xc->cap_err = e;
         xc->cap_where = "condition handle";
     }
+}
+
+// Capture body() on s as one graph and instantiate it.  with_cond: the body's steps create
+// rebuild conditions (new_step_condition) that their kick-drift or check kernels set.
+// kernels = launches per replay; keep: the graph is handed back instead of destroyed.
+// Stage timing is off while capturing.
+template <class F>
+cudaError_t capture_graph(ap_ctx* xc, cudaStream_t s, bool with_cond, cudaGraphExec_t* out, long long* kernels,
+                          F&& body, cudaGraph_t* keep = nullptr) {
+    ap::Ctx& c = xc->c;
+    cudaGraph_t g = nullptr;
+    xc->cap_err = cudaSuccess;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    xc->cap_where = "";
+    c.rb_cond_on = with_cond;
+    const int prof = c.prof;
+    c.prof = 0;
+    const long long before = c.launches;
+    body();
+    *kernels = c.launches - before;
+    c.launches = before;
+    c.prof = prof;
+    c.rb_cond_on = false;
+    const cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    if (e == cudaSuccess && e2 != cudaSuccess) { e = e2; xc->cap_where = "end capture"; }
+    if (e == cudaSuccess) e = xc->cap_err;
+    if (e == cudaSuccess) {
+        e = cudaGraphInstantiate(out, g, 0);
+        if (e != cudaSuccess) xc->cap_where = "instantiate";
+    }
+    if (e != cudaSuccess) *out = nullptr;
+    if (keep && e == cudaSuccess) *keep = g;
+    else if (g) cudaGraphDestroy(g);
+    return e;
+}
+
+ap_status graph_error(ap_ctx* xc, cudaError_t e) {
+    const std::string what = std::string("graph capture (") + xc->cap_where + ")";
+    return cuda_check(xc->c, e, what.c_str());
+}
+
+bool capturable(cudaStream_t s) {
+    return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
 }
 
 void drain_events(ap_ctx* x) {
@@ -375,7 +426,9 @@ void to_soa(const double* aos, int n, std::vector<double>& soa) {
 // also applies the step's second half kick.
 void run_forces_pre(ap_ctx* xc, cudaStream_t s, bool after_drift) {
     ap::Ctx& c = xc->c;
-    if (after_drift && c.rb_cond_on) {
+    if (c.rb_cond_on) {
+        // inside a graph: the kick-drift kernel, or else the check kernel, sets the condition
+        if (!after_drift) stage(xc, AP_STAGE_NEIGHBOR, s, [&] { return ap::launch_check(c, s); });
         stage(xc, AP_STAGE_PREPARE, s, [&] { return prepare_then_rebuild(xc, s); });
     } else {
         stage(xc, AP_STAGE_NEIGHBOR, s, [&] { return (after_drift ? 0 : ap::launch_check(c, s)) + ap::launch_rebuild(c, s); });
@@ -651,15 +704,43 @@ ap_status ap_compute_forces_host(ap_ctx* xc, const double* h_pos, float* h_force
     ap_status st;
     if (!c.pos_stage && ((st = dalloc(c, &c.pos_stage, 3 * N)) || (st = dalloc(c, &c.f_stage, 3 * N)))) return st;
     cudaError_t e = cudaSuccess;
-    if (h_pos) {
-        e = cudaMemcpyAsync(c.pos_stage, h_pos, 3 * N * sizeof(double), cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return cuda_check(c, e, "ap_compute_forces_host H2D");
-        c.launches += ap::launch_pos_in(c, s, c.pos_stage);
-    }
-    run_forces(xc, s, c.f_stage);
-    if (h_energy) {
-        ensure_energy(xc, s, false);                    // the total energy only
-        c.launches += ap::launch_reduce(c, s, 0);
+    if (capturable(s) && c.prof == 0) {
+        // the kernels as one replayed graph (the check kernel sets its rebuild condition)
+        const int mode = (h_pos ? 1 : 0) | (h_energy ? 2 : 0);
+        if (xc->host_exec && (xc->host_stream != s || xc->host_gen != c.layout_gen || xc->host_mode != mode)) {
+            cudaGraphExecDestroy(xc->host_exec);
+            xc->host_exec = nullptr;
+        }
+        if (!xc->host_exec) {
+            e = capture_graph(xc, s, true, &xc->host_exec, &xc->host_kernels, [&] {
+                new_step_condition(xc, s);
+                if (h_pos) c.launches += ap::launch_pos_in(c, s, c.pos_stage);
+                run_forces(xc, s, c.f_stage);
+                if (h_energy) c.launches += ap::launch_energy(c, s, false) + ap::launch_reduce(c, s, 0);
+            });
+            if (e != cudaSuccess) return graph_error(xc, e);
+            xc->host_stream = s;
+            xc->host_gen = c.layout_gen;
+            xc->host_mode = mode;
+        }
+        if (h_pos) e = cudaMemcpyAsync(c.pos_stage, h_pos, 3 * N * sizeof(double), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaGraphLaunch(xc->host_exec, s);
+        if (e != cudaSuccess) return cuda_check(c, e, "ap_compute_forces_host");
+        c.launches += xc->host_kernels;
+        c.forces_valid = true;
+        c.energy_fresh = h_energy != nullptr;
+        if (h_energy) xc->energy_virial = false;
+    } else {
+        if (h_pos) {
+            e = cudaMemcpyAsync(c.pos_stage, h_pos, 3 * N * sizeof(double), cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) return cuda_check(c, e, "ap_compute_forces_host H2D");
+            c.launches += ap::launch_pos_in(c, s, c.pos_stage);
+        }
+        run_forces(xc, s, c.f_stage);
+        if (h_energy) {
+            ensure_energy(xc, s, false);                    // the total energy only
+            c.launches += ap::launch_reduce(c, s, 0);
+        }
     }
     if (h_force) e = cudaMemcpyAsync(h_force, c.f_stage, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && h_energy) e = cudaMemcpyAsync(c.h_totals, c.totals, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -689,14 +770,6 @@ int step_kernels(ap::Ctx& c, cudaStream_t s, double dt, int part) {
     return k;
 }
 
-ap_status graph_error(ap_ctx* xc, cudaError_t e) {
-    const std::string what = std::string("ap_step graph (") + xc->cap_where + ")";
-    return cuda_check(xc->c, e, what.c_str());
-}
-
-bool capturable(cudaStream_t s) {
-    return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
-}
 
 ap_status ap_step(ap_ctx* xc, int n_steps, double dt, void* stream) {
     if (!xc || n_steps < 0 || !(dt > 0.0)) return AP_ERR_ARG;
@@ -717,37 +790,6 @@ ap_status ap_step(ap_ctx* xc, int n_steps, double dt, void* stream) {
     if ((xc->step_exec || xc->timed_exec) &&
         (xc->step_stream != s || xc->step_dt != dt || xc->step_gen != c.layout_gen))
         drop_step_graph(xc);
-    // capture body() on s as one graph; with_cond: each captured step gets a rebuild
-    // condition that its kick-drift kernel sets; kernels = launches per replay; keep: the
-    // graph is handed back instead of destroyed
-    auto capture = [&](bool with_cond, cudaGraphExec_t* out, long long* kernels, auto&& body,
-                       cudaGraph_t* keep = nullptr) -> cudaError_t {
-        cudaGraph_t g = nullptr;
-        xc->cap_err = cudaSuccess;
-        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return e;
-        xc->cap_where = "";
-        c.rb_cond_on = with_cond;
-        const int prof = c.prof;                         // no stage events inside a capture
-        c.prof = 0;
-        const long long before = c.launches;
-        body();
-        *kernels = c.launches - before;
-        c.launches = before;
-        c.prof = prof;
-        c.rb_cond_on = false;
-        const cudaError_t e2 = cudaStreamEndCapture(s, &g);
-        if (e == cudaSuccess && e2 != cudaSuccess) { e = e2; xc->cap_where = "end capture"; }
-        if (e == cudaSuccess) e = xc->cap_err;
-        if (e == cudaSuccess) {
-            e = cudaGraphInstantiate(out, g, 0);
-            if (e != cudaSuccess) xc->cap_where = "instantiate";
-        }
-        if (e != cudaSuccess) *out = nullptr;
-        if (keep && e == cudaSuccess) *keep = g;
-        else if (g) cudaGraphDestroy(g);
-        return e;
-    };
     auto tag = [&] {
         xc->step_stream = s;
         xc->step_dt = dt;
@@ -769,7 +811,7 @@ ap_status ap_step(ap_ctx* xc, int n_steps, double dt, void* stream) {
             for (int q = 0; q < 2 && e == cudaSuccess; ++q)
                 if (!xc->ev_mark[q]) e = cudaEventCreate(&xc->ev_mark[q]);
             if (e == cudaSuccess)
-                e = capture(true, &xc->timed_exec, &xc->timed_kernels, [&] {
+                e = capture_graph(xc, s, true, &xc->timed_exec, &xc->timed_kernels, [&] {
                     new_step_condition(xc, s);
                     c.launches += step_kernels(c, s, dt, 0);
                     run_forces_pre(xc, s, true);
@@ -811,7 +853,7 @@ ap_status ap_step(ap_ctx* xc, int n_steps, double dt, void* stream) {
         }
         if (c.prof == 3 && !xc->step_exec) {
             long long kernels = 0;
-            cudaError_t e = capture(true, &xc->step_exec, &kernels, steps(1));
+            cudaError_t e = capture_graph(xc, s, true, &xc->step_exec, &kernels, steps(1));
             if (e != cudaSuccess) return graph_error(xc, e);
             xc->step_kernels = kernels;
         }
@@ -842,13 +884,13 @@ ap_status ap_step(ap_ctx* xc, int n_steps, double dt, void* stream) {
     }
     long long kernels = 0;
     if (!xc->step_exec) {
-        cudaError_t e = capture(true, &xc->step_exec, &kernels, steps(1));
+        cudaError_t e = capture_graph(xc, s, true, &xc->step_exec, &kernels, steps(1));
         if (e != cudaSuccess) return graph_error(xc, e);
         xc->step_kernels = kernels;
         tag();
     }
     if (n_steps >= kStepBlock && !xc->block_exec) {
-        cudaError_t e = capture(true, &xc->block_exec, &kernels, steps(kStepBlock));
+        cudaError_t e = capture_graph(xc, s, true, &xc->block_exec, &kernels, steps(kStepBlock));
         if (e != cudaSuccess) return graph_error(xc, e);
     }
     int left = n_steps;

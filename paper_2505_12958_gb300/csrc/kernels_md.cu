@@ -256,8 +256,7 @@ __global__ void __launch_bounds__(kRedBlock) k_reduce(const double* __restrict__
 // first half kick and drift; the neighbour-list displacement test of the step is taken here,
 // where x is in registers (an atom that moved more than skin/2 since the last build sets the
 // rebuild flag), and the compaction counter of the coming force pass is reset
-// set_rb: launched inside a step graph; the last block to finish reads the final rebuild
-// decision and sets the graph's condition rb (one caller: a ticket counter picks the block)
+// set_rb: launched inside a step graph, whose rebuild condition rb this kernel sets
 __global__ void k_kick_drift(double* __restrict__ x, double* __restrict__ v, const float* __restrict__ f,
                              const unsigned char* __restrict__ fixed, int n, double hdta, double dt,
                              double* __restrict__ tptr, long long* __restrict__ step,
@@ -280,20 +279,7 @@ __global__ void k_kick_drift(double* __restrict__ x, double* __restrict__ v, con
             __threadfence();
         }
     }
-    if (!set_rb) return;                              // uniform over the grid
-    __shared__ int last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(&flags[kFlagTicket], 1) == (int)gridDim.x - 1;
-    }
-    __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
-        const int r = atomicOr(&flags[kFlagRebuild], 0);
-        flags[kFlagTicket] = 0;
-        cudaGraphSetConditional(rb, r != 0 ? 1u : 0u);
-    }
+    if (set_rb) publish_rebuild(flags, rb);           // set_rb is uniform over the grid
 }
 
 __global__ void k_kick(double* __restrict__ v, const float* __restrict__ f, const unsigned char* __restrict__ fixed,

@@ -19,13 +19,20 @@ namespace ap {
 
 namespace {
 
+// the list displacement test; set_rb: launched inside a graph, whose rebuild condition rb
+// this kernel sets
 __global__ void k_check(const double* __restrict__ x, const double* __restrict__ xb, int n, double lim2,
-                        int* flags) {
+                        int* flags, cudaGraphConditionalHandle rb, int set_rb) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) flags[kFlagNAce] = 0;
-    if (i >= n) return;
-    double dx = x[i] - xb[i], dy = x[n + i] - xb[n + i], dz = x[2 * n + i] - xb[2 * n + i];
-    if (dx * dx + dy * dy + dz * dz > lim2) flags[kFlagRebuild] = 1;
+    if (i < n) {
+        double dx = x[i] - xb[i], dy = x[n + i] - xb[n + i], dz = x[2 * n + i] - xb[2 * n + i];
+        if (dx * dx + dy * dy + dz * dz > lim2) {
+            atomicOr(&flags[kFlagRebuild], 1);
+            __threadfence();
+        }
+    }
+    if (set_rb) publish_rebuild(flags, rb);           // set_rb is uniform over the grid
 }
 
 __global__ void k_wrap_bin(double* __restrict__ x, double* __restrict__ xb, int n, const GridDev g,
@@ -303,7 +310,7 @@ __global__ void __launch_bounds__(kBuildBlock) k_build(const float4* __restrict_
 
 int launch_check(Ctx& c, cudaStream_t s) {
     double lim = 0.5 * c.skin;
-    k_check<<<(c.n + 255) / 256, 256, 0, s>>>(c.x, c.xb, c.n, lim * lim, c.flags);
+    k_check<<<(c.n + 255) / 256, 256, 0, s>>>(c.x, c.xb, c.n, lim * lim, c.flags, c.rb_cond, c.rb_cond_on ? 1 : 0);
     return 1;
 }
 
