@@ -167,9 +167,7 @@ ap_status ap_compute_forces_host(ap_ctx* ctx, const double* h_pos, float* h_forc
 /* n_steps velocity-Verlet steps of dt_fs on the library-owned positions and velocities.
  * Fixed atoms keep x and v.  The indenter (and a following region) advance with time.
  * On a stream other than the legacy default stream one step (and a block of 8 steps) is
- * captured once as a CUDA graph and replayed.  The neighbour-rebuild kernels sit in
- * conditional nodes of the graph: the kick-drift kernel's displacement test sets the
- * condition, and they run only on rebuild steps.  With only the ACE contraction profiled
+ * captured as a CUDA graph on first need and replayed.  With only the ACE contraction profiled
  * (ap_profile 2 or 3) one step at a time is replayed, the timed steps from a graph whose
  * event-record nodes around the contraction are set to a fresh event pair each time; with every stage profiled (ap_profile 1),
  * or on the legacy stream, steps are plain launches.  The results are the same bits on
@@ -286,8 +284,7 @@ enum { AP_STAGE_NEIGHBOR = 0, AP_STAGE_PREPARE = 1, AP_STAGE_EAM_DENSITY = 2,
 ap_status ap_profile(ap_ctx* ctx, int enable);
 ap_status ap_profile_read(ap_ctx* ctx, double* ms, long long* launches);
 
-/* Number of kernels this context has launched since creation (those of the conditional
- * rebuild nodes of a step graph, which run on rebuild steps only, are not counted). */
+/* Number of kernels this context has launched since creation. */
 long long ap_launch_count(const ap_ctx* ctx);
 /* Neighbour-list capacity per atom and the number of list rebuilds so far. */
 ap_status ap_neighbor_info(ap_ctx* ctx, int* capacity, long long* rebuilds);

@@ -97,8 +97,7 @@ struct DynDev {               // time-dependent geometry; time is read from devi
     float reg_in2_lo, reg_out2_hi, ind_R2_hi, pad2;
 };
 
-enum : int { kFlagRebuild = 0, kFlagNAce = 1, kFlagErr = 2, kFlagBad = 3, kFlagMaxNbr = 4, kFlagRebuilds = 5, kFlagTicket = 6,
-             kFlagCount = 8 };
+enum : int { kFlagRebuild = 0, kFlagNAce = 1, kFlagErr = 2, kFlagBad = 3, kFlagMaxNbr = 4, kFlagRebuilds = 5, kFlagCount = 8 };
 enum : int { kErrDomain = 1, kErrCapacity = 2, kErrAceCapacity = 4 };
 
 constexpr int kNbrShift = 25;               // neighbour entry = j | code << 25
@@ -174,10 +173,6 @@ struct Ctx {
     int nred = 0;
     int ncell_cap = 0;                                   // allocated length of the cell arrays
     long long layout_gen = 0;                            // bumped when kernel arguments change
-    // while a step graph is captured: the graph's condition "the list is rebuilt this step",
-    // set by the kick-drift kernel and read by the conditional nodes around the rebuild launches
-    cudaGraphConditionalHandle rb_cond = 0;
-    bool rb_cond_on = false;
 
     int* h_flags = nullptr;                              // pinned
     double* h_totals = nullptr;                          // pinned
@@ -193,33 +188,12 @@ struct Ctx {
     long long stage_n[AP_NSTAGE] = {0};
 };
 
-#ifdef __CUDACC__
-// Inside a graph: the last block of the kernel that took the displacement test reads the
-// final rebuild flag and sets the graph's rebuild condition (one caller, picked by a ticket
-// counter that it resets).  Every thread of the grid must reach this call.
-__device__ __forceinline__ void publish_rebuild(int* flags, cudaGraphConditionalHandle rb) {
-    __shared__ int last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(&flags[kFlagTicket], 1) == (int)gridDim.x - 1;
-    }
-    __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
-        const int r = atomicOr(&flags[kFlagRebuild], 0);
-        flags[kFlagTicket] = 0;
-        cudaGraphSetConditional(rb, r != 0 ? 1u : 0u);
-    }
-}
-#endif
-
 static_assert(sizeof(EamDev) % 16 == 0, "EamDev is staged in 16-byte words");
 static_assert(sizeof(AceDev) % 16 == 0, "AceDev is staged in 16-byte words");
 
 // kernel launchers (one per stage); each returns the number of kernels launched
 int launch_rebuild(Ctx& c, cudaStream_t s);          // wrap, bin, scan, scatter, sort (skip when no rebuild)
-int launch_prepare(Ctx& c, cudaStream_t s, bool only_if_rebuild = false);   // x_rel, weights, compaction
+int launch_prepare(Ctx& c, cudaStream_t s);          // x_rel, weights, compaction
 int launch_build(Ctx& c, cudaStream_t s, int count_only);
 int launch_eam_density(Ctx& c, cudaStream_t s);
 int launch_eam_force(Ctx& c, cudaStream_t s);

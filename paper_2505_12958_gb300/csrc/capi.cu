@@ -46,9 +46,7 @@ struct ap_ctx {
     long long host_gen = -1;
     int host_mode = -1;
     long long host_kernels = 0;
-    // captures the bodies of conditional nodes
-    cudaStream_t aux = nullptr;
-    cudaError_t cap_err = cudaSuccess;
+    cudaError_t cap_err = cudaSuccess;                  // the first error inside a capture
     const char* cap_where = "";                          // the capture call that failed
 };
 
@@ -119,90 +117,17 @@ void drop_step_graph(ap_ctx* x) {
     x->ev_node[0] = x->ev_node[1] = nullptr;
 }
 
-// While s is being captured, for a step whose kick-drift kernel was captured with the
-// condition c.rb_cond: the prepare kernel, then one conditional node on that condition whose
-// body rebuilds the neighbour list (binning, prepare again on the new cells, list build).
-// Without the node the rebuild kernels would run every step and return at once; the first
-// prepare pass is wasted on rebuild steps only.  Returns the kernels that run on every
-// replay.
-int prepare_then_rebuild(ap_ctx* xc, cudaStream_t s) {
-    ap::Ctx& c = xc->c;
-    const int k = ap::launch_prepare(c, s);
-    const char* where = "capture info";
-    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
-    cudaGraph_t g = nullptr;
-    const cudaGraphNode_t* deps = nullptr;
-    size_t nd = 0;
-    cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd);
-    if (e == cudaSuccess && st != cudaStreamCaptureStatusActive) e = cudaErrorStreamCaptureInvalidated;
-    if (e == cudaSuccess && !xc->aux) {
-        where = "body stream";
-        e = cudaStreamCreateWithFlags(&xc->aux, cudaStreamNonBlocking);
-    }
-    cudaGraphNodeParams p{};
-    p.type = cudaGraphNodeTypeConditional;
-    p.conditional.handle = c.rb_cond;
-    p.conditional.type = cudaGraphCondTypeIf;
-    p.conditional.size = 1;
-    cudaGraphNode_t node = nullptr;
-    if (e == cudaSuccess) {
-        where = "conditional node";
-        e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &p);
-    }
-    if (e == cudaSuccess) {
-        where = "capture dependencies";
-        e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
-    }
-    if (e == cudaSuccess) {
-        where = "body capture";
-        e = cudaStreamBeginCaptureToGraph(xc->aux, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                          cudaStreamCaptureModeThreadLocal);
-    }
-    if (e == cudaSuccess) {
-        ap::launch_rebuild(c, xc->aux);
-        ap::launch_prepare(c, xc->aux, true);
-        ap::launch_build(c, xc->aux, 0);
-        cudaGraph_t body = nullptr;
-        where = "body end";
-        e = cudaStreamEndCapture(xc->aux, &body);
-    }
-    if (e != cudaSuccess && xc->cap_err == cudaSuccess) {
-        xc->cap_err = e;
-        xc->cap_where = where;
-    }
-    return k;
-}
-
-// While s is being captured: a new condition for the next step (a conditional node takes a
-// handle of its own), set by that step's kick-drift kernel.  Its default at every replay
-// is 1, so a condition that were never set would run the rebuild body, whose kernels all
-// check the device flag themselves.
-void new_step_condition(ap_ctx* xc, cudaStream_t s) {
-    ap::Ctx& c = xc->c;
-    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g);
-    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&c.rb_cond, g, 1, cudaGraphCondAssignDefault);
-    if (e != cudaSuccess && xc->cap_err == cudaSuccess) {
-        xc->cap_err = e;
-        xc->cap_where = "condition handle";
-    }
-}
-
-// Capture body() on s as one graph and instantiate it.  with_cond: the body's steps create
-// rebuild conditions (new_step_condition) that their kick-drift or check kernels set.
-// kernels = launches per replay; keep: the graph is handed back instead of destroyed.
-// Stage timing is off while capturing.
+// Capture body() on s as one graph and instantiate it.  kernels = launches per replay;
+// keep: the graph is handed back instead of destroyed.  Stage timing is off while capturing.
 template <class F>
-cudaError_t capture_graph(ap_ctx* xc, cudaStream_t s, bool with_cond, cudaGraphExec_t* out, long long* kernels,
-                          F&& body, cudaGraph_t* keep = nullptr) {
+cudaError_t capture_graph(ap_ctx* xc, cudaStream_t s, cudaGraphExec_t* out, long long* kernels, F&& body,
+                          cudaGraph_t* keep = nullptr) {
     ap::Ctx& c = xc->c;
     cudaGraph_t g = nullptr;
     xc->cap_err = cudaSuccess;
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     xc->cap_where = "";
-    c.rb_cond_on = with_cond;
     const int prof = c.prof;
     c.prof = 0;
     const long long before = c.launches;
@@ -210,7 +135,6 @@ cudaError_t capture_graph(ap_ctx* xc, cudaStream_t s, bool with_cond, cudaGraphE
     *kernels = c.launches - before;
     c.launches = before;
     c.prof = prof;
-    c.rb_cond_on = false;
     const cudaError_t e2 = cudaStreamEndCapture(s, &g);
     if (e == cudaSuccess && e2 != cudaSuccess) { e = e2; xc->cap_where = "end capture"; }
     if (e == cudaSuccess) e = xc->cap_err;
@@ -421,20 +345,13 @@ void to_soa(const double* aos, int n, std::vector<double>& soa) {
 // one AP force evaluation of the current positions (stages a1-a7), in two parts around the
 // ACE contraction.  after_drift: the kick-drift kernel of this step already took the
 // neighbour-list displacement test (positions change only there between evaluations of a
-// step loop), so the separate check is left out; inside a step graph the rebuild launches
-// then sit in a conditional node on that kernel's decision.  kick_dt > 0: the blend kernel
-// also applies the step's second half kick.
+// step loop), so the separate check is left out.  kick_dt > 0: the blend kernel also
+// applies the step's second half kick.
 void run_forces_pre(ap_ctx* xc, cudaStream_t s, bool after_drift) {
     ap::Ctx& c = xc->c;
-    if (c.rb_cond_on) {
-        // inside a graph: the kick-drift kernel, or else the check kernel, sets the condition
-        if (!after_drift) stage(xc, AP_STAGE_NEIGHBOR, s, [&] { return ap::launch_check(c, s); });
-        stage(xc, AP_STAGE_PREPARE, s, [&] { return prepare_then_rebuild(xc, s); });
-    } else {
-        stage(xc, AP_STAGE_NEIGHBOR, s, [&] { return (after_drift ? 0 : ap::launch_check(c, s)) + ap::launch_rebuild(c, s); });
-        stage(xc, AP_STAGE_PREPARE, s, [&] { return ap::launch_prepare(c, s); });
-        stage(xc, AP_STAGE_NEIGHBOR, s, [&] { return ap::launch_build(c, s, 0); });
-    }
+    stage(xc, AP_STAGE_NEIGHBOR, s, [&] { return (after_drift ? 0 : ap::launch_check(c, s)) + ap::launch_rebuild(c, s); });
+    stage(xc, AP_STAGE_PREPARE, s, [&] { return ap::launch_prepare(c, s); });
+    stage(xc, AP_STAGE_NEIGHBOR, s, [&] { return ap::launch_build(c, s, 0); });
     stage(xc, AP_STAGE_EAM_DENSITY, s, [&] { return ap::launch_eam_density(c, s); });
     stage(xc, AP_STAGE_EAM_FORCE, s, [&] { return ap::launch_eam_force(c, s); });
     stage(xc, AP_STAGE_ACE_BASIS, s, [&] { return ap::launch_ace_basis(c, s); });
@@ -705,15 +622,14 @@ ap_status ap_compute_forces_host(ap_ctx* xc, const double* h_pos, float* h_force
     if (!c.pos_stage && ((st = dalloc(c, &c.pos_stage, 3 * N)) || (st = dalloc(c, &c.f_stage, 3 * N)))) return st;
     cudaError_t e = cudaSuccess;
     if (capturable(s) && c.prof == 0) {
-        // the kernels as one replayed graph (the check kernel sets its rebuild condition)
+        // the kernels as one replayed graph
         const int mode = (h_pos ? 1 : 0) | (h_energy ? 2 : 0);
         if (xc->host_exec && (xc->host_stream != s || xc->host_gen != c.layout_gen || xc->host_mode != mode)) {
             cudaGraphExecDestroy(xc->host_exec);
             xc->host_exec = nullptr;
         }
         if (!xc->host_exec) {
-            e = capture_graph(xc, s, true, &xc->host_exec, &xc->host_kernels, [&] {
-                new_step_condition(xc, s);
+            e = capture_graph(xc, s, &xc->host_exec, &xc->host_kernels, [&] {
                 if (h_pos) c.launches += ap::launch_pos_in(c, s, c.pos_stage);
                 run_forces(xc, s, c.f_stage);
                 if (h_energy) c.launches += ap::launch_energy(c, s, false) + ap::launch_reduce(c, s, 0);
@@ -771,13 +687,75 @@ int step_kernels(ap::Ctx& c, cudaStream_t s, double dt, int part) {
 }
 
 
+// The kernels of one captured MD step: kick-drift, the force pass, the kicks.  timed:
+// event-record nodes of xc->ev_mark bracket the ACE contraction.
+void captured_step(ap_ctx* xc, cudaStream_t s, double dt, bool timed) {
+    ap::Ctx& c = xc->c;
+    const double kick = kick_in_blend(c) ? dt : 0.0;
+    c.launches += step_kernels(c, s, dt, 0);
+    if (!timed) {
+        run_forces(xc, s, nullptr, true, kick);
+    } else {
+        run_forces_pre(xc, s, true);
+        cudaError_t r = cudaEventRecordWithFlags(xc->ev_mark[0], s, cudaEventRecordExternal);
+        c.launches += ap::launch_ace(c, s);
+        if (r == cudaSuccess) r = cudaEventRecordWithFlags(xc->ev_mark[1], s, cudaEventRecordExternal);
+        if (r != cudaSuccess && xc->cap_err == cudaSuccess) {
+            xc->cap_err = r;
+            xc->cap_where = "event record";
+        }
+        run_forces_post(xc, s, nullptr, kick);
+    }
+    c.launches += step_kernels(c, s, dt, 1);
+}
+
+// the timed step graph and the handles of its two event-record nodes
+cudaError_t capture_timed_step(ap_ctx* xc, cudaStream_t s, double dt) {
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < 2 && e == cudaSuccess; ++q)
+        if (!xc->ev_mark[q]) e = cudaEventCreate(&xc->ev_mark[q]);
+    if (e == cudaSuccess)
+        e = capture_graph(xc, s, &xc->timed_exec, &xc->timed_kernels, [&] { captured_step(xc, s, dt, true); },
+                          &xc->timed_graph);
+    if (e != cudaSuccess) return e;
+    size_t nn = 0;
+    e = cudaGraphGetNodes(xc->timed_graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (e == cudaSuccess && nn) e = cudaGraphGetNodes(xc->timed_graph, nodes.data(), &nn);
+    for (size_t k = 0; k < nn && e == cudaSuccess; ++k) {
+        cudaGraphNodeType t;
+        e = cudaGraphNodeGetType(nodes[k], &t);
+        if (e != cudaSuccess || t != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev = nullptr;
+        e = cudaGraphEventRecordNodeGetEvent(nodes[k], &ev);
+        for (int q = 0; q < 2; ++q)
+            if (ev == xc->ev_mark[q]) xc->ev_node[q] = nodes[k];
+    }
+    if (e == cudaSuccess && (!xc->ev_node[0] || !xc->ev_node[1])) {
+        e = cudaErrorInvalidValue;
+        xc->cap_where = "event nodes";
+    }
+    return e;
+}
+
+// one replay of the timed step graph with a fresh event pair on its event-record nodes
+cudaError_t replay_timed_step(ap_ctx* xc, cudaStream_t s) {
+    if (xc->pending.size() >= 64) drain_ready(xc);
+    cudaEvent_t a = get_event(xc), b = get_event(xc);
+    cudaError_t e = cudaGraphExecEventRecordNodeSetEvent(xc->timed_exec, xc->ev_node[0], a);
+    if (e == cudaSuccess) e = cudaGraphExecEventRecordNodeSetEvent(xc->timed_exec, xc->ev_node[1], b);
+    if (e == cudaSuccess) e = cudaGraphLaunch(xc->timed_exec, s);
+    if (e == cudaSuccess) xc->pending.push_back({AP_STAGE_ACE, a, b});
+    return e;
+}
+
 ap_status ap_step(ap_ctx* xc, int n_steps, double dt, void* stream) {
     if (!xc || n_steps < 0 || !(dt > 0.0)) return AP_ERR_ARG;
     ap::Ctx& c = xc->c;
     cudaStream_t s = pick(xc, stream);
     if (!c.forces_valid) run_forces(xc, s, nullptr);
-    const double kick = kick_in_blend(c) ? dt : 0.0;
     if (c.prof == 1 || !capturable(s) || n_steps == 0) {
+        const double kick = kick_in_blend(c) ? dt : 0.0;
         for (int k = 0; k < n_steps; ++k) {
             stage(xc, AP_STAGE_INTEGRATE, s, [&] { return step_kernels(c, s, dt, 0); });
             run_forces(xc, s, nullptr, true, kick);
@@ -787,123 +765,53 @@ ap_status ap_step(ap_ctx* xc, int n_steps, double dt, void* stream) {
         }
         return cuda_check(c, cudaGetLastError(), "ap_step");
     }
-    if ((xc->step_exec || xc->timed_exec) &&
+    if ((xc->step_exec || xc->block_exec || xc->timed_exec) &&
         (xc->step_stream != s || xc->step_dt != dt || xc->step_gen != c.layout_gen))
         drop_step_graph(xc);
-    auto tag = [&] {
-        xc->step_stream = s;
-        xc->step_dt = dt;
-        xc->step_gen = c.layout_gen;
-    };
-    auto steps = [&](int k) {
-        return [&, k] {
-            for (int q = 0; q < k; ++q) {
-                new_step_condition(xc, s);
-                c.launches += step_kernels(c, s, dt, 0);
-                run_forces(xc, s, nullptr, true, kick);
-                c.launches += step_kernels(c, s, dt, 1);
-            }
-        };
-    };
-    if (c.prof >= 2) {
-        if (!xc->timed_exec) {
-            cudaError_t e = cudaSuccess;
-            for (int q = 0; q < 2 && e == cudaSuccess; ++q)
-                if (!xc->ev_mark[q]) e = cudaEventCreate(&xc->ev_mark[q]);
-            if (e == cudaSuccess)
-                e = capture_graph(xc, s, true, &xc->timed_exec, &xc->timed_kernels, [&] {
-                    new_step_condition(xc, s);
-                    c.launches += step_kernels(c, s, dt, 0);
-                    run_forces_pre(xc, s, true);
-                    cudaError_t r = cudaEventRecordWithFlags(xc->ev_mark[0], s, cudaEventRecordExternal);
-                    c.launches += ap::launch_ace(c, s);
-                    if (r == cudaSuccess) r = cudaEventRecordWithFlags(xc->ev_mark[1], s, cudaEventRecordExternal);
-                    if (r != cudaSuccess && xc->cap_err == cudaSuccess) {
-                        xc->cap_err = r;
-                        xc->cap_where = "event record";
-                    }
-                    run_forces_post(xc, s, nullptr, kick);
-                    c.launches += step_kernels(c, s, dt, 1);
-                }, &xc->timed_graph);
-            if (e == cudaSuccess) {
-                // the two event-record nodes of the capture
-                size_t nn = 0;
-                e = cudaGraphGetNodes(xc->timed_graph, nullptr, &nn);
-                std::vector<cudaGraphNode_t> nodes(nn);
-                if (e == cudaSuccess && nn) e = cudaGraphGetNodes(xc->timed_graph, nodes.data(), &nn);
-                for (size_t k = 0; k < nn && e == cudaSuccess; ++k) {
-                    cudaGraphNodeType t;
-                    e = cudaGraphNodeGetType(nodes[k], &t);
-                    if (e != cudaSuccess || t != cudaGraphNodeTypeEventRecord) continue;
-                    cudaEvent_t ev = nullptr;
-                    e = cudaGraphEventRecordNodeGetEvent(nodes[k], &ev);
-                    for (int q = 0; q < 2; ++q)
-                        if (ev == xc->ev_mark[q]) xc->ev_node[q] = nodes[k];
-                }
-                if (e == cudaSuccess && (!xc->ev_node[0] || !xc->ev_node[1])) {
-                    e = cudaErrorInvalidValue;
-                    xc->cap_where = "event nodes";
-                }
-            }
-            if (e != cudaSuccess) {
-                drop_step_graph(xc);
-                return graph_error(xc, e);
-            }
-            tag();
-        }
-        if (c.prof == 3 && !xc->step_exec) {
-            long long kernels = 0;
-            cudaError_t e = capture_graph(xc, s, true, &xc->step_exec, &kernels, steps(1));
-            if (e != cudaSuccess) return graph_error(xc, e);
-            xc->step_kernels = kernels;
-        }
-        for (int k = 0; k < n_steps; ++k) {
-            // mode 3: the other seven of eight steps replay the untimed step graph
-            if (c.prof == 3 && (xc->timed_count++ & 7) != 0) {
-                cudaError_t e = cudaGraphLaunch(xc->step_exec, s);
-                if (e != cudaSuccess) return cuda_check(c, e, "ap_step launch");
-                c.launches += xc->step_kernels;
-                c.t += dt;
-                c.step += 1;
-                continue;
-            }
-            if (xc->pending.size() >= 64) drain_ready(xc);
-            cudaEvent_t a = get_event(xc), b = get_event(xc);
-            cudaError_t e = cudaGraphExecEventRecordNodeSetEvent(xc->timed_exec, xc->ev_node[0], a);
-            if (e == cudaSuccess) e = cudaGraphExecEventRecordNodeSetEvent(xc->timed_exec, xc->ev_node[1], b);
-            if (e == cudaSuccess) e = cudaGraphLaunch(xc->timed_exec, s);
-            if (e != cudaSuccess) return cuda_check(c, e, "ap_step launch");
-            xc->pending.push_back({AP_STAGE_ACE, a, b});
-            c.launches += xc->timed_kernels;
-            c.t += dt;
-            c.step += 1;
-        }
-        c.forces_valid = true;
-        c.energy_fresh = false;
-        return AP_OK;
-    }
+    xc->step_stream = s;
+    xc->step_dt = dt;
+    xc->step_gen = c.layout_gen;
+    // the graphs this call replays, captured on first need: the timed step (profiling modes
+    // 2 and 3), the single step, the block of kStepBlock steps
+    const bool timed = c.prof >= 2;
+    const bool need_single = timed ? c.prof == 3 : n_steps % kStepBlock != 0;
+    const bool need_block = !timed && n_steps >= kStepBlock;
     long long kernels = 0;
-    if (!xc->step_exec) {
-        cudaError_t e = capture_graph(xc, s, true, &xc->step_exec, &kernels, steps(1));
-        if (e != cudaSuccess) return graph_error(xc, e);
-        xc->step_kernels = kernels;
-        tag();
+    cudaError_t e = cudaSuccess;
+    if (timed && !xc->timed_exec) e = capture_timed_step(xc, s, dt);
+    if (e == cudaSuccess && need_single && !xc->step_exec) {
+        e = capture_graph(xc, s, &xc->step_exec, &kernels, [&] { captured_step(xc, s, dt, false); });
+        if (e == cudaSuccess) xc->step_kernels = kernels;
     }
-    if (n_steps >= kStepBlock && !xc->block_exec) {
-        cudaError_t e = capture_graph(xc, s, true, &xc->block_exec, &kernels, steps(kStepBlock));
-        if (e != cudaSuccess) return graph_error(xc, e);
+    if (e == cudaSuccess && need_block && !xc->block_exec) {
+        e = capture_graph(xc, s, &xc->block_exec, &kernels, [&] {
+            for (int q = 0; q < kStepBlock; ++q) captured_step(xc, s, dt, false);
+        });
+        if (e == cudaSuccess) xc->step_kernels = kernels / kStepBlock;
     }
-    int left = n_steps;
-    while (left > 0) {
-        const bool block = left >= kStepBlock && xc->block_exec;
-        const int k = block ? kStepBlock : 1;
-        cudaError_t e = cudaGraphLaunch(block ? xc->block_exec : xc->step_exec, s);
-        if (e != cudaSuccess) return cuda_check(c, e, "ap_step launch");
-        c.launches += xc->step_kernels * k;
+    if (e != cudaSuccess) {
+        drop_step_graph(xc);
+        return graph_error(xc, e);
+    }
+    for (int left = n_steps; left > 0 && e == cudaSuccess;) {
+        int k = 1;
+        long long launched = xc->step_kernels;
+        if (timed && (c.prof == 2 || (xc->timed_count++ & 7) == 0)) {
+            // mode 3: one step in eight is timed, the others replay the untimed step graph
+            e = replay_timed_step(xc, s);
+            launched = xc->timed_kernels;
+        } else if (!timed && left >= kStepBlock) {
+            e = cudaGraphLaunch(xc->block_exec, s);
+            k = kStepBlock;
+        } else {
+            e = cudaGraphLaunch(xc->step_exec, s);
+        }
+        c.launches += launched * k;
         c.t += dt * k;
         c.step += k;
         left -= k;
     }
+    if (e != cudaSuccess) return cuda_check(c, e, "ap_step launch");
     c.forces_valid = true;
     c.energy_fresh = false;
     return AP_OK;
@@ -1208,7 +1116,6 @@ void ap_destroy(ap_ctx* xc) {
     if (!xc) return;
     cudaStreamSynchronize(xc->c.stream);
     drop_step_graph(xc);
-    if (xc->aux) cudaStreamDestroy(xc->aux);
     for (cudaEvent_t e : xc->ev_mark)
         if (e) cudaEventDestroy(e);
     drain_events(xc);

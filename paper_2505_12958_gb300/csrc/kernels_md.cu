@@ -256,30 +256,23 @@ __global__ void __launch_bounds__(kRedBlock) k_reduce(const double* __restrict__
 // first half kick and drift; the neighbour-list displacement test of the step is taken here,
 // where x is in registers (an atom that moved more than skin/2 since the last build sets the
 // rebuild flag), and the compaction counter of the coming force pass is reset
-// set_rb: launched inside a step graph, whose rebuild condition rb this kernel sets
 __global__ void k_kick_drift(double* __restrict__ x, double* __restrict__ v, const float* __restrict__ f,
                              const unsigned char* __restrict__ fixed, int n, double hdta, double dt,
                              double* __restrict__ tptr, long long* __restrict__ step,
-                             const double* __restrict__ xb, double lim2, int* __restrict__ flags,
-                             cudaGraphConditionalHandle rb, int set_rb) {
+                             const double* __restrict__ xb, double lim2, int* __restrict__ flags) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) { *tptr += dt; *step += 1; flags[kFlagNAce] = 0; }
-    if (i < n && !fixed[i]) {
-        double d2 = 0.0;
-        for (int k = 0; k < 3; ++k) {
-            const double vk = v[(size_t)k * n + i] + hdta * (double)f[(size_t)k * n + i];
-            v[(size_t)k * n + i] = vk;
-            const double xk = x[(size_t)k * n + i] + dt * vk;
-            x[(size_t)k * n + i] = xk;
-            const double d = xk - xb[(size_t)k * n + i];
-            d2 += d * d;
-        }
-        if (d2 > lim2) {
-            atomicOr(&flags[kFlagRebuild], 1);
-            __threadfence();
-        }
+    if (i >= n || fixed[i]) return;
+    double d2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        const double vk = v[(size_t)k * n + i] + hdta * (double)f[(size_t)k * n + i];
+        v[(size_t)k * n + i] = vk;
+        const double xk = x[(size_t)k * n + i] + dt * vk;
+        x[(size_t)k * n + i] = xk;
+        const double d = xk - xb[(size_t)k * n + i];
+        d2 += d * d;
     }
-    if (set_rb) publish_rebuild(flags, rb);           // set_rb is uniform over the grid
+    if (d2 > lim2) flags[kFlagRebuild] = 1;
 }
 
 __global__ void k_kick(double* __restrict__ v, const float* __restrict__ f, const unsigned char* __restrict__ fixed,
@@ -462,7 +455,7 @@ int launch_reduce(Ctx& c, cudaStream_t s, int with_kinetic) {
 int launch_kick_drift(Ctx& c, cudaStream_t s, double dt, int) {
     const double lim = 0.5 * c.skin;
     k_kick_drift<<<(c.n + 255) / 256, 256, 0, s>>>(c.x, c.v, c.f, c.fixed, c.n, 0.5 * dt * kFtm / c.mass, dt, c.d_time,
-                                                    c.d_step, c.xb, lim * lim, c.flags, c.rb_cond, c.rb_cond_on ? 1 : 0);
+                                                    c.d_step, c.xb, lim * lim, c.flags);
     return 1;
 }
 

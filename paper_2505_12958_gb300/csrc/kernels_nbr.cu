@@ -19,29 +19,20 @@ namespace ap {
 
 namespace {
 
-// the list displacement test; set_rb: launched inside a graph, whose rebuild condition rb
-// this kernel sets
 __global__ void k_check(const double* __restrict__ x, const double* __restrict__ xb, int n, double lim2,
-                        int* flags, cudaGraphConditionalHandle rb, int set_rb) {
+                        int* flags) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) flags[kFlagNAce] = 0;
-    if (i < n) {
-        double dx = x[i] - xb[i], dy = x[n + i] - xb[n + i], dz = x[2 * n + i] - xb[2 * n + i];
-        if (dx * dx + dy * dy + dz * dz > lim2) {
-            atomicOr(&flags[kFlagRebuild], 1);
-            __threadfence();
-        }
-    }
-    if (set_rb) publish_rebuild(flags, rb);           // set_rb is uniform over the grid
+    if (i >= n) return;
+    double dx = x[i] - xb[i], dy = x[n + i] - xb[n + i], dz = x[2 * n + i] - xb[2 * n + i];
+    if (dx * dx + dy * dy + dz * dz > lim2) flags[kFlagRebuild] = 1;
 }
 
 __global__ void k_wrap_bin(double* __restrict__ x, double* __restrict__ xb, int n, const GridDev g,
                            int* __restrict__ cell, int* __restrict__ cell_count, int* __restrict__ flags) {
     if (flags[kFlagRebuild] == 0) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    // a prepare pass on the old cells may have compacted already (inside a step graph); the
-    // prepare pass after this rebuild counts afresh
-    if (i == 0) { flags[kFlagRebuilds] += 1; flags[kFlagNAce] = 0; }
+    if (i == 0) flags[kFlagRebuilds] += 1;
     if (i >= n) return;
     double r[3] = {x[i], x[n + i], x[2 * n + i]};
     double d[3] = {r[0] - g.origin[0], r[1] - g.origin[1], r[2] - g.origin[2]};
@@ -128,9 +119,7 @@ __global__ void k_sort_cells(int* __restrict__ cell_atoms, const int* __restrict
 __global__ void k_prepare(const double* __restrict__ x, int n, const GridDev g, const DynDev dy,
                           const double* __restrict__ tptr, const int* __restrict__ cell,
                           const double* __restrict__ w_fixed, float4* __restrict__ pos4,
-                          float* __restrict__ wout, int* __restrict__ ace_list, int* __restrict__ flags,
-                          int only_if_rebuild) {
-    if (only_if_rebuild && flags[kFlagRebuild] == 0) return;      // uniform over the grid
+                          float* __restrict__ wout, int* __restrict__ ace_list, int* __restrict__ flags) {
     __shared__ float sh[9];          // box origin, cell edges (orthorhombic), zone centre at time t
     if (threadIdx.x == 0 && dy.reg_kind == AP_REGION_SPHERE && g.ortho) {
         const double t = *tptr;
@@ -310,7 +299,7 @@ __global__ void __launch_bounds__(kBuildBlock) k_build(const float4* __restrict_
 
 int launch_check(Ctx& c, cudaStream_t s) {
     double lim = 0.5 * c.skin;
-    k_check<<<(c.n + 255) / 256, 256, 0, s>>>(c.x, c.xb, c.n, lim * lim, c.flags, c.rb_cond, c.rb_cond_on ? 1 : 0);
+    k_check<<<(c.n + 255) / 256, 256, 0, s>>>(c.x, c.xb, c.n, lim * lim, c.flags);
     return 1;
 }
 
@@ -323,9 +312,9 @@ int launch_rebuild(Ctx& c, cudaStream_t s) {
     return 4;
 }
 
-int launch_prepare(Ctx& c, cudaStream_t s, bool only_if_rebuild) {
+int launch_prepare(Ctx& c, cudaStream_t s) {
     k_prepare<<<(c.n + 255) / 256, 256, 0, s>>>(c.x, c.n, c.grid, c.dyn, c.d_time, c.cell, c.w_fixed, c.pos4, c.w,
-                                               c.ace_list, c.flags, only_if_rebuild ? 1 : 0);
+                                               c.ace_list, c.flags);
     return 1;
 }
 

@@ -39,10 +39,10 @@ def test_energy_report_after_host_evaluation_has_the_virial(apl):
 
 
 def test_host_evaluation_graph_matches_plain_launches(apl):
-    """On a non-legacy stream the host-buffer evaluation replays a captured graph whose
-    rebuild kernels sit in a conditional node set by the check kernel; it must give the bits
-    of the plain launches on the legacy stream, also when the positions move far enough to
-    rebuild the neighbour list, and without positions (the library-owned ones)."""
+    """On a non-legacy stream the host-buffer evaluation replays a captured graph; it must
+    give the bits of the plain launches on the legacy stream, also when the positions move far
+    enough to rebuild the neighbour list (decided on the device inside the graph), and without
+    positions (the library-owned ones)."""
     import torch
     c = synth.configs.w_slab(ncell=8, nz=6, r_in=6.0, r_sw=3.0, R=8.0, penetration=1.0)
     rng = np.random.default_rng(3)

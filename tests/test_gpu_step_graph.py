@@ -1,7 +1,6 @@
 """Replayed step graphs and batched stepping: a step captured as a CUDA graph on a
-non-blocking stream (its rebuild kernels in conditional nodes) must give the same bits as
-the plain launch loop on the legacy stream, and a context stepped inside a batch the same
-bits as the context stepped alone."""
+non-blocking stream must give the same bits as the plain launch loop on the legacy stream,
+and a context stepped inside a batch the same bits as the context stepped alone."""
 import numpy as np
 import pytest
 
@@ -55,8 +54,7 @@ def test_graph_replay_matches_plain_loop(apl):
 
 def test_timed_step_graph_matches_plain_loop(apl):
     """With only the ACE contraction timed, a step replays a graph whose event-record nodes
-    around the contraction get a fresh event pair each time; the rebuild kernels sit in a
-    conditional node."""
+    around the contraction get a fresh event pair each time."""
     import torch
     c = _hot_slab()
     s = torch.cuda.Stream()
