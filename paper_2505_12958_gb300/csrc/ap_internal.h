@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <string>
+#include <utility>
 
 #include "ap.h"
 #include "ace_pattern.h"
@@ -187,6 +188,32 @@ struct Ctx {
     double stage_ms[AP_NSTAGE] = {0};
     long long stage_n[AP_NSTAGE] = {0};
 };
+
+// Programmatic dependent launch.  The kernels of a force pass and a step are launched with
+// launch_pdl, so that each may be scheduled while the previous kernel on the stream drains.
+// Each calls pdl_wait() before its first access to device data that an earlier kernel
+// writes or reads; before it, only constant tables (potential, cell offsets) are read.  A
+// kernel that ends only after its wait keeps the order transitive.  Launched plainly, the
+// wait returns at once.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#endif
+
+template <class... KArgs, class... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 static_assert(sizeof(EamDev) % 16 == 0, "EamDev is staged in 16-byte words");
 static_assert(sizeof(AceDev) % 16 == 0, "AceDev is staged in 16-byte words");

@@ -893,6 +893,7 @@ __global__ void __launch_bounds__(256) k_ace_basis(const float4* __restrict__ po
     __shared__ BasisSmem WS[8];
     for (int k = threadIdx.x; k < ncode; k += blockDim.x) Ds[k] = Dtab[k];
     __syncthreads();
+    pdl_wait();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gq = lane >> 2, tq = lane & 3;
     BasisSmem& S = WS[warp];
@@ -1039,6 +1040,7 @@ k_ace_contract(const AceDev* __restrict__ tab, const int* __restrict__ ace_list,
         for (int k = threadIdx.x; k < kContractWarps * 4 * (kApad + 1); k += blockDim.x) z[k] = 0.0f;
     }
     __syncthreads();
+    pdl_wait();                                            // the constant tables are staged
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     ContractSmem& S = WS[warp];
     const int n_ace = flags[kFlagNAce];
@@ -1211,6 +1213,7 @@ __global__ void __launch_bounds__(256) k_ace_force(const float4* __restrict__ po
     __shared__ ForceSmem WS[8];
     for (int k = threadIdx.x; k < ncode; k += blockDim.x) Ds[k] = Dtab[k];
     __syncthreads();
+    pdl_wait();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     ForceSmem& S = WS[warp];
     const float rc = tab->rc, rc2 = rc * rc, nrefi = tab->nref_inv;
@@ -1296,8 +1299,8 @@ int persistent_blocks(K kernel, int dev, int threads, size_t smem) {
 template <int MODE>
 void launch_basis_mode(Ctx& c, cudaStream_t s) {
     const int nb = persistent_blocks(k_ace_basis<MODE>, c.dev, 256, 0);
-    k_ace_basis<MODE><<<nb, 256, 0, s>>>(c.pos4, c.nbr, c.nnbr, c.n, c.D, c.grid.ncode, c.ace_d, c.ace_list, c.flags,
-                                         c.ace_A);
+    launch_pdl(k_ace_basis<MODE>, nb, 256, 0, s, c.pos4, c.nbr, c.nnbr, c.n, c.D, c.grid.ncode, c.ace_d, c.ace_list,
+               c.flags, c.ace_A);
 }
 
 int launch_ace_basis(Ctx& c, cudaStream_t s) {
@@ -1319,15 +1322,15 @@ int launch_ace(Ctx& c, cudaStream_t s) {
     }
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c.dev);
-    k_ace_contract<<<nsm * 2, kContractWarps * 32, ace_contract_smem_bytes(), s>>>(c.ace_d, c.ace_list, c.flags,
-                                                                                 c.ace_A, c.ace_dA, c.e_ace);
+    launch_pdl(k_ace_contract, nsm * 2, kContractWarps * 32, ace_contract_smem_bytes(), s, c.ace_d, c.ace_list, c.flags,
+               c.ace_A, c.ace_dA, c.e_ace);
     return 1;
 }
 
 int launch_ace_force(Ctx& c, cudaStream_t s) {
     const int nb = persistent_blocks(k_ace_force, c.dev, 256, 0);
-    k_ace_force<<<nb, 256, 0, s>>>(c.pos4, c.nbr, c.nnbr, c.n, c.D, c.grid.ncode, c.ace_d, c.ace_list, c.w,
-                                        c.flags, c.ace_dA, c.vir_ace, c.acc);
+    launch_pdl(k_ace_force, nb, 256, 0, s, c.pos4, c.nbr, c.nnbr, c.n, c.D, c.grid.ncode, c.ace_d, c.ace_list, c.w,
+               c.flags, c.ace_dA, c.vir_ace, c.acc);
     return 1;
 }
 

@@ -42,7 +42,8 @@ __global__ void __launch_bounds__(kEamBlock) k_eam_density(const float4* __restr
                                                      double* __restrict__ e_emb, int* __restrict__ flags) {
     __shared__ EamDev T;
     __shared__ float4 Ds[125];
-    stage_tables(&T, eam, Ds, D, ncode);
+    stage_tables(&T, eam, Ds, D, ncode);          // constant tables: before the wait
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) flags[kFlagRebuild] = 0;        // the list built this step is in use now
     if (i >= n) return;
@@ -98,7 +99,8 @@ __global__ void __launch_bounds__(kEamBlock) k_eam_force(const float4* __restric
                                                    float* __restrict__ f, double* __restrict__ e_eam) {
     __shared__ EamDev T;
     __shared__ float4 Ds[125];
-    stage_tables(&T, eam, Ds, D, ncode);
+    stage_tables(&T, eam, Ds, D, ncode);          // constant tables: before the wait
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float4 p = pos4[i];
@@ -332,14 +334,14 @@ int launch_eam_energy(Ctx& c, cudaStream_t s, bool virial) {
 }
 
 int launch_eam_density(Ctx& c, cudaStream_t s) {
-    k_eam_density<<<(c.n + kEamBlock - 1) / kEamBlock, kEamBlock, 0, s>>>(c.pos4, c.nbr, c.nnbr, c.n, c.eam_d, c.D, c.grid.ncode, c.uxi,
-                                                   c.e_emb, c.flags);
+    launch_pdl(k_eam_density, (c.n + kEamBlock - 1) / kEamBlock, kEamBlock, 0, s, c.pos4, c.nbr, c.nnbr, c.n, c.eam_d,
+               c.D, c.grid.ncode, c.uxi, c.e_emb, c.flags);
     return 1;
 }
 
 int launch_eam_force(Ctx& c, cudaStream_t s) {
-    k_eam_force<<<(c.n + kEamBlock - 1) / kEamBlock, kEamBlock, 0, s>>>(c.pos4, c.nbr, c.nnbr, c.n, c.eam_d, c.D, c.grid.ncode, c.uxi,
-                                                 c.e_emb, c.w, c.f, c.e_eam);
+    launch_pdl(k_eam_force, (c.n + kEamBlock - 1) / kEamBlock, kEamBlock, 0, s, c.pos4, c.nbr, c.nnbr, c.n, c.eam_d,
+               c.D, c.grid.ncode, c.uxi, c.e_emb, c.w, c.f, c.e_eam);
     return 1;
 }
 

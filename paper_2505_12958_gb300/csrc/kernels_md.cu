@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(kRedBlock) k_blend(
     const float* __restrict__ wv, float* __restrict__ f, unsigned long long* __restrict__ acc,
     const float* __restrict__ e_ace, const double* __restrict__ e_eam, double c1_0, float* __restrict__ out_aos,
     int* __restrict__ flags, double hdta, const unsigned char* __restrict__ fixed, double* __restrict__ v) {
+    pdl_wait();
     // FP64 runs at 1/64 of the FP32 rate on this GPU.  Positions are taken in FP32 from the
     // cell origin and x_rel (absolute error ~1e-5 A) for the indenter pre-test, inside its
     // margin, and for the weight-gradient force of the switching shell, whose relative error
@@ -260,6 +261,7 @@ __global__ void k_kick_drift(double* __restrict__ x, double* __restrict__ v, con
                              const unsigned char* __restrict__ fixed, int n, double hdta, double dt,
                              double* __restrict__ tptr, long long* __restrict__ step,
                              const double* __restrict__ xb, double lim2, int* __restrict__ flags) {
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) { *tptr += dt; *step += 1; flags[kFlagNAce] = 0; }
     if (i >= n || fixed[i]) return;
@@ -277,6 +279,7 @@ __global__ void k_kick_drift(double* __restrict__ x, double* __restrict__ v, con
 
 __global__ void k_kick(double* __restrict__ v, const float* __restrict__ f, const unsigned char* __restrict__ fixed,
                        int n, double hdta) {
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || fixed[i]) return;
     for (int k = 0; k < 3; ++k) v[(size_t)k * n + i] += hdta * (double)f[(size_t)k * n + i];
@@ -427,8 +430,8 @@ int launch_pos_in(Ctx& c, cudaStream_t s, const double* pos) {
 
 int launch_blend(Ctx& c, cudaStream_t s, float* out_aos, double kick_dt) {
     const double hdta = kick_dt > 0.0 ? 0.5 * kick_dt * kFtm / c.mass : 0.0;
-    k_blend<<<c.nred, kRedBlock, 0, s>>>(c.x, c.n, c.grid, c.dyn, c.d_time, c.pos4, c.cell, c.w, c.f, c.acc, c.e_ace,
-                                         c.e_eam, c.ace_c1_0, out_aos, c.flags, hdta, c.fixed, c.v);
+    launch_pdl(k_blend, c.nred, kRedBlock, 0, s, c.x, c.n, c.grid, c.dyn, c.d_time, c.pos4, c.cell, c.w, c.f, c.acc,
+               c.e_ace, c.e_eam, c.ace_c1_0, out_aos, c.flags, hdta, c.fixed, c.v);
     return 1;
 }
 
@@ -454,13 +457,13 @@ int launch_reduce(Ctx& c, cudaStream_t s, int with_kinetic) {
 
 int launch_kick_drift(Ctx& c, cudaStream_t s, double dt, int) {
     const double lim = 0.5 * c.skin;
-    k_kick_drift<<<(c.n + 255) / 256, 256, 0, s>>>(c.x, c.v, c.f, c.fixed, c.n, 0.5 * dt * kFtm / c.mass, dt, c.d_time,
-                                                    c.d_step, c.xb, lim * lim, c.flags);
+    launch_pdl(k_kick_drift, (c.n + 255) / 256, 256, 0, s, c.x, c.v, c.f, c.fixed, c.n, 0.5 * dt * kFtm / c.mass, dt,
+               c.d_time, c.d_step, c.xb, lim * lim, c.flags);
     return 1;
 }
 
 int launch_kick(Ctx& c, cudaStream_t s, double dt) {
-    k_kick<<<(c.n + 255) / 256, 256, 0, s>>>(c.v, c.f, c.fixed, c.n, 0.5 * dt * kFtm / c.mass);
+    launch_pdl(k_kick, (c.n + 255) / 256, 256, 0, s, c.v, c.f, c.fixed, c.n, 0.5 * dt * kFtm / c.mass);
     return 1;
 }
 

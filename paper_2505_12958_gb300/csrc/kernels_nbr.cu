@@ -21,6 +21,7 @@ namespace {
 
 __global__ void k_check(const double* __restrict__ x, const double* __restrict__ xb, int n, double lim2,
                         int* flags) {
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) flags[kFlagNAce] = 0;
     if (i >= n) return;
@@ -30,6 +31,7 @@ __global__ void k_check(const double* __restrict__ x, const double* __restrict__
 
 __global__ void k_wrap_bin(double* __restrict__ x, double* __restrict__ xb, int n, const GridDev g,
                            int* __restrict__ cell, int* __restrict__ cell_count, int* __restrict__ flags) {
+    pdl_wait();
     if (flags[kFlagRebuild] == 0) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) flags[kFlagRebuilds] += 1;
@@ -60,6 +62,7 @@ __global__ void k_wrap_bin(double* __restrict__ x, double* __restrict__ xb, int 
 // that the scatter can reuse them as fill pointers
 __global__ void k_scan(int* __restrict__ cell_count, int* __restrict__ cell_start, int ncell,
                        const int* __restrict__ flags) {
+    pdl_wait();
     if (flags[kFlagRebuild] == 0) return;
     __shared__ int part[1024];
     int tid = threadIdx.x, nt = blockDim.x;
@@ -86,6 +89,7 @@ __global__ void k_scan(int* __restrict__ cell_count, int* __restrict__ cell_star
 
 __global__ void k_scatter(const int* __restrict__ cell, int n, const int* __restrict__ cell_start,
                           int* __restrict__ fill, int* __restrict__ cell_atoms, const int* __restrict__ flags) {
+    pdl_wait();
     if (flags[kFlagRebuild] == 0) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -97,6 +101,7 @@ __global__ void k_scatter(const int* __restrict__ cell, int n, const int* __rest
 // order each cell's atoms by index and clear the per-cell counters for the next build
 __global__ void k_sort_cells(int* __restrict__ cell_atoms, const int* __restrict__ cell_start, int* __restrict__ fill,
                              int ncell, const int* __restrict__ flags) {
+    pdl_wait();
     if (flags[kFlagRebuild] == 0) return;
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
@@ -120,6 +125,7 @@ __global__ void k_prepare(const double* __restrict__ x, int n, const GridDev g, 
                           const double* __restrict__ tptr, const int* __restrict__ cell,
                           const double* __restrict__ w_fixed, float4* __restrict__ pos4,
                           float* __restrict__ wout, int* __restrict__ ace_list, int* __restrict__ flags) {
+    pdl_wait();
     __shared__ float sh[9];          // box origin, cell edges (orthorhombic), zone centre at time t
     if (threadIdx.x == 0 && dy.reg_kind == AP_REGION_SPHERE && g.ortho) {
         const double t = *tptr;
@@ -200,6 +206,7 @@ __global__ void __launch_bounds__(kBuildBlock) k_build(const float4* __restrict_
                                                        const int* __restrict__ cell_atoms, int* __restrict__ nbr,
                                                        int* __restrict__ nnbr, int cap, int* __restrict__ flags,
                                                        int count_only) {
+    pdl_wait();
     if (!count_only && flags[kFlagRebuild] == 0) return;
     __shared__ float4 D[125];
     __shared__ char4 O[125];                          // cell offset of each code (no divisions in the scan)
@@ -299,28 +306,29 @@ __global__ void __launch_bounds__(kBuildBlock) k_build(const float4* __restrict_
 
 int launch_check(Ctx& c, cudaStream_t s) {
     double lim = 0.5 * c.skin;
-    k_check<<<(c.n + 255) / 256, 256, 0, s>>>(c.x, c.xb, c.n, lim * lim, c.flags);
+    launch_pdl(k_check, (c.n + 255) / 256, 256, 0, s, c.x, c.xb, c.n, lim * lim, c.flags);
     return 1;
 }
 
 int launch_rebuild(Ctx& c, cudaStream_t s) {
     int nb = (c.n + 255) / 256;
-    k_wrap_bin<<<nb, 256, 0, s>>>(c.x, c.xb, c.n, c.grid, c.cell, c.cell_count, c.flags);
-    k_scan<<<1, 1024, 0, s>>>(c.cell_count, c.cell_start, c.grid.ncell, c.flags);
-    k_scatter<<<nb, 256, 0, s>>>(c.cell, c.n, c.cell_start, c.cell_count, c.cell_atoms, c.flags);
-    k_sort_cells<<<(c.grid.ncell + 255) / 256, 256, 0, s>>>(c.cell_atoms, c.cell_start, c.cell_count, c.grid.ncell, c.flags);
+    launch_pdl(k_wrap_bin, nb, 256, 0, s, c.x, c.xb, c.n, c.grid, c.cell, c.cell_count, c.flags);
+    launch_pdl(k_scan, 1, 1024, 0, s, c.cell_count, c.cell_start, c.grid.ncell, c.flags);
+    launch_pdl(k_scatter, nb, 256, 0, s, c.cell, c.n, c.cell_start, c.cell_count, c.cell_atoms, c.flags);
+    launch_pdl(k_sort_cells, (c.grid.ncell + 255) / 256, 256, 0, s, c.cell_atoms, c.cell_start, c.cell_count,
+               c.grid.ncell, c.flags);
     return 4;
 }
 
 int launch_prepare(Ctx& c, cudaStream_t s) {
-    k_prepare<<<(c.n + 255) / 256, 256, 0, s>>>(c.x, c.n, c.grid, c.dyn, c.d_time, c.cell, c.w_fixed, c.pos4, c.w,
-                                               c.ace_list, c.flags);
+    launch_pdl(k_prepare, (c.n + 255) / 256, 256, 0, s, c.x, c.n, c.grid, c.dyn, c.d_time, c.cell, c.w_fixed, c.pos4,
+               c.w, c.ace_list, c.flags);
     return 1;
 }
 
 int launch_build(Ctx& c, cudaStream_t s, int count_only) {
-    k_build<<<(c.n + kBuildBlock - 1) / kBuildBlock, kBuildBlock, 0, s>>>(c.pos4, c.cell, c.n, c.grid, c.D, c.cell_start, c.cell_atoms, c.nbr,
-                                             c.nnbr, c.cap, c.flags, count_only);
+    launch_pdl(k_build, (c.n + kBuildBlock - 1) / kBuildBlock, kBuildBlock, 0, s, c.pos4, c.cell, c.n, c.grid, c.D,
+               c.cell_start, c.cell_atoms, c.nbr, c.nnbr, c.cap, c.flags, count_only);
     return 1;
 }
 
