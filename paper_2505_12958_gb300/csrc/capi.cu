@@ -47,6 +47,10 @@ struct ap_ctx {
     int host_mode = -1;
     long long host_kernels = 0;
     cudaError_t cap_err = cudaSuccess;                  // the first error inside a capture
+    // the EAM passes run on a branch of their own (side), forked after the list build and
+    // joined before the blend, beside the ACE basis, contraction and force kernels
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     const char* cap_where = "";                          // the capture call that failed
 };
 
@@ -302,6 +306,13 @@ void free_all(ap_ctx* xc) {
     xc->arena = nullptr;
     xc->arena_bytes = 0;
     cudaStreamSynchronize(c.stream);
+    if (xc->side) cudaStreamSynchronize(xc->side);
+    for (cudaEvent_t* e : {&xc->fork_ev, &xc->join_ev}) {
+        if (*e) cudaEventDestroy(*e);
+        *e = nullptr;
+    }
+    if (xc->side) cudaStreamDestroy(xc->side);
+    xc->side = nullptr;
     pinned_give((char*)c.h_totals);
     c.h_totals = nullptr;
     c.h_flags = nullptr;
@@ -352,14 +363,26 @@ void run_forces_pre(ap_ctx* xc, cudaStream_t s, bool after_drift) {
     stage(xc, AP_STAGE_NEIGHBOR, s, [&] { return (after_drift ? 0 : ap::launch_check(c, s)) + ap::launch_rebuild(c, s); });
     stage(xc, AP_STAGE_PREPARE, s, [&] { return ap::launch_prepare(c, s); });
     stage(xc, AP_STAGE_NEIGHBOR, s, [&] { return ap::launch_build(c, s, 0); });
-    stage(xc, AP_STAGE_EAM_DENSITY, s, [&] { return ap::launch_eam_density(c, s); });
-    stage(xc, AP_STAGE_EAM_FORCE, s, [&] { return ap::launch_eam_force(c, s); });
+    if (c.prof == 1) {
+        // every stage timed: the EAM passes stay on s, inside their own events
+        stage(xc, AP_STAGE_EAM_DENSITY, s, [&] { return ap::launch_eam_density(c, s); });
+        stage(xc, AP_STAGE_EAM_FORCE, s, [&] { return ap::launch_eam_force(c, s); });
+    } else {
+        // the EAM branch: it writes only its own buffers (f, e_eam, uxi, e_emb), and the
+        // ACE kernels on s read none of them
+        cudaEventRecord(xc->fork_ev, s);
+        cudaStreamWaitEvent(xc->side, xc->fork_ev, 0);
+        c.launches += ap::launch_eam_density(c, xc->side);
+        c.launches += ap::launch_eam_force(c, xc->side);
+        cudaEventRecord(xc->join_ev, xc->side);
+    }
     stage(xc, AP_STAGE_ACE_BASIS, s, [&] { return ap::launch_ace_basis(c, s); });
 }
 
 void run_forces_post(ap_ctx* xc, cudaStream_t s, float* out_aos, double kick_dt) {
     ap::Ctx& c = xc->c;
     stage(xc, AP_STAGE_ACE_FORCE, s, [&] { return ap::launch_ace_force(c, s); });
+    if (c.prof != 1) cudaStreamWaitEvent(s, xc->join_ev, 0);      // join the EAM branch
     stage(xc, AP_STAGE_BLEND, s, [&] { return ap::launch_blend(c, s, out_aos, kick_dt); });
     c.forces_valid = true;
     c.energy_fresh = false;
@@ -469,6 +492,12 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
     };
     if (cudaGetDevice(&c.dev) != cudaSuccess) { c.err = "no CUDA device"; return fail(AP_ERR_CUDA); }
     pool_setup(c.dev);
+    if (cudaStreamCreateWithFlags(&xc->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&xc->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&xc->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+        c.err = "stream or event creation failed";
+        return fail(AP_ERR_CUDA);
+    }
     std::string err;
     if (ap::build_eam_tables(*pot, c.eam_h, err)) { c.err = err; return fail(AP_ERR_ARG); }
     c.ace_h = new (std::nothrow) ap::AceDev();
