@@ -41,3 +41,22 @@ def test_max_over_ranks_and_aggregate_rate():
     import bench
     assert bench.aggregate_rate(2, 128000, 10, 2.0) == pytest.approx(2 * 128000 * 10 / 2.0)
     assert bench.max_over_ranks(torch, 3.5, "cpu") == 3.5      # single process: unchanged
+
+
+def test_roofline_line_from_stage_events():
+    """The roofline entry divides the algorithmic work of one launch (the per-atom count
+    times the compacted atoms) by the CUDA-event average of the timed launches; the entry for
+    the kernel alone does the same with the per-stage pass's average."""
+    import bench
+    from paper_2505_12958_gb300.workload import ace_contract_flops_per_atom
+    atoms = list(range(1000))
+    prof = {"ace": (2.5, 5)}                          # 5 launches, 0.5 ms each
+    r = bench.ace_kernel_roofline(prof, 5, None, {"sm_max_mhz": 2000.0}, "test", atoms, fma_peak=80.0,
+                                  alone_ms=0.4)
+    flops = ace_contract_flops_per_atom() * 1000
+    assert r["algorithmic_flops_per_launch"] == flops and r["timed_launches"] == 5
+    assert abs(r["achieved"] - flops / 0.5e-3 / 1e12) < 1e-9 and abs(r["frac"] - r["achieved"] / 80.0) < 1e-12
+    assert abs(r["alone"]["achieved"] - flops / 0.4e-3 / 1e12) < 1e-9
+    assert r["alone"]["frac"] > r["frac"]
+    assert r["peak"] == 80.0 and abs(r["peak_derived_unit_count"] - 152 * 128 * 2 * 2.0e9 / 1e12) < 1e-9
+    assert bench.ace_kernel_roofline(prof, 5, None, {}, "test", atoms, fma_peak=80.0)["alone"] is None
