@@ -195,6 +195,112 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _with_neighbours(x, box, idx, rc):
+    """idx and every atom within rc of one of them (box periodic in x and y, open in z)."""
+    from scipy.spatial import cKDTree
+    h = np.asarray(box["h"]).reshape(3, 3)
+    L = np.diag(h)
+    y = np.array(x, dtype=np.float64) - np.asarray(box.get("origin", (0.0, 0.0, 0.0)))
+    y[:, :2] = np.mod(y[:, :2], L[:2])
+    y[:, 2] -= y[:, 2].min()
+    tree = cKDTree(y, boxsize=[L[0], L[1], 1e9])
+    near = tree.query_ball_point(y[np.asarray(idx)], r=rc)
+    return np.unique(np.concatenate([np.asarray(idx)] + [np.asarray(v, dtype=np.int64) for v in near]))
+
+
+def oracle_check(torch, ctx, c, nsample=64, seed=77, rc=5.5):
+    """Validity of the timed run: forces and per-atom energies of the timed context at its final
+    state (after the timed steps, at the GPU's positions and indenter time) against the FP64
+    oracle on sampled atoms (inside the ACE zone, in its shell, outside, under the tip, fixed).
+    The oracle evaluates the energies of every atom within rc (> the largest cutoff) of a sampled
+    atom, which makes the sampled forces and energies complete."""
+    import oracle
+    oracle.build()
+    x, _, t = ctx.get_state()
+    F = ctx.forces().astype(np.float64)
+    ea = torch.empty(len(x), dtype=torch.float64, device="cuda")
+    ctx.energy(e_atom=ea)
+    ea = ea.cpu().numpy()
+    reg = c["region"]
+    ind = dict(c["indenter"])
+    ind["center"] = tuple(np.asarray(ind["center"]) - np.asarray(c["ind_vel"]) * t)
+    d = np.linalg.norm(x - np.asarray(reg["center"]), axis=1)
+    di = np.linalg.norm(x - np.asarray(ind["center"]), axis=1)
+    free = c["fixed"] == 0
+    groups = [np.where((d < reg["r_in"]) & free)[0],
+              np.where((d >= reg["r_in"]) & (d < reg["r_in"] + reg["r_sw"]) & free)[0],
+              np.where((d >= reg["r_in"] + reg["r_sw"]) & free)[0], np.where(di < ind["R"])[0],
+              np.where(~free)[0]]
+    rng = np.random.default_rng(seed)
+    sample = np.unique(np.concatenate([rng.choice(g, size=min(len(g), nsample // len(groups) + 1), replace=False)
+                                       for g in groups if len(g)]))
+    centers = _with_neighbours(x, c["box"], sample, rc)
+    t0 = time.perf_counter()
+    ref = oracle.evaluate(x, c["box"], c["eam"], c["ace"], reg, ind, centers=centers)
+    dt = time.perf_counter() - t0
+    dF = float(np.abs(F[sample] - ref["forces"][sample]).max())
+    dE = ea[sample] - ref["e_atom"][sample]
+    return {"atoms": int(len(sample)), "centres": int(len(centers)), "time_fs": t, "oracle_status": ref["status"],
+            "max_dF_eV_A": dF, "max_abs_F_eV_A": float(np.abs(ref["forces"][sample]).max()),
+            "max_dE_atom_eV": float(np.abs(dE).max()), "mean_dE_atom_eV": float(dE.mean()),
+            "bars": {"max_dF_eV_A": 1e-4, "mean_dE_atom_eV": 1e-6, "max_dE_atom_eV": 2e-5},
+            "ok": bool(ref["status"] == 0 and dF <= 1e-4 and abs(dE.mean()) <= 1e-6 and np.abs(dE).max() <= 2e-5),
+            "oracle_s": dt}
+
+
+def precision_leg(torch, ap, steps=500, every=50, modes=("fp64", "fp32", "tf32x3", "bf16", "fp16"), nsample=1000):
+    """Precision form on the 2,000,000-atom Cu (001) slab (5 % ACE, thermal snapshot, 300 K):
+    for each precision mode of A_nlm, the max per-atom force error against the FP64 oracle on
+    seeded sampled atoms (half with w > 0), the MD time per step, and the NVE energy drift per
+    ps over `steps` steps with the indenter off (total energy sampled every `every` steps; the
+    drift is the slope of a least-squares line through them, per atom)."""
+    import oracle
+    oracle.build()
+    c = synth.configs.cu_slab(sigma=0.066)
+    n = len(c["x"])
+    reg = c["region"]
+    d = np.linalg.norm(c["x"] - np.asarray(reg["center"]), axis=1)
+    rng = np.random.default_rng(3003)
+    ace = np.where(d < reg["r_in"] + reg["r_sw"])[0]
+    rest = np.where(d >= reg["r_in"] + reg["r_sw"])[0]
+    cen = np.concatenate([rng.choice(ace, nsample // 2, replace=False), rng.choice(rest, nsample // 2, replace=False)])
+    t0 = time.perf_counter()
+    ref = oracle.evaluate(c["x"], c["box"], c["eam"], c["ace"], reg, None,
+                          centers=_with_neighbours(c["x"], c["box"], cen, 5.0 + 1e-6))
+    oracle_s = time.perf_counter() - t0
+    fref = ref["forces"][cen]
+    out = {}
+    for mode in modes:
+        ctx = ap.APContext(c["eam"], c["ace"], c["box"], c["x"], c["v"], c["fixed"], reg, None, None, c["mass"],
+                           precision=mode)
+        Fd = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+        ctx.compute_forces(None, Fd)
+        ctx.check()
+        dF = float(np.abs(Fd.cpu().numpy().astype(np.float64)[cen] - fref).max())
+        r0 = ctx.energy()
+        ts, es, ms = [0.0], [r0["e_total"] + r0["e_kin"]], 0.0
+        for k in range(steps // every):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ctx.step(every, 1.0)
+            b.record()
+            r = ctx.energy()
+            ms += a.elapsed_time(b)
+            ts.append(r["time_fs"])
+            es.append(r["e_total"] + r["e_kin"])
+        ctx.check()
+        ctx.close()
+        ts, es = np.asarray(ts), np.asarray(es) / n
+        slope = float(np.polyfit(ts / 1000.0, es, 1)[0])
+        out[mode] = {"max_dF_vs_oracle_eV_A": dF, "ms_per_step": ms / (steps - steps % every),
+                     "atom_steps_per_s": n * (steps - steps % every) / (ms / 1000.0),
+                     "nve_drift_eV_per_atom_per_ps": slope, "nve_max_dev_eV_per_atom": float(np.abs(es - es[0]).max())}
+    return {"workload": "Cu FCC (001) slab 100x100x50 cells, 2,000,000 atoms, ACE hemisphere r=82.6 A (5 %), "
+                        "thermal snapshot sigma 0.066 A, 300 K velocities, indenter off (NVE), dt=1 fs",
+            "sampled_atoms": int(len(cen)), "oracle_s": oracle_s, "steps": steps, "energy_every": every,
+            "modes": out}
+
+
 def ace_kernel_roofline(prof, n_steps, c, pk, peak_src, ctx_atoms_in_rc, fma_peak=None, alone_ms=None):
     """Roofline of the dominant kernel, k_ace_contract (products, densities and dE/dA of the
     compacted atoms); its CUDA-event time comes from the library's per-stage events.  The
@@ -418,8 +524,12 @@ def main():
     ap_.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap_.add_argument("--no-cpu-baseline", action="store_true")
     ap_.add_argument("--variants", default="ace,eam", help="extra single-potential runs (comma list or 'none')")
-    ap_.add_argument("--serve-requests", type=int, default=300,
+    ap_.add_argument("--serve-requests", type=int, default=2000,
                      help="requests in the serving run reported beside the metric (0: skip)")
+    ap_.add_argument("--precision-steps", type=int, default=500,
+                     help="NVE steps per precision mode of the 2M-atom Cu slab leg reported beside the metric (0: skip)")
+    ap_.add_argument("--no-oracle-check", action="store_true",
+                     help="skip the sampled oracle check of the timed context's final state")
     ap_.add_argument("--serve-chunk", type=int, default=8, help="MD steps per request per scheduling pass")
     ap_.add_argument("--serve-active", type=int, default=64, help="cap on concurrently active requests")
     ap_.add_argument("--mode", default="ap", choices=["ap", "serve", "precision", "autograd"],
@@ -477,6 +587,7 @@ def main():
     launches = ctx.launch_count - l0
     ctx.check()
     rep = ctx.energy()
+    validity = None if args.no_oracle_check or rank != 0 else oracle_check(torch, ctx, c)
     dev_s = max_over_ranks(torch, sum(ms) / 1000.0, "cuda")
     value = aggregate_rate(ws, n, args.steps, dev_s)
     clocks = clk.summary()
@@ -527,6 +638,7 @@ def main():
 
     serving = (serving_bench(torch, args.serve_requests, chunk=args.serve_chunk, max_active=args.serve_active)
                if args.serve_requests > 0 else None)
+    precision = precision_leg(torch, ap, steps=args.precision_steps) if args.precision_steps > 0 and rank == 0 else None
     csp = csp_timing(torch, ap, c)
 
     if rank != 0:
@@ -545,6 +657,11 @@ def main():
                              "(about 2.5 us per stage); in the timed steps only the ACE contraction is bracketed" % k_stage,
             "gpu_launches": launches, "clocks": clocks, "e2e": e2e, "roofline": roof,
             "wall_s_timed_region": wall}
+    if validity is not None:
+        line["max_dF_vs_oracle"] = validity["max_dF_eV_A"]
+        line["oracle_check"] = validity
+    if precision is not None:
+        line["precision"] = precision
     if serving is not None:
         line["serving"] = serving
     csp["per_step_share_at_every_step"] = csp["csp_ms"] / line["ms_per_step"]

@@ -44,9 +44,14 @@ typedef enum {
     AP_ERR_OOM = -2,       /* device or host allocation failed                       */
     AP_ERR_CUDA = -3,      /* a CUDA runtime call failed (text in ap_last_error)     */
     AP_ERR_DOMAIN = -4,    /* phi2 <= 1e-3, rho < 0 or a non-finite value; atom index in ap_last_error */
-    AP_ERR_CAPACITY = -5,  /* neighbour capacity exceeded; the next call rebuilds with a larger one */
+    AP_ERR_CAPACITY = -5,  /* neighbour-list capacity exceeded: the call that reports it grows the
+                              list (AP_ERR_OOM instead when that allocation fails) and the next
+                              evaluation rebuilds it; the evaluation that overflowed is discarded */
     AP_ERR_TIMEOUT = -6,   /* reserved for bounded waits                             */
-    AP_ERR_STATE = -7      /* call not valid in the current state                   */
+    AP_ERR_STATE = -7,     /* call not valid in the current state                   */
+    AP_ERR_LIMIT = -8      /* a fixed limit of this build was exceeded: more than 128 neighbours
+                              within the ACE cutoff of one atom (index in ap_last_error).  Sticky
+                              and not retried: the structure is outside what the build evaluates */
 } ap_status;
 
 /* Precision of the atomic-base contraction A_nlm = sum_j g_n(r_ij) Y_lm(rhat_ij). */
@@ -246,6 +251,20 @@ typedef struct {
 ap_status ap_csp_accumulate(ap_ctx* ctx, const ap_csp_params* p, float* d_csp);
 ap_status ap_csp_update_weights(ap_ctx* ctx, const ap_csp_params* p, int* n_seeds);
 
+/* Indentation load history kept on the device (Sec. 3.1, Eq. P_ind).  With capacity > 0,
+ * every later MD step of ap_step adds the load of its force evaluation, sum_i F_ind,i . dir,
+ * to a device ring of `capacity` (time, load) entries, without any synchronisation; the
+ * per-atom terms are summed as 64-bit fixed point (2^-32 eV/A), so the history is the same
+ * bits in every run.  capacity = 0 stops recording and frees the ring.  Synchronises.
+ * AP_ERR_STATE for a context without an indenter, AP_ERR_OOM when the ring cannot be
+ * allocated. */
+ap_status ap_record_load(ap_ctx* ctx, int capacity);
+/* Host copy of the recorded load history: the most recent min(max, steps recorded,
+ * capacity) entries, oldest first, t_fs[k] the time after the step (fs) and load[k] its
+ * load (eV/A); *count receives how many were written.  Synchronises (one read-back of the
+ * ring).  AP_ERR_STATE when no history is recorded. */
+ap_status ap_load_history(ap_ctx* ctx, double* t_fs, double* load, int max, int* count);
+
 /* Totals of the last force evaluation; d_e_atom (device, n FP64, nullable) receives
  * the per-atom energies E_i + V_ind(r_i).  Synchronises; returns sticky device errors. */
 ap_status ap_energy(ap_ctx* ctx, ap_report* out, double* d_e_atom);
@@ -298,7 +317,14 @@ size_t ap_footprint_bytes(const ap_potential* pot, int n_atoms, double ace_fract
 /* Device bytes ctx holds right now (its stream-ordered allocations, including any
  * capacity growth); 0 for NULL. */
 size_t ap_memory_bytes(const ap_ctx* ctx);
-/* Text of the last error of ctx (or of the last failed ap_init when ctx is NULL). */
+/* Test hook for the failure paths: the next `count` device allocations of this library
+ * (context arenas, capacity growth) fail as if the device were out of memory, so the calls
+ * that make them return AP_ERR_OOM.  count <= 0 clears pending failures.  Host-side only: no
+ * device state is touched and nothing is launched. */
+void ap_inject_alloc_failures(int count);
+
+/* Text of the last error of ctx, or with ctx NULL of the last failed ap_init or
+ * ap_ace_forces_noalloc call of this thread. */
 const char* ap_last_error(const ap_ctx* ctx);
 void ap_destroy(ap_ctx* ctx);
 int ap_version(void);
@@ -315,22 +341,24 @@ ap_status ap_probe_fp32_peak(int iters, double* tflops, double* ms_out);
  * allocations of their own - a program or plugin whose GPU memory is owned entirely by
  * another allocator (a framework's caching pool that must account for every byte), or a
  * time-critical loop that rules out the latency and the failure modes of cudaMalloc once
- * it is running.  It evaluates E = sum_i w_i E_i^ACE (Eq. energy_ace, the same kernel
- * arithmetic as the context path) and F_k = -dE/dr_k for up to 65,536 atoms, and calls no
- * cudaMalloc, cudaFree or other allocating routine.
+ * it is running.  It evaluates E = sum_i w_i E_i^ACE (Eq. energy_ace, with the frozen
+ * weights w_i) and F_k = -dE/dr_k for up to 65,536 atoms, and calls no cudaMalloc, cudaFree
+ * or other allocating routine.
  *   d_nbr_idx  device, n_atoms x max_nb ints: neighbour atom index j of atom i, -1 = unused
  *   d_rvec     device, n_atoms x max_nb x 3 FP32: r_j (image) - r_i for those slots
  *   d_w        device, n_atoms FP32 weights w_i, or NULL for w = 1 (atoms with w = 0 are skipped)
- *   d_force    device, n_atoms x 3 FP32 output
- *   d_energy   device, n_atoms FP64 output: E_i^ACE (0 where w = 0, NaN where phi2 <= 1e-3)
- * Limits: n_atoms <= 65536, max_nb <= 128, else AP_ERR_ARG.  Scratch (the coefficient
- * tables and 64-bit force accumulators, ~1.6 MB) is one file-scope device array that every
- * GPU loading the library holds until the process exits; the first call on a device looks
- * up its address and uploads constant tables, so make that first call before any stream
- * capture.  Every call shares the array and the call clears the accumulators it uses
- * before its kernels run; calls that overlap on the GPU (other streams, other threads)
- * race on it.  Asynchronous on `stream`; errors of the launch are returned, a domain error
- * shows as a NaN energy. */
+ *   d_force    device, n_atoms x 3 FP32 output: the weighted forces F_k above
+ *   d_energy   device, n_atoms FP64 output: the unweighted E_i^ACE (0 where w = 0, NaN
+ *              where phi2 <= 1e-3)
+ * Limits: n_atoms <= 65536, max_nb <= 128, ace_precision AP_ACE_FP32, else AP_ERR_ARG; the
+ * reason is in ap_last_error(NULL).  Scratch (the coefficient tables and 64-bit force
+ * accumulators, ~1.6 MB) is one file-scope device array that every GPU loading the library
+ * holds until the process exits.  The first call on a device looks up its address and
+ * uploads constant tables, and a call whose potential differs from the previous call's on
+ * that device uploads its coefficient tables; make those calls before any stream capture.
+ * Every call shares the array and clears the accumulators it uses before its kernels run;
+ * calls that overlap on the GPU (other streams, other threads) race on it.  Asynchronous on
+ * `stream`; errors of the launch are returned, a domain error shows as a NaN energy. */
 ap_status ap_ace_forces_noalloc(const ap_potential* pot, int n_atoms, int max_nb, const int* d_nbr_idx,
                                 const float* d_rvec, const float* d_w, float* d_force, double* d_energy,
                                 void* stream);

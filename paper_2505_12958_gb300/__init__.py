@@ -259,6 +259,25 @@ class APContext:
         self._chk(self._L.ap_csp_update_weights(self._h, C.byref(p), C.byref(ns)))
         return ns.value
 
+    def record_load(self, capacity):
+        """Keep the load of every later MD step in a device ring of `capacity` entries
+        (ap_record_load); 0 stops."""
+        self._chk(self._L.ap_record_load(self._h, int(capacity)))
+        self._load_cap = int(capacity)
+
+    def load_history(self, max_entries=None):
+        """(time_fs, load) arrays of the recorded steps, oldest first (ap_load_history; one
+        synchronising read-back)."""
+        cap = getattr(self, "_load_cap", 0)
+        if max_entries is not None:
+            cap = min(cap, int(max_entries))
+        t = np.empty(cap)
+        p = np.empty(cap)
+        cnt = C.c_int()
+        self._chk(self._L.ap_load_history(self._h, t.ctypes.data_as(_capi.PD), p.ctypes.data_as(_capi.PD), cap,
+                                          C.byref(cnt)))
+        return t[:cnt.value].copy(), p[:cnt.value].copy()
+
     def memory_bytes(self):
         """Device bytes this context holds (ap_memory_bytes)."""
         return int(self._L.ap_memory_bytes(self._h))

@@ -12,8 +12,9 @@ PD, PF, PI, PLL = C.POINTER(C.c_double), C.POINTER(C.c_float), C.POINTER(C.c_int
 VP = C.c_void_p
 
 AP_OK, AP_ERR_ARG, AP_ERR_OOM, AP_ERR_CUDA, AP_ERR_DOMAIN, AP_ERR_CAPACITY, AP_ERR_TIMEOUT, AP_ERR_STATE = 0, -1, -2, -3, -4, -5, -6, -7
+AP_ERR_LIMIT = -8
 STATUS = {0: "AP_OK", -1: "AP_ERR_ARG", -2: "AP_ERR_OOM", -3: "AP_ERR_CUDA", -4: "AP_ERR_DOMAIN",
-          -5: "AP_ERR_CAPACITY", -6: "AP_ERR_TIMEOUT", -7: "AP_ERR_STATE"}
+          -5: "AP_ERR_CAPACITY", -6: "AP_ERR_TIMEOUT", -7: "AP_ERR_STATE", -8: "AP_ERR_LIMIT"}
 PRECISION = {"fp32": 0, "tf32x3": 1, "bf16": 2, "fp16": 3, "fp64": 4}
 REGION = {None: 0, "none": 0, "sphere": 1, "explicit": 2, "const": 3}
 STAGES = ["neighbor", "prepare", "eam_density", "eam_force", "ace", "blend", "integrate", "ace_basis", "ace_force"]
@@ -97,6 +98,9 @@ def lib():
         "ap_neighbor_info": (I, [VP, PI, PLL]),
         "ap_footprint_bytes": (SZ, [P(Potential), I, D]),
         "ap_last_error": (C.c_char_p, [VP]),
+        "ap_inject_alloc_failures": (None, [I]),
+        "ap_record_load": (I, [VP, I]),
+        "ap_load_history": (I, [VP, PD, PD, I, PI]),
         "ap_destroy": (None, [VP]),
         "ap_version": (I, []),
         "ap_ace_forces_noalloc": (I, [P(Potential), I, I, VP, VP, VP, VP, VP, VP]),

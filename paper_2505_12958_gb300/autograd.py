@@ -8,6 +8,9 @@ evaluation, because the force kernels already produced the adjoint:
     dE/dx_i   = -F'_i (I + eps)           (F' the forces of the strained configuration)
     dE/deps   = -W' (I + eps)^-T          (W' its virial, -sum r_ij (x) dE_i/dr_ij)
 
+The energy is returned in FP64 whatever the input dtype (it is an FP64 reduction of the
+per-atom energies on the device); the gradients come back in the dtypes of the inputs.
+
 The strain derivative treats w as fixed per atom, so contexts used with a strain must have a
 constant or explicit weight and no indenter (position-dependent external fields are not part
 of the homogeneous-deformation identity).
@@ -38,7 +41,7 @@ class _APEnergy(torch.autograd.Function):
         W = _virial_matrix(rep["virial"], dev)
         fctx.save_for_backward(forces, Fm, W)
         fctx.dtypes = (positions.dtype, strain.dtype)
-        return torch.tensor(rep["e_total"], dtype=positions.dtype, device=dev)
+        return torch.tensor(rep["e_total"], dtype=torch.float64, device=dev)
 
     @staticmethod
     def backward(fctx, gE):

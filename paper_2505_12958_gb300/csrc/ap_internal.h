@@ -63,6 +63,25 @@ struct AceDev {
     float c1_0, c2_0, nref_inv, rc;
 };
 
+// Coefficient tables of the tensor-core contraction.  The five (0, l, l) triples, whose
+// Gaunt coefficients are delta_{m2 m3} G_l (G_l = 1/sqrt(4 pi)), are stored as c0ll[p][l]
+// [(n2, n3)][n1] = G_l C3[n1, n2, n3] for the two-factor pass.  For the other nine triples
+// (t = 5 .. 13) and density p the coefficients form a 64 x 8 matrix C[q = n1 * 8 + n2][n3];
+// for the l1 = l2 triples the (n1 <= n2) coefficients are spread evenly over both orders
+// (n1, n2) and (n2, n1), whose product factors are equal.  Each entry is split into two
+// TF32 numbers hi + lo (13 low mantissa bits zero) for 3xTF32 products, and n3 is stored at
+// position n3 ^ (4 ((q >> 2) & 1)) so that the kernel's two fragment reads of the matrix
+// (as C and as its transpose) are free of shared-memory bank conflicts.
+constexpr int kNT3 = 9;             // l-triples on tensor cores
+constexpr int kTcTriple0 = 5;       // ... t = 5 .. 13
+struct alignas(16) AceTc {
+    float c3[2][2][kNT3][64][8];    // [hi/lo][density][t - 5][q][n3 (swizzled)]
+    float c0ll[2][5][64][8];        // [density][l][n2 * 8 + n3][n1]
+    float c2[2][5][64];             // as AceDev
+    float c1[2][8];
+    float c1_0, c2_0, nref_inv, rc;
+};
+
 // Cell grid: cells are the parallelepipeds of the box divided n_d times along each edge;
 // an atom's FP32 position is stored relative to its cell's origin, and a neighbour in
 // the cell offset o (per edge, -S..S) is at x_rel_j + D[code(o)] - x_rel_i.
@@ -105,6 +124,7 @@ constexpr int kNbrShift = 25;               // neighbour entry = j | code << 25
 constexpr int kNbrMask = (1 << kNbrShift) - 1;
 constexpr int kMaxAtoms = (1 << kNbrShift) - 1;
 constexpr double kFixScale = 1099511627776.0;   // 2^40: fixed-point scale of ACE force sums
+constexpr double kLoadScale = 4294967296.0;      // 2^32: fixed-point scale of the load history
 constexpr double kFtm = 0.0096485332;           // 1 eV/(Angstrom amu) in Angstrom/fs^2
 constexpr int kAceNbrCap = 128;                 // neighbours within the ACE cutoff per atom
 constexpr int kRedBlock = 256;
@@ -121,6 +141,7 @@ struct Ctx {
     bool energy_fresh = false;                           // energy pass done for the last forces
     AceDev* ace_h = nullptr;
     AceDev* ace_d = nullptr;
+    AceTc* ace_tc_d = nullptr;                           // tensor-core contraction tables
     GridDev grid{};
     float4* D = nullptr;                                 // cell-offset vectors, FP32
     float4* Dlo = nullptr;                               // their FP32 residuals (o . cellvec - D)
@@ -168,6 +189,10 @@ struct Ctx {
     long long lv_base = 0;                               // step count at ap_set_thermostat
     int lv_zero_every = 0;
     long long* d_step = nullptr;                         // device step counter (advanced by k_kick_drift)
+    long long* load_ring = nullptr;                      // [load_cap] load of step k in slot k % load_cap (2^-32 eV/A)
+    double* load_ring_t = nullptr;                       // [load_cap] time of that step (fs)
+    int load_cap = 0;                                    // 0: no load history is recorded
+    long long load_step0 = 0;                            // step count when recording started
     double* com = nullptr;                               // [4 nred + 4] momentum-zeroing partials and result
     double* pos_stage = nullptr;                         // n x 3 host-transfer staging
     float* f_stage = nullptr;                            // n x 3 host-transfer staging
@@ -217,6 +242,7 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 
 static_assert(sizeof(EamDev) % 16 == 0, "EamDev is staged in 16-byte words");
 static_assert(sizeof(AceDev) % 16 == 0, "AceDev is staged in 16-byte words");
+static_assert(sizeof(AceTc) % 16 == 0, "AceTc is staged in 16-byte words");
 
 // kernel launchers (one per stage); each returns the number of kernels launched
 int launch_rebuild(Ctx& c, cudaStream_t s);          // wrap, bin, scan, scatter, sort (skip when no rebuild)
@@ -227,7 +253,9 @@ int launch_eam_force(Ctx& c, cudaStream_t s);
 int launch_ace_basis(Ctx& c, cudaStream_t s);        // A_nlm of the compacted atoms
 int launch_ace(Ctx& c, cudaStream_t s);              // products, densities, dE/dA
 int launch_ace_force(Ctx& c, cudaStream_t s);        // pair forces and scatter
-int launch_blend(Ctx& c, cudaStream_t s, float* out_aos, double kick_dt = 0.0);   // kick_dt > 0: fused second half kick
+// kick_dt > 0: fused second half kick; in_step: the evaluation of an MD step (adds its load to
+// the load history when one is recorded)
+int launch_blend(Ctx& c, cudaStream_t s, float* out_aos, double kick_dt = 0.0, bool in_step = false);
 int launch_energy(Ctx& c, cudaStream_t s, bool virial = true);   // compensated EAM energies + energy blend (+ virial)
 int launch_reduce(Ctx& c, cudaStream_t s, int with_kinetic);
 int launch_kick_drift(Ctx& c, cudaStream_t s, double dt, int first_half);
@@ -243,11 +271,13 @@ int launch_check(Ctx& c, cudaStream_t s);
 // host-side tables (tables.cpp)
 int build_eam_tables(const ap_potential& p, EamDev& out, std::string& err);
 int build_ace_tables(const ap_potential& p, AceDev& out, std::string& err);
+void build_ace_tc(const AceDev& in, AceTc& out);     // split, symmetrised, swizzled copy of in
 double gaunt_real_racah(int l1, int m1, int l2, int m2, int l3, int m3);
 int gaunt_values(float* out, std::string& err);      // kNG entries in pattern order
 // which = 0: Phi, 1: zeta from the FP64 segments; 2: Phi, 3: zeta from the FP32 device
 // table through the kernels' own segment lookup (eam_table.h)
 int eam_table_eval(const ap_potential& p, int which, double r, double* f, double* df);
 void upload_gaunt(const float* g);                   // kernels_ace.cu
+void set_global_error(const std::string& m);         // capi.cu: the text of ap_last_error(NULL)
 
 }  // namespace ap

@@ -3,9 +3,11 @@
 // synchronisation: the neighbour rebuild decision, the ACE atom count and all error
 // conditions live in device memory.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -58,9 +60,29 @@ namespace {
 
 thread_local std::string g_init_err;
 
+}  // namespace
+
+namespace ap {
+// the text ap_last_error(NULL) returns on this thread: the last failed ap_init or
+// ap_ace_forces_noalloc
+void set_global_error(const std::string& m) { g_init_err = m; }
+}  // namespace ap
+
+namespace {
+
 ap_status set_err(ap::Ctx& c, ap_status s, const std::string& m) {
     c.err = m;
     return s;
+}
+
+// pending injected allocation failures (ap_inject_alloc_failures)
+std::atomic<int> g_fail_allocs{0};
+
+bool injected_alloc_failure() {
+    int v = g_fail_allocs.load();
+    while (v > 0)
+        if (g_fail_allocs.compare_exchange_weak(v, v - 1)) return true;
+    return false;
 }
 
 ap_status cuda_check(ap::Ctx& c, cudaError_t e, const char* what) {
@@ -258,6 +280,10 @@ void pool_setup(int dev) {
 template <class T>
 ap_status dalloc(ap::Ctx& c, T** p, size_t count) {
     if (count == 0) count = 1;
+    if (injected_alloc_failure()) {
+        *p = nullptr;
+        return cuda_check(c, cudaErrorMemoryAllocation, "cudaMallocAsync (injected failure)");
+    }
     cudaError_t e = cudaMallocAsync((void**)p, count * sizeof(T), c.stream);
     if (e != cudaSuccess) { *p = nullptr; return cuda_check(c, e, "cudaMallocAsync"); }
     c.dev_bytes += count * sizeof(T);
@@ -297,7 +323,7 @@ void free_all(ap_ctx* xc) {
                   c.vir_eam, c.vir_ace, c.acc, c.fixed, c.w_fixed, c.cell, c.cell_count, c.cell_start,
                   c.cell_atoms, c.nbr, c.nnbr, c.ace_list, c.flags, c.d_time, c.partials, c.totals, c.e_atom,
                   c.pos_stage, c.f_stage, c.csp_sum, c.csp_under, c.csp_w0, c.csp_wnew, c.csp_seeds, c.csp_nseed,
-                  c.thermo_group, c.nh_state, c.nh_partials, c.d_step, c.com};
+                  c.thermo_group, c.nh_state, c.nh_partials, c.d_step, c.com, c.load_ring, c.load_ring_t};
     for (void* p : ps) {
         const bool carved = xc->arena && (char*)p >= xc->arena && (char*)p < xc->arena + xc->arena_bytes;
         if (p && !carved) cudaFreeAsync(p, c.stream);
@@ -335,7 +361,8 @@ ap_status arena_commit(ap_ctx* xc, const ArenaPlan& plan) {
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
     size_t total = 0;
     for (const auto& it : plan.items) total += up(it.bytes);
-    cudaError_t e = cudaMallocAsync((void**)&xc->arena, total, c.stream);
+    cudaError_t e = injected_alloc_failure() ? cudaErrorMemoryAllocation
+                                             : cudaMallocAsync((void**)&xc->arena, total, c.stream);
     if (e != cudaSuccess) { xc->arena = nullptr; return cuda_check(c, e, "cudaMallocAsync"); }
     xc->arena_bytes = total;
     size_t off = 0;
@@ -379,11 +406,11 @@ void run_forces_pre(ap_ctx* xc, cudaStream_t s, bool after_drift) {
     stage(xc, AP_STAGE_ACE_BASIS, s, [&] { return ap::launch_ace_basis(c, s); });
 }
 
-void run_forces_post(ap_ctx* xc, cudaStream_t s, float* out_aos, double kick_dt) {
+void run_forces_post(ap_ctx* xc, cudaStream_t s, float* out_aos, double kick_dt, bool in_step) {
     ap::Ctx& c = xc->c;
     stage(xc, AP_STAGE_ACE_FORCE, s, [&] { return ap::launch_ace_force(c, s); });
     if (c.prof != 1) cudaStreamWaitEvent(s, xc->join_ev, 0);      // join the EAM branch
-    stage(xc, AP_STAGE_BLEND, s, [&] { return ap::launch_blend(c, s, out_aos, kick_dt); });
+    stage(xc, AP_STAGE_BLEND, s, [&] { return ap::launch_blend(c, s, out_aos, kick_dt, in_step); });
     c.forces_valid = true;
     c.energy_fresh = false;
 }
@@ -391,7 +418,7 @@ void run_forces_post(ap_ctx* xc, cudaStream_t s, float* out_aos, double kick_dt)
 void run_forces(ap_ctx* xc, cudaStream_t s, float* out_aos, bool after_drift = false, double kick_dt = 0.0) {
     run_forces_pre(xc, s, after_drift);
     stage(xc, AP_STAGE_ACE, s, [&] { return ap::launch_ace(xc->c, s); });
-    run_forces_post(xc, s, out_aos, kick_dt);
+    run_forces_post(xc, s, out_aos, kick_dt, after_drift);
 }
 
 // accurate energies of the last force evaluation, once
@@ -409,21 +436,36 @@ ap_status read_flags(ap::Ctx& c, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_check(c, e, "synchronise");
     int err = c.h_flags[ap::kFlagErr];
+    if (err & ap::kErrAceCapacity) {
+        // checked first: the skipped atoms' ACE terms are not evaluated, so a domain error
+        // that comes with it may be a consequence
+        c.forces_valid = false;
+        return set_err(c, AP_ERR_LIMIT, "more than " + std::to_string(ap::kAceNbrCap) +
+                                            " neighbours within the ACE cutoff at atom " +
+                                            std::to_string(c.h_flags[ap::kFlagBad]));
+    }
     if (err & ap::kErrDomain)
         return set_err(c, AP_ERR_DOMAIN, "domain error (phi2 <= 1e-3, rho < 0 or non-finite) at atom " + std::to_string(c.h_flags[ap::kFlagBad]));
-    if (err & (ap::kErrCapacity | ap::kErrAceCapacity)) {
+    if (err & ap::kErrCapacity) {
         // grow the list capacity; the next evaluation rebuilds
         int need = c.h_flags[ap::kFlagMaxNbr];
         std::string m = "neighbour capacity exceeded (" + std::to_string(need) + " > " + std::to_string(c.cap) + ")";
-        if (err & ap::kErrCapacity) {
+        ap_status grown = AP_ERR_CAPACITY;
+        {
             int cap = ((int)(need * 1.25) + 8 + 3) & ~3;
             int* nb = nullptr;
-            if (cudaMallocAsync((void**)&nb, (size_t)cap * c.n * sizeof(int), c.stream) == cudaSuccess) {
+            cudaError_t ea = injected_alloc_failure() ? cudaErrorMemoryAllocation
+                                                      : cudaMallocAsync((void**)&nb, (size_t)cap * c.n * sizeof(int), c.stream);
+            if (ea == cudaSuccess) {
                 cudaFreeAsync(c.nbr, c.stream);
                 c.dev_bytes += ((size_t)cap - (size_t)c.cap) * c.n * sizeof(int);
                 c.nbr = nb;
                 c.cap = cap;
                 c.layout_gen += 1;
+            } else {
+                cudaGetLastError();
+                grown = AP_ERR_OOM;
+                m += "; growing the list failed (out of device memory)";
             }
         }
         int zero[2] = {1, 0};
@@ -431,7 +473,7 @@ ap_status read_flags(ap::Ctx& c, cudaStream_t s) {
         cudaMemcpyAsync(&c.flags[ap::kFlagErr], &zero[1], sizeof(int), cudaMemcpyHostToDevice, s);
         cudaStreamSynchronize(s);
         c.forces_valid = false;
-        return set_err(c, AP_ERR_CAPACITY, m);
+        return set_err(c, grown, m);
     }
     return AP_OK;
 }
@@ -461,7 +503,7 @@ size_t ap_footprint_bytes(const ap_potential* pot, int n_atoms, double ace_fract
                             4 + 4 + 4 + 4 + 8 + 3 * 8 + 3 * 4 + cap * 4;
     const size_t cells = 2 * sizeof(int) * ((size_t)n_atoms + 1);   // cell count/start (<= 1 per atom)
     const size_t nred = (size_t)(n_atoms + ap::kRedBlock - 1) / ap::kRedBlock + 1;
-    return (size_t)n_atoms * per_atom + cells + nred * 10 * 8 + 2 * 125 * 16 + sizeof(ap::AceDev) +
+    return (size_t)n_atoms * per_atom + cells + nred * 10 * 8 + 2 * 125 * 16 + sizeof(ap::AceDev) + sizeof(ap::AceTc) + 512 +
            sizeof(ap::EamDev) + (1u << 16);
 }
 
@@ -555,7 +597,7 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
     c.nred = (n + ap::kRedBlock - 1) / ap::kRedBlock;
     {
         ArenaPlan plan;
-        plan.add(&c.eam_d, 1); plan.add(&c.ace_d, 1); plan.add(&c.D, 125); plan.add(&c.Dlo, 125);
+        plan.add(&c.eam_d, 1); plan.add(&c.ace_d, 1); plan.add(&c.ace_tc_d, 1); plan.add(&c.D, 125); plan.add(&c.Dlo, 125);
         plan.add(&c.pos_lo, N); plan.add(&c.x, 3 * N); plan.add(&c.v, 3 * N); plan.add(&c.xb, 3 * N);
         plan.add(&c.f, 3 * N); plan.add(&c.pos4, N); plan.add(&c.uxi, N); plan.add(&c.w, N);
         plan.add(&c.e_emb, N); plan.add(&c.e_eam, N); plan.add(&c.e_ace, N);
@@ -589,6 +631,10 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
     };
     cp(c.eam_d, &c.eam_h, sizeof(ap::EamDev));
     cp(c.ace_d, c.ace_h, sizeof(ap::AceDev));
+    std::unique_ptr<ap::AceTc> tc(new (std::nothrow) ap::AceTc());
+    if (!tc) { c.err = "host allocation"; return fail(AP_ERR_OOM); }
+    ap::build_ace_tc(*c.ace_h, *tc);
+    cp(c.ace_tc_d, tc.get(), sizeof(ap::AceTc));
     cp(c.D, D.data(), D.size() * sizeof(float4));
     cp(c.Dlo, Dlo.data(), Dlo.size() * sizeof(float4));
     cp(c.x, soa.data(), 3 * N * sizeof(double));
@@ -733,7 +779,7 @@ void captured_step(ap_ctx* xc, cudaStream_t s, double dt, bool timed) {
             xc->cap_err = r;
             xc->cap_where = "event record";
         }
-        run_forces_post(xc, s, nullptr, kick);
+        run_forces_post(xc, s, nullptr, kick, true);
     }
     c.launches += step_kernels(c, s, dt, 1);
 }
@@ -1137,6 +1183,59 @@ ap_status ap_neighbor_info(ap_ctx* xc, int* capacity, long long* rebuilds) {
     if (capacity) *capacity = xc->c.cap;
     if (rebuilds) *rebuilds = xc->c.h_flags[ap::kFlagRebuilds] - 1;   // the sizing pass at ap_init is not counted
     return st;
+}
+
+void ap_inject_alloc_failures(int count) { g_fail_allocs.store(count > 0 ? count : 0); }
+
+ap_status ap_record_load(ap_ctx* xc, int capacity) {
+    if (!xc || capacity < 0) return AP_ERR_ARG;
+    ap::Ctx& c = xc->c;
+    if (capacity > 0 && !c.dyn.ind_on) return set_err(c, AP_ERR_STATE, "ap_record_load: the context has no indenter");
+    cudaError_t e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "ap_record_load");
+    drop_step_graph(xc);
+    c.layout_gen += 1;                                   // the step kernels' arguments change
+    if (c.load_ring) {
+        cudaFreeAsync(c.load_ring, c.stream);
+        cudaFreeAsync(c.load_ring_t, c.stream);
+        c.dev_bytes -= (size_t)c.load_cap * (sizeof(long long) + sizeof(double));
+        c.load_ring = nullptr;
+        c.load_ring_t = nullptr;
+        c.load_cap = 0;
+    }
+    if (capacity == 0) return AP_OK;
+    ap_status st;
+    if ((st = dalloc(c, &c.load_ring, (size_t)capacity)) || (st = dalloc(c, &c.load_ring_t, (size_t)capacity))) {
+        if (c.load_ring) { cudaFreeAsync(c.load_ring, c.stream); c.dev_bytes -= (size_t)capacity * sizeof(long long); }
+        c.load_ring = nullptr;
+        return st;
+    }
+    c.load_cap = capacity;
+    c.load_step0 = c.step;
+    return AP_OK;
+}
+
+ap_status ap_load_history(ap_ctx* xc, double* t_fs, double* load, int max, int* count) {
+    if (!xc || max < 0 || (max > 0 && (!t_fs || !load)) || !count) return AP_ERR_ARG;
+    ap::Ctx& c = xc->c;
+    *count = 0;
+    if (!c.load_ring) return set_err(c, AP_ERR_STATE, "ap_load_history: no load history is recorded");
+    const long long have = std::min<long long>(c.step - c.load_step0, c.load_cap);
+    const int m = (int)std::min<long long>(have, max);
+    std::vector<long long> ring((size_t)c.load_cap);
+    std::vector<double> tt((size_t)c.load_cap);
+    cudaError_t e = cudaMemcpyAsync(ring.data(), c.load_ring, ring.size() * sizeof(long long), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tt.data(), c.load_ring_t, tt.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "ap_load_history");
+    for (int k = 0; k < m; ++k) {
+        const long long step = c.step - m + 1 + k;
+        const size_t slot = (size_t)(step % c.load_cap);
+        t_fs[k] = tt[slot];
+        load[k] = (double)ring[slot] / ap::kLoadScale;
+    }
+    *count = m;
+    return AP_OK;
 }
 
 const char* ap_last_error(const ap_ctx* xc) { return xc ? xc->c.err.c_str() : g_init_err.c_str(); }

@@ -23,6 +23,7 @@
 #include <cuda_fp16.h>
 
 #include <cstdint>
+#include <cstdlib>
 #include <mutex>
 #include <string>
 #include <utility>
@@ -1269,6 +1270,470 @@ __global__ void __launch_bounds__(256) k_ace_force(const float4* __restrict__ po
     }
 }
 
+
+// ---------------------------------------------------------------------------------
+// Tensor-core contraction.  For an l-triple t the three-factor part of phi_p is
+//     phi_p^t = sum_{q, n3, m3} C_p[q, n3] P[q, m3] A[n3, m3],
+//     P[q = (n1, n2), m3] = sum_{m1, m2} G A[n1, m1] A[n2, m2]      (Gaunt, FP32 lanes),
+// and its gradients need two contractions with the coefficient matrix C_p, which every
+// atom shares:
+//     R_p = C_p^T P     (8 x W3): phi_p^t = sum R_p . A_{l3} and the third-factor gradient
+//                                 dE/dA[n3, l3 m3] += R_1 + s R_2, s = 1 / (2 sqrt(phi2));
+//     Q   = C_1 A + C_2 (s A)   (64 x W3): the first- and second-factor gradients
+//                                 d1 += G Q A[n2], d2 += G Q A[n1]  (Gaunt, FP32 lanes).
+// Both run as mma.sync m16n8k8 TF32 with 3xTF32 splitting (hi/lo of both operands, the
+// lo*lo product dropped: relative error ~2^-21, FP32-like).  R: M = (density, n3) = 16,
+// K = q = 64, N = m3 of one atom; its accumulators for all triples with the same l3 are
+// chained, so one epilogue per l3 forms phi and the third-factor gradient.  Q: M = q, K =
+// (density, n3) = 16, N = m3.  P and Q pass between the lanes (one (n1, n2) pair each) and
+// the fragments through a per-warp staging block of rows m3, columns q.
+//
+// The five (0, l, l) triples have G = delta_{m2 m3} / sqrt(4 pi): their functions are
+// A[n1, 00] times a two-factor product, so they join the two-factor pass with per-atom
+// coefficients c2 + sum_n1 C3[n1, (n2, n3)] A[n1, 00] G (and a gradient for A[n1, 00]).
+// The other nine triples run on tensor cores.  One warp per atom, no block barriers in the
+// atom loop.
+// ---------------------------------------------------------------------------------
+constexpr int kTcWarps = 16;
+constexpr int kStRow = 68;                     // staging row stride: 8 rows fall on distinct bank quads
+
+struct TcWarpSmem {
+    float A[kNmax * kApad];     // A[n][l-block layout] (Gaunt operands)
+    float dA[kNmax * kApad];    // dE/dA, same layout
+    float At[32][8];            // A[lm][n3], n3 chunk (n3 / 4) at (n3 / 4) ^ ((lm >> 2) & 1); rows 25..31 zero
+    float St[9][kStRow];        // staging of P or Q: row m3, column q
+    float R2[kNmax][28];        // second-density third-factor gradient [n3][lm]
+};
+static_assert(sizeof(TcWarpSmem) % 16 == 0, "16-byte aligned warp regions");
+static_assert(kNT3 == 9 && kTcTriple0 == 5, "the tensor-core triples are t = 5 .. 13");
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+    hi = to_tf32(x);
+    lo = __float_as_uint(x - __uint_as_float(hi));   // the tensor core reads its top 19 bits
+}
+
+// d += (ah + al)(bh + bl) without al bl; the small terms first
+__device__ __forceinline__ void mma3(float* d, const uint32_t* ah, const uint32_t* al, uint32_t bh0, uint32_t bh1,
+                                     uint32_t bl0, uint32_t bl1) {
+    mma_tf32(d, al[0], al[1], al[2], al[3], bh0, bh1);
+    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bl0, bl1);
+    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bh0, bh1);
+}
+
+// 8 x 4 FP32 tiles (as 8 x 8 b16 matrices) from shared memory; thread t gives the row
+// address of matrix t / 8, row t % 8, and receives word t % 4 of row t / 4 of each matrix
+__device__ __forceinline__ void ldsm_x4(uint32_t* r, const float* p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t* r, const float* p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
+}
+
+// P of the lane's pairs q = lane and lane + 32 into the staging rows
+template <int T>
+__device__ __forceinline__ void tc_stage_p(TcWarpSmem& S, int lane) {
+    using R = Tri<T>;
+    const int n2 = lane & 7;
+    float A2[R::W2];
+    load_row<R::W2>(A2, S.A + n2 * kApad + R::B2);
+#pragma unroll 1
+    for (int pp = 0; pp < 2; ++pp) {
+        const int q = lane + 32 * pp, n1 = q >> 3;
+        float A1[R::W1], P[R::W3];
+        load_row<R::W1>(A1, S.A + n1 * kApad + R::B1);
+#pragma unroll
+        for (int k = 0; k < R::W3; ++k) P[k] = 0.0f;
+        all_p<T>(P, A1, A2, std::make_integer_sequence<int, R::N>{});
+#pragma unroll
+        for (int k = 0; k < R::W3; ++k) S.St[k][q] = P[k];
+    }
+}
+
+// R_p += C_p^T P: rows (density, n3), K = q over 8 steps, columns m3; even and odd steps
+// accumulate in separate chains (RA0 / RA1; RB for column 8)
+template <int T>
+__device__ __forceinline__ void tc_r_gemm(const AceTc& C, const TcWarpSmem& S, int lane, float* RA0, float* RA1,
+                                          float* RB0, float* RB1) {
+    using R = Tri<T>;
+    constexpr int U = T - kTcTriple0;
+    const int gq = lane >> 2, tq = lane & 3;
+    // ldmatrix rows of the B fragment: matrix j = lane / 8 reads row m3 = lane % 8, q chunk j
+    const float* brow = &S.St[lane & 7][4 * ((lane >> 3) & 1)];
+#pragma unroll 2
+    for (int ks = 0; ks < 8; ++ks) {
+        const int qa = 8 * ks + tq, qb = qa + 4;
+        uint32_t ah[4], al[4];
+        ah[0] = __float_as_uint(C.c3[0][0][U][qa][gq]);
+        ah[1] = __float_as_uint(C.c3[0][1][U][qa][gq]);
+        ah[2] = __float_as_uint(C.c3[0][0][U][qb][gq ^ 4]);
+        ah[3] = __float_as_uint(C.c3[0][1][U][qb][gq ^ 4]);
+        al[0] = __float_as_uint(C.c3[1][0][U][qa][gq]);
+        al[1] = __float_as_uint(C.c3[1][1][U][qa][gq]);
+        al[2] = __float_as_uint(C.c3[1][0][U][qb][gq ^ 4]);
+        al[3] = __float_as_uint(C.c3[1][1][U][qb][gq ^ 4]);
+        uint32_t b[2], bh0, bl0, bh1, bl1;
+        ldsm_x2(b, brow + 8 * ks);
+        split_tf32(__uint_as_float(b[0]), bh0, bl0);
+        split_tf32(__uint_as_float(b[1]), bh1, bl1);
+        mma3((ks & 1) ? RA1 : RA0, ah, al, bh0, bh1, bl0, bl1);
+        if constexpr (R::W3 > 8) {
+            split_tf32(gq == 0 ? S.St[8][qa] : 0.0f, bh0, bl0);
+            split_tf32(gq == 0 ? S.St[8][qb] : 0.0f, bh1, bl1);
+            mma3((ks & 1) ? RB1 : RB0, ah, al, bh0, bh1, bl0, bl1);
+        }
+    }
+}
+
+template <int T>
+__device__ __forceinline__ void tc_forward_triple(const AceTc& C, TcWarpSmem& S, int lane, float* RA0, float* RA1,
+                                                  float* RB0, float* RB1) {
+    tc_stage_p<T>(S, lane);
+    __syncwarp();
+    tc_r_gemm<T>(C, S, lane, RA0, RA1, RB0, RB1);
+    __syncwarp();
+}
+
+// the tensor-core triples of one l3: chained R accumulators, then phi and the third-factor
+// gradient (thread (g, t) holds R_1[n3 = g][m3 = 2t, 2t + 1] in RA[0..1] and R_2 in RA[2..3])
+template <int L, int... T>
+__device__ __forceinline__ void tc_forward_group(const AceTc& C, TcWarpSmem& S, int lane, float& p1, float& p2,
+                                                 std::integer_sequence<int, T...>) {
+    float RA0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, RA1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float RB0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, RB1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    (tc_forward_triple<T>(C, S, lane, RA0, RA1, RB0, RB1), ...);
+    constexpr int W = 2 * L + 1;
+    const int gq = lane >> 2, tq = lane & 3;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int m = 2 * tq + e;
+        if (m < W) {
+            const float r1 = RA0[e] + RA1[e], r2 = RA0[2 + e] + RA1[2 + e];
+            const float a = S.A[gq * kApad + lblk(L) + m];
+            p1 = fmaf(r1, a, p1);
+            p2 = fmaf(r2, a, p2);
+            S.dA[gq * kApad + lblk(L) + m] += r1;
+            S.R2[gq][L * L + m] = r2;
+        }
+    }
+    if constexpr (W > 8) {
+        if (tq == 0) {
+            const float r1 = RB0[0] + RB1[0], r2 = RB0[2] + RB1[2];
+            const float a = S.A[gq * kApad + lblk(L) + 8];
+            p1 = fmaf(r1, a, p1);
+            p2 = fmaf(r2, a, p2);
+            S.dA[gq * kApad + lblk(L) + 8] += r1;
+            S.R2[gq][L * L + 8] = r2;
+        }
+    }
+}
+
+// one m-tile of Q = C_1 A + C_2 (s A) into the staging rows
+template <int T, int NT>
+__device__ __forceinline__ void tc_q_tile(const AceTc& C, TcWarpSmem& S, int lane, int mt, const uint32_t (*bh)[2][2],
+                                          const uint32_t (*bl)[2][2]) {
+    constexpr int U = T - kTcTriple0;
+    const int gq = lane >> 2, tq = lane & 3;
+    // ldmatrix row of this thread: matrix j = lane / 8 (rows + 8 for odd j, n3 chunk j / 2)
+    const int qr = 16 * mt + (lane & 7) + 8 * ((lane >> 3) & 1);
+    const int off = 4 * ((lane >> 4) ^ ((qr >> 2) & 1));
+    uint32_t ah[2][4], al[2][4];
+    ldsm_x4(ah[0], &C.c3[0][0][U][qr][off]);
+    ldsm_x4(al[0], &C.c3[1][0][U][qr][off]);
+    ldsm_x4(ah[1], &C.c3[0][1][U][qr][off]);
+    ldsm_x4(al[1], &C.c3[1][1][U][qr][off]);
+    float D[NT][4];
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+        D[nt][0] = D[nt][1] = D[nt][2] = D[nt][3] = 0.0f;
+#pragma unroll
+        for (int p = 0; p < 2; ++p) mma3(D[nt], ah[p], al[p], bh[nt][p][0], bh[nt][p][1], bl[nt][p][0], bl[nt][p][1]);
+    }
+    // D[nt]: rows q = 16 mt + g (+8), columns m3 = 8 nt + 2t (+1)
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int q = 16 * mt + gq + 8 * r;
+        S.St[2 * tq][q] = D[0][2 * r];
+        S.St[2 * tq + 1][q] = D[0][2 * r + 1];
+        if constexpr (NT > 1) {
+            if (tq == 0) S.St[8][q] = D[1][2 * r];
+        }
+    }
+}
+
+// Q into the staging, then the first- and second-factor gradients
+template <int T>
+__device__ __forceinline__ void tc_adjoint_triple(const AceTc& C, TcWarpSmem& S, float s, int lane) {
+    using R = Tri<T>;
+    constexpr int NT = R::W3 > 8 ? 2 : 1;
+    // B fragments: B[k = n3][n = m3] = A[n3][lm = l3^2 + 8 nt + n] (first density), s times
+    // that (second); ldmatrix rows lm, chunks n3 0..3 and 4..7
+    uint32_t bh[NT][2][2], bl[NT][2][2];
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+        const int lm = R::L3 * R::L3 + 8 * nt + (lane & 7);
+        const int chunk = ((lane >> 3) & 1) ^ ((lm >> 2) & 1);
+        uint32_t b[2];
+        ldsm_x2(b, &S.At[lm][4 * chunk]);
+        const float x0 = __uint_as_float(b[0]), x1 = __uint_as_float(b[1]);
+        split_tf32(x0, bh[nt][0][0], bl[nt][0][0]);
+        split_tf32(x1, bh[nt][0][1], bl[nt][0][1]);
+        split_tf32(s * x0, bh[nt][1][0], bl[nt][1][0]);
+        split_tf32(s * x1, bh[nt][1][1], bl[nt][1][1]);
+    }
+#pragma unroll 2
+    for (int mt = 0; mt < 4; ++mt) tc_q_tile<T, NT>(C, S, lane, mt, bh, bl);
+    __syncwarp();
+    // Gaunt adjoint of the lane's pairs (n1, n2) = (lane / 8 + 4 pp, lane % 8)
+    const int n1 = lane >> 3, n2 = lane & 7;
+    float A2[R::W2], d2[R::W2];
+    load_row<R::W2>(A2, S.A + n2 * kApad + R::B2);
+#pragma unroll
+    for (int k = 0; k < R::W2; ++k) d2[k] = 0.0f;
+#pragma unroll 1
+    for (int pp = 0; pp < 2; ++pp) {
+        const int q = lane + 32 * pp, r1 = n1 + 4 * pp;
+        float A1[R::W1], d1[R::W1], Q[R::W3];
+        load_row<R::W1>(A1, S.A + r1 * kApad + R::B1);
+#pragma unroll
+        for (int k = 0; k < R::W3; ++k) Q[k] = S.St[k][q];
+#pragma unroll
+        for (int k = 0; k < R::W1; ++k) d1[k] = 0.0f;
+        all_x<T>(d1, d2, A1, A2, Q, std::make_integer_sequence<int, R::N>{});
+#pragma unroll
+        for (int k = 0; k < R::W1; ++k) {
+            float v = d1[k];
+            v += __shfl_xor_sync(0xffffffffu, v, 1);
+            v += __shfl_xor_sync(0xffffffffu, v, 2);
+            v += __shfl_xor_sync(0xffffffffu, v, 4);
+            d1[k] = v;
+        }
+        if ((lane & 7) == 0) {
+#pragma unroll
+            for (int k = 0; k < R::W1; ++k) S.dA[r1 * kApad + R::B1 + k] += d1[k];
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int k = 0; k < R::W2; ++k) {
+        float v = d2[k];
+        v += __shfl_xor_sync(0xffffffffu, v, 8);
+        v += __shfl_xor_sync(0xffffffffu, v, 16);
+        d2[k] = v;
+    }
+    if (lane < 8) {
+#pragma unroll
+        for (int k = 0; k < R::W2; ++k) S.dA[lane * kApad + R::B2 + k] += d2[k];
+    }
+    __syncwarp();
+}
+
+template <int... T>
+__device__ __forceinline__ void tc_adjoint_all(const AceTc& C, TcWarpSmem& S, float s, int lane,
+                                               std::integer_sequence<int, T...>) {
+    (tc_adjoint_triple<T>(C, S, s, lane), ...);
+}
+
+// sum_n1 c[n1] a[n1] for a 16-byte aligned row c of 8 floats
+__device__ __forceinline__ float dot8(const float* c, const float* a) {
+    const float4 u = *reinterpret_cast<const float4*>(c), v = *reinterpret_cast<const float4*>(c + 4);
+    float r = u.x * a[0];
+    r = fmaf(u.y, a[1], r);
+    r = fmaf(u.z, a[2], r);
+    r = fmaf(u.w, a[3], r);
+    r = fmaf(v.x, a[4], r);
+    r = fmaf(v.y, a[5], r);
+    r = fmaf(v.z, a[6], r);
+    return fmaf(v.w, a[7], r);
+}
+
+// stages a5/a6 core on tensor cores: phi1, phi2, E = phi1 + sqrt(phi2) and dE/dA from A,
+// one warp per compacted atom
+__global__ void __launch_bounds__(kTcWarps * 32, 1)
+k_ace_contract_tc(const AceTc* __restrict__ tab, const int* __restrict__ ace_list, int* __restrict__ flags,
+                  const float* __restrict__ Ain, float* __restrict__ dAout, float* __restrict__ e_ace) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AceTc& C = *reinterpret_cast<AceTc*>(smem_raw);
+    TcWarpSmem* WS = reinterpret_cast<TcWarpSmem*>(smem_raw + sizeof(AceTc));
+    {
+        const int4* src = reinterpret_cast<const int4*>(tab);
+        int4* dst = reinterpret_cast<int4*>(smem_raw);
+        for (int k = threadIdx.x; k < (int)(sizeof(AceTc) / 16); k += blockDim.x) dst[k] = src[k];
+        // every warp region starts at zero: the padding of A and At and the staging stay finite
+        float4* z = reinterpret_cast<float4*>(WS);
+        for (int k = threadIdx.x; k < (int)(kTcWarps * sizeof(TcWarpSmem) / 16); k += blockDim.x)
+            z[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    pdl_wait();                                            // the constant tables are staged
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    TcWarpSmem& S = WS[warp];
+    const int n_ace = flags[kFlagNAce];
+    int lam_l = 0;
+    if (lane >= 1) lam_l = 1;
+    if (lane >= 4) lam_l = 2;
+    if (lane >= 9) lam_l = 3;
+    if (lane >= 16) lam_l = 4;
+    const int lam_pad = lblk(lam_l) + (lane - lam_l * lam_l);
+    for (int a = blockIdx.x * kTcWarps + warp; a < n_ace; a += gridDim.x * kTcWarps) {
+        if (lane < kNLM) {
+            const float4* src = reinterpret_cast<const float4*>(Ain + ((size_t)a * kNLM + lane) * kNmax);
+            const float4 g0 = src[0], g1 = src[1];
+            const float v[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+#pragma unroll
+            for (int q = 0; q < kNmax; ++q) S.A[q * kApad + lam_pad] = v[q];
+            const int sw = (lane >> 2) & 1;
+            reinterpret_cast<float4*>(&S.At[lane][0])[sw] = g0;
+            reinterpret_cast<float4*>(&S.At[lane][0])[sw ^ 1] = g1;
+        }
+        for (int k = lane; k < kNmax * kApad; k += 32) S.dA[k] = 0.0f;
+        __syncwarp();
+        float a00[kNmax];
+#pragma unroll
+        for (int k = 0; k < kNmax; ++k) a00[k] = S.A[k * kApad];
+        // one- and two-factor functions, with the (0, l, l) triples folded into the latter
+        float p1 = 0.0f, p2 = 0.0f;
+        if (lane < kNmax) {
+            p1 = C.c1[0][lane] * a00[lane];
+            p2 = C.c1[1][lane] * a00[lane];
+        }
+#pragma unroll 1
+        for (int pp = 0; pp < 2; ++pp) {
+            const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
+#pragma unroll
+            for (int l = 0; l <= kLmax; ++l) {
+                float mm = 0.0f;
+#pragma unroll
+                for (int k = 0; k < 2 * l + 1; ++k)
+                    mm = fmaf(S.A[n1 * kApad + lblk(l) + k], S.A[n2 * kApad + lblk(l) + k], mm);
+                p1 = fmaf(C.c2[0][l][q] + dot8(C.c0ll[0][l][q], a00), mm, p1);
+                p2 = fmaf(C.c2[1][l][q] + dot8(C.c0ll[1][l][q], a00), mm, p2);
+            }
+        }
+        // the tensor-core triples, grouped by l3
+        tc_forward_group<2>(C, S, lane, p1, p2, std::integer_sequence<int, 5, 8>{});
+        tc_forward_group<3>(C, S, lane, p1, p2, std::integer_sequence<int, 6, 10>{});
+        tc_forward_group<4>(C, S, lane, p1, p2, std::integer_sequence<int, 7, 9, 11, 12, 13>{});
+        __syncwarp();                                      // the epilogues' dA and R2 are visible
+        p1 = warp_sum(p1);
+        p2 = warp_sum(p2);
+        const bool ok = C.c2_0 + p2 > 1e-3f && p1 == p1;
+        const float sq = ok ? sqrtf(C.c2_0 + p2) : 0.0f;
+        const float s = ok ? 0.5f / sq : 0.0f;
+        // adjoint: one- and two-factor functions (with the folded triples and their A[n1, 00]
+        // gradient g00), the second density's third-factor part
+        if (lane < kNmax) S.dA[lane * kApad] += fmaf(s, C.c1[1][lane], C.c1[0][lane]);
+        __syncwarp();
+        float g00[kNmax];
+#pragma unroll
+        for (int k = 0; k < kNmax; ++k) g00[k] = 0.0f;
+#pragma unroll
+        for (int l = 0; l <= kLmax; ++l) {
+            constexpr int WM = 9;
+            float d2[WM];
+#pragma unroll
+            for (int k = 0; k < WM; ++k) d2[k] = 0.0f;
+#pragma unroll 1
+            for (int pp = 0; pp < 2; ++pp) {
+                const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
+                float cs[kNmax];
+                {
+                    const float* c0 = C.c0ll[0][l][q];
+                    const float* c1 = C.c0ll[1][l][q];
+                    const float4 u0 = *reinterpret_cast<const float4*>(c0), u1 = *reinterpret_cast<const float4*>(c0 + 4);
+                    const float4 v0 = *reinterpret_cast<const float4*>(c1), v1 = *reinterpret_cast<const float4*>(c1 + 4);
+                    cs[0] = fmaf(s, v0.x, u0.x); cs[1] = fmaf(s, v0.y, u0.y); cs[2] = fmaf(s, v0.z, u0.z);
+                    cs[3] = fmaf(s, v0.w, u0.w); cs[4] = fmaf(s, v1.x, u1.x); cs[5] = fmaf(s, v1.y, u1.y);
+                    cs[6] = fmaf(s, v1.z, u1.z); cs[7] = fmaf(s, v1.w, u1.w);
+                }
+                float ct = fmaf(s, C.c2[1][l][q], C.c2[0][l][q]);
+                float mm = 0.0f;
+                float d1[WM];
+#pragma unroll
+                for (int k = 0; k < 2 * l + 1; ++k) {
+                    const float a1 = S.A[n1 * kApad + lblk(l) + k], a2 = S.A[n2 * kApad + lblk(l) + k];
+                    mm = fmaf(a1, a2, mm);
+                }
+#pragma unroll
+                for (int k = 0; k < kNmax; ++k) {
+                    ct = fmaf(cs[k], a00[k], ct);
+                    g00[k] = fmaf(cs[k], mm, g00[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < 2 * l + 1; ++k) {
+                    const float a1 = S.A[n1 * kApad + lblk(l) + k], a2 = S.A[n2 * kApad + lblk(l) + k];
+                    d1[k] = ct * a2;
+                    d2[k] = fmaf(ct, a1, d2[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < 2 * l + 1; ++k) {
+                    float v = d1[k];
+                    v += __shfl_xor_sync(0xffffffffu, v, 1);
+                    v += __shfl_xor_sync(0xffffffffu, v, 2);
+                    v += __shfl_xor_sync(0xffffffffu, v, 4);
+                    d1[k] = v;
+                }
+                if ((lane & 7) == 0) {
+#pragma unroll
+                    for (int k = 0; k < 2 * l + 1; ++k) S.dA[n1 * kApad + lblk(l) + k] += d1[k];
+                }
+                __syncwarp();
+            }
+#pragma unroll
+            for (int k = 0; k < 2 * l + 1; ++k) {
+                float v = d2[k];
+                v += __shfl_xor_sync(0xffffffffu, v, 8);
+                v += __shfl_xor_sync(0xffffffffu, v, 16);
+                d2[k] = v;
+            }
+            if (lane < 8) {
+#pragma unroll
+                for (int k = 0; k < 2 * l + 1; ++k) S.dA[lane * kApad + lblk(l) + k] += d2[k];
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int k = 0; k < kNmax; ++k) g00[k] = warp_sum(g00[k]);
+        if (lane < kNmax) {
+            float g = g00[0];
+#pragma unroll
+            for (int k = 1; k < kNmax; ++k) g = lane == k ? g00[k] : g;
+            S.dA[lane * kApad] += g;
+        }
+        for (int e = lane; e < kNmax * 21; e += 32) {
+            // lm = 4 .. 24: l3 = 2, 3, 4 of the tensor-core triples
+            const int n3 = e / 21, lm = 4 + (e - n3 * 21);
+            const int l = lm < 9 ? 2 : (lm < 16 ? 3 : 4);
+            S.dA[n3 * kApad + lblk(l) + (lm - l * l)] += s * S.R2[n3][lm];
+        }
+        __syncwarp();
+        tc_adjoint_all(C, S, s, lane, std::integer_sequence<int, 5, 6, 7, 8, 9, 10, 11, 12, 13>{});
+        const int i = ace_list[a];
+        if (!ok) {
+            if (lane == 0) { atomicOr(&flags[kFlagErr], kErrDomain); flags[kFlagBad] = i; e_ace[i] = __int_as_float(0x7fc00000); }
+            if (lane < kNLM) {
+                float4* o = reinterpret_cast<float4*>(dAout + ((size_t)a * kNLM + lane) * kNmax);
+                o[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+                o[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        } else {
+            if (lane < kNLM) {
+                float v[kNmax];
+#pragma unroll
+                for (int q = 0; q < kNmax; ++q) v[q] = S.dA[q * kApad + lam_pad];
+                float4* o = reinterpret_cast<float4*>(dAout + ((size_t)a * kNLM + lane) * kNmax);
+                o[0] = make_float4(v[0], v[1], v[2], v[3]);
+                o[1] = make_float4(v[4], v[5], v[6], v[7]);
+            }
+            if (lane == 0) e_ace[i] = p1 + sq;
+        }
+        __syncwarp();
+    }
+}
+
 }  // namespace
 
 size_t ace_smem_bytes() { return sizeof(AceDev) + 128 * sizeof(float4) + kWarps * sizeof(WarpSmem); }
@@ -1314,16 +1779,27 @@ int launch_ace_basis(Ctx& c, cudaStream_t s) {
     return 1;
 }
 
+size_t ace_tc_smem_bytes() { return sizeof(AceTc) + kTcWarps * sizeof(TcWarpSmem); }
+
 int launch_ace(Ctx& c, cudaStream_t s) {
     static int configured = -1;
+    static const bool fp32_lanes = [] {
+        const char* e = getenv("AP_CONTRACT");
+        return !(e && std::string(e) == "tc");
+    }();
     if (configured != c.dev) {
         cudaFuncSetAttribute(k_ace_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ace_contract_smem_bytes());
+        cudaFuncSetAttribute(k_ace_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ace_tc_smem_bytes());
         configured = c.dev;
     }
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c.dev);
-    launch_pdl(k_ace_contract, nsm * 2, kContractWarps * 32, ace_contract_smem_bytes(), s, c.ace_d, c.ace_list, c.flags,
-               c.ace_A, c.ace_dA, c.e_ace);
+    if (fp32_lanes)
+        launch_pdl(k_ace_contract, nsm * 2, kContractWarps * 32, ace_contract_smem_bytes(), s, c.ace_d, c.ace_list,
+                   c.flags, c.ace_A, c.ace_dA, c.e_ace);
+    else
+        launch_pdl(k_ace_contract_tc, nsm, kTcWarps * 32, ace_tc_smem_bytes(), s, c.ace_tc_d, c.ace_list, c.flags,
+                   c.ace_A, c.ace_dA, c.e_ace);
     return 1;
 }
 
@@ -1586,9 +2062,40 @@ __global__ void k_ace_noalloc_forces(const unsigned char* __restrict__ scratch, 
 }
 
 std::mutex g_noalloc_mu;
-void* g_noalloc_dev_ptr[64] = {};
+struct NoallocDevice {
+    void* scratch = nullptr;             // device address of the scratch array on this device
+    unsigned long long key = 0;          // content hash of the potential whose tables it holds
+    bool tables = false;
+};
+NoallocDevice g_noalloc_dev[64];
 AceDev g_noalloc_tables;                 // host staging of the tables (guarded by the mutex)
-std::string g_noalloc_err;
+
+// FNV-1a over the bytes that define the ACE tables of a potential
+unsigned long long potential_key(const ap_potential& p) {
+    unsigned long long h = 1469598103934665603ull;
+    auto mix = [&](const void* d, size_t n) {
+        const unsigned char* b = static_cast<const unsigned char*>(d);
+        for (size_t k = 0; k < n; ++k) { h ^= b[k]; h *= 1099511628211ull; }
+    };
+    mix(&p.ace_rc, sizeof(double));
+    mix(&p.ace_nref, sizeof(double));
+    mix(&p.ace_nmax, sizeof(int));
+    mix(&p.ace_lmax, sizeof(int));
+    mix(&p.ace_nfunc, sizeof(int));
+    mix(&p.ace_c1_0, sizeof(double));
+    mix(&p.ace_c2_0, sizeof(double));
+    if (p.ace_nfunc > 0 && p.ace_idx && p.ace_c1 && p.ace_c2) {
+        mix(p.ace_idx, sizeof(int) * 7 * (size_t)p.ace_nfunc);
+        mix(p.ace_c1, sizeof(double) * (size_t)p.ace_nfunc);
+        mix(p.ace_c2, sizeof(double) * (size_t)p.ace_nfunc);
+    }
+    return h;
+}
+
+ap_status noalloc_fail(ap_status st, const std::string& m) {
+    set_global_error(m);
+    return st;
+}
 
 }  // namespace
 
@@ -1598,48 +2105,56 @@ extern "C" ap_status ap_ace_forces_noalloc(const ap_potential* pot, int n_atoms,
                                            const float* d_rvec, const float* d_w, float* d_force, double* d_energy,
                                            void* stream) {
     using namespace ap;
-    if (!pot || !d_nbr_idx || !d_rvec || !d_force || !d_energy || n_atoms < 1 || max_nb < 0) return AP_ERR_ARG;
-    if (n_atoms > kNoAllocMaxAtoms || max_nb > kAceNbrCap) {
-        std::lock_guard<std::mutex> g(g_noalloc_mu);
-        g_noalloc_err = "ap_ace_forces_noalloc: at most 65536 atoms and 128 neighbour slots per atom";
-        return AP_ERR_ARG;
-    }
-    if (pot->ace_precision != AP_ACE_FP32) return AP_ERR_ARG;
+    if (!pot || !d_nbr_idx || !d_rvec || !d_force || !d_energy || n_atoms < 1 || max_nb < 0)
+        return noalloc_fail(AP_ERR_ARG, "ap_ace_forces_noalloc: missing argument, n_atoms < 1 or max_nb < 0");
+    if (n_atoms > kNoAllocMaxAtoms || max_nb > kAceNbrCap)
+        return noalloc_fail(AP_ERR_ARG, "ap_ace_forces_noalloc: at most 65536 atoms and 128 neighbour slots per atom");
+    if (pot->ace_precision != AP_ACE_FP32)
+        return noalloc_fail(AP_ERR_ARG, "ap_ace_forces_noalloc: only ace_precision = AP_ACE_FP32 is built");
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return AP_ERR_CUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return noalloc_fail(AP_ERR_CUDA, "ap_ace_forces_noalloc: no current CUDA device");
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> g(g_noalloc_mu);
-    if (!g_noalloc_dev_ptr[dev]) {
+    NoallocDevice& D = g_noalloc_dev[dev];
+    if (!D.scratch) {
         // once per device, with that device current (the first call on a device does this)
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_ace_noalloc_scratch) != cudaSuccess || !p) {
-            g_noalloc_err = "cudaGetSymbolAddress failed for the scratch array";
-            return AP_ERR_CUDA;
-        }
+        if (cudaGetSymbolAddress(&p, g_ace_noalloc_scratch) != cudaSuccess || !p)
+            return noalloc_fail(AP_ERR_CUDA, "ap_ace_forces_noalloc: cudaGetSymbolAddress failed for the scratch array");
         static float gv[kNG];
         std::string err;
-        if (gaunt_values(gv, err)) { g_noalloc_err = err; return AP_ERR_ARG; }
+        if (gaunt_values(gv, err)) return noalloc_fail(AP_ERR_ARG, err);
         upload_gaunt(gv);
         if (cudaFuncSetAttribute(k_ace_noalloc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ace_smem_bytes()) !=
-            cudaSuccess) {
-            g_noalloc_err = "cudaFuncSetAttribute failed";
-            return AP_ERR_CUDA;
-        }
-        g_noalloc_dev_ptr[dev] = p;
+            cudaSuccess)
+            return noalloc_fail(AP_ERR_CUDA, "ap_ace_forces_noalloc: cudaFuncSetAttribute failed");
+        D.scratch = p;
     }
-    unsigned char* scratch = static_cast<unsigned char*>(g_noalloc_dev_ptr[dev]);
-    std::string err;
-    if (build_ace_tables(*pot, g_noalloc_tables, err)) { g_noalloc_err = err; return AP_ERR_ARG; }
-    cudaError_t e = cudaMemcpyAsync(scratch, &g_noalloc_tables, sizeof(AceDev), cudaMemcpyHostToDevice, s);
+    unsigned char* scratch = static_cast<unsigned char*>(D.scratch);
+    cudaError_t e = cudaSuccess;
+    // the coefficient tables are built and uploaded when the potential differs from the one
+    // whose tables the array holds (the first call on a device, or a new potential)
+    const unsigned long long key = potential_key(*pot);
+    if (!D.tables || D.key != key) {
+        std::string err;
+        if (build_ace_tables(*pot, g_noalloc_tables, err)) return noalloc_fail(AP_ERR_ARG, err);
+        D.tables = false;
+        // pageable source: the call returns once the host buffer has been read, and the copy
+        // is ordered on `stream` after the previous call's kernels there
+        e = cudaMemcpyAsync(scratch, &g_noalloc_tables, sizeof(AceDev), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return noalloc_fail(AP_ERR_CUDA, std::string("ap_ace_forces_noalloc: ") + cudaGetErrorString(e));
+        D.tables = true;
+        D.key = key;
+    }
     // the accumulators must start at zero; the array keeps whatever the last call left
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(scratch + kNoAllocTableBytes, 0, 3 * (size_t)n_atoms * sizeof(unsigned long long), s);
-    if (e != cudaSuccess) { g_noalloc_err = cudaGetErrorString(e); return AP_ERR_CUDA; }
+    e = cudaMemsetAsync(scratch + kNoAllocTableBytes, 0, 3 * (size_t)n_atoms * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return noalloc_fail(AP_ERR_CUDA, std::string("ap_ace_forces_noalloc: ") + cudaGetErrorString(e));
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     k_ace_noalloc<<<nsm, kWarps * 32, ace_smem_bytes(), s>>>(d_nbr_idx, d_rvec, n_atoms, max_nb, d_w, scratch, d_energy);
     k_ace_noalloc_forces<<<(n_atoms + 255) / 256, 256, 0, s>>>(scratch, n_atoms, d_force);
     e = cudaGetLastError();
-    if (e != cudaSuccess) { g_noalloc_err = cudaGetErrorString(e); return AP_ERR_CUDA; }
+    if (e != cudaSuccess) return noalloc_fail(AP_ERR_CUDA, std::string("ap_ace_forces_noalloc: ") + cudaGetErrorString(e));
     return AP_OK;
 }

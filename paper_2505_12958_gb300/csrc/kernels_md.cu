@@ -71,7 +71,8 @@ __global__ void __launch_bounds__(kRedBlock) k_blend(
     const float4* __restrict__ pos4, const int* __restrict__ cell,
     const float* __restrict__ wv, float* __restrict__ f, unsigned long long* __restrict__ acc,
     const float* __restrict__ e_ace, const double* __restrict__ e_eam, double c1_0, float* __restrict__ out_aos,
-    int* __restrict__ flags, double hdta, const unsigned char* __restrict__ fixed, double* __restrict__ v) {
+    int* __restrict__ flags, double hdta, const unsigned char* __restrict__ fixed, double* __restrict__ v,
+    const long long* __restrict__ step, long long* __restrict__ load_ring, int load_cap) {
     pdl_wait();
     // FP64 runs at 1/64 of the FP32 rate on this GPU.  Positions are taken in FP32 from the
     // cell origin and x_rel (absolute error ~1e-5 A) for the indenter pre-test, inside its
@@ -151,6 +152,13 @@ __global__ void __launch_bounds__(kRedBlock) k_blend(
             if (d2 < dy.R * dy.R && d2 > 0.0) {
                 const double dist = sqrt(d2), h = dy.R - dist, c = dy.K * h * h / dist;
                 for (int k = 0; k < 3; ++k) F[k] += (float)(c * d[k]);
+                if (load_ring) {
+                    // this atom's share of Eq. P_ind in fixed point: integer sums do not
+                    // depend on the order of the atomics
+                    const double l = c * (d[0] * dy.ind_dir[0] + d[1] * dy.ind_dir[1] + d[2] * dy.ind_dir[2]);
+                    atomicAdd(reinterpret_cast<unsigned long long*>(&load_ring[*step % load_cap]),
+                              (unsigned long long)__double2ll_rn(l * kLoadScale));
+                }
             }
         }
     }
@@ -260,10 +268,21 @@ __global__ void __launch_bounds__(kRedBlock) k_reduce(const double* __restrict__
 __global__ void k_kick_drift(double* __restrict__ x, double* __restrict__ v, const float* __restrict__ f,
                              const unsigned char* __restrict__ fixed, int n, double hdta, double dt,
                              double* __restrict__ tptr, long long* __restrict__ step,
-                             const double* __restrict__ xb, double lim2, int* __restrict__ flags) {
+                             const double* __restrict__ xb, double lim2, int* __restrict__ flags,
+                             long long* __restrict__ load_ring, double* __restrict__ load_ring_t, int load_cap) {
     pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) { *tptr += dt; *step += 1; flags[kFlagNAce] = 0; }
+    if (i == 0) {
+        *tptr += dt;
+        *step += 1;
+        flags[kFlagNAce] = 0;
+        if (load_ring) {
+            // the slot of this step starts at zero; the blend of its force pass adds the load
+            const long long slot = *step % load_cap;
+            load_ring[slot] = 0;
+            load_ring_t[slot] = *tptr;
+        }
+    }
     if (i >= n || fixed[i]) return;
     double d2 = 0.0;
     for (int k = 0; k < 3; ++k) {
@@ -428,10 +447,12 @@ int launch_pos_in(Ctx& c, cudaStream_t s, const double* pos) {
     return 1;
 }
 
-int launch_blend(Ctx& c, cudaStream_t s, float* out_aos, double kick_dt) {
+int launch_blend(Ctx& c, cudaStream_t s, float* out_aos, double kick_dt, bool in_step) {
     const double hdta = kick_dt > 0.0 ? 0.5 * kick_dt * kFtm / c.mass : 0.0;
+    long long* ring = in_step && c.dyn.ind_on ? c.load_ring : nullptr;
     launch_pdl(k_blend, c.nred, kRedBlock, 0, s, c.x, c.n, c.grid, c.dyn, c.d_time, c.pos4, c.cell, c.w, c.f, c.acc,
-               c.e_ace, c.e_eam, c.ace_c1_0, out_aos, c.flags, hdta, c.fixed, c.v);
+               c.e_ace, c.e_eam, c.ace_c1_0, out_aos, c.flags, hdta, c.fixed, c.v, (const long long*)c.d_step, ring,
+               c.load_cap);
     return 1;
 }
 
@@ -458,7 +479,7 @@ int launch_reduce(Ctx& c, cudaStream_t s, int with_kinetic) {
 int launch_kick_drift(Ctx& c, cudaStream_t s, double dt, int) {
     const double lim = 0.5 * c.skin;
     launch_pdl(k_kick_drift, (c.n + 255) / 256, 256, 0, s, c.x, c.v, c.f, c.fixed, c.n, 0.5 * dt * kFtm / c.mass, dt,
-               c.d_time, c.d_step, c.xb, lim * lim, c.flags);
+               c.d_time, c.d_step, c.xb, lim * lim, c.flags, c.load_ring, c.load_ring_t, c.load_cap);
     return 1;
 }
 

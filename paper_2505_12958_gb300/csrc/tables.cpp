@@ -384,4 +384,52 @@ int build_ace_tables(const ap_potential& p, AceDev& out, std::string& err) {
     return AP_OK;
 }
 
+// FP32 -> TF32 rounding to nearest, ties away from zero (the rule of cvt.rna.tf32.f32): the
+// result keeps 10 explicit mantissa bits, the 13 low bits are zero
+static float tf32_rna(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    u = (u + 0x1000u) & 0xFFFFE000u;
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+}
+
+void build_ace_tc(const AceDev& in, AceTc& out) {
+    std::memset(&out, 0, sizeof(out));
+    for (int d = 0; d < 2; ++d) {
+        for (int l = 0; l <= kLmax; ++l) {
+            // triple t = l is (0, l, l): G = delta_{m2 m3} G_l
+            const float g = (float)gaunt_real_racah(0, 0, l, 0, l, 0);
+            for (int n1 = 0; n1 < kNmax; ++n1)
+                for (int n2 = 0; n2 < kNmax; ++n2)
+                    for (int n3 = 0; n3 < kNmax; ++n3)
+                        out.c0ll[d][l][n2 * 8 + n3][n1] = g * in.c3[d][l][n3][n1 * 8 + n2];
+        }
+        for (int u = 0; u < kNT3; ++u) {
+            const int t = kTcTriple0 + u;
+            const bool sym = tri_l(t, 0) == tri_l(t, 1);
+            for (int n3 = 0; n3 < kNmax; ++n3)
+                for (int n1 = 0; n1 < kNmax; ++n1)
+                    for (int n2 = 0; n2 < kNmax; ++n2) {
+                        const int q = n1 * 8 + n2;
+                        float v = in.c3[d][t][n3][q];
+                        // the product of the first two factors is symmetric in (n1, n2) when
+                        // l1 = l2: both orders carry half of the function's coefficient
+                        if (sym && n1 != n2) v = 0.5f * (in.c3[d][t][n3][q] + in.c3[d][t][n3][n2 * 8 + n1]);
+                        const float hi = tf32_rna(v), lo = tf32_rna(v - hi);
+                        const int pos = n3 ^ (4 * ((q >> 2) & 1));
+                        out.c3[0][d][u][q][pos] = hi;
+                        out.c3[1][d][u][q][pos] = lo;
+                    }
+        }
+    }
+    std::memcpy(out.c2, in.c2, sizeof(out.c2));
+    std::memcpy(out.c1, in.c1, sizeof(out.c1));
+    out.c1_0 = in.c1_0;
+    out.c2_0 = in.c2_0;
+    out.nref_inv = in.nref_inv;
+    out.rc = in.rc;
+}
+
 }  // namespace ap

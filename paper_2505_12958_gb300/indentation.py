@@ -1,9 +1,10 @@
 """Indentation observables from a running context (Sec. 2.1 and 3: Eqs. P_ind, hertz_fit,
 p_m, contact_radius).
 
-The load P_ind (Eq. P_ind) is computed on the device by the energy pass (ap_energy's
-`load`); this module records it against the indentation depth and evaluates the paper's
-closed forms on the series:
+The load P_ind (Eq. P_ind) of every MD step is kept on the device (ap_record_load: the
+blend kernel adds each step's load to a ring buffer) and read back once per recording;
+this module records it against the indentation depth and evaluates the paper's closed
+forms on the series:
 
     depth            h = z_surf + R - z_tip(t)        (z_tip moves with the indenter velocity)
     Hertz load       P_H = 4/3 E* R^(1/2) h^(3/2)     (E* by linear least squares through 0)
@@ -20,26 +21,28 @@ __all__ = ["record_indentation", "hertz_modulus", "contact_radius", "hardness", 
 
 
 def record_indentation(ctx, indenter, ind_vel, z_surf, n_steps, every, dt=1.0, stream=None):
-    """Advance ctx by n_steps MD steps, reading the load every `every` steps (each read
-    synchronises).  indenter: the dict the context was created with (center, R); ind_vel:
-    its velocity (A/fs, moves along -z for (0, 0, v)).  Returns dict(time_fs, depth, load)."""
+    """Advance ctx by n_steps MD steps and return the load of the starting state and of every
+    `every`-th step (and of the last one).  The steps' loads stay on the device until one
+    read-back at the end; the starting state's load comes from one ap_energy call.
+    indenter: the dict the context was created with (center, R); ind_vel: its velocity (A/fs,
+    moves along -z for (0, 0, v)).  Returns dict(time_fs, depth, load)."""
     R = float(indenter["R"])
     z0 = float(indenter["center"][2])
     vz = float(np.asarray(ind_vel)[2])
-    times, depth, load = [], [], []
-    done = 0
-    while done <= n_steps:
-        rep = ctx.energy()
-        t = rep["time_fs"]
-        times.append(t)
-        depth.append(z_surf + R - (z0 - vz * t))
-        load.append(rep["load"])
-        if done == n_steps:
-            break
-        k = min(every, n_steps - done)
-        ctx.step(k, dt, stream)
-        done += k
-    return {"time_fs": np.array(times), "depth": np.array(depth), "load": np.array(load)}
+    rep = ctx.energy()
+    ctx.record_load(max(1, n_steps))
+    try:
+        ctx.step(n_steps, dt, stream)
+        t_all, p_all = ctx.load_history()
+    finally:
+        ctx.record_load(0)
+    pick = list(range(every - 1, n_steps, every))
+    if n_steps > 0 and (not pick or pick[-1] != n_steps - 1):
+        pick.append(n_steps - 1)
+    times = np.concatenate([[rep["time_fs"]], t_all[pick]])
+    load = np.concatenate([[rep["load"]], p_all[pick]])
+    depth = z_surf + R - (z0 - vz * times)
+    return {"time_fs": times, "depth": depth, "load": load}
 
 
 def hertz_modulus(depth, load, R, h_max=None):

@@ -11,6 +11,11 @@ completed, which the server learns from a CUDA event without blocking the others
 Latency runs from a request's arrival to the moment its final positions, velocities,
 forces and energy are readable on the host.  A request's results do not depend on what it
 is batched with: every kernel is deterministic and contexts share no device state.
+
+A request that fails is reported in its Result (`error`, the library status text) and
+leaves the others untouched: one whose context cannot be created (for instance AP_ERR_OOM)
+is refused at admission, one whose steps end in a device error (AP_ERR_DOMAIN,
+AP_ERR_LIMIT, ...) is retired with that error when it completes.
 """
 import collections
 import time
@@ -18,14 +23,14 @@ import time
 import numpy as np
 import torch
 
-from . import APContext, footprint_bytes, step_batch
+from . import APContext, APError, footprint_bytes, step_batch
 
 __all__ = ["Server", "Result", "percentile_ms"]
 
 
 class Result:
     __slots__ = ("id", "n_atoms", "n_steps", "n_ace", "arrival_s", "admit_s", "done_s", "energy",
-                 "x", "v", "forces", "memory_bytes", "footprint_bytes")
+                 "x", "v", "forces", "memory_bytes", "footprint_bytes", "error")
 
     @property
     def latency_s(self):
@@ -67,31 +72,51 @@ class Server:
     def _stream(self):
         return self._streams.pop() if self._streams else torch.cuda.Stream()
 
+    @staticmethod
+    def _failed(req, now, err, foot=0):
+        r = Result()
+        r.id, r.n_atoms, r.n_steps = req["id"], len(req["x"]), int(req["n_steps"])
+        r.arrival_s, r.admit_s, r.done_s = req["arrival_s"], now, now
+        r.energy, r.n_ace = None, 0
+        r.x = r.v = r.forces = None
+        r.memory_bytes, r.footprint_bytes = 0, foot
+        r.error = str(err)
+        return r
+
     def _admit(self, req, foot, now):
+        """The request's context on its own stream, or (None, refused Result) when it cannot
+        be created."""
         a = _Active()
         a.req, a.foot, a.admit_s = req, foot, now
         a.stream = self._stream()
-        a.ctx = APContext(req["eam"], req["ace"], req["box"], req["x"], req["v"], req["fixed"], req["region"],
-                          req.get("indenter"), req.get("ind_vel"), req["mass"], precision=self.precision,
-                          stream=a.stream)
+        try:
+            a.ctx = APContext(req["eam"], req["ace"], req["box"], req["x"], req["v"], req["fixed"], req["region"],
+                              req.get("indenter"), req.get("ind_vel"), req["mass"], precision=self.precision,
+                              stream=a.stream)
+        except APError as e:
+            self._streams.append(a.stream)
+            return None, self._failed(req, now, e, foot)
         a.left = int(req["n_steps"])
         a.events = collections.deque()
         self.used += foot
         self.peak_used = max(self.peak_used, self.used)
-        return a
+        return a, None
 
     def _retire(self, a, t0):
         r = Result()
         q = a.req
         r.id, r.n_atoms, r.n_steps = q["id"], len(q["x"]), int(q["n_steps"])
         r.arrival_s, r.admit_s = q["arrival_s"], a.admit_s
-        r.energy = a.ctx.energy()
-        r.n_ace = r.energy["n_ace"]
-        if self.keep_arrays:
-            r.x, r.v, _ = a.ctx.get_state()
-            r.forces = a.ctx.forces()
-        else:
-            r.x = r.v = r.forces = None
+        r.error = None
+        r.x = r.v = r.forces = None
+        try:
+            r.energy = a.ctx.energy()
+            r.n_ace = r.energy["n_ace"]
+            if self.keep_arrays:
+                r.x, r.v, _ = a.ctx.get_state()
+                r.forces = a.ctx.forces()
+        except APError as e:
+            r.energy, r.n_ace, r.error = None, 0, str(e)
         r.memory_bytes = a.ctx.memory_bytes()
         r.footprint_bytes = a.foot
         r.done_s = time.perf_counter() - t0
@@ -125,7 +150,11 @@ class Server:
                 if active and self.used + foot > self.mem_budget:
                     break
                 queue.popleft()
-                active.append(self._admit(q, foot, time.perf_counter() - t0))
+                a, refused = self._admit(q, foot, time.perf_counter() - t0)
+                if a is None:
+                    done.append(refused)
+                else:
+                    active.append(a)
             self.peak_active = max(self.peak_active, len(active))
             # retire finished requests; trim completed chunk events
             still = []
@@ -141,7 +170,12 @@ class Server:
             batch = [a for a in active if a.left > 0 and len(a.events) < self.inflight]
             if batch:
                 ks = [min(self.chunk, a.left) for a in batch]
-                step_batch([a.ctx for a in batch], ks, self.dt)
+                try:
+                    step_batch([a.ctx for a in batch], ks, self.dt)
+                except APError:
+                    # a launch was refused: every context was still issued; the failing ones
+                    # report their status when they retire
+                    pass
                 for a, k in zip(batch, ks):
                     a.left -= k
                     ev = torch.cuda.Event()

@@ -2,9 +2,12 @@
 virial and against central finite differences, on strained triclinic W cells with
 vacancies and noise (the differentiation workload), for FP64 and FP32 inputs.
 
-Finite differences of the library energy are noise-limited: each energy carries FP32
-rounding of ~1e-7 eV per affected atom, so h = 1e-3 A gives ~5e-4 eV/A of noise (h = 1e-4 A
-would give ~5e-3); the analytic checks against the oracle hold the 1e-4 eV/A bar.
+The energy is an FP64 total whatever the input dtype, so FP32 and FP64 inputs share the
+1e-6 eV/atom bar.  Finite differences of the library energy are noise-limited: each per-atom
+ACE energy carries FP32 rounding of ~1e-7 eV and a displacement changes ~60 of them, so the
+central difference at h = 1e-4 A (the differentiation workload's step) carries ~5e-3 eV/A of
+noise and is held to 2e-2 eV/A, and at h = 1e-3 A ~5e-4 eV/A, held to 2e-3 eV/A; the analytic
+checks against the oracle hold the 1e-4 eV/A bar.
 """
 import numpy as np
 import pytest
@@ -44,23 +47,23 @@ def test_backward_matches_oracle_and_finite_differences(apl, orc, ncell, seed, d
         xr = x.detach().double().cpu().numpy() if dtype == "float32" else c["x"]
         ref = orc.evaluate(xr, c["box"], c["eam"], c["ace"], reg)
         assert np.abs(-gx - ref["forces"]).max() <= 1e-4
-        assert abs(E.item() - ref["e_total"]) / n <= (1e-6 if dtype == "float64" else 1e-5)
+        assert E.dtype == torch.float64
+        assert abs(E.item() - ref["e_total"]) / n <= 1e-6
         v = ref["virial"]
         W = np.array([[v[0], v[3], v[4]], [v[3], v[1], v[5]], [v[4], v[5], v[2]]])
         assert np.abs(-gs - W).max() <= 2e-5 * np.abs(W).max() + 1e-5 * n
-        # central differences of the library energy (taken in FP64: an FP32 total energy of
-        # ~5e3 eV has a resolution of ~5e-4 eV)
-        h = 1e-3
+        # central differences of the library energy
         x64 = x.detach().double()
         e64 = eps.detach().double()
         rng = np.random.default_rng(seed)
-        for i in rng.choice(n, size=3, replace=False):
-            for k in range(3):
-                xp = x64.clone(); xp[i, k] += h
-                xm = x64.clone(); xm[i, k] -= h
-                e_p = ap_energy(xp, e64, ctx, c["box"]).item()
-                e_m = ap_energy(xm, e64, ctx, c["box"]).item()
-                assert abs((e_p - e_m) / (2 * h) - gx[i, k]) <= 2e-3
+        for h, tol in ((1e-4, 2e-2), (1e-3, 2e-3)):
+            for i in rng.choice(n, size=3, replace=False):
+                for k in range(3):
+                    xp = x64.clone(); xp[i, k] += h
+                    xm = x64.clone(); xm[i, k] -= h
+                    e_p = ap_energy(xp, e64, ctx, c["box"]).item()
+                    e_m = ap_energy(xm, e64, ctx, c["box"]).item()
+                    assert abs((e_p - e_m) / (2 * h) - gx[i, k]) <= tol, (h, i, k)
         # strain differences: E carries ~1e-5-1e-4 eV of FP32 rounding per evaluation, so hs is
         # kept large enough for that noise to stay below ~0.1 eV after the division, while the
         # O(hs^2) truncation (third strain derivative ~1e5 eV) stays at ~1e-2 eV
@@ -94,7 +97,7 @@ def test_strained_cell_sweep_against_oracle(apl, orc, dtype):
             xr = x.detach().double().cpu().numpy()
             ref = orc.evaluate(xr, c["box"], c["eam"], c["ace"], reg)
             assert np.abs(-x.grad.double().cpu().numpy() - ref["forces"]).max() <= 1e-4, ncell
-            assert abs(E.item() - ref["e_total"]) / n <= (1e-6 if dtype == "float64" else 1e-5), ncell
+            assert abs(E.item() - ref["e_total"]) / n <= 1e-6, ncell
             v = ref["virial"]
             W = np.array([[v[0], v[3], v[4]], [v[3], v[1], v[5]], [v[4], v[5], v[2]]])
             gs = eps.grad.double().cpu().numpy()

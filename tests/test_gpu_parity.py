@@ -215,28 +215,74 @@ def test_nve_energy_conservation_on_gpu(apl):
     assert worst / len(c["x"]) < 2e-4
 
 
-@pytest.mark.parametrize("nsample", [96])
-def test_w_indentation_slab_full_size_sampled(apl, orc, nsample):
-    """128,000-atom W slab (the timed workload) at t = 0: sampled atoms against the oracle."""
-    c = synth.configs.w_slab()
-    with ctx_of(apl, c) as ctx:
-        ctx.compute_forces()
-        rep = ctx.energy()
-        F = ctx.forces().astype(np.float64)
-        w = ctx.weights()
-    x = c["x"]
+def _slab_sample(x, c, ind_center, nsample, seed):
+    """Seeded sample of the W slab's atoms, spread over the ACE zone, its shell, the EAM
+    region, the atoms under the tip and the fixed layers."""
     reg = c["region"]
     d = np.linalg.norm(x - np.array(reg["center"]), axis=1)
-    di = np.linalg.norm(x - np.array(c["indenter"]["center"]), axis=1)
-    rng = np.random.default_rng(11)
-    groups = [np.where(d < reg["r_in"])[0], np.where((d >= reg["r_in"]) & (d < reg["r_in"] + reg["r_sw"]))[0],
-              np.where(d >= reg["r_in"] + reg["r_sw"])[0], np.where(di < c["indenter"]["R"])[0],
-              np.where(c["fixed"] > 0)[0]]
-    sample = np.unique(np.concatenate([rng.choice(g, size=min(len(g), nsample // 5), replace=False) for g in groups]))
-    pi, pj, _ = orc.neighbors(x, c["box"], 5.46)
-    centers = np.unique(np.concatenate([sample, pj[np.isin(pi, sample)]]))
-    ref = orc.evaluate(x, c["box"], c["eam"], c["ace"], reg, c["indenter"], centers=centers)
-    assert np.abs(F[sample] - ref["forces"][sample]).max() <= FTOL
+    di = np.linalg.norm(x - np.array(ind_center), axis=1)
+    free = c["fixed"] == 0
+    groups = [np.where((d < reg["r_in"]) & free)[0],
+              np.where((d >= reg["r_in"]) & (d < reg["r_in"] + reg["r_sw"]) & free)[0],
+              np.where((d >= reg["r_in"] + reg["r_sw"]) & free)[0], np.where(di < c["indenter"]["R"])[0],
+              np.where(~free)[0]]
+    rng = np.random.default_rng(seed)
+    return np.unique(np.concatenate([rng.choice(g, size=min(len(g), nsample // len(groups)), replace=False)
+                                     for g in groups if len(g)]))
+
+
+def _with_neighbours(x, box, idx, rc):
+    """idx and every atom within rc of one of them (periodic in x and y, open in z): the
+    oracle centres that make the sampled atoms' forces and energies complete."""
+    from scipy.spatial import cKDTree
+    L = np.diag(np.asarray(box["h"]).reshape(3, 3))
+    y = np.array(x) - np.asarray(box["origin"])
+    y[:, :2] = np.mod(y[:, :2], L[:2])
+    y[:, 2] -= y[:, 2].min()
+    near = cKDTree(y, boxsize=[L[0], L[1], 1e9]).query_ball_point(y[idx], r=rc)
+    return np.unique(np.concatenate([np.asarray(idx)] + [np.asarray(v, dtype=np.int64) for v in near]))
+
+
+def _slab_check(orc, c, x, t, F, ea, w, sample):
+    ind = dict(c["indenter"])
+    ind["center"] = tuple(np.asarray(ind["center"]) - np.asarray(c["ind_vel"]) * t)
+    centers = _with_neighbours(x, c["box"], sample, 5.46)
+    ref = orc.evaluate(x, c["box"], c["eam"], c["ace"], c["region"], ind, centers=centers)
+    assert ref["status"] == 0
+    dF = np.abs(F[sample] - ref["forces"][sample]).max()
+    dE = ea[sample] - ref["e_atom"][sample]
+    assert dF <= FTOL, dF
+    assert np.abs(dE).max() <= EATOM, np.abs(dE).max()
+    assert abs(dE.mean()) <= ETOL, dE.mean()
     assert np.abs(w[sample] - ref["w"][sample]).max() < 1e-6
-    assert rep["n_ace"] == 21241
-    assert rep["load"] > 0
+    return ref
+
+
+@pytest.mark.parametrize("nsample", [600])
+def test_w_indentation_slab_full_size_sampled(apl, orc, nsample):
+    """128,000-atom W slab (the timed workload), in the bench's launch path (the default
+    stream), at t = 0 and after 50 MD steps: forces, per-atom energies (each <= 2e-5 eV, mean
+    error <= 1e-6 eV/atom) and weights of ~600 sampled atoms against the oracle at the GPU's
+    positions and indenter time."""
+    import torch
+    c = synth.configs.w_slab()
+    n = len(c["x"])
+    ea = torch.empty(n, dtype=torch.float64, device="cuda")
+    with ctx_of(apl, c) as ctx:
+        ctx.compute_forces()
+        rep = ctx.energy(e_atom=ea)
+        F, w = ctx.forces().astype(np.float64), ctx.weights()
+        sample = _slab_sample(c["x"], c, c["indenter"]["center"], nsample, 11)
+        assert len(sample) >= 500
+        _slab_check(orc, c, c["x"], 0.0, F, ea.cpu().numpy(), w, sample)
+        assert rep["n_ace"] == 21241
+        assert rep["load"] > 0
+        ctx.step(50, 1.0)
+        ctx.check()
+        x, _, t = ctx.get_state()
+        ctx.energy(e_atom=ea)
+        F, w = ctx.forces().astype(np.float64), ctx.weights()
+    assert abs(t - 50.0) < 1e-9
+    ind_c = np.asarray(c["indenter"]["center"]) - np.asarray(c["ind_vel"]) * t
+    sample = _slab_sample(x, c, ind_c, nsample, 12)
+    _slab_check(orc, c, x, t, F, ea.cpu().numpy(), w, sample)

@@ -105,3 +105,34 @@ def test_full_size_cu_slab_sampled(apl, slab, mode):
         assert dF <= 10 * 2 * U[mode] * fscale
     else:
         assert dF <= 1e-4
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp32", "tf32x3", "bf16", "fp16"])
+def test_nve_drift_per_precision_mode(apl, mode):
+    """NVE energy drift per ps of each A_nlm precision mode: a W (001) slab with the ACE
+    hemisphere (geometric weights, so the -grad w force is part of the dynamics), 300 K, no
+    indenter, fixed bottom layers, 1000 steps of 1 fs.  The drift is the slope of a
+    least-squares line through the total energy sampled every 50 steps.  Velocity Verlet
+    keeps the energy of an exact gradient to O(dt^2) without drift; FP32 forces add
+    rounding noise (~1e-7 relative), which random-walks the energy by far less than 1e-5
+    eV/atom per ps.  BF16 and FP16 round A to 2u relative (u = 2^-9, 2^-12), so their forces
+    are not the exact gradient of the energy they report: their bars are 2u times the ACE
+    force scale (~1 eV/A) times the ~0.01 A/fs velocity scale times 1000 fs, over 10."""
+    c = synth.configs.w_slab(ncell=8, nz=8, r_in=6.0, r_sw=3.0)
+    n = len(c["x"])
+    with apl.APContext(c["eam"], c["ace"], c["box"], c["x"], c["v"], c["fixed"], c["region"], None, None, c["mass"],
+                       precision=mode) as ctx:
+        ctx.compute_forces()
+        r = ctx.energy()
+        ts, es = [0.0], [(r["e_total"] + r["e_kin"]) / n]
+        for _ in range(20):
+            ctx.step(50, 1.0)
+            r = ctx.energy()
+            ts.append(r["time_fs"])
+            es.append((r["e_total"] + r["e_kin"]) / n)
+    slope = np.polyfit(np.asarray(ts) / 1000.0, np.asarray(es), 1)[0]
+    dev = np.abs(np.asarray(es) - es[0]).max()
+    print("mode %-7s NVE drift %.3e eV/atom/ps, max deviation %.3e eV/atom" % (mode, slope, dev))
+    bar = 2 * U[mode] * 1.0 * 0.01 * 1000 / 10 if mode in U else 1e-5
+    assert abs(slope) <= bar, (slope, bar)
+    assert dev <= max(bar, 2e-4)

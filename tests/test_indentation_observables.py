@@ -42,6 +42,17 @@ def test_recorded_load_matches_the_oracle(orc):
                       c["ind_vel"], c["mass"]) as ctx:
         rec = record_indentation(ctx, c["indenter"], c["ind_vel"], z_surf, 60, 20)
         x, _, t = ctx.get_state()
+        # the device history (fixed-point sum in the step's blend) agrees with the energy
+        # pass's FP64 load of the same state
+        p_end = ctx.energy()["load"]
+        assert abs(p_end - rec["load"][-1]) <= 1e-8 * abs(p_end) + 1e-8
+        # every step is kept: 30 more steps give 30 entries whose times advance by dt
+        ctx.record_load(40)
+        ctx.step(30, 1.0)
+        th, ph = ctx.load_history()
+        assert len(th) == 30 and np.allclose(np.diff(th), 1.0) and abs(th[-1] - (t + 30.0)) < 1e-9
+        assert ph[-1] > 0
+    assert len(rec["load"]) == 4
     assert np.allclose(np.diff(rec["depth"]), 20 * c["ind_vel"][2])            # the tip advances at v
     assert rec["load"][0] > 0 and rec["load"][-1] > rec["load"][0]              # deeper, harder push
     ind = dict(c["indenter"])

@@ -79,3 +79,61 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
         st = _capi.lib().ap_ace_forces_noalloc(C.byref(pot), n, m, C.c_void_p(d.data_ptr()), C.c_void_p(d.data_ptr()),
                                                None, C.c_void_p(d.data_ptr()), C.c_void_p(d.data_ptr()), None)
         assert st == _capi.AP_ERR_ARG
+
+
+def test_noalloc_weighted_against_oracle_per_atom(orc):
+    """Mixed weights (0, fractional, 1): the weighted forces and the unweighted per-atom ACE
+    energies against the FP64 oracle (explicit frozen weights, no EAM), on two calls in a
+    row with the same potential (the second reuses the uploaded tables)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("needs a CUDA device")
+    import paper_2505_12958_gb300 as ap
+    from paper_2505_12958_gb300 import _capi
+    ap.build()
+    c = synth.configs.w_bulk(ncell=5, seed=77)
+    n = len(c["x"])
+    L = 5 * 3.165
+    w = np.random.default_rng(5).choice([0.0, 0.37, 1.0], size=n)
+    ref = orc.evaluate(c["x"], c["box"], None, c["ace"], {"kind": "explicit", "w": w})
+    assert ref["status"] == 0
+    idx, vec = _neighbor_lists(c["x"], L, c["ace"]["rc"], 96)
+    d_idx = torch.tensor(idx, device="cuda")
+    d_vec = torch.tensor(vec, device="cuda")
+    d_w = torch.tensor(w, dtype=torch.float32, device="cuda")
+    pot, keep = ap.potential_struct(c["eam"], c["ace"], c["mass"])
+    for call in range(2):
+        d_f = torch.full((n, 3), float("nan"), dtype=torch.float32, device="cuda")
+        d_e = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+        st = _capi.lib().ap_ace_forces_noalloc(C.byref(pot), n, 96, C.c_void_p(d_idx.data_ptr()),
+                                               C.c_void_p(d_vec.data_ptr()), C.c_void_p(d_w.data_ptr()),
+                                               C.c_void_p(d_f.data_ptr()), C.c_void_p(d_e.data_ptr()), None)
+        assert st == 0
+        torch.cuda.synchronize()
+        f = d_f.cpu().numpy().astype(np.float64)
+        e = d_e.cpu().numpy()
+        assert np.abs(f - ref["forces"]).max() <= 1e-4, (call, np.abs(f - ref["forces"]).max())
+        on = w > 0
+        assert np.all(e[~on] == 0.0)
+        assert np.abs(e[on] - ref["e_ace"][on]).max() <= 2e-5, call
+        assert abs((e[on] - ref["e_ace"][on]).mean()) <= 1e-6, call
+
+
+def test_noalloc_reports_why_it_refused():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("needs a CUDA device")
+    import paper_2505_12958_gb300 as ap
+    from paper_2505_12958_gb300 import _capi
+    c = synth.configs.w_bulk(ncell=3)
+    pot, keep = ap.potential_struct(c["eam"], c["ace"], c["mass"], precision="bf16")
+    d = torch.zeros(16, device="cuda")
+    st = _capi.lib().ap_ace_forces_noalloc(C.byref(pot), 8, 8, C.c_void_p(d.data_ptr()), C.c_void_p(d.data_ptr()),
+                                           None, C.c_void_p(d.data_ptr()), C.c_void_p(d.data_ptr()), None)
+    assert st == _capi.AP_ERR_ARG
+    assert b"AP_ACE_FP32" in _capi.lib().ap_last_error(None)
+    pot, keep = ap.potential_struct(c["eam"], c["ace"], c["mass"])
+    st = _capi.lib().ap_ace_forces_noalloc(C.byref(pot), 65537, 8, C.c_void_p(d.data_ptr()), C.c_void_p(d.data_ptr()),
+                                           None, C.c_void_p(d.data_ptr()), C.c_void_p(d.data_ptr()), None)
+    assert st == _capi.AP_ERR_ARG
+    assert b"65536" in _capi.lib().ap_last_error(None)
