@@ -303,16 +303,26 @@ def precision_leg(torch, ap, steps=500, every=50, modes=("fp64", "fp32", "tf32x3
 
 def ace_kernel_roofline(prof, n_steps, c, pk, peak_src, ctx_atoms_in_rc, fma_peak=None, alone_ms=None):
     """Roofline of the dominant kernel, k_ace_contract (products, densities and dE/dA of the
-    compacted atoms); its CUDA-event time comes from the library's per-stage events.  The
-    peak is the FP32 FMA throughput measured on this device (ap_probe_fp32_peak); the
-    unit-count figure at the maximum SM clock is reported beside it."""
-    from paper_2505_12958_gb300.workload import ace_contract_flops_per_atom
+    compacted atoms); its CUDA-event time comes from the library's per-stage events.
+
+    The headline figure divides the algorithmic work of the factored ACE evaluation (the
+    arithmetic it cannot avoid, 403,704 FLOP per atom: workload.ace_contract_flops_per_atom)
+    by the kernel time and compares it with the FP32 FMA peak measured on this device
+    (ap_probe_fp32_peak), as in every earlier measurement of this kernel.  Part of that work
+    now runs on tensor cores, so two more entries split it by pipe: the FP32-lane arithmetic
+    against the FP32 peak, and the TF32 tensor-core products (useful and as executed by the
+    3xTF32 mma.sync tiles) against the dense TF32 peak, taken as the measured BF16 cuBLAS
+    figure times the nominal TF32 / BF16 ratio (1.1 / 2.25)."""
+    from paper_2505_12958_gb300.workload import ace_contract_flops_per_atom, ace_tc_contract_work
     ms, nl = prof["ace"]
     avg_s = ms / max(1, nl) / 1000.0
-    flops = ace_contract_flops_per_atom() * len(ctx_atoms_in_rc)
+    n_ace = len(ctx_atoms_in_rc)
+    flops = ace_contract_flops_per_atom() * n_ace
     achieved = flops / avg_s / 1e12
     derived = 152 * 128 * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
     peak = fma_peak if fma_peak else derived
+    work = ace_tc_contract_work()
+    tf32_peak = float(pk.get("bf16_tflops", 1900.0)) * 1.1 / 2.25
     traffic = None
     tf = os.path.join(ROOT, "profiles", "k_ace_contract_traffic.json")
     if os.path.exists(tf):
@@ -320,6 +330,17 @@ def ace_kernel_roofline(prof, n_steps, c, pk, peak_src, ctx_atoms_in_rc, fma_pea
         rec = json.load(open(tf))
         if rec.get("source_hash") == source_hash(CONTRACT_FILES):
             traffic = rec["dram_bytes_per_launch"]
+
+    def at(ms_launch):
+        s_ = ms_launch / 1000.0
+        return {"avg_launch_ms": ms_launch, "achieved": flops / s_ / 1e12, "frac": flops / s_ / 1e12 / peak,
+                "fp32_lanes": {"achieved": work["fp32"] * n_ace / s_ / 1e12,
+                               "frac": work["fp32"] * n_ace / s_ / 1e12 / peak},
+                "tensor": {"achieved_useful": work["tensor"] * n_ace / s_ / 1e12,
+                           "achieved_executed": work["tensor_executed"] * n_ace / s_ / 1e12, "peak": tf32_peak,
+                           "frac_executed": work["tensor_executed"] * n_ace / s_ / 1e12 / tf32_peak}}
+
+    timed = at(avg_s * 1000.0)
     return {"kernel": "k_ace_contract", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
             "peak_source": ("measured: FP32 FMA microbenchmark on this device (ap_probe_fp32_peak)" if fma_peak else
@@ -327,11 +348,13 @@ def ace_kernel_roofline(prof, n_steps, c, pk, peak_src, ctx_atoms_in_rc, fma_pea
                             % (float(pk.get("sm_max_mhz", 2070.0)), peak_src)),
             "peak_derived_unit_count": derived,
             "algorithmic_flops_per_launch": int(flops), "avg_launch_ms": avg_s * 1000.0, "timed_launches": nl,
+            "fp32_lanes": dict(timed["fp32_lanes"], flops_per_atom=work["fp32"], peak=peak),
+            "tensor": dict(timed["tensor"], flops_per_atom_useful=work["tensor"],
+                           flops_per_atom_executed=work["tensor_executed"],
+                           peak_source="measured BF16 cuBLAS x nominal TF32/BF16 ratio 1.1/2.25 (%s peaks file)" % peak_src),
             "overlap": "in the timed steps the EAM branch runs beside this kernel on the same SMs",
-            "alone": None if not alone_ms else
-            {"avg_launch_ms": alone_ms, "achieved": flops / (alone_ms / 1000.0) / 1e12,
-             "frac": flops / (alone_ms / 1000.0) / 1e12 / peak,
-             "source": "per-stage pass of the same run: every stage bracketed, EAM on the main stream"}}
+            "alone": None if not alone_ms else dict(at(alone_ms), source="per-stage pass of the same run: every stage "
+                                                                        "bracketed, EAM on the main stream")}
 
 
 def serving_bench(torch, n_req, seed=1005, load=0.7, chunk=8, max_active=64):

@@ -53,11 +53,11 @@ struct alignas(16) EamDev {
     double F_a1, F_a2, F_dxi;
 };
 
-// ACE coefficient tensors, zero-padded to full n-ranges (a basis function sits at its
-// sorted (n, l) position; the other orderings carry zero).
+// ACE coefficient tensors on the host, zero-padded to full n-ranges (a basis function sits at
+// its sorted (n, l) position; the other orderings carry zero); the device tables (AceTc)
+// are built from them.
 struct AceDev {
-    float c3[2][kNT][8][65];  // [density][l-triple][n3][n1 * 8 + n2], row padded to 65 floats so that
-                              // both lane mappings of the contraction read it without bank conflicts
+    float c3[2][kNT][8][64];  // [density][l-triple][n3][n1 * 8 + n2]
     float c2[2][5][64];       // [density][l][n1 * 8 + n2]
     float c1[2][8];           // [density][n]
     float c1_0, c2_0, nref_inv, rc;
@@ -139,9 +139,8 @@ struct Ctx {
     EamDev eam_h{};
     EamDev* eam_d = nullptr;
     bool energy_fresh = false;                           // energy pass done for the last forces
-    AceDev* ace_h = nullptr;
-    AceDev* ace_d = nullptr;
-    AceTc* ace_tc_d = nullptr;                           // tensor-core contraction tables
+    AceDev* ace_h = nullptr;                             // host coefficient tensors
+    AceTc* ace_tc_d = nullptr;                           // device ACE tables
     GridDev grid{};
     float4* D = nullptr;                                 // cell-offset vectors, FP32
     float4* Dlo = nullptr;                               // their FP32 residuals (o . cellvec - D)

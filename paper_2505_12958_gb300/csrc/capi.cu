@@ -319,7 +319,7 @@ void pinned_give(char* p) {
 
 void free_all(ap_ctx* xc) {
     ap::Ctx& c = xc->c;
-    void* ps[] = {c.eam_d, c.ace_d, c.D, c.Dlo, c.pos_lo, c.ace_A, c.ace_dA, c.x, c.v, c.xb, c.f, c.pos4, c.uxi, c.w, c.e_emb, c.e_eam, c.e_ace,
+    void* ps[] = {c.eam_d, c.ace_tc_d, c.D, c.Dlo, c.pos_lo, c.ace_A, c.ace_dA, c.x, c.v, c.xb, c.f, c.pos4, c.uxi, c.w, c.e_emb, c.e_eam, c.e_ace,
                   c.vir_eam, c.vir_ace, c.acc, c.fixed, c.w_fixed, c.cell, c.cell_count, c.cell_start,
                   c.cell_atoms, c.nbr, c.nnbr, c.ace_list, c.flags, c.d_time, c.partials, c.totals, c.e_atom,
                   c.pos_stage, c.f_stage, c.csp_sum, c.csp_under, c.csp_w0, c.csp_wnew, c.csp_seeds, c.csp_nseed,
@@ -503,7 +503,7 @@ size_t ap_footprint_bytes(const ap_potential* pot, int n_atoms, double ace_fract
                             4 + 4 + 4 + 4 + 8 + 3 * 8 + 3 * 4 + cap * 4;
     const size_t cells = 2 * sizeof(int) * ((size_t)n_atoms + 1);   // cell count/start (<= 1 per atom)
     const size_t nred = (size_t)(n_atoms + ap::kRedBlock - 1) / ap::kRedBlock + 1;
-    return (size_t)n_atoms * per_atom + cells + nred * 10 * 8 + 2 * 125 * 16 + sizeof(ap::AceDev) + sizeof(ap::AceTc) + 512 +
+    return (size_t)n_atoms * per_atom + cells + nred * 10 * 8 + 2 * 125 * 16 + sizeof(ap::AceTc) + 512 +
            sizeof(ap::EamDev) + (1u << 16);
 }
 
@@ -597,7 +597,7 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
     c.nred = (n + ap::kRedBlock - 1) / ap::kRedBlock;
     {
         ArenaPlan plan;
-        plan.add(&c.eam_d, 1); plan.add(&c.ace_d, 1); plan.add(&c.ace_tc_d, 1); plan.add(&c.D, 125); plan.add(&c.Dlo, 125);
+        plan.add(&c.eam_d, 1); plan.add(&c.ace_tc_d, 1); plan.add(&c.D, 125); plan.add(&c.Dlo, 125);
         plan.add(&c.pos_lo, N); plan.add(&c.x, 3 * N); plan.add(&c.v, 3 * N); plan.add(&c.xb, 3 * N);
         plan.add(&c.f, 3 * N); plan.add(&c.pos4, N); plan.add(&c.uxi, N); plan.add(&c.w, N);
         plan.add(&c.e_emb, N); plan.add(&c.e_eam, N); plan.add(&c.e_ace, N);
@@ -630,7 +630,6 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
         if (e == cudaSuccess) e = cudaMemsetAsync(dst, 0, bytes, c.stream);
     };
     cp(c.eam_d, &c.eam_h, sizeof(ap::EamDev));
-    cp(c.ace_d, c.ace_h, sizeof(ap::AceDev));
     std::unique_ptr<ap::AceTc> tc(new (std::nothrow) ap::AceTc());
     if (!tc) { c.err = "host allocation"; return fail(AP_ERR_OOM); }
     ap::build_ace_tc(*c.ace_h, *tc);

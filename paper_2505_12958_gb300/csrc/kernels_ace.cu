@@ -7,23 +7,21 @@
 //                      (FP32 FMA, 3xTF32 / BF16 / FP16 mma.sync, or FP64 accumulation);
 //                      A is written [atom][lm][n].
 //   k_ace_contract     phi_p = c_p0 + sum_v c_p[v] B_v, p = 1, 2 (B: one, two and three A
-//                      factors) with lanes over the 64 (n1, n2) pairs; three-factor products
-//                      as P[m3] = sum G A_n1 A_n2 (compile-time Gaunt pattern, operands in
-//                      registers) contracted with A_n3 and the coefficient tensor; then the
-//                      adjoint dE/dA with the combined coefficients c1 + c2 / (2 sqrt(phi2)):
-//                      first and second factors from the (n1, n2) mapping, the third from an
-//                      (n1, n3) mapping, lane partial sums reduced by butterfly shuffles in a
-//                      fixed order.  Writes dE/dA and E_i^ACE.
+//                      factors) and the adjoint dE/dA with the combined coefficients
+//                      c1 + c2 / (2 sqrt(phi2)): the Gaunt products of the first two factors
+//                      on FP32 lanes (one (n1, n2) pair per lane, compile-time coupling
+//                      pattern), their contractions with the coefficient matrices on tensor
+//                      cores (mma.sync, 3xTF32).  Writes dE/dA and E_i^ACE.
 //   k_ace_force        f_ij = dE_i/dr_ij = (1/nref) sum dE/dA_nlm grad(g_n Y_lm), weighted by
 //                      w_i, added to atom j (minus) and atom i (plus) through 64-bit fixed-point
 //                      atomics (2^-40 eV/A resolution), whose integer sums do not depend on order.
 // E_i^ACE is stored without the constant c1_0, which the blend adds in FP64.  The allocation-
-// free entry point at the end of the file runs the same arithmetic in one kernel.
+// free entry point at the end of the file runs the same per-atom device functions (neighbour
+// tiles, the contraction, the pair forces) in one kernel.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <cstdint>
-#include <cstdlib>
 #include <mutex>
 #include <string>
 #include <utility>
@@ -39,32 +37,7 @@ void upload_gaunt(const float* g) { cudaMemcpyToSymbol(c_gaunt, g, sizeof(float)
 
 namespace {
 
-// unroll factors of the contraction loops (tuning constants; results do not depend on them)
-#ifndef AP_N3_UNROLL
-#define AP_N3_UNROLL 2
-#endif
-#ifndef AP_PP_UNROLL
-#define AP_PP_UNROLL 1
-#endif
-constexpr int kN3Unroll = AP_N3_UNROLL;
-constexpr int kPPUnroll = AP_PP_UNROLL;
-#ifndef AP_J_UNROLL
-#define AP_J_UNROLL 1
-#endif
-constexpr int kJUnroll = AP_J_UNROLL;
-
-constexpr int kWarps = 8;
-constexpr int kTile = 32;
-
-struct WarpSmem {
-    float A[kNmax * kApad];
-    float dA[kNmax * kApad];
-    float dAT[kNLM][kNmax];
-    float4 nb[kAceNbrCap];
-    int nbj[kAceNbrCap];
-    float tileY[kTile][kNLM];
-    float tileG[kTile][kNmax];
-};
+constexpr int kTile = 32;                      // neighbours per basis tile (one per lane)
 
 // ---------------------------------------------------------------------------------
 // radial basis g_n = T_n(2r/rc - 1) fc(r), fc = (1 + cos(pi r/rc))/2, and dg_n/dr
@@ -237,19 +210,6 @@ __device__ __forceinline__ void all_x(float* d1, float* d2, const float* A1, con
     (ent_x<T, E>(d1, d2, A1, A2, Q, u), ...);
 }
 
-template <int T, int E>
-__device__ __forceinline__ void ent_y(float* d3, const float* A1, const float* Tm, float& t) {
-    using R = Tri<T>;
-    constexpr int i1 = R::template m1<E>(), i2 = R::template m2<E>(), i3 = R::template m3<E>();
-    if constexpr (R::template first12<E>()) t = A1[i1] * Tm[i2];
-    d3[i3] = fmaf(c_gaunt[R::OFF + E], t, d3[i3]);
-}
-template <int T, int... E>
-__device__ __forceinline__ void all_y(float* d3, const float* A1, const float* Tm, std::integer_sequence<int, E...>) {
-    float t = 0.0f;
-    (ent_y<T, E>(d3, A1, Tm, t), ...);
-}
-
 template <int W>
 __device__ __forceinline__ void load_row(float* dst, const float* src) {
 #pragma unroll
@@ -260,532 +220,6 @@ __device__ __forceinline__ void load_row(float* dst, const float* src) {
         if (k + 2 < W) dst[k + 2] = v.z;
         if (k + 3 < W) dst[k + 3] = v.w;
     }
-}
-
-// sum_k P[k] * row[k] over a 16-byte aligned shared-memory row
-template <int W>
-__device__ __forceinline__ float dot_row(const float* P, const float* row) {
-    float r = 0.0f;
-#pragma unroll
-    for (int k = 0; k < W; k += 4) {
-        float4 v = *reinterpret_cast<const float4*>(row + k);
-        r = fmaf(P[k], v.x, r);
-        if (k + 1 < W) r = fmaf(P[k + 1], v.y, r);
-        if (k + 2 < W) r = fmaf(P[k + 2], v.z, r);
-        if (k + 3 < W) r = fmaf(P[k + 3], v.w, r);
-    }
-    return r;
-}
-
-// sum_k P[k] * row[k] over a 16-byte aligned shared-memory row, two accumulator chains
-template <int W>
-__device__ __forceinline__ float dot_row2(const float* P, const float* row) {
-    float r0 = 0.0f, r1 = 0.0f;
-#pragma unroll
-    for (int k = 0; k < W; k += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(row + k);
-        r0 = fmaf(P[k], v.x, r0);
-        if (k + 1 < W) r1 = fmaf(P[k + 1], v.y, r1);
-        if (k + 2 < W) r0 = fmaf(P[k + 2], v.z, r0);
-        if (k + 3 < W) r1 = fmaf(P[k + 3], v.w, r1);
-    }
-    return r0 + r1;
-}
-
-// Q[k] += ce * row[k] over a 16-byte aligned shared-memory row (one broadcast load per 4 FMA)
-template <int W>
-__device__ __forceinline__ void axpy_row(float* Q, float ce, const float* row) {
-#pragma unroll
-    for (int k = 0; k < W; k += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(row + k);
-        Q[k] = fmaf(ce, v.x, Q[k]);
-        if (k + 1 < W) Q[k + 1] = fmaf(ce, v.y, Q[k + 1]);
-        if (k + 2 < W) Q[k + 2] = fmaf(ce, v.z, Q[k + 2]);
-        if (k + 3 < W) Q[k + 3] = fmaf(ce, v.w, Q[k + 3]);
-    }
-}
-
-// Pa . row and Pb . row over a 16-byte aligned shared-memory row: one broadcast load serves
-// both products; each keeps the two accumulator chains (even and odd k) of dot_row2
-template <int W>
-__device__ __forceinline__ void dot_row2_x2(const float* Pa, const float* Pb, const float* row, float& ra, float& rb) {
-    float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
-#pragma unroll
-    for (int k = 0; k < W; k += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(row + k);
-        a0 = fmaf(Pa[k], v.x, a0);
-        b0 = fmaf(Pb[k], v.x, b0);
-        if (k + 1 < W) { a1 = fmaf(Pa[k + 1], v.y, a1); b1 = fmaf(Pb[k + 1], v.y, b1); }
-        if (k + 2 < W) { a0 = fmaf(Pa[k + 2], v.z, a0); b0 = fmaf(Pb[k + 2], v.z, b0); }
-        if (k + 3 < W) { a1 = fmaf(Pa[k + 3], v.w, a1); b1 = fmaf(Pb[k + 3], v.w, b1); }
-    }
-    ra = a0 + a1;
-    rb = b0 + b1;
-}
-
-// Qa[k] += ca * row[k], Qb[k] += cb * row[k]: one broadcast load per 8 FMA
-template <int W>
-__device__ __forceinline__ void axpy_row_x2(float* Qa, float* Qb, float ca, float cb, const float* row) {
-#pragma unroll
-    for (int k = 0; k < W; k += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(row + k);
-        Qa[k] = fmaf(ca, v.x, Qa[k]);
-        Qb[k] = fmaf(cb, v.x, Qb[k]);
-        if (k + 1 < W) { Qa[k + 1] = fmaf(ca, v.y, Qa[k + 1]); Qb[k + 1] = fmaf(cb, v.y, Qb[k + 1]); }
-        if (k + 2 < W) { Qa[k + 2] = fmaf(ca, v.z, Qa[k + 2]); Qb[k + 2] = fmaf(cb, v.z, Qb[k + 2]); }
-        if (k + 3 < W) { Qa[k + 3] = fmaf(ca, v.w, Qa[k + 3]); Qb[k + 3] = fmaf(cb, v.w, Qb[k + 3]); }
-    }
-}
-
-// The two (n1, n2) pairs of a lane and the n3 / n2 contractions are runtime loops; only the
-// Gaunt entries are unrolled (their operands are register-indexed), which keeps the code
-// of all 14 l-triples small enough for the instruction cache.
-
-// forward of one (n1, n2) pair: P[m3] = sum G A_n1 A_n2, then sum_n3 c_p[n1 n2 n3] P . A_n3
-template <int T>
-__device__ __forceinline__ void nu3_forward_pair(const float* As, const AceDev& C, int n1, int n2, float& p1,
-                                                 float& p2) {
-    using R = Tri<T>;
-    const int q = n1 * 8 + n2;
-    float A1[R::W1], A2[R::W2], P[R::W3];
-    load_row<R::W1>(A1, As + n1 * kApad + R::B1);
-    load_row<R::W2>(A2, As + n2 * kApad + R::B2);
-#pragma unroll
-    for (int k = 0; k < R::W3; ++k) P[k] = 0.0f;
-    all_p<T>(P, A1, A2, std::make_integer_sequence<int, R::N>{});
-    const float* c1 = &C.c3[0][T][0][q];
-    const float* c2 = &C.c3[1][T][0][q];
-    float s1 = 0.0f, s2 = 0.0f;
-#pragma unroll kN3Unroll
-    for (int n3 = 0; n3 < kNmax; ++n3) {
-        const float r = dot_row2<R::W3>(P, As + n3 * kApad + R::B3);
-        s1 = fmaf(c1[n3 * 65], r, s1);
-        s2 = fmaf(c2[n3 * 65], r, s2);
-    }
-    p1 += s1;
-    p2 += s2;
-}
-
-// forward of a lane's two pairs (n1, n2) and (n1 + 4, n2), one after the other
-template <int T>
-__device__ __forceinline__ void nu3_forward_seq(const float* As, const AceDev& C, int lane, float& p1, float& p2) {
-#pragma unroll kPPUnroll
-    for (int pp = 0; pp < 2; ++pp) {
-        const int q = lane + 32 * pp;
-        nu3_forward_pair<T>(As, C, q >> 3, q & 7, p1, p2);
-    }
-}
-
-// the same two pairs together: they share the A_n2 row and every A_n3 row, so each
-// broadcast row load serves both (the contraction is bound by shared-memory bandwidth).
-// The sums keep the order of evaluating the pairs one after the other (identical bits).
-template <int T>
-__device__ __forceinline__ void nu3_forward_joint(const float* As, const AceDev& C, int lane, float& p1, float& p2) {
-    using R = Tri<T>;
-    const int n1 = lane >> 3, n2 = lane & 7, q = lane;
-    float Pa[R::W3], Pb[R::W3];
-    {
-        float A2[R::W2];
-        load_row<R::W2>(A2, As + n2 * kApad + R::B2);
-        // one copy of the unrolled Gaunt code for both pairs (instruction cache)
-#pragma unroll 1
-        for (int pp = 0; pp < 2; ++pp) {
-            float A1[R::W1];
-            load_row<R::W1>(A1, As + (n1 + 4 * pp) * kApad + R::B1);
-#pragma unroll
-            for (int k = 0; k < R::W3; ++k) Pb[k] = 0.0f;
-            all_p<T>(Pb, A1, A2, std::make_integer_sequence<int, R::N>{});
-            if (pp == 0) {
-#pragma unroll
-                for (int k = 0; k < R::W3; ++k) Pa[k] = Pb[k];
-            }
-        }
-    }
-    const float* c1 = &C.c3[0][T][0][q];
-    const float* c2 = &C.c3[1][T][0][q];
-    float a1 = 0.0f, a2 = 0.0f, b1 = 0.0f, b2 = 0.0f;
-#pragma unroll kJUnroll
-    for (int n3 = 0; n3 < kNmax; ++n3) {
-        float ra, rb;
-        dot_row2_x2<R::W3>(Pa, Pb, As + n3 * kApad + R::B3, ra, rb);
-        a1 = fmaf(c1[n3 * 65], ra, a1);
-        a2 = fmaf(c2[n3 * 65], ra, a2);
-        b1 = fmaf(c1[n3 * 65 + 32], rb, b1);
-        b2 = fmaf(c2[n3 * 65 + 32], rb, b2);
-    }
-    p1 += a1;
-    p2 += a2;
-    p1 += b1;
-    p2 += b2;
-}
-
-// joint where the two P rows fit the register budget of two blocks per SM (W3 <= 7; the
-// l3 = 4 triples would spill)
-template <int T>
-__device__ __forceinline__ void nu3_forward(const float* As, const AceDev& C, int lane, float& p1, float& p2) {
-    if constexpr (Tri<T>::W3 <= 7) nu3_forward_joint<T>(As, C, lane, p1, p2);
-    else nu3_forward_seq<T>(As, C, lane, p1, p2);
-}
-
-// adjoint of one (n1, n2) pair with respect to its first two factors:
-// Q[m3] = sum_n3 (c1 + s c2)[n1 n2 n3] A_n3, then d1 += G Q A_n2, d2 += G Q A_n1
-template <int T>
-__device__ __forceinline__ void nu3_adjoint_x_pair(const float* As, const AceDev& C, float s, int n1, int n2,
-                                                   float* d1, float* d2) {
-    using R = Tri<T>;
-    const int q = n1 * 8 + n2;
-    float A1[R::W1], A2[R::W2], Q[R::W3];
-    load_row<R::W1>(A1, As + n1 * kApad + R::B1);
-    load_row<R::W2>(A2, As + n2 * kApad + R::B2);
-#pragma unroll
-    for (int m = 0; m < R::W3; ++m) Q[m] = 0.0f;
-    const float* c1 = &C.c3[0][T][0][q];
-    const float* c2 = &C.c3[1][T][0][q];
-#pragma unroll kN3Unroll
-    for (int n3 = 0; n3 < kNmax; ++n3) {
-        const float ce = fmaf(s, c2[n3 * 65], c1[n3 * 65]);
-        axpy_row<R::W3>(Q, ce, As + n3 * kApad + R::B3);
-    }
-    all_x<T>(d1, d2, A1, A2, Q, std::make_integer_sequence<int, R::N>{});
-}
-
-// (n1, n2) mapping: gradients with respect to the first and second factor.  A lane's two
-// pairs (n1, n2) and (n1 + 4, n2) run together: their Q rows share every A_n3 row load.
-// The sums keep the order of evaluating the pairs one after the other.
-template <int T>
-__device__ __forceinline__ void nu3_adjoint_x(const float* As, float* dAs, const AceDev& C, float s, int lane) {
-    using R = Tri<T>;
-    const int n1 = lane >> 3, n2 = lane & 7, q = lane;
-    float Qa[R::W3], Qb[R::W3];
-#pragma unroll
-    for (int m = 0; m < R::W3; ++m) { Qa[m] = 0.0f; Qb[m] = 0.0f; }
-    const float* c1 = &C.c3[0][T][0][q];
-    const float* c2 = &C.c3[1][T][0][q];
-#pragma unroll kJUnroll
-    for (int n3 = 0; n3 < kNmax; ++n3) {
-        const float ca = fmaf(s, c2[n3 * 65], c1[n3 * 65]);
-        const float cb = fmaf(s, c2[n3 * 65 + 32], c1[n3 * 65 + 32]);
-        axpy_row_x2<R::W3>(Qa, Qb, ca, cb, As + n3 * kApad + R::B3);
-    }
-    float d2[R::W2];
-#pragma unroll
-    for (int k = 0; k < R::W2; ++k) d2[k] = 0.0f;
-#pragma unroll 1
-    for (int pp = 0; pp < 2; ++pp) {
-        const int r1 = n1 + 4 * pp;
-        float A1[R::W1], A2[R::W2], d1[R::W1];
-        load_row<R::W1>(A1, As + r1 * kApad + R::B1);
-        load_row<R::W2>(A2, As + n2 * kApad + R::B2);
-#pragma unroll
-        for (int k = 0; k < R::W1; ++k) d1[k] = 0.0f;
-        float Qt[R::W3];
-#pragma unroll
-        for (int m = 0; m < R::W3; ++m) Qt[m] = pp ? Qb[m] : Qa[m];
-        all_x<T>(d1, d2, A1, A2, Qt, std::make_integer_sequence<int, R::N>{});
-#pragma unroll
-        for (int k = 0; k < R::W1; ++k) {
-            float v = d1[k];
-            v += __shfl_xor_sync(0xffffffffu, v, 1);
-            v += __shfl_xor_sync(0xffffffffu, v, 2);
-            v += __shfl_xor_sync(0xffffffffu, v, 4);
-            d1[k] = v;
-        }
-        if ((lane & 7) == 0) {
-#pragma unroll
-            for (int k = 0; k < R::W1; ++k) dAs[r1 * kApad + R::B1 + k] += d1[k];
-        }
-        __syncwarp();
-    }
-#pragma unroll
-    for (int k = 0; k < R::W2; ++k) {
-        float v = d2[k];
-        v += __shfl_xor_sync(0xffffffffu, v, 8);
-        v += __shfl_xor_sync(0xffffffffu, v, 16);
-        d2[k] = v;
-    }
-    if (lane < 8) {
-#pragma unroll
-        for (int k = 0; k < R::W2; ++k) dAs[lane * kApad + R::B2 + k] += d2[k];
-    }
-    __syncwarp();
-}
-
-// (n1, n3) mapping: gradient with respect to the third factor; a lane's two pairs (n1, n3)
-// and (n1 + 4, n3) one after the other
-template <int T>
-__device__ __forceinline__ void nu3_adjoint_y_seq(const float* As, float* dAs, const AceDev& C, float s, int lane) {
-    using R = Tri<T>;
-    float d3[R::W3];
-#pragma unroll
-    for (int k = 0; k < R::W3; ++k) d3[k] = 0.0f;
-#pragma unroll kPPUnroll
-    for (int pp = 0; pp < 2; ++pp) {
-        const int q = lane + 32 * pp, n1 = q >> 3, n3 = q & 7;
-        float A1[R::W1], Tm[R::W2];
-        load_row<R::W1>(A1, As + n1 * kApad + R::B1);
-#pragma unroll
-        for (int m = 0; m < R::W2; ++m) Tm[m] = 0.0f;
-#pragma unroll kN3Unroll
-        for (int n2 = 0; n2 < kNmax; ++n2) {
-            const float ce = fmaf(s, C.c3[1][T][n3][n1 * 8 + n2], C.c3[0][T][n3][n1 * 8 + n2]);
-            axpy_row<R::W2>(Tm, ce, As + n2 * kApad + R::B2);
-        }
-        all_y<T>(d3, A1, Tm, std::make_integer_sequence<int, R::N>{});
-    }
-#pragma unroll
-    for (int k = 0; k < R::W3; ++k) {
-        float v = d3[k];
-        v += __shfl_xor_sync(0xffffffffu, v, 8);
-        v += __shfl_xor_sync(0xffffffffu, v, 16);
-        d3[k] = v;
-    }
-    if (lane < 8) {
-#pragma unroll
-        for (int k = 0; k < R::W3; ++k) dAs[lane * kApad + R::B3 + k] += d3[k];
-    }
-    __syncwarp();
-}
-
-// the same two pairs together: their Tm rows share every A_n2 row load (identical bits)
-template <int T>
-__device__ __forceinline__ void nu3_adjoint_y_joint(const float* As, float* dAs, const AceDev& C, float s, int lane) {
-    using R = Tri<T>;
-    const int n1 = lane >> 3, n3 = lane & 7;
-    float Ta[R::W2], Tb[R::W2];
-#pragma unroll
-    for (int m = 0; m < R::W2; ++m) { Ta[m] = 0.0f; Tb[m] = 0.0f; }
-    const float* c1 = &C.c3[0][T][n3][n1 * 8];
-    const float* c2 = &C.c3[1][T][n3][n1 * 8];
-#pragma unroll kJUnroll
-    for (int n2 = 0; n2 < kNmax; ++n2) {
-        const float ca = fmaf(s, c2[n2], c1[n2]);
-        const float cb = fmaf(s, c2[n2 + 32], c1[n2 + 32]);
-        axpy_row_x2<R::W2>(Ta, Tb, ca, cb, As + n2 * kApad + R::B2);
-    }
-    float d3[R::W3];
-#pragma unroll
-    for (int k = 0; k < R::W3; ++k) d3[k] = 0.0f;
-#pragma unroll 1
-    for (int pp = 0; pp < 2; ++pp) {
-        float A1[R::W1], Tt[R::W2];
-        load_row<R::W1>(A1, As + (n1 + 4 * pp) * kApad + R::B1);
-#pragma unroll
-        for (int m = 0; m < R::W2; ++m) Tt[m] = pp ? Tb[m] : Ta[m];
-        all_y<T>(d3, A1, Tt, std::make_integer_sequence<int, R::N>{});
-    }
-#pragma unroll
-    for (int k = 0; k < R::W3; ++k) {
-        float v = d3[k];
-        v += __shfl_xor_sync(0xffffffffu, v, 8);
-        v += __shfl_xor_sync(0xffffffffu, v, 16);
-        d3[k] = v;
-    }
-    if (lane < 8) {
-#pragma unroll
-        for (int k = 0; k < R::W3; ++k) dAs[lane * kApad + R::B3 + k] += d3[k];
-    }
-    __syncwarp();
-}
-
-// joint where the two Tm rows fit the register budget of two blocks per SM: W2 <= 5 (wider
-// rows measured slower or spilled)
-template <int T>
-__device__ __forceinline__ void nu3_adjoint_y(const float* As, float* dAs, const AceDev& C, float s, int lane) {
-    if constexpr (Tri<T>::W2 <= 5) nu3_adjoint_y_joint<T>(As, dAs, C, s, lane);
-    else nu3_adjoint_y_seq<T>(As, dAs, C, s, lane);
-}
-
-template <int T>
-__device__ __forceinline__ void nu3_adjoint(const float* As, float* dAs, const AceDev& C, float s, int lane) {
-    nu3_adjoint_x<T>(As, dAs, C, s, lane);
-    nu3_adjoint_y<T>(As, dAs, C, s, lane);
-}
-
-// ---------------------------------------------------------------------------------
-// l-triples with l1 = l2 carry only the (n1 <= n2) pairs, 36 of the 64 (the coefficients
-// of the others are zero).  k_ace_contract evaluates 32 of them in one lane pass and
-// leaves the four diagonal pairs (4,4) ... (7,7) to "diagonal units": one warp of the
-// block (the triple's unit warp) runs a second trip through the same code that takes the
-// triple's diagonal pairs for all eight atoms of the block, lane (slot, k) = (lane / 4,
-// lane % 4) taking atom slot's pair (4 + k, 4 + k).
-// ---------------------------------------------------------------------------------
-constexpr int kDiag = 6;                       // l-triples with l1 = l2
-
-// folded lane mapping of the (n1 <= n2) pairs: lane (a, b) = (lane / 8, lane % 8) takes
-// (a, b) when b >= a (every pair of rows 0-3) and (7 - a, 7 - b) otherwise (the
-// off-diagonal pairs of rows 4-7)
-__device__ __forceinline__ void folded_pair(int lane, int& n1, int& n2, bool& lo) {
-    const int a = lane >> 3, b = lane & 7;
-    lo = b >= a;
-    n1 = lo ? a : 7 - a;
-    n2 = lo ? b : 7 - b;
-}
-
-// 2368 bytes: the 64-byte pad puts the A of neighbouring warps 4 bank groups apart, so a
-// diagonal unit's lanes (8 atoms, one row each) read without bank conflicts
-struct ContractSmem {
-    float A[kNmax * kApad];
-    float dA[kNmax * kApad];
-    float pad[16];
-};
-
-constexpr int kContractWarps = 8;              // atoms of the block per iteration (one per warp)
-
-// block-shared state of the diagonal units
-struct DiagSmem {
-    float pm[kContractWarps][2];               // phi1, phi2 sums of each warp's own passes
-    float lf[kDiag][kContractWarps][2];        // diagonal-unit sums per l1 = l2 triple and atom
-    float ldA[kContractWarps][4][kApad + 1];   // diagonal-unit gradients, rows n = 4..7 (odd stride:
-                                               // the 32 lanes of a unit write 32 different banks)
-};
-
-static_assert(sizeof(AceDev) % 16 == 0 && sizeof(ContractSmem) % 128 == 64,
-              "A rows 16-byte aligned, warps 4 bank groups apart");
-
-// phi1, phi2 sums of atom slot, in a fixed order (every reader computes the same bits)
-__device__ __forceinline__ float2 phi_sums(const DiagSmem& D, int slot) {
-    float p1 = D.pm[slot][0], p2 = D.pm[slot][1];
-#pragma unroll
-    for (int u = 0; u < kDiag; ++u) {
-        p1 += D.lf[u][slot][0];
-        p2 += D.lf[u][slot][1];
-    }
-    return make_float2(p1, p2);
-}
-
-__device__ __forceinline__ bool phi_ok(const AceDev& C, float2 P) { return C.c2_0 + P.y > 1e-3f && P.x == P.x; }
-
-// unit index u of the l1 = l2 triples (0,0,0) (1,1,2) (2,2,2) (2,2,4) (3,3,4) (4,4,4), and the
-// warp that runs unit u; the two l = 2 triples write the same rows of ldA and share a warp
-__host__ __device__ constexpr int diag_unit_of(int t) {
-    return t == 0 ? 0 : t == 5 ? 1 : t == 8 ? 2 : t == 9 ? 3 : t == 12 ? 4 : 5;
-}
-__host__ __device__ constexpr int diag_warp(int u) { return u == 5 ? 0 : u == 4 ? 1 : u == 3 || u == 2 ? 2 : u == 1 ? 3 : 4; }
-
-// phi sums of the forward: an l1 = l2 triple's folded pass, and on its unit warp a second
-// trip through the same code for the diagonal pairs of the block's 8 atoms (lane (slot, k)
-// = (lane / 4, lane % 4) takes atom slot's pair (4 + k, 4 + k))
-template <int T>
-__device__ __forceinline__ void nu3_forward_main(const ContractSmem* WS, const float* As, const AceDev& C, DiagSmem& D,
-                                                 int warp, int lane, float& p1, float& p2) {
-    using R = Tri<T>;
-    if constexpr (R::L1 == R::L2) {
-        constexpr int U = diag_unit_of(T);
-        int n1, n2;
-        bool lo;
-        folded_pair(lane, n1, n2, lo);
-        const int slot = lane >> 2, nd = 4 + (lane & 3);
-        const int trips = warp == diag_warp(U) ? 2 : 1;
-#pragma unroll 1
-        for (int t = 0; t < trips; ++t) {
-            float a1 = 0.0f, a2 = 0.0f;
-            nu3_forward_pair<T>(t ? WS[slot].A : As, C, t ? nd : n1, t ? nd : n2, a1, a2);
-            if (t == 0) {
-                p1 += a1;
-                p2 += a2;
-            } else {
-                a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
-                a2 += __shfl_xor_sync(0xffffffffu, a2, 1);
-                a1 += __shfl_xor_sync(0xffffffffu, a1, 2);
-                a2 += __shfl_xor_sync(0xffffffffu, a2, 2);
-                if ((lane & 3) == 0) { D.lf[U][slot][0] = a1; D.lf[U][slot][1] = a2; }
-            }
-        }
-    } else {
-        nu3_forward<T>(As, C, lane, p1, p2);
-    }
-}
-
-// first- and second-factor gradients of the folded pass.  Both go to the same l-block.
-// Row sums: d1 of group a (8 lanes) belongs to row a (lo lanes) or 7 - a (hi lanes); d2 of
-// column b (4 lanes) to row b (lo) or 7 - b (hi).  Lane (a, b) with a = min(b, 7 - b)
-// gathers everything of row b and is its only writer.
-// On the triple's unit warp a second trip through the same code takes the diagonal pairs
-// of the block's 8 atoms, each lane with its atom's scale s, and adds their gradients
-// (both to row n) to the block's ldA rows.
-template <int T>
-__device__ __forceinline__ void nu3_adjoint_x_folded(const ContractSmem* WS, const float* As, float* dAs,
-                                                     const AceDev& C, DiagSmem& D, float s, float s_slot, int warp,
-                                                     int lane) {
-    using R = Tri<T>;
-    static_assert(R::L1 == R::L2, "folded pass needs l1 = l2");
-    constexpr int W = R::W1;
-    constexpr int U = diag_unit_of(T);
-    int n1, n2;
-    bool lo;
-    folded_pair(lane, n1, n2, lo);
-    const int slot = lane >> 2, kd = lane & 3, nd = 4 + kd;
-    const int trips = warp == diag_warp(U) ? 2 : 1;
-#pragma unroll 1
-    for (int t = 0; t < trips; ++t) {
-        float d1[W], d2[W];
-#pragma unroll
-        for (int k = 0; k < W; ++k) { d1[k] = 0.0f; d2[k] = 0.0f; }
-        nu3_adjoint_x_pair<T>(t ? WS[slot].A : As, C, t ? s_slot : s, t ? nd : n1, t ? nd : n2, d1, d2);
-        if (t) {
-#pragma unroll
-            for (int m = 0; m < W; ++m) D.ldA[slot][kd][R::B1 + m] += d1[m] + d2[m];
-        } else {
-            const int b = lane & 7;
-            const bool low_row = b < 4;
-            const bool owner = (lane >> 3) == (low_row ? b : 7 - b);
-#pragma unroll
-            for (int k = 0; k < W; ++k) {
-                float u = lo ? d1[k] : 0.0f, v = lo ? 0.0f : d1[k];
-                float x = lo ? d2[k] : 0.0f, y = lo ? 0.0f : d2[k];
-                u += __shfl_xor_sync(0xffffffffu, u, 1);
-                v += __shfl_xor_sync(0xffffffffu, v, 1);
-                u += __shfl_xor_sync(0xffffffffu, u, 2);
-                v += __shfl_xor_sync(0xffffffffu, v, 2);
-                u += __shfl_xor_sync(0xffffffffu, u, 4);
-                v += __shfl_xor_sync(0xffffffffu, v, 4);
-                x += __shfl_xor_sync(0xffffffffu, x, 8);
-                y += __shfl_xor_sync(0xffffffffu, y, 8);
-                x += __shfl_xor_sync(0xffffffffu, x, 16);
-                y += __shfl_xor_sync(0xffffffffu, y, 16);
-                y = __shfl_xor_sync(0xffffffffu, y, 7);       // column 7 - b's hi sum belongs to row b
-                d1[k] = (low_row ? u : v) + x + y;
-            }
-            if (owner) {
-#pragma unroll
-                for (int k = 0; k < W; ++k) dAs[b * kApad + R::B1 + k] += d1[k];
-            }
-            __syncwarp();
-        }
-    }
-}
-
-template <int T>
-__device__ __forceinline__ void nu3_adjoint_main(const ContractSmem* WS, const float* As, float* dAs, const AceDev& C,
-                                                 DiagSmem& D, float s, float s_slot, int warp, int lane) {
-    using R = Tri<T>;
-    if constexpr (R::L1 == R::L2) nu3_adjoint_x_folded<T>(WS, As, dAs, C, D, s, s_slot, warp, lane);
-    else nu3_adjoint_x<T>(As, dAs, C, s, lane);
-    nu3_adjoint_y<T>(As, dAs, C, s, lane);
-}
-
-template <int... T>
-__device__ __forceinline__ void nu3_forward_all(const float* As, const AceDev& C, int lane, float& p1, float& p2,
-                                                std::integer_sequence<int, T...>) {
-    (nu3_forward<T>(As, C, lane, p1, p2), ...);
-}
-template <int... T>
-__device__ __forceinline__ void nu3_adjoint_all(const float* As, float* dAs, const AceDev& C, float s, int lane,
-                                                std::integer_sequence<int, T...>) {
-    (nu3_adjoint<T>(As, dAs, C, s, lane), ...);
-}
-
-template <int... T>
-__device__ __forceinline__ void nu3_forward_main_all(const ContractSmem* WS, const float* As, const AceDev& C,
-                                                     DiagSmem& D, int warp, int lane, float& p1, float& p2,
-                                                     std::integer_sequence<int, T...>) {
-    (nu3_forward_main<T>(WS, As, C, D, warp, lane, p1, p2), ...);
-}
-template <int... T>
-__device__ __forceinline__ void nu3_adjoint_main_all(const ContractSmem* WS, const float* As, float* dAs,
-                                                     const AceDev& C, DiagSmem& D, float s, float s_slot, int warp,
-                                                     int lane, std::integer_sequence<int, T...>) {
-    (nu3_adjoint_main<T>(WS, As, dAs, C, D, s, s_slot, warp, lane), ...);
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -881,13 +315,70 @@ __device__ __forceinline__ void mma_16bit(float* d, uint32_t a0, uint32_t a1, ui
 // element (row lm, column j) of the A operand Y^T; rows 25..31 are padding
 __device__ __forceinline__ float yt(const BasisSmem& S, int lm, int j) { return lm < kNLM ? S.tileY[j][lm] : 0.0f; }
 
+// g_n and Y_lm of the neighbours t0 .. t0 + 31 of the list nb (zeros beyond cnt), one per
+// lane, into the tile rows
+__device__ __forceinline__ void basis_tile(const float4* nb, int t0, int cnt, float rc, float (*tileY)[kNLM],
+                                           float (*tileG)[kNmax], int lane) {
+    const int jj = t0 + lane;
+    float g[kNmax], dg[kNmax], Y[kNLM];
+    if (jj < cnt) {
+        const float4 v = nb[jj];
+        const float ri = 1.0f / v.w;
+        radial(v.w, rc, g, dg);
+        ylm(v.x * ri, v.y * ri, v.z * ri, Y);
+    } else {
+#pragma unroll
+        for (int q = 0; q < kNmax; ++q) g[q] = 0.0f;
+#pragma unroll
+        for (int q = 0; q < kNLM; ++q) Y[q] = 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < kNmax; ++q) tileG[lane][q] = g[q];
+#pragma unroll
+    for (int q = 0; q < kNLM; ++q) tileY[lane][q] = Y[q];
+}
+
+// accA[n] += sum_j Y_lm(j) g_n(j) over the first nt tile rows, lane = lm < 25 (FP32 FMA)
+__device__ __forceinline__ void basis_accum_fp32(const float (*tileY)[kNLM], const float (*tileG)[kNmax], int nt,
+                                                 int lane, float* accA) {
+    if (lane >= kNLM) return;
+    for (int jj2 = 0; jj2 < nt; ++jj2) {
+        const float y = tileY[jj2][lane];
+        const float4 g0 = *reinterpret_cast<const float4*>(&tileG[jj2][0]);
+        const float4 g1 = *reinterpret_cast<const float4*>(&tileG[jj2][4]);
+        const float gg[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+#pragma unroll
+        for (int q = 0; q < kNmax; ++q) accA[q] = fmaf(y, gg[q], accA[q]);
+    }
+}
+
+// w_i f_ij with f_ij = dE_i/dr_ij = (1/nref) sum_nlm dE/dA_nlm grad(g_n Y_lm) for the pair
+// vector v = (r_ij, |r_ij|); dAT[lm][n] is dE/dA of atom i
+__device__ __forceinline__ float3 ace_pair_force(float4 v, float rc, float nrefi, float wi,
+                                                 const float (*dAT)[kNmax]) {
+    const float ri = 1.0f / v.w;
+    const float ux = v.x * ri, uy = v.y * ri, uz = v.z * ri;
+    float g[kNmax], dg[kNmax];
+    radial(v.w, rc, g, dg);
+    float sc = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+    auto ab = [&](int lm, float& aa, float& bb) {
+        const float4 d0 = *reinterpret_cast<const float4*>(&dAT[lm][0]);
+        const float4 d1 = *reinterpret_cast<const float4*>(&dAT[lm][4]);
+        aa = d0.x * g[0] + d0.y * g[1] + d0.z * g[2] + d0.w * g[3] + d1.x * g[4] + d1.y * g[5] + d1.z * g[6] + d1.w * g[7];
+        bb = d0.x * dg[0] + d0.y * dg[1] + d0.z * dg[2] + d0.w * dg[3] + d1.x * dg[4] + d1.y * dg[5] + d1.z * dg[6] + d1.w * dg[7];
+    };
+    force_terms(ux, uy, uz, ri, ab, sc, gx, gy, gz);
+    return make_float3(nrefi * (sc * ux + gx * ri) * wi, nrefi * (sc * uy + gy * ri) * wi,
+                       nrefi * (sc * uz + gz * ri) * wi);
+}
+
 // stage a1 of the ACE pass: A_nlm = (1/nref) sum_j g_n(r_ij) Y_lm(rhat_ij), stored [atom][lm][n].
 // MODE (AP_ACE_*) sets the precision of the contraction over neighbours: FP32 FMA, tensor
 // cores (3xTF32 split, BF16 or FP16 inputs; FP32 accumulation), or FP64 accumulation.
 template <int MODE>
 __global__ void __launch_bounds__(256) k_ace_basis(const float4* __restrict__ pos4, const int* __restrict__ nbr,
                                                    const int* __restrict__ nnbr, int n, const float4* __restrict__ Dtab,
-                                                   int ncode, const AceDev* __restrict__ tab,
+                                                   int ncode, const AceTc* __restrict__ tab,
                                                    const int* __restrict__ ace_list, int* __restrict__ flags,
                                                    float* __restrict__ Aout) {
     __shared__ float4 Ds[125];
@@ -917,39 +408,20 @@ __global__ void __launch_bounds__(256) k_ace_basis(const float4* __restrict__ po
 #pragma unroll
         for (int q = 0; q < 8; ++q) acc_tc[q >> 2][q & 3] = 0.0f;
         for (int t0 = 0; t0 < cnt; t0 += kTile) {
-            const int jj = t0 + lane;
-            float g[kNmax], dg[kNmax], Y[kNLM];
-            if (jj < cnt) {
-                const float4 v = S.nb[jj];
-                const float ri = 1.0f / v.w;
-                radial(v.w, rc, g, dg);
-                ylm(v.x * ri, v.y * ri, v.z * ri, Y);
-            } else {
-#pragma unroll
-                for (int q = 0; q < kNmax; ++q) g[q] = 0.0f;
-#pragma unroll
-                for (int q = 0; q < kNLM; ++q) Y[q] = 0.0f;
-            }
-#pragma unroll
-            for (int q = 0; q < kNmax; ++q) S.tileG[lane][q] = g[q];
-#pragma unroll
-            for (int q = 0; q < kNLM; ++q) S.tileY[lane][q] = Y[q];
+            basis_tile(S.nb, t0, cnt, rc, S.tileY, S.tileG, lane);
             __syncwarp();
             const int nt = min(kTile, cnt - t0);
-            if (MODE == AP_ACE_FP32 || MODE == AP_ACE_FP64) {
+            if (MODE == AP_ACE_FP32) {
+                basis_accum_fp32(S.tileY, S.tileG, nt, lane, accA);
+            } else if (MODE == AP_ACE_FP64) {
                 if (lane < kNLM) {
                     for (int jj2 = 0; jj2 < nt; ++jj2) {
                         const float y = S.tileY[jj2][lane];
                         const float4 g0 = *reinterpret_cast<const float4*>(&S.tileG[jj2][0]);
                         const float4 g1 = *reinterpret_cast<const float4*>(&S.tileG[jj2][4]);
                         const float gg[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
-                        if (MODE == AP_ACE_FP64) {
 #pragma unroll
-                            for (int q = 0; q < kNmax; ++q) accD[q] = fma((double)y, (double)gg[q], accD[q]);
-                        } else {
-#pragma unroll
-                            for (int q = 0; q < kNmax; ++q) accA[q] = fmaf(y, gg[q], accA[q]);
-                        }
+                        for (int q = 0; q < kNmax; ++q) accD[q] = fma((double)y, (double)gg[q], accD[q]);
                     }
                 }
             } else if (MODE == AP_ACE_TC_TF32X3) {
@@ -1020,256 +492,6 @@ __global__ void __launch_bounds__(256) k_ace_basis(const float4* __restrict__ po
         }
     }
 }
-
-// stage a5/a6 core: phi1, phi2, E = phi1 + sqrt(phi2) and dE/dA from A.  The block works on
-// 8 atoms at a time, one per warp, in three barrier-separated phases: the forward (after
-// every atom's A is in shared memory, since the diagonal units read all of them), the
-// adjoint (after every phi sum is complete, since the units need each atom's scale), and
-// the write-out (after the units' gradients are in ldA).
-__global__ void __launch_bounds__(kContractWarps * 32, 2)
-k_ace_contract(const AceDev* __restrict__ tab, const int* __restrict__ ace_list, int* __restrict__ flags,
-               const float* __restrict__ Ain, float* __restrict__ dAout, float* __restrict__ e_ace) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    AceDev& C = *reinterpret_cast<AceDev*>(smem_raw);
-    ContractSmem* WS = reinterpret_cast<ContractSmem*>(smem_raw + sizeof(AceDev));
-    DiagSmem& D = *reinterpret_cast<DiagSmem*>(smem_raw + sizeof(AceDev) + kContractWarps * sizeof(ContractSmem));
-    {
-        const int4* src = reinterpret_cast<const int4*>(tab);
-        int4* dst = reinterpret_cast<int4*>(smem_raw);
-        for (int k = threadIdx.x; k < (int)(sizeof(AceDev) / 16); k += blockDim.x) dst[k] = src[k];
-        float* z = &D.ldA[0][0][0];
-        for (int k = threadIdx.x; k < kContractWarps * 4 * (kApad + 1); k += blockDim.x) z[k] = 0.0f;
-    }
-    __syncthreads();
-    pdl_wait();                                            // the constant tables are staged
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    ContractSmem& S = WS[warp];
-    const int n_ace = flags[kFlagNAce];
-    int lam_l = 0;
-    if (lane >= 1) lam_l = 1;
-    if (lane >= 4) lam_l = 2;
-    if (lane >= 9) lam_l = 3;
-    if (lane >= 16) lam_l = 4;
-    const int lam_pad = lblk(lam_l) + (lane - lam_l * lam_l);
-    // the padding of S.A stays zero; each iteration writes only the (l, m) entries
-    for (int k = lane; k < kNmax * kApad; k += 32) S.A[k] = 0.0f;
-    // A of this warp's next atom, loaded a phase ahead of its use
-    float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
-    {
-        const int a0 = blockIdx.x * kContractWarps + warp;
-        if (a0 < n_ace && lane < kNLM) {
-            const float4* src = reinterpret_cast<const float4*>(Ain + ((size_t)a0 * kNLM + lane) * kNmax);
-            g0 = src[0];
-            g1 = src[1];
-        }
-    }
-    // the loop bound is uniform over the block: every warp reaches every barrier
-    for (int base = blockIdx.x * kContractWarps; base < n_ace; base += gridDim.x * kContractWarps) {
-        const int a = base + warp;
-        const bool act = a < n_ace;
-        for (int k = lane; k < kNmax * kApad; k += 32) S.dA[k] = 0.0f;
-        if (lane < kNLM) {
-            const float v[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
-#pragma unroll
-            for (int q = 0; q < kNmax; ++q) S.A[q * kApad + lam_pad] = act ? v[q] : 0.0f;
-        }
-        __syncthreads();                                   // every atom's A is visible
-        float p1 = 0.0f, p2 = 0.0f;
-        if (lane < kNmax) {
-            const float a0 = S.A[lane * kApad];
-            p1 = C.c1[0][lane] * a0;
-            p2 = C.c1[1][lane] * a0;
-        }
-#pragma unroll 1
-        for (int pp = 0; pp < 2; ++pp) {
-            const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
-#pragma unroll
-            for (int l = 0; l <= kLmax; ++l) {
-                float mm = 0.0f;
-#pragma unroll
-                for (int k = 0; k < 2 * l + 1; ++k)
-                    mm = fmaf(S.A[n1 * kApad + lblk(l) + k], S.A[n2 * kApad + lblk(l) + k], mm);
-                p1 = fmaf(C.c2[0][l][q], mm, p1);
-                p2 = fmaf(C.c2[1][l][q], mm, p2);
-            }
-        }
-        nu3_forward_main_all(WS, S.A, C, D, warp, lane, p1, p2, std::make_integer_sequence<int, kNT>{});
-        p1 = warp_sum(p1);
-        p2 = warp_sum(p2);
-        if (lane == 0) { D.pm[warp][0] = p1; D.pm[warp][1] = p2; }
-        __syncthreads();                                   // every sum of the block is visible
-        {
-            const int an = a + gridDim.x * kContractWarps;
-            if (an < n_ace && lane < kNLM) {
-                const float4* src = reinterpret_cast<const float4*>(Ain + ((size_t)an * kNLM + lane) * kNmax);
-                g0 = src[0];
-                g1 = src[1];
-            }
-        }
-        const float2 P = phi_sums(D, warp);
-        const bool ok = phi_ok(C, P);
-        const float sq = ok ? sqrtf(C.c2_0 + P.y) : 0.0f;
-        // the scale of atom slot lane / 4, for the diagonal trips of this warp
-        const float2 Ps = phi_sums(D, lane >> 2);
-        const float s_slot = phi_ok(C, Ps) ? 0.5f / sqrtf(C.c2_0 + Ps.y) : 0.0f;
-        {
-            // an atom outside the domain runs with s = 0 (its results are discarded); its warp
-            // may carry a diagonal trip for the other atoms
-            const float s = ok ? 0.5f / sq : 0.0f;
-            if (lane < kNmax) S.dA[lane * kApad] += fmaf(s, C.c1[1][lane], C.c1[0][lane]);
-            __syncwarp();
-#pragma unroll
-            for (int l = 0; l <= kLmax; ++l) {
-                constexpr int WM = 9;
-                float d2[WM];
-#pragma unroll
-                for (int k = 0; k < WM; ++k) d2[k] = 0.0f;
-#pragma unroll 1
-                for (int pp = 0; pp < 2; ++pp) {
-                    const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
-                    const float c = fmaf(s, C.c2[1][l][q], C.c2[0][l][q]);
-                    float d1[WM];
-#pragma unroll
-                    for (int k = 0; k < 2 * l + 1; ++k) {
-                        const float a1 = S.A[n1 * kApad + lblk(l) + k], a2 = S.A[n2 * kApad + lblk(l) + k];
-                        d1[k] = c * a2;
-                        d2[k] = fmaf(c, a1, d2[k]);
-                    }
-#pragma unroll
-                    for (int k = 0; k < 2 * l + 1; ++k) {
-                        float v = d1[k];
-                        v += __shfl_xor_sync(0xffffffffu, v, 1);
-                        v += __shfl_xor_sync(0xffffffffu, v, 2);
-                        v += __shfl_xor_sync(0xffffffffu, v, 4);
-                        d1[k] = v;
-                    }
-                    if ((lane & 7) == 0) {
-#pragma unroll
-                        for (int k = 0; k < 2 * l + 1; ++k) S.dA[n1 * kApad + lblk(l) + k] += d1[k];
-                    }
-                    __syncwarp();
-                }
-#pragma unroll
-                for (int k = 0; k < 2 * l + 1; ++k) {
-                    float v = d2[k];
-                    v += __shfl_xor_sync(0xffffffffu, v, 8);
-                    v += __shfl_xor_sync(0xffffffffu, v, 16);
-                    d2[k] = v;
-                }
-                if (lane < 8) {
-#pragma unroll
-                    for (int k = 0; k < 2 * l + 1; ++k) S.dA[lane * kApad + lblk(l) + k] += d2[k];
-                }
-                __syncwarp();
-            }
-            nu3_adjoint_main_all(WS, S.A, S.dA, C, D, s, s_slot, warp, lane, std::make_integer_sequence<int, kNT>{});
-        }
-        __syncthreads();                                   // every diagonal gradient is in ldA
-        for (int e = lane; e < 4 * kApad; e += 32) {
-            const int r = e / kApad, m = e - r * kApad;
-            S.dA[(4 + r) * kApad + m] += D.ldA[warp][r][m];
-            D.ldA[warp][r][m] = 0.0f;
-        }
-        __syncwarp();
-        if (act) {
-            const int i = ace_list[a];
-            if (!ok) {
-                if (lane == 0) { atomicOr(&flags[kFlagErr], kErrDomain); flags[kFlagBad] = i; e_ace[i] = __int_as_float(0x7fc00000); }
-                // zero adjoint: the force stage then adds nothing for this atom
-                if (lane < kNLM) {
-                    float4* o = reinterpret_cast<float4*>(dAout + ((size_t)a * kNLM + lane) * kNmax);
-                    o[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    o[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-            } else {
-                if (lane < kNLM) {
-                    float v[kNmax];
-#pragma unroll
-                    for (int q = 0; q < kNmax; ++q) v[q] = S.dA[q * kApad + lam_pad];
-                    float4* o = reinterpret_cast<float4*>(dAout + ((size_t)a * kNLM + lane) * kNmax);
-                    o[0] = make_float4(v[0], v[1], v[2], v[3]);
-                    o[1] = make_float4(v[4], v[5], v[6], v[7]);
-                }
-                if (lane == 0) e_ace[i] = P.x + sq;
-            }
-        }
-        __syncwarp();
-    }
-}
-
-struct ForceSmem {
-    float dAT[kNLM][kNmax];
-    float4 nb[kAceNbrCap];
-    int nbj[kAceNbrCap];
-};
-
-// stage a6: f_ij = (1/nref) sum dE/dA_nlm grad(g_n Y_lm), scattered with weight w_i
-__global__ void __launch_bounds__(256) k_ace_force(const float4* __restrict__ pos4, const int* __restrict__ nbr,
-                                                   const int* __restrict__ nnbr, int n, const float4* __restrict__ Dtab,
-                                                   int ncode, const AceDev* __restrict__ tab,
-                                                   const int* __restrict__ ace_list, const float* __restrict__ wv,
-                                                   int* __restrict__ flags, const float* __restrict__ dAin,
-                                                   float* __restrict__ vir, unsigned long long* __restrict__ acc) {
-    __shared__ float4 Ds[125];
-    __shared__ ForceSmem WS[8];
-    for (int k = threadIdx.x; k < ncode; k += blockDim.x) Ds[k] = Dtab[k];
-    __syncthreads();
-    pdl_wait();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    ForceSmem& S = WS[warp];
-    const float rc = tab->rc, rc2 = rc * rc, nrefi = tab->nref_inv;
-    const int n_ace = flags[kFlagNAce];
-    for (int a = blockIdx.x * 8 + warp; a < n_ace; a += gridDim.x * 8) {
-        const int i = ace_list[a];
-        const float wi = wv[i];
-        const int cnt = gather_ace_neighbors(pos4, nbr, n, i, nnbr[i], Ds, rc2, S.nb, S.nbj, lane);
-        if (cnt < 0) continue;
-        for (int k = lane; k < kNLM * 2; k += 32)
-            reinterpret_cast<float4*>(&S.dAT[0][0])[k] = reinterpret_cast<const float4*>(dAin + (size_t)a * kNLM * kNmax)[k];
-        __syncwarp();
-        float fsx = 0.f, fsy = 0.f, fsz = 0.f;
-        float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f, v4 = 0.f, v5 = 0.f;
-        for (int t0 = 0; t0 < cnt; t0 += 32) {
-            const int jj = t0 + lane;
-            if (jj < cnt) {
-                const float4 v = S.nb[jj];
-                const int j = S.nbj[jj];
-                const float ri = 1.0f / v.w;
-                const float ux = v.x * ri, uy = v.y * ri, uz = v.z * ri;
-                float g[kNmax], dg[kNmax];
-                radial(v.w, rc, g, dg);
-                float sc = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-                auto ab = [&](int lm, float& aa, float& bb) {
-                    const float4 d0 = *reinterpret_cast<const float4*>(&S.dAT[lm][0]);
-                    const float4 d1 = *reinterpret_cast<const float4*>(&S.dAT[lm][4]);
-                    aa = d0.x * g[0] + d0.y * g[1] + d0.z * g[2] + d0.w * g[3] + d1.x * g[4] + d1.y * g[5] + d1.z * g[6] + d1.w * g[7];
-                    bb = d0.x * dg[0] + d0.y * dg[1] + d0.z * dg[2] + d0.w * dg[3] + d1.x * dg[4] + d1.y * dg[5] + d1.z * dg[6] + d1.w * dg[7];
-                };
-                force_terms(ux, uy, uz, ri, ab, sc, gx, gy, gz);
-                const float fx = nrefi * (sc * ux + gx * ri) * wi;
-                const float fy = nrefi * (sc * uy + gy * ri) * wi;
-                const float fz = nrefi * (sc * uz + gz * ri) * wi;
-                fix_add(&acc[j], -fx);
-                fix_add(&acc[(size_t)n + j], -fy);
-                fix_add(&acc[(size_t)2 * n + j], -fz);
-                fsx += fx; fsy += fy; fsz += fz;
-                v0 -= v.x * fx; v1 -= v.y * fy; v2 -= v.z * fz;
-                v3 -= 0.5f * (v.x * fy + v.y * fx); v4 -= 0.5f * (v.x * fz + v.z * fx); v5 -= 0.5f * (v.y * fz + v.z * fy);
-            }
-        }
-        fsx = warp_sum(fsx); fsy = warp_sum(fsy); fsz = warp_sum(fsz);
-        v0 = warp_sum(v0); v1 = warp_sum(v1); v2 = warp_sum(v2);
-        v3 = warp_sum(v3); v4 = warp_sum(v4); v5 = warp_sum(v5);
-        if (lane == 0) {
-            fix_add(&acc[i], fsx);
-            fix_add(&acc[(size_t)n + i], fsy);
-            fix_add(&acc[(size_t)2 * n + i], fsz);
-            vir[i] = v0; vir[n + i] = v1; vir[2 * n + i] = v2; vir[3 * n + i] = v3; vir[4 * n + i] = v4; vir[5 * n + i] = v5;
-        }
-        __syncwarp();
-    }
-}
-
 
 // ---------------------------------------------------------------------------------
 // Tensor-core contraction.  For an l-triple t the three-factor part of phi_p is
@@ -1550,11 +772,172 @@ __device__ __forceinline__ float dot8(const float* c, const float* a) {
     return fmaf(v.w, a[7], r);
 }
 
+// phi1, phi2 of the atom whose A is in S (tc_load_atom), E = phi1 + sqrt(phi2) without the
+// constant c1_0 into e_out, and dE/dA into S.dA; false outside the domain (phi2 <= 1e-3 or
+// a NaN), where E and dA carry no meaning
+__device__ __forceinline__ bool tc_contract_atom(const AceTc& C, TcWarpSmem& S, int lane, float& e_out) {
+    float a00[kNmax];
+#pragma unroll
+    for (int k = 0; k < kNmax; ++k) a00[k] = S.A[k * kApad];
+    // one- and two-factor functions, with the (0, l, l) triples folded into the latter
+    float p1 = 0.0f, p2 = 0.0f;
+    if (lane < kNmax) {
+        p1 = C.c1[0][lane] * a00[lane];
+        p2 = C.c1[1][lane] * a00[lane];
+    }
+#pragma unroll 1
+    for (int pp = 0; pp < 2; ++pp) {
+        const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
+#pragma unroll
+        for (int l = 0; l <= kLmax; ++l) {
+            float mm = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 2 * l + 1; ++k)
+                mm = fmaf(S.A[n1 * kApad + lblk(l) + k], S.A[n2 * kApad + lblk(l) + k], mm);
+            p1 = fmaf(C.c2[0][l][q] + dot8(C.c0ll[0][l][q], a00), mm, p1);
+            p2 = fmaf(C.c2[1][l][q] + dot8(C.c0ll[1][l][q], a00), mm, p2);
+        }
+    }
+    // the tensor-core triples, grouped by l3
+    tc_forward_group<2>(C, S, lane, p1, p2, std::integer_sequence<int, 5, 8>{});
+    tc_forward_group<3>(C, S, lane, p1, p2, std::integer_sequence<int, 6, 10>{});
+    tc_forward_group<4>(C, S, lane, p1, p2, std::integer_sequence<int, 7, 9, 11, 12, 13>{});
+    __syncwarp();                                      // the epilogues' dA and R2 are visible
+    p1 = warp_sum(p1);
+    p2 = warp_sum(p2);
+    const bool ok = C.c2_0 + p2 > 1e-3f && p1 == p1;
+    const float sq = ok ? sqrtf(C.c2_0 + p2) : 0.0f;
+    const float s = ok ? 0.5f / sq : 0.0f;
+    // adjoint: one- and two-factor functions (with the folded triples and their A[n1, 00]
+    // gradient g00), the second density's third-factor part
+    if (lane < kNmax) S.dA[lane * kApad] += fmaf(s, C.c1[1][lane], C.c1[0][lane]);
+    __syncwarp();
+    float g00[kNmax];
+#pragma unroll
+    for (int k = 0; k < kNmax; ++k) g00[k] = 0.0f;
+#pragma unroll
+    for (int l = 0; l <= kLmax; ++l) {
+        constexpr int WM = 9;
+        float d2[WM];
+#pragma unroll
+        for (int k = 0; k < WM; ++k) d2[k] = 0.0f;
+#pragma unroll 1
+        for (int pp = 0; pp < 2; ++pp) {
+            const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
+            float cs[kNmax];
+            {
+                const float* c0 = C.c0ll[0][l][q];
+                const float* c1 = C.c0ll[1][l][q];
+                const float4 u0 = *reinterpret_cast<const float4*>(c0), u1 = *reinterpret_cast<const float4*>(c0 + 4);
+                const float4 v0 = *reinterpret_cast<const float4*>(c1), v1 = *reinterpret_cast<const float4*>(c1 + 4);
+                cs[0] = fmaf(s, v0.x, u0.x); cs[1] = fmaf(s, v0.y, u0.y); cs[2] = fmaf(s, v0.z, u0.z);
+                cs[3] = fmaf(s, v0.w, u0.w); cs[4] = fmaf(s, v1.x, u1.x); cs[5] = fmaf(s, v1.y, u1.y);
+                cs[6] = fmaf(s, v1.z, u1.z); cs[7] = fmaf(s, v1.w, u1.w);
+            }
+            float ct = fmaf(s, C.c2[1][l][q], C.c2[0][l][q]);
+            float mm = 0.0f;
+            float d1[WM];
+#pragma unroll
+            for (int k = 0; k < 2 * l + 1; ++k) {
+                const float a1 = S.A[n1 * kApad + lblk(l) + k], a2 = S.A[n2 * kApad + lblk(l) + k];
+                mm = fmaf(a1, a2, mm);
+            }
+#pragma unroll
+            for (int k = 0; k < kNmax; ++k) {
+                ct = fmaf(cs[k], a00[k], ct);
+                g00[k] = fmaf(cs[k], mm, g00[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < 2 * l + 1; ++k) {
+                const float a1 = S.A[n1 * kApad + lblk(l) + k], a2 = S.A[n2 * kApad + lblk(l) + k];
+                d1[k] = ct * a2;
+                d2[k] = fmaf(ct, a1, d2[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < 2 * l + 1; ++k) {
+                float v = d1[k];
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                v += __shfl_xor_sync(0xffffffffu, v, 2);
+                v += __shfl_xor_sync(0xffffffffu, v, 4);
+                d1[k] = v;
+            }
+            if ((lane & 7) == 0) {
+#pragma unroll
+                for (int k = 0; k < 2 * l + 1; ++k) S.dA[n1 * kApad + lblk(l) + k] += d1[k];
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int k = 0; k < 2 * l + 1; ++k) {
+            float v = d2[k];
+            v += __shfl_xor_sync(0xffffffffu, v, 8);
+            v += __shfl_xor_sync(0xffffffffu, v, 16);
+            d2[k] = v;
+        }
+        if (lane < 8) {
+#pragma unroll
+            for (int k = 0; k < 2 * l + 1; ++k) S.dA[lane * kApad + lblk(l) + k] += d2[k];
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int k = 0; k < kNmax; ++k) g00[k] = warp_sum(g00[k]);
+    if (lane < kNmax) {
+        float g = g00[0];
+#pragma unroll
+        for (int k = 1; k < kNmax; ++k) g = lane == k ? g00[k] : g;
+        S.dA[lane * kApad] += g;
+    }
+    for (int e = lane; e < kNmax * 21; e += 32) {
+        // lm = 4 .. 24: l3 = 2, 3, 4 of the tensor-core triples
+        const int n3 = e / 21, lm = 4 + (e - n3 * 21);
+        const int l = lm < 9 ? 2 : (lm < 16 ? 3 : 4);
+        S.dA[n3 * kApad + lblk(l) + (lm - l * l)] += s * S.R2[n3][lm];
+    }
+    __syncwarp();
+    tc_adjoint_all(C, S, s, lane, std::integer_sequence<int, 5, 6, 7, 8, 9, 10, 11, 12, 13>{});
+    e_out = p1 + sq;
+    return ok;
+}
+
+// A of one atom into the warp's region (lane lm < 25 gives A[n][lm] for n = 0..3 in g0 and
+// 4..7 in g1; lam_pad is the lane's column in the l-block layout), dA cleared
+__device__ __forceinline__ void tc_load_atom(TcWarpSmem& S, int lane, int lam_pad, float4 g0, float4 g1) {
+    if (lane < kNLM) {
+        const float v[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+#pragma unroll
+        for (int q = 0; q < kNmax; ++q) S.A[q * kApad + lam_pad] = v[q];
+        const int sw = (lane >> 2) & 1;
+        reinterpret_cast<float4*>(&S.At[lane][0])[sw] = g0;
+        reinterpret_cast<float4*>(&S.At[lane][0])[sw ^ 1] = g1;
+    }
+    for (int k = lane; k < kNmax * kApad; k += 32) S.dA[k] = 0.0f;
+    __syncwarp();
+}
+
+// the lane's column lm of the l-block layout (l-blocks at 0, 4, 8, 16, 24)
+__device__ __forceinline__ int lane_lm_pad(int lane) {
+    int l = 0;
+    if (lane >= 1) l = 1;
+    if (lane >= 4) l = 2;
+    if (lane >= 9) l = 3;
+    if (lane >= 16) l = 4;
+    return lblk(l) + (lane - l * l);
+}
+
+// one-time set-up of a warp region: zero, so that the padding of A and At and the staging
+// rows stay finite
+__device__ __forceinline__ void tc_zero_regions(TcWarpSmem* WS, int nwarps) {
+    float4* z = reinterpret_cast<float4*>(WS);
+    for (int k = threadIdx.x; k < (int)(nwarps * sizeof(TcWarpSmem) / 16); k += blockDim.x)
+        z[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 // stages a5/a6 core on tensor cores: phi1, phi2, E = phi1 + sqrt(phi2) and dE/dA from A,
 // one warp per compacted atom
 __global__ void __launch_bounds__(kTcWarps * 32, 1)
-k_ace_contract_tc(const AceTc* __restrict__ tab, const int* __restrict__ ace_list, int* __restrict__ flags,
-                  const float* __restrict__ Ain, float* __restrict__ dAout, float* __restrict__ e_ace) {
+k_ace_contract(const AceTc* __restrict__ tab, const int* __restrict__ ace_list, int* __restrict__ flags,
+               const float* __restrict__ Ain, float* __restrict__ dAout, float* __restrict__ e_ace) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     AceTc& C = *reinterpret_cast<AceTc*>(smem_raw);
     TcWarpSmem* WS = reinterpret_cast<TcWarpSmem*>(smem_raw + sizeof(AceTc));
@@ -1562,155 +945,24 @@ k_ace_contract_tc(const AceTc* __restrict__ tab, const int* __restrict__ ace_lis
         const int4* src = reinterpret_cast<const int4*>(tab);
         int4* dst = reinterpret_cast<int4*>(smem_raw);
         for (int k = threadIdx.x; k < (int)(sizeof(AceTc) / 16); k += blockDim.x) dst[k] = src[k];
-        // every warp region starts at zero: the padding of A and At and the staging stay finite
-        float4* z = reinterpret_cast<float4*>(WS);
-        for (int k = threadIdx.x; k < (int)(kTcWarps * sizeof(TcWarpSmem) / 16); k += blockDim.x)
-            z[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        tc_zero_regions(WS, kTcWarps);
     }
     __syncthreads();
     pdl_wait();                                            // the constant tables are staged
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     TcWarpSmem& S = WS[warp];
     const int n_ace = flags[kFlagNAce];
-    int lam_l = 0;
-    if (lane >= 1) lam_l = 1;
-    if (lane >= 4) lam_l = 2;
-    if (lane >= 9) lam_l = 3;
-    if (lane >= 16) lam_l = 4;
-    const int lam_pad = lblk(lam_l) + (lane - lam_l * lam_l);
+    const int lam_pad = lane_lm_pad(lane);
     for (int a = blockIdx.x * kTcWarps + warp; a < n_ace; a += gridDim.x * kTcWarps) {
+        float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
         if (lane < kNLM) {
             const float4* src = reinterpret_cast<const float4*>(Ain + ((size_t)a * kNLM + lane) * kNmax);
-            const float4 g0 = src[0], g1 = src[1];
-            const float v[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
-#pragma unroll
-            for (int q = 0; q < kNmax; ++q) S.A[q * kApad + lam_pad] = v[q];
-            const int sw = (lane >> 2) & 1;
-            reinterpret_cast<float4*>(&S.At[lane][0])[sw] = g0;
-            reinterpret_cast<float4*>(&S.At[lane][0])[sw ^ 1] = g1;
+            g0 = src[0];
+            g1 = src[1];
         }
-        for (int k = lane; k < kNmax * kApad; k += 32) S.dA[k] = 0.0f;
-        __syncwarp();
-        float a00[kNmax];
-#pragma unroll
-        for (int k = 0; k < kNmax; ++k) a00[k] = S.A[k * kApad];
-        // one- and two-factor functions, with the (0, l, l) triples folded into the latter
-        float p1 = 0.0f, p2 = 0.0f;
-        if (lane < kNmax) {
-            p1 = C.c1[0][lane] * a00[lane];
-            p2 = C.c1[1][lane] * a00[lane];
-        }
-#pragma unroll 1
-        for (int pp = 0; pp < 2; ++pp) {
-            const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
-#pragma unroll
-            for (int l = 0; l <= kLmax; ++l) {
-                float mm = 0.0f;
-#pragma unroll
-                for (int k = 0; k < 2 * l + 1; ++k)
-                    mm = fmaf(S.A[n1 * kApad + lblk(l) + k], S.A[n2 * kApad + lblk(l) + k], mm);
-                p1 = fmaf(C.c2[0][l][q] + dot8(C.c0ll[0][l][q], a00), mm, p1);
-                p2 = fmaf(C.c2[1][l][q] + dot8(C.c0ll[1][l][q], a00), mm, p2);
-            }
-        }
-        // the tensor-core triples, grouped by l3
-        tc_forward_group<2>(C, S, lane, p1, p2, std::integer_sequence<int, 5, 8>{});
-        tc_forward_group<3>(C, S, lane, p1, p2, std::integer_sequence<int, 6, 10>{});
-        tc_forward_group<4>(C, S, lane, p1, p2, std::integer_sequence<int, 7, 9, 11, 12, 13>{});
-        __syncwarp();                                      // the epilogues' dA and R2 are visible
-        p1 = warp_sum(p1);
-        p2 = warp_sum(p2);
-        const bool ok = C.c2_0 + p2 > 1e-3f && p1 == p1;
-        const float sq = ok ? sqrtf(C.c2_0 + p2) : 0.0f;
-        const float s = ok ? 0.5f / sq : 0.0f;
-        // adjoint: one- and two-factor functions (with the folded triples and their A[n1, 00]
-        // gradient g00), the second density's third-factor part
-        if (lane < kNmax) S.dA[lane * kApad] += fmaf(s, C.c1[1][lane], C.c1[0][lane]);
-        __syncwarp();
-        float g00[kNmax];
-#pragma unroll
-        for (int k = 0; k < kNmax; ++k) g00[k] = 0.0f;
-#pragma unroll
-        for (int l = 0; l <= kLmax; ++l) {
-            constexpr int WM = 9;
-            float d2[WM];
-#pragma unroll
-            for (int k = 0; k < WM; ++k) d2[k] = 0.0f;
-#pragma unroll 1
-            for (int pp = 0; pp < 2; ++pp) {
-                const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
-                float cs[kNmax];
-                {
-                    const float* c0 = C.c0ll[0][l][q];
-                    const float* c1 = C.c0ll[1][l][q];
-                    const float4 u0 = *reinterpret_cast<const float4*>(c0), u1 = *reinterpret_cast<const float4*>(c0 + 4);
-                    const float4 v0 = *reinterpret_cast<const float4*>(c1), v1 = *reinterpret_cast<const float4*>(c1 + 4);
-                    cs[0] = fmaf(s, v0.x, u0.x); cs[1] = fmaf(s, v0.y, u0.y); cs[2] = fmaf(s, v0.z, u0.z);
-                    cs[3] = fmaf(s, v0.w, u0.w); cs[4] = fmaf(s, v1.x, u1.x); cs[5] = fmaf(s, v1.y, u1.y);
-                    cs[6] = fmaf(s, v1.z, u1.z); cs[7] = fmaf(s, v1.w, u1.w);
-                }
-                float ct = fmaf(s, C.c2[1][l][q], C.c2[0][l][q]);
-                float mm = 0.0f;
-                float d1[WM];
-#pragma unroll
-                for (int k = 0; k < 2 * l + 1; ++k) {
-                    const float a1 = S.A[n1 * kApad + lblk(l) + k], a2 = S.A[n2 * kApad + lblk(l) + k];
-                    mm = fmaf(a1, a2, mm);
-                }
-#pragma unroll
-                for (int k = 0; k < kNmax; ++k) {
-                    ct = fmaf(cs[k], a00[k], ct);
-                    g00[k] = fmaf(cs[k], mm, g00[k]);
-                }
-#pragma unroll
-                for (int k = 0; k < 2 * l + 1; ++k) {
-                    const float a1 = S.A[n1 * kApad + lblk(l) + k], a2 = S.A[n2 * kApad + lblk(l) + k];
-                    d1[k] = ct * a2;
-                    d2[k] = fmaf(ct, a1, d2[k]);
-                }
-#pragma unroll
-                for (int k = 0; k < 2 * l + 1; ++k) {
-                    float v = d1[k];
-                    v += __shfl_xor_sync(0xffffffffu, v, 1);
-                    v += __shfl_xor_sync(0xffffffffu, v, 2);
-                    v += __shfl_xor_sync(0xffffffffu, v, 4);
-                    d1[k] = v;
-                }
-                if ((lane & 7) == 0) {
-#pragma unroll
-                    for (int k = 0; k < 2 * l + 1; ++k) S.dA[n1 * kApad + lblk(l) + k] += d1[k];
-                }
-                __syncwarp();
-            }
-#pragma unroll
-            for (int k = 0; k < 2 * l + 1; ++k) {
-                float v = d2[k];
-                v += __shfl_xor_sync(0xffffffffu, v, 8);
-                v += __shfl_xor_sync(0xffffffffu, v, 16);
-                d2[k] = v;
-            }
-            if (lane < 8) {
-#pragma unroll
-                for (int k = 0; k < 2 * l + 1; ++k) S.dA[lane * kApad + lblk(l) + k] += d2[k];
-            }
-            __syncwarp();
-        }
-#pragma unroll
-        for (int k = 0; k < kNmax; ++k) g00[k] = warp_sum(g00[k]);
-        if (lane < kNmax) {
-            float g = g00[0];
-#pragma unroll
-            for (int k = 1; k < kNmax; ++k) g = lane == k ? g00[k] : g;
-            S.dA[lane * kApad] += g;
-        }
-        for (int e = lane; e < kNmax * 21; e += 32) {
-            // lm = 4 .. 24: l3 = 2, 3, 4 of the tensor-core triples
-            const int n3 = e / 21, lm = 4 + (e - n3 * 21);
-            const int l = lm < 9 ? 2 : (lm < 16 ? 3 : 4);
-            S.dA[n3 * kApad + lblk(l) + (lm - l * l)] += s * S.R2[n3][lm];
-        }
-        __syncwarp();
-        tc_adjoint_all(C, S, s, lane, std::integer_sequence<int, 5, 6, 7, 8, 9, 10, 11, 12, 13>{});
+        tc_load_atom(S, lane, lam_pad, g0, g1);
+        float e = 0.0f;
+        const bool ok = tc_contract_atom(C, S, lane, e);
         const int i = ace_list[a];
         if (!ok) {
             if (lane == 0) { atomicOr(&flags[kFlagErr], kErrDomain); flags[kFlagBad] = i; e_ace[i] = __int_as_float(0x7fc00000); }
@@ -1728,7 +980,67 @@ k_ace_contract_tc(const AceTc* __restrict__ tab, const int* __restrict__ ace_lis
                 o[0] = make_float4(v[0], v[1], v[2], v[3]);
                 o[1] = make_float4(v[4], v[5], v[6], v[7]);
             }
-            if (lane == 0) e_ace[i] = p1 + sq;
+            if (lane == 0) e_ace[i] = e;
+        }
+        __syncwarp();
+    }
+}
+
+struct ForceSmem {
+    float dAT[kNLM][kNmax];
+    float4 nb[kAceNbrCap];
+    int nbj[kAceNbrCap];
+};
+
+// stage a6: f_ij = (1/nref) sum dE/dA_nlm grad(g_n Y_lm), scattered with weight w_i
+__global__ void __launch_bounds__(256) k_ace_force(const float4* __restrict__ pos4, const int* __restrict__ nbr,
+                                                   const int* __restrict__ nnbr, int n, const float4* __restrict__ Dtab,
+                                                   int ncode, const AceTc* __restrict__ tab,
+                                                   const int* __restrict__ ace_list, const float* __restrict__ wv,
+                                                   int* __restrict__ flags, const float* __restrict__ dAin,
+                                                   float* __restrict__ vir, unsigned long long* __restrict__ acc) {
+    __shared__ float4 Ds[125];
+    __shared__ ForceSmem WS[8];
+    for (int k = threadIdx.x; k < ncode; k += blockDim.x) Ds[k] = Dtab[k];
+    __syncthreads();
+    pdl_wait();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    ForceSmem& S = WS[warp];
+    const float rc = tab->rc, rc2 = rc * rc, nrefi = tab->nref_inv;
+    const int n_ace = flags[kFlagNAce];
+    for (int a = blockIdx.x * 8 + warp; a < n_ace; a += gridDim.x * 8) {
+        const int i = ace_list[a];
+        const float wi = wv[i];
+        const int cnt = gather_ace_neighbors(pos4, nbr, n, i, nnbr[i], Ds, rc2, S.nb, S.nbj, lane);
+        if (cnt < 0) continue;
+        for (int k = lane; k < kNLM * 2; k += 32)
+            reinterpret_cast<float4*>(&S.dAT[0][0])[k] = reinterpret_cast<const float4*>(dAin + (size_t)a * kNLM * kNmax)[k];
+        __syncwarp();
+        float fsx = 0.f, fsy = 0.f, fsz = 0.f;
+        float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f, v4 = 0.f, v5 = 0.f;
+        for (int t0 = 0; t0 < cnt; t0 += 32) {
+            const int jj = t0 + lane;
+            if (jj < cnt) {
+                const float4 v = S.nb[jj];
+                const int j = S.nbj[jj];
+                const float3 fp = ace_pair_force(v, rc, nrefi, wi, S.dAT);
+                const float fx = fp.x, fy = fp.y, fz = fp.z;
+                fix_add(&acc[j], -fx);
+                fix_add(&acc[(size_t)n + j], -fy);
+                fix_add(&acc[(size_t)2 * n + j], -fz);
+                fsx += fx; fsy += fy; fsz += fz;
+                v0 -= v.x * fx; v1 -= v.y * fy; v2 -= v.z * fz;
+                v3 -= 0.5f * (v.x * fy + v.y * fx); v4 -= 0.5f * (v.x * fz + v.z * fx); v5 -= 0.5f * (v.y * fz + v.z * fy);
+            }
+        }
+        fsx = warp_sum(fsx); fsy = warp_sum(fsy); fsz = warp_sum(fsz);
+        v0 = warp_sum(v0); v1 = warp_sum(v1); v2 = warp_sum(v2);
+        v3 = warp_sum(v3); v4 = warp_sum(v4); v5 = warp_sum(v5);
+        if (lane == 0) {
+            fix_add(&acc[i], fsx);
+            fix_add(&acc[(size_t)n + i], fsy);
+            fix_add(&acc[(size_t)2 * n + i], fsz);
+            vir[i] = v0; vir[n + i] = v1; vir[2 * n + i] = v2; vir[3 * n + i] = v3; vir[4 * n + i] = v4; vir[5 * n + i] = v5;
         }
         __syncwarp();
     }
@@ -1736,15 +1048,6 @@ k_ace_contract_tc(const AceTc* __restrict__ tab, const int* __restrict__ ace_lis
 
 }  // namespace
 
-size_t ace_smem_bytes() { return sizeof(AceDev) + 128 * sizeof(float4) + kWarps * sizeof(WarpSmem); }
-
-size_t ace_contract_smem_bytes() {
-    return sizeof(AceDev) + kContractWarps * sizeof(ContractSmem) + sizeof(DiagSmem);
-}
-
-// Persistent grids: as many resident blocks per SM as the kernel's registers and shared
-// memory allow (the gather kernels are latency-bound, so every resident warp helps),
-// computed once per kernel and device.
 template <class K>
 int persistent_blocks(K kernel, int dev, int threads, size_t smem) {
     struct Entry { const void* k; int dev, threads; size_t smem; int blocks; };
@@ -1764,7 +1067,7 @@ int persistent_blocks(K kernel, int dev, int threads, size_t smem) {
 template <int MODE>
 void launch_basis_mode(Ctx& c, cudaStream_t s) {
     const int nb = persistent_blocks(k_ace_basis<MODE>, c.dev, 256, 0);
-    launch_pdl(k_ace_basis<MODE>, nb, 256, 0, s, c.pos4, c.nbr, c.nnbr, c.n, c.D, c.grid.ncode, c.ace_d, c.ace_list,
+    launch_pdl(k_ace_basis<MODE>, nb, 256, 0, s, c.pos4, c.nbr, c.nnbr, c.n, c.D, c.grid.ncode, c.ace_tc_d, c.ace_list,
                c.flags, c.ace_A);
 }
 
@@ -1783,32 +1086,24 @@ size_t ace_tc_smem_bytes() { return sizeof(AceTc) + kTcWarps * sizeof(TcWarpSmem
 
 int launch_ace(Ctx& c, cudaStream_t s) {
     static int configured = -1;
-    static const bool fp32_lanes = [] {
-        const char* e = getenv("AP_CONTRACT");
-        return !(e && std::string(e) == "tc");
-    }();
     if (configured != c.dev) {
-        cudaFuncSetAttribute(k_ace_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ace_contract_smem_bytes());
-        cudaFuncSetAttribute(k_ace_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ace_tc_smem_bytes());
+        cudaFuncSetAttribute(k_ace_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ace_tc_smem_bytes());
         configured = c.dev;
     }
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c.dev);
-    if (fp32_lanes)
-        launch_pdl(k_ace_contract, nsm * 2, kContractWarps * 32, ace_contract_smem_bytes(), s, c.ace_d, c.ace_list,
-                   c.flags, c.ace_A, c.ace_dA, c.e_ace);
-    else
-        launch_pdl(k_ace_contract_tc, nsm, kTcWarps * 32, ace_tc_smem_bytes(), s, c.ace_tc_d, c.ace_list, c.flags,
-                   c.ace_A, c.ace_dA, c.e_ace);
+    launch_pdl(k_ace_contract, nsm, kTcWarps * 32, ace_tc_smem_bytes(), s, c.ace_tc_d, c.ace_list, c.flags, c.ace_A,
+               c.ace_dA, c.e_ace);
     return 1;
 }
 
 int launch_ace_force(Ctx& c, cudaStream_t s) {
     const int nb = persistent_blocks(k_ace_force, c.dev, 256, 0);
-    launch_pdl(k_ace_force, nb, 256, 0, s, c.pos4, c.nbr, c.nnbr, c.n, c.D, c.grid.ncode, c.ace_d, c.ace_list, c.w,
+    launch_pdl(k_ace_force, nb, 256, 0, s, c.pos4, c.nbr, c.nnbr, c.n, c.D, c.grid.ncode, c.ace_tc_d, c.ace_list, c.w,
                c.flags, c.ace_dA, c.vir_ace, c.acc);
     return 1;
 }
+
 
 }  // namespace ap
 
@@ -1819,8 +1114,8 @@ int launch_ace_force(Ctx& c, cudaStream_t s) {
 // program or plugin whose GPU memory is owned entirely by another allocator (a
 // framework's caching pool that must see every byte), or a time-critical step loop that
 // forbids the latency and the failure modes of cudaMalloc after start-up.  For them
-// ap_ace_forces_noalloc evaluates the ACE pass (the same warp-per-atom arithmetic as
-// k_ace) on neighbour lists they pass in, and keeps its scratch - the coefficient
+// ap_ace_forces_noalloc evaluates the ACE pass (the same per-atom device functions as the
+// context path) on neighbour lists they pass in, and keeps its scratch - the coefficient
 // tables and the 64-bit fixed-point force accumulators - in the file-scope array below,
 // which every GPU that loads this library holds until the process exits.
 // =====================================================================================
@@ -1829,14 +1124,14 @@ namespace ap {
 namespace {
 
 constexpr int kNoAllocMaxAtoms = 65536;
-constexpr size_t kNoAllocTableBytes = (sizeof(AceDev) + 255) / 256 * 256;
+constexpr size_t kNoAllocTableBytes = (sizeof(AceTc) + 255) / 256 * 256;
 constexpr size_t kNoAllocBytes = kNoAllocTableBytes + 3 * (size_t)kNoAllocMaxAtoms * sizeof(unsigned long long);
 
 }  // namespace
 
 }  // namespace ap
 
-// ~1.6 MB: the coefficient tables, then accumulators for up to 65,536 atoms.  In host
+// ~1.7 MB: the coefficient tables, then accumulators for up to 65,536 atoms.  In host
 // code this name is only a stand-in; kernels receive its device address, obtained once
 // per device with cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_ace_noalloc_scratch[ap::kNoAllocBytes];
@@ -1845,36 +1140,47 @@ namespace ap {
 
 namespace {
 
-__global__ void __launch_bounds__(kWarps * 32, 1)
+constexpr int kNaWarps = 8;
+
+struct NoallocWarpSmem {
+    TcWarpSmem tc;
+    float4 nb[kAceNbrCap];
+    int nbj[kAceNbrCap];
+    float tileY[kTile][kNLM];
+    float tileG[kTile][kNmax];
+    float dAT[kNLM][kNmax];
+};
+static_assert(sizeof(NoallocWarpSmem) % 16 == 0, "16-byte aligned warp regions");
+
+size_t noalloc_smem_bytes() { return sizeof(AceTc) + kNaWarps * sizeof(NoallocWarpSmem); }
+
+__global__ void __launch_bounds__(kNaWarps * 32, 1)
 k_ace_noalloc(const int* __restrict__ nbr_idx, const float* __restrict__ rvec, int n, int max_nb,
               const float* __restrict__ wv, unsigned char* __restrict__ scratch, double* __restrict__ e_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    AceDev& C = *reinterpret_cast<AceDev*>(smem_raw);
-    WarpSmem* WS = reinterpret_cast<WarpSmem*>(smem_raw + sizeof(AceDev) + 128 * sizeof(float4));
+    AceTc& C = *reinterpret_cast<AceTc*>(smem_raw);
+    NoallocWarpSmem* WS = reinterpret_cast<NoallocWarpSmem*>(smem_raw + sizeof(AceTc));
     unsigned long long* acc = reinterpret_cast<unsigned long long*>(scratch + kNoAllocTableBytes);
     {
         const int4* src = reinterpret_cast<const int4*>(scratch);
         int4* dst = reinterpret_cast<int4*>(smem_raw);
-        for (int k = threadIdx.x; k < (int)(sizeof(AceDev) / 16); k += blockDim.x) dst[k] = src[k];
+        for (int k = threadIdx.x; k < (int)(sizeof(AceTc) / 16); k += blockDim.x) dst[k] = src[k];
+        float4* z = reinterpret_cast<float4*>(WS);
+        for (int k = threadIdx.x; k < (int)(kNaWarps * sizeof(NoallocWarpSmem) / 16); k += blockDim.x)
+            z[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpSmem& S = WS[warp];
+    NoallocWarpSmem& S = WS[warp];
     const float rc = C.rc, rc2 = rc * rc, nrefi = C.nref_inv;
-    int lam_l = 0;
-    if (lane >= 1) lam_l = 1;
-    if (lane >= 4) lam_l = 2;
-    if (lane >= 9) lam_l = 3;
-    if (lane >= 16) lam_l = 4;
-    const int lam_pad = lblk(lam_l) + (lane - lam_l * lam_l);
-
-    for (int i = blockIdx.x * kWarps + warp; i < n; i += gridDim.x * kWarps) {
+    const int lam_pad = lane_lm_pad(lane);
+    for (int i = blockIdx.x * kNaWarps + warp; i < n; i += gridDim.x * kNaWarps) {
         const float wi = wv ? wv[i] : 1.0f;
         if (!(wi > 0.0f)) {
             if (lane == 0) e_out[i] = 0.0;
             continue;
         }
-        // neighbours inside the cutoff; S.nbj keeps the atom index
+        // neighbours inside the cutoff; S.nbj keeps the atom index (max_nb <= kAceNbrCap)
         int cnt = 0;
         for (int k0 = 0; k0 < max_nb; k0 += 32) {
             const int k = k0 + lane;
@@ -1900,146 +1206,33 @@ k_ace_noalloc(const int* __restrict__ nbr_idx, const float* __restrict__ rvec, i
 #pragma unroll
         for (int q = 0; q < kNmax; ++q) accA[q] = 0.0f;
         for (int t0 = 0; t0 < cnt; t0 += kTile) {
-            const int jj = t0 + lane;
-            if (jj < cnt) {
-                const float4 v = S.nb[jj];
-                const float ri = 1.0f / v.w;
-                float g[kNmax], dg[kNmax], Y[kNLM];
-                radial(v.w, rc, g, dg);
-                ylm(v.x * ri, v.y * ri, v.z * ri, Y);
-#pragma unroll
-                for (int q = 0; q < kNmax; ++q) S.tileG[lane][q] = g[q];
-#pragma unroll
-                for (int q = 0; q < kNLM; ++q) S.tileY[lane][q] = Y[q];
-            }
+            basis_tile(S.nb, t0, cnt, rc, S.tileY, S.tileG, lane);
             __syncwarp();
-            const int nt = min(kTile, cnt - t0);
-            if (lane < kNLM) {
-                for (int jj2 = 0; jj2 < nt; ++jj2) {
-                    const float y = S.tileY[jj2][lane];
-#pragma unroll
-                    for (int q = 0; q < kNmax; ++q) accA[q] = fmaf(y, S.tileG[jj2][q], accA[q]);
-                }
-            }
+            basis_accum_fp32(S.tileY, S.tileG, min(kTile, cnt - t0), lane, accA);
             __syncwarp();
         }
-        for (int k = lane; k < kNmax * kApad; k += 32) { S.A[k] = 0.0f; S.dA[k] = 0.0f; }
-        __syncwarp();
-        if (lane < kNLM) {
-#pragma unroll
-            for (int q = 0; q < kNmax; ++q) S.A[q * kApad + lam_pad] = accA[q] * nrefi;
-        }
-        __syncwarp();
-        float p1 = 0.0f, p2 = 0.0f;
-        if (lane < kNmax) {
-            const float a0 = S.A[lane * kApad];
-            p1 = C.c1[0][lane] * a0;
-            p2 = C.c1[1][lane] * a0;
-        }
-#pragma unroll
-        for (int l = 0; l <= kLmax; ++l) {
-#pragma unroll
-            for (int pp = 0; pp < 2; ++pp) {
-                const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
-                float mm = 0.0f;
-#pragma unroll
-                for (int k = 0; k < 2 * l + 1; ++k)
-                    mm = fmaf(S.A[n1 * kApad + lblk(l) + k], S.A[n2 * kApad + lblk(l) + k], mm);
-                p1 = fmaf(C.c2[0][l][q], mm, p1);
-                p2 = fmaf(C.c2[1][l][q], mm, p2);
-            }
-        }
-        nu3_forward_all(S.A, C, lane, p1, p2, std::make_integer_sequence<int, kNT>{});
-        p1 = warp_sum(p1);
-        p2 = warp_sum(p2);
-        const float phi2 = C.c2_0 + p2;
-        if (!(phi2 > 1e-3f) || !(p1 == p1)) {
+        tc_load_atom(S.tc, lane, lam_pad, make_float4(accA[0] * nrefi, accA[1] * nrefi, accA[2] * nrefi, accA[3] * nrefi),
+                     make_float4(accA[4] * nrefi, accA[5] * nrefi, accA[6] * nrefi, accA[7] * nrefi));
+        float e = 0.0f;
+        if (!tc_contract_atom(C, S.tc, lane, e)) {
             if (lane == 0) e_out[i] = __longlong_as_double(0x7ff8000000000000ll);
             continue;
         }
-        const float sq = sqrtf(phi2);
-        const float s = 0.5f / sq;
-        if (lane < kNmax) S.dA[lane * kApad] += fmaf(s, C.c1[1][lane], C.c1[0][lane]);
-        __syncwarp();
-#pragma unroll
-        for (int l = 0; l <= kLmax; ++l) {
-            constexpr int WM = 9;
-            float d2[WM];
-#pragma unroll
-            for (int k = 0; k < WM; ++k) d2[k] = 0.0f;
-#pragma unroll
-            for (int pp = 0; pp < 2; ++pp) {
-                const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
-                const float c = fmaf(s, C.c2[1][l][q], C.c2[0][l][q]);
-                float d1[WM];
-#pragma unroll
-                for (int k = 0; k < 2 * l + 1; ++k) {
-                    const float a1 = S.A[n1 * kApad + lblk(l) + k], a2 = S.A[n2 * kApad + lblk(l) + k];
-                    d1[k] = c * a2;
-                    d2[k] = fmaf(c, a1, d2[k]);
-                }
-#pragma unroll
-                for (int k = 0; k < 2 * l + 1; ++k) {
-                    float v = d1[k];
-                    v += __shfl_xor_sync(0xffffffffu, v, 1);
-                    v += __shfl_xor_sync(0xffffffffu, v, 2);
-                    v += __shfl_xor_sync(0xffffffffu, v, 4);
-                    d1[k] = v;
-                }
-                if ((lane & 7) == 0) {
-#pragma unroll
-                    for (int k = 0; k < 2 * l + 1; ++k) S.dA[n1 * kApad + lblk(l) + k] += d1[k];
-                }
-                __syncwarp();
-            }
-#pragma unroll
-            for (int k = 0; k < 2 * l + 1; ++k) {
-                float v = d2[k];
-                v += __shfl_xor_sync(0xffffffffu, v, 8);
-                v += __shfl_xor_sync(0xffffffffu, v, 16);
-                d2[k] = v;
-            }
-            if (lane < 8) {
-#pragma unroll
-                for (int k = 0; k < 2 * l + 1; ++k) S.dA[lane * kApad + lblk(l) + k] += d2[k];
-            }
-            __syncwarp();
-        }
-        nu3_adjoint_all(S.A, S.dA, C, s, lane, std::make_integer_sequence<int, kNT>{});
         if (lane < kNLM) {
 #pragma unroll
-            for (int q = 0; q < kNmax; ++q) S.dAT[lane][q] = S.dA[q * kApad + lam_pad];
+            for (int q = 0; q < kNmax; ++q) S.dAT[lane][q] = S.tc.dA[q * kApad + lam_pad];
         }
         __syncwarp();
         float fsx = 0.f, fsy = 0.f, fsz = 0.f;
         for (int t0 = 0; t0 < cnt; t0 += 32) {
             const int jj = t0 + lane;
             if (jj < cnt) {
-                const float4 v = S.nb[jj];
                 const int j = S.nbj[jj];
-                const float ri = 1.0f / v.w;
-                const float ux = v.x * ri, uy = v.y * ri, uz = v.z * ri;
-                float g[kNmax], dg[kNmax];
-                radial(v.w, rc, g, dg);
-                float sc = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-                auto ab = [&](int lm, float& aa, float& bb) {
-                    float a_ = 0.f, b_ = 0.f;
-#pragma unroll
-                    for (int q = 0; q < kNmax; ++q) {
-                        a_ = fmaf(S.dAT[lm][q], g[q], a_);
-                        b_ = fmaf(S.dAT[lm][q], dg[q], b_);
-                    }
-                    aa = a_;
-                    bb = b_;
-                };
-                force_terms(ux, uy, uz, ri, ab, sc, gx, gy, gz);
-                const float fx = nrefi * (sc * ux + gx * ri) * wi;
-                const float fy = nrefi * (sc * uy + gy * ri) * wi;
-                const float fz = nrefi * (sc * uz + gz * ri) * wi;
-                fix_add(&acc[j], -fx);
-                fix_add(&acc[(size_t)n + j], -fy);
-                fix_add(&acc[(size_t)2 * n + j], -fz);
-                fsx += fx; fsy += fy; fsz += fz;
+                const float3 fp = ace_pair_force(S.nb[jj], rc, nrefi, wi, S.dAT);
+                fix_add(&acc[j], -fp.x);
+                fix_add(&acc[(size_t)n + j], -fp.y);
+                fix_add(&acc[(size_t)2 * n + j], -fp.z);
+                fsx += fp.x; fsy += fp.y; fsz += fp.z;
             }
         }
         fsx = warp_sum(fsx); fsy = warp_sum(fsy); fsz = warp_sum(fsz);
@@ -2047,7 +1240,7 @@ k_ace_noalloc(const int* __restrict__ nbr_idx, const float* __restrict__ rvec, i
             fix_add(&acc[i], fsx);
             fix_add(&acc[(size_t)n + i], fsy);
             fix_add(&acc[(size_t)2 * n + i], fsz);
-            e_out[i] = (double)C.c1_0 + (double)(p1 + sq);
+            e_out[i] = (double)C.c1_0 + (double)e;
         }
         __syncwarp();
     }
@@ -2068,7 +1261,8 @@ struct NoallocDevice {
     bool tables = false;
 };
 NoallocDevice g_noalloc_dev[64];
-AceDev g_noalloc_tables;                 // host staging of the tables (guarded by the mutex)
+AceDev g_noalloc_dev_tables;             // host staging of the tables (guarded by the mutex)
+AceTc g_noalloc_tables;
 
 // FNV-1a over the bytes that define the ACE tables of a potential
 unsigned long long potential_key(const ap_potential& p) {
@@ -2126,7 +1320,7 @@ extern "C" ap_status ap_ace_forces_noalloc(const ap_potential* pot, int n_atoms,
         std::string err;
         if (gaunt_values(gv, err)) return noalloc_fail(AP_ERR_ARG, err);
         upload_gaunt(gv);
-        if (cudaFuncSetAttribute(k_ace_noalloc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ace_smem_bytes()) !=
+        if (cudaFuncSetAttribute(k_ace_noalloc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)noalloc_smem_bytes()) !=
             cudaSuccess)
             return noalloc_fail(AP_ERR_CUDA, "ap_ace_forces_noalloc: cudaFuncSetAttribute failed");
         D.scratch = p;
@@ -2138,11 +1332,12 @@ extern "C" ap_status ap_ace_forces_noalloc(const ap_potential* pot, int n_atoms,
     const unsigned long long key = potential_key(*pot);
     if (!D.tables || D.key != key) {
         std::string err;
-        if (build_ace_tables(*pot, g_noalloc_tables, err)) return noalloc_fail(AP_ERR_ARG, err);
+        if (build_ace_tables(*pot, g_noalloc_dev_tables, err)) return noalloc_fail(AP_ERR_ARG, err);
+        build_ace_tc(g_noalloc_dev_tables, g_noalloc_tables);
         D.tables = false;
         // pageable source: the call returns once the host buffer has been read, and the copy
         // is ordered on `stream` after the previous call's kernels there
-        e = cudaMemcpyAsync(scratch, &g_noalloc_tables, sizeof(AceDev), cudaMemcpyHostToDevice, s);
+        e = cudaMemcpyAsync(scratch, &g_noalloc_tables, sizeof(AceTc), cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return noalloc_fail(AP_ERR_CUDA, std::string("ap_ace_forces_noalloc: ") + cudaGetErrorString(e));
         D.tables = true;
         D.key = key;
@@ -2152,7 +1347,7 @@ extern "C" ap_status ap_ace_forces_noalloc(const ap_potential* pot, int n_atoms,
     if (e != cudaSuccess) return noalloc_fail(AP_ERR_CUDA, std::string("ap_ace_forces_noalloc: ") + cudaGetErrorString(e));
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    k_ace_noalloc<<<nsm, kWarps * 32, ace_smem_bytes(), s>>>(d_nbr_idx, d_rvec, n_atoms, max_nb, d_w, scratch, d_energy);
+    k_ace_noalloc<<<nsm, kNaWarps * 32, noalloc_smem_bytes(), s>>>(d_nbr_idx, d_rvec, n_atoms, max_nb, d_w, scratch, d_energy);
     k_ace_noalloc_forces<<<(n_atoms + 255) / 256, 256, 0, s>>>(scratch, n_atoms, d_force);
     e = cudaGetLastError();
     if (e != cudaSuccess) return noalloc_fail(AP_ERR_CUDA, std::string("ap_ace_forces_noalloc: ") + cudaGetErrorString(e));

@@ -62,6 +62,38 @@ def ace_flops_per_atom(n_neighbors):
     return tot + PER_NEIGHBOR_FLOPS * n_neighbors
 
 
+def ace_tc_contract_work():
+    """Work per compacted atom of the tensor-core contraction kernel (FMA = 2 FLOPs), counted
+    over structurally nonzero index combinations as above:
+
+      fp32:   the arithmetic left on the FP32 lanes: the Gaunt products P of the nine triples
+              with l1 > 0 (per active (n1, n2) pair g12 + 2 nnz; 36 pairs when l1 = l2, else
+              64) and their first/second-factor adjoint (2 nnz + 3 g12 per pair); the
+              two-factor terms with the five (0, l, l) triples folded in (36 pairs, per l:
+              forward W_l FMA, per density 8 FMA for the folded coefficient and 1 FMA;
+              adjoint 3 W_l + 50); the epilogue per l3 (phi and the third-factor gradient);
+              the one-factor terms.
+      tensor: the two coefficient contractions R = C^T P and Q = C [A; sA] over the active
+              pairs: 2 x 16 x pairs x W3 FLOPs each.
+      tensor_executed: what the mma.sync tiles execute: three TF32 products (3xTF32) of
+              16 x 64 x (W3 rounded up to 8) per contraction."""
+    fp32 = tensor = executed = 0
+    for (l1, l2, l3), nnz in zip(TRIPLES, NNZ):
+        if l1 == 0:
+            continue
+        g12 = len({(a, b) for a, b, _ in _pattern(l1, l2, l3)})
+        w3 = 2 * l3 + 1
+        pairs = 36 if l1 == l2 else 64
+        fp32 += pairs * (g12 + 2 * nnz) + pairs * (2 * nnz + 3 * g12)
+        tensor += 2 * (2 * 16 * pairs * w3)
+        executed += 2 * 3 * (2 * 16 * 64 * (8 * ((w3 + 7) // 8)))
+    fp32 += 36 * sum(2 * (2 * l + 1) + 2 * (16 + 2) for l in range(5))
+    fp32 += 36 * sum(3 * (2 * l + 1) + 50 for l in range(5))
+    fp32 += 2 * 2 * 8 * sum(2 * l + 1 for l in (2, 3, 4)) + 2 * 8 * sum(2 * l + 1 for l in (2, 3, 4))
+    fp32 += 8 * 4 + 8 * 2
+    return {"fp32": fp32, "tensor": tensor, "tensor_executed": executed}
+
+
 def eam_bytes_per_atom(n_list):
     """Minimum HBM bytes of the two EAM passes per atom with a materialised list:
     list entries read twice (4 B each), own position/weight 16 B twice, forces 12 B,

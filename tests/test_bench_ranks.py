@@ -60,3 +60,11 @@ def test_roofline_line_from_stage_events():
     assert r["alone"]["frac"] > r["frac"]
     assert r["peak"] == 80.0 and abs(r["peak_derived_unit_count"] - 152 * 128 * 2 * 2.0e9 / 1e12) < 1e-9
     assert bench.ace_kernel_roofline(prof, 5, None, {}, "test", atoms, fma_peak=80.0)["alone"] is None
+    # the split by pipe: FP32-lane work against the FP32 peak, tensor-core products against the
+    # TF32 peak (measured BF16 x 1.1 / 2.25)
+    from paper_2505_12958_gb300.workload import ace_tc_contract_work
+    w = ace_tc_contract_work()
+    r = bench.ace_kernel_roofline(prof, 5, None, {"bf16_tflops": 2000.0}, "test", atoms, fma_peak=80.0)
+    assert abs(r["fp32_lanes"]["achieved"] - w["fp32"] * 1000 / 0.5e-3 / 1e12) < 1e-9
+    assert abs(r["tensor"]["peak"] - 2000.0 * 1.1 / 2.25) < 1e-9
+    assert abs(r["tensor"]["frac_executed"] - w["tensor_executed"] * 1000 / 0.5e-3 / 1e12 / r["tensor"]["peak"]) < 1e-12

@@ -30,3 +30,14 @@ def test_pattern_sizes_and_total():
     f = workload.ace_contract_flops_per_atom()
     assert f == 403704
     assert workload.ace_flops_per_atom(10) == f + 10 * workload.PER_NEIGHBOR_FLOPS
+
+
+def test_tensor_core_kernel_work_split():
+    """The tensor-core kernel's work: the coefficient contractions over the active (n1, n2)
+    pairs of the nine triples with l1 > 0 (36 pairs when l1 = l2) and their 3xTF32 tiles."""
+    w = workload.ace_tc_contract_work()
+    tc = [(t, 36 if t[0] == t[1] else 64) for t in TRIPLES if t[0] > 0]
+    assert len(tc) == 9
+    assert w["tensor"] == sum(2 * 2 * 16 * p * (2 * t[2] + 1) for t, p in tc)
+    assert w["tensor_executed"] == sum(2 * 3 * 2 * 16 * 64 * (8 if t[2] < 4 else 16) for t, _ in tc)
+    assert w == {"fp32": 150348, "tensor": 216320, "tensor_executed": 1376256}
