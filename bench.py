@@ -357,7 +357,7 @@ def ace_kernel_roofline(prof, n_steps, c, pk, peak_src, ctx_atoms_in_rc, fma_pea
                                                                         "bracketed, EAM on the main stream")}
 
 
-def serving_bench(torch, n_req, seed=1005, load=0.7, chunk=8, max_active=64):
+def serving_bench(torch, n_req, seed=1005, load=0.7, chunk=8, max_active=64, batched=False, batch_atoms=1024):
     """Continuous-batching server on a Poisson stream of uneven Cu/W requests.
 
     The saturated throughput comes from a closed-loop run (all requests waiting at t = 0);
@@ -369,16 +369,17 @@ def serving_bench(torch, n_req, seed=1005, load=0.7, chunk=8, max_active=64):
     gen_s = time.perf_counter() - t
     base = [r["arrival_s"] for r in reqs]
     work = np.array([len(r["x"]) * r["n_steps"] for r in reqs], dtype=np.float64)
-    Server(keep_arrays=False, chunk=chunk, max_active=max_active).run(reqs[:8], realtime=False)   # warm-up
+    kw = dict(keep_arrays=False, chunk=chunk, max_active=max_active, batched=batched, batch_atoms=batch_atoms)
+    Server(**kw).run(reqs[:8], realtime=False)
     torch.cuda.synchronize()
-    sat = Server(keep_arrays=False, chunk=chunk, max_active=max_active)
+    sat = Server(**kw)
     res = sat.run(reqs, realtime=False)
     makespan = max(r.done_s for r in res)
     sat_rate = work.sum() / makespan
     rate = load * sat_rate / work.mean()
     for r, b in zip(reqs, base):
         r["arrival_s"] = b / rate
-    srv = Server(keep_arrays=False, chunk=chunk, max_active=max_active)
+    srv = Server(**kw)
     res = srv.run(reqs, realtime=True)
     span = max(r.done_s for r in res) - min(r.arrival_s for r in res)
     lat = np.array([r.latency_s for r in res])
@@ -389,6 +390,9 @@ def serving_bench(torch, n_req, seed=1005, load=0.7, chunk=8, max_active=64):
             "p50_latency_ms": percentile_ms(res, 50), "p99_latency_ms": percentile_ms(res, 99),
             "mean_latency_ms": float(lat.mean() * 1e3), "max_latency_ms": float(lat.max() * 1e3),
             "peak_active": srv.peak_active, "chunk_steps": chunk, "max_active": max_active,
+            "launch": ("requests of at most %d atoms: one launch per stage for all of them (ap_step_batch); "
+                       "larger ones: their own step graphs on their own streams" % batch_atoms) if batched else
+                      "each request's own step graphs on its own stream",
             "generation_s": gen_s,
             "workload": "Cu/W 50/50; bulk, vacancy, (001) and (110) surfaces, indented; 64-50,000 atoms "
                         "log-uniform; 0-1000 K; ACE fraction U(0,1) via the sphere radius; 1-100 steps; "
@@ -555,6 +559,11 @@ def main():
                      help="skip the sampled oracle check of the timed context's final state")
     ap_.add_argument("--serve-chunk", type=int, default=8, help="MD steps per request per scheduling pass")
     ap_.add_argument("--serve-active", type=int, default=64, help="cap on concurrently active requests")
+    ap_.add_argument("--serve-batch-atoms", type=int, default=1024,
+                     help="with --serve-batched: requests of at most this many atoms are stepped by the "
+                          "batched launches (one launch per stage for all of them)")
+    ap_.add_argument("--serve-batched", action="store_true",
+                     help="--mode serve: the batched form instead of each request's own step graphs")
     ap_.add_argument("--mode", default="ap", choices=["ap", "serve", "precision", "autograd"],
                      help="ap: the metric line; serve: only the serving run; precision: the A_nlm "
                           "precision sweep on the 2M-atom Cu slab; autograd: forward+backward of the "
@@ -567,7 +576,8 @@ def main():
         import paper_2505_12958_gb300 as ap
         ap.build()
         if args.mode == "serve":
-            out = serving_bench(torch, args.serve_requests, chunk=args.serve_chunk, max_active=args.serve_active)
+            out = serving_bench(torch, args.serve_requests, chunk=args.serve_chunk, max_active=args.serve_active,
+                                batched=args.serve_batched, batch_atoms=args.serve_batch_atoms)
         elif args.mode == "precision":
             out = precision_sweep(torch, ap, args.steps, args.warmup)
         else:
@@ -661,6 +671,9 @@ def main():
 
     serving = (serving_bench(torch, args.serve_requests, chunk=args.serve_chunk, max_active=args.serve_active)
                if args.serve_requests > 0 else None)
+    serving_batched = (serving_bench(torch, args.serve_requests, chunk=args.serve_chunk, max_active=args.serve_active,
+                                     batched=True, batch_atoms=args.serve_batch_atoms)
+                       if args.serve_requests > 0 else None)
     precision = precision_leg(torch, ap, steps=args.precision_steps) if args.precision_steps > 0 and rank == 0 else None
     csp = csp_timing(torch, ap, c)
 
@@ -687,6 +700,7 @@ def main():
         line["precision"] = precision
     if serving is not None:
         line["serving"] = serving
+        line["serving_batched"] = serving_batched
     csp["per_step_share_at_every_step"] = csp["csp_ms"] / line["ms_per_step"]
     line["csp_weights"] = csp
     line.update(extra)

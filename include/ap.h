@@ -182,17 +182,25 @@ ap_status ap_compute_forces_host(ap_ctx* ctx, const double* h_pos, float* h_forc
 ap_status ap_step(ap_ctx* ctx, int n_steps, double dt_fs, void* stream);
 
 /* Serving form: n_steps[k] velocity-Verlet steps (dt_fs) for each of n_ctx independent
- * contexts, each issued on its own context's stream (give every context its own
- * non-blocking stream at ap_init and the steps of different contexts overlap on the
- * device).  A context's results do not depend on which others are stepped with it.
- * Asynchronous; returns the first error. */
-ap_status ap_step_batch(ap_ctx* const* ctxs, const int* n_steps, int n_ctx, double dt_fs);
+ * contexts, batched: every stage of a step (kick-drift, neighbour rebuild, weights and
+ * compaction, list build, EAM density and forces, ACE basis, contraction and pair forces,
+ * blend with the second half kick) is ONE kernel launch on `stream` for all contexts that
+ * still have steps to go.  The per-atom stages give each context its own blocks of the
+ * launch; the ACE stages share one persistent grid over the compacted atoms of all contexts,
+ * and contexts with the same potential share one coefficient table, staged once per block.
+ * The batch waits for each context's earlier work on its own stream, and each context's
+ * stream waits for the batch, so calls on the contexts before and after stay ordered.  A
+ * context with a thermostat, stage timing or a precision mode other than AP_ACE_FP32 (and
+ * any beyond the first 256) is stepped on its own stream instead.  Every context's results
+ * are the same bits as when it is stepped alone (the same per-atom arithmetic, and the
+ * integer force sums do not depend on order).  Asynchronous; returns the first error. */
+ap_status ap_step_batch(ap_ctx* const* ctxs, const int* n_steps, int n_ctx, double dt_fs, void* stream);
 
-/* Serving form of ap_compute_forces: one AP force evaluation of the library-owned
- * positions of each of n_ctx contexts, each on its own context's stream.  Arguments are
- * checked before anything is launched (AP_ERR_ARG for a NULL entry).  Asynchronous;
- * returns the first error. */
-ap_status ap_compute_forces_batch(ap_ctx* const* ctxs, int n_ctx);
+/* Serving form of ap_compute_forces: one AP force evaluation of the library-owned positions
+ * of each of n_ctx contexts, batched as ap_step_batch (one launch per stage on `stream`).
+ * Arguments are checked before anything is launched (AP_ERR_ARG for a NULL entry).
+ * Asynchronous; returns the first error. */
+ap_status ap_compute_forces_batch(ap_ctx* const* ctxs, int n_ctx, void* stream);
 
 /* Thermostat of a group of atoms (Appendix A: during the indentation the central part of
  * the slab is an NVT ensemble, Nose-Hoover with damping time gamma_T^NH = 0.1 ps at 300 K

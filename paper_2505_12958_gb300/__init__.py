@@ -331,24 +331,26 @@ def csp_params(d):
     return p
 
 
-def step_batch(ctxs, n_steps, dt):
-    """n_steps[k] MD steps for each context ctxs[k], each on its own stream (ap_step_batch)."""
+def step_batch(ctxs, n_steps, dt, stream=None):
+    """n_steps[k] MD steps for each context ctxs[k], one kernel launch per stage for all of
+    them on `stream` (ap_step_batch)."""
     L = _capi.lib()
     k = len(ctxs)
     hs = (C.c_void_p * k)(*[c._h.value for c in ctxs])
     ns = (C.c_int * k)(*[int(s) for s in n_steps])
-    st = L.ap_step_batch(hs, ns, k, float(dt))
+    st = L.ap_step_batch(hs, ns, k, float(dt), _stream(stream))
     if st != 0:
         msgs = "; ".join(L.ap_last_error(c._h).decode() for c in ctxs)
         raise APError(st, msgs)
 
 
-def compute_forces_batch(ctxs):
-    """One force evaluation for each context, each on its own stream (ap_compute_forces_batch)."""
+def compute_forces_batch(ctxs, stream=None):
+    """One force evaluation for each context, one kernel launch per stage for all of them on
+    `stream` (ap_compute_forces_batch)."""
     L = _capi.lib()
     k = len(ctxs)
     hs = (C.c_void_p * k)(*[c._h.value for c in ctxs])
-    st = L.ap_compute_forces_batch(hs, k)
+    st = L.ap_compute_forces_batch(hs, k, _stream(stream))
     if st != 0:
         raise APError(st, "; ".join(L.ap_last_error(c._h).decode() for c in ctxs))
 

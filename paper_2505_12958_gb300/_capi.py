@@ -78,8 +78,8 @@ def lib():
         "ap_compute_forces": (I, [VP, VP, VP, VP]),
         "ap_compute_forces_host": (I, [VP, PD, PF, PD, VP]),
         "ap_step": (I, [VP, I, D, VP]),
-        "ap_step_batch": (I, [C.POINTER(VP), PI, I, D]),
-        "ap_compute_forces_batch": (I, [C.POINTER(VP), I]),
+        "ap_step_batch": (I, [C.POINTER(VP), PI, I, D, VP]),
+        "ap_compute_forces_batch": (I, [C.POINTER(VP), I, VP]),
         "ap_csp_accumulate": (I, [VP, P(CspParams), VP]),
         "ap_set_thermostat": (I, [VP, P(Thermostat), C.POINTER(C.c_ubyte)]),
         "ap_csp_update_weights": (I, [VP, P(CspParams), PI]),

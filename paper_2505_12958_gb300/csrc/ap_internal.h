@@ -140,7 +140,10 @@ struct Ctx {
     EamDev* eam_d = nullptr;
     bool energy_fresh = false;                           // energy pass done for the last forces
     AceDev* ace_h = nullptr;                             // host coefficient tensors
-    AceTc* ace_tc_d = nullptr;                           // device ACE tables
+    const AceTc* ace_tc_d = nullptr;                     // device ACE tables (shared per potential)
+    struct CtxDev* desc_d = nullptr;                     // device descriptor for batched launches
+    unsigned char desc_h[1024];                          // its last uploaded contents
+    bool desc_valid = false;
     GridDev grid{};
     float4* D = nullptr;                                 // cell-offset vectors, FP32
     float4* Dlo = nullptr;                               // their FP32 residuals (o . cellvec - D)
@@ -266,6 +269,73 @@ int launch_pos_in(Ctx& c, cudaStream_t s, const double* pos_aos);
 int launch_csp(Ctx& c, cudaStream_t s, const ap_csp_params& P, float* d_csp);
 int launch_csp_weights(Ctx& c, cudaStream_t s, const ap_csp_params& P, int nacc, const int S[3]);
 int launch_check(Ctx& c, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------
+// Batched launches (serving): one launch per stage runs the stage for several contexts.
+// The contexts' device pointers and parameters travel as an array of descriptors; a
+// per-atom stage gives context k the blocks start[k] .. start[k + 1] - 1 of its grid (block
+// b acts as block b - start[k] of that context), and the ACE stages share a persistent grid
+// over chunks of compacted atoms of all contexts (prefix sums of the device atom counts).
+// ---------------------------------------------------------------------------------
+struct CtxDev {
+    int n, ncode, cap, load_cap;
+    double mass;                      // amu (the half kick is 0.5 dt kFtm / mass, as on the host)
+    double lim2;                      // (skin / 2)^2: the list displacement bound
+    double ace_c1_0;
+    GridDev grid;
+    DynDev dyn;
+    double *x, *v, *xb;
+    float* f;
+    float4* pos4;
+    float *uxi, *w, *e_ace, *ace_A, *ace_dA, *vir_ace;
+    double *e_emb, *e_eam, *w_fixed, *d_time;
+    unsigned long long* acc;
+    unsigned char* fixed;
+    int *cell, *cell_count, *cell_start, *cell_atoms, *nbr, *nnbr, *ace_list, *flags;
+    long long* d_step;
+    long long* load_ring;
+    double* load_ring_t;
+    const EamDev* eam;
+    const AceTc* ace;
+    const float4* D;
+};
+
+// The batch travels as a kernel parameter (about 5 KB): each context's resident descriptor and
+// the block prefixes of the per-atom stages.
+constexpr int kMaxBatchCtx = 256;
+struct BatchTable {
+    int nctx;
+    int atoms;                        // sum of the contexts' atom counts
+    const CtxDev* d[kMaxBatchCtx];
+    int b256[kMaxBatchCtx + 1];       // blocks of 256 threads per context (atoms)
+    int b128[kMaxBatchCtx + 1];       // blocks of 128 threads per context (atoms)
+    int bcell[kMaxBatchCtx + 1];      // blocks of 256 threads per context (cells)
+};
+
+static_assert(sizeof(CtxDev) <= sizeof(Ctx::desc_h), "descriptor copy fits its host record");
+
+void fill_ctx_dev(const Ctx& c, CtxDev& d);
+int launch_batch_step_pre(const BatchTable& t, double dt, cudaStream_t s);
+int launch_batch_check(const BatchTable& t, cudaStream_t s);
+int launch_batch_rebuild(const BatchTable& t, cudaStream_t s);
+int launch_batch_prepare(const BatchTable& t, cudaStream_t s);
+int launch_batch_eam(const BatchTable& t, cudaStream_t s);
+int launch_batch_ace(const BatchTable& t, int dev, cudaStream_t s);
+int launch_batch_blend(const BatchTable& t, double kick_dt, int record, cudaStream_t s);
+
+// ACE device tables shared by every context of the same potential on a device (built once,
+// kept until the process exits): a batched contraction stages them once per block
+const AceTc* shared_ace_tables(const AceTc& host, int dev, std::string& err);
+
+__host__ __device__ __forceinline__ int batch_find(const int* start, int nctx, int b) {
+    int lo = 0, hi = nctx - 1;                    // the k with start[k] <= b < start[k + 1]
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 // host-side tables (tables.cpp)
 int build_eam_tables(const ap_potential& p, EamDev& out, std::string& err);

@@ -59,6 +59,7 @@ struct ap_ctx {
 namespace {
 
 thread_local std::string g_init_err;
+bool injected_alloc_failure();
 
 }  // namespace
 
@@ -66,6 +67,51 @@ namespace ap {
 // the text ap_last_error(NULL) returns on this thread: the last failed ap_init or
 // ap_ace_forces_noalloc
 void set_global_error(const std::string& m) { g_init_err = m; }
+
+const AceTc* shared_ace_tables(const AceTc& host, int dev, std::string& err) {
+    struct Entry { int dev; std::unique_ptr<AceTc> host; AceTc* d; };
+    static std::mutex mu;
+    static std::vector<Entry> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    for (const Entry& e : cache)
+        if (e.dev == dev && std::memcmp(e.host.get(), &host, sizeof(AceTc)) == 0) return e.d;
+    std::unique_ptr<AceTc> copy(new (std::nothrow) AceTc(host));
+    AceTc* d = nullptr;
+    if (!copy || injected_alloc_failure() || cudaMalloc((void**)&d, sizeof(AceTc)) != cudaSuccess) {
+        cudaGetLastError();
+        err = "ACE table allocation failed";
+        return nullptr;
+    }
+    if (cudaMemcpy(d, &host, sizeof(AceTc), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d);
+        err = "ACE table upload failed";
+        return nullptr;
+    }
+    cache.push_back({dev, std::move(copy), d});
+    return d;
+}
+
+void fill_ctx_dev(const Ctx& c, CtxDev& d) {
+    std::memset(&d, 0, sizeof(d));
+    d.n = c.n;
+    d.ncode = c.grid.ncode;
+    d.cap = c.cap;
+    d.load_cap = c.load_cap;
+    d.mass = c.mass;
+    const double lim = 0.5 * c.skin;
+    d.lim2 = lim * lim;
+    d.ace_c1_0 = c.ace_c1_0;
+    d.grid = c.grid;
+    d.dyn = c.dyn;
+    d.x = c.x; d.v = c.v; d.xb = c.xb; d.f = c.f; d.pos4 = c.pos4;
+    d.uxi = c.uxi; d.w = c.w; d.e_ace = c.e_ace; d.ace_A = c.ace_A; d.ace_dA = c.ace_dA; d.vir_ace = c.vir_ace;
+    d.e_emb = c.e_emb; d.e_eam = c.e_eam; d.w_fixed = c.w_fixed; d.d_time = c.d_time;
+    d.acc = c.acc; d.fixed = c.fixed;
+    d.cell = c.cell; d.cell_count = c.cell_count; d.cell_start = c.cell_start; d.cell_atoms = c.cell_atoms;
+    d.nbr = c.nbr; d.nnbr = c.nnbr; d.ace_list = c.ace_list; d.flags = c.flags;
+    d.d_step = c.d_step; d.load_ring = c.load_ring; d.load_ring_t = c.load_ring_t;
+    d.eam = c.eam_d; d.ace = c.ace_tc_d; d.D = c.D;
+}
 }  // namespace ap
 
 namespace {
@@ -319,7 +365,7 @@ void pinned_give(char* p) {
 
 void free_all(ap_ctx* xc) {
     ap::Ctx& c = xc->c;
-    void* ps[] = {c.eam_d, c.ace_tc_d, c.D, c.Dlo, c.pos_lo, c.ace_A, c.ace_dA, c.x, c.v, c.xb, c.f, c.pos4, c.uxi, c.w, c.e_emb, c.e_eam, c.e_ace,
+    void* ps[] = {c.eam_d, c.D, c.Dlo, c.pos_lo, c.ace_A, c.ace_dA, c.x, c.v, c.xb, c.f, c.pos4, c.uxi, c.w, c.e_emb, c.e_eam, c.e_ace,
                   c.vir_eam, c.vir_ace, c.acc, c.fixed, c.w_fixed, c.cell, c.cell_count, c.cell_start,
                   c.cell_atoms, c.nbr, c.nnbr, c.ace_list, c.flags, c.d_time, c.partials, c.totals, c.e_atom,
                   c.pos_stage, c.f_stage, c.csp_sum, c.csp_under, c.csp_w0, c.csp_wnew, c.csp_seeds, c.csp_nseed,
@@ -597,7 +643,7 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
     c.nred = (n + ap::kRedBlock - 1) / ap::kRedBlock;
     {
         ArenaPlan plan;
-        plan.add(&c.eam_d, 1); plan.add(&c.ace_tc_d, 1); plan.add(&c.D, 125); plan.add(&c.Dlo, 125);
+        plan.add(&c.eam_d, 1); plan.add(&c.desc_d, 1); plan.add(&c.D, 125); plan.add(&c.Dlo, 125);
         plan.add(&c.pos_lo, N); plan.add(&c.x, 3 * N); plan.add(&c.v, 3 * N); plan.add(&c.xb, 3 * N);
         plan.add(&c.f, 3 * N); plan.add(&c.pos4, N); plan.add(&c.uxi, N); plan.add(&c.w, N);
         plan.add(&c.e_emb, N); plan.add(&c.e_eam, N); plan.add(&c.e_ace, N);
@@ -630,10 +676,13 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
         if (e == cudaSuccess) e = cudaMemsetAsync(dst, 0, bytes, c.stream);
     };
     cp(c.eam_d, &c.eam_h, sizeof(ap::EamDev));
-    std::unique_ptr<ap::AceTc> tc(new (std::nothrow) ap::AceTc());
-    if (!tc) { c.err = "host allocation"; return fail(AP_ERR_OOM); }
-    ap::build_ace_tc(*c.ace_h, *tc);
-    cp(c.ace_tc_d, tc.get(), sizeof(ap::AceTc));
+    {
+        std::unique_ptr<ap::AceTc> tc(new (std::nothrow) ap::AceTc());
+        if (!tc) { c.err = "host allocation"; return fail(AP_ERR_OOM); }
+        ap::build_ace_tc(*c.ace_h, *tc);
+        c.ace_tc_d = ap::shared_ace_tables(*tc, c.dev, err);
+        if (!c.ace_tc_d) { c.err = err; return fail(AP_ERR_OOM); }
+    }
     cp(c.D, D.data(), D.size() * sizeof(float4));
     cp(c.Dlo, Dlo.data(), Dlo.size() * sizeof(float4));
     cp(c.x, soa.data(), 3 * N * sizeof(double));
@@ -891,25 +940,205 @@ ap_status ap_step(ap_ctx* xc, int n_steps, double dt, void* stream) {
     return AP_OK;
 }
 
-ap_status ap_step_batch(ap_ctx* const* ctxs, const int* n_steps, int n_ctx, double dt) {
+}  // extern "C"
+
+namespace {
+
+// the context's resident descriptor for batched launches, re-sent (on its own stream) when
+// its contents changed: list capacity, box, load ring
+void refresh_desc(ap_ctx* xc) {
+    ap::Ctx& c = xc->c;
+    ap::CtxDev d;
+    ap::fill_ctx_dev(c, d);
+    if (c.desc_valid && std::memcmp(c.desc_h, &d, sizeof(d)) == 0) return;
+    std::memcpy(c.desc_h, &d, sizeof(d));
+    cudaMemcpyAsync(c.desc_d, c.desc_h, sizeof(d), cudaMemcpyHostToDevice, c.stream);
+    c.desc_valid = true;
+}
+
+// the batch table of a set of contexts: their descriptors and block prefixes
+void batch_table(const std::vector<ap_ctx*>& cs, ap::BatchTable& t) {
+    t.nctx = (int)cs.size();
+    t.atoms = 0;
+    t.b256[0] = t.b128[0] = t.bcell[0] = 0;
+    for (int k = 0; k < t.nctx; ++k) {
+        const ap::Ctx& c = cs[k]->c;
+        t.d[k] = c.desc_d;
+        t.b256[k + 1] = t.b256[k] + (c.n + 255) / 256;
+        t.b128[k + 1] = t.b128[k] + (c.n + 127) / 128;
+        t.bcell[k + 1] = t.bcell[k] + (c.grid.ncell + 255) / 256;
+        t.atoms += c.n;
+    }
+}
+
+// one AP force evaluation of every context of t, one launch per stage; kick_dt > 0: the
+// blend applies the second half kick of a step (whose kick-drift ran the displacement test)
+int batch_forces(const ap::BatchTable& t, int dev, cudaStream_t s, bool after_drift, double kick_dt) {
+    int k = 0;
+    if (!after_drift) k += ap::launch_batch_check(t, s);
+    k += ap::launch_batch_rebuild(t, s);
+    k += ap::launch_batch_prepare(t, s);
+    k += ap::launch_batch_eam(t, s);
+    k += ap::launch_batch_ace(t, dev, s);
+    k += ap::launch_batch_blend(t, kick_dt, kick_dt > 0.0 ? 1 : 0, s);
+    return k;
+}
+
+// contexts a batched launch can take: the plain step (no thermostat, no stage timing), the
+// FP32 atomic base, the current device
+bool batchable(const ap::Ctx& c, int dev) {
+    return c.prof == 0 && c.thermo_kind == AP_THERMO_NONE && c.ace_prec == AP_ACE_FP32 && c.dev == dev;
+}
+
+// the batch stream waits for the contexts' earlier work
+void batch_join_in(const std::vector<ap_ctx*>& cs, cudaStream_t bs) {
+    for (ap_ctx* xc : cs) {
+        refresh_desc(xc);
+        cudaEvent_t e = get_event(xc);
+        cudaEventRecord(e, xc->c.stream);
+        cudaStreamWaitEvent(bs, e, 0);
+        xc->free_ev.push_back(e);
+    }
+}
+
+// the contexts' later work waits for the batch
+void batch_join_out(const std::vector<ap_ctx*>& cs, cudaStream_t bs) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return;
+    cudaEventRecord(e, bs);
+    for (ap_ctx* xc : cs) cudaStreamWaitEvent(xc->c.stream, e, 0);
+    cudaEventDestroy(e);
+}
+
+ap_status batch_status(const std::vector<ap_ctx*>& cs, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) return AP_OK;
+    ap_status st = AP_OK;
+    for (ap_ctx* xc : cs) st = cuda_check(xc->c, e, what);
+    return st;
+}
+
+// the batched form of ap_step for the contexts in cs (all batchable), with their step counts
+ap_status batch_steps(std::vector<ap_ctx*> cs, std::vector<int> ns, double dt, cudaStream_t bs) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    // contexts sharing a potential side by side: a block of the batched contraction then
+    // stages coefficient tables only where the potential changes
+    std::vector<int> order(cs.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return cs[a]->c.ace_tc_d < cs[b]->c.ace_tc_d; });
+    std::vector<ap_ctx*> sc;
+    std::vector<int> sn;
+    for (int k : order) { sc.push_back(cs[k]); sn.push_back(ns[k]); }
+    batch_join_in(sc, bs);
+    std::unique_ptr<ap::BatchTable> t(new ap::BatchTable());
+    std::vector<ap_ctx*> init;
+    for (ap_ctx* xc : sc)
+        if (!xc->c.forces_valid) init.push_back(xc);
+    if (!init.empty()) {
+        batch_table(init, *t);
+        const int k = batch_forces(*t, dev, bs, false, 0.0);
+        for (ap_ctx* xc : init) { xc->c.launches += k; xc->c.forces_valid = true; }
+    }
+    int maxs = 0;
+    for (int v : sn) maxs = std::max(maxs, v);
+    std::vector<ap_ctx*> active = sc;
+    std::vector<int> left = sn;
+    bool table = false;
+    for (int st = 0; st < maxs; ++st) {
+        // contexts whose steps are done leave the batch and are released to their own streams
+        std::vector<ap_ctx*> now, done;
+        std::vector<int> nl;
+        for (size_t k = 0; k < active.size(); ++k) {
+            if (left[k] > 0) { now.push_back(active[k]); nl.push_back(left[k]); }
+            else done.push_back(active[k]);
+        }
+        if (!done.empty()) batch_join_out(done, bs);
+        if (now.size() != active.size() || !table) {
+            active = now;
+            left = nl;
+            batch_table(active, *t);
+            table = true;
+        }
+        int k = ap::launch_batch_step_pre(*t, dt, bs);
+        k += batch_forces(*t, dev, bs, true, dt);
+        for (size_t q = 0; q < active.size(); ++q) {
+            ap::Ctx& c = active[q]->c;
+            c.launches += k;
+            c.t += dt;
+            c.step += 1;
+            left[q] -= 1;
+        }
+    }
+    for (ap_ctx* xc : sc) {
+        xc->c.forces_valid = true;
+        xc->c.energy_fresh = false;
+    }
+    batch_join_out(active, bs);
+    return batch_status(sc, cudaSuccess, "batched step");
+}
+
+}  // namespace
+
+extern "C" {
+
+ap_status ap_step_batch(ap_ctx* const* ctxs, const int* n_steps, int n_ctx, double dt, void* stream) {
     if (!ctxs || !n_steps || n_ctx < 0 || !(dt > 0.0)) return AP_ERR_ARG;
     for (int k = 0; k < n_ctx; ++k)
         if (!ctxs[k] || n_steps[k] < 0) return AP_ERR_ARG;
+    int dev = 0;
+    cudaGetDevice(&dev);
     ap_status first = AP_OK;
+    std::vector<ap_ctx*> bc;
+    std::vector<int> bn;
     for (int k = 0; k < n_ctx; ++k) {
-        ap_status st = ap_step(ctxs[k], n_steps[k], dt, nullptr);
+        if (n_steps[k] == 0) continue;
+        if (batchable(ctxs[k]->c, dev) && (int)bc.size() < ap::kMaxBatchCtx) {
+            bc.push_back(ctxs[k]);
+            bn.push_back(n_steps[k]);
+        } else {
+            ap_status st = ap_step(ctxs[k], n_steps[k], dt, nullptr);
+            if (st != AP_OK && first == AP_OK) first = st;
+        }
+    }
+    if (!bc.empty()) {
+        ap_status st = batch_steps(bc, bn, dt, (cudaStream_t)stream);
         if (st != AP_OK && first == AP_OK) first = st;
     }
     return first;
 }
 
-ap_status ap_compute_forces_batch(ap_ctx* const* ctxs, int n_ctx) {
+ap_status ap_compute_forces_batch(ap_ctx* const* ctxs, int n_ctx, void* stream) {
     if (!ctxs || n_ctx < 0) return AP_ERR_ARG;
     for (int k = 0; k < n_ctx; ++k)
         if (!ctxs[k]) return AP_ERR_ARG;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaStream_t bs = (cudaStream_t)stream;
     ap_status first = AP_OK;
+    std::vector<ap_ctx*> bc;
     for (int k = 0; k < n_ctx; ++k) {
-        ap_status st = ap_compute_forces(ctxs[k], nullptr, nullptr, nullptr);
+        if (batchable(ctxs[k]->c, dev) && (int)bc.size() < ap::kMaxBatchCtx) {
+            bc.push_back(ctxs[k]);
+        } else {
+            ap_status st = ap_compute_forces(ctxs[k], nullptr, nullptr, nullptr);
+            if (st != AP_OK && first == AP_OK) first = st;
+        }
+    }
+    if (!bc.empty()) {
+        std::stable_sort(bc.begin(), bc.end(), [](ap_ctx* a, ap_ctx* b) { return a->c.ace_tc_d < b->c.ace_tc_d; });
+        batch_join_in(bc, bs);
+        std::unique_ptr<ap::BatchTable> t(new ap::BatchTable());
+        batch_table(bc, *t);
+        const int k = batch_forces(*t, dev, bs, false, 0.0);
+        for (ap_ctx* xc : bc) {
+            xc->c.launches += k;
+            xc->c.forces_valid = true;
+            xc->c.energy_fresh = false;
+        }
+        batch_join_out(bc, bs);
+        ap_status st = batch_status(bc, cudaSuccess, "batched force evaluation");
         if (st != AP_OK && first == AP_OK) first = st;
     }
     return first;

@@ -21,6 +21,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 #include <string>
@@ -375,6 +376,114 @@ __device__ __forceinline__ float3 ace_pair_force(float4 v, float rc, float nrefi
 // stage a1 of the ACE pass: A_nlm = (1/nref) sum_j g_n(r_ij) Y_lm(rhat_ij), stored [atom][lm][n].
 // MODE (AP_ACE_*) sets the precision of the contraction over neighbours: FP32 FMA, tensor
 // cores (3xTF32 split, BF16 or FP16 inputs; FP32 accumulation), or FP64 accumulation.
+// the A_nlm of compacted atom a (stage a1), one warp; neighbour offsets Ds staged by the caller
+template <int MODE>
+__device__ __forceinline__ void basis_atom(const float4* __restrict__ pos4, const int* __restrict__ nbr,
+                                           const int* __restrict__ nnbr, int n, const float4* Ds, float rc,
+                                           float nrefi, const int* __restrict__ ace_list, int* __restrict__ flags,
+                                           float* __restrict__ Aout, int a, BasisSmem& S, int lane) {
+    const int gq = lane >> 2, tq = lane & 3;
+    const float rc2 = rc * rc;
+    const int i = ace_list[a];
+    const int cnt = gather_ace_neighbors(pos4, nbr, n, i, nnbr[i], Ds, rc2, S.nb, S.nbj, lane);
+    if (cnt < 0) {
+        if (lane == 0) { atomicOr(&flags[kFlagErr], kErrAceCapacity); flags[kFlagBad] = i; }
+        return;
+    }
+    float accA[kNmax];
+    double accD[MODE == AP_ACE_FP64 ? kNmax : 1];
+    float acc_tc[2][4];
+#pragma unroll
+    for (int q = 0; q < kNmax; ++q) accA[q] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < (MODE == AP_ACE_FP64 ? kNmax : 1); ++q) accD[q] = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc_tc[q >> 2][q & 3] = 0.0f;
+    for (int t0 = 0; t0 < cnt; t0 += kTile) {
+        basis_tile(S.nb, t0, cnt, rc, S.tileY, S.tileG, lane);
+        __syncwarp();
+        const int nt = min(kTile, cnt - t0);
+        if (MODE == AP_ACE_FP32) {
+            basis_accum_fp32(S.tileY, S.tileG, nt, lane, accA);
+        } else if (MODE == AP_ACE_FP64) {
+            if (lane < kNLM) {
+                for (int jj2 = 0; jj2 < nt; ++jj2) {
+                    const float y = S.tileY[jj2][lane];
+                    const float4 g0 = *reinterpret_cast<const float4*>(&S.tileG[jj2][0]);
+                    const float4 g1 = *reinterpret_cast<const float4*>(&S.tileG[jj2][4]);
+                    const float gg[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+#pragma unroll
+                    for (int q = 0; q < kNmax; ++q) accD[q] = fma((double)y, (double)gg[q], accD[q]);
+                }
+            }
+        } else if (MODE == AP_ACE_TC_TF32X3) {
+#pragma unroll
+            for (int k0 = 0; k0 < kTile; k0 += 8) {
+                const float bv0 = S.tileG[k0 + tq][gq], bv1 = S.tileG[k0 + tq + 4][gq];
+                const uint32_t bh0 = to_tf32(bv0), bh1 = to_tf32(bv1);
+                const uint32_t bl0 = to_tf32(bv0 - __uint_as_float(bh0)), bl1 = to_tf32(bv1 - __uint_as_float(bh1));
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    const int m0 = 16 * mt;
+                    const float av[4] = {yt(S, m0 + gq, k0 + tq), yt(S, m0 + gq + 8, k0 + tq),
+                                         yt(S, m0 + gq, k0 + tq + 4), yt(S, m0 + gq + 8, k0 + tq + 4)};
+                    uint32_t ah[4], al[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        ah[q] = to_tf32(av[q]);
+                        al[q] = to_tf32(av[q] - __uint_as_float(ah[q]));
+                    }
+                    mma_tf32(acc_tc[mt], al[0], al[1], al[2], al[3], bh0, bh1);
+                    mma_tf32(acc_tc[mt], ah[0], ah[1], ah[2], ah[3], bl0, bl1);
+                    mma_tf32(acc_tc[mt], ah[0], ah[1], ah[2], ah[3], bh0, bh1);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k0 = 0; k0 < kTile; k0 += 16) {
+                const uint32_t b0 = pack2<MODE>(S.tileG[k0 + 2 * tq][gq], S.tileG[k0 + 2 * tq + 1][gq]);
+                const uint32_t b1 = pack2<MODE>(S.tileG[k0 + 2 * tq + 8][gq], S.tileG[k0 + 2 * tq + 9][gq]);
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    const int r0 = 16 * mt + gq, r1 = r0 + 8, c0 = k0 + 2 * tq;
+                    const uint32_t a0 = pack2<MODE>(yt(S, r0, c0), yt(S, r0, c0 + 1));
+                    const uint32_t a1 = pack2<MODE>(yt(S, r1, c0), yt(S, r1, c0 + 1));
+                    const uint32_t a2 = pack2<MODE>(yt(S, r0, c0 + 8), yt(S, r0, c0 + 9));
+                    const uint32_t a3 = pack2<MODE>(yt(S, r1, c0 + 8), yt(S, r1, c0 + 9));
+                    mma_16bit<MODE>(acc_tc[mt], a0, a1, a2, a3, b0, b1);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    if (MODE == AP_ACE_FP32 || MODE == AP_ACE_FP64) {
+        if (lane < kNLM) {
+            if (MODE == AP_ACE_FP64) {
+#pragma unroll
+                for (int q = 0; q < kNmax; ++q) accA[q] = (float)(accD[q] * (double)nrefi);
+            } else {
+#pragma unroll
+                for (int q = 0; q < kNmax; ++q) accA[q] *= nrefi;
+            }
+            float4* o = reinterpret_cast<float4*>(Aout + ((size_t)a * kNLM + lane) * kNmax);
+            o[0] = make_float4(accA[0], accA[1], accA[2], accA[3]);
+            o[1] = make_float4(accA[4], accA[5], accA[6], accA[7]);
+        }
+    } else {
+        // D fragment: (row g, cols 2t, 2t+1) and (row g + 8, same cols) of each 16-row tile
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            const int r0 = 16 * mt + gq, r1 = r0 + 8;
+            if (r0 < kNLM)
+                *reinterpret_cast<float2*>(Aout + ((size_t)a * kNLM + r0) * kNmax + 2 * tq) =
+                    make_float2(acc_tc[mt][0] * nrefi, acc_tc[mt][1] * nrefi);
+            if (r1 < kNLM)
+                *reinterpret_cast<float2*>(Aout + ((size_t)a * kNLM + r1) * kNmax + 2 * tq) =
+                    make_float2(acc_tc[mt][2] * nrefi, acc_tc[mt][3] * nrefi);
+        }
+    }
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(256) k_ace_basis(const float4* __restrict__ pos4, const int* __restrict__ nbr,
                                                    const int* __restrict__ nnbr, int n, const float4* __restrict__ Dtab,
@@ -387,109 +496,11 @@ __global__ void __launch_bounds__(256) k_ace_basis(const float4* __restrict__ po
     __syncthreads();
     pdl_wait();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gq = lane >> 2, tq = lane & 3;
     BasisSmem& S = WS[warp];
-    const float rc = tab->rc, rc2 = rc * rc, nrefi = tab->nref_inv;
+    const float rc = tab->rc, nrefi = tab->nref_inv;
     const int n_ace = flags[kFlagNAce];
     for (int a = blockIdx.x * 8 + warp; a < n_ace; a += gridDim.x * 8) {
-        const int i = ace_list[a];
-        const int cnt = gather_ace_neighbors(pos4, nbr, n, i, nnbr[i], Ds, rc2, S.nb, S.nbj, lane);
-        if (cnt < 0) {
-            if (lane == 0) { atomicOr(&flags[kFlagErr], kErrAceCapacity); flags[kFlagBad] = i; }
-            continue;
-        }
-        float accA[kNmax];
-        double accD[MODE == AP_ACE_FP64 ? kNmax : 1];
-        float acc_tc[2][4];
-#pragma unroll
-        for (int q = 0; q < kNmax; ++q) accA[q] = 0.0f;
-#pragma unroll
-        for (int q = 0; q < (MODE == AP_ACE_FP64 ? kNmax : 1); ++q) accD[q] = 0.0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) acc_tc[q >> 2][q & 3] = 0.0f;
-        for (int t0 = 0; t0 < cnt; t0 += kTile) {
-            basis_tile(S.nb, t0, cnt, rc, S.tileY, S.tileG, lane);
-            __syncwarp();
-            const int nt = min(kTile, cnt - t0);
-            if (MODE == AP_ACE_FP32) {
-                basis_accum_fp32(S.tileY, S.tileG, nt, lane, accA);
-            } else if (MODE == AP_ACE_FP64) {
-                if (lane < kNLM) {
-                    for (int jj2 = 0; jj2 < nt; ++jj2) {
-                        const float y = S.tileY[jj2][lane];
-                        const float4 g0 = *reinterpret_cast<const float4*>(&S.tileG[jj2][0]);
-                        const float4 g1 = *reinterpret_cast<const float4*>(&S.tileG[jj2][4]);
-                        const float gg[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
-#pragma unroll
-                        for (int q = 0; q < kNmax; ++q) accD[q] = fma((double)y, (double)gg[q], accD[q]);
-                    }
-                }
-            } else if (MODE == AP_ACE_TC_TF32X3) {
-#pragma unroll
-                for (int k0 = 0; k0 < kTile; k0 += 8) {
-                    const float bv0 = S.tileG[k0 + tq][gq], bv1 = S.tileG[k0 + tq + 4][gq];
-                    const uint32_t bh0 = to_tf32(bv0), bh1 = to_tf32(bv1);
-                    const uint32_t bl0 = to_tf32(bv0 - __uint_as_float(bh0)), bl1 = to_tf32(bv1 - __uint_as_float(bh1));
-#pragma unroll
-                    for (int mt = 0; mt < 2; ++mt) {
-                        const int m0 = 16 * mt;
-                        const float av[4] = {yt(S, m0 + gq, k0 + tq), yt(S, m0 + gq + 8, k0 + tq),
-                                             yt(S, m0 + gq, k0 + tq + 4), yt(S, m0 + gq + 8, k0 + tq + 4)};
-                        uint32_t ah[4], al[4];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            ah[q] = to_tf32(av[q]);
-                            al[q] = to_tf32(av[q] - __uint_as_float(ah[q]));
-                        }
-                        mma_tf32(acc_tc[mt], al[0], al[1], al[2], al[3], bh0, bh1);
-                        mma_tf32(acc_tc[mt], ah[0], ah[1], ah[2], ah[3], bl0, bl1);
-                        mma_tf32(acc_tc[mt], ah[0], ah[1], ah[2], ah[3], bh0, bh1);
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int k0 = 0; k0 < kTile; k0 += 16) {
-                    const uint32_t b0 = pack2<MODE>(S.tileG[k0 + 2 * tq][gq], S.tileG[k0 + 2 * tq + 1][gq]);
-                    const uint32_t b1 = pack2<MODE>(S.tileG[k0 + 2 * tq + 8][gq], S.tileG[k0 + 2 * tq + 9][gq]);
-#pragma unroll
-                    for (int mt = 0; mt < 2; ++mt) {
-                        const int r0 = 16 * mt + gq, r1 = r0 + 8, c0 = k0 + 2 * tq;
-                        const uint32_t a0 = pack2<MODE>(yt(S, r0, c0), yt(S, r0, c0 + 1));
-                        const uint32_t a1 = pack2<MODE>(yt(S, r1, c0), yt(S, r1, c0 + 1));
-                        const uint32_t a2 = pack2<MODE>(yt(S, r0, c0 + 8), yt(S, r0, c0 + 9));
-                        const uint32_t a3 = pack2<MODE>(yt(S, r1, c0 + 8), yt(S, r1, c0 + 9));
-                        mma_16bit<MODE>(acc_tc[mt], a0, a1, a2, a3, b0, b1);
-                    }
-                }
-            }
-            __syncwarp();
-        }
-        if (MODE == AP_ACE_FP32 || MODE == AP_ACE_FP64) {
-            if (lane < kNLM) {
-                if (MODE == AP_ACE_FP64) {
-#pragma unroll
-                    for (int q = 0; q < kNmax; ++q) accA[q] = (float)(accD[q] * (double)nrefi);
-                } else {
-#pragma unroll
-                    for (int q = 0; q < kNmax; ++q) accA[q] *= nrefi;
-                }
-                float4* o = reinterpret_cast<float4*>(Aout + ((size_t)a * kNLM + lane) * kNmax);
-                o[0] = make_float4(accA[0], accA[1], accA[2], accA[3]);
-                o[1] = make_float4(accA[4], accA[5], accA[6], accA[7]);
-            }
-        } else {
-            // D fragment: (row g, cols 2t, 2t+1) and (row g + 8, same cols) of each 16-row tile
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int r0 = 16 * mt + gq, r1 = r0 + 8;
-                if (r0 < kNLM)
-                    *reinterpret_cast<float2*>(Aout + ((size_t)a * kNLM + r0) * kNmax + 2 * tq) =
-                        make_float2(acc_tc[mt][0] * nrefi, acc_tc[mt][1] * nrefi);
-                if (r1 < kNLM)
-                    *reinterpret_cast<float2*>(Aout + ((size_t)a * kNLM + r1) * kNmax + 2 * tq) =
-                        make_float2(acc_tc[mt][2] * nrefi, acc_tc[mt][3] * nrefi);
-            }
-        }
+        basis_atom<MODE>(pos4, nbr, nnbr, n, Ds, rc, nrefi, ace_list, flags, Aout, a, S, lane);
     }
 }
 
@@ -933,6 +944,42 @@ __device__ __forceinline__ void tc_zero_regions(TcWarpSmem* WS, int nwarps) {
         z[k] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// contraction of compacted atom a: A from Ain, dE/dA to dAout, E_i^ACE to e_ace (one warp)
+__device__ __forceinline__ void contract_atom(const AceTc& C, TcWarpSmem& S, int lane, int lam_pad,
+                                              const float* __restrict__ Ain, float* __restrict__ dAout,
+                                              float* __restrict__ e_ace, const int* __restrict__ ace_list,
+                                              int* __restrict__ flags, int a) {
+    float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
+    if (lane < kNLM) {
+        const float4* src = reinterpret_cast<const float4*>(Ain + ((size_t)a * kNLM + lane) * kNmax);
+        g0 = src[0];
+        g1 = src[1];
+    }
+    tc_load_atom(S, lane, lam_pad, g0, g1);
+    float e = 0.0f;
+    const bool ok = tc_contract_atom(C, S, lane, e);
+    const int i = ace_list[a];
+    if (!ok) {
+        if (lane == 0) { atomicOr(&flags[kFlagErr], kErrDomain); flags[kFlagBad] = i; e_ace[i] = __int_as_float(0x7fc00000); }
+        if (lane < kNLM) {
+            float4* o = reinterpret_cast<float4*>(dAout + ((size_t)a * kNLM + lane) * kNmax);
+            o[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+            o[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    } else {
+        if (lane < kNLM) {
+            float v[kNmax];
+#pragma unroll
+            for (int q = 0; q < kNmax; ++q) v[q] = S.dA[q * kApad + lam_pad];
+            float4* o = reinterpret_cast<float4*>(dAout + ((size_t)a * kNLM + lane) * kNmax);
+            o[0] = make_float4(v[0], v[1], v[2], v[3]);
+            o[1] = make_float4(v[4], v[5], v[6], v[7]);
+        }
+        if (lane == 0) e_ace[i] = e;
+    }
+    __syncwarp();
+}
+
 // stages a5/a6 core on tensor cores: phi1, phi2, E = phi1 + sqrt(phi2) and dE/dA from A,
 // one warp per compacted atom
 __global__ void __launch_bounds__(kTcWarps * 32, 1)
@@ -953,37 +1000,8 @@ k_ace_contract(const AceTc* __restrict__ tab, const int* __restrict__ ace_list, 
     TcWarpSmem& S = WS[warp];
     const int n_ace = flags[kFlagNAce];
     const int lam_pad = lane_lm_pad(lane);
-    for (int a = blockIdx.x * kTcWarps + warp; a < n_ace; a += gridDim.x * kTcWarps) {
-        float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
-        if (lane < kNLM) {
-            const float4* src = reinterpret_cast<const float4*>(Ain + ((size_t)a * kNLM + lane) * kNmax);
-            g0 = src[0];
-            g1 = src[1];
-        }
-        tc_load_atom(S, lane, lam_pad, g0, g1);
-        float e = 0.0f;
-        const bool ok = tc_contract_atom(C, S, lane, e);
-        const int i = ace_list[a];
-        if (!ok) {
-            if (lane == 0) { atomicOr(&flags[kFlagErr], kErrDomain); flags[kFlagBad] = i; e_ace[i] = __int_as_float(0x7fc00000); }
-            if (lane < kNLM) {
-                float4* o = reinterpret_cast<float4*>(dAout + ((size_t)a * kNLM + lane) * kNmax);
-                o[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-                o[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        } else {
-            if (lane < kNLM) {
-                float v[kNmax];
-#pragma unroll
-                for (int q = 0; q < kNmax; ++q) v[q] = S.dA[q * kApad + lam_pad];
-                float4* o = reinterpret_cast<float4*>(dAout + ((size_t)a * kNLM + lane) * kNmax);
-                o[0] = make_float4(v[0], v[1], v[2], v[3]);
-                o[1] = make_float4(v[4], v[5], v[6], v[7]);
-            }
-            if (lane == 0) e_ace[i] = e;
-        }
-        __syncwarp();
-    }
+    for (int a = blockIdx.x * kTcWarps + warp; a < n_ace; a += gridDim.x * kTcWarps)
+        contract_atom(C, S, lane, lam_pad, Ain, dAout, e_ace, ace_list, flags, a);
 }
 
 struct ForceSmem {
@@ -991,6 +1009,50 @@ struct ForceSmem {
     float4 nb[kAceNbrCap];
     int nbj[kAceNbrCap];
 };
+
+// the pair forces of compacted atom a (stage a6), one warp; neighbour offsets Ds staged by the caller
+__device__ __forceinline__ void force_atom(const float4* __restrict__ pos4, const int* __restrict__ nbr,
+                                           const int* __restrict__ nnbr, int n, const float4* Ds, float rc,
+                                           float nrefi, const int* __restrict__ ace_list, const float* __restrict__ wv,
+                                           const float* __restrict__ dAin, float* __restrict__ vir,
+                                           unsigned long long* __restrict__ acc, int a, ForceSmem& S, int lane) {
+    const float rc2 = rc * rc;
+    const int i = ace_list[a];
+    const float wi = wv[i];
+    const int cnt = gather_ace_neighbors(pos4, nbr, n, i, nnbr[i], Ds, rc2, S.nb, S.nbj, lane);
+    if (cnt < 0) return;
+    for (int k = lane; k < kNLM * 2; k += 32)
+        reinterpret_cast<float4*>(&S.dAT[0][0])[k] = reinterpret_cast<const float4*>(dAin + (size_t)a * kNLM * kNmax)[k];
+    __syncwarp();
+    float fsx = 0.f, fsy = 0.f, fsz = 0.f;
+    float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f, v4 = 0.f, v5 = 0.f;
+    for (int t0 = 0; t0 < cnt; t0 += 32) {
+        const int jj = t0 + lane;
+        if (jj < cnt) {
+            const float4 v = S.nb[jj];
+            const int j = S.nbj[jj];
+            const float3 fp = ace_pair_force(v, rc, nrefi, wi, S.dAT);
+            const float fx = fp.x, fy = fp.y, fz = fp.z;
+            fix_add(&acc[j], -fx);
+            fix_add(&acc[(size_t)n + j], -fy);
+            fix_add(&acc[(size_t)2 * n + j], -fz);
+            fsx += fx; fsy += fy; fsz += fz;
+            v0 -= v.x * fx; v1 -= v.y * fy; v2 -= v.z * fz;
+            v3 -= 0.5f * (v.x * fy + v.y * fx); v4 -= 0.5f * (v.x * fz + v.z * fx); v5 -= 0.5f * (v.y * fz + v.z * fy);
+        }
+    }
+    fsx = warp_sum(fsx); fsy = warp_sum(fsy); fsz = warp_sum(fsz);
+    v0 = warp_sum(v0); v1 = warp_sum(v1); v2 = warp_sum(v2);
+    v3 = warp_sum(v3); v4 = warp_sum(v4); v5 = warp_sum(v5);
+    if (lane == 0) {
+        fix_add(&acc[i], fsx);
+        fix_add(&acc[(size_t)n + i], fsy);
+        fix_add(&acc[(size_t)2 * n + i], fsz);
+        vir[i] = v0; vir[n + i] = v1; vir[2 * n + i] = v2; vir[3 * n + i] = v3; vir[4 * n + i] = v4; vir[5 * n + i] = v5;
+    }
+    __syncwarp();
+}
+
 
 // stage a6: f_ij = (1/nref) sum dE/dA_nlm grad(g_n Y_lm), scattered with weight w_i
 __global__ void __launch_bounds__(256) k_ace_force(const float4* __restrict__ pos4, const int* __restrict__ nbr,
@@ -1006,43 +1068,109 @@ __global__ void __launch_bounds__(256) k_ace_force(const float4* __restrict__ po
     pdl_wait();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     ForceSmem& S = WS[warp];
-    const float rc = tab->rc, rc2 = rc * rc, nrefi = tab->nref_inv;
+    const float rc = tab->rc, nrefi = tab->nref_inv;
     const int n_ace = flags[kFlagNAce];
     for (int a = blockIdx.x * 8 + warp; a < n_ace; a += gridDim.x * 8) {
-        const int i = ace_list[a];
-        const float wi = wv[i];
-        const int cnt = gather_ace_neighbors(pos4, nbr, n, i, nnbr[i], Ds, rc2, S.nb, S.nbj, lane);
-        if (cnt < 0) continue;
-        for (int k = lane; k < kNLM * 2; k += 32)
-            reinterpret_cast<float4*>(&S.dAT[0][0])[k] = reinterpret_cast<const float4*>(dAin + (size_t)a * kNLM * kNmax)[k];
-        __syncwarp();
-        float fsx = 0.f, fsy = 0.f, fsz = 0.f;
-        float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f, v4 = 0.f, v5 = 0.f;
-        for (int t0 = 0; t0 < cnt; t0 += 32) {
-            const int jj = t0 + lane;
-            if (jj < cnt) {
-                const float4 v = S.nb[jj];
-                const int j = S.nbj[jj];
-                const float3 fp = ace_pair_force(v, rc, nrefi, wi, S.dAT);
-                const float fx = fp.x, fy = fp.y, fz = fp.z;
-                fix_add(&acc[j], -fx);
-                fix_add(&acc[(size_t)n + j], -fy);
-                fix_add(&acc[(size_t)2 * n + j], -fz);
-                fsx += fx; fsy += fy; fsz += fz;
-                v0 -= v.x * fx; v1 -= v.y * fy; v2 -= v.z * fz;
-                v3 -= 0.5f * (v.x * fy + v.y * fx); v4 -= 0.5f * (v.x * fz + v.z * fx); v5 -= 0.5f * (v.y * fz + v.z * fy);
-            }
+        force_atom(pos4, nbr, nnbr, n, Ds, rc, nrefi, ace_list, wv, dAin, vir, acc, a, S, lane);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Batched ACE stages over several contexts: a persistent grid walks chunks of compacted
+// atoms (per chunk one atom per warp) of all contexts in order; chunk c belongs to the
+// context k with pre[k] <= c < pre[k + 1], pre the prefix of the contexts' chunk counts,
+// formed from their device atom counts at the start of each launch.  A block restages a
+// context's constant tables only when the context (the neighbour offsets) or the potential
+// (the coefficient tables, shared per potential) changes.
+// ---------------------------------------------------------------------------------
+// chunks of `per` atoms of every context into pre[0 .. nctx] (shared memory); the total.
+// The atom counts come from the preceding stage: this is where a programmatically launched
+// batch kernel waits for it.
+__device__ __forceinline__ int batch_chunks(const BatchTable& t, int per, int* pre) {
+    pdl_wait();
+    if ((int)threadIdx.x < t.nctx) {
+        const int na = t.d[threadIdx.x]->flags[kFlagNAce];
+        pre[threadIdx.x + 1] = (na + per - 1) / per;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        pre[0] = 0;
+        for (int k = 0; k < t.nctx; ++k) pre[k + 1] += pre[k];
+    }
+    __syncthreads();
+    return pre[t.nctx];
+}
+
+__global__ void __launch_bounds__(256) kb_ace_basis(const BatchTable t) {
+    __shared__ float4 Ds[125];
+    __shared__ BasisSmem WS[8];
+    __shared__ int pre[kMaxBatchCtx + 1];
+    const int total = batch_chunks(t, 8, pre);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int cur = -1;
+    for (int ch = blockIdx.x; ch < total; ch += gridDim.x) {
+        const int k = batch_find(pre, t.nctx, ch);
+        const CtxDev& c = *t.d[k];
+        if (k != cur) {
+            __syncthreads();
+            for (int q = threadIdx.x; q < c.grid.ncode; q += blockDim.x) Ds[q] = c.D[q];
+            __syncthreads();
+            cur = k;
         }
-        fsx = warp_sum(fsx); fsy = warp_sum(fsy); fsz = warp_sum(fsz);
-        v0 = warp_sum(v0); v1 = warp_sum(v1); v2 = warp_sum(v2);
-        v3 = warp_sum(v3); v4 = warp_sum(v4); v5 = warp_sum(v5);
-        if (lane == 0) {
-            fix_add(&acc[i], fsx);
-            fix_add(&acc[(size_t)n + i], fsy);
-            fix_add(&acc[(size_t)2 * n + i], fsz);
-            vir[i] = v0; vir[n + i] = v1; vir[2 * n + i] = v2; vir[3 * n + i] = v3; vir[4 * n + i] = v4; vir[5 * n + i] = v5;
+        const int a = (ch - pre[k]) * 8 + warp;
+        if (a < c.flags[kFlagNAce])
+            basis_atom<AP_ACE_FP32>(c.pos4, c.nbr, c.nnbr, c.n, Ds, c.ace->rc, c.ace->nref_inv, c.ace_list, c.flags,
+                                    c.ace_A, a, WS[warp], lane);
+    }
+}
+
+__global__ void __launch_bounds__(kTcWarps * 32, 1) kb_ace_contract(const BatchTable t) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AceTc& C = *reinterpret_cast<AceTc*>(smem_raw);
+    TcWarpSmem* WS = reinterpret_cast<TcWarpSmem*>(smem_raw + sizeof(AceTc));
+    __shared__ int pre[kMaxBatchCtx + 1];
+    tc_zero_regions(WS, kTcWarps);
+    const int total = batch_chunks(t, kTcWarps, pre);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lam_pad = lane_lm_pad(lane);
+    const AceTc* cur = nullptr;
+    for (int ch = blockIdx.x; ch < total; ch += gridDim.x) {
+        const int k = batch_find(pre, t.nctx, ch);
+        const CtxDev& c = *t.d[k];
+        if (c.ace != cur) {
+            __syncthreads();
+            const int4* src = reinterpret_cast<const int4*>(c.ace);
+            int4* dst = reinterpret_cast<int4*>(smem_raw);
+            for (int q = threadIdx.x; q < (int)(sizeof(AceTc) / 16); q += blockDim.x) dst[q] = src[q];
+            __syncthreads();
+            cur = c.ace;
         }
-        __syncwarp();
+        const int a = (ch - pre[k]) * kTcWarps + warp;
+        if (a < c.flags[kFlagNAce])
+            contract_atom(C, WS[warp], lane, lam_pad, c.ace_A, c.ace_dA, c.e_ace, c.ace_list, c.flags, a);
+    }
+}
+
+__global__ void __launch_bounds__(256) kb_ace_force(const BatchTable t) {
+    __shared__ float4 Ds[125];
+    __shared__ ForceSmem WS[8];
+    __shared__ int pre[kMaxBatchCtx + 1];
+    const int total = batch_chunks(t, 8, pre);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int cur = -1;
+    for (int ch = blockIdx.x; ch < total; ch += gridDim.x) {
+        const int k = batch_find(pre, t.nctx, ch);
+        const CtxDev& c = *t.d[k];
+        if (k != cur) {
+            __syncthreads();
+            for (int q = threadIdx.x; q < c.grid.ncode; q += blockDim.x) Ds[q] = c.D[q];
+            __syncthreads();
+            cur = k;
+        }
+        const int a = (ch - pre[k]) * 8 + warp;
+        if (a < c.flags[kFlagNAce])
+            force_atom(c.pos4, c.nbr, c.nnbr, c.n, Ds, c.ace->rc, c.ace->nref_inv, c.ace_list, c.w, c.ace_dA,
+                       c.vir_ace, c.acc, a, WS[warp], lane);
     }
 }
 
@@ -1064,9 +1192,16 @@ int persistent_blocks(K kernel, int dev, int threads, size_t smem) {
     return blocks;
 }
 
+// Grids of the ACE kernels: persistent, but no larger than the context's atoms can fill (n is
+// the host's bound on the compacted count): a small context then leaves the other SMs to the
+// kernels of other contexts instead of occupying every SM with idle blocks.
+int ace_grid(int persistent, int n, int atoms_per_block) {
+    return std::max(1, std::min(persistent, (n + atoms_per_block - 1) / atoms_per_block));
+}
+
 template <int MODE>
 void launch_basis_mode(Ctx& c, cudaStream_t s) {
-    const int nb = persistent_blocks(k_ace_basis<MODE>, c.dev, 256, 0);
+    const int nb = ace_grid(persistent_blocks(k_ace_basis<MODE>, c.dev, 256, 0), c.n, 8);
     launch_pdl(k_ace_basis<MODE>, nb, 256, 0, s, c.pos4, c.nbr, c.nnbr, c.n, c.D, c.grid.ncode, c.ace_tc_d, c.ace_list,
                c.flags, c.ace_A);
 }
@@ -1092,13 +1227,28 @@ int launch_ace(Ctx& c, cudaStream_t s) {
     }
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c.dev);
-    launch_pdl(k_ace_contract, nsm, kTcWarps * 32, ace_tc_smem_bytes(), s, c.ace_tc_d, c.ace_list, c.flags, c.ace_A,
-               c.ace_dA, c.e_ace);
+    launch_pdl(k_ace_contract, ace_grid(nsm, c.n, kTcWarps), kTcWarps * 32, ace_tc_smem_bytes(), s, c.ace_tc_d,
+               c.ace_list, c.flags, c.ace_A, c.ace_dA, c.e_ace);
     return 1;
 }
 
+int launch_batch_ace(const BatchTable& t, int dev, cudaStream_t s) {
+    if (t.nctx < 1 || t.nctx > kMaxBatchCtx) return 0;
+    static int configured = -1;
+    if (configured != dev) {
+        cudaFuncSetAttribute(kb_ace_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ace_tc_smem_bytes());
+        configured = dev;
+    }
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    launch_pdl(kb_ace_basis, ace_grid(persistent_blocks(kb_ace_basis, dev, 256, 0), t.atoms, 8), 256, 0, s, t);
+    launch_pdl(kb_ace_contract, ace_grid(nsm, t.atoms, kTcWarps), kTcWarps * 32, ace_tc_smem_bytes(), s, t);
+    launch_pdl(kb_ace_force, ace_grid(persistent_blocks(kb_ace_force, dev, 256, 0), t.atoms, 8), 256, 0, s, t);
+    return 3;
+}
+
 int launch_ace_force(Ctx& c, cudaStream_t s) {
-    const int nb = persistent_blocks(k_ace_force, c.dev, 256, 0);
+    const int nb = ace_grid(persistent_blocks(k_ace_force, c.dev, 256, 0), c.n, 8);
     launch_pdl(k_ace_force, nb, 256, 0, s, c.pos4, c.nbr, c.nnbr, c.n, c.D, c.grid.ncode, c.ace_tc_d, c.ace_list, c.w,
                c.flags, c.ace_dA, c.vir_ace, c.acc);
     return 1;

@@ -36,15 +36,15 @@ __device__ __forceinline__ void stage_tables(EamDev* sm, const EamDev* __restric
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kEamBlock) k_eam_density(const float4* __restrict__ pos4, const int* __restrict__ nbr,
+__device__ __forceinline__ void eam_density_body(const float4* __restrict__ pos4, const int* __restrict__ nbr,
                                                      const int* __restrict__ nnbr, int n, const EamDev* __restrict__ eam,
                                                      const float4* __restrict__ D, int ncode, float* __restrict__ uxi,
-                                                     double* __restrict__ e_emb, int* __restrict__ flags) {
+                                                     double* __restrict__ e_emb, int* __restrict__ flags, int bid) {
     __shared__ EamDev T;
     __shared__ float4 Ds[125];
     stage_tables(&T, eam, Ds, D, ncode);          // constant tables: before the wait
     pdl_wait();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = bid * blockDim.x + threadIdx.x;
     if (i == 0) flags[kFlagRebuild] = 0;        // the list built this step is in use now
     if (i >= n) return;
     float4 p = pos4[i];
@@ -89,19 +89,26 @@ __global__ void __launch_bounds__(kEamBlock) k_eam_density(const float4* __restr
     e_emb[i] = F;
 }
 
+__global__ void __launch_bounds__(kEamBlock) k_eam_density(const float4* __restrict__ pos4, const int* __restrict__ nbr,
+                                                     const int* __restrict__ nnbr, int n, const EamDev* __restrict__ eam,
+                                                     const float4* __restrict__ D, int ncode, float* __restrict__ uxi,
+                                                     double* __restrict__ e_emb, int* __restrict__ flags) {
+    eam_density_body(pos4, nbr, nnbr, n, eam, D, ncode, uxi, e_emb, flags, blockIdx.x);
+}
+
 // per step: EAM forces.  The pair value Phi is needed only for the FP32 estimate of E_i^EAM
 // that the weight-gradient force of transition atoms (0 < w < 1) uses; exact energies and
 // the virial come from the on-request energy pass.
-__global__ void __launch_bounds__(kEamBlock) k_eam_force(const float4* __restrict__ pos4, const int* __restrict__ nbr,
+__device__ __forceinline__ void eam_force_body(const float4* __restrict__ pos4, const int* __restrict__ nbr,
                                                    const int* __restrict__ nnbr, int n, const EamDev* __restrict__ eam,
                                                    const float4* __restrict__ D, int ncode, const float* __restrict__ uxi,
                                                    const double* __restrict__ e_emb, const float* __restrict__ wv,
-                                                   float* __restrict__ f, double* __restrict__ e_eam) {
+                                                   float* __restrict__ f, double* __restrict__ e_eam, int bid) {
     __shared__ EamDev T;
     __shared__ float4 Ds[125];
     stage_tables(&T, eam, Ds, D, ncode);          // constant tables: before the wait
     pdl_wait();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = bid * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float4 p = pos4[i];
     const float ui = p.w, xi = uxi[i];
@@ -147,6 +154,14 @@ __global__ void __launch_bounds__(kEamBlock) k_eam_force(const float4* __restric
     }
     f[i] = fx; f[n + i] = fy; f[2 * n + i] = fz;
     if (want_e) e_eam[i] = e_emb[i] + 0.5 * (double)eph;
+}
+
+__global__ void __launch_bounds__(kEamBlock) k_eam_force(const float4* __restrict__ pos4, const int* __restrict__ nbr,
+                                                   const int* __restrict__ nnbr, int n, const EamDev* __restrict__ eam,
+                                                   const float4* __restrict__ D, int ncode, const float* __restrict__ uxi,
+                                                   const double* __restrict__ e_emb, const float* __restrict__ wv,
+                                                   float* __restrict__ f, double* __restrict__ e_eam) {
+    eam_force_body(pos4, nbr, nnbr, n, eam, D, ncode, uxi, e_emb, wv, f, e_eam, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------------
@@ -320,6 +335,20 @@ __global__ void __launch_bounds__(256) k_eam_energy(const float4* __restrict__ p
     e_eam[i] = F + 0.5 * ((double)ph + (double)pl_);
 }
 
+__global__ void __launch_bounds__(kEamBlock) kb_eam_density(const BatchTable t) {
+    const int k = batch_find(t.b128, t.nctx, blockIdx.x);
+    const CtxDev& c = *t.d[k];
+    eam_density_body(c.pos4, c.nbr, c.nnbr, c.n, c.eam, c.D, c.grid.ncode, c.uxi, c.e_emb, c.flags,
+                     blockIdx.x - t.b128[k]);
+}
+
+__global__ void __launch_bounds__(kEamBlock) kb_eam_force(const BatchTable t) {
+    const int k = batch_find(t.b128, t.nctx, blockIdx.x);
+    const CtxDev& c = *t.d[k];
+    eam_force_body(c.pos4, c.nbr, c.nnbr, c.n, c.eam, c.D, c.grid.ncode, c.uxi, c.e_emb, c.w, c.f, c.e_eam,
+                   blockIdx.x - t.b128[k]);
+}
+
 }  // namespace
 
 int launch_eam_energy(Ctx& c, cudaStream_t s, bool virial) {
@@ -343,6 +372,14 @@ int launch_eam_force(Ctx& c, cudaStream_t s) {
     launch_pdl(k_eam_force, (c.n + kEamBlock - 1) / kEamBlock, kEamBlock, 0, s, c.pos4, c.nbr, c.nnbr, c.n, c.eam_d,
                c.D, c.grid.ncode, c.uxi, c.e_emb, c.w, c.f, c.e_eam);
     return 1;
+}
+
+
+int launch_batch_eam(const BatchTable& t, cudaStream_t s) {
+    static_assert(kEamBlock == 128, "the batch table counts EAM blocks of 128 threads");
+    launch_pdl(kb_eam_density, t.b128[t.nctx], kEamBlock, 0, s, t);
+    launch_pdl(kb_eam_force, t.b128[t.nctx], kEamBlock, 0, s, t);
+    return 2;
 }
 
 }  // namespace ap

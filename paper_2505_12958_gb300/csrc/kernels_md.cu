@@ -66,13 +66,13 @@ __global__ void k_pos_in(const double* __restrict__ pos, int n, double* __restri
 }
 
 // per step: F_i = F_i^EAM (carries u) + ACE sum (carries w) - grad w_i (E^ACE - E^EAM) + F_ind
-__global__ void __launch_bounds__(kRedBlock) k_blend(
+__device__ __forceinline__ void blend_body(
     const double* __restrict__ x, int n, const GridDev g, const DynDev dy, const double* __restrict__ tptr,
     const float4* __restrict__ pos4, const int* __restrict__ cell,
     const float* __restrict__ wv, float* __restrict__ f, unsigned long long* __restrict__ acc,
     const float* __restrict__ e_ace, const double* __restrict__ e_eam, double c1_0, float* __restrict__ out_aos,
     int* __restrict__ flags, double hdta, const unsigned char* __restrict__ fixed, double* __restrict__ v,
-    const long long* __restrict__ step, long long* __restrict__ load_ring, int load_cap) {
+    const long long* __restrict__ step, long long* __restrict__ load_ring, int load_cap, int bid) {
     pdl_wait();
     // FP64 runs at 1/64 of the FP32 rate on this GPU.  Positions are taken in FP32 from the
     // cell origin and x_rel (absolute error ~1e-5 A) for the indenter pre-test, inside its
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kRedBlock) k_blend(
         }
     }
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bid * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float wi = wv[i];
     float F[3];
@@ -173,6 +173,16 @@ __global__ void __launch_bounds__(kRedBlock) k_blend(
         atomicOr(&flags[kFlagErr], kErrDomain);
         flags[kFlagBad] = i;
     }
+}
+
+__global__ void __launch_bounds__(kRedBlock) k_blend(
+    const double* __restrict__ x, int n, const GridDev g, const DynDev dy, const double* __restrict__ tptr,
+    const float4* __restrict__ pos4, const int* __restrict__ cell,
+    const float* __restrict__ wv, float* __restrict__ f, unsigned long long* __restrict__ acc,
+    const float* __restrict__ e_ace, const double* __restrict__ e_eam, double c1_0, float* __restrict__ out_aos,
+    int* __restrict__ flags, double hdta, const unsigned char* __restrict__ fixed, double* __restrict__ v,
+    const long long* __restrict__ step, long long* __restrict__ load_ring, int load_cap) {
+    blend_body(x, n, g, dy, tptr, pos4, cell, wv, f, acc, e_ace, e_eam, c1_0, out_aos, flags, hdta, fixed, v, step, load_ring, load_cap, blockIdx.x);
 }
 
 // on request: per-atom E_i + V_ind, and block sums of the energies, the virial and the load
@@ -265,13 +275,13 @@ __global__ void __launch_bounds__(kRedBlock) k_reduce(const double* __restrict__
 // first half kick and drift; the neighbour-list displacement test of the step is taken here,
 // where x is in registers (an atom that moved more than skin/2 since the last build sets the
 // rebuild flag), and the compaction counter of the coming force pass is reset
-__global__ void k_kick_drift(double* __restrict__ x, double* __restrict__ v, const float* __restrict__ f,
+__device__ __forceinline__ void kick_drift_body(double* __restrict__ x, double* __restrict__ v, const float* __restrict__ f,
                              const unsigned char* __restrict__ fixed, int n, double hdta, double dt,
                              double* __restrict__ tptr, long long* __restrict__ step,
                              const double* __restrict__ xb, double lim2, int* __restrict__ flags,
-                             long long* __restrict__ load_ring, double* __restrict__ load_ring_t, int load_cap) {
+                             long long* __restrict__ load_ring, double* __restrict__ load_ring_t, int load_cap, int bid) {
     pdl_wait();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bid * blockDim.x + threadIdx.x;
     if (i == 0) {
         *tptr += dt;
         *step += 1;
@@ -294,6 +304,14 @@ __global__ void k_kick_drift(double* __restrict__ x, double* __restrict__ v, con
         d2 += d * d;
     }
     if (d2 > lim2) flags[kFlagRebuild] = 1;
+}
+
+__global__ void k_kick_drift(double* __restrict__ x, double* __restrict__ v, const float* __restrict__ f,
+                             const unsigned char* __restrict__ fixed, int n, double hdta, double dt,
+                             double* __restrict__ tptr, long long* __restrict__ step,
+                             const double* __restrict__ xb, double lim2, int* __restrict__ flags,
+                             long long* __restrict__ load_ring, double* __restrict__ load_ring_t, int load_cap) {
+    kick_drift_body(x, v, f, fixed, n, hdta, dt, tptr, step, xb, lim2, flags, load_ring, load_ring_t, load_cap, blockIdx.x);
 }
 
 __global__ void k_kick(double* __restrict__ v, const float* __restrict__ f, const unsigned char* __restrict__ fixed,
@@ -420,6 +438,22 @@ __global__ void k_sub_com(double* __restrict__ v, const unsigned char* __restric
     for (int k = 0; k < 3; ++k) v[(size_t)k * n + i] -= com[k];
 }
 
+__global__ void __launch_bounds__(kRedBlock) kb_blend(const BatchTable t, double kick_dt, int record) {
+    const int k = batch_find(t.b256, t.nctx, blockIdx.x);
+    const CtxDev& c = *t.d[k];
+    long long* ring = record && c.dyn.ind_on ? c.load_ring : nullptr;
+    blend_body(c.x, c.n, c.grid, c.dyn, c.d_time, c.pos4, c.cell, c.w, c.f, c.acc, c.e_ace, c.e_eam, c.ace_c1_0,
+               nullptr, c.flags, kick_dt > 0.0 ? 0.5 * kick_dt * kFtm / c.mass : 0.0, c.fixed, c.v, c.d_step, ring,
+               c.load_cap, blockIdx.x - t.b256[k]);
+}
+
+__global__ void kb_kick_drift(const BatchTable t, double dt) {
+    const int k = batch_find(t.b256, t.nctx, blockIdx.x);
+    const CtxDev& c = *t.d[k];
+    kick_drift_body(c.x, c.v, c.f, c.fixed, c.n, 0.5 * dt * kFtm / c.mass, dt, c.d_time, c.d_step, c.xb, c.lim2,
+                    c.flags, c.load_ring, c.load_ring_t, c.load_cap, blockIdx.x - t.b256[k]);
+}
+
 }  // namespace
 
 int launch_langevin(Ctx& c, cudaStream_t s, double dt) {
@@ -485,6 +519,18 @@ int launch_kick_drift(Ctx& c, cudaStream_t s, double dt, int) {
 
 int launch_kick(Ctx& c, cudaStream_t s, double dt) {
     launch_pdl(k_kick, (c.n + 255) / 256, 256, 0, s, c.v, c.f, c.fixed, c.n, 0.5 * dt * kFtm / c.mass);
+    return 1;
+}
+
+
+int launch_batch_blend(const BatchTable& t, double kick_dt, int record, cudaStream_t s) {
+    static_assert(kRedBlock == 256, "the batch table counts blend blocks of 256 threads");
+    launch_pdl(kb_blend, t.b256[t.nctx], kRedBlock, 0, s, t, kick_dt, record);
+    return 1;
+}
+
+int launch_batch_step_pre(const BatchTable& t, double dt, cudaStream_t s) {
+    launch_pdl(kb_kick_drift, t.b256[t.nctx], 256, 0, s, t, dt);
     return 1;
 }
 

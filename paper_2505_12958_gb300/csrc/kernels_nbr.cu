@@ -19,21 +19,26 @@ namespace ap {
 
 namespace {
 
-__global__ void k_check(const double* __restrict__ x, const double* __restrict__ xb, int n, double lim2,
-                        int* flags) {
+__device__ __forceinline__ void check_body(const double* __restrict__ x, const double* __restrict__ xb, int n, double lim2,
+                        int* flags, int bid) {
     pdl_wait();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = bid * blockDim.x + threadIdx.x;
     if (i == 0) flags[kFlagNAce] = 0;
     if (i >= n) return;
     double dx = x[i] - xb[i], dy = x[n + i] - xb[n + i], dz = x[2 * n + i] - xb[2 * n + i];
     if (dx * dx + dy * dy + dz * dz > lim2) flags[kFlagRebuild] = 1;
 }
 
-__global__ void k_wrap_bin(double* __restrict__ x, double* __restrict__ xb, int n, const GridDev g,
-                           int* __restrict__ cell, int* __restrict__ cell_count, int* __restrict__ flags) {
+__global__ void k_check(const double* __restrict__ x, const double* __restrict__ xb, int n, double lim2,
+                        int* flags) {
+    check_body(x, xb, n, lim2, flags, blockIdx.x);
+}
+
+__device__ __forceinline__ void wrap_bin_body(double* __restrict__ x, double* __restrict__ xb, int n, const GridDev g,
+                           int* __restrict__ cell, int* __restrict__ cell_count, int* __restrict__ flags, int bid) {
     pdl_wait();
     if (flags[kFlagRebuild] == 0) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = bid * blockDim.x + threadIdx.x;
     if (i == 0) flags[kFlagRebuilds] += 1;
     if (i >= n) return;
     double r[3] = {x[i], x[n + i], x[2 * n + i]};
@@ -58,10 +63,15 @@ __global__ void k_wrap_bin(double* __restrict__ x, double* __restrict__ xb, int 
     atomicAdd(&cell_count[ci], 1);
 }
 
+__global__ void k_wrap_bin(double* __restrict__ x, double* __restrict__ xb, int n, const GridDev g,
+                           int* __restrict__ cell, int* __restrict__ cell_count, int* __restrict__ flags) {
+    wrap_bin_body(x, xb, n, g, cell, cell_count, flags, blockIdx.x);
+}
+
 // exclusive scan of cell_count into cell_start (one block); the counters are cleared so
 // that the scatter can reuse them as fill pointers
-__global__ void k_scan(int* __restrict__ cell_count, int* __restrict__ cell_start, int ncell,
-                       const int* __restrict__ flags) {
+__device__ __forceinline__ void scan_body(int* __restrict__ cell_count, int* __restrict__ cell_start, int ncell,
+                       const int* __restrict__ flags, int bid) {
     pdl_wait();
     if (flags[kFlagRebuild] == 0) return;
     __shared__ int part[1024];
@@ -87,23 +97,33 @@ __global__ void k_scan(int* __restrict__ cell_count, int* __restrict__ cell_star
     if (tid == nt - 1) cell_start[ncell] = part[nt - 1];
 }
 
-__global__ void k_scatter(const int* __restrict__ cell, int n, const int* __restrict__ cell_start,
-                          int* __restrict__ fill, int* __restrict__ cell_atoms, const int* __restrict__ flags) {
+__global__ void k_scan(int* __restrict__ cell_count, int* __restrict__ cell_start, int ncell,
+                       const int* __restrict__ flags) {
+    scan_body(cell_count, cell_start, ncell, flags, blockIdx.x);
+}
+
+__device__ __forceinline__ void scatter_body(const int* __restrict__ cell, int n, const int* __restrict__ cell_start,
+                          int* __restrict__ fill, int* __restrict__ cell_atoms, const int* __restrict__ flags, int bid) {
     pdl_wait();
     if (flags[kFlagRebuild] == 0) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = bid * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int c = cell[i];
     int slot = atomicAdd(&fill[c], 1);
     cell_atoms[cell_start[c] + slot] = i;
 }
 
+__global__ void k_scatter(const int* __restrict__ cell, int n, const int* __restrict__ cell_start,
+                          int* __restrict__ fill, int* __restrict__ cell_atoms, const int* __restrict__ flags) {
+    scatter_body(cell, n, cell_start, fill, cell_atoms, flags, blockIdx.x);
+}
+
 // order each cell's atoms by index and clear the per-cell counters for the next build
-__global__ void k_sort_cells(int* __restrict__ cell_atoms, const int* __restrict__ cell_start, int* __restrict__ fill,
-                             int ncell, const int* __restrict__ flags) {
+__device__ __forceinline__ void sort_cells_body(int* __restrict__ cell_atoms, const int* __restrict__ cell_start, int* __restrict__ fill,
+                             int ncell, const int* __restrict__ flags, int bid) {
     pdl_wait();
     if (flags[kFlagRebuild] == 0) return;
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    int c = bid * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
     int b = cell_start[c], e = cell_start[c + 1];
     for (int p = b + 1; p < e; ++p) {
@@ -115,16 +135,21 @@ __global__ void k_sort_cells(int* __restrict__ cell_atoms, const int* __restrict
     fill[c] = 0;
 }
 
+__global__ void k_sort_cells(int* __restrict__ cell_atoms, const int* __restrict__ cell_start, int* __restrict__ fill,
+                             int ncell, const int* __restrict__ flags) {
+    sort_cells_body(cell_atoms, cell_start, fill, ncell, flags, blockIdx.x);
+}
+
 // Per step: x_rel = x - cell origin as FP32 (the force kernels' coordinates), the weight
 // w_i of the fixed zone, and the compaction of the atoms with w > 0.  FP64 runs at 1/64 of
 // the FP32 rate on this GPU, so the region test is first taken in FP32 from the cell origin
 // and x_rel (absolute error ~1e-5 A, far inside the pre-test margins); only atoms the FP32
 // test cannot place (the switching shell and its edges) take the FP64 path.  The FP32
 // residual of x_rel is formed on demand, for the energy pass (k_pos_lo).
-__global__ void k_prepare(const double* __restrict__ x, int n, const GridDev g, const DynDev dy,
+__device__ __forceinline__ void prepare_body(const double* __restrict__ x, int n, const GridDev g, const DynDev dy,
                           const double* __restrict__ tptr, const int* __restrict__ cell,
                           const double* __restrict__ w_fixed, float4* __restrict__ pos4,
-                          float* __restrict__ wout, int* __restrict__ ace_list, int* __restrict__ flags) {
+                          float* __restrict__ wout, int* __restrict__ ace_list, int* __restrict__ flags, int bid) {
     pdl_wait();
     __shared__ float sh[9];          // box origin, cell edges (orthorhombic), zone centre at time t
     if (threadIdx.x == 0 && dy.reg_kind == AP_REGION_SPHERE && g.ortho) {
@@ -136,7 +161,7 @@ __global__ void k_prepare(const double* __restrict__ x, int n, const GridDev g, 
         }
     }
     __syncthreads();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = bid * blockDim.x + threadIdx.x;
     float wf = 0.0f;
     bool need = false;                 // w > 0, decided in the precision w is given in
     if (i < n) {
@@ -192,6 +217,13 @@ __global__ void k_prepare(const double* __restrict__ x, int n, const GridDev g, 
     }
 }
 
+__global__ void k_prepare(const double* __restrict__ x, int n, const GridDev g, const DynDev dy,
+                          const double* __restrict__ tptr, const int* __restrict__ cell,
+                          const double* __restrict__ w_fixed, float4* __restrict__ pos4,
+                          float* __restrict__ wout, int* __restrict__ ace_list, int* __restrict__ flags) {
+    prepare_body(x, n, g, dy, tptr, cell, w_fixed, pos4, wout, ace_list, flags, blockIdx.x);
+}
+
 // Full neighbour list, r < r_list.  Each atom's entries are written in order of distance
 // band (kBands bands of r_list / kBands; within a band, in cell-scan order): the pair kernels
 // visit the k-th entries of neighbouring atoms together, and with band-ordered lists those
@@ -200,12 +232,12 @@ __global__ void k_prepare(const double* __restrict__ x, int n, const GridDev g, 
 constexpr int kBands = 16;
 constexpr int kBuildBlock = 128;
 
-__global__ void __launch_bounds__(kBuildBlock) k_build(const float4* __restrict__ pos4, const int* __restrict__ cell,
+__device__ __forceinline__ void build_body(const float4* __restrict__ pos4, const int* __restrict__ cell,
                                                        int n, const GridDev g, const float4* __restrict__ Dtab,
                                                        const int* __restrict__ cell_start,
                                                        const int* __restrict__ cell_atoms, int* __restrict__ nbr,
                                                        int* __restrict__ nnbr, int cap, int* __restrict__ flags,
-                                                       int count_only) {
+                                                       int count_only, int bid) {
     pdl_wait();
     if (!count_only && flags[kFlagRebuild] == 0) return;
     __shared__ float4 D[125];
@@ -220,7 +252,7 @@ __global__ void __launch_bounds__(kBuildBlock) k_build(const float4* __restrict_
     }
     for (int b = 0; b < kBands; ++b) band_at[b][threadIdx.x] = 0;
     __syncthreads();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = bid * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float4 p = pos4[i];
     int cc[3];
@@ -302,7 +334,84 @@ __global__ void __launch_bounds__(kBuildBlock) k_build(const float4* __restrict_
     atomicMax(&flags[kFlagMaxNbr], cnt);
 }
 
+__global__ void __launch_bounds__(kBuildBlock) k_build(const float4* __restrict__ pos4, const int* __restrict__ cell,
+                                                       int n, const GridDev g, const float4* __restrict__ Dtab,
+                                                       const int* __restrict__ cell_start,
+                                                       const int* __restrict__ cell_atoms, int* __restrict__ nbr,
+                                                       int* __restrict__ nnbr, int cap, int* __restrict__ flags,
+                                                       int count_only) {
+    build_body(pos4, cell, n, g, Dtab, cell_start, cell_atoms, nbr, nnbr, cap, flags, count_only, blockIdx.x);
+}
+
+// batched launches: block b of a launch over several contexts acts as block b - start[k] of
+// context k (start: the per-context prefix of blocks)
+__device__ __forceinline__ const CtxDev& batch_ctx(const BatchTable& t, const int* start, int& bid) {
+    const int k = batch_find(start, t.nctx, blockIdx.x);
+    bid = blockIdx.x - start[k];
+    return *t.d[k];
+}
+
+__global__ void kb_check(const BatchTable t) {
+    int bid;
+    const CtxDev& c = batch_ctx(t, t.b256, bid);
+    check_body(c.x, c.xb, c.n, c.lim2, c.flags, bid);
+}
+
+__global__ void kb_wrap_bin(const BatchTable t) {
+    int bid;
+    const CtxDev& c = batch_ctx(t, t.b256, bid);
+    wrap_bin_body(c.x, c.xb, c.n, c.grid, c.cell, c.cell_count, c.flags, bid);
+}
+
+__global__ void kb_scan(const BatchTable t) {          // one block per context
+    const CtxDev& c = *t.d[blockIdx.x];
+    scan_body(c.cell_count, c.cell_start, c.grid.ncell, c.flags, 0);
+}
+
+__global__ void kb_scatter(const BatchTable t) {
+    int bid;
+    const CtxDev& c = batch_ctx(t, t.b256, bid);
+    scatter_body(c.cell, c.n, c.cell_start, c.cell_count, c.cell_atoms, c.flags, bid);
+}
+
+__global__ void kb_sort_cells(const BatchTable t) {
+    int bid;
+    const CtxDev& c = batch_ctx(t, t.bcell, bid);
+    sort_cells_body(c.cell_atoms, c.cell_start, c.cell_count, c.grid.ncell, c.flags, bid);
+}
+
+__global__ void kb_prepare(const BatchTable t) {
+    int bid;
+    const CtxDev& c = batch_ctx(t, t.b256, bid);
+    prepare_body(c.x, c.n, c.grid, c.dyn, c.d_time, c.cell, c.w_fixed, c.pos4, c.w, c.ace_list, c.flags, bid);
+}
+
+__global__ void __launch_bounds__(kBuildBlock) kb_build(const BatchTable t) {
+    int bid;
+    const CtxDev& c = batch_ctx(t, t.b128, bid);
+    build_body(c.pos4, c.cell, c.n, c.grid, c.D, c.cell_start, c.cell_atoms, c.nbr, c.nnbr, c.cap, c.flags, 0, bid);
+}
+
 }  // namespace
+
+int launch_batch_check(const BatchTable& t, cudaStream_t s) {
+    launch_pdl(kb_check, t.b256[t.nctx], 256, 0, s, t);
+    return 1;
+}
+
+int launch_batch_rebuild(const BatchTable& t, cudaStream_t s) {
+    launch_pdl(kb_wrap_bin, t.b256[t.nctx], 256, 0, s, t);
+    launch_pdl(kb_scan, t.nctx, 1024, 0, s, t);
+    launch_pdl(kb_scatter, t.b256[t.nctx], 256, 0, s, t);
+    launch_pdl(kb_sort_cells, t.bcell[t.nctx], 256, 0, s, t);
+    return 4;
+}
+
+int launch_batch_prepare(const BatchTable& t, cudaStream_t s) {
+    launch_pdl(kb_prepare, t.b256[t.nctx], 256, 0, s, t);
+    launch_pdl(kb_build, t.b128[t.nctx], kBuildBlock, 0, s, t);
+    return 2;
+}
 
 int launch_check(Ctx& c, cudaStream_t s) {
     double lim = 0.5 * c.skin;

@@ -2,8 +2,12 @@
 
 Continuous batching over whole MD requests.  Each admitted request gets its own context
 (`APContext`) on its own non-blocking stream.  In every scheduling pass the server issues
-one chunk of velocity-Verlet steps for each active request in a single `ap_step_batch`
-call, so the replayed step graphs of different requests overlap on the device.  Requests
+one chunk of velocity-Verlet steps for every active request: by default each request
+replays its own step graphs on its own stream, so the requests' kernels overlap on the
+device; with `batched`, the requests of at most `batch_atoms` atoms go through one
+`ap_step_batch` call on the server's stream instead, where every stage of a step is one
+kernel launch for all of them (per-atom stages give each request its own blocks, the ACE
+stages share one persistent grid over the compacted atoms of all requests).  Requests
 join at any pass once their device footprint (`ap_footprint_bytes`) fits the memory budget
 (first come, first served, no overtaking) and leave as soon as their last chunk has
 completed, which the server learns from a CUDA event without blocking the others.
@@ -49,10 +53,15 @@ class Server:
     max_active   cap on concurrently active requests
     inflight     chunks a request may have queued on its stream at once
     keep_arrays  keep final x, v, forces in each Result (else only the energy report)
+    batched      one ap_step_batch call per pass for the requests of at most batch_atoms
+                 atoms (every stage one launch for all of them); larger requests, which fill
+                 the GPU by themselves, step with their own replayed graphs on their own
+                 streams beside the batch.  False (the default, lower latency) steps every
+                 request on its own stream.
     """
 
     def __init__(self, mem_budget=None, chunk=8, dt=1.0, max_active=64, inflight=2, precision="fp32",
-                 keep_arrays=True):
+                 keep_arrays=True, batched=False, batch_atoms=1024):
         if mem_budget is None:
             free, _ = torch.cuda.mem_get_info()
             mem_budget = int(0.8 * free)
@@ -63,7 +72,10 @@ class Server:
         self.inflight = int(inflight)
         self.precision = precision
         self.keep_arrays = keep_arrays
+        self.batched = batched
+        self.batch_atoms = int(batch_atoms)
         self._streams = []
+        self.stream = torch.cuda.Stream()       # the batched launches
         self.used = 0
         self.peak_used = 0
         self.peak_active = 0
@@ -171,7 +183,12 @@ class Server:
             if batch:
                 ks = [min(self.chunk, a.left) for a in batch]
                 try:
-                    step_batch([a.ctx for a in batch], ks, self.dt)
+                    small = [q for q, a in enumerate(batch) if self.batched and len(a.req["x"]) <= self.batch_atoms]
+                    if small:
+                        step_batch([batch[q].ctx for q in small], [ks[q] for q in small], self.dt, self.stream)
+                    big = set(range(len(batch))) - set(small)
+                    for q in sorted(big):
+                        batch[q].ctx.step(ks[q], self.dt)
                 except APError:
                     # a launch was refused: every context was still issued; the failing ones
                     # report their status when they retire

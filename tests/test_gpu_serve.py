@@ -95,3 +95,47 @@ def test_realtime_arrivals_report_latency(apl):
     for r in res:
         assert r.admit_s >= r.arrival_s - 1e-9 and r.done_s >= r.admit_s
     assert 0 < percentile_ms(res, 50) <= percentile_ms(res, 99)
+
+
+def test_batched_step_equals_single_steps_bitwise(apl):
+    """ap_step_batch runs each stage as one launch for all contexts (Cu and W mixed, so the
+    batched contraction restages its coefficient tables); every context ends with the same
+    bits as the same steps taken alone, including contexts that leave the batch early."""
+    import torch
+    reqs = _mix(31, 7, max_atoms=2500)
+    steps = [int(r["n_steps"]) % 9 + 3 for r in reqs]
+
+    def ctx(r):
+        return apl.APContext(r["eam"], r["ace"], r["box"], r["x"], r["v"], r["fixed"], r["region"], None, None,
+                             r["mass"], stream=torch.cuda.Stream())
+
+    batch = [ctx(r) for r in reqs]
+    apl.step_batch(batch, steps, 1.0, torch.cuda.Stream())
+    for r, c, k in zip(reqs, batch, steps):
+        alone = ctx(r)
+        alone.step(k, 1.0)
+        xa, va, ta = alone.get_state()
+        xb, vb, tb = c.get_state()
+        assert ta == tb == k
+        assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+        assert np.array_equal(alone.forces(), c.forces())
+        assert alone.energy()["e_total"] == c.energy()["e_total"]
+        alone.close()
+        c.close()
+
+
+def test_batched_force_evaluation_equals_single(apl, orc):
+    import torch
+    reqs = _mix(32, 5, max_atoms=1500)
+    ctxs = [apl.APContext(r["eam"], r["ace"], r["box"], r["x"], None, None, r["region"], None, None, r["mass"])
+            for r in reqs]
+    apl.compute_forces_batch(ctxs, torch.cuda.Stream())
+    for r, c in zip(reqs, ctxs):
+        ref = orc.evaluate(r["x"], r["box"], r["eam"], r["ace"], r["region"])
+        F = c.forces()
+        assert np.abs(F.astype(np.float64) - ref["forces"]).max() <= FTOL
+        with apl.APContext(r["eam"], r["ace"], r["box"], r["x"], None, None, r["region"], None, None,
+                           r["mass"]) as one:
+            one.compute_forces()
+            assert np.array_equal(one.forces(), F)
+        c.close()
