@@ -64,19 +64,27 @@ struct AceDev {
 };
 
 // Coefficient tables of the tensor-core contraction.  The five (0, l, l) triples, whose
-// Gaunt coefficients are delta_{m2 m3} G_l (G_l = 1/sqrt(4 pi)), are stored as c0ll[p][l]
-// [(n2, n3)][n1] = G_l C3[n1, n2, n3] for the two-factor pass.  For the other nine triples
+// Gaunt coefficients are delta_{m2 m3} G_l (G_l = 1/sqrt(4 pi)), are stored for the
+// two-factor pass as c0ll[p][l][n1 / 4][c0ll_pos(n2 * 8 + n3)][n1 % 4] = G_l C3[n1, n2, n3]:
+// rows of four n1 (16 bytes) at a permuted pair position, so that the pass's 16-byte reads
+// (the pairs 8 g + 2 t + j of an mma accumulator tile) fall on distinct bank groups.  For the other nine triples
 // (t = 5 .. 13) and density p the coefficients form a 64 x 8 matrix C[q = n1 * 8 + n2][n3];
 // for the l1 = l2 triples the (n1 <= n2) coefficients are spread evenly over both orders
 // (n1, n2) and (n2, n1), whose product factors are equal.  Each entry is split into two
 // TF32 numbers hi + lo (13 low mantissa bits zero) for 3xTF32 products, and n3 is stored at
 // position n3 ^ (4 ((q >> 2) & 1)) so that the kernel's two fragment reads of the matrix
 // (as C and as its transpose) are free of shared-memory bank conflicts.
+// position of pair q = 8 g + 2 t + j (g = q / 8, t = (q / 2) % 4, j = q % 2) in the c0ll rows:
+// (g / 2, j, g % 2, t), so that the eight threads of a quarter warp (g in {2i, 2i + 1}, all t)
+// read eight distinct 16-byte units modulo 128 bytes
+__host__ __device__ constexpr int c0ll_pos(int q) {
+    return (q & 0x30) | ((q & 1) << 3) | (((q >> 3) & 1) << 2) | ((q >> 1) & 3);
+}
 constexpr int kNT3 = 9;             // l-triples on tensor cores
 constexpr int kTcTriple0 = 5;       // ... t = 5 .. 13
 struct alignas(16) AceTc {
     float c3[2][2][kNT3][64][8];    // [hi/lo][density][t - 5][q][n3 (swizzled)]
-    float c0ll[2][5][64][8];        // [density][l][n2 * 8 + n3][n1]
+    float c0ll[2][5][2][64][4];     // [density][l][n1 / 4][c0ll_pos(n2 * 8 + n3)][n1 % 4]
     float c2[2][5][64];             // as AceDev
     float c1[2][8];
     float c1_0, c2_0, nref_inv, rc;

@@ -770,134 +770,162 @@ __device__ __forceinline__ void tc_adjoint_all(const AceTc& C, TcWarpSmem& S, fl
     (tc_adjoint_triple<T>(C, S, s, lane), ...);
 }
 
-// sum_n1 c[n1] a[n1] for a 16-byte aligned row c of 8 floats
-__device__ __forceinline__ float dot8(const float* c, const float* a) {
-    const float4 u = *reinterpret_cast<const float4*>(c), v = *reinterpret_cast<const float4*>(c + 4);
-    float r = u.x * a[0];
-    r = fmaf(u.y, a[1], r);
-    r = fmaf(u.z, a[2], r);
-    r = fmaf(u.w, a[3], r);
-    r = fmaf(v.x, a[4], r);
-    r = fmaf(v.y, a[5], r);
-    r = fmaf(v.z, a[6], r);
-    return fmaf(v.w, a[7], r);
+// The one- and two-factor functions, with the (0, l, l) triples folded into the latter:
+//   phi_p += sum_l sum_q F_p[l][q] mm_l[q],  F_p[l][q] = c2_p[l][q] + sum_n1 c0ll_p[l][q][n1] A[n1, 00],
+//   mm_l[n1 n2] = sum_m A[n1, lm] A[n2, lm]  (the Gram matrix of the l-block, one 3xTF32 tile)
+// Thread (g, t) holds the pairs q = 8 g + 2 t + j (j = 0, 1) of the tile's accumulator rows.
+struct Nu2 {
+    float f[2][5][2];    // F_p[l][q_j]
+    float g[2][8];       // the thread's part of sum_{l, q} c0ll_p[l][q][n1] mm_l[q], the A[n1, 00] gradient
+};
+
+// mm_l[g][2 t + j] into mm[j] (rows g + 8 of the tile are zero); the A fragment of the Gram
+// tile is also its B fragment.  Columns past the l-block are read as zero: the padding of
+// the l-block layout is zero, and the next block's columns are masked
+template <int L>
+__device__ __forceinline__ void nu2_gram(const TcWarpSmem& S, int g, int t, float* mm) {
+    constexpr int B = lblk(L);
+    mm[0] = mm[1] = mm[2] = mm[3] = 0.0f;
+    const float x0 = S.A[g * kApad + B + t];
+    const float x2 = L >= 2 ? S.A[g * kApad + B + 4 + t] : 0.0f;
+    uint32_t h0, l0, h2, l2;
+    split_tf32(x0, h0, l0);
+    split_tf32(x2, h2, l2);
+    mma_tf32(mm, l0, 0u, l2, 0u, h0, h2);
+    mma_tf32(mm, h0, 0u, h2, 0u, l0, l2);
+    mma_tf32(mm, h0, 0u, h2, 0u, h0, h2);
+    if constexpr (L == 4) {                            // m = 8 and the block's zero padding
+        const float x4 = S.A[g * kApad + B + 8 + t];
+        split_tf32(x4, h0, l0);
+        mma_tf32(mm, l0, 0u, 0u, 0u, h0, 0u);
+        mma_tf32(mm, h0, 0u, 0u, 0u, l0, 0u);
+        mma_tf32(mm, h0, 0u, 0u, 0u, h0, 0u);
+    }
+}
+
+template <int L>
+__device__ __forceinline__ void nu2_forward_l(const AceTc& C, const TcWarpSmem& S, int g, int t, const float* a00,
+                                              float& p1, float& p2, Nu2& N) {
+    float mm[4];
+    nu2_gram<L>(S, g, t, mm);
+    const int q0 = 8 * g + 2 * t;
+    const float2 c20 = *reinterpret_cast<const float2*>(&C.c2[0][L][q0]);
+    const float2 c21 = *reinterpret_cast<const float2*>(&C.c2[1][L][q0]);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int pos = c0ll_pos(q0 + j);
+        const float4 u0 = *reinterpret_cast<const float4*>(C.c0ll[0][L][0][pos]);
+        const float4 u1 = *reinterpret_cast<const float4*>(C.c0ll[0][L][1][pos]);
+        const float4 v0 = *reinterpret_cast<const float4*>(C.c0ll[1][L][0][pos]);
+        const float4 v1 = *reinterpret_cast<const float4*>(C.c0ll[1][L][1][pos]);
+        const float cu[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+        const float cv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+        float f0 = j ? c20.y : c20.x, f1 = j ? c21.y : c21.x;
+#pragma unroll
+        for (int k = 0; k < kNmax; ++k) {
+            f0 = fmaf(cu[k], a00[k], f0);
+            f1 = fmaf(cv[k], a00[k], f1);
+            N.g[0][k] = fmaf(cu[k], mm[j], N.g[0][k]);
+            N.g[1][k] = fmaf(cv[k], mm[j], N.g[1][k]);
+        }
+        p1 = fmaf(f0, mm[j], p1);
+        p2 = fmaf(f1, mm[j], p2);
+        N.f[0][L][j] = f0;
+        N.f[1][L][j] = f1;
+    }
+}
+
+// dA_l[n1][m] += sum_n2 (CT[n1][n2] + CT[n2][n1]) A[n2, lm], CT = F_1 + s F_2, as one 3xTF32
+// tile (two for l = 4); CT and its transpose are staged in the (free) staging rows
+template <int L>
+__device__ __forceinline__ void nu2_adjoint_l(TcWarpSmem& S, int g, int t, float s, const Nu2& N) {
+    constexpr int B = lblk(L), W = 2 * L + 1;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float ct = fmaf(s, N.f[1][L][j], N.f[0][L][j]);
+        S.St[g][2 * t + j] = ct;                       // CT[n1][n2] at St[n1][n2]
+        S.St[2 * t + j][32 + g] = ct;                  // ... and at St[n2][32 + n1]
+    }
+    __syncwarp();
+    const float m0 = S.St[g][t] + S.St[g][32 + t];     // M[g][t] = CT[g][t] + CT[t][g]
+    const float m2 = S.St[g][t + 4] + S.St[g][36 + t]; // M[g][t + 4]
+    __syncwarp();                                      // the rows are free for the next l
+    uint32_t mh0, ml0, mh2, ml2;
+    split_tf32(m0, mh0, ml0);
+    split_tf32(m2, mh2, ml2);
+    // B[k = n2][n = m] = A[n2, lm]; columns past the block (l <= 1) give discarded outputs
+    {
+        float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        uint32_t bh0, bl0, bh1, bl1;
+        split_tf32(S.A[t * kApad + B + g], bh0, bl0);
+        split_tf32(S.A[(t + 4) * kApad + B + g], bh1, bl1);
+        mma_tf32(d, ml0, 0u, ml2, 0u, bh0, bh1);
+        mma_tf32(d, mh0, 0u, mh2, 0u, bl0, bl1);
+        mma_tf32(d, mh0, 0u, mh2, 0u, bh0, bh1);
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+            if (2 * t + j < W) S.dA[g * kApad + B + 2 * t + j] += d[j];
+    }
+    if constexpr (W > 8) {                             // m = 8: column 0 of the second tile
+        float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        uint32_t bh0, bl0, bh1, bl1;
+        split_tf32(g == 0 ? S.A[t * kApad + B + 8] : 0.0f, bh0, bl0);
+        split_tf32(g == 0 ? S.A[(t + 4) * kApad + B + 8] : 0.0f, bh1, bl1);
+        mma_tf32(d, ml0, 0u, ml2, 0u, bh0, bh1);
+        mma_tf32(d, mh0, 0u, mh2, 0u, bl0, bl1);
+        mma_tf32(d, mh0, 0u, mh2, 0u, bh0, bh1);
+        if (t == 0) S.dA[g * kApad + B + 8] += d[0];
+    }
 }
 
 // phi1, phi2 of the atom whose A is in S (tc_load_atom), E = phi1 + sqrt(phi2) without the
 // constant c1_0 into e_out, and dE/dA into S.dA; false outside the domain (phi2 <= 1e-3 or
 // a NaN), where E and dA carry no meaning
 __device__ __forceinline__ bool tc_contract_atom(const AceTc& C, TcWarpSmem& S, int lane, float& e_out) {
-    float a00[kNmax];
-#pragma unroll
-    for (int k = 0; k < kNmax; ++k) a00[k] = S.A[k * kApad];
-    // one- and two-factor functions, with the (0, l, l) triples folded into the latter
+    const int g = lane >> 2, t = lane & 3;
     float p1 = 0.0f, p2 = 0.0f;
-    if (lane < kNmax) {
-        p1 = C.c1[0][lane] * a00[lane];
-        p2 = C.c1[1][lane] * a00[lane];
-    }
-#pragma unroll 1
-    for (int pp = 0; pp < 2; ++pp) {
-        const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
-#pragma unroll
-        for (int l = 0; l <= kLmax; ++l) {
-            float mm = 0.0f;
-#pragma unroll
-            for (int k = 0; k < 2 * l + 1; ++k)
-                mm = fmaf(S.A[n1 * kApad + lblk(l) + k], S.A[n2 * kApad + lblk(l) + k], mm);
-            p1 = fmaf(C.c2[0][l][q] + dot8(C.c0ll[0][l][q], a00), mm, p1);
-            p2 = fmaf(C.c2[1][l][q] + dot8(C.c0ll[1][l][q], a00), mm, p2);
-        }
-    }
     // the tensor-core triples, grouped by l3
     tc_forward_group<2>(C, S, lane, p1, p2, std::integer_sequence<int, 5, 8>{});
     tc_forward_group<3>(C, S, lane, p1, p2, std::integer_sequence<int, 6, 10>{});
     tc_forward_group<4>(C, S, lane, p1, p2, std::integer_sequence<int, 7, 9, 11, 12, 13>{});
     __syncwarp();                                      // the epilogues' dA and R2 are visible
+    // one- and two-factor functions
+    float a00[kNmax];
+#pragma unroll
+    for (int k = 0; k < kNmax; ++k) a00[k] = S.A[k * kApad];
+    if (lane < kNmax) {
+        p1 = fmaf(C.c1[0][lane], a00[lane], p1);
+        p2 = fmaf(C.c1[1][lane], a00[lane], p2);
+    }
+    Nu2 N;
+#pragma unroll
+    for (int k = 0; k < kNmax; ++k) N.g[0][k] = N.g[1][k] = 0.0f;
+    nu2_forward_l<0>(C, S, g, t, a00, p1, p2, N);
+    nu2_forward_l<1>(C, S, g, t, a00, p1, p2, N);
+    nu2_forward_l<2>(C, S, g, t, a00, p1, p2, N);
+    nu2_forward_l<3>(C, S, g, t, a00, p1, p2, N);
+    nu2_forward_l<4>(C, S, g, t, a00, p1, p2, N);
     p1 = warp_sum(p1);
     p2 = warp_sum(p2);
     const bool ok = C.c2_0 + p2 > 1e-3f && p1 == p1;
     const float sq = ok ? sqrtf(C.c2_0 + p2) : 0.0f;
     const float s = ok ? 0.5f / sq : 0.0f;
     // adjoint: one- and two-factor functions (with the folded triples and their A[n1, 00]
-    // gradient g00), the second density's third-factor part
-    if (lane < kNmax) S.dA[lane * kApad] += fmaf(s, C.c1[1][lane], C.c1[0][lane]);
-    __syncwarp();
+    // gradient), the second density's third-factor part
+    nu2_adjoint_l<0>(S, g, t, s, N);
+    nu2_adjoint_l<1>(S, g, t, s, N);
+    nu2_adjoint_l<2>(S, g, t, s, N);
+    nu2_adjoint_l<3>(S, g, t, s, N);
+    nu2_adjoint_l<4>(S, g, t, s, N);
     float g00[kNmax];
 #pragma unroll
-    for (int k = 0; k < kNmax; ++k) g00[k] = 0.0f;
-#pragma unroll
-    for (int l = 0; l <= kLmax; ++l) {
-        constexpr int WM = 9;
-        float d2[WM];
-#pragma unroll
-        for (int k = 0; k < WM; ++k) d2[k] = 0.0f;
-#pragma unroll 1
-        for (int pp = 0; pp < 2; ++pp) {
-            const int q = lane + 32 * pp, n1 = q >> 3, n2 = q & 7;
-            float cs[kNmax];
-            {
-                const float* c0 = C.c0ll[0][l][q];
-                const float* c1 = C.c0ll[1][l][q];
-                const float4 u0 = *reinterpret_cast<const float4*>(c0), u1 = *reinterpret_cast<const float4*>(c0 + 4);
-                const float4 v0 = *reinterpret_cast<const float4*>(c1), v1 = *reinterpret_cast<const float4*>(c1 + 4);
-                cs[0] = fmaf(s, v0.x, u0.x); cs[1] = fmaf(s, v0.y, u0.y); cs[2] = fmaf(s, v0.z, u0.z);
-                cs[3] = fmaf(s, v0.w, u0.w); cs[4] = fmaf(s, v1.x, u1.x); cs[5] = fmaf(s, v1.y, u1.y);
-                cs[6] = fmaf(s, v1.z, u1.z); cs[7] = fmaf(s, v1.w, u1.w);
-            }
-            float ct = fmaf(s, C.c2[1][l][q], C.c2[0][l][q]);
-            float mm = 0.0f;
-            float d1[WM];
-#pragma unroll
-            for (int k = 0; k < 2 * l + 1; ++k) {
-                const float a1 = S.A[n1 * kApad + lblk(l) + k], a2 = S.A[n2 * kApad + lblk(l) + k];
-                mm = fmaf(a1, a2, mm);
-            }
-#pragma unroll
-            for (int k = 0; k < kNmax; ++k) {
-                ct = fmaf(cs[k], a00[k], ct);
-                g00[k] = fmaf(cs[k], mm, g00[k]);
-            }
-#pragma unroll
-            for (int k = 0; k < 2 * l + 1; ++k) {
-                const float a1 = S.A[n1 * kApad + lblk(l) + k], a2 = S.A[n2 * kApad + lblk(l) + k];
-                d1[k] = ct * a2;
-                d2[k] = fmaf(ct, a1, d2[k]);
-            }
-#pragma unroll
-            for (int k = 0; k < 2 * l + 1; ++k) {
-                float v = d1[k];
-                v += __shfl_xor_sync(0xffffffffu, v, 1);
-                v += __shfl_xor_sync(0xffffffffu, v, 2);
-                v += __shfl_xor_sync(0xffffffffu, v, 4);
-                d1[k] = v;
-            }
-            if ((lane & 7) == 0) {
-#pragma unroll
-                for (int k = 0; k < 2 * l + 1; ++k) S.dA[n1 * kApad + lblk(l) + k] += d1[k];
-            }
-            __syncwarp();
-        }
-#pragma unroll
-        for (int k = 0; k < 2 * l + 1; ++k) {
-            float v = d2[k];
-            v += __shfl_xor_sync(0xffffffffu, v, 8);
-            v += __shfl_xor_sync(0xffffffffu, v, 16);
-            d2[k] = v;
-        }
-        if (lane < 8) {
-#pragma unroll
-            for (int k = 0; k < 2 * l + 1; ++k) S.dA[lane * kApad + lblk(l) + k] += d2[k];
-        }
-        __syncwarp();
-    }
-#pragma unroll
-    for (int k = 0; k < kNmax; ++k) g00[k] = warp_sum(g00[k]);
+    for (int k = 0; k < kNmax; ++k) g00[k] = warp_sum(fmaf(s, N.g[1][k], N.g[0][k]));
+    __syncwarp();
     if (lane < kNmax) {
-        float g = g00[0];
+        float gk = g00[0];
 #pragma unroll
-        for (int k = 1; k < kNmax; ++k) g = lane == k ? g00[k] : g;
-        S.dA[lane * kApad] += g;
+        for (int k = 1; k < kNmax; ++k) gk = lane == k ? g00[k] : gk;
+        S.dA[lane * kApad] += gk + fmaf(s, C.c1[1][lane], C.c1[0][lane]);
     }
     for (int e = lane; e < kNmax * 21; e += 32) {
         // lm = 4 .. 24: l3 = 2, 3, 4 of the tensor-core triples

@@ -404,7 +404,7 @@ void build_ace_tc(const AceDev& in, AceTc& out) {
             for (int n1 = 0; n1 < kNmax; ++n1)
                 for (int n2 = 0; n2 < kNmax; ++n2)
                     for (int n3 = 0; n3 < kNmax; ++n3)
-                        out.c0ll[d][l][n2 * 8 + n3][n1] = g * in.c3[d][l][n3][n1 * 8 + n2];
+                        out.c0ll[d][l][n1 / 4][c0ll_pos(n2 * 8 + n3)][n1 % 4] = g * in.c3[d][l][n3][n1 * 8 + n2];
         }
         for (int u = 0; u < kNT3; ++u) {
             const int t = kTcTriple0 + u;
