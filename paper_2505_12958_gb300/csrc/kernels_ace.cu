@@ -192,7 +192,9 @@ __device__ __forceinline__ void all_p(float* P, const float* A1, const float* A2
     (ent_p<T, E>(P, A1, A2, t), ...);
 }
 
-template <int T, int E>
+// with D2 false only the first-factor gradient d1 (the l1 = l2 triples, whose second-factor
+// gradient summed over pairs equals the first-factor one)
+template <int T, bool D2, int E>
 __device__ __forceinline__ void ent_x(float* d1, float* d2, const float* A1, const float* A2, const float* Q,
                                       float& u) {
     using R = Tri<T>;
@@ -201,14 +203,14 @@ __device__ __forceinline__ void ent_x(float* d1, float* d2, const float* A1, con
     else u = fmaf(c_gaunt[R::OFF + E], Q[i3], u);
     if constexpr (R::template last12<E>()) {
         d1[i1] = fmaf(u, A2[i2], d1[i1]);
-        d2[i2] = fmaf(u, A1[i1], d2[i2]);
+        if constexpr (D2) d2[i2] = fmaf(u, A1[i1], d2[i2]);
     }
 }
-template <int T, int... E>
+template <int T, bool D2, int... E>
 __device__ __forceinline__ void all_x(float* d1, float* d2, const float* A1, const float* A2, const float* Q,
                                       std::integer_sequence<int, E...>) {
     float u = 0.0f;
-    (ent_x<T, E>(d1, d2, A1, A2, Q, u), ...);
+    (ent_x<T, D2, E>(d1, d2, A1, A2, Q, u), ...);
 }
 
 template <int W>
@@ -720,7 +722,12 @@ __device__ __forceinline__ void tc_adjoint_triple(const AceTc& C, TcWarpSmem& S,
 #pragma unroll 2
     for (int mt = 0; mt < 4; ++mt) tc_q_tile<T, NT>(C, S, lane, mt, bh, bl);
     __syncwarp();
-    // Gaunt adjoint of the lane's pairs (n1, n2) = (lane / 8 + 4 pp, lane % 8)
+    // Gaunt adjoint of the lane's pairs (n1, n2) = (lane / 8 + 4 pp, lane % 8).  For l1 = l2
+    // the coefficients are symmetric in (n1, n2) and the Gaunt coefficients in (m1, m2), so
+    // the second-factor gradient summed over the pairs equals the first-factor one: d1 is
+    // taken twice and d2 is not formed
+    constexpr bool SYM = R::L1 == R::L2;
+    constexpr float F1 = SYM ? 2.0f : 1.0f;
     const int n1 = lane >> 3, n2 = lane & 7;
     float A2[R::W2], d2[R::W2];
     load_row<R::W2>(A2, S.A + n2 * kApad + R::B2);
@@ -735,7 +742,7 @@ __device__ __forceinline__ void tc_adjoint_triple(const AceTc& C, TcWarpSmem& S,
         for (int k = 0; k < R::W3; ++k) Q[k] = S.St[k][q];
 #pragma unroll
         for (int k = 0; k < R::W1; ++k) d1[k] = 0.0f;
-        all_x<T>(d1, d2, A1, A2, Q, std::make_integer_sequence<int, R::N>{});
+        all_x<T, !SYM>(d1, d2, A1, A2, Q, std::make_integer_sequence<int, R::N>{});
 #pragma unroll
         for (int k = 0; k < R::W1; ++k) {
             float v = d1[k];
@@ -746,22 +753,24 @@ __device__ __forceinline__ void tc_adjoint_triple(const AceTc& C, TcWarpSmem& S,
         }
         if ((lane & 7) == 0) {
 #pragma unroll
-            for (int k = 0; k < R::W1; ++k) S.dA[r1 * kApad + R::B1 + k] += d1[k];
+            for (int k = 0; k < R::W1; ++k) S.dA[r1 * kApad + R::B1 + k] = fmaf(F1, d1[k], S.dA[r1 * kApad + R::B1 + k]);
         }
         __syncwarp();
     }
+    if constexpr (!SYM) {
 #pragma unroll
-    for (int k = 0; k < R::W2; ++k) {
-        float v = d2[k];
-        v += __shfl_xor_sync(0xffffffffu, v, 8);
-        v += __shfl_xor_sync(0xffffffffu, v, 16);
-        d2[k] = v;
-    }
-    if (lane < 8) {
+        for (int k = 0; k < R::W2; ++k) {
+            float v = d2[k];
+            v += __shfl_xor_sync(0xffffffffu, v, 8);
+            v += __shfl_xor_sync(0xffffffffu, v, 16);
+            d2[k] = v;
+        }
+        if (lane < 8) {
 #pragma unroll
-        for (int k = 0; k < R::W2; ++k) S.dA[lane * kApad + R::B2 + k] += d2[k];
+            for (int k = 0; k < R::W2; ++k) S.dA[lane * kApad + R::B2 + k] += d2[k];
+        }
+        __syncwarp();
     }
-    __syncwarp();
 }
 
 template <int... T>
