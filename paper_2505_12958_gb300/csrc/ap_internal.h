@@ -68,9 +68,10 @@ struct AceDev {
 // two-factor pass as c0ll[p][l][n1 / 4][c0ll_pos(n2 * 8 + n3)][n1 % 4] = G_l C3[n1, n2, n3]:
 // rows of four n1 (16 bytes) at a permuted pair position, so that the pass's 16-byte reads
 // (the pairs 8 g + 2 t + j of an mma accumulator tile) fall on distinct bank groups.  For the other nine triples
-// (t = 5 .. 13) and density p the coefficients form a 64 x 8 matrix C[q = n1 * 8 + n2][n3];
-// for the l1 = l2 triples the (n1 <= n2) coefficients are spread evenly over both orders
-// (n1, n2) and (n2, n1), whose product factors are equal.  Each entry is split into two
+// (t = 5 .. 13) and density p the coefficients form a 64 x 8 matrix C[q = n1 * 8 + n2][n3].
+// For the l1 = l2 triples the product of the first two factors is symmetric in (n1, n2): their
+// rows are packed, row sym_pair(n1, n2) (n1 <= n2, 36 rows, the rest zero) holding the mean of
+// the coefficients of (n1, n2) and (n2, n1).  Each entry is split into two
 // TF32 numbers hi + lo (13 low mantissa bits zero) for 3xTF32 products, and n3 is stored at
 // position n3 ^ (4 ((q >> 2) & 1)) so that the kernel's two fragment reads of the matrix
 // (as C and as its transpose) are free of shared-memory bank conflicts.
@@ -80,6 +81,9 @@ struct AceDev {
 __host__ __device__ constexpr int c0ll_pos(int q) {
     return (q & 0x30) | ((q & 1) << 3) | (((q >> 3) & 1) << 2) | ((q >> 1) & 3);
 }
+// packed index of the unordered pair n1 <= n2 (row-major upper triangle of 8 x 8)
+constexpr int kSymPairs = 36;
+__host__ __device__ constexpr int sym_pair(int n1, int n2) { return n1 * (15 - n1) / 2 + n2; }
 constexpr int kNT3 = 9;             // l-triples on tensor cores
 constexpr int kTcTriple0 = 5;       // ... t = 5 .. 13
 struct alignas(16) AceTc {

@@ -572,6 +572,7 @@ __device__ __forceinline__ void ldsm_x2(uint32_t* r, const float* p) {
 template <int T>
 __device__ __forceinline__ void tc_stage_p(TcWarpSmem& S, int lane) {
     using R = Tri<T>;
+    constexpr bool SYM = R::L1 == R::L2;
     const int n2 = lane & 7;
     float A2[R::W2];
     load_row<R::W2>(A2, S.A + n2 * kApad + R::B2);
@@ -583,8 +584,21 @@ __device__ __forceinline__ void tc_stage_p(TcWarpSmem& S, int lane) {
 #pragma unroll
         for (int k = 0; k < R::W3; ++k) P[k] = 0.0f;
         all_p<T>(P, A1, A2, std::make_integer_sequence<int, R::N>{});
+        if constexpr (SYM) {
+            // packed columns: the pair n1 <= n2 stands for both orders (P is symmetric)
+            if (n1 <= n2) {
+                const float f = n1 < n2 ? 2.0f : 1.0f;
 #pragma unroll
-        for (int k = 0; k < R::W3; ++k) S.St[k][q] = P[k];
+                for (int k = 0; k < R::W3; ++k) S.St[k][sym_pair(n1, n2)] = f * P[k];
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < R::W3; ++k) S.St[k][q] = P[k];
+        }
+    }
+    if constexpr (SYM) {
+        // K runs to 40: columns 36..39 meet zero coefficient rows and must hold finite values
+        for (int e = lane; e < 4 * R::W3; e += 32) S.St[e >> 2][kSymPairs + (e & 3)] = 0.0f;
     }
 }
 
@@ -599,7 +613,7 @@ __device__ __forceinline__ void tc_r_gemm(const AceTc& C, const TcWarpSmem& S, i
     // ldmatrix rows of the B fragment: matrix j = lane / 8 reads row m3 = lane % 8, q chunk j
     const float* brow = &S.St[lane & 7][4 * ((lane >> 3) & 1)];
 #pragma unroll 2
-    for (int ks = 0; ks < 8; ++ks) {
+    for (int ks = 0; ks < (R::L1 == R::L2 ? 5 : 8); ++ks) {    // packed pairs of the l1 = l2 triples: K = 40
         const int qa = 8 * ks + tq, qb = qa + 4;
         uint32_t ah[4], al[4];
         ah[0] = __float_as_uint(C.c3[0][0][U][qa][gq]);
@@ -720,7 +734,7 @@ __device__ __forceinline__ void tc_adjoint_triple(const AceTc& C, TcWarpSmem& S,
         split_tf32(s * x1, bh[nt][1][1], bl[nt][1][1]);
     }
 #pragma unroll 2
-    for (int mt = 0; mt < 4; ++mt) tc_q_tile<T, NT>(C, S, lane, mt, bh, bl);
+    for (int mt = 0; mt < (R::L1 == R::L2 ? 3 : 4); ++mt) tc_q_tile<T, NT>(C, S, lane, mt, bh, bl);
     __syncwarp();
     // Gaunt adjoint of the lane's pairs (n1, n2) = (lane / 8 + 4 pp, lane % 8).  For l1 = l2
     // the coefficients are symmetric in (n1, n2) and the Gaunt coefficients in (m1, m2), so
@@ -739,7 +753,9 @@ __device__ __forceinline__ void tc_adjoint_triple(const AceTc& C, TcWarpSmem& S,
         float A1[R::W1], d1[R::W1], Q[R::W3];
         load_row<R::W1>(A1, S.A + r1 * kApad + R::B1);
 #pragma unroll
-        for (int k = 0; k < R::W3; ++k) Q[k] = S.St[k][q];
+        const int qs = SYM ? sym_pair(min(r1, n2), max(r1, n2)) : q;    // Q is symmetric for l1 = l2
+#pragma unroll
+        for (int k = 0; k < R::W3; ++k) Q[k] = S.St[k][qs];
 #pragma unroll
         for (int k = 0; k < R::W1; ++k) d1[k] = 0.0f;
         all_x<T, !SYM>(d1, d2, A1, A2, Q, std::make_integer_sequence<int, R::N>{});

@@ -412,11 +412,13 @@ void build_ace_tc(const AceDev& in, AceTc& out) {
             for (int n3 = 0; n3 < kNmax; ++n3)
                 for (int n1 = 0; n1 < kNmax; ++n1)
                     for (int n2 = 0; n2 < kNmax; ++n2) {
-                        const int q = n1 * 8 + n2;
-                        float v = in.c3[d][t][n3][q];
+                        if (sym && n1 > n2) continue;
                         // the product of the first two factors is symmetric in (n1, n2) when
-                        // l1 = l2: both orders carry half of the function's coefficient
-                        if (sym && n1 != n2) v = 0.5f * (in.c3[d][t][n3][q] + in.c3[d][t][n3][n2 * 8 + n1]);
+                        // l1 = l2: the packed row of the pair n1 <= n2 holds the mean of both
+                        // orders' coefficients (the kernel doubles the product of n1 < n2)
+                        const int q = sym ? sym_pair(n1, n2) : n1 * 8 + n2;
+                        float v = in.c3[d][t][n3][n1 * 8 + n2];
+                        if (sym && n1 != n2) v = 0.5f * (in.c3[d][t][n3][n1 * 8 + n2] + in.c3[d][t][n3][n2 * 8 + n1]);
                         const float hi = tf32_rna(v), lo = tf32_rna(v - hi);
                         const int pos = n3 ^ (4 * ((q >> 2) & 1));
                         out.c3[0][d][u][q][pos] = hi;
