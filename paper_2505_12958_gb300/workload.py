@@ -68,27 +68,40 @@ def ace_tc_contract_work():
 
       fp32:   the arithmetic left on the FP32 lanes: the Gaunt products P of the nine triples
               with l1 > 0 (per active (n1, n2) pair g12 + 2 nnz; 36 pairs when l1 = l2, else
-              64) and their first/second-factor adjoint (2 nnz + 3 g12 per pair); the
-              two-factor terms with the five (0, l, l) triples folded in (36 pairs, per l:
-              forward W_l FMA, per density 8 FMA for the folded coefficient and 1 FMA;
-              adjoint 3 W_l + 50); the epilogue per l3 (phi and the third-factor gradient);
-              the one-factor terms.
-      tensor: the two coefficient contractions R = C^T P and Q = C [A; sA] over the active
-              pairs: 2 x 16 x pairs x W3 FLOPs each.
-      tensor_executed: what the mma.sync tiles execute: three TF32 products (3xTF32) of
-              16 x 64 x (W3 rounded up to 8) per contraction."""
+              64) and their factor gradients (per ordered pair: 2 nnz + 3 g12 for d1 and d2;
+              for l1 = l2 only d1, 2 nnz + g12, taken twice); for the two-factor terms with
+              the five (0, l, l) triples folded in, per l and nonzero pair (36): the folded
+              coefficient, phi and the A[n1, 00] gradient of both densities (68), and the
+              adjoint coefficient (2); the A[n1, 00] gradient's combination and warp sum; the
+              epilogue per l3 (phi and the third-factor gradient); the one-factor terms.
+      tensor: the coefficient contractions R = C^T P and Q = C [A; sA] over the active pairs
+              (2 x 16 x pairs x W3 FLOPs each), and the two-factor Gram products
+              mm_l = A_l A_l^T (36 pairs x W_l) and their adjoint (CT + CT^T) A_l (64 x W_l).
+      tensor_executed: what the mma.sync m16n8k8 tiles execute (2048 FLOPs each; 3xTF32 =
+              three per product): R over 8 K steps (5 for the packed l1 = l2 triples) and Q
+              over 4 row tiles (3 packed), two column tiles where W3 = 9; per l one Gram and
+              one adjoint tile (two K steps or two column tiles at l = 4)."""
+    mma = 2 * 16 * 8 * 8
     fp32 = tensor = executed = 0
     for (l1, l2, l3), nnz in zip(TRIPLES, NNZ):
         if l1 == 0:
             continue
         g12 = len({(a, b) for a, b, _ in _pattern(l1, l2, l3)})
         w3 = 2 * l3 + 1
-        pairs = 36 if l1 == l2 else 64
-        fp32 += pairs * (g12 + 2 * nnz) + pairs * (2 * nnz + 3 * g12)
+        sym = l1 == l2
+        pairs = 36 if sym else 64
+        nt = (w3 + 7) // 8
+        fp32 += pairs * (g12 + 2 * nnz)
+        fp32 += 64 * (2 * nnz + g12) if sym else 64 * (2 * nnz + 3 * g12)
         tensor += 2 * (2 * 16 * pairs * w3)
-        executed += 2 * 3 * (2 * 16 * 64 * (8 * ((w3 + 7) // 8)))
-    fp32 += 36 * sum(2 * (2 * l + 1) + 2 * (16 + 2) for l in range(5))
-    fp32 += 36 * sum(3 * (2 * l + 1) + 50 for l in range(5))
+        executed += 3 * mma * nt * (5 if sym else 8)            # R: K steps x column tiles
+        executed += 3 * mma * nt * 2 * (3 if sym else 4)        # Q: row tiles x 2 densities
+    for l in range(5):
+        w = 2 * l + 1
+        fp32 += 36 * (68 + 2)
+        tensor += 2 * 36 * w + 2 * 64 * w
+        executed += 2 * 3 * mma * (2 if l == 4 else 1)
+    fp32 += 32 * 2 * 8 + 2 * 8 * 31
     fp32 += 2 * 2 * 8 * sum(2 * l + 1 for l in (2, 3, 4)) + 2 * 8 * sum(2 * l + 1 for l in (2, 3, 4))
     fp32 += 8 * 4 + 8 * 2
     return {"fp32": fp32, "tensor": tensor, "tensor_executed": executed}

@@ -34,10 +34,16 @@ def test_pattern_sizes_and_total():
 
 def test_tensor_core_kernel_work_split():
     """The tensor-core kernel's work: the coefficient contractions over the active (n1, n2)
-    pairs of the nine triples with l1 > 0 (36 pairs when l1 = l2) and their 3xTF32 tiles."""
+    pairs of the nine triples with l1 > 0 (36 pairs when l1 = l2), the two-factor Gram
+    products and their adjoint, and the 3xTF32 m16n8k8 tiles that run them (the packed
+    l1 = l2 triples: 5 K steps of R and 3 row tiles of Q)."""
     w = workload.ace_tc_contract_work()
     tc = [(t, 36 if t[0] == t[1] else 64) for t in TRIPLES if t[0] > 0]
     assert len(tc) == 9
-    assert w["tensor"] == sum(2 * 2 * 16 * p * (2 * t[2] + 1) for t, p in tc)
-    assert w["tensor_executed"] == sum(2 * 3 * 2 * 16 * 64 * (8 if t[2] < 4 else 16) for t, _ in tc)
-    assert w == {"fp32": 150348, "tensor": 216320, "tensor_executed": 1376256}
+    gram = sum(2 * 36 * (2 * l + 1) + 2 * 64 * (2 * l + 1) for l in range(5))
+    assert w["tensor"] == sum(2 * 2 * 16 * p * (2 * t[2] + 1) for t, p in tc) + gram
+    tile = 2 * 16 * 8 * 8
+    r_tiles = sum((5 if t[0] == t[1] else 8) * (2 if t[2] == 4 else 1) for t, _ in tc)
+    q_tiles = sum(2 * (3 if t[0] == t[1] else 4) * (2 if t[2] == 4 else 1) for t, _ in tc)
+    assert w["tensor_executed"] == 3 * tile * (r_tiles + q_tiles + 2 * 6)
+    assert w == {"fp32": 149284, "tensor": 221320, "tensor_executed": 1204224}
