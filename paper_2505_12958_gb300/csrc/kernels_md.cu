@@ -79,6 +79,33 @@ __device__ __forceinline__ void blend_body(
     // margin, and for the weight-gradient force of the switching shell, whose relative error
     // of ~1e-6 stays far below the force bar; only atoms near the tip read FP64 positions.
     __shared__ float sh[12];         // box origin, cell edges, tip centre and zone centre at time t
+    const int i = bid * blockDim.x + threadIdx.x;
+    // Every load of the atom's own data is issued here, before the block barrier and before
+    // any store: a store to acc or v between loads of the same array would order them into a
+    // chain of dependent memory round trips (the compiler cannot rule out that the k-th and
+    // (k+1)-th components alias).
+    const bool kick = hdta != 0.0;
+    float wi = 0.0f, F0[3] = {0.0f, 0.0f, 0.0f};
+    long long qa[3] = {0, 0, 0};
+    float4 p = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    int ci = 0;
+    bool fixed_i = true;
+    double vv[3] = {0.0, 0.0, 0.0};
+    if (i < n) {
+        wi = wv[i];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            qa[k] = (long long)acc[(size_t)k * n + i];
+            F0[k] = f[(size_t)k * n + i];
+        }
+        p = pos4[i];
+        ci = cell[i];
+        if (kick) {
+            fixed_i = fixed[i] != 0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) vv[k] = v[(size_t)k * n + i];
+        }
+    }
     if (threadIdx.x == 0 && g.ortho) {
         const double t = *tptr;
         for (int q = 0; q < 3; ++q) {
@@ -89,25 +116,22 @@ __device__ __forceinline__ void blend_body(
         }
     }
     __syncthreads();
-    const int i = bid * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float wi = wv[i];
     float F[3];
     for (int k = 0; k < 3; ++k) {
-        const long long q = (long long)acc[(size_t)k * n + i];
+        const long long q = qa[k];
         acc[(size_t)k * n + i] = 0ull;
         // q 2^-40 without FP64 instructions: q = hi 2^32 + lo, lo in [0, 2^32); hi 2^-8 is
         // exact in FP32 for forces below 2^16 eV/A and the sum is rounded once
         const int hi = (int)(q >> 32);
         const unsigned lo = (unsigned)(q & 0xffffffffll);
-        F[k] = f[(size_t)k * n + i] + fmaf((float)hi, 0x1p-8f, (float)lo * 0x1p-40f);
+        F[k] = F0[k] + fmaf((float)hi, 0x1p-8f, (float)lo * 0x1p-40f);
     }
     const bool trans = dy.reg_kind == AP_REGION_SPHERE && wi > 0.0f && wi < 1.0f;
     bool near_tip = dy.ind_on;
     if (g.ortho && (trans || near_tip)) {
-        const float4 p = pos4[i];
         int cc[3];
-        cell_coords(g, cell[i], cc);
+        cell_coords(g, ci, cc);
         float xf[3];
         xf[0] = fmaf((float)cc[0], sh[3], sh[0]) + p.x;
         xf[1] = fmaf((float)cc[1], sh[4], sh[1]) + p.y;
@@ -167,8 +191,8 @@ __device__ __forceinline__ void blend_body(
         for (int k = 0; k < 3; ++k) out_aos[3 * (size_t)i + k] = F[k];
     // the second half kick of a velocity-Verlet step, when nothing else adds to F before it
     // (the same arithmetic as k_kick)
-    if (hdta != 0.0 && !fixed[i])
-        for (int k = 0; k < 3; ++k) v[(size_t)k * n + i] += hdta * (double)F[k];
+    if (kick && !fixed_i)
+        for (int k = 0; k < 3; ++k) v[(size_t)k * n + i] = vv[k] + hdta * (double)F[k];
     if (!(F[0] == F[0]) || !(F[1] == F[1]) || !(F[2] == F[2])) {
         atomicOr(&flags[kFlagErr], kErrDomain);
         flags[kFlagBad] = i;
@@ -293,14 +317,27 @@ __device__ __forceinline__ void kick_drift_body(double* __restrict__ x, double* 
             load_ring_t[slot] = *tptr;
         }
     }
-    if (i >= n || fixed[i]) return;
-    double d2 = 0.0;
+    if (i >= n) return;
+    // all loads first (see blend_body): the stores to v and x would otherwise order the
+    // component loads into dependent round trips
+    double v0[3], x0[3], b0[3];
+    float f0[3];
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const double vk = v[(size_t)k * n + i] + hdta * (double)f[(size_t)k * n + i];
+        v0[k] = v[(size_t)k * n + i];
+        f0[k] = f[(size_t)k * n + i];
+        x0[k] = x[(size_t)k * n + i];
+        b0[k] = xb[(size_t)k * n + i];
+    }
+    if (fixed[i]) return;
+    double d2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double vk = v0[k] + hdta * (double)f0[k];
         v[(size_t)k * n + i] = vk;
-        const double xk = x[(size_t)k * n + i] + dt * vk;
+        const double xk = x0[k] + dt * vk;
         x[(size_t)k * n + i] = xk;
-        const double d = xk - xb[(size_t)k * n + i];
+        const double d = xk - b0[k];
         d2 += d * d;
     }
     if (d2 > lim2) flags[kFlagRebuild] = 1;
