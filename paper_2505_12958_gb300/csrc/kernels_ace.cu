@@ -243,24 +243,36 @@ __device__ __forceinline__ int gather_ace_neighbors(const float4* __restrict__ p
                                                     int* nbj, int lane) {
     const float4 p = pos4[i];
     int cnt = 0;
-    for (int k0 = 0; k0 < m; k0 += 32) {
-        const int k = k0 + lane;
-        bool in = false;
-        float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
-        int j = 0;
-        if (k < m) {
-            const int e = nbr[(size_t)k * n + i];
-            j = e & kNbrMask;
-            const float4 d = Ds[(unsigned)e >> kNbrShift];
-            const float4 q = pos4[j];
-            dx = q.x + d.x - p.x; dy = q.y + d.y - p.y; dz = q.z + d.z - p.z;
-            r2 = dx * dx + dy * dy + dz * dz;
-            in = r2 < rc2 && r2 > 0.0f;
+    // four rounds of 32 list entries at a time: all list loads, then all position gathers,
+    // then the compaction in list order (two dependent memory round trips per 128 entries
+    // instead of two per 32)
+    constexpr int U = 4;
+    for (int k0 = 0; k0 < m; k0 += 32 * U) {
+        int e[U];                                      // j | code << 25 (the code may set bit 31)
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = k0 + 32 * u + lane;
+            e[u] = k < m ? nbr[(size_t)k * n + i] : 0;
         }
-        const unsigned bm = __ballot_sync(0xffffffffu, in);
-        const int pos = cnt + __popc(bm & ((1u << lane) - 1u));
-        if (in && pos < kAceNbrCap) { nb[pos] = make_float4(dx, dy, dz, sqrtf(r2)); nbj[pos] = j; }
-        cnt += __popc(bm);
+        float4 q[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            q[u] = k0 + 32 * u + lane < m ? pos4[e[u] & kNbrMask] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            bool in = false;
+            float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+            if (k0 + 32 * u + lane < m) {
+                const float4 d = Ds[(unsigned)e[u] >> kNbrShift];
+                dx = q[u].x + d.x - p.x; dy = q[u].y + d.y - p.y; dz = q[u].z + d.z - p.z;
+                r2 = dx * dx + dy * dy + dz * dz;
+                in = r2 < rc2 && r2 > 0.0f;
+            }
+            const unsigned bm = __ballot_sync(0xffffffffu, in);
+            const int pos = cnt + __popc(bm & ((1u << lane) - 1u));
+            if (in && pos < kAceNbrCap) { nb[pos] = make_float4(dx, dy, dz, sqrtf(r2)); nbj[pos] = e[u] & kNbrMask; }
+            cnt += __popc(bm);
+        }
     }
     __syncwarp();
     return cnt > kAceNbrCap ? -1 : cnt;
@@ -1070,12 +1082,15 @@ __device__ __forceinline__ void force_atom(const float4* __restrict__ pos4, cons
                                            const float* __restrict__ dAin, float* __restrict__ vir,
                                            unsigned long long* __restrict__ acc, int a, ForceSmem& S, int lane) {
     const float rc2 = rc * rc;
+    // dE/dA of the atom is requested before the gather, so that its load overlaps it
+    const float4* dsrc = reinterpret_cast<const float4*>(dAin + (size_t)a * kNLM * kNmax);
+    const float4 da0 = dsrc[lane], da1 = lane < 2 * kNLM - 32 ? dsrc[32 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
     const int i = ace_list[a];
     const float wi = wv[i];
     const int cnt = gather_ace_neighbors(pos4, nbr, n, i, nnbr[i], Ds, rc2, S.nb, S.nbj, lane);
     if (cnt < 0) return;
-    for (int k = lane; k < kNLM * 2; k += 32)
-        reinterpret_cast<float4*>(&S.dAT[0][0])[k] = reinterpret_cast<const float4*>(dAin + (size_t)a * kNLM * kNmax)[k];
+    reinterpret_cast<float4*>(&S.dAT[0][0])[lane] = da0;
+    if (lane < 2 * kNLM - 32) reinterpret_cast<float4*>(&S.dAT[0][0])[32 + lane] = da1;
     __syncwarp();
     float fsx = 0.f, fsy = 0.f, fsz = 0.f;
     float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f, v4 = 0.f, v5 = 0.f;
