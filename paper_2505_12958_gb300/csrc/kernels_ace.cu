@@ -238,15 +238,15 @@ __device__ __forceinline__ void fix_add(unsigned long long* p, float v) {
 
 // neighbours of atom i inside the ACE cutoff, from the full list, into S (warp-uniform count;
 // returns -1 when there are more than kAceNbrCap)
+// U rounds of 32 list entries at a time: all their list loads, then all their position
+// gathers, then the compaction in list order (two dependent memory round trips per 32 U
+// entries); the neighbour order does not depend on U
+template <int U>
 __device__ __forceinline__ int gather_ace_neighbors(const float4* __restrict__ pos4, const int* __restrict__ nbr,
                                                     int n, int i, int m, const float4* Ds, float rc2, float4* nb,
                                                     int* nbj, int lane) {
     const float4 p = pos4[i];
     int cnt = 0;
-    // four rounds of 32 list entries at a time: all list loads, then all position gathers,
-    // then the compaction in list order (two dependent memory round trips per 128 entries
-    // instead of two per 32)
-    constexpr int U = 4;
     for (int k0 = 0; k0 < m; k0 += 32 * U) {
         int e[U];                                      // j | code << 25 (the code may set bit 31)
 #pragma unroll
@@ -399,7 +399,7 @@ __device__ __forceinline__ void basis_atom(const float4* __restrict__ pos4, cons
     const int gq = lane >> 2, tq = lane & 3;
     const float rc2 = rc * rc;
     const int i = ace_list[a];
-    const int cnt = gather_ace_neighbors(pos4, nbr, n, i, nnbr[i], Ds, rc2, S.nb, S.nbj, lane);
+    const int cnt = gather_ace_neighbors<1>(pos4, nbr, n, i, nnbr[i], Ds, rc2, S.nb, S.nbj, lane);
     if (cnt < 0) {
         if (lane == 0) { atomicOr(&flags[kFlagErr], kErrAceCapacity); flags[kFlagBad] = i; }
         return;
@@ -1087,7 +1087,7 @@ __device__ __forceinline__ void force_atom(const float4* __restrict__ pos4, cons
     const float4 da0 = dsrc[lane], da1 = lane < 2 * kNLM - 32 ? dsrc[32 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
     const int i = ace_list[a];
     const float wi = wv[i];
-    const int cnt = gather_ace_neighbors(pos4, nbr, n, i, nnbr[i], Ds, rc2, S.nb, S.nbj, lane);
+    const int cnt = gather_ace_neighbors<4>(pos4, nbr, n, i, nnbr[i], Ds, rc2, S.nb, S.nbj, lane);
     if (cnt < 0) return;
     reinterpret_cast<float4*>(&S.dAT[0][0])[lane] = da0;
     if (lane < 2 * kNLM - 32) reinterpret_cast<float4*>(&S.dAT[0][0])[32 + lane] = da1;

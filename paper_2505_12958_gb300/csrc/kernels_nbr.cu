@@ -152,17 +152,6 @@ __device__ __forceinline__ void prepare_body(const double* __restrict__ x, int n
                           float* __restrict__ wout, int* __restrict__ ace_list, int* __restrict__ flags, int bid) {
     pdl_wait();
     __shared__ float sh[9];          // box origin, cell edges (orthorhombic), zone centre at time t
-    int i = bid * blockDim.x + threadIdx.x;
-    // the atom's loads are issued before the block barrier, so that they overlap the time
-    // load of thread 0
-    double r[3] = {0.0, 0.0, 0.0}, wfix = 0.0;
-    int ci = 0;
-    if (i < n) {
-#pragma unroll
-        for (int q = 0; q < 3; ++q) r[q] = x[(size_t)q * n + i];
-        ci = cell[i];
-        if (dy.reg_kind == AP_REGION_EXPLICIT) wfix = w_fixed[i];
-    }
     if (threadIdx.x == 0 && dy.reg_kind == AP_REGION_SPHERE && g.ortho) {
         const double t = *tptr;
         for (int q = 0; q < 3; ++q) {
@@ -172,11 +161,13 @@ __device__ __forceinline__ void prepare_body(const double* __restrict__ x, int n
         }
     }
     __syncthreads();
+    int i = bid * blockDim.x + threadIdx.x;
     float wf = 0.0f;
     bool need = false;                 // w > 0, decided in the precision w is given in
     if (i < n) {
+        double r[3] = {x[i], x[n + i], x[2 * n + i]};
         int cc[3];
-        cell_coords(g, ci, cc);
+        cell_coords(g, cell[i], cc);
         double o[3];
         cell_origin(g, cc, o);
         const float hx = (float)(r[0] - o[0]), hy = (float)(r[1] - o[1]), hz = (float)(r[2] - o[2]);
@@ -186,7 +177,7 @@ __device__ __forceinline__ void prepare_body(const double* __restrict__ x, int n
             u = (float)(1.0 - dy.w_const);
             need = dy.w_const > 0.0;
         } else if (dy.reg_kind == AP_REGION_EXPLICIT) {
-            const double w = wfix;
+            const double w = w_fixed[i];
             wf = (float)w;
             u = (float)(1.0 - w);
             need = w > 0.0;
