@@ -168,7 +168,8 @@ struct Ctx {
     float* uxi = nullptr;                                // u_i xi'(rho_i)
     float* w = nullptr;
     double* e_emb = nullptr;                             // xi(rho_i) + Delta xi
-    double* e_eam = nullptr;                             // E_i^EAM (FP64)
+    double* e_eam = nullptr;                             // E_i^EAM (FP64) of the force pass (the blend's -grad w term)
+    double* e_eam_acc = nullptr;                         // E_i^EAM of the compensated energy pass
     float* e_ace = nullptr;                              // E_i^ACE - c1_0
     float* ace_A = nullptr;                              // [n_ace][25][8] atomic base of the compacted atoms
     float* ace_dA = nullptr;                             // [n_ace][25][8] dE/dA
@@ -271,6 +272,8 @@ int launch_ace_force(Ctx& c, cudaStream_t s);        // pair forces and scatter
 // the load history when one is recorded)
 int launch_blend(Ctx& c, cudaStream_t s, float* out_aos, double kick_dt = 0.0, bool in_step = false);
 int launch_energy(Ctx& c, cudaStream_t s, bool virial = true);   // compensated EAM energies + energy blend (+ virial)
+int launch_eam_energy(Ctx& c, cudaStream_t s, bool virial);       // the compensated EAM energies alone
+int launch_energy_blend(Ctx& c, cudaStream_t s, bool virial);     // the energy blend alone (after the two above)
 int launch_reduce(Ctx& c, cudaStream_t s, int with_kinetic);
 int launch_kick_drift(Ctx& c, cudaStream_t s, double dt, int first_half);
 int launch_kick(Ctx& c, cudaStream_t s, double dt);

@@ -431,7 +431,10 @@ void to_soa(const double* aos, int n, std::vector<double>& soa) {
 // neighbour-list displacement test (positions change only there between evaluations of a
 // step loop), so the separate check is left out.  kick_dt > 0: the blend kernel also
 // applies the step's second half kick.
-void run_forces_pre(ap_ctx* xc, cudaStream_t s, bool after_drift) {
+// eam_energy: the caller will ask for the total energy; the compensated EAM energies are then
+// formed on the EAM branch, beside the ACE kernels (they write their own buffer, so the force
+// pass's results do not change), and only the energy blend follows the force blend
+void run_forces_pre(ap_ctx* xc, cudaStream_t s, bool after_drift, bool eam_energy = false) {
     ap::Ctx& c = xc->c;
     stage(xc, AP_STAGE_NEIGHBOR, s, [&] { return (after_drift ? 0 : ap::launch_check(c, s)) + ap::launch_rebuild(c, s); });
     stage(xc, AP_STAGE_PREPARE, s, [&] { return ap::launch_prepare(c, s); });
@@ -447,6 +450,7 @@ void run_forces_pre(ap_ctx* xc, cudaStream_t s, bool after_drift) {
         cudaStreamWaitEvent(xc->side, xc->fork_ev, 0);
         c.launches += ap::launch_eam_density(c, xc->side);
         c.launches += ap::launch_eam_force(c, xc->side);
+        if (eam_energy) c.launches += ap::launch_eam_energy(c, xc->side, false);
         cudaEventRecord(xc->join_ev, xc->side);
     }
     stage(xc, AP_STAGE_ACE_BASIS, s, [&] { return ap::launch_ace_basis(c, s); });
@@ -461,8 +465,9 @@ void run_forces_post(ap_ctx* xc, cudaStream_t s, float* out_aos, double kick_dt,
     c.energy_fresh = false;
 }
 
-void run_forces(ap_ctx* xc, cudaStream_t s, float* out_aos, bool after_drift = false, double kick_dt = 0.0) {
-    run_forces_pre(xc, s, after_drift);
+void run_forces(ap_ctx* xc, cudaStream_t s, float* out_aos, bool after_drift = false, double kick_dt = 0.0,
+                bool eam_energy = false) {
+    run_forces_pre(xc, s, after_drift, eam_energy);
     stage(xc, AP_STAGE_ACE, s, [&] { return ap::launch_ace(xc->c, s); });
     run_forces_post(xc, s, out_aos, kick_dt, after_drift);
 }
@@ -544,7 +549,7 @@ size_t ap_footprint_bytes(const ap_potential* pot, int n_atoms, double ace_fract
     const double need = 4.18879 * rl * rl * rl * 0.1;
     const size_t cap = (size_t)(need * 1.25 + 8 + 4);
     // per-atom arrays allocated by ap_init (and the host-transfer staging buffers)
-    const size_t per_atom = 16 + 3 * 8 * 3 + 3 * 4 + 16 + 4 + 4 + 8 + 8 + 4 +
+    const size_t per_atom = 16 + 3 * 8 * 3 + 3 * 4 + 16 + 4 + 4 + 8 + 8 + 8 + 4 +
                             2 * sizeof(float) * ap::kNLM * ap::kNmax + 2 * 6 * 4 + 3 * 8 + 1 + 8 +
                             4 + 4 + 4 + 4 + 8 + 3 * 8 + 3 * 4 + cap * 4;
     const size_t cells = 2 * sizeof(int) * ((size_t)n_atoms + 1);   // cell count/start (<= 1 per atom)
@@ -646,7 +651,7 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
         plan.add(&c.eam_d, 1); plan.add(&c.desc_d, 1); plan.add(&c.D, 125); plan.add(&c.Dlo, 125);
         plan.add(&c.pos_lo, N); plan.add(&c.x, 3 * N); plan.add(&c.v, 3 * N); plan.add(&c.xb, 3 * N);
         plan.add(&c.f, 3 * N); plan.add(&c.pos4, N); plan.add(&c.uxi, N); plan.add(&c.w, N);
-        plan.add(&c.e_emb, N); plan.add(&c.e_eam, N); plan.add(&c.e_ace, N);
+        plan.add(&c.e_emb, N); plan.add(&c.e_eam, N); plan.add(&c.e_eam_acc, N); plan.add(&c.e_ace, N);
         plan.add(&c.ace_A, (size_t)ap::kNLM * ap::kNmax * N); plan.add(&c.ace_dA, (size_t)ap::kNLM * ap::kNmax * N);
         plan.add(&c.vir_eam, 6 * N); plan.add(&c.vir_ace, 6 * N); plan.add(&c.acc, 3 * N); plan.add(&c.fixed, N);
         plan.add(&c.w_fixed, N); plan.add(&c.cell, N); plan.add(&c.cell_atoms, N); plan.add(&c.nnbr, N);
@@ -704,6 +709,7 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
     zero(c.vir_ace, 6 * N * sizeof(float));
     zero(c.e_ace, N * sizeof(float));
     zero(c.e_eam, N * sizeof(double));
+    zero(c.e_eam_acc, N * sizeof(double));
     zero(c.e_emb, N * sizeof(double));
     zero(c.vir_eam, 6 * N * sizeof(float));
     int one = 1;
@@ -754,8 +760,8 @@ ap_status ap_compute_forces_host(ap_ctx* xc, const double* h_pos, float* h_force
         if (!xc->host_exec) {
             e = capture_graph(xc, s, &xc->host_exec, &xc->host_kernels, [&] {
                 if (h_pos) c.launches += ap::launch_pos_in(c, s, c.pos_stage);
-                run_forces(xc, s, c.f_stage);
-                if (h_energy) c.launches += ap::launch_energy(c, s, false) + ap::launch_reduce(c, s, 0);
+                run_forces(xc, s, c.f_stage, false, 0.0, h_energy != nullptr);
+                if (h_energy) c.launches += ap::launch_energy_blend(c, s, false) + ap::launch_reduce(c, s, 0);
             });
             if (e != cudaSuccess) return graph_error(xc, e);
             xc->host_stream = s;
@@ -775,9 +781,17 @@ ap_status ap_compute_forces_host(ap_ctx* xc, const double* h_pos, float* h_force
             if (e != cudaSuccess) return cuda_check(c, e, "ap_compute_forces_host H2D");
             c.launches += ap::launch_pos_in(c, s, c.pos_stage);
         }
-        run_forces(xc, s, c.f_stage);
+        // with every stage timed the EAM passes stay on s and the energy pass follows
+        const bool branch_energy = h_energy && c.prof != 1;
+        run_forces(xc, s, c.f_stage, false, 0.0, branch_energy);
         if (h_energy) {
-            ensure_energy(xc, s, false);                    // the total energy only
+            if (branch_energy) {                            // the total energy only
+                c.launches += ap::launch_energy_blend(c, s, false);
+                c.energy_fresh = true;
+                xc->energy_virial = false;
+            } else {
+                ensure_energy(xc, s, false);
+            }
             c.launches += ap::launch_reduce(c, s, 0);
         }
     }

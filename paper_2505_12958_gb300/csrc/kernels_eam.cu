@@ -355,10 +355,10 @@ int launch_eam_energy(Ctx& c, cudaStream_t s, bool virial) {
     k_pos_lo<<<(c.n + 255) / 256, 256, 0, s>>>(c.x, c.n, c.grid, c.cell, c.pos4, c.pos_lo);
     if (virial)
         k_eam_energy<true><<<(c.n + 255) / 256, 256, 0, s>>>(c.pos4, c.pos_lo, c.nbr, c.nnbr, c.n, c.eam_d, c.D,
-                                                             c.Dlo, c.grid.ncode, c.uxi, c.e_eam, c.vir_eam);
+                                                             c.Dlo, c.grid.ncode, c.uxi, c.e_eam_acc, c.vir_eam);
     else
         k_eam_energy<false><<<(c.n + 255) / 256, 256, 0, s>>>(c.pos4, c.pos_lo, c.nbr, c.nnbr, c.n, c.eam_d, c.D,
-                                                              c.Dlo, c.grid.ncode, c.uxi, c.e_eam, c.vir_eam);
+                                                              c.Dlo, c.grid.ncode, c.uxi, c.e_eam_acc, c.vir_eam);
     return 2;
 }
 

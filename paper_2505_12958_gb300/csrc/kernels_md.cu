@@ -527,14 +527,15 @@ int launch_blend(Ctx& c, cudaStream_t s, float* out_aos, double kick_dt, bool in
     return 1;
 }
 
-int launch_eam_energy(Ctx& c, cudaStream_t s, bool virial);
+int launch_energy_blend(Ctx& c, cudaStream_t s, bool virial) {
+    k_energy_blend<<<c.nred, kRedBlock, 0, s>>>(c.x, c.n, c.grid, c.dyn, c.d_time, c.w, c.pos4, c.cell, c.e_ace,
+                                                c.e_eam_acc, c.ace_c1_0, c.vir_eam, c.vir_ace, c.e_atom, c.partials,
+                                                c.flags, virial ? 1 : 0);
+    return 1;
+}
 
 int launch_energy(Ctx& c, cudaStream_t s, bool virial) {
-    int k = launch_eam_energy(c, s, virial);
-    k_energy_blend<<<c.nred, kRedBlock, 0, s>>>(c.x, c.n, c.grid, c.dyn, c.d_time, c.w, c.pos4, c.cell, c.e_ace,
-                                                c.e_eam, c.ace_c1_0, c.vir_eam, c.vir_ace, c.e_atom, c.partials,
-                                                c.flags, virial ? 1 : 0);
-    return k + 1;
+    return launch_eam_energy(c, s, virial) + launch_energy_blend(c, s, virial);
 }
 
 int launch_reduce(Ctx& c, cudaStream_t s, int with_kinetic) {

@@ -89,6 +89,21 @@ def test_w_slab_with_indenter_and_fixed_layers(apl, orc):
     assert ref["load"] > 0 and ref["n_ace"] > 50
 
 
+def test_compressed_cell_with_lists_longer_than_four_rounds(apl, orc):
+    """A W cell compressed to 0.8 of its lattice constant: up to 146 entries in an atom's
+    list (the ACE gathers run past their first 128-entry round) and about 62 neighbours
+    inside the ACE cutoff.  Pure ACE against the oracle (forces up to 0.8 eV/A; with EAM the
+    compressed cell's forces reach 50 eV/A, beyond what FP32 pair sums hold to 1e-4)."""
+    from scipy.spatial import cKDTree
+    c = synth.configs.w_bulk(ncell=6)
+    s = 0.8
+    c = dict(c, x=c["x"] * s, box=dict(c["box"], h=np.asarray(c["box"]["h"], dtype=np.float64) * s))
+    L = 6 * 3.165 * s
+    t = cKDTree(c["x"] % L, boxsize=L)
+    assert (t.query_ball_point(c["x"] % L, r=6.5, return_length=True) - 1).max() > 128
+    compare(apl, orc, c, region={"kind": "const", "w": 1.0}, rel_ace=True)
+
+
 def test_small_triclinic_cells_with_many_images(apl, orc):
     for seed in (1, 2):
         c = synth.configs.strained_w_cell(2, seed=seed, vacancy=0.0)     # 16 atoms, box ~ 6.3 A < r_list
