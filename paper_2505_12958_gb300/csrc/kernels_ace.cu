@@ -11,7 +11,9 @@
 //                      c1 + c2 / (2 sqrt(phi2)): the Gaunt products of the first two factors
 //                      on FP32 lanes (one (n1, n2) pair per lane, compile-time coupling
 //                      pattern), their contractions with the coefficient matrices on tensor
-//                      cores (mma.sync, 3xTF32).  Writes dE/dA and E_i^ACE.
+//                      cores (mma.sync, 3xTF32; the l1 = l2 triples over the 36 pairs
+//                      n1 <= n2), and the one- and two-factor functions through tensor-core
+//                      Gram tiles A_l A_l^T and their adjoint.  Writes dE/dA and E_i^ACE.
 //   k_ace_force        f_ij = dE_i/dr_ij = (1/nref) sum dE/dA_nlm grad(g_n Y_lm), weighted by
 //                      w_i, added to atom j (minus) and atom i (plus) through 64-bit fixed-point
 //                      atomics (2^-40 eV/A resolution), whose integer sums do not depend on order.
@@ -535,11 +537,16 @@ __global__ void __launch_bounds__(256) k_ace_basis(const float4* __restrict__ po
 // (density, n3) = 16, N = m3.  P and Q pass between the lanes (one (n1, n2) pair each) and
 // the fragments through a per-warp staging block of rows m3, columns q.
 //
+// For the five l1 = l2 triples P and the coefficients are symmetric in (n1, n2): their
+// coefficient rows are packed to the 36 pairs n1 <= n2 (R over K = 40, Q over three row
+// tiles), and only the first-factor gradient is formed, taken twice.
+//
 // The five (0, l, l) triples have G = delta_{m2 m3} / sqrt(4 pi): their functions are
 // A[n1, 00] times a two-factor product, so they join the two-factor pass with per-atom
-// coefficients c2 + sum_n1 C3[n1, (n2, n3)] A[n1, 00] G (and a gradient for A[n1, 00]).
-// The other nine triples run on tensor cores.  One warp per atom, no block barriers in the
-// atom loop.
+// coefficients c2 + sum_n1 C3[n1, (n2, n3)] A[n1, 00] G (and a gradient for A[n1, 00]).  The
+// two-factor products are Gram matrices A_l A_l^T, one 3xTF32 tile per l, and so is their
+// adjoint.  The other nine triples run through R and Q.  One warp per atom, no block barriers
+// in the atom loop.
 // ---------------------------------------------------------------------------------
 constexpr int kTcWarps = 16;
 constexpr int kStRow = 68;                     // staging row stride: 8 rows fall on distinct bank quads
