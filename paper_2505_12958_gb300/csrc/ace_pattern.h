@@ -28,6 +28,16 @@ __host__ __device__ constexpr int tri_l(int t, int k) {
     return L[t][k];
 }
 
+// The order in which the contraction kernel takes the factors of triple t: the real Gaunt
+// coefficient is symmetric in its three (l, m) pairs, so a triple's function does not depend
+// on the order of its factors.  The two triples with l1 < l2 = l3, (2, 3, 3) and (2, 4, 4), are
+// taken as (3, 3, 2) and (4, 4, 2): their equal pair comes first, where the kernel packs the
+// symmetric (n1, n2) pairs, and their third factor has 5 columns instead of 7 or 9.
+__host__ __device__ constexpr int kern_perm(int t, int k) {
+    return (t == 10 || t == 11) ? (k + 1) % 3 : k;
+}
+__host__ __device__ constexpr int ktri_l(int t, int k) { return tri_l(t, kern_perm(t, k)); }
+
 __host__ __device__ constexpr int iabs_c(int a) { return a < 0 ? -a : a; }
 
 __host__ __device__ constexpr bool gaunt_allowed(int m1, int m2, int m3) {
@@ -60,6 +70,7 @@ __host__ __device__ constexpr int pat_entry(int l1, int l2, int l3, int e, int w
     return 0;
 }
 
+// (the count does not depend on the order of the factors)
 __host__ __device__ constexpr int tri_count(int t) { return pat_count(tri_l(t, 0), tri_l(t, 1), tri_l(t, 2)); }
 
 __host__ __device__ constexpr int tri_offset(int t) {

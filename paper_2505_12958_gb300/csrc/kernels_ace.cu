@@ -158,7 +158,7 @@ __device__ __forceinline__ void force_terms(float x, float y, float z, float rin
 // ---------------------------------------------------------------------------------
 template <int T>
 struct Tri {
-    static constexpr int L1 = tri_l(T, 0), L2 = tri_l(T, 1), L3 = tri_l(T, 2);
+    static constexpr int L1 = ktri_l(T, 0), L2 = ktri_l(T, 1), L3 = ktri_l(T, 2);   // kernel order
     static constexpr int W1 = 2 * L1 + 1, W2 = 2 * L2 + 1, W3 = 2 * L3 + 1;
     static constexpr int N = tri_count(T), OFF = tri_offset(T);
     static constexpr int B1 = lblk(L1), B2 = lblk(L2), B3 = lblk(L3);
@@ -929,9 +929,9 @@ __device__ __forceinline__ bool tc_contract_atom(const AceTc& C, TcWarpSmem& S, 
     const int g = lane >> 2, t = lane & 3;
     float p1 = 0.0f, p2 = 0.0f;
     // the tensor-core triples, grouped by l3
-    tc_forward_group<2>(C, S, lane, p1, p2, std::integer_sequence<int, 5, 8>{});
-    tc_forward_group<3>(C, S, lane, p1, p2, std::integer_sequence<int, 6, 10>{});
-    tc_forward_group<4>(C, S, lane, p1, p2, std::integer_sequence<int, 7, 9, 11, 12, 13>{});
+    tc_forward_group<2>(C, S, lane, p1, p2, std::integer_sequence<int, 5, 8, 10, 11>{});
+    tc_forward_group<3>(C, S, lane, p1, p2, std::integer_sequence<int, 6>{});
+    tc_forward_group<4>(C, S, lane, p1, p2, std::integer_sequence<int, 7, 9, 12, 13>{});
     __syncwarp();                                      // the epilogues' dA and R2 are visible
     // one- and two-factor functions
     float a00[kNmax];

@@ -207,7 +207,8 @@ double gaunt_real_racah(int l1, int m1, int l2, int m2, int l3, int m3) {
 int gaunt_values(float* out, std::string& err) {
     int e = 0;
     for (int t = 0; t < kNT; ++t) {
-        int l1 = tri_l(t, 0), l2 = tri_l(t, 1), l3 = tri_l(t, 2);
+        // in the kernel's order of the factors (the pattern the kernel compiles)
+        int l1 = ktri_l(t, 0), l2 = ktri_l(t, 1), l3 = ktri_l(t, 2);
         for (int m1 = -l1; m1 <= l1; ++m1)
             for (int m2 = -l2; m2 <= l2; ++m2)
                 for (int m3 = -l3; m3 <= l3; ++m3) {
@@ -408,7 +409,17 @@ void build_ace_tc(const AceDev& in, AceTc& out) {
         }
         for (int u = 0; u < kNT3; ++u) {
             const int t = kTcTriple0 + u;
-            const bool sym = tri_l(t, 0) == tri_l(t, 1);
+            const bool sym = ktri_l(t, 0) == ktri_l(t, 1);
+            // coefficient of the kernel's factors (n1, n2, n3); the factor order of the basis
+            // is (tri_l(t, 0), tri_l(t, 1), tri_l(t, 2)) and kernel factor k is basis factor
+            // kern_perm(t, k)
+            auto coef = [&](int n1, int n2, int n3) {
+                int nb[3];
+                nb[kern_perm(t, 0)] = n1;
+                nb[kern_perm(t, 1)] = n2;
+                nb[kern_perm(t, 2)] = n3;
+                return in.c3[d][t][nb[2]][nb[0] * 8 + nb[1]];
+            };
             for (int n3 = 0; n3 < kNmax; ++n3)
                 for (int n1 = 0; n1 < kNmax; ++n1)
                     for (int n2 = 0; n2 < kNmax; ++n2) {
@@ -417,8 +428,8 @@ void build_ace_tc(const AceDev& in, AceTc& out) {
                         // l1 = l2: the packed row of the pair n1 <= n2 holds the mean of both
                         // orders' coefficients (the kernel doubles the product of n1 < n2)
                         const int q = sym ? sym_pair(n1, n2) : n1 * 8 + n2;
-                        float v = in.c3[d][t][n3][n1 * 8 + n2];
-                        if (sym && n1 != n2) v = 0.5f * (in.c3[d][t][n3][n1 * 8 + n2] + in.c3[d][t][n3][n2 * 8 + n1]);
+                        float v = coef(n1, n2, n3);
+                        if (sym && n1 != n2) v = 0.5f * (coef(n1, n2, n3) + coef(n2, n1, n3));
                         const float hi = tf32_rna(v), lo = tf32_rna(v - hi);
                         const int pos = n3 ^ (4 * ((q >> 2) & 1));
                         out.c3[0][d][u][q][pos] = hi;

@@ -19,7 +19,7 @@ formed once.
   per neighbour inside the cutoff: A = g Y (400), basis values (~100), pair force
   (25 x (32 + 10) + radial 40, ~1090).
 """
-from .csrc_constants import NNZ, TRIPLES
+from .csrc_constants import KERNEL_TRIPLES, NNZ, TRIPLES
 
 PER_NEIGHBOR_FLOPS = 400 + 100 + 25 * 42 + 40
 
@@ -66,7 +66,9 @@ def ace_tc_contract_work():
     """Work per compacted atom of the tensor-core contraction kernel (FMA = 2 FLOPs), counted
     over structurally nonzero index combinations as above:
 
-      fp32:   the arithmetic left on the FP32 lanes: the Gaunt products P of the nine triples
+      fp32:   the arithmetic left on the FP32 lanes, with each triple's factors in the
+              kernel's order ((2, 3, 3) and (2, 4, 4) taken as (3, 3, 2) and (4, 4, 2)): the
+              Gaunt products P of the nine triples
               with l1 > 0 (per active (n1, n2) pair g12 + 2 nnz; 36 pairs when l1 = l2, else
               64) and their factor gradients (per ordered pair: 2 nnz + 3 g12 for d1 and d2;
               for l1 = l2 only d1, 2 nnz + g12, taken twice); for the two-factor terms with
@@ -83,7 +85,7 @@ def ace_tc_contract_work():
               one adjoint tile (two K steps or two column tiles at l = 4)."""
     mma = 2 * 16 * 8 * 8
     fp32 = tensor = executed = 0
-    for (l1, l2, l3), nnz in zip(TRIPLES, NNZ):
+    for (l1, l2, l3), nnz in zip(KERNEL_TRIPLES, NNZ):
         if l1 == 0:
             continue
         g12 = len({(a, b) for a, b, _ in _pattern(l1, l2, l3)})

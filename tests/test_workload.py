@@ -5,7 +5,7 @@ import numpy as np
 
 import synth
 from paper_2505_12958_gb300 import workload
-from paper_2505_12958_gb300.csrc_constants import NNZ, TRIPLES
+from paper_2505_12958_gb300.csrc_constants import KERNEL_TRIPLES, NNZ, TRIPLES
 
 
 def test_counted_combinations_are_the_three_factor_functions():
@@ -34,16 +34,20 @@ def test_pattern_sizes_and_total():
 
 def test_tensor_core_kernel_work_split():
     """The tensor-core kernel's work: the coefficient contractions over the active (n1, n2)
-    pairs of the nine triples with l1 > 0 (36 pairs when l1 = l2), the two-factor Gram
-    products and their adjoint, and the 3xTF32 m16n8k8 tiles that run them (the packed
-    l1 = l2 triples: 5 K steps of R and 3 row tiles of Q)."""
+    pairs of the nine triples with l1 > 0 (36 pairs when l1 = l2, in the kernel's factor
+    order), the two-factor Gram products and their adjoint, and the 3xTF32 m16n8k8 tiles that
+    run them (the packed l1 = l2 triples: 5 K steps of R and 3 row tiles of Q)."""
+    # the kernel's order permutes the factors of (2, 3, 3) and (2, 4, 4) only
+    for t, k in zip(TRIPLES, KERNEL_TRIPLES):
+        assert sorted(t) == sorted(k)
+    assert [k for t, k in zip(TRIPLES, KERNEL_TRIPLES) if t != k] == [(3, 3, 2), (4, 4, 2)]
     w = workload.ace_tc_contract_work()
-    tc = [(t, 36 if t[0] == t[1] else 64) for t in TRIPLES if t[0] > 0]
-    assert len(tc) == 9
+    tc = [(t, 36 if t[0] == t[1] else 64) for t in KERNEL_TRIPLES if min(t) > 0]
+    assert len(tc) == 9 and sum(1 for t, p in tc if p == 36) == 7
     gram = sum(2 * 36 * (2 * l + 1) + 2 * 64 * (2 * l + 1) for l in range(5))
     assert w["tensor"] == sum(2 * 2 * 16 * p * (2 * t[2] + 1) for t, p in tc) + gram
     tile = 2 * 16 * 8 * 8
     r_tiles = sum((5 if t[0] == t[1] else 8) * (2 if t[2] == 4 else 1) for t, _ in tc)
     q_tiles = sum(2 * (3 if t[0] == t[1] else 4) * (2 if t[2] == 4 else 1) for t, _ in tc)
     assert w["tensor_executed"] == 3 * tile * (r_tiles + q_tiles + 2 * 6)
-    assert w == {"fp32": 149284, "tensor": 221320, "tensor_executed": 1204224}
+    assert w == {"fp32": 133492, "tensor": 178824, "tensor_executed": 1044480}
