@@ -32,9 +32,11 @@ __host__ __device__ constexpr int tri_l(int t, int k) {
 // coefficient is symmetric in its three (l, m) pairs, so a triple's function does not depend
 // on the order of its factors.  The two triples with l1 < l2 = l3, (2, 3, 3) and (2, 4, 4), are
 // taken as (3, 3, 2) and (4, 4, 2): their equal pair comes first, where the kernel packs the
-// symmetric (n1, n2) pairs, and their third factor has 5 columns instead of 7 or 9.
+// symmetric (n1, n2) pairs, and their third factor has 5 columns instead of 7 or 9.  The two
+// with l1 = 1 < l2 < l3, (1, 2, 3) and (1, 3, 4), are taken as (2, 3, 1) and (3, 4, 1): their
+// third factor has 3 columns instead of 7 or 9.
 __host__ __device__ constexpr int kern_perm(int t, int k) {
-    return (t == 10 || t == 11) ? (k + 1) % 3 : k;
+    return (t == 6 || t == 7 || t == 10 || t == 11) ? (k + 1) % 3 : k;
 }
 __host__ __device__ constexpr int ktri_l(int t, int k) { return tri_l(t, kern_perm(t, k)); }
 

@@ -929,9 +929,9 @@ __device__ __forceinline__ bool tc_contract_atom(const AceTc& C, TcWarpSmem& S, 
     const int g = lane >> 2, t = lane & 3;
     float p1 = 0.0f, p2 = 0.0f;
     // the tensor-core triples, grouped by l3
+    tc_forward_group<1>(C, S, lane, p1, p2, std::integer_sequence<int, 6, 7>{});
     tc_forward_group<2>(C, S, lane, p1, p2, std::integer_sequence<int, 5, 8, 10, 11>{});
-    tc_forward_group<3>(C, S, lane, p1, p2, std::integer_sequence<int, 6>{});
-    tc_forward_group<4>(C, S, lane, p1, p2, std::integer_sequence<int, 7, 9, 12, 13>{});
+    tc_forward_group<4>(C, S, lane, p1, p2, std::integer_sequence<int, 9, 12, 13>{});
     __syncwarp();                                      // the epilogues' dA and R2 are visible
     // one- and two-factor functions
     float a00[kNmax];
@@ -971,10 +971,11 @@ __device__ __forceinline__ bool tc_contract_atom(const AceTc& C, TcWarpSmem& S, 
         for (int k = 1; k < kNmax; ++k) gk = lane == k ? g00[k] : gk;
         S.dA[lane * kApad] += gk + fmaf(s, C.c1[1][lane], C.c1[0][lane]);
     }
-    for (int e = lane; e < kNmax * 21; e += 32) {
-        // lm = 4 .. 24: l3 = 2, 3, 4 of the tensor-core triples
-        const int n3 = e / 21, lm = 4 + (e - n3 * 21);
-        const int l = lm < 9 ? 2 : (lm < 16 ? 3 : 4);
+    for (int e = lane; e < kNmax * 17; e += 32) {
+        // lm = 1 .. 8 and 16 .. 24: the third factors (l = 1, 2 and 4 in the kernel's order)
+        // of the tensor-core triples
+        const int n3 = e / 17, k = e - n3 * 17, lm = k < 8 ? 1 + k : 8 + k;
+        const int l = lm < 4 ? 1 : (lm < 9 ? 2 : 4);
         S.dA[n3 * kApad + lblk(l) + (lm - l * l)] += s * S.R2[n3][lm];
     }
     __syncwarp();

@@ -20,5 +20,6 @@ TRIPLES = [(0, 0, 0), (0, 1, 1), (0, 2, 2), (0, 3, 3), (0, 4, 4), (1, 1, 2), (1,
            (2, 2, 2), (2, 2, 4), (2, 3, 3), (2, 4, 4), (3, 3, 4), (4, 4, 4)]
 NNZ = [_pattern_count(*t) for t in TRIPLES]
 
-# the contraction kernel's factor order: (2, 3, 3) and (2, 4, 4) as (3, 3, 2) and (4, 4, 2)
-KERNEL_TRIPLES = [(t[1], t[2], t[0]) if k in (10, 11) else t for k, t in enumerate(TRIPLES)]
+# the contraction kernel's factor order: (1, 2, 3), (1, 3, 4), (2, 3, 3) and (2, 4, 4) as
+# (2, 3, 1), (3, 4, 1), (3, 3, 2) and (4, 4, 2)
+KERNEL_TRIPLES = [(t[1], t[2], t[0]) if k in (6, 7, 10, 11) else t for k, t in enumerate(TRIPLES)]
