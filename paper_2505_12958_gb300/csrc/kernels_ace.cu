@@ -667,7 +667,11 @@ __device__ __forceinline__ void tc_forward_triple(const AceTc& C, TcWarpSmem& S,
 
 // the tensor-core triples of one l3: chained R accumulators, then phi and the third-factor
 // gradient (thread (g, t) holds R_1[n3 = g][m3 = 2t, 2t + 1] in RA[0..1] and R_2 in RA[2..3])
-template <int L, int... T>
+// GW: weight of the third-factor gradient (3 for the triples whose three factors have equal
+// l, whose coefficients are fully symmetric: their gradient is the same for all three factors,
+// so the first- and second-factor passes are left out); ACC: another group with the same l3
+// already wrote its second-density rows R2, which this one adds to
+template <int L, int GW, bool ACC, int... T>
 __device__ __forceinline__ void tc_forward_group(const AceTc& C, TcWarpSmem& S, int lane, float& p1, float& p2,
                                                  std::integer_sequence<int, T...>) {
     float RA0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, RA1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -683,8 +687,9 @@ __device__ __forceinline__ void tc_forward_group(const AceTc& C, TcWarpSmem& S, 
             const float a = S.A[gq * kApad + lblk(L) + m];
             p1 = fmaf(r1, a, p1);
             p2 = fmaf(r2, a, p2);
-            S.dA[gq * kApad + lblk(L) + m] += r1;
-            S.R2[gq][L * L + m] = r2;
+            S.dA[gq * kApad + lblk(L) + m] = fmaf((float)GW, r1, S.dA[gq * kApad + lblk(L) + m]);
+            if constexpr (ACC) S.R2[gq][L * L + m] = fmaf((float)GW, r2, S.R2[gq][L * L + m]);
+            else S.R2[gq][L * L + m] = (float)GW * r2;
         }
     }
     if constexpr (W > 8) {
@@ -693,8 +698,9 @@ __device__ __forceinline__ void tc_forward_group(const AceTc& C, TcWarpSmem& S, 
             const float a = S.A[gq * kApad + lblk(L) + 8];
             p1 = fmaf(r1, a, p1);
             p2 = fmaf(r2, a, p2);
-            S.dA[gq * kApad + lblk(L) + 8] += r1;
-            S.R2[gq][L * L + 8] = r2;
+            S.dA[gq * kApad + lblk(L) + 8] = fmaf((float)GW, r1, S.dA[gq * kApad + lblk(L) + 8]);
+            if constexpr (ACC) S.R2[gq][L * L + 8] = fmaf((float)GW, r2, S.R2[gq][L * L + 8]);
+            else S.R2[gq][L * L + 8] = (float)GW * r2;
         }
     }
 }
@@ -929,9 +935,11 @@ __device__ __forceinline__ bool tc_contract_atom(const AceTc& C, TcWarpSmem& S, 
     const int g = lane >> 2, t = lane & 3;
     float p1 = 0.0f, p2 = 0.0f;
     // the tensor-core triples, grouped by l3
-    tc_forward_group<1>(C, S, lane, p1, p2, std::integer_sequence<int, 6, 7>{});
-    tc_forward_group<2>(C, S, lane, p1, p2, std::integer_sequence<int, 5, 8, 10, 11>{});
-    tc_forward_group<4>(C, S, lane, p1, p2, std::integer_sequence<int, 9, 12, 13>{});
+    tc_forward_group<1, 1, false>(C, S, lane, p1, p2, std::integer_sequence<int, 6, 7>{});
+    tc_forward_group<2, 1, false>(C, S, lane, p1, p2, std::integer_sequence<int, 5, 10, 11>{});
+    tc_forward_group<2, 3, true>(C, S, lane, p1, p2, std::integer_sequence<int, 8>{});      // (2, 2, 2)
+    tc_forward_group<4, 1, false>(C, S, lane, p1, p2, std::integer_sequence<int, 9, 12>{});
+    tc_forward_group<4, 3, true>(C, S, lane, p1, p2, std::integer_sequence<int, 13>{});     // (4, 4, 4)
     __syncwarp();                                      // the epilogues' dA and R2 are visible
     // one- and two-factor functions
     float a00[kNmax];
@@ -979,7 +987,9 @@ __device__ __forceinline__ bool tc_contract_atom(const AceTc& C, TcWarpSmem& S, 
         S.dA[n3 * kApad + lblk(l) + (lm - l * l)] += s * S.R2[n3][lm];
     }
     __syncwarp();
-    tc_adjoint_all(C, S, s, lane, std::integer_sequence<int, 5, 6, 7, 8, 9, 10, 11, 12, 13>{});
+    // (2, 2, 2) and (4, 4, 4) have no first- and second-factor pass (their gradient is the
+    // third-factor one taken three times)
+    tc_adjoint_all(C, S, s, lane, std::integer_sequence<int, 5, 6, 7, 9, 10, 11, 12>{});
     e_out = p1 + sq;
     return ok;
 }

@@ -410,6 +410,7 @@ void build_ace_tc(const AceDev& in, AceTc& out) {
         for (int u = 0; u < kNT3; ++u) {
             const int t = kTcTriple0 + u;
             const bool sym = ktri_l(t, 0) == ktri_l(t, 1);
+            const bool sym3 = sym && ktri_l(t, 1) == ktri_l(t, 2);
             // coefficient of the kernel's factors (n1, n2, n3); the factor order of the basis
             // is (tri_l(t, 0), tri_l(t, 1), tri_l(t, 2)) and kernel factor k is basis factor
             // kern_perm(t, k)
@@ -429,7 +430,19 @@ void build_ace_tc(const AceDev& in, AceTc& out) {
                         // orders' coefficients (the kernel doubles the product of n1 < n2)
                         const int q = sym ? sym_pair(n1, n2) : n1 * 8 + n2;
                         float v = coef(n1, n2, n3);
-                        if (sym && n1 != n2) v = 0.5f * (coef(n1, n2, n3) + coef(n2, n1, n3));
+                        if (sym3) {
+                            // all three factors have equal l: the coefficient of the sorted
+                            // (n1, n2, n3) spread evenly over its distinct orderings, so that the
+                            // coefficients are symmetric in all three indices
+                            int a = n1, b = n2, c = n3;
+                            if (a > b) std::swap(a, b);
+                            if (b > c) std::swap(b, c);
+                            if (a > b) std::swap(a, b);
+                            const int mult = (a == b && b == c) ? 1 : (a == b || b == c) ? 3 : 6;
+                            v = coef(a, b, c) / (float)mult;
+                        } else if (sym && n1 != n2) {
+                            v = 0.5f * (coef(n1, n2, n3) + coef(n2, n1, n3));
+                        }
                         const float hi = tf32_rna(v), lo = tf32_rna(v - hi);
                         const int pos = n3 ^ (4 * ((q >> 2) & 1));
                         out.c3[0][d][u][q][pos] = hi;

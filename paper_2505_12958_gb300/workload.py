@@ -71,17 +71,19 @@ def ace_tc_contract_work():
               Gaunt products P of the nine triples
               with l1 > 0 (per active (n1, n2) pair g12 + 2 nnz; 36 pairs when l1 = l2, else
               64) and their factor gradients (per ordered pair: 2 nnz + 3 g12 for d1 and d2;
-              for l1 = l2 only d1, 2 nnz + g12, taken twice); for the two-factor terms with
+              for l1 = l2 only d1, 2 nnz + g12, taken twice; none for l1 = l2 = l3, whose
+              gradient is three times the third-factor one from R); for the two-factor terms with
               the five (0, l, l) triples folded in, per l and nonzero pair (36): the folded
               coefficient, phi and the A[n1, 00] gradient of both densities (68), and the
               adjoint coefficient (2); the A[n1, 00] gradient's combination and warp sum; the
               epilogue per l3 (phi and the third-factor gradient); the one-factor terms.
       tensor: the coefficient contractions R = C^T P and Q = C [A; sA] over the active pairs
-              (2 x 16 x pairs x W3 FLOPs each), and the two-factor Gram products
+              (2 x 16 x pairs x W3 FLOPs each; no Q for l1 = l2 = l3), and the two-factor Gram products
               mm_l = A_l A_l^T (36 pairs x W_l) and their adjoint (CT + CT^T) A_l (64 x W_l).
       tensor_executed: what the mma.sync m16n8k8 tiles execute (2048 FLOPs each; 3xTF32 =
               three per product): R over 8 K steps (5 for the packed l1 = l2 triples) and Q
-              over 4 row tiles (3 packed), two column tiles where W3 = 9; per l one Gram and
+              over 4 row tiles (3 packed; none for l1 = l2 = l3), two column tiles where
+              W3 = 9; per l one Gram and
               one adjoint tile (two K steps or two column tiles at l = 4)."""
     mma = 2 * 16 * 8 * 8
     fp32 = tensor = executed = 0
@@ -91,13 +93,16 @@ def ace_tc_contract_work():
         g12 = len({(a, b) for a, b, _ in _pattern(l1, l2, l3)})
         w3 = 2 * l3 + 1
         sym = l1 == l2
+        sym3 = sym and l2 == l3                                  # the gradient is 3 x the third-factor one
         pairs = 36 if sym else 64
         nt = (w3 + 7) // 8
         fp32 += pairs * (g12 + 2 * nnz)
-        fp32 += 64 * (2 * nnz + g12) if sym else 64 * (2 * nnz + 3 * g12)
-        tensor += 2 * (2 * 16 * pairs * w3)
+        if not sym3:
+            fp32 += 64 * (2 * nnz + g12) if sym else 64 * (2 * nnz + 3 * g12)
+        tensor += (1 if sym3 else 2) * (2 * 16 * pairs * w3)
         executed += 3 * mma * nt * (5 if sym else 8)            # R: K steps x column tiles
-        executed += 3 * mma * nt * 2 * (3 if sym else 4)        # Q: row tiles x 2 densities
+        if not sym3:
+            executed += 3 * mma * nt * 2 * (3 if sym else 4)    # Q: row tiles x 2 densities
     for l in range(5):
         w = 2 * l + 1
         fp32 += 36 * (68 + 2)

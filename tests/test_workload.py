@@ -45,9 +45,12 @@ def test_tensor_core_kernel_work_split():
     tc = [(t, 36 if t[0] == t[1] else 64) for t in KERNEL_TRIPLES if min(t) > 0]
     assert len(tc) == 9 and sum(1 for t, p in tc if p == 36) == 7
     gram = sum(2 * 36 * (2 * l + 1) + 2 * 64 * (2 * l + 1) for l in range(5))
-    assert w["tensor"] == sum(2 * 2 * 16 * p * (2 * t[2] + 1) for t, p in tc) + gram
+    # (2, 2, 2) and (4, 4, 4): R only (their gradient is three times the third-factor one)
+    sym3 = [t for t, _ in tc if t[0] == t[1] == t[2]]
+    assert sym3 == [(2, 2, 2), (4, 4, 4)]
+    assert w["tensor"] == sum((1 if t in sym3 else 2) * 2 * 16 * p * (2 * t[2] + 1) for t, p in tc) + gram
     tile = 2 * 16 * 8 * 8
     r_tiles = sum((5 if t[0] == t[1] else 8) * (2 if t[2] == 4 else 1) for t, _ in tc)
-    q_tiles = sum(2 * (3 if t[0] == t[1] else 4) * (2 if t[2] == 4 else 1) for t, _ in tc)
+    q_tiles = sum(2 * (3 if t[0] == t[1] else 4) * (2 if t[2] == 4 else 1) for t, _ in tc if t not in sym3)
     assert w["tensor_executed"] == 3 * tile * (r_tiles + q_tiles + 2 * 6)
-    assert w == {"fp32": 137588, "tensor": 137864, "tensor_executed": 946176}
+    assert w == {"fp32": 115572, "tensor": 121736, "tensor_executed": 835584}
