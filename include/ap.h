@@ -363,7 +363,8 @@ ap_status ap_probe_fp32_peak(int iters, double* tflops, double* ms_out);
  * accumulators, ~1.6 MB) is one file-scope device array that every GPU loading the library
  * holds until the process exits.  The first call on a device looks up its address and
  * uploads constant tables, and a call whose potential differs from the previous call's on
- * that device uploads its coefficient tables; make those calls before any stream capture.
+ * that device uploads its coefficient tables; make those calls before any stream capture
+ * (while `stream` is capturing they return AP_ERR_STATE and issue nothing).
  * Every call shares the array and clears the accumulators it uses before its kernels run;
  * calls that overlap on the GPU (other streams, other threads) race on it.  Asynchronous on
  * `stream`; errors of the launch are returned, a domain error shows as a NaN energy. */

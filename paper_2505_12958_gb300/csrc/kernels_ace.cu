@@ -1547,6 +1547,19 @@ extern "C" ap_status ap_ace_forces_noalloc(const ap_potential* pot, int n_atoms,
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> g(g_noalloc_mu);
     NoallocDevice& D = g_noalloc_dev[dev];
+    const unsigned long long key = potential_key(*pot);
+    if (!D.scratch || !D.tables || D.key != key) {
+        // the set-up and the table upload are synchronous or read pageable host memory, which
+        // a stream capture would record or reject: refuse them while `stream` is capturing
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+            (void)cudaGetLastError();
+            cs = cudaStreamCaptureStatusActive;
+        }
+        if (cs != cudaStreamCaptureStatusNone)
+            return noalloc_fail(AP_ERR_STATE, "ap_ace_forces_noalloc: the first call on a device and the first call "
+                                              "with a new potential upload tables and cannot run under stream capture");
+    }
     if (!D.scratch) {
         // once per device, with that device current (the first call on a device does this)
         void* p = nullptr;
@@ -1565,7 +1578,6 @@ extern "C" ap_status ap_ace_forces_noalloc(const ap_potential* pot, int n_atoms,
     cudaError_t e = cudaSuccess;
     // the coefficient tables are built and uploaded when the potential differs from the one
     // whose tables the array holds (the first call on a device, or a new potential)
-    const unsigned long long key = potential_key(*pot);
     if (!D.tables || D.key != key) {
         std::string err;
         if (build_ace_tables(*pot, g_noalloc_dev_tables, err)) return noalloc_fail(AP_ERR_ARG, err);

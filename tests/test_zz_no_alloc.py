@@ -137,3 +137,40 @@ def test_noalloc_reports_why_it_refused():
                                            None, C.c_void_p(d.data_ptr()), C.c_void_p(d.data_ptr()), None)
     assert st == _capi.AP_ERR_ARG
     assert b"65536" in _capi.lib().ap_last_error(None)
+
+
+def test_noalloc_refuses_table_upload_under_capture():
+    """A call that would upload tables (a potential this device has not seen) while its
+    stream is being captured returns AP_ERR_STATE and issues nothing; the same call outside
+    the capture then succeeds."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("needs a CUDA device")
+    import paper_2505_12958_gb300 as ap
+    from paper_2505_12958_gb300 import _capi
+    ap.build()
+    c = synth.configs.w_bulk(ncell=4)                # 128 atoms, 12.7 A box
+    n = len(c["x"])
+    ace = dict(c["ace"])
+    ace["c1"] = np.asarray(ace["c1"], dtype=np.float64) * 1.03125      # a potential no other call used
+    pot, keep = ap.potential_struct(c["eam"], ace, c["mass"])
+    idx, vec = _neighbor_lists(c["x"], 4 * 3.165, c["ace"]["rc"], 96)
+    d_idx = torch.tensor(idx, device="cuda")
+    d_vec = torch.tensor(vec, device="cuda")
+    d_f = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+    d_e = torch.zeros((n,), dtype=torch.float64, device="cuda")
+    args = (n, 96, C.c_void_p(d_idx.data_ptr()), C.c_void_p(d_vec.data_ptr()), None, C.c_void_p(d_f.data_ptr()),
+            C.c_void_p(d_e.data_ptr()))
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        g.capture_begin()
+        st = _capi.lib().ap_ace_forces_noalloc(C.byref(pot), *args, C.c_void_p(s.cuda_stream))
+        g.capture_end()
+    assert st == _capi.AP_ERR_STATE
+    assert b"capture" in _capi.lib().ap_last_error(None)
+    st = _capi.lib().ap_ace_forces_noalloc(C.byref(pot), *args, None)
+    assert st == 0
+    torch.cuda.synchronize()
+    assert np.isfinite(d_e.cpu().numpy()).all()
