@@ -21,9 +21,11 @@
  * copies asynchronous).  A cuda stream argument of NULL means the stream given to
  * ap_init.  Every call returns an ap_status; nothing aborts, prints, or traps on the
  * device.  Device-side errors (domain, capacity) are sticky and reported by the next
- * synchronising call (ap_energy, ap_check).  Only ap_init, ap_energy, ap_check,
- * ap_get_state, ap_get_forces, ap_compute_forces_host and ap_destroy synchronise.
- * A context is not thread-safe; distinct contexts are independent.
+ * synchronising call (ap_energy, ap_check).  Only ap_init (with counted list sizing),
+ * ap_energy, ap_check, ap_get_state, ap_get_forces, ap_compute_forces_host and ap_destroy
+ * synchronise.  A context is not thread-safe; distinct contexts share no device state.
+ * The library is exercised from one host thread: calls on distinct contexts from several
+ * threads at once are not supported.
  */
 #ifndef AP_H
 #define AP_H
@@ -96,7 +98,16 @@ typedef struct {
 
     double mass_amu;             /* one species per context                         */
     double skin;                 /* neighbour-list skin (Angstrom), e.g. 1.0         */
+    int list_sizing;             /* neighbour slots per atom: AP_LIST_COUNTED (0) from a
+                                    counting pass over the first binning, which makes
+                                    ap_init synchronise once; AP_LIST_BOUND (1) from the
+                                    bound 0.1 atoms / A^3 inside the list sphere (no
+                                    synchronisation; a denser structure reports
+                                    AP_ERR_CAPACITY at its first check, which grows the
+                                    list, and the next evaluation is complete)      */
 } ap_potential;
+
+enum { AP_LIST_COUNTED = 0, AP_LIST_BOUND = 1 };
 
 /* Box: edge vectors as rows of h (triclinic allowed), lower corner at origin.  In a
  * non-periodic direction the box only sizes the cell grid; atoms may leave it. */
@@ -154,7 +165,8 @@ typedef struct {
  * pos (n x 3), vel (n x 3 or NULL = 0) and fixed (n bytes, nonzero = frozen, or NULL),
  * builds the tables, allocates device memory, and evaluates nothing yet.  n >= 1.
  * Errors: AP_ERR_ARG (bad parameter, box thinner than half the list cutoff),
- * AP_ERR_OOM, AP_ERR_CUDA.  Synchronises. */
+ * AP_ERR_OOM, AP_ERR_CUDA.  Synchronises once with pot->list_sizing = AP_LIST_COUNTED;
+ * with AP_LIST_BOUND it issues its uploads on `stream` and returns without waiting. */
 ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* region,
                   const ap_indenter* indenter, int n_atoms, const double* pos,
                   const double* vel, const unsigned char* fixed, void* stream, ap_ctx** out);

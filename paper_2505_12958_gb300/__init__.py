@@ -41,8 +41,10 @@ def _f64(a, shape=None):
     return a
 
 
-def potential_struct(eam, ace, mass, skin=1.0, precision="fp32"):
-    """Fill the ap_potential struct; returns (struct, keep-alive arrays)."""
+def potential_struct(eam, ace, mass, skin=1.0, precision="fp32", list_sizing="counted"):
+    """Fill the ap_potential struct; returns (struct, keep-alive arrays).  list_sizing:
+    "counted" (ap_init sizes the neighbour list by a counting pass and synchronises once) or
+    "bound" (the 0.1 atoms / A^3 bound; ap_init does not wait)."""
     p = _capi.Potential()
     p.eam_n_phi = len(eam["phi_a"])
     p.eam_n_rho = len(eam["rho_a"])
@@ -70,6 +72,7 @@ def potential_struct(eam, ace, mass, skin=1.0, precision="fp32"):
     p.ace_precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
     p.mass_amu = float(mass)
     p.skin = float(skin)
+    p.list_sizing = {"counted": 0, "bound": 1}[list_sizing]
     return p, (idx, c1, c2)
 
 
@@ -134,11 +137,11 @@ class APContext:
     """One structure on the current CUDA device (wraps ap_init / ap_destroy)."""
 
     def __init__(self, eam, ace, box, x, v=None, fixed=None, region=None, indenter=None, ind_vel=None,
-                 mass=1.0, skin=1.0, precision="fp32", stream=None):
+                 mass=1.0, skin=1.0, precision="fp32", stream=None, list_sizing="counted"):
         L = _capi.lib()
         x = _f64(x, (-1, 3))
         self.n = x.shape[0]
-        pot, keep = potential_struct(eam, ace, mass, skin, precision)
+        pot, keep = potential_struct(eam, ace, mass, skin, precision, list_sizing)
         bs = _box_struct(box)
         rs, rkeep = _region_struct(region, self.n)
         ins = _indenter_struct(indenter, ind_vel)

@@ -28,7 +28,7 @@ class Potential(C.Structure):
                 ("eam_r_lo", D), ("eam_r_hi", D), ("eam_b", D * 6),
                 ("ace_rc", D), ("ace_nref", D), ("ace_nmax", I), ("ace_lmax", I), ("ace_nfunc", I),
                 ("ace_idx", PI), ("ace_c1", PD), ("ace_c2", PD), ("ace_c1_0", D), ("ace_c2_0", D),
-                ("ace_precision", I), ("mass_amu", D), ("skin", D)]
+                ("ace_precision", I), ("mass_amu", D), ("skin", D), ("list_sizing", I)]
 
 
 class Box(C.Structure):

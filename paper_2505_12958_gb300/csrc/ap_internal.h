@@ -181,6 +181,7 @@ struct Ctx {
     double* w_fixed = nullptr;
     int *cell = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cell_atoms = nullptr;
     int* nbr = nullptr;                                  // [cap][n]
+    int* nbr_tmp = nullptr;                              // [n][cap]: hits of the staged list build
     int* nnbr = nullptr;
     int cap = 0;
     int* ace_list = nullptr;
@@ -324,7 +325,7 @@ struct BatchTable {
     const CtxDev* d[kMaxBatchCtx];
     int b256[kMaxBatchCtx + 1];       // blocks of 256 threads per context (atoms)
     int b128[kMaxBatchCtx + 1];       // blocks of 128 threads per context (atoms)
-    int bcell[kMaxBatchCtx + 1];      // blocks of 256 threads per context (cells)
+    int bcell[kMaxBatchCtx + 1];      // blocks of 256 threads per context (cells, a warp per cell)
 };
 
 static_assert(sizeof(CtxDev) <= sizeof(Ctx::desc_h), "descriptor copy fits its host record");

@@ -367,7 +367,7 @@ void free_all(ap_ctx* xc) {
     ap::Ctx& c = xc->c;
     void* ps[] = {c.eam_d, c.D, c.Dlo, c.pos_lo, c.ace_A, c.ace_dA, c.x, c.v, c.xb, c.f, c.pos4, c.uxi, c.w, c.e_emb, c.e_eam, c.e_ace,
                   c.vir_eam, c.vir_ace, c.acc, c.fixed, c.w_fixed, c.cell, c.cell_count, c.cell_start,
-                  c.cell_atoms, c.nbr, c.nnbr, c.ace_list, c.flags, c.d_time, c.partials, c.totals, c.e_atom,
+                  c.cell_atoms, c.nbr, c.nbr_tmp, c.nnbr, c.ace_list, c.flags, c.d_time, c.partials, c.totals, c.e_atom,
                   c.pos_stage, c.f_stage, c.csp_sum, c.csp_under, c.csp_w0, c.csp_wnew, c.csp_seeds, c.csp_nseed,
                   c.thermo_group, c.nh_state, c.nh_partials, c.d_step, c.com, c.load_ring, c.load_ring_t};
     for (void* p : ps) {
@@ -420,10 +420,79 @@ ap_status arena_commit(ap_ctx* xc, const ArenaPlan& plan) {
     return AP_OK;
 }
 
-void to_soa(const double* aos, int n, std::vector<double>& soa) {
-    soa.resize(3 * (size_t)n);
+void to_soa(const double* aos, int n, double* soa) {
     for (int i = 0; i < n; ++i)
         for (int k = 0; k < 3; ++k) soa[(size_t)k * n + i] = aos[3 * (size_t)i + k];
+}
+
+void to_soa(const double* aos, int n, std::vector<double>& soa) {
+    soa.resize(3 * (size_t)n);
+    to_soa(aos, n, soa.data());
+}
+
+// Pinned staging blocks for the uploads of ap_init.  A copy from pageable memory passes
+// through the driver's own staging buffers and can hold the calling thread for milliseconds
+// while transfers of other streams occupy them; a copy from pinned memory is queued and
+// returns at once.  A block is used by one context's uploads and recycled once the event
+// recorded after them has completed; blocks are never freed (like the pinned slots above).
+struct Staging {
+    char* p = nullptr;
+    size_t bytes = 0;
+    int dev = -1;
+    cudaEvent_t ev = nullptr;
+};
+std::mutex g_stage_mu;
+std::vector<Staging> g_stage_free, g_stage_busy;
+
+bool staging_take(size_t bytes, int dev, Staging& out) {
+    std::lock_guard<std::mutex> lk(g_stage_mu);
+    for (size_t k = 0; k < g_stage_busy.size();) {
+        if (cudaEventQuery(g_stage_busy[k].ev) == cudaSuccess) {
+            g_stage_free.push_back(g_stage_busy[k]);
+            g_stage_busy[k] = g_stage_busy.back();
+            g_stage_busy.pop_back();
+        } else {
+            ++k;
+        }
+    }
+    int best = -1;
+    for (int k = 0; k < (int)g_stage_free.size(); ++k)
+        if (g_stage_free[k].dev == dev && g_stage_free[k].bytes >= bytes &&
+            (best < 0 || g_stage_free[k].bytes < g_stage_free[best].bytes))
+            best = k;
+    if (best >= 0) {
+        out = g_stage_free[best];
+        g_stage_free[best] = g_stage_free.back();
+        g_stage_free.pop_back();
+        return true;
+    }
+    Staging b;
+    b.bytes = (size_t)1 << 20;
+    while (b.bytes < bytes) b.bytes <<= 1;
+    b.dev = dev;
+    if (cudaMallocHost((void**)&b.p, b.bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(b.p);
+        return false;
+    }
+    out = b;
+    return true;
+}
+
+// the block's copies are queued on s: it returns to the pool when they have completed
+void staging_give(const Staging& b, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_stage_mu);
+    if (cudaEventRecord(b.ev, s) == cudaSuccess) {
+        g_stage_busy.push_back(b);
+    } else {
+        cudaGetLastError();
+        cudaStreamSynchronize(s);
+        g_stage_free.push_back(b);
+    }
 }
 
 // one AP force evaluation of the current positions (stages a1-a7), in two parts around the
@@ -504,13 +573,19 @@ ap_status read_flags(ap::Ctx& c, cudaStream_t s) {
         ap_status grown = AP_ERR_CAPACITY;
         {
             int cap = ((int)(need * 1.25) + 8 + 3) & ~3;
-            int* nb = nullptr;
+            int *nb = nullptr, *nt = nullptr;
             cudaError_t ea = injected_alloc_failure() ? cudaErrorMemoryAllocation
                                                       : cudaMallocAsync((void**)&nb, (size_t)cap * c.n * sizeof(int), c.stream);
             if (ea == cudaSuccess) {
+                ea = cudaMallocAsync((void**)&nt, (size_t)cap * c.n * sizeof(int), c.stream);
+                if (ea != cudaSuccess) cudaFreeAsync(nb, c.stream);
+            }
+            if (ea == cudaSuccess) {
                 cudaFreeAsync(c.nbr, c.stream);
-                c.dev_bytes += ((size_t)cap - (size_t)c.cap) * c.n * sizeof(int);
+                cudaFreeAsync(c.nbr_tmp, c.stream);
+                c.dev_bytes += 2 * ((size_t)cap - (size_t)c.cap) * c.n * sizeof(int);
                 c.nbr = nb;
+                c.nbr_tmp = nt;
                 c.cap = cap;
                 c.layout_gen += 1;
             } else {
@@ -535,23 +610,30 @@ extern "C" {
 
 int ap_version(void) { return AP_API_VERSION; }
 
+// neighbour slots per atom for the list sphere of radius rl at 0.1 atoms / A^3 (denser than
+// any metal here), with the 25 % margin and the rounding of the counted capacity
+int list_capacity_bound(double rl) {
+    const double need = 4.18879 * rl * rl * rl * 0.1;
+    return ((int)(need * 1.25) + 8 + 3) & ~3;
+}
+
 size_t ap_footprint_bytes(const ap_potential* pot, int n_atoms, double ace_fraction) {
     (void)ace_fraction;   // the ACE arrays are sized for every atom (the region moves)
     double rl = 6.5;
     if (pot) {
         double rc = 0.0;
         for (int k = 0; k < pot->eam_n_phi && k < 32; ++k) rc = std::max(rc, pot->eam_phi_d[k]);
+        for (int k = 0; k < pot->eam_n_rho && k < 16; ++k) rc = std::max(rc, pot->eam_rho_d[k]);
         rc = std::max(rc, pot->ace_rc);
         rl = rc + (pot->skin > 0 ? pot->skin : 1.0);
     }
-    // neighbour capacity: the list sphere at 0.1 atoms / A^3 (denser than any metal here),
-    // with the 25 % margin and rounding the context applies
-    const double need = 4.18879 * rl * rl * rl * 0.1;
-    const size_t cap = (size_t)(need * 1.25 + 8 + 4);
+    // the neighbour capacity of bound sizing, which the counted capacity stays below for
+    // structures of metallic density
+    const size_t cap = (size_t)list_capacity_bound(rl) + 4;
     // per-atom arrays allocated by ap_init (and the host-transfer staging buffers)
     const size_t per_atom = 16 + 3 * 8 * 3 + 3 * 4 + 16 + 4 + 4 + 8 + 8 + 8 + 4 +
                             2 * sizeof(float) * ap::kNLM * ap::kNmax + 2 * 6 * 4 + 3 * 8 + 1 + 8 +
-                            4 + 4 + 4 + 4 + 8 + 3 * 8 + 3 * 4 + cap * 4;
+                            4 + 4 + 4 + 4 + 8 + 3 * 8 + 3 * 4 + 2 * cap * 4;   // the list and the build's scratch
     const size_t cells = 2 * sizeof(int) * ((size_t)n_atoms + 1);   // cell count/start (<= 1 per atom)
     const size_t nred = (size_t)(n_atoms + ap::kRedBlock - 1) / ap::kRedBlock + 1;
     return (size_t)n_atoms * per_atom + cells + nred * 10 * 8 + 2 * 125 * 16 + sizeof(ap::AceTc) + 512 +
@@ -568,6 +650,7 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
     if (!pot || !box || !pos || n < 1 || n > ap::kMaxAtoms) { g_init_err = "ap_init: missing argument or bad atom count"; return AP_ERR_ARG; }
     if (!(pot->mass_amu > 0.0) || !(pot->skin >= 0.0)) { g_init_err = "ap_init: mass must be > 0 and skin >= 0"; return AP_ERR_ARG; }
     if (pot->ace_precision < AP_ACE_FP32 || pot->ace_precision > AP_ACE_FP64) { g_init_err = "ap_init: unknown ace_precision"; return AP_ERR_ARG; }
+    if (pot->list_sizing != AP_LIST_COUNTED && pot->list_sizing != AP_LIST_BOUND) { g_init_err = "ap_init: unknown list_sizing"; return AP_ERR_ARG; }
     ap_ctx* xc = new (std::nothrow) ap_ctx();
     if (!xc) return AP_ERR_OOM;
     ap::Ctx& c = xc->c;
@@ -671,8 +754,44 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
         c.err = "pinned host allocation";
         return fail(AP_ERR_OOM);
     }
+    // the host arrays go through a pinned staging block (pageable copies if none is had)
+    const bool explicit_w = region && region->kind == AP_REGION_EXPLICIT;
+    const size_t up_bytes = sizeof(ap::EamDev) + 2 * D.size() * sizeof(float4) + 2 * 3 * N * sizeof(double) +
+                            (fixed ? N : 0) + (explicit_w ? N * sizeof(double) : 0) + 8 * 64;
+    Staging stg;
+    const bool staged = staging_take(up_bytes, c.dev, stg);
+    struct StagingReturn {          // back to the pool on every path out of ap_init
+        const Staging& b;
+        cudaStream_t s;
+        bool on;
+        ~StagingReturn() { if (on) staging_give(b, s); }
+    } stg_return{stg, c.stream, staged};
+    size_t stg_used = 0;
+    auto stage_copy = [&](const void* src, size_t bytes) -> const void* {
+        if (!staged) return src;
+        char* d = stg.p + stg_used;
+        std::memcpy(d, src, bytes);
+        stg_used += (bytes + 63) & ~(size_t)63;
+        return d;
+    };
     std::vector<double> soa;
-    to_soa(pos, n, soa);
+    const double* pos_soa;
+    const double* vel_soa = nullptr;
+    if (staged) {
+        double* d = (double*)(stg.p + stg_used);
+        to_soa(pos, n, d);
+        stg_used += (3 * N * sizeof(double) + 63) & ~(size_t)63;
+        pos_soa = d;
+        if (vel) {
+            d = (double*)(stg.p + stg_used);
+            to_soa(vel, n, d);
+            stg_used += (3 * N * sizeof(double) + 63) & ~(size_t)63;
+            vel_soa = d;
+        }
+    } else {
+        to_soa(pos, n, soa);
+        pos_soa = soa.data();
+    }
     cudaError_t e = cudaSuccess;
     auto cp = [&](void* dst, const void* src, size_t bytes) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c.stream);
@@ -680,7 +799,7 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
     auto zero = [&](void* dst, size_t bytes) {
         if (e == cudaSuccess) e = cudaMemsetAsync(dst, 0, bytes, c.stream);
     };
-    cp(c.eam_d, &c.eam_h, sizeof(ap::EamDev));
+    cp(c.eam_d, stage_copy(&c.eam_h, sizeof(ap::EamDev)), sizeof(ap::EamDev));
     {
         std::unique_ptr<ap::AceTc> tc(new (std::nothrow) ap::AceTc());
         if (!tc) { c.err = "host allocation"; return fail(AP_ERR_OOM); }
@@ -688,18 +807,22 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
         c.ace_tc_d = ap::shared_ace_tables(*tc, c.dev, err);
         if (!c.ace_tc_d) { c.err = err; return fail(AP_ERR_OOM); }
     }
-    cp(c.D, D.data(), D.size() * sizeof(float4));
-    cp(c.Dlo, Dlo.data(), Dlo.size() * sizeof(float4));
-    cp(c.x, soa.data(), 3 * N * sizeof(double));
-    cp(c.xb, soa.data(), 3 * N * sizeof(double));
-    if (vel) { to_soa(vel, n, soa); cp(c.v, soa.data(), 3 * N * sizeof(double)); }
-    else zero(c.v, 3 * N * sizeof(double));
-    if (fixed) cp(c.fixed, fixed, N);
+    cp(c.D, stage_copy(D.data(), D.size() * sizeof(float4)), D.size() * sizeof(float4));
+    cp(c.Dlo, stage_copy(Dlo.data(), Dlo.size() * sizeof(float4)), Dlo.size() * sizeof(float4));
+    cp(c.x, pos_soa, 3 * N * sizeof(double));
+    cp(c.xb, pos_soa, 3 * N * sizeof(double));
+    if (vel) {
+        if (!staged) { to_soa(vel, n, soa); vel_soa = soa.data(); }
+        cp(c.v, vel_soa, 3 * N * sizeof(double));
+    } else {
+        zero(c.v, 3 * N * sizeof(double));
+    }
+    if (fixed) cp(c.fixed, stage_copy(fixed, N), N);
     else zero(c.fixed, N);
-    if (region && region->kind == AP_REGION_EXPLICIT) {
+    if (explicit_w) {
         for (int i = 0; i < n; ++i)
             if (!(region->w_explicit[i] >= 0.0 && region->w_explicit[i] <= 1.0)) { c.err = "explicit weights must lie in [0, 1]"; return fail(AP_ERR_ARG); }
-        cp(c.w_fixed, region->w_explicit, N * sizeof(double));
+        cp(c.w_fixed, stage_copy(region->w_explicit, N * sizeof(double)), N * sizeof(double));
     }
     zero(c.acc, 3 * N * sizeof(unsigned long long));
     zero(c.cell_count, (size_t)c.grid.ncell * sizeof(int));
@@ -716,18 +839,23 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
     cp(&c.flags[ap::kFlagRebuild], &one, sizeof(int));
     if (e != cudaSuccess) { cuda_check(c, e, "ap_init upload"); return fail(AP_ERR_CUDA); }
 
-    // size the neighbour capacity from a counting pass over the first binning
     cudaStream_t s = c.stream;
-    c.launches += ap::launch_rebuild(c, s);
-    c.launches += ap::launch_prepare(c, s);
-    c.launches += ap::launch_build(c, s, 1);
-    e = cudaMemcpyAsync(c.h_flags, c.flags, sizeof(int) * ap::kFlagCount, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) { cuda_check(c, e, "ap_init neighbour sizing"); return fail(AP_ERR_CUDA); }
-    int need = c.h_flags[ap::kFlagMaxNbr];
-    c.cap = std::max(8, ((int)(need * 1.25) + 8 + 3) & ~3);
-    if ((st = dalloc(c, &c.nbr, (size_t)c.cap * N))) return fail(st);
+    if (pot->list_sizing == AP_LIST_BOUND) {
+        // neighbour capacity from the density bound: nothing to wait for
+        c.cap = list_capacity_bound(c.rc_list);
+    } else {
+        // size the neighbour capacity from a counting pass over the first binning
+        c.launches += ap::launch_rebuild(c, s);
+        c.launches += ap::launch_prepare(c, s);
+        c.launches += ap::launch_build(c, s, 1);
+        e = cudaMemcpyAsync(c.h_flags, c.flags, sizeof(int) * ap::kFlagCount, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) { cuda_check(c, e, "ap_init neighbour sizing"); return fail(AP_ERR_CUDA); }
+        int need = c.h_flags[ap::kFlagMaxNbr];
+        c.cap = std::max(8, ((int)(need * 1.25) + 8 + 3) & ~3);
+    }
+    if ((st = dalloc(c, &c.nbr, (size_t)c.cap * N)) || (st = dalloc(c, &c.nbr_tmp, (size_t)c.cap * N))) return fail(st);
     c.rebuilds = 0;
     *out = xc;
     return AP_OK;
@@ -980,7 +1108,7 @@ void batch_table(const std::vector<ap_ctx*>& cs, ap::BatchTable& t) {
         t.d[k] = c.desc_d;
         t.b256[k + 1] = t.b256[k] + (c.n + 255) / 256;
         t.b128[k + 1] = t.b128[k] + (c.n + 127) / 128;
-        t.bcell[k + 1] = t.bcell[k] + (c.grid.ncell + 255) / 256;
+        t.bcell[k + 1] = t.bcell[k] + (c.grid.ncell + 7) / 8;          // a warp per cell, 8 per block
         t.atoms += c.n;
     }
 }

@@ -1,7 +1,8 @@
 """Serving form: many independent structures stepped concurrently on one GPU.
 
 Continuous batching over whole MD requests.  Each admitted request gets its own context
-(`APContext`) on its own non-blocking stream.  In every scheduling pass the server issues
+(`APContext`) on its own non-blocking stream, with its neighbour list sized from the density
+bound, so that creating it never waits for the GPU.  In every scheduling pass the server issues
 one chunk of velocity-Verlet steps for every active request: by default each request
 replays its own step graphs on its own stream, so the requests' kernels overlap on the
 device; with `batched`, the requests of at most `batch_atoms` atoms go through one
@@ -104,7 +105,7 @@ class Server:
         try:
             a.ctx = APContext(req["eam"], req["ace"], req["box"], req["x"], req["v"], req["fixed"], req["region"],
                               req.get("indenter"), req.get("ind_vel"), req["mass"], precision=self.precision,
-                              stream=a.stream)
+                              stream=a.stream, list_sizing="bound")
         except APError as e:
             self._streams.append(a.stream)
             return None, self._failed(req, now, e, foot)

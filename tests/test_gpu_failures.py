@@ -135,6 +135,50 @@ def _same(a, b):
     assert a.energy["e_total"] == b.energy["e_total"]
 
 
+def test_bound_list_sizing_equals_counted_sizing(apl):
+    """ap_init with the density-bound capacity (no synchronisation) gives the same bits as
+    the counted capacity: the list holds the same entries in the same order."""
+    c = synth.configs.w_slab(ncell=8, nz=6, r_in=7.0, r_sw=3.0, R=9.0, penetration=1.0)
+    out = []
+    for sizing in ("counted", "bound"):
+        with apl.APContext(c["eam"], c["ace"], c["box"], c["x"], c["v"], c["fixed"], c["region"], c["indenter"],
+                           c["ind_vel"], c["mass"], list_sizing=sizing) as ctx:
+            ctx.step(12, 1.0)
+            ctx.check()
+            x, v, _ = ctx.get_state()
+            out.append((ctx.neighbor_info()[0], x, v, ctx.forces(), ctx.energy()["e_total"], ctx.memory_bytes()))
+    (cap_c, xc, vc, fc, ec, mc), (cap_b, xb, vb, fb, eb, mb) = out
+    assert cap_b >= cap_c
+    assert np.array_equal(xc, xb) and np.array_equal(vc, vb) and np.array_equal(fc, fb) and ec == eb
+    assert mb <= apl.footprint_bytes(c["eam"], c["ace"], len(c["x"]), c["mass"])
+
+
+def test_bound_list_sizing_grows_on_a_denser_structure(apl):
+    """A cell compressed beyond the bound's 0.1 atoms / A^3 overflows the bound capacity:
+    the first check reports AP_ERR_CAPACITY and grows the list, and the next evaluation
+    equals that of a context sized by counting."""
+    from paper_2505_12958_gb300._capi import AP_ERR_CAPACITY
+    c = synth.configs.w_bulk(ncell=6)
+    reg = {"kind": "const", "w": 0.0}
+    xc, boxc = _scaled(c, 0.72)           # 0.17 atoms / A^3
+    with apl.APContext(c["eam"], c["ace"], boxc, xc, None, None, reg, None, None, c["mass"],
+                       list_sizing="bound") as ctx:
+        cap0, _ = ctx.neighbor_info()
+        ctx.compute_forces()
+        with pytest.raises(apl.APError) as e:
+            ctx.check()
+        assert e.value.status == AP_ERR_CAPACITY
+        assert ctx.neighbor_info()[0] > cap0
+        ctx.compute_forces()
+        ctx.check()
+        F = ctx.forces()
+        E = ctx.energy()["e_total"]
+    with _ctx(apl, c, x=xc, box=boxc, region=reg) as counted:
+        counted.compute_forces()
+        assert np.array_equal(F, counted.forces())
+        assert E == counted.energy()["e_total"]
+
+
 def test_server_refuses_a_request_whose_context_fails_and_serves_the_rest(apl):
     from paper_2505_12958_gb300._capi import lib
     from paper_2505_12958_gb300.serve import Server
