@@ -263,6 +263,15 @@ __global__ void k_prepare(const double* __restrict__ x, int n, const GridDev g, 
 constexpr int kBands = 16;
 constexpr int kBuildBlock = 128;
 
+// squared length of the pair vector x_rel_j + D[code] - x_rel_i, with every rounding fixed
+// (no contraction left to the compiler), so that both build kernels include the same pairs
+__device__ __forceinline__ float pair_r2(const float4& pj, const float4& d, const float4& p) {
+    const float dx = __fsub_rn(__fadd_rn(pj.x, d.x), p.x);
+    const float dy = __fsub_rn(__fadd_rn(pj.y, d.y), p.y);
+    const float dz = __fsub_rn(__fadd_rn(pj.z, d.z), p.z);
+    return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+
 // distance band of a list entry, r = r2 rsqrt(r2) with the hardware reciprocal square root:
 // both build kernels evaluate it with the same instructions, so they order entries alike
 __device__ __forceinline__ int list_band(float r2, float bscale) {
@@ -366,8 +375,7 @@ __device__ __forceinline__ int build_atom_global(int i, const float4* __restrict
                     for (int t = 0; t < 4; ++t) {
                         const int j = jj[t];
                         if (j < 0 || (self_cell && j == i)) continue;
-                        const float dx = pj[t].x + d.x - p.x, dy = pj[t].y + d.y - p.y, dz = pj[t].z + d.z - p.z;
-                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        const float r2 = pair_r2(pj[t], d, p);
                         if (r2 < g.rlist2) visit(j | (code << kNbrShift), list_band(r2, bscale));
                     }
                 }
@@ -530,12 +538,21 @@ __global__ void __launch_bounds__(kStBlock) k_build_staged(const float4* __restr
                         if (qb >= qe) continue;
                         const bool self_cell = oc4.x == 0 && oc4.y == 0 && oc4.z == 0;
                         const float4 d = D[code];
-                        for (int qq = qb; qq < qe; ++qq) {
-                            const float4 pj = st[qq];
-                            if (self_cell && __float_as_int(pj.w) == i) continue;
-                            const float dx = pj.x + d.x - p.x, dy = pj.y + d.y - p.y, dz = pj.z + d.z - p.z;
-                            const float r2 = dx * dx + dy * dy + dz * dz;
-                            if (r2 < g.rlist2) visit(qq, code, list_band(r2, bscale));
+                        // two candidates per iteration (independent chains), visited in order
+                        int qq = qb;
+                        for (; qq + 2 <= qe; qq += 2) {
+                            const float4 pa = st[qq], pb = st[qq + 1];
+                            const float ra = pair_r2(pa, d, p), rb = pair_r2(pb, d, p);
+                            const bool ha = ra < g.rlist2 && !(self_cell && __float_as_int(pa.w) == i);
+                            const bool hb = rb < g.rlist2 && !(self_cell && __float_as_int(pb.w) == i);
+                            if (ha) visit(qq, code, list_band(ra, bscale));
+                            if (hb) visit(qq + 1, code, list_band(rb, bscale));
+                        }
+                        if (qq < qe) {
+                            const float4 pa = st[qq];
+                            const float ra = pair_r2(pa, d, p);
+                            if (ra < g.rlist2 && !(self_cell && __float_as_int(pa.w) == i))
+                                visit(qq, code, list_band(ra, bscale));
                         }
                     }
                 };
