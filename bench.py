@@ -444,6 +444,44 @@ def precision_sweep(torch, ap, steps, warmup, modes=("fp64", "fp32", "tf32x3", "
             "modes": res}
 
 
+def fraction_sweep(torch, ap, steps=200, r_ins=(17.0, 23.0, 30.0, 38.5, 50.0, 64.0)):
+    """AP throughput against the size of the precise region on the 128,000-atom W slab (the
+    hemisphere's inner radius r_in, 4 A shell; r_in = 50 A is the metric's workload), beside the
+    same slab in pure ACE (w = 1) and pure EAM (w = 0).  The paper's AP-over-ACE time ratios
+    (21x for Cu, 27x for W; Secs. 3.1, 3.2 and 4) come from runs whose precise regions hold a few
+    per cent of the atoms.  additive_model is the ratio if an AP step cost f t_ACE + t_EAM (f the ACE
+    fraction, t the pure-potential step times)."""
+    c = synth.configs.w_slab()
+    n = len(c["x"])
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def rate(region, k):
+        ctx = make_ctx(ap, c, region=region)
+        ctx.step(3, 1.0)
+        ctx.check()
+        n_ace = ctx.energy()["n_ace"]
+        ms, _ = timed_steps(torch, ctx, k, flush)
+        ctx.check()
+        ctx.close()
+        return sum(ms) / k, n_ace
+
+    t_ace, _ = rate({"kind": "const", "w": 1.0}, max(5, steps // 8))
+    t_eam, _ = rate({"kind": "const", "w": 0.0}, steps)
+    points = []
+    for r_in in r_ins:
+        reg = dict(c["region"])
+        reg["r_in"] = float(r_in)
+        t, n_ace = rate(reg, steps)
+        f = n_ace / n
+        points.append({"r_in_A": r_in, "n_ace": n_ace, "ace_fraction": f, "ms_per_step": t,
+                       "atom_steps_per_s": n / (t / 1000.0), "speedup_vs_pure_ace": t_ace / t,
+                       "additive_model": t_ace / (f * t_ace + t_eam)})
+    return {"workload": "W BCC (001) slab 40x40x40 cells, 128,000 atoms, hemisphere of radius r_in + 4 A under "
+                        "the indenter, 300 K, dt = 1 fs; L2 flushed before every timed step",
+            "steps": steps, "pure_ace": {"ms_per_step": t_ace, "atom_steps_per_s": n / (t_ace / 1000.0)},
+            "pure_eam": {"ms_per_step": t_eam, "atom_steps_per_s": n / (t_eam / 1000.0)}, "points": points}
+
+
 def autograd_bench(torch, ap, n_cells=256, seed=1004):
     """Forward + backward of the differentiable AP energy (positions and strain) over 256
     strained triclinic W cells of 4^3 .. 12^3 BCC cells (128 .. 3456 atoms, 1 % vacancies,
@@ -564,14 +602,15 @@ def main():
                           "batched launches (one launch per stage for all of them)")
     ap_.add_argument("--serve-batched", action="store_true",
                      help="--mode serve: the batched form instead of each request's own step graphs")
-    ap_.add_argument("--mode", default="ap", choices=["ap", "serve", "precision", "autograd"],
+    ap_.add_argument("--mode", default="ap", choices=["ap", "serve", "precision", "autograd", "fraction"],
                      help="ap: the metric line; serve: only the serving run; precision: the A_nlm "
                           "precision sweep on the 2M-atom Cu slab; autograd: forward+backward of the "
-                          "differentiable energy (each as its own line)")
+                          "differentiable energy; fraction: AP throughput against the precise "
+                          "region's size (each as its own line)")
     args = ap_.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.mode in ("serve", "precision", "autograd"):
+    if args.mode in ("serve", "precision", "autograd", "fraction"):
         import torch
         import paper_2505_12958_gb300 as ap
         ap.build()
@@ -580,6 +619,8 @@ def main():
                                 batched=args.serve_batched, batch_atoms=args.serve_batch_atoms)
         elif args.mode == "precision":
             out = precision_sweep(torch, ap, args.steps, args.warmup)
+        elif args.mode == "fraction":
+            out = fraction_sweep(torch, ap, steps=min(args.steps, 200))
         else:
             out = autograd_bench(torch, ap)
         print(json.dumps({"mode": args.mode, **out}, default=_jsonable), flush=True)
