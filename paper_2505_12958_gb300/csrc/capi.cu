@@ -612,7 +612,7 @@ int ap_version(void) { return AP_API_VERSION; }
 
 // neighbour slots per atom for the list sphere of radius rl at 0.1 atoms / A^3 (denser than
 // any metal here), with the 25 % margin and the rounding of the counted capacity
-int list_capacity_bound(double rl) {
+static int list_capacity_bound(double rl) {
     const double need = 4.18879 * rl * rl * rl * 0.1;
     return ((int)(need * 1.25) + 8 + 3) & ~3;
 }
@@ -933,11 +933,11 @@ ap_status ap_compute_forces_host(ap_ctx* xc, const double* h_pos, float* h_force
 
 // the second half kick runs inside the force pass's blend kernel unless Langevin forces are
 // added between them
-bool kick_in_blend(const ap::Ctx& c) { return c.thermo_kind != AP_THERMO_LANGEVIN; }
+static bool kick_in_blend(const ap::Ctx& c) { return c.thermo_kind != AP_THERMO_LANGEVIN; }
 
 // the integration kernels around a force pass: part 0 before it (thermostat half step,
 // kick-drift), part 1 after it (Langevin forces, kick, thermostat half step, momentum zeroing)
-int step_kernels(ap::Ctx& c, cudaStream_t s, double dt, int part) {
+static int step_kernels(ap::Ctx& c, cudaStream_t s, double dt, int part) {
     int k = 0;
     if (part == 0) {
         if (c.thermo_kind == AP_THERMO_NOSE_HOOVER) k += ap::launch_nh_half(c, s, dt);
@@ -954,7 +954,7 @@ int step_kernels(ap::Ctx& c, cudaStream_t s, double dt, int part) {
 
 // The kernels of one captured MD step: kick-drift, the force pass, the kicks.  timed:
 // event-record nodes of xc->ev_mark bracket the ACE contraction.
-void captured_step(ap_ctx* xc, cudaStream_t s, double dt, bool timed) {
+static void captured_step(ap_ctx* xc, cudaStream_t s, double dt, bool timed) {
     ap::Ctx& c = xc->c;
     const double kick = kick_in_blend(c) ? dt : 0.0;
     c.launches += step_kernels(c, s, dt, 0);
@@ -975,7 +975,7 @@ void captured_step(ap_ctx* xc, cudaStream_t s, double dt, bool timed) {
 }
 
 // the timed step graph and the handles of its two event-record nodes
-cudaError_t capture_timed_step(ap_ctx* xc, cudaStream_t s, double dt) {
+static cudaError_t capture_timed_step(ap_ctx* xc, cudaStream_t s, double dt) {
     cudaError_t e = cudaSuccess;
     for (int q = 0; q < 2 && e == cudaSuccess; ++q)
         if (!xc->ev_mark[q]) e = cudaEventCreate(&xc->ev_mark[q]);
@@ -1004,7 +1004,7 @@ cudaError_t capture_timed_step(ap_ctx* xc, cudaStream_t s, double dt) {
 }
 
 // one replay of the timed step graph with a fresh event pair on its event-record nodes
-cudaError_t replay_timed_step(ap_ctx* xc, cudaStream_t s) {
+static cudaError_t replay_timed_step(ap_ctx* xc, cudaStream_t s) {
     if (xc->pending.size() >= 64) drain_ready(xc);
     cudaEvent_t a = get_event(xc), b = get_event(xc);
     cudaError_t e = cudaGraphExecEventRecordNodeSetEvent(xc->timed_exec, xc->ev_node[0], a);

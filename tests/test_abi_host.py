@@ -30,6 +30,22 @@ def test_library_exports_every_declared_symbol(apl):
     assert _capi.lib().ap_version() == 1
 
 
+def test_library_exports_no_undeclared_c_symbols(apl):
+    """Every unmangled function the library exports is one include/ap.h declares: the
+    library's internal helpers have file or C++ namespace scope and cannot clash with another
+    library's symbols."""
+    import shutil
+    import subprocess
+    from paper_2505_12958_gb300 import _capi
+    if shutil.which("nm") is None:
+        pytest.skip("nm is not installed")
+    out = subprocess.run(["nm", "-D", "--defined-only", _capi.LIBPATH], capture_output=True, text=True, check=True).stdout
+    exported = {parts[2] for parts in (line.split() for line in out.splitlines())
+                if len(parts) == 3 and parts[1] == "T" and not parts[2].startswith("_Z")}
+    undeclared = sorted(exported - set(_capi.header_symbols()))
+    assert not undeclared, undeclared
+
+
 def test_gaunt_racah_matches_oracle_quadrature(apl, orc):
     worst = 0.0
     for l1 in range(5):
