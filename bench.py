@@ -581,6 +581,31 @@ def neighbors_in_ace_cutoff(c):
     return cnt
 
 
+def eam_roofline(stage_ms, c, pk, peak_src, skin=1.0):
+    """The two EAM passes against the HBM roofline: their minimum HBM bytes per step
+    (workload.eam_bytes_per_atom at the mean list length of the initial configuration, from a
+    host k-d tree) over their per-stage CUDA-event times.  They are bound by the L1/TEX unit
+    (their gathers and table lookups), not by HBM: the fraction shows how far."""
+    from scipy.spatial import cKDTree
+    from paper_2505_12958_gb300.workload import eam_bytes_per_atom
+    x = c["x"]
+    L = np.diag(np.asarray(c["box"]["h"]).reshape(3, 3))       # orthorhombic boxes
+    per = c["box"]["periodic"]
+    xx = np.array(x) - np.asarray(c["box"].get("origin", (0.0, 0.0, 0.0)))
+    for k in range(3):
+        xx[:, k] = np.mod(xx[:, k], L[k]) if per[k] else xx[:, k] - xx[:, k].min()
+    size = [L[k] if per[k] else 1e9 for k in range(3)]
+    rc = max(max(c["eam"]["phi_d"]), max(c["eam"]["rho_d"]), c["ace"]["rc"]) + skin
+    n_list = float(np.mean(cKDTree(xx, boxsize=size).query_ball_point(xx, r=rc, return_length=True) - 1))
+    ms = stage_ms.get("eam_density", 0.0) + stage_ms.get("eam_force", 0.0)
+    bytes_step = len(x) * eam_bytes_per_atom(n_list)
+    gbs = bytes_step / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+    return {"kernels": ["k_eam_density", "k_eam_force"], "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"],
+            "unit": "GB/s", "frac": gbs / pk["hbm_gbs"], "peak_source": peak_src, "mean_list_length": n_list,
+            "algorithmic_bytes_per_step": bytes_step, "ms_per_step": ms,
+            "source": "per-stage pass of the same run (every stage bracketed); the passes are L1/TEX-bound"}
+
+
 def main():
     ap_ = argparse.ArgumentParser()
     ap_.add_argument("--gpus", type=int, default=1)
@@ -733,6 +758,7 @@ def main():
             "stage_profile": "separate pass of %d steps with every stage bracketed by CUDA events "
                              "(about 2.5 us per stage); in the timed steps only the ACE contraction is bracketed" % k_stage,
             "gpu_launches": launches, "clocks": clocks, "e2e": e2e, "roofline": roof,
+            "eam_roofline": eam_roofline(stage_ms, c, pk, peak_src),
             "wall_s_timed_region": wall}
     if validity is not None:
         line["max_dF_vs_oracle"] = validity["max_dF_eV_A"]

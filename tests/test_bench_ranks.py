@@ -68,3 +68,25 @@ def test_roofline_line_from_stage_events():
     assert abs(r["fp32_lanes"]["achieved"] - w["fp32"] * 1000 / 0.5e-3 / 1e12) < 1e-9
     assert abs(r["tensor"]["peak"] - 2000.0 * 1.1 / 2.25) < 1e-9
     assert abs(r["tensor"]["frac_executed"] - w["tensor_executed"] * 1000 / 0.5e-3 / 1e12 / r["tensor"]["peak"]) < 1e-12
+
+
+def test_eam_roofline_from_stage_times():
+    """The EAM entry divides the passes' minimum HBM bytes (the per-atom model at the mean list
+    length, counted here by brute force on a small periodic cell) by their per-stage times."""
+    import numpy as np
+
+    import bench
+    import synth
+    from paper_2505_12958_gb300.workload import eam_bytes_per_atom
+    c = synth.configs.w_bulk(ncell=6)                 # 432 atoms, 19 A periodic box
+    x = c["x"]
+    L = np.asarray(c["box"]["h"]).reshape(3, 3)[0, 0]
+    rc = max(max(c["eam"]["phi_d"]), max(c["eam"]["rho_d"]), c["ace"]["rc"]) + 1.0
+    d = x[None, :, :] - x[:, None, :]
+    d -= L * np.round(d / L)                          # periodic in all three directions
+    cnt = (np.linalg.norm(d, axis=2) < rc).sum(axis=1) - 1
+    r = bench.eam_roofline({"eam_density": 0.01, "eam_force": 0.03}, c, {"hbm_gbs": 5000.0}, "test")
+    assert abs(r["mean_list_length"] - cnt.mean()) < 1e-9
+    assert abs(r["algorithmic_bytes_per_step"] - len(x) * eam_bytes_per_atom(cnt.mean())) < 1e-6
+    assert abs(r["achieved"] - r["algorithmic_bytes_per_step"] / 0.04e-3 / 1e9) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / 5000.0) < 1e-12 and r["unit"] == "GB/s"
