@@ -36,13 +36,45 @@ __device__ __forceinline__ void stage_tables(EamDev* sm, const EamDev* __restric
     __syncthreads();
 }
 
+// The image offset D[code] of a pair.  In an orthorhombic box it is (o0 cx, o1 cy, o2 cz) with
+// cell offsets o in -2..2 and c the FP32 cell edges: those products are exact, and equal the
+// host table's FP32 entries, so a 4-byte offset record replaces the 16-byte table read.
+struct PairOffsets {
+    char4 o[125];
+    float cx, cy, cz;
+    int ortho;
+};
+
+__device__ __forceinline__ void stage_offsets(PairOffsets& P, const GridDev& g) {
+    const int w1 = 2 * g.S[1] + 1, w2 = 2 * g.S[2] + 1;
+    for (int k = threadIdx.x; k < g.ncode; k += blockDim.x)
+        P.o[k] = make_char4((char)(k / (w1 * w2) - g.S[0]), (char)((k / w2) % w1 - g.S[1]), (char)(k % w2 - g.S[2]), 0);
+    if (threadIdx.x == 0) {
+        P.cx = (float)g.cellvec[0];
+        P.cy = (float)g.cellvec[4];
+        P.cz = (float)g.cellvec[8];
+        P.ortho = g.ortho;
+    }
+}
+
+__device__ __forceinline__ float4 pair_offset(const PairOffsets& P, const float4* Ds, int code) {
+    if (P.ortho) {
+        const char4 o = P.o[code];
+        return make_float4((float)o.x * P.cx, (float)o.y * P.cy, (float)o.z * P.cz, 0.0f);
+    }
+    return Ds[code];
+}
+
 __device__ __forceinline__ void eam_density_body(const float4* __restrict__ pos4, const int* __restrict__ nbr,
                                                      const int* __restrict__ nnbr, int n, const EamDev* __restrict__ eam,
-                                                     const float4* __restrict__ D, int ncode, float* __restrict__ uxi,
-                                                     double* __restrict__ e_emb, int* __restrict__ flags, int bid) {
+                                                     const float4* __restrict__ D, const GridDev& g,
+                                                     float* __restrict__ uxi, double* __restrict__ e_emb,
+                                                     int* __restrict__ flags, int bid) {
     __shared__ EamDev T;
     __shared__ float4 Ds[125];
-    stage_tables(&T, eam, Ds, D, ncode);          // constant tables: before the wait
+    __shared__ PairOffsets PO;
+    stage_offsets(PO, g);
+    stage_tables(&T, eam, Ds, D, g.ncode);        // constant tables: before the wait
     pdl_wait();
     int i = bid * blockDim.x + threadIdx.x;
     if (i == 0) flags[kFlagRebuild] = 0;        // the list built this step is in use now
@@ -54,7 +86,7 @@ __device__ __forceinline__ void eam_density_body(const float4* __restrict__ pos4
     float rho = 0.0f;
     const int m = nnbr[i];
     auto pair = [&](int e, const float4& q) {
-        const float4 d = Ds[(unsigned)e >> kNbrShift];
+        const float4 d = pair_offset(PO, Ds, (int)((unsigned)e >> kNbrShift));
         const float dx = q.x + d.x - p.x, dy = q.y + d.y - p.y, dz = q.z + d.z - p.z;
         const float r2 = dx * dx + dy * dy + dz * dz;
         if (r2 < rc2) rho += eam_zeta(T, sqrtf(r2));
@@ -91,9 +123,9 @@ __device__ __forceinline__ void eam_density_body(const float4* __restrict__ pos4
 
 __global__ void __launch_bounds__(kEamBlock) k_eam_density(const float4* __restrict__ pos4, const int* __restrict__ nbr,
                                                      const int* __restrict__ nnbr, int n, const EamDev* __restrict__ eam,
-                                                     const float4* __restrict__ D, int ncode, float* __restrict__ uxi,
+                                                     const float4* __restrict__ D, const GridDev g, float* __restrict__ uxi,
                                                      double* __restrict__ e_emb, int* __restrict__ flags) {
-    eam_density_body(pos4, nbr, nnbr, n, eam, D, ncode, uxi, e_emb, flags, blockIdx.x);
+    eam_density_body(pos4, nbr, nnbr, n, eam, D, g, uxi, e_emb, flags, blockIdx.x);
 }
 
 // per step: EAM forces.  The pair value Phi is needed only for the FP32 estimate of E_i^EAM
@@ -101,12 +133,15 @@ __global__ void __launch_bounds__(kEamBlock) k_eam_density(const float4* __restr
 // the virial come from the on-request energy pass.
 __device__ __forceinline__ void eam_force_body(const float4* __restrict__ pos4, const int* __restrict__ nbr,
                                                    const int* __restrict__ nnbr, int n, const EamDev* __restrict__ eam,
-                                                   const float4* __restrict__ D, int ncode, const float* __restrict__ uxi,
-                                                   const double* __restrict__ e_emb, const float* __restrict__ wv,
-                                                   float* __restrict__ f, double* __restrict__ e_eam, int bid) {
+                                                   const float4* __restrict__ D, const GridDev& g,
+                                                   const float* __restrict__ uxi, const double* __restrict__ e_emb,
+                                                   const float* __restrict__ wv, float* __restrict__ f,
+                                                   double* __restrict__ e_eam, int bid) {
     __shared__ EamDev T;
     __shared__ float4 Ds[125];
-    stage_tables(&T, eam, Ds, D, ncode);          // constant tables: before the wait
+    __shared__ PairOffsets PO;
+    stage_offsets(PO, g);
+    stage_tables(&T, eam, Ds, D, g.ncode);        // constant tables: before the wait
     pdl_wait();
     int i = bid * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -118,7 +153,7 @@ __device__ __forceinline__ void eam_force_body(const float4* __restrict__ pos4, 
     float fx = 0.f, fy = 0.f, fz = 0.f, eph = 0.f;
     const int m = nnbr[i];
     auto pair = [&](int e, const float4& q, float xj) {
-        const float4 d = Ds[(unsigned)e >> kNbrShift];
+        const float4 d = pair_offset(PO, Ds, (int)((unsigned)e >> kNbrShift));
         const float dx = q.x + d.x - p.x, dy = q.y + d.y - p.y, dz = q.z + d.z - p.z;
         const float r2 = dx * dx + dy * dy + dz * dz;
         const float us = ui + q.w;
@@ -158,10 +193,10 @@ __device__ __forceinline__ void eam_force_body(const float4* __restrict__ pos4, 
 
 __global__ void __launch_bounds__(kEamBlock) k_eam_force(const float4* __restrict__ pos4, const int* __restrict__ nbr,
                                                    const int* __restrict__ nnbr, int n, const EamDev* __restrict__ eam,
-                                                   const float4* __restrict__ D, int ncode, const float* __restrict__ uxi,
+                                                   const float4* __restrict__ D, const GridDev g, const float* __restrict__ uxi,
                                                    const double* __restrict__ e_emb, const float* __restrict__ wv,
                                                    float* __restrict__ f, double* __restrict__ e_eam) {
-    eam_force_body(pos4, nbr, nnbr, n, eam, D, ncode, uxi, e_emb, wv, f, e_eam, blockIdx.x);
+    eam_force_body(pos4, nbr, nnbr, n, eam, D, g, uxi, e_emb, wv, f, e_eam, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------------
@@ -338,14 +373,14 @@ __global__ void __launch_bounds__(256) k_eam_energy(const float4* __restrict__ p
 __global__ void __launch_bounds__(kEamBlock) kb_eam_density(const BatchTable t) {
     const int k = batch_find(t.b128, t.nctx, blockIdx.x);
     const CtxDev& c = *t.d[k];
-    eam_density_body(c.pos4, c.nbr, c.nnbr, c.n, c.eam, c.D, c.grid.ncode, c.uxi, c.e_emb, c.flags,
+    eam_density_body(c.pos4, c.nbr, c.nnbr, c.n, c.eam, c.D, c.grid, c.uxi, c.e_emb, c.flags,
                      blockIdx.x - t.b128[k]);
 }
 
 __global__ void __launch_bounds__(kEamBlock) kb_eam_force(const BatchTable t) {
     const int k = batch_find(t.b128, t.nctx, blockIdx.x);
     const CtxDev& c = *t.d[k];
-    eam_force_body(c.pos4, c.nbr, c.nnbr, c.n, c.eam, c.D, c.grid.ncode, c.uxi, c.e_emb, c.w, c.f, c.e_eam,
+    eam_force_body(c.pos4, c.nbr, c.nnbr, c.n, c.eam, c.D, c.grid, c.uxi, c.e_emb, c.w, c.f, c.e_eam,
                    blockIdx.x - t.b128[k]);
 }
 
@@ -364,13 +399,13 @@ int launch_eam_energy(Ctx& c, cudaStream_t s, bool virial) {
 
 int launch_eam_density(Ctx& c, cudaStream_t s) {
     launch_pdl(k_eam_density, (c.n + kEamBlock - 1) / kEamBlock, kEamBlock, 0, s, c.pos4, c.nbr, c.nnbr, c.n, c.eam_d,
-               c.D, c.grid.ncode, c.uxi, c.e_emb, c.flags);
+               c.D, c.grid, c.uxi, c.e_emb, c.flags);
     return 1;
 }
 
 int launch_eam_force(Ctx& c, cudaStream_t s) {
     launch_pdl(k_eam_force, (c.n + kEamBlock - 1) / kEamBlock, kEamBlock, 0, s, c.pos4, c.nbr, c.nnbr, c.n, c.eam_d,
-               c.D, c.grid.ncode, c.uxi, c.e_emb, c.w, c.f, c.e_eam);
+               c.D, c.grid, c.uxi, c.e_emb, c.w, c.f, c.e_eam);
     return 1;
 }
 
