@@ -265,6 +265,7 @@ int launch_rebuild(Ctx& c, cudaStream_t s);          // wrap, bin, scan, scatter
 int launch_prepare(Ctx& c, cudaStream_t s);          // x_rel, weights, compaction
 int launch_build(Ctx& c, cudaStream_t s, int count_only);
 int launch_eam_density(Ctx& c, cudaStream_t s);
+int launch_eam_density_energy(Ctx& c, cudaStream_t s);  // + the compensated EAM energies (no virial)
 int launch_eam_force(Ctx& c, cudaStream_t s);
 int launch_ace_basis(Ctx& c, cudaStream_t s);        // A_nlm of the compacted atoms
 int launch_ace(Ctx& c, cudaStream_t s);              // products, densities, dE/dA

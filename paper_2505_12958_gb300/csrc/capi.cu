@@ -517,9 +517,10 @@ void run_forces_pre(ap_ctx* xc, cudaStream_t s, bool after_drift, bool eam_energ
         // ACE kernels on s read none of them
         cudaEventRecord(xc->fork_ev, s);
         cudaStreamWaitEvent(xc->side, xc->fork_ev, 0);
-        c.launches += ap::launch_eam_density(c, xc->side);
+        // with eam_energy the density pass also forms the compensated EAM energies (the bits
+        // of the on-request energy pass without the virial)
+        c.launches += eam_energy ? ap::launch_eam_density_energy(c, xc->side) : ap::launch_eam_density(c, xc->side);
         c.launches += ap::launch_eam_force(c, xc->side);
-        if (eam_energy) c.launches += ap::launch_eam_energy(c, xc->side, false);
         cudaEventRecord(xc->join_ev, xc->side);
     }
     stage(xc, AP_STAGE_ACE_BASIS, s, [&] { return ap::launch_ace_basis(c, s); });
