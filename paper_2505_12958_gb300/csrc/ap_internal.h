@@ -182,6 +182,7 @@ struct Ctx {
     int *cell = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cell_atoms = nullptr;
     int* nbr = nullptr;                                  // [cap][n]
     int* nbr_tmp = nullptr;                              // [n][cap]: hits of the staged list build
+    int* nbr_row = nullptr;                              // [n][cap]: nbr row by row (the warp-per-atom ACE kernels)
     int* nnbr = nullptr;
     int cap = 0;
     int* ace_list = nullptr;
@@ -308,7 +309,7 @@ struct CtxDev {
     double *e_emb, *e_eam, *w_fixed, *d_time;
     unsigned long long* acc;
     unsigned char* fixed;
-    int *cell, *cell_count, *cell_start, *cell_atoms, *nbr, *nnbr, *ace_list, *flags;
+    int *cell, *cell_count, *cell_start, *cell_atoms, *nbr, *nbr_row, *nnbr, *ace_list, *flags;
     long long* d_step;
     long long* load_ring;
     double* load_ring_t;

@@ -108,7 +108,7 @@ void fill_ctx_dev(const Ctx& c, CtxDev& d) {
     d.e_emb = c.e_emb; d.e_eam = c.e_eam; d.w_fixed = c.w_fixed; d.d_time = c.d_time;
     d.acc = c.acc; d.fixed = c.fixed;
     d.cell = c.cell; d.cell_count = c.cell_count; d.cell_start = c.cell_start; d.cell_atoms = c.cell_atoms;
-    d.nbr = c.nbr; d.nnbr = c.nnbr; d.ace_list = c.ace_list; d.flags = c.flags;
+    d.nbr = c.nbr; d.nbr_row = c.nbr_row; d.nnbr = c.nnbr; d.ace_list = c.ace_list; d.flags = c.flags;
     d.d_step = c.d_step; d.load_ring = c.load_ring; d.load_ring_t = c.load_ring_t;
     d.eam = c.eam_d; d.ace = c.ace_tc_d; d.D = c.D;
 }
@@ -367,7 +367,7 @@ void free_all(ap_ctx* xc) {
     ap::Ctx& c = xc->c;
     void* ps[] = {c.eam_d, c.D, c.Dlo, c.pos_lo, c.ace_A, c.ace_dA, c.x, c.v, c.xb, c.f, c.pos4, c.uxi, c.w, c.e_emb, c.e_eam, c.e_ace,
                   c.vir_eam, c.vir_ace, c.acc, c.fixed, c.w_fixed, c.cell, c.cell_count, c.cell_start,
-                  c.cell_atoms, c.nbr, c.nbr_tmp, c.nnbr, c.ace_list, c.flags, c.d_time, c.partials, c.totals, c.e_atom,
+                  c.cell_atoms, c.nbr, c.nbr_tmp, c.nbr_row, c.nnbr, c.ace_list, c.flags, c.d_time, c.partials, c.totals, c.e_atom,
                   c.pos_stage, c.f_stage, c.csp_sum, c.csp_under, c.csp_w0, c.csp_wnew, c.csp_seeds, c.csp_nseed,
                   c.thermo_group, c.nh_state, c.nh_partials, c.d_step, c.com, c.load_ring, c.load_ring_t};
     for (void* p : ps) {
@@ -574,7 +574,7 @@ ap_status read_flags(ap::Ctx& c, cudaStream_t s) {
         ap_status grown = AP_ERR_CAPACITY;
         {
             int cap = ((int)(need * 1.25) + 8 + 3) & ~3;
-            int *nb = nullptr, *nt = nullptr;
+            int *nb = nullptr, *nt = nullptr, *nr = nullptr;
             cudaError_t ea = injected_alloc_failure() ? cudaErrorMemoryAllocation
                                                       : cudaMallocAsync((void**)&nb, (size_t)cap * c.n * sizeof(int), c.stream);
             if (ea == cudaSuccess) {
@@ -582,11 +582,20 @@ ap_status read_flags(ap::Ctx& c, cudaStream_t s) {
                 if (ea != cudaSuccess) cudaFreeAsync(nb, c.stream);
             }
             if (ea == cudaSuccess) {
+                ea = cudaMallocAsync((void**)&nr, (size_t)cap * c.n * sizeof(int), c.stream);
+                if (ea != cudaSuccess) {
+                    cudaFreeAsync(nb, c.stream);
+                    cudaFreeAsync(nt, c.stream);
+                }
+            }
+            if (ea == cudaSuccess) {
                 cudaFreeAsync(c.nbr, c.stream);
                 cudaFreeAsync(c.nbr_tmp, c.stream);
-                c.dev_bytes += 2 * ((size_t)cap - (size_t)c.cap) * c.n * sizeof(int);
+                cudaFreeAsync(c.nbr_row, c.stream);
+                c.dev_bytes += 3 * ((size_t)cap - (size_t)c.cap) * c.n * sizeof(int);
                 c.nbr = nb;
                 c.nbr_tmp = nt;
+                c.nbr_row = nr;
                 c.cap = cap;
                 c.layout_gen += 1;
             } else {
@@ -634,7 +643,7 @@ size_t ap_footprint_bytes(const ap_potential* pot, int n_atoms, double ace_fract
     // per-atom arrays allocated by ap_init (and the host-transfer staging buffers)
     const size_t per_atom = 16 + 3 * 8 * 3 + 3 * 4 + 16 + 4 + 4 + 8 + 8 + 8 + 4 +
                             2 * sizeof(float) * ap::kNLM * ap::kNmax + 2 * 6 * 4 + 3 * 8 + 1 + 8 +
-                            4 + 4 + 4 + 4 + 8 + 3 * 8 + 3 * 4 + 2 * cap * 4;   // the list and the build's scratch
+                            4 + 4 + 4 + 4 + 8 + 3 * 8 + 3 * 4 + 3 * cap * 4;   // the list, its row copy, the build's scratch
     const size_t cells = 2 * sizeof(int) * ((size_t)n_atoms + 1);   // cell count/start (<= 1 per atom)
     const size_t nred = (size_t)(n_atoms + ap::kRedBlock - 1) / ap::kRedBlock + 1;
     return (size_t)n_atoms * per_atom + cells + nred * 10 * 8 + 2 * 125 * 16 + sizeof(ap::AceTc) + 512 +
@@ -856,7 +865,9 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
         int need = c.h_flags[ap::kFlagMaxNbr];
         c.cap = std::max(8, ((int)(need * 1.25) + 8 + 3) & ~3);
     }
-    if ((st = dalloc(c, &c.nbr, (size_t)c.cap * N)) || (st = dalloc(c, &c.nbr_tmp, (size_t)c.cap * N))) return fail(st);
+    if ((st = dalloc(c, &c.nbr, (size_t)c.cap * N)) || (st = dalloc(c, &c.nbr_tmp, (size_t)c.cap * N)) ||
+        (st = dalloc(c, &c.nbr_row, (size_t)c.cap * N)))
+        return fail(st);
     c.rebuilds = 0;
     *out = xc;
     return AP_OK;

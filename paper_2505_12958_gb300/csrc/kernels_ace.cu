@@ -239,13 +239,16 @@ __device__ __forceinline__ void fix_add(unsigned long long* p, float v) {
 }
 
 // neighbours of atom i inside the ACE cutoff, from the full list, into S (warp-uniform count;
-// returns -1 when there are more than kAceNbrCap)
+// returns -1 when there are more than kAceNbrCap).  The list is read from its row-major copy
+// nrow[i cap + k] (the same entries in the same order as the column-major list of the
+// thread-per-atom kernels): the lanes of a round read one row, a few cache lines, instead of
+// 32 rows of the column-major list.
 // U rounds of 32 list entries at a time: all their list loads, then all their position
 // gathers, then the compaction in list order (two dependent memory round trips per 32 U
 // entries); the neighbour order does not depend on U
 template <int U>
-__device__ __forceinline__ int gather_ace_neighbors(const float4* __restrict__ pos4, const int* __restrict__ nbr,
-                                                    int n, int i, int m, const float4* Ds, float rc2, float4* nb,
+__device__ __forceinline__ int gather_ace_neighbors(const float4* __restrict__ pos4, const int* __restrict__ nrow,
+                                                    int cap, int i, int m, const float4* Ds, float rc2, float4* nb,
                                                     int* nbj, int lane) {
     const float4 p = pos4[i];
     int cnt = 0;
@@ -254,7 +257,7 @@ __device__ __forceinline__ int gather_ace_neighbors(const float4* __restrict__ p
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int k = k0 + 32 * u + lane;
-            e[u] = k < m ? nbr[(size_t)k * n + i] : 0;
+            e[u] = k < m ? nrow[(size_t)i * cap + k] : 0;
         }
         float4 q[U];
 #pragma unroll
@@ -394,14 +397,14 @@ __device__ __forceinline__ float3 ace_pair_force(float4 v, float rc, float nrefi
 // cores (3xTF32 split, BF16 or FP16 inputs; FP32 accumulation), or FP64 accumulation.
 // the A_nlm of compacted atom a (stage a1), one warp; neighbour offsets Ds staged by the caller
 template <int MODE>
-__device__ __forceinline__ void basis_atom(const float4* __restrict__ pos4, const int* __restrict__ nbr,
-                                           const int* __restrict__ nnbr, int n, const float4* Ds, float rc,
+__device__ __forceinline__ void basis_atom(const float4* __restrict__ pos4, const int* __restrict__ nrow,
+                                           const int* __restrict__ nnbr, int cap, const float4* Ds, float rc,
                                            float nrefi, const int* __restrict__ ace_list, int* __restrict__ flags,
                                            float* __restrict__ Aout, int a, BasisSmem& S, int lane) {
     const int gq = lane >> 2, tq = lane & 3;
     const float rc2 = rc * rc;
     const int i = ace_list[a];
-    const int cnt = gather_ace_neighbors<1>(pos4, nbr, n, i, nnbr[i], Ds, rc2, S.nb, S.nbj, lane);
+    const int cnt = gather_ace_neighbors<1>(pos4, nrow, cap, i, nnbr[i], Ds, rc2, S.nb, S.nbj, lane);
     if (cnt < 0) {
         if (lane == 0) { atomicOr(&flags[kFlagErr], kErrAceCapacity); flags[kFlagBad] = i; }
         return;
@@ -501,8 +504,8 @@ __device__ __forceinline__ void basis_atom(const float4* __restrict__ pos4, cons
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(256) k_ace_basis(const float4* __restrict__ pos4, const int* __restrict__ nbr,
-                                                   const int* __restrict__ nnbr, int n, const float4* __restrict__ Dtab,
+__global__ void __launch_bounds__(256) k_ace_basis(const float4* __restrict__ pos4, const int* __restrict__ nrow,
+                                                   const int* __restrict__ nnbr, int cap, const float4* __restrict__ Dtab,
                                                    int ncode, const AceTc* __restrict__ tab,
                                                    const int* __restrict__ ace_list, int* __restrict__ flags,
                                                    float* __restrict__ Aout) {
@@ -516,7 +519,7 @@ __global__ void __launch_bounds__(256) k_ace_basis(const float4* __restrict__ po
     const float rc = tab->rc, nrefi = tab->nref_inv;
     const int n_ace = flags[kFlagNAce];
     for (int a = blockIdx.x * 8 + warp; a < n_ace; a += gridDim.x * 8) {
-        basis_atom<MODE>(pos4, nbr, nnbr, n, Ds, rc, nrefi, ace_list, flags, Aout, a, S, lane);
+        basis_atom<MODE>(pos4, nrow, nnbr, cap, Ds, rc, nrefi, ace_list, flags, Aout, a, S, lane);
     }
 }
 
@@ -1094,7 +1097,7 @@ struct ForceSmem {
 };
 
 // the pair forces of compacted atom a (stage a6), one warp; neighbour offsets Ds staged by the caller
-__device__ __forceinline__ void force_atom(const float4* __restrict__ pos4, const int* __restrict__ nbr,
+__device__ __forceinline__ void force_atom(const float4* __restrict__ pos4, const int* __restrict__ nrow, int cap,
                                            const int* __restrict__ nnbr, int n, const float4* Ds, float rc,
                                            float nrefi, const int* __restrict__ ace_list, const float* __restrict__ wv,
                                            const float* __restrict__ dAin, float* __restrict__ vir,
@@ -1105,7 +1108,7 @@ __device__ __forceinline__ void force_atom(const float4* __restrict__ pos4, cons
     const float4 da0 = dsrc[lane], da1 = lane < 2 * kNLM - 32 ? dsrc[32 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
     const int i = ace_list[a];
     const float wi = wv[i];
-    const int cnt = gather_ace_neighbors<4>(pos4, nbr, n, i, nnbr[i], Ds, rc2, S.nb, S.nbj, lane);
+    const int cnt = gather_ace_neighbors<4>(pos4, nrow, cap, i, nnbr[i], Ds, rc2, S.nb, S.nbj, lane);
     if (cnt < 0) return;
     reinterpret_cast<float4*>(&S.dAT[0][0])[lane] = da0;
     if (lane < 2 * kNLM - 32) reinterpret_cast<float4*>(&S.dAT[0][0])[32 + lane] = da1;
@@ -1141,8 +1144,8 @@ __device__ __forceinline__ void force_atom(const float4* __restrict__ pos4, cons
 
 
 // stage a6: f_ij = (1/nref) sum dE/dA_nlm grad(g_n Y_lm), scattered with weight w_i
-__global__ void __launch_bounds__(256) k_ace_force(const float4* __restrict__ pos4, const int* __restrict__ nbr,
-                                                   const int* __restrict__ nnbr, int n, const float4* __restrict__ Dtab,
+__global__ void __launch_bounds__(256) k_ace_force(const float4* __restrict__ pos4, const int* __restrict__ nrow,
+                                                   int cap, const int* __restrict__ nnbr, int n, const float4* __restrict__ Dtab,
                                                    int ncode, const AceTc* __restrict__ tab,
                                                    const int* __restrict__ ace_list, const float* __restrict__ wv,
                                                    int* __restrict__ flags, const float* __restrict__ dAin,
@@ -1157,7 +1160,7 @@ __global__ void __launch_bounds__(256) k_ace_force(const float4* __restrict__ po
     const float rc = tab->rc, nrefi = tab->nref_inv;
     const int n_ace = flags[kFlagNAce];
     for (int a = blockIdx.x * 8 + warp; a < n_ace; a += gridDim.x * 8) {
-        force_atom(pos4, nbr, nnbr, n, Ds, rc, nrefi, ace_list, wv, dAin, vir, acc, a, S, lane);
+        force_atom(pos4, nrow, cap, nnbr, n, Ds, rc, nrefi, ace_list, wv, dAin, vir, acc, a, S, lane);
     }
 }
 
@@ -1205,7 +1208,7 @@ __global__ void __launch_bounds__(256) kb_ace_basis(const BatchTable t) {
         }
         const int a = (ch - pre[k]) * 8 + warp;
         if (a < c.flags[kFlagNAce])
-            basis_atom<AP_ACE_FP32>(c.pos4, c.nbr, c.nnbr, c.n, Ds, c.ace->rc, c.ace->nref_inv, c.ace_list, c.flags,
+            basis_atom<AP_ACE_FP32>(c.pos4, c.nbr_row, c.nnbr, c.cap, Ds, c.ace->rc, c.ace->nref_inv, c.ace_list, c.flags,
                                     c.ace_A, a, WS[warp], lane);
     }
 }
@@ -1255,7 +1258,7 @@ __global__ void __launch_bounds__(256) kb_ace_force(const BatchTable t) {
         }
         const int a = (ch - pre[k]) * 8 + warp;
         if (a < c.flags[kFlagNAce])
-            force_atom(c.pos4, c.nbr, c.nnbr, c.n, Ds, c.ace->rc, c.ace->nref_inv, c.ace_list, c.w, c.ace_dA,
+            force_atom(c.pos4, c.nbr_row, c.cap, c.nnbr, c.n, Ds, c.ace->rc, c.ace->nref_inv, c.ace_list, c.w, c.ace_dA,
                        c.vir_ace, c.acc, a, WS[warp], lane);
     }
 }
@@ -1288,7 +1291,7 @@ int ace_grid(int persistent, int n, int atoms_per_block) {
 template <int MODE>
 void launch_basis_mode(Ctx& c, cudaStream_t s) {
     const int nb = ace_grid(persistent_blocks(k_ace_basis<MODE>, c.dev, 256, 0), c.n, 8);
-    launch_pdl(k_ace_basis<MODE>, nb, 256, 0, s, c.pos4, c.nbr, c.nnbr, c.n, c.D, c.grid.ncode, c.ace_tc_d, c.ace_list,
+    launch_pdl(k_ace_basis<MODE>, nb, 256, 0, s, c.pos4, c.nbr_row, c.nnbr, c.cap, c.D, c.grid.ncode, c.ace_tc_d, c.ace_list,
                c.flags, c.ace_A);
 }
 
@@ -1335,7 +1338,7 @@ int launch_batch_ace(const BatchTable& t, int dev, cudaStream_t s) {
 
 int launch_ace_force(Ctx& c, cudaStream_t s) {
     const int nb = ace_grid(persistent_blocks(k_ace_force, c.dev, 256, 0), c.n, 8);
-    launch_pdl(k_ace_force, nb, 256, 0, s, c.pos4, c.nbr, c.nnbr, c.n, c.D, c.grid.ncode, c.ace_tc_d, c.ace_list, c.w,
+    launch_pdl(k_ace_force, nb, 256, 0, s, c.pos4, c.nbr_row, c.cap, c.nnbr, c.n, c.D, c.grid.ncode, c.ace_tc_d, c.ace_list, c.w,
                c.flags, c.ace_dA, c.vir_ace, c.acc);
     return 1;
 }

@@ -289,7 +289,8 @@ __device__ __forceinline__ void load_codes(const GridDev& g, const float4* __res
 // count the band entries of atom i (pass 1), then place them (pass 2) from the band counters
 // band[b * bstride] of this thread; scan(visit) runs the cell scan.  Returns the entry count.
 template <class BT, class Scan>
-__device__ __forceinline__ int place_banded(int i, int n, int* __restrict__ nbr, int* __restrict__ nnbr, int cap,
+__device__ __forceinline__ int place_banded(int i, int n, int* __restrict__ nbr, int* __restrict__ nrow,
+                                            int* __restrict__ nnbr, int cap,
                                             int* __restrict__ flags, int count_only, BT* band, int bstride, Scan&& scan) {
     for (int b = 0; b < kBands; ++b) band[b * bstride] = 0;
     int cnt = 0;
@@ -304,7 +305,10 @@ __device__ __forceinline__ int place_banded(int i, int n, int* __restrict__ nbr,
         scan([&](int e, int b) {
             const int at = band[b * bstride];
             band[b * bstride] = (BT)(at + 1);
-            if (at < cap) nbr[(size_t)at * n + i] = e;
+            if (at < cap) {
+                nbr[(size_t)at * n + i] = e;
+                nrow[(size_t)i * cap + at] = e;
+            }
         });
         nnbr[i] = cnt < cap ? cnt : cap;
         if (cnt > cap) atomicOr(&flags[kFlagErr], kErrCapacity);
@@ -324,7 +328,7 @@ template <class BT>
 __device__ __forceinline__ int build_atom_global(int i, const float4* __restrict__ pos4, const int* __restrict__ cell,
                                                  int n, const GridDev& g, const float4* D, const char4* O,
                                                  const int* __restrict__ cell_start, const int* __restrict__ cell_atoms,
-                                                 int* __restrict__ nbr, int* __restrict__ nnbr, int cap,
+                                                 int* __restrict__ nbr, int* __restrict__ nrow, int* __restrict__ nnbr, int cap,
                                                  int* __restrict__ flags, int count_only, BT* band, int bstride) {
     const float4 p = pos4[i];
     int cc[3];
@@ -382,7 +386,7 @@ __device__ __forceinline__ int build_atom_global(int i, const float4* __restrict
             }
         }
     };
-    return place_banded(i, n, nbr, nnbr, cap, flags, count_only, band, bstride, scan);
+    return place_banded(i, n, nbr, nrow, nnbr, cap, flags, count_only, band, bstride, scan);
 }
 
 // thread per atom, atoms in index order (the batched launches)
@@ -390,8 +394,8 @@ __device__ __forceinline__ void build_body(const float4* __restrict__ pos4, cons
                                                        int n, const GridDev g, const float4* __restrict__ Dtab,
                                                        const int* __restrict__ cell_start,
                                                        const int* __restrict__ cell_atoms, int* __restrict__ nbr,
-                                                       int* __restrict__ nnbr, int cap, int* __restrict__ flags,
-                                                       int count_only, int bid) {
+                                                       int* __restrict__ nrow, int* __restrict__ nnbr, int cap,
+                                                       int* __restrict__ flags, int count_only, int bid) {
     pdl_wait();
     if (!count_only && flags[kFlagRebuild] == 0) return;
     __shared__ float4 D[125];
@@ -402,7 +406,7 @@ __device__ __forceinline__ void build_body(const float4* __restrict__ pos4, cons
     const int i = bid * blockDim.x + threadIdx.x;
     int cnt = 0;
     if (i < n)
-        cnt = build_atom_global(i, pos4, cell, n, g, D, O, cell_start, cell_atoms, nbr, nnbr, cap, flags, count_only,
+        cnt = build_atom_global(i, pos4, cell, n, g, D, O, cell_start, cell_atoms, nbr, nrow, nnbr, cap, flags, count_only,
                                 &band_at[0][threadIdx.x], kBuildBlock);
     max_nbr_warp(cnt, flags);
 }
@@ -411,9 +415,9 @@ __global__ void __launch_bounds__(kBuildBlock) k_build(const float4* __restrict_
                                                        int n, const GridDev g, const float4* __restrict__ Dtab,
                                                        const int* __restrict__ cell_start,
                                                        const int* __restrict__ cell_atoms, int* __restrict__ nbr,
-                                                       int* __restrict__ nnbr, int cap, int* __restrict__ flags,
-                                                       int count_only) {
-    build_body(pos4, cell, n, g, Dtab, cell_start, cell_atoms, nbr, nnbr, cap, flags, count_only, blockIdx.x);
+                                                       int* __restrict__ nrow, int* __restrict__ nnbr, int cap,
+                                                       int* __restrict__ flags, int count_only) {
+    build_body(pos4, cell, n, g, Dtab, cell_start, cell_atoms, nbr, nrow, nnbr, cap, flags, count_only, blockIdx.x);
 }
 
 // Staged build: one block per box of sb cells.  The block first copies the positions of every
@@ -432,7 +436,8 @@ __global__ void __launch_bounds__(kStBlock) k_build_staged(const float4* __restr
                                                           int n, const GridDev g, const float4* __restrict__ Dtab,
                                                           const int* __restrict__ cell_start,
                                                           const int* __restrict__ cell_atoms, int* __restrict__ nbr,
-                                                          int* __restrict__ tmp, int* __restrict__ nnbr, int cap,
+                                                          int* __restrict__ nrow, int* __restrict__ tmp,
+                                                          int* __restrict__ nnbr, int cap,
                                                           int* __restrict__ flags, int count_only, int3 sb, int3 nsb) {
     pdl_wait();
     if (!count_only && flags[kFlagRebuild] == 0) return;
@@ -590,7 +595,11 @@ __global__ void __launch_bounds__(kStBlock) k_build_staged(const float4* __restr
                         scan([&](int q, int code, int bb) {
                             const int at = band[bb][tid];
                             band[bb][tid] = (unsigned short)(at + 1);
-                            if (at < cap) nbr[(size_t)at * n + i] = __float_as_int(st[q].w) | (code << kNbrShift);
+                            if (at < cap) {
+                                const int e = __float_as_int(st[q].w) | (code << kNbrShift);
+                                nbr[(size_t)at * n + i] = e;
+                                nrow[(size_t)i * cap + at] = e;
+                            }
                         });
                     }
                     for (int k4 = 0; k4 < m && cnt <= cap; k4 += 4) {
@@ -603,7 +612,10 @@ __global__ void __launch_bounds__(kStBlock) k_build_staged(const float4* __restr
                             const int j = __float_as_int(st[v & 0xfff].w);
                             const int at = band[bb][tid];
                             band[bb][tid] = (unsigned short)(at + 1);
-                            if (at < cap) nbr[(size_t)at * n + i] = j | (code << kNbrShift);
+                            if (at < cap) {
+                                nbr[(size_t)at * n + i] = j | (code << kNbrShift);
+                                nrow[(size_t)i * cap + at] = j | (code << kNbrShift);
+                            }
                         }
                     }
                     nnbr[i] = m;
@@ -611,7 +623,7 @@ __global__ void __launch_bounds__(kStBlock) k_build_staged(const float4* __restr
                 }
             } else {
                 const int i = cell_atoms[cell_start[rgc[r0]] + (t - own_pre[oc])];
-                cnt = build_atom_global(i, pos4, cell, n, g, D, O, cell_start, cell_atoms, nbr, nnbr, cap, flags,
+                cnt = build_atom_global(i, pos4, cell, n, g, D, O, cell_start, cell_atoms, nbr, nrow, nnbr, cap, flags,
                                         count_only, &band[0][tid], kStBlock);
             }
         }
@@ -685,7 +697,8 @@ __global__ void kb_prepare(const BatchTable t) {
 __global__ void __launch_bounds__(kBuildBlock) kb_build(const BatchTable t) {
     int bid;
     const CtxDev& c = batch_ctx(t, t.b128, bid);
-    build_body(c.pos4, c.cell, c.n, c.grid, c.D, c.cell_start, c.cell_atoms, c.nbr, c.nnbr, c.cap, c.flags, 0, bid);
+    build_body(c.pos4, c.cell, c.n, c.grid, c.D, c.cell_start, c.cell_atoms, c.nbr, c.nbr_row, c.nnbr, c.cap, c.flags, 0,
+               bid);
 }
 
 }  // namespace
@@ -735,7 +748,7 @@ int launch_build(Ctx& c, cudaStream_t s, int count_only) {
     const int reg_min = (1 + 2 * c.grid.S[0]) * (1 + 2 * c.grid.S[1]) * (1 + 2 * c.grid.S[2]);
     if (reg_min > kStRegCap) {                       // (S = 2 on every axis) per-thread scan
         launch_pdl(k_build, (c.n + kBuildBlock - 1) / kBuildBlock, kBuildBlock, 0, s, c.pos4, c.cell, c.n, c.grid, c.D,
-                   c.cell_start, c.cell_atoms, c.nbr, c.nnbr, c.cap, c.flags, count_only);
+                   c.cell_start, c.cell_atoms, c.nbr, c.nbr_row, c.nnbr, c.cap, c.flags, count_only);
         return 1;
     }
     static int attr_dev = -1;
@@ -746,7 +759,7 @@ int launch_build(Ctx& c, cudaStream_t s, int count_only) {
     int3 sb, nsb;
     staged_boxes(c.grid, sb, nsb);
     launch_pdl(k_build_staged, nsb.x * nsb.y * nsb.z, kStBlock, kStCap * sizeof(float4), s, c.pos4, c.cell, c.n, c.grid,
-               c.D, c.cell_start, c.cell_atoms, c.nbr, c.nbr_tmp, c.nnbr, c.cap, c.flags, count_only, sb, nsb);
+               c.D, c.cell_start, c.cell_atoms, c.nbr, c.nbr_row, c.nbr_tmp, c.nnbr, c.cap, c.flags, count_only, sb, nsb);
     return 1;
 }
 
