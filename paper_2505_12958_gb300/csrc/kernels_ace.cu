@@ -283,6 +283,16 @@ __device__ __forceinline__ int gather_ace_neighbors(const float4* __restrict__ p
     return cnt > kAceNbrCap ? -1 : cnt;
 }
 
+// list rounds of 32 entries whose loads and gathers the basis kernel issues together, and
+// its minimum resident blocks per SM (tuning constants; results do not depend on them)
+#ifndef AP_BASIS_ROUNDS
+#define AP_BASIS_ROUNDS 2
+#endif
+#ifndef AP_BASIS_MINB
+#define AP_BASIS_MINB 1
+#endif
+constexpr int kBasisRounds = AP_BASIS_ROUNDS;
+
 struct BasisSmem {
     float4 nb[kAceNbrCap];
     int nbj[kAceNbrCap];
@@ -404,7 +414,7 @@ __device__ __forceinline__ void basis_atom(const float4* __restrict__ pos4, cons
     const int gq = lane >> 2, tq = lane & 3;
     const float rc2 = rc * rc;
     const int i = ace_list[a];
-    const int cnt = gather_ace_neighbors<1>(pos4, nrow, cap, i, nnbr[i], Ds, rc2, S.nb, S.nbj, lane);
+    const int cnt = gather_ace_neighbors<kBasisRounds>(pos4, nrow, cap, i, nnbr[i], Ds, rc2, S.nb, S.nbj, lane);
     if (cnt < 0) {
         if (lane == 0) { atomicOr(&flags[kFlagErr], kErrAceCapacity); flags[kFlagBad] = i; }
         return;
@@ -504,7 +514,13 @@ __device__ __forceinline__ void basis_atom(const float4* __restrict__ pos4, cons
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(256) k_ace_basis(const float4* __restrict__ pos4, const int* __restrict__ nrow,
+__global__ void
+#if AP_BASIS_MINB > 1
+__launch_bounds__(256, AP_BASIS_MINB)
+#else
+__launch_bounds__(256)
+#endif
+k_ace_basis(const float4* __restrict__ pos4, const int* __restrict__ nrow,
                                                    const int* __restrict__ nnbr, int cap, const float4* __restrict__ Dtab,
                                                    int ncode, const AceTc* __restrict__ tab,
                                                    const int* __restrict__ ace_list, int* __restrict__ flags,
