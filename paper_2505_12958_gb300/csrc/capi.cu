@@ -53,6 +53,9 @@ struct ap_ctx {
     // joined before the blend, beside the ACE basis, contraction and force kernels
     cudaStream_t side = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    // the contraction is done: with the energies of a host-buffer evaluation, the energy blend
+    // and its reduction run on the branch after it, beside the ACE force kernel
+    cudaEvent_t ace_ev = nullptr;
     const char* cap_where = "";                          // the capture call that failed
 };
 
@@ -379,7 +382,7 @@ void free_all(ap_ctx* xc) {
     xc->arena_bytes = 0;
     cudaStreamSynchronize(c.stream);
     if (xc->side) cudaStreamSynchronize(xc->side);
-    for (cudaEvent_t* e : {&xc->fork_ev, &xc->join_ev}) {
+    for (cudaEvent_t* e : {&xc->fork_ev, &xc->join_ev, &xc->ace_ev}) {
         if (*e) cudaEventDestroy(*e);
         *e = nullptr;
     }
@@ -521,7 +524,7 @@ void run_forces_pre(ap_ctx* xc, cudaStream_t s, bool after_drift, bool eam_energ
         // of the on-request energy pass without the virial)
         c.launches += eam_energy ? ap::launch_eam_density_energy(c, xc->side) : ap::launch_eam_density(c, xc->side);
         c.launches += ap::launch_eam_force(c, xc->side);
-        cudaEventRecord(xc->join_ev, xc->side);
+        if (!eam_energy) cudaEventRecord(xc->join_ev, xc->side);      // else after the energy blend
     }
     stage(xc, AP_STAGE_ACE_BASIS, s, [&] { return ap::launch_ace_basis(c, s); });
 }
@@ -539,6 +542,14 @@ void run_forces(ap_ctx* xc, cudaStream_t s, float* out_aos, bool after_drift = f
                 bool eam_energy = false) {
     run_forces_pre(xc, s, after_drift, eam_energy);
     stage(xc, AP_STAGE_ACE, s, [&] { return ap::launch_ace(xc->c, s); });
+    if (eam_energy && xc->c.prof != 1) {
+        // the energy blend reads E_i^ACE of the contraction and the branch's EAM energies, not
+        // the forces: it and the total's reduction run on the branch beside the ACE force kernel
+        cudaEventRecord(xc->ace_ev, s);
+        cudaStreamWaitEvent(xc->side, xc->ace_ev, 0);
+        xc->c.launches += ap::launch_energy_blend(xc->c, xc->side, false) + ap::launch_reduce(xc->c, xc->side, 0);
+        cudaEventRecord(xc->join_ev, xc->side);
+    }
     run_forces_post(xc, s, out_aos, kick_dt, after_drift);
 }
 
@@ -680,7 +691,8 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
     pool_setup(c.dev);
     if (cudaStreamCreateWithFlags(&xc->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&xc->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&xc->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&xc->join_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&xc->ace_ev, cudaEventDisableTiming) != cudaSuccess) {
         c.err = "stream or event creation failed";
         return fail(AP_ERR_CUDA);
     }
@@ -900,8 +912,7 @@ ap_status ap_compute_forces_host(ap_ctx* xc, const double* h_pos, float* h_force
         if (!xc->host_exec) {
             e = capture_graph(xc, s, &xc->host_exec, &xc->host_kernels, [&] {
                 if (h_pos) c.launches += ap::launch_pos_in(c, s, c.pos_stage);
-                run_forces(xc, s, c.f_stage, false, 0.0, h_energy != nullptr);
-                if (h_energy) c.launches += ap::launch_energy_blend(c, s, false) + ap::launch_reduce(c, s, 0);
+                run_forces(xc, s, c.f_stage, false, 0.0, h_energy != nullptr);   // with the energy blend
             });
             if (e != cudaSuccess) return graph_error(xc, e);
             xc->host_stream = s;
@@ -923,16 +934,15 @@ ap_status ap_compute_forces_host(ap_ctx* xc, const double* h_pos, float* h_force
         }
         // with every stage timed the EAM passes stay on s and the energy pass follows
         const bool branch_energy = h_energy && c.prof != 1;
-        run_forces(xc, s, c.f_stage, false, 0.0, branch_energy);
+        run_forces(xc, s, c.f_stage, false, 0.0, branch_energy);   // with the energy blend on the branch
         if (h_energy) {
             if (branch_energy) {                            // the total energy only
-                c.launches += ap::launch_energy_blend(c, s, false);
                 c.energy_fresh = true;
                 xc->energy_virial = false;
             } else {
                 ensure_energy(xc, s, false);
+                c.launches += ap::launch_reduce(c, s, 0);
             }
-            c.launches += ap::launch_reduce(c, s, 0);
         }
     }
     if (h_force) e = cudaMemcpyAsync(h_force, c.f_stage, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, s);
