@@ -177,7 +177,10 @@ ap_status ap_init(const ap_potential* pot, const ap_box* box, const ap_region* r
 ap_status ap_compute_forces(ap_ctx* ctx, const double* d_pos, float* d_force, void* stream);
 
 /* The same with host buffers: h_pos (n x 3 FP64) is copied in, h_force (n x 3 FP32)
- * and *h_energy (total energy) are copied out.  On a stream other than the legacy default
+ * and *h_energy (total energy) are copied out.  *h_energy is the e_pot + e_ind that a
+ * following ap_energy reports, bit for bit: the EAM density pass of this evaluation forms
+ * the same compensated per-atom energies as ap_energy's own pass (without the per-atom
+ * virial, which ap_energy then computes).  On a stream other than the legacy default
  * stream (profiling off) the kernels between the copies replay as one CUDA graph, captured
  * once per stream, buffer layout and choice of h_pos / h_energy.  Synchronises. */
 ap_status ap_compute_forces_host(ap_ctx* ctx, const double* h_pos, float* h_force,
