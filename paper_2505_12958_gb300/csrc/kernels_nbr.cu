@@ -2,7 +2,9 @@
 //
 // The neighbour list is a full list (each pair appears from both sides) within
 // r_list = max(EAM cutoff, ACE cutoff) + skin, stored column-major nbr[k * n + i]
-// so that thread-per-atom kernels read it coalesced.  An entry packs the neighbour
+// so that thread-per-atom kernels read it coalesced; the build also writes the same entries
+// row by row, nrow[i * cap + k], for the warp-per-atom ACE kernels, whose lanes then read
+// one atom's row (a few cache lines) instead of 32 rows.  An entry packs the neighbour
 // index j with the code of the cell offset o (per edge -S..S) it was found in; the
 // pair vector is then x_rel_j + D[code] - x_rel_i in FP32, where x_rel is the position
 // relative to the atom's own cell origin.  This keeps every FP32 operand below the
