@@ -200,6 +200,11 @@ class Server:
                     ev.record(a.stream)
                     a.events.append(ev)
                 self.passes += 1
+            elif not active and (queue or k_next == len(reqs)):
+                # every active request retired in this pass: admit the head of the queue now
+                # (it waited for room) instead of idling until the next arrival, or end the
+                # run when nothing is left to arrive
+                continue
             else:
                 # nothing to issue: wait for a completion or the next arrival
                 nxt = reqs[k_next]["arrival_s"] - (time.perf_counter() - t0) if k_next < len(reqs) else 1.0
