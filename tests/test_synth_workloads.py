@@ -67,3 +67,29 @@ def test_cu_precision_slab_recipe():
     assert c["fixed"].sum() == 3 * 2 * 100 * 100               # two atoms per cell per (001) layer
     _, n_ace = _region_counts(c)
     assert 0.045 < n_ace / len(c["x"]) < 0.055, n_ace          # the ACE hemisphere holds 5 %
+
+
+def test_strained_cell_recipe():
+    """Differentiation cells: BCC W, symmetric strain with entries in [-0.02, 0.02], about 1 %
+    vacancies, Gaussian noise sigma = 0.1 A about the strained lattice sites."""
+    for ncell, seed in ((4, 3), (8, 5), (12, 9)):
+        c = synth.configs.strained_w_cell(ncell, seed)
+        h = np.asarray(c["box"]["h"]).reshape(3, 3)
+        F = h.T / (ncell * 3.165)                                 # h = diag(L) F^T
+        e = F - np.eye(3)
+        assert np.allclose(e, e.T) and np.abs(e).max() <= 0.02
+        n0 = 2 * ncell ** 3
+        x = np.asarray(c["x"])
+        assert 0.95 * n0 <= len(x) <= n0 and tuple(c["box"]["periodic"]) == (1, 1, 1)
+        if ncell >= 8:
+            assert abs(1.0 - len(x) / n0 - 0.01) < 0.006            # about 1 % vacancies
+        # each atom lies within noise of a strained BCC site: in half-cell units of the
+        # unstrained lattice a site has three even or three odd coordinates
+        s = np.linalg.solve(F, x.T).T / (3.165 / 2)
+        site = np.round(s).astype(np.int64)
+        par = np.mod(site, 2)
+        assert np.all(par.min(axis=1) == par.max(axis=1))
+        assert len(np.unique(np.mod(site, 2 * ncell), axis=0)) == len(x)   # no site twice
+        noise = x - (site @ F.T) * (3.165 / 2)
+        if ncell >= 8:
+            assert abs(noise.std() - 0.1) < 0.01, noise.std()
